@@ -1,0 +1,389 @@
+"""FP64 CPU oracle for the reduced implicit-Euler Newton step -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline
+leg and ``--impl reference``) may import this package.  The product path never
+calls it; it shares no code with the CUDA library.
+
+It evaluates the plain definitions of every quantity in the paper's reduced
+system (Sec. 3, Eqs. 6-12; Sec. 5 cubature), in FP64, with exact hyper-dual
+derivatives of the decoder (``hyperdual.c``), and the Newton iteration with a
+dense LU solve (``numpy.linalg.solve``).
+
+Notation (r = latent size, N = 3V output DOFs, vertex-major x0,y0,z0,x1,...):
+  Delta = q - qbar,   z = Delta - dt*qbar_dot,   w = 3*Delta - dt*qbar_dot
+  J = dD/dq (N x r),  H = d2D/dq2,  S = d3D/dq3 (never formed in full)
+  HDD    = H[Delta, Delta]                    (f_fict = M HDD, Eq. 8)
+  Hqq    = H[qdot, qdot], qdot = Delta/dt     (the inertial term of Eq. 5)
+  dJ     = S[.,Delta,Delta] + H[., w]         (Eq. 12)
+  f_C    = sum_{e in C} w_e scatter(f_e)      (cubature force, Sec. 5)
+  phi    = J^T M (J z + HDD) + dt^2 (J^T f_C - J^T f_ext)        (Eq. 7, x dt^2 form)
+  a      = M (J z + HDD) + dt^2 (f_C - f_ext)
+  A      = a^T H + J^T M (J + dJ) + dt^2 K_r,  K_r = sum w_e J_e^T K_e J_e   (Eq. 11, n_p = 0)
+
+Readings of the paper taken here (each also listed in the design notes):
+  * Eq. 11 prints "- h^2 H^T (f_int - f_ext)"; differentiating Eq. 10 gives "+".
+    ``tests/test_oracle_pins.py`` pins A against central differences of phi.
+  * Eq. 11 is not symmetric in general (J^T M dJ is not), so the Newton step uses
+    LU with partial pivoting rather than the Cholesky the paper mentions.
+  * The paper does not specify a line search; backtracking (Armijo on |phi|^2,
+    c = 1e-4, step halving, at most 8 halvings) is used.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hyperdual.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+ACT = {"tanh": 0, "sin": 1, "linear": 2}
+MAT = {"stvk": 0, "neohookean": 1}
+
+
+def build(force=False):
+    """Compile hyperdual.c into oracle/_build/liboracle.so with gcc (+OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c99", "-fsigned-char",
+           _SRC, "-o", _LIB + ".tmp", "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        fpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_float))
+        L.orc_act_jet.argtypes = [ctypes.c_int, dp, dp]
+        L.orc_decoder_jets.argtypes = [ctypes.c_int, ip, fpp, fpp, ctypes.c_int, ctypes.c_int,
+                                       dp, ctypes.c_int, dp, dp, dp, ctypes.c_int, ip, dp]
+        L.orc_decoder_jets.restype = ctypes.c_int
+        L.orc_tets_fk.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, dp, dp, dp, ip]
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+class _DecoderView:
+    """Keeps the float32 weight arrays alive and exposes them as C pointer arrays."""
+
+    def __init__(self, dec):
+        self.dec = dec
+        self.W = [np.ascontiguousarray(w, dtype=np.float32) for w in dec.W]
+        self.b = [np.ascontiguousarray(x, dtype=np.float32) for x in dec.b]
+        fp = ctypes.POINTER(ctypes.c_float)
+        self.Wp = (fp * len(self.W))(*[w.ctypes.data_as(fp) for w in self.W])
+        self.bp = (fp * len(self.b))(*[x.ctypes.data_as(fp) for x in self.b])
+        self.widths = np.asarray(dec.widths, dtype=np.int32)
+
+
+_views = {}
+
+
+def _view(dec):
+    v = _views.get(id(dec))
+    if v is None or v.dec is not dec:
+        v = _DecoderView(dec)
+        _views[id(dec)] = v
+    return v
+
+
+# ----------------------------------------------------------------- decoder --
+
+def act_jet(act, x8):
+    """Activation applied to one 8-component hyper-dual jet."""
+    x8 = np.ascontiguousarray(x8, dtype=np.float64)
+    out = np.zeros(8)
+    lib().orc_act_jet(ACT[act], _dp(x8), _dp(out))
+    return out
+
+
+def decoder_jets(dec, q, s1=None, s2=None, s3=None, rows=None, n_run=None):
+    """Jets of D(q + e1 s1 + e2 s2 + e3 s3).
+
+    s1, s2, s3: None, (r,) or (n_seed, r) seed directions.  Returns an array of
+    shape (n_seed, n_rows, 8) with components [u, D[s1], D[s2], D2[s1,s2], D[s3],
+    D2[s1,s3], D2[s2,s3], D3[s1,s2,s3]] (or the hidden activations after
+    ``n_run`` layers when n_run < number of layers).
+    """
+    v = _view(dec)
+    L = len(dec.W)
+    r = dec.r
+    n_run = L if n_run is None else n_run
+    seeds = [s for s in (s1, s2, s3) if s is not None]
+    n_seed = max([np.atleast_2d(s).shape[0] for s in seeds], default=1)
+
+    def prep(s):
+        if s is None:
+            return None
+        s = np.atleast_2d(np.asarray(s, dtype=np.float64))
+        if s.shape[0] == 1 and n_seed > 1:
+            s = np.repeat(s, n_seed, 0)
+        assert s.shape == (n_seed, r)
+        return np.ascontiguousarray(s)
+
+    S1, S2, S3 = prep(s1), prep(s2), prep(s3)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if n_run == L and rows is not None:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        n_rows = rows.size
+        rp = _ip(rows)
+    else:
+        rows = None
+        n_rows = dec.widths[n_run]
+        rp = None
+    out = np.zeros((n_seed, n_rows, 8))
+    nul = ctypes.POINTER(ctypes.c_double)()
+    st = lib().orc_decoder_jets(L, _ip(v.widths), v.Wp, v.bp, ACT[dec.act], n_run, _dp(q),
+                                n_seed, _dp(S1) if S1 is not None else nul,
+                                _dp(S2) if S2 is not None else nul,
+                                _dp(S3) if S3 is not None else nul, n_rows, rp, _dp(out))
+    if st != 0:
+        raise RuntimeError("orc_decoder_jets failed: %d" % st)
+    return out
+
+
+def decode(dec, q, rows=None):
+    """u = D(q) (FP64)."""
+    return decoder_jets(dec, q, rows=rows)[0, :, 0]
+
+
+def derivs(dec, q, qbar, qbar_dot, dt, rows=None):
+    """All first-, second- and third-order quantities of the decoder at q.
+
+    Returns dict with u (N), J (N,r), HDe (N,r) = H[Delta, e_j], Hw (N,r) = H[w, e_j],
+    Sdd (N,r) = S[e_j, Delta, Delta], dJ = Sdd + Hw (Eq. 12), HDD (N) = H[Delta,Delta],
+    Hqq (N) = H[qdot,qdot] with qdot = Delta/dt.
+    """
+    r = dec.r
+    q = np.asarray(q, np.float64)
+    D = q - qbar
+    w = 3.0 * D - dt * qbar_dot
+    E = np.eye(r)
+    # job j: seeds (e_j, Delta, Delta) -> [1]=J e_j, [3]=H[e_j,D], [6]=H[D,D], [7]=S[e_j,D,D]
+    j1 = decoder_jets(dec, q, E, D, D, rows=rows)
+    # job j: seeds (e_j, w) -> [3]=H[e_j,w]
+    j2 = decoder_jets(dec, q, E, w, None, rows=rows)
+    u = j1[0, :, 0]
+    J = j1[:, :, 1].T.copy()
+    HDe = j1[:, :, 3].T.copy()
+    Sdd = j1[:, :, 7].T.copy()
+    Hw = j2[:, :, 3].T.copy()
+    HDD = j1[0, :, 6].copy()
+    return dict(u=u, J=J, HDe=HDe, Hw=Hw, Sdd=Sdd, dJ=Sdd + Hw, HDD=HDD, Hqq=HDD / dt ** 2)
+
+
+def aTH(dec, q, a):
+    """(a^T H)[i,j] = sum_n a_n H[n,i,j]: the plain definition, one second-order
+    jet per pair (i <= j) over all N outputs."""
+    r = dec.r
+    E = np.eye(r)
+    I, Jx = np.triu_indices(r)
+    jets = decoder_jets(dec, q, E[I], E[Jx])          # (npairs, N, 8)
+    vals = jets[:, :, 3] @ np.asarray(a, np.float64)
+    out = np.zeros((r, r))
+    out[I, Jx] = vals
+    out[Jx, I] = vals
+    return out
+
+
+def aTH_regrouped(dec, q, a):
+    """Same contraction for large decoders: with a linear output layer,
+    sum_n a_n H[n,i,j] = (W_L^T a) . d2h_{L-1}[e_i,e_j] where h_{L-1} is the last
+    hidden activation (associativity of the output layer's sum).  Pinned against
+    ``aTH`` in the tests."""
+    r = dec.r
+    L = len(dec.W)
+    E = np.eye(r)
+    I, Jx = np.triu_indices(r)
+    v = dec.W[L - 1].astype(np.float64).T @ np.asarray(a, np.float64)
+    jets = decoder_jets(dec, q, E[I], E[Jx], n_run=L - 1)   # (npairs, K, 8)
+    vals = jets[:, :, 3] @ v
+    out = np.zeros((r, r))
+    out[I, Jx] = vals
+    out[Jx, I] = vals
+    return out
+
+
+# -------------------------------------------------------------------- FEM --
+
+def lame(E, nu):
+    mu = E / (2.0 * (1.0 + nu))
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    return mu, lam
+
+
+def tets_fk(mesh, u, tet_ids, want_K=True):
+    """Energy, force and stiffness of the listed tets at displacement u (FP64)."""
+    tet_ids = np.asarray(tet_ids, dtype=np.int64)
+    n = tet_ids.size
+    T = mesh.tets[tet_ids]                                # (n,4)
+    X = mesh.X[T].reshape(n, 12)
+    x = X + np.asarray(u, np.float64).reshape(-1, 3)[T].reshape(n, 12)
+    X = np.ascontiguousarray(X)
+    x = np.ascontiguousarray(x)
+    mu, lam = lame(mesh.E, mesh.nu)
+    en = np.zeros(n)
+    f = np.zeros((n, 12))
+    K = np.zeros((n, 144)) if want_K else None
+    st = np.zeros(n, dtype=np.int32)
+    lib().orc_tets_fk(n, _dp(X), _dp(x), MAT[mesh.material], mu, lam, _dp(en), _dp(f),
+                      _dp(K) if want_K else ctypes.POINTER(ctypes.c_double)(), _ip(st))
+    return en, f, (K.reshape(n, 12, 12) if want_K else None), st
+
+
+def tet_dofs(mesh, tet_ids):
+    T = mesh.tets[np.asarray(tet_ids, dtype=np.int64)]
+    return (3 * T[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
+
+
+def mass_diag(mesh):
+    return np.repeat(mesh.vmass, 3)
+
+
+# --------------------------------------------------------- reduced system --
+
+class Inverted(RuntimeError):
+    pass
+
+
+def reduced_system(wl, q, qbar=None, qbar_dot=None, dt=None, cub_w=None, aH="auto"):
+    """phi (r), A (r x r), elastic cubature energy and intermediates at q.
+
+    Follows Eq. 7/8 (phi, multiplied through by dt^2 as in Eq. 10) and Eq. 11
+    with n_p = 0 (A), Eq. 12 (dJ), and the cubature sums of Sec. 5.
+    """
+    dec, mesh = wl.dec, wl.mesh
+    st = wl.state
+    qbar = st.qbar if qbar is None else qbar
+    qbar_dot = st.qbar_dot if qbar_dot is None else qbar_dot
+    dt = st.dt if dt is None else dt
+    cw = np.asarray(wl.cub_w if cub_w is None else cub_w, np.float64)
+    q = np.asarray(q, np.float64)
+    D = q - qbar
+    z = D - dt * qbar_dot
+    d = derivs(dec, q, qbar, qbar_dot, dt)
+    J, HDD, dJ, u = d["J"], d["HDD"], d["dJ"], d["u"]
+    Mdiag = mass_diag(mesh)
+    fext = np.asarray(wl.f_ext, np.float64)
+    # cubature: f_e, K_e at the deformed cubature tets
+    en, fe, Ke, stat = tets_fk(mesh, u, wl.cub_tets)
+    if np.any(stat == -7):
+        raise Inverted("inverted cubature tet")
+    dofs = tet_dofs(mesh, wl.cub_tets)                    # (C,12)
+    fC = np.zeros(dec.n_out)
+    np.add.at(fC, dofs.reshape(-1), (cw[:, None] * fe).reshape(-1))
+    Je = J[dofs]                                          # (C,12,r)
+    Kr = np.einsum("e,eai,eab,ebj->ij", cw, Je, Ke, Je)
+    energy = float(np.sum(cw * en))
+    y = J @ z + HDD
+    phi = J.T @ (Mdiag * y) + dt ** 2 * (J.T @ fC - J.T @ fext)
+    a = Mdiag * y + dt ** 2 * (fC - fext)
+    if aH == "auto":
+        aH = "plain" if dec.n_params < 20_000_000 else "regrouped"
+    aHm = aTH(dec, q, a) if aH == "plain" else aTH_regrouped(dec, q, a)
+    Mr = J.T @ (Mdiag[:, None] * J)
+    B = J.T @ (Mdiag[:, None] * dJ)
+    A = aHm + Mr + B + dt ** 2 * Kr
+    return dict(phi=phi, A=A, energy=energy, a=a, aH=aHm, Mr=Mr, B=B, Kr=Kr, fC=fC,
+                g_int=J.T @ fC, **d)
+
+
+def phi_only(wl, q, qbar=None, qbar_dot=None, dt=None, cub_w=None):
+    """phi alone (no second-order terms beyond H[Delta,Delta]); used by the
+    line search and by the finite-difference pin of A."""
+    dec, mesh = wl.dec, wl.mesh
+    st = wl.state
+    qbar = st.qbar if qbar is None else qbar
+    qbar_dot = st.qbar_dot if qbar_dot is None else qbar_dot
+    dt = st.dt if dt is None else dt
+    cw = np.asarray(wl.cub_w if cub_w is None else cub_w, np.float64)
+    q = np.asarray(q, np.float64)
+    D = q - qbar
+    z = D - dt * qbar_dot
+    r = dec.r
+    j1 = decoder_jets(dec, q, np.eye(r), D, D)
+    u = j1[0, :, 0]
+    J = j1[:, :, 1].T
+    HDD = j1[0, :, 6]
+    en, fe, _, stat = tets_fk(mesh, u, wl.cub_tets, want_K=False)
+    if np.any(stat == -7):
+        raise Inverted("inverted cubature tet")
+    dofs = tet_dofs(mesh, wl.cub_tets)
+    fC = np.zeros(dec.n_out)
+    np.add.at(fC, dofs.reshape(-1), (cw[:, None] * fe).reshape(-1))
+    Mdiag = mass_diag(mesh)
+    y = J @ z + HDD
+    fext = np.asarray(wl.f_ext, np.float64)
+    return J.T @ (Mdiag * y) + dt ** 2 * (J.T @ fC - J.T @ fext)
+
+
+def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvings=8,
+                 cub_w=None, qbar=None, qbar_dot=None, dt=None):
+    """Implicit-Euler Newton iteration on phi(q) = 0 (Eq. 7) with A from Eq. 11.
+
+    Each iteration solves A delta = -phi (LU, partial pivoting) and backtracks
+    on |phi|^2 (Armijo).  Stops when |phi| <= tol * max(1, |phi_0|).
+    Returns (q, report dict).
+    """
+    st = wl.state
+    qbar = st.qbar if qbar is None else qbar
+    qbar_dot = st.qbar_dot if qbar_dot is None else qbar_dot
+    dt = st.dt if dt is None else dt
+    q = (qbar + dt * qbar_dot) if q0 is None else np.asarray(q0, np.float64).copy()
+    max_iter = wl.max_iter if max_iter is None else max_iter
+    kw = dict(qbar=qbar, qbar_dot=qbar_dot, dt=dt, cub_w=cub_w)
+    rs = reduced_system(wl, q, **kw)
+    phi0 = np.linalg.norm(rs["phi"])
+    hist = [phi0]
+    it = 0
+    converged = phi0 <= tol * max(1.0, phi0)
+    while not converged and it < max_iter:
+        delta = np.linalg.solve(rs["A"], -rs["phi"])
+        m0 = float(rs["phi"] @ rs["phi"])
+        alpha = 1.0
+        for _ in range(max_halvings + 1):
+            qt = q + alpha * delta
+            try:
+                rt = reduced_system(wl, qt, **kw)
+                mt = float(rt["phi"] @ rt["phi"])
+                ok = mt <= (1.0 - 2.0 * c_armijo * alpha) * m0
+            except Inverted:
+                ok = False
+            if ok:
+                break
+            alpha *= 0.5
+        else:
+            break
+        q, rs = qt, rt
+        it += 1
+        hist.append(float(np.linalg.norm(rs["phi"])))
+        converged = hist[-1] <= tol * max(1.0, phi0)
+    return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs,
+                   qdot=(q - qbar) / dt)

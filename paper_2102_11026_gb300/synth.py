@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module only draws random numbers and builds input structure (decoder
+weights, a regular tet grid, lumped masses, cubature sets, latent states).  It
+holds none of the method's arithmetic: no decoder evaluation, no derivatives,
+no forces.  Both the CUDA library and the FP64 oracle consume the arrays it
+returns, so neither side depends on the other.
+
+Workloads (the paper ships no meshes or trained decoders, so these stand in):
+
+* ``small``  -- latent r=5, widths 5-64-256-1024-3000 (1000 vertices on a
+  10x10x10 grid, 3645 tets), tanh, StVK E=1e5 nu=0.4, 64 cubature tets.
+* ``paper``  -- latent r=30, ten layers 30-128-256-512-1024-2048-2048-2048-
+  4096-4096-60000 (20x20x50 grid, 88445 tets), tanh, Neo-Hookean E=5e5
+  nu=0.45, 500 cubature tets, gravity.  Decoder depth ("10+ layers", Sec. 1),
+  latent size ("below a couple of dozens", Sec. 3.5) and cubature counts
+  (Table 2: 100-11400) follow the paper's reported scale.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+GRAVITY = 9.81
+
+
+@dataclasses.dataclass
+class Decoder:
+    widths: list            # [r, n_1, ..., N]
+    W: list                 # W[l]: float32 (n_out, n_in), row-major
+    b: list                 # b[l]: float32 (n_out,)
+    act: str = "tanh"       # hidden activation: tanh | sin | linear
+
+    @property
+    def r(self):
+        return self.widths[0]
+
+    @property
+    def n_out(self):
+        return self.widths[-1]
+
+    @property
+    def n_params(self):
+        return sum(w.size for w in self.W)
+
+
+@dataclasses.dataclass
+class Mesh:
+    X: np.ndarray           # float64 (V, 3) rest positions
+    tets: np.ndarray        # int32 (T, 4), positively oriented
+    vmass: np.ndarray       # float64 (V,) lumped vertex masses
+    material: str = "stvk"  # stvk | neohookean
+    E: float = 1e5
+    nu: float = 0.4
+
+    @property
+    def n_vert(self):
+        return self.X.shape[0]
+
+    @property
+    def n_tet(self):
+        return self.tets.shape[0]
+
+
+@dataclasses.dataclass
+class State:
+    qbar: np.ndarray        # float64 (r,)
+    qbar_dot: np.ndarray    # float64 (r,)
+    dt: float = 1.0 / 60.0
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dec: Decoder
+    mesh: Mesh
+    cub_tets: np.ndarray    # int32 (C,) distinct tet indices
+    cub_w: np.ndarray       # float32 (C,) weights in [0.5, 2]
+    state: State
+    f_ext: np.ndarray       # float32 (N,) external force (zeros or gravity)
+    max_iter: int = 5
+
+
+def make_decoder(widths, seed, act="tanh", out_scale=0.1):
+    """Xavier-normal weights, U(+-1/sqrt(fan_in)) biases; the output layer is
+    scaled by ``out_scale`` so decoded displacements stay a fraction of the
+    grid spacing (1.0) and no tet inverts."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W, b = [], []
+    L = len(widths) - 1
+    for l in range(L):
+        n_in, n_out = widths[l], widths[l + 1]
+        std = np.sqrt(2.0 / (n_in + n_out))
+        w = rng.standard_normal((n_out, n_in), dtype=np.float32) * np.float32(std)
+        bb = rng.uniform(-1.0, 1.0, n_out).astype(np.float32) / np.float32(np.sqrt(n_in))
+        if l == L - 1:
+            w *= np.float32(out_scale)
+            bb *= np.float32(out_scale)
+        W.append(np.ascontiguousarray(w))
+        b.append(np.ascontiguousarray(bb))
+    return Decoder(list(widths), W, b, act)
+
+
+def make_grid_mesh(nx, ny, nz, seed, material="stvk", E=1e5, nu=0.4, spacing=1.0):
+    """Regular vertex grid (nx*ny*nz vertices, spacing 1, origin 0), five tets
+    per cube alternating with the parity of (i+j+k), positive orientation,
+    lumped masses uniform in [0.5, 1.5]."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    X = np.stack([ii, jj, kk], -1).reshape(-1, 3).astype(np.float64) * spacing
+
+    def vid(i, j, k):
+        return (i * ny + j) * nz + k
+
+    tets = []
+    for i in range(nx - 1):
+        for j in range(ny - 1):
+            for k in range(nz - 1):
+                def v(o):
+                    return vid(i + o[0], j + o[1], k + o[2])
+                par = (i + j + k) & 1
+                cen = [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+                oth = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)]
+                if par:
+                    cen, oth = oth, cen
+                tets.append([v(o) for o in cen])
+                for corner in oth:
+                    nb = [o for o in cen if sum(abs(a - b) for a, b in zip(o, corner)) == 1]
+                    tets.append([v(corner)] + [v(o) for o in nb])
+    tets = np.asarray(tets, dtype=np.int32)
+    # orient: det[x1-x0, x2-x0, x3-x0] > 0
+    P = X[tets]
+    D = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], -1)
+    neg = np.linalg.det(D) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    vmass = rng.uniform(0.5, 1.5, X.shape[0])
+    return Mesh(X, np.ascontiguousarray(tets), vmass, material, E, nu)
+
+
+def make_cubature(n_tet, n_cub, seed, frame=0):
+    """Distinct seeded cubature tets (fixed per workload) and weights uniform in
+    [0.5, 2] (redrawn per frame: the frame index enters the weight stream)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    idx = np.sort(rng.choice(n_tet, size=n_cub, replace=False)).astype(np.int32)
+    wrng = np.random.Generator(np.random.PCG64([seed + 1299709, frame]))
+    w = wrng.uniform(0.5, 2.0, n_cub).astype(np.float32)
+    return idx, w
+
+
+def make_state(r, seed, dt=1.0 / 60.0):
+    rng = np.random.Generator(np.random.PCG64(seed + 15485863))
+    return State(rng.normal(0.0, 0.5, r), rng.normal(0.0, 0.1, r), dt)
+
+
+def gravity_force(vmass):
+    f = np.zeros((vmass.shape[0], 3), dtype=np.float64)
+    f[:, 1] = -GRAVITY * vmass
+    return f.reshape(-1).astype(np.float32)
+
+
+SMALL_WIDTHS = [5, 64, 256, 1024, 3000]
+PAPER_WIDTHS = [30, 128, 256, 512, 1024, 2048, 2048, 2048, 4096, 4096, 60000]
+
+
+def small(seed=1, act="tanh"):
+    """Latent 5, 1000-vertex grid, StVK, 64 cubature tets, no external force."""
+    dec = make_decoder(SMALL_WIDTHS, seed, act)
+    mesh = make_grid_mesh(10, 10, 10, seed, "stvk", 1e5, 0.4)
+    cub, w = make_cubature(mesh.n_tet, 64, seed)
+    st = make_state(dec.r, seed)
+    return Workload("small", dec, mesh, cub, w, st, np.zeros(dec.n_out, np.float32))
+
+
+def paper(seed=2, act="tanh"):
+    """Latent 30, ten-layer decoder onto a 20000-vertex grid, Neo-Hookean,
+    500 cubature tets, gravity."""
+    dec = make_decoder(PAPER_WIDTHS, seed, act)
+    mesh = make_grid_mesh(20, 20, 50, seed, "neohookean", 5e5, 0.45)
+    cub, w = make_cubature(mesh.n_tet, 500, seed)
+    st = make_state(dec.r, seed)
+    return Workload("paper", dec, mesh, cub, w, st, gravity_force(mesh.vmass))
+
+
+def custom(widths, grid, n_cub, seed, act="tanh", material="stvk", E=1e5, nu=0.4,
+           gravity=False):
+    """Arbitrary-shape workload for parity sweeps; ``widths[-1]`` must equal
+    3 * prod(grid)."""
+    assert widths[-1] == 3 * grid[0] * grid[1] * grid[2]
+    dec = make_decoder(widths, seed, act)
+    mesh = make_grid_mesh(*grid, seed, material, E, nu)
+    cub, w = make_cubature(mesh.n_tet, min(n_cub, mesh.n_tet), seed)
+    st = make_state(dec.r, seed)
+    f = gravity_force(mesh.vmass) if gravity else np.zeros(dec.n_out, np.float32)
+    return Workload("custom", dec, mesh, cub, w, st, f)
+
+
+def newton_start(state):
+    """Initial Newton iterate q0 = qbar + dt * qbar_dot (so (q0-qbar)/dt = qbar_dot)."""
+    return state.qbar + state.dt * state.qbar_dot
