@@ -1,0 +1,236 @@
+/*
+ * dae.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * "High-order Differentiable Autoencoder for Nonlinear Model Reduction"
+ * (Shen et al., arXiv 2102.11026).
+ *
+ * What the library computes, per call, for a fully connected decoder
+ * u = D(q) (Sec. 3.5, Fig. 3; hidden activation tanh, sin or none, linear output
+ * layer) and a tetrahedral mesh with lumped diagonal mass M (Sec. 3.1, Eq. 1):
+ *
+ *   Delta = q - qbar,  z = Delta - dt*qbar_dot,  w = 3*Delta - dt*qbar_dot
+ *   u = D(q),  J = dD/dq (Eq. 4),  H[qdot,qdot] with qdot = Delta/dt (Eq. 5),
+ *   dJ = S[.,Delta,Delta] + H[., w]                                   (Eq. 12)
+ *   phi = J^T M (J z + H[Delta,Delta]) + dt^2 J^T (f_C - f_ext)        (Eqs. 7-8)
+ *   A   = a^T H + J^T M (J + dJ) + dt^2 sum_{e in C} w_e J_e^T K_e J_e  (Eq. 11, n_p = 0)
+ *   a   = M (J z + H[Delta,Delta]) + dt^2 (f_C - f_ext)
+ *   f_C = sum_{e in C} w_e f_e(u)   (cubature force, Sec. 5)
+ *
+ * and the reduced implicit-Euler Newton step A delta = -phi with a backtracking
+ * line search.  The right contractions (J, H[Delta,.], dJ, H[Delta,Delta]) come
+ * from one stacked complex-step forward pass (Sec. 4.3, Eqs. 16-17); a^T H comes
+ * from complex-step backpropagation (Sec. 4.4).  Eq. 11 is evaluated with a "+"
+ * sign on the dt^2 H^T (f_int - f_ext) term (the derivative of Eq. 10; the paper
+ * prints "-").
+ *
+ * Conventions
+ *   - Layouts: decoder weights W_l are row-major (n_out x n_in); displacement-like
+ *     vectors have N = 3V entries, vertex-major (x0,y0,z0,x1,...); N x r matrices
+ *     (J, dJ, ...) are column-major (column j = derivative along e_j, contiguous);
+ *     r x r matrices are column-major.  q-like vectors are FP64, decoder outputs FP32.
+ *   - Residency: every array argument may be host or device memory; the library
+ *     detects which with cudaPointerGetAttributes.  Host inputs are copied to the
+ *     device, host outputs are copied back and the call then synchronizes the
+ *     context's stream.  With device-only arguments a call only enqueues work on
+ *     the context's stream (except where noted) and returns.
+ *   - Ownership: the caller owns every buffer it passes; the library owns
+ *     contexts, decoders and meshes until the matching dae_destroy / dae_free_*.
+ *   - Errors: functions return a dae_status and never abort; the message of the
+ *     most recent failure on a context is available from dae_last_error.  Errors
+ *     raised on the device (non-finite values, inverted tets, bounded waits that
+ *     gave up) are recorded in a device status word and reported by the next
+ *     call that synchronizes (dae_sync, or any call with host outputs).
+ *   - Threads: contexts are independent; one context must not be used from two
+ *     host threads at once.
+ */
+#ifndef DAE_H
+#define DAE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dae_ctx dae_ctx;
+typedef struct dae_decoder dae_decoder;
+typedef struct dae_mesh dae_mesh;
+
+typedef enum {
+    DAE_OK = 0,
+    DAE_ERR_INVALID_ARG = -1,
+    DAE_ERR_CUDA = -2,
+    DAE_ERR_OOM = -3,
+    DAE_ERR_NOT_CONVERGED = -4,
+    DAE_ERR_NONFINITE = -5,
+    DAE_ERR_SINGULAR = -6,
+    DAE_ERR_INVERTED = -7,
+    DAE_ERR_TIMEOUT = -8,
+    DAE_ERR_UNSUPPORTED = -9
+} dae_status;
+
+/* Hidden-layer activation.  The paper uses sin (Sec. 3.5); tanh is the default
+ * of the synthetic workloads; LINEAR makes D affine (H = S = 0). */
+typedef enum { DAE_ACT_TANH = 0, DAE_ACT_SIN = 1, DAE_ACT_LINEAR = 2 } dae_act;
+
+/* Arithmetic of the decoder GEMMs (accumulation is always FP32):
+ *   FP32    CUDA-core FFMA tiles
+ *   TF32    tcgen05 kind::tf32 tensor cores
+ *   BF16    tcgen05 kind::f16 with BF16 operands
+ *   BF16X3  three BF16 products (hi*hi + hi*lo + lo*hi) per split operand pair */
+typedef enum { DAE_FP32 = 0, DAE_TF32 = 1, DAE_BF16 = 2, DAE_BF16X3 = 3 } dae_prec;
+
+/* Constitutive law of the tets (Sec. 5 names StVK; Neo-Hookean is the second
+ * law the synthetic workloads use). */
+typedef enum { DAE_STVK = 0, DAE_NEOHOOKEAN = 1 } dae_material;
+
+/* Newton options (dae_default_newton_opts fills the defaults shown). */
+typedef struct {
+    int max_iter;        /* Newton updates per frame (5) */
+    int max_evals;       /* evaluation budget per frame incl. backtracking (max_iter + 3) */
+    int max_halvings;    /* step halvings per line search (8) */
+    double tol;          /* stop when |phi| <= tol * max(1, |phi_0|)  (1e-8) */
+    double c_armijo;     /* |phi(alpha)|^2 <= (1 - 2 c alpha) |phi|^2  (1e-4) */
+    double h_cs;         /* complex-step size; a power of two keeps the scaling exact (2^-20) */
+} dae_newton_opts;
+
+/* Per-frame outcome of dae_newton_step / dae_rollout. */
+typedef struct {
+    int iters;           /* accepted Newton updates */
+    int evals;           /* full evaluations (derivatives + cubature + assembly) */
+    int converged;       /* 1 if |phi| reached tol */
+    int status;          /* dae_status of the frame (device-side errors included) */
+    double phi_norm0;    /* |phi| at the first iterate */
+    double phi_norm;     /* |phi| at the returned iterate */
+    double energy;       /* cubature elastic energy sum w_e V_e Psi_e at the returned iterate */
+    double alpha;        /* last accepted step length */
+} dae_newton_report;
+
+/* ---------------------------------------------------------------- context -- */
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the per-thread default stream). */
+dae_status dae_create(dae_ctx** ctx, int device, void* cuda_stream);
+dae_status dae_destroy(dae_ctx* ctx);
+/* Message of the most recent failure on ctx ("" if none); valid until the next call. */
+const char* dae_last_error(const dae_ctx* ctx);
+const char* dae_status_string(dae_status s);
+/* Wait for the context's stream; returns (and clears) the device status word. */
+dae_status dae_sync(dae_ctx* ctx);
+void dae_default_newton_opts(dae_newton_opts* opts);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int dae_version(void);
+
+/* ---------------------------------------------------------------- decoder -- */
+
+/*
+ * Upload a decoder with n_layers fully connected layers (Sec. 3.5, Fig. 3):
+ * z_l = W_l a_{l-1} + b_l, a_l = act(z_l) for l < n_layers, u = z_{n_layers}.
+ *   widths   n_layers+1 ints: widths[0] = r (latent size, 1..32), widths[n_layers] = N
+ *            (a multiple of 3 when used with a mesh)
+ *   W[l]     row-major widths[l+1] x widths[l] FP32 (host or device)
+ *   b[l]     widths[l+1] FP32
+ *   prec     arithmetic of the decoder GEMMs (the library keeps FP32 weights and
+ *            builds the BF16 hi/lo splits it needs)
+ * The library copies the weights; the caller may free its arrays on return.
+ * This call synchronizes.  Errors: INVALID_ARG (shapes), OOM, CUDA, UNSUPPORTED
+ * (r > 32).
+ */
+dae_status dae_load_decoder(dae_ctx* ctx, int n_layers, const int* widths,
+                            const float* const* W, const float* const* b,
+                            dae_act act, dae_prec prec, dae_decoder** out);
+dae_status dae_free_decoder(dae_decoder* dec);
+/* Change the GEMM arithmetic of a loaded decoder (builds splits if needed; synchronizes). */
+dae_status dae_decoder_set_precision(dae_decoder* dec, dae_prec prec);
+
+/* ------------------------------------------------------------------- mesh -- */
+
+/*
+ * Upload a tet mesh (Sec. 3.1: FEM discretisation, lumped mass).
+ *   X      3*n_vert FP64 rest positions, vertex-major
+ *   tets   4*n_tet vertex indices (int32), positively oriented
+ *   vmass  n_vert lumped vertex masses (each repeated on the vertex's 3 DOFs)
+ *   E, nu  Young's modulus and Poisson ratio (Lame: mu = E/(2(1+nu)),
+ *          lam = E nu / ((1+nu)(1-2nu)))
+ * Precomputes Dm^{-1} and rest volumes.  Synchronizes.  Errors: INVALID_ARG
+ * (index out of range, degenerate rest tet, nu outside (-1, 0.5)), OOM, CUDA.
+ */
+dae_status dae_load_mesh(dae_ctx* ctx, int n_vert, const double* X, int n_tet,
+                         const int* tets, const double* vmass, dae_material material,
+                         double E, double nu, dae_mesh** out);
+dae_status dae_free_mesh(dae_mesh* mesh);
+
+/* ------------------------------------------------------ hot-path entries -- */
+
+/*
+ * Decoder derivatives at q (Sec. 4.3: one stacked complex-step forward pass).
+ *   q, qbar, qbar_dot  r FP64 each; dt > 0 (Sec. 3.2 implicit Euler)
+ *   u     N       D(q)
+ *   J     N x r   dD/dq                                   (Eq. 4)
+ *   Hqq   N       H[qdot, qdot], qdot = (q - qbar)/dt     (Eq. 5's inertial term)
+ *   dJ    N x r   S[.,Delta,Delta] + H[., w]              (Eq. 12)
+ *   Hw    N x r   H[., w]       (costs one extra pass when requested)
+ *   Sdd   N x r   S[.,Delta,Delta] (costs one extra pass when requested)
+ * Any output may be NULL (not computed where that saves work).  Errors:
+ * INVALID_ARG, CUDA, OOM.
+ */
+dae_status dae_eval_derivs(dae_ctx* ctx, const dae_decoder* dec, const double* q,
+                           const double* qbar, const double* qbar_dot, double dt,
+                           float* u, float* J, float* Hqq, float* dJ, float* Hw, float* Sdd);
+
+/*
+ * Reduced system at q: phi (Eqs. 7-8 times dt^2), A (Eq. 11 with n_p = 0) and
+ * the cubature elastic energy sum_e w_e V_e Psi_e(F_e).
+ *   cub_tets  n_cub tet indices (distinct), cub_w n_cub non-negative weights (Sec. 5)
+ *   f_ext     N FP32 external force, or NULL for zero
+ *   phi       r FP64;  A  r x r FP64 column-major;  energy 1 FP64 (any may be NULL)
+ *   terms     optional r x r x 4 + r FP64: [a^T H | J^T M J | J^T M dJ | K_r | J^T f_C]
+ *             (column-major blocks), or NULL
+ * Errors: INVALID_ARG, INVERTED (det F <= 0 at a Neo-Hookean cubature tet),
+ * NONFINITE, CUDA.
+ */
+dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mesh,
+                                int n_cub, const int* cub_tets, const float* cub_w,
+                                const double* q, const double* qbar, const double* qbar_dot,
+                                double dt, const float* f_ext, double* phi, double* A,
+                                double* energy, double* terms);
+
+/*
+ * One implicit-Euler frame: Newton iterations on phi(q) = 0 starting from the
+ * value in q (commonly qbar + dt*qbar_dot), each solving A delta = -phi in FP64
+ * (LU with partial pivoting) with Armijo backtracking on |phi|^2.  All control
+ * runs on the device; the host reads only the report.
+ *   q     in: first iterate; out: solution (r FP64)
+ *   opts  NULL = defaults;  rep  may be NULL (then the call does not synchronize
+ *         when every array is on the device; read the report later with
+ *         dae_last_report)
+ * Errors: INVALID_ARG, INVERTED, NONFINITE, SINGULAR, CUDA.  Not reaching tol
+ * within max_iter is reported in rep->converged, not as an error.
+ */
+dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mesh,
+                           int n_cub, const int* cub_tets, const float* cub_w, double* q,
+                           const double* qbar, const double* qbar_dot, double dt,
+                           const float* f_ext, const dae_newton_opts* opts,
+                           dae_newton_report* rep);
+
+/* Report of the most recent dae_newton_step on ctx (synchronizes). */
+dae_status dae_last_report(dae_ctx* ctx, dae_newton_report* rep);
+
+/*
+ * Implicit-Euler rollout of n_frames frames (Sec. 3.2): frame f solves phi = 0
+ * from q = qbar + dt*qbar_dot with cubature weights cub_w[f*n_cub ...], then sets
+ * qbar_dot = (q - qbar)/dt and qbar = q.
+ *   q, qdot   in: state before frame 0; out: state after the last frame (r FP64 each)
+ *   cub_w     n_frames x n_cub weights (per-frame redraws)
+ *   q_traj    optional n_frames x r FP64 trajectory;  reports optional n_frames
+ * The frames run back to back on the device with no host round trip.
+ */
+dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mesh,
+                       int n_cub, const int* cub_tets, const float* cub_w, int n_frames,
+                       double* q, double* qdot, double dt, const float* f_ext,
+                       const dae_newton_opts* opts, double* q_traj,
+                       dae_newton_report* reports);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DAE_H */

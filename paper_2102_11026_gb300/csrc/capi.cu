@@ -1,0 +1,862 @@
+// Host side of the C ABI in include/dae.h: contexts, uploads, argument staging
+// and the enqueueing of one evaluation of the reduced system.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dae_internal.h"
+
+using namespace dae;
+
+#define DAE_VERSION 10000
+
+namespace {
+
+dae_status fail(dae_ctx* ctx, dae_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define CU(ctx, call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DAE_ERR_OOM : DAE_ERR_CUDA,  \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(x)                          \
+    do {                                \
+        dae_status s_ = (x);            \
+        if (s_ != DAE_OK) return s_;    \
+    } while (0)
+
+inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+bool on_device(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+dae_status dmalloc(dae_ctx* ctx, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) return DAE_OK;
+    CU(ctx, cudaMalloc((void**)p, n * sizeof(T)));
+    CU(ctx, cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream));
+    return DAE_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+// Per-call staging of host arguments into the context's device arena.
+struct Stage {
+    dae_ctx* ctx;
+    std::vector<char*> host_out;
+    std::vector<const char*> dev_out;
+    std::vector<size_t> out_bytes;
+    size_t used = 0;
+    bool any_host = false;
+    explicit Stage(dae_ctx* c) : ctx(c) {}
+
+    dae_status reserve(size_t bytes) {
+        if (ctx->dstage_bytes >= bytes) return DAE_OK;
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(ctx->dstage);
+        size_t nb = std::max(bytes, (size_t)1 << 20);
+        CU(ctx, cudaMalloc(&ctx->dstage, nb));
+        ctx->dstage_bytes = nb;
+        return DAE_OK;
+    }
+    // Plan: call need() for every host argument first, then reserve(), then map().
+    size_t plan = 0;
+    void need(const void* p, size_t bytes) {
+        if (p && !on_device(p)) plan += round_up(bytes, 256);
+    }
+    template <class T>
+    dae_status in(const T* p, size_t n, const T** out) {
+        *out = p;
+        if (!p || on_device(p)) return DAE_OK;
+        any_host = true;
+        char* d = (char*)ctx->dstage + used;
+        used += round_up(n * sizeof(T), 256);
+        CU(ctx, cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+        *out = (const T*)d;
+        return DAE_OK;
+    }
+    template <class T>
+    dae_status inout(T* p, size_t n, T** out, bool copy_in) {
+        *out = p;
+        if (!p || on_device(p)) return DAE_OK;
+        any_host = true;
+        char* d = (char*)ctx->dstage + used;
+        used += round_up(n * sizeof(T), 256);
+        if (copy_in)
+            CU(ctx, cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+        host_out.push_back((char*)p);
+        dev_out.push_back(d);
+        out_bytes.push_back(n * sizeof(T));
+        *out = (T*)d;
+        return DAE_OK;
+    }
+    dae_status finish() {
+        for (size_t i = 0; i < host_out.size(); ++i)
+            CU(ctx, cudaMemcpyAsync(host_out[i], dev_out[i], out_bytes[i], cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+        if (any_host) CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return DAE_OK;
+    }
+};
+
+dae_status check_device_status(dae_ctx* ctx) {
+    int st = 0;
+    CU(ctx, cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (st != 0) {
+        CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        return fail(ctx, (dae_status)st, "device reported %s", dae_status_string((dae_status)st));
+    }
+    return DAE_OK;
+}
+
+int out_bf16_of(dae_prec p) { return p == DAE_BF16 ? 1 : (p == DAE_BF16X3 ? 2 : 0); }
+
+// ----------------------------------------------------------- workspace --
+dae_status alloc_workspace(dae_decoder* d) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    const int r = d->r, L = d->L, N = d->N;
+    w.C = n_cols(r);
+    w.Cp = pad_cols(r);
+    size_t ldmax = 0, wmax = 0;
+    for (int l = 0; l <= L - 1; ++l) ldmax = std::max(ldmax, round_up(d->widths[l], kKPad));
+    for (int l = 1; l < L; ++l) wmax = std::max(wmax, (size_t)d->widths[l]);
+    w.ldx_max = ldmax;
+    for (int i = 0; i < 2; ++i) {
+        TRY(dmalloc(ctx, &w.X[i], w.Cp * ldmax));
+        TRY(dmalloc(ctx, &w.Xh[i], w.Cp * ldmax));
+        TRY(dmalloc(ctx, &w.Xl[i], w.Cp * ldmax));
+    }
+    w.S1.assign(L - 1, nullptr);
+    w.T.assign(L - 1, nullptr);
+    for (int l = 0; l < L - 1; ++l) {
+        TRY(dmalloc(ctx, &w.S1[l], (size_t)d->widths[l + 1]));
+        TRY(dmalloc(ctx, &w.T[l], (size_t)r * d->widths[l + 1]));
+    }
+    TRY(dmalloc(ctx, &w.u, (size_t)N));
+    TRY(dmalloc(ctx, &w.HDD, (size_t)N));
+    TRY(dmalloc(ctx, &w.a, (size_t)N));
+    TRY(dmalloc(ctx, &w.J, (size_t)r * N));
+    TRY(dmalloc(ctx, &w.dJ, (size_t)r * N));
+    w.n_row_blocks = (N + 127) / 128;
+    w.row_stride = r + r * (r + 1) / 2 + r * r;
+    TRY(dmalloc(ctx, &w.row_part, (size_t)w.n_row_blocks * w.row_stride));
+    // reverse-pass partials: the largest of the W_L^T a splits and the hidden splits
+    const int sm = ctx->sm_count;
+    const int K = d->widths[L - 1];
+    size_t need = (size_t)(128 + 64) * K;
+    for (int l = L - 2; l >= 0; --l) {
+        int n_o = d->widths[l + 1], n_i = d->widths[l];
+        int mb = (n_i + 127) / 128;
+        int split = std::max(1, std::min((2 * sm + mb - 1) / mb, std::max(1, n_o / 32)));
+        need = std::max(need, (size_t)split * (1 + r) * n_i);
+    }
+    w.bwd_part_elems = need;
+    TRY(dmalloc(ctx, &w.bwd_part[0], need));
+    TRY(dmalloc(ctx, &w.bwd_part[1], need));
+    TRY(dmalloc(ctx, &w.gbuf, (size_t)(1 + r) * std::max(wmax, (size_t)1)));
+    TRY(dmalloc(ctx, &w.red, red_size(r)));
+    TRY(dmalloc(ctx, &w.ns, 1));
+    TRY(dmalloc(ctx, &w.qbar, (size_t)r));
+    TRY(dmalloc(ctx, &w.qbar_dot, (size_t)r));
+    TRY(dmalloc(ctx, &w.q0, (size_t)r));
+    TRY(dmalloc(ctx, &w.zvec, (size_t)r));
+    TRY(dmalloc(ctx, &w.eval_flag, 1));
+    TRY(dmalloc(ctx, &w.f_ext, (size_t)N));
+    return DAE_OK;
+}
+
+void free_workspace(Workspace& w) {
+    for (int i = 0; i < 2; ++i) { dfree(w.X[i]); dfree(w.Xh[i]); dfree(w.Xl[i]); dfree(w.bwd_part[i]); }
+    for (auto& p : w.S1) dfree(p);
+    for (auto& p : w.T) dfree(p);
+    dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
+    dfree(w.gbuf); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
+    dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
+    dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
+}
+
+dae_status ensure_cubature(dae_decoder* d, int n_cub, int n_w) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    const int r = d->r;
+    w.cub_stride = r + r * (r + 1) / 2;
+    if (n_cub > w.cub_cap) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.fe_w); dfree(w.fe_dof); dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets);
+        int cap = std::max(n_cub, 64);
+        TRY(dmalloc(ctx, &w.fe_w, (size_t)cap * 12));
+        TRY(dmalloc(ctx, &w.fe_dof, (size_t)cap * 12));
+        TRY(dmalloc(ctx, &w.cub_part, (size_t)cap * w.cub_stride));
+        TRY(dmalloc(ctx, &w.cub_energy, (size_t)cap));
+        TRY(dmalloc(ctx, &w.cub_tets, (size_t)cap));
+        w.cub_cap = cap;
+    }
+    if (n_w > w.cub_w_cap) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.cub_w);
+        TRY(dmalloc(ctx, &w.cub_w, (size_t)n_w));
+        w.cub_w_cap = n_w;
+    }
+    return DAE_OK;
+}
+
+// ----------------------------------------------------------- evaluation --
+struct Outs {
+    float *u = nullptr, *J = nullptr, *dJ = nullptr, *HDD = nullptr, *Hqq = nullptr;
+};
+
+dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* q_override,
+                           double dt, double h, int mode, const Outs& o) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    cudaStream_t s = ctx->stream;
+    const int r = d->r, L = d->L;
+    const int ob = out_bf16_of(d->prec);
+    const int ld0 = (int)round_up(r, kKPad);
+    launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0], w.Xh[0],
+                w.Xl[0], ob, w.zvec);
+    for (int l = 0; l < L; ++l) {
+        const Layer& ly = d->layers[l];
+        FwdArgs a;
+        memset(&a, 0, sizeof a);
+        a.W = ly.W; a.ld = ly.ld; a.Wh = ly.Wh; a.Wl = ly.Wl; a.bias = ly.b;
+        a.X = w.X[l & 1]; a.Xh = w.Xh[l & 1]; a.Xl = w.Xl[l & 1];
+        a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = r; a.Cp = w.Cp;
+        a.act = d->act;
+        a.last = (l == L - 1);
+        a.ns = ns;
+        a.status = ctx->d_status;
+        a.inv_h = 1.0 / h; a.inv_h2 = 1.0 / (h * h); a.inv_h3 = 1.0 / (h * h * h);
+        a.inv_dt2 = 1.0 / (dt * dt);
+        if (!a.last) {
+            a.Y = w.X[(l + 1) & 1]; a.Yh = w.Xh[(l + 1) & 1]; a.Yl = w.Xl[(l + 1) & 1];
+            a.ldy = (int)round_up(ly.n_out, kKPad);
+            a.out_bf16 = ob;
+            a.S1 = w.S1[l]; a.T = w.T[l];
+        } else {
+            a.u = o.u; a.J = o.J; a.dJ = o.dJ; a.HDD = o.HDD; a.Hqq = o.Hqq;
+        }
+        if (d->prec == DAE_FP32) {
+            launch_fwd_simt(s, a);
+        } else if (!launch_fwd_tc(s, a, d->prec, ctx->sm_count)) {
+            return fail(ctx, DAE_ERR_UNSUPPORTED, "precision %d not available for layer %d", d->prec, l);
+        }
+    }
+    CU(ctx, cudaGetLastError());
+    return DAE_OK;
+}
+
+struct EvalParams {
+    double dt, h;
+    const int* cub_tets; const float* cub_w; int n_cub;
+    const float* f_ext;       // device, may be null
+    int control;
+    const dae_newton_opts* opts;
+};
+
+dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
+                        const double* q_override, const EvalParams& P) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    cudaStream_t s = ctx->stream;
+    const int r = d->r, L = d->L, N = d->N;
+    const int sm = ctx->sm_count;
+    Outs o;
+    o.u = w.u; o.J = w.J; o.dJ = w.dJ; o.HDD = w.HDD;
+    TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o));
+    RowArgs ra;
+    ra.J = w.J; ra.dJ = w.dJ; ra.HDD = w.HDD; ra.mdof = m->mdof; ra.f_ext = P.f_ext;
+    ra.zvec = w.zvec; ra.a = w.a; ra.part = w.row_part; ra.N = N; ra.r = r;
+    ra.stride = w.row_stride; ra.dt = P.dt; ra.ns = ns;
+    launch_row_reduce(s, ra, w.n_row_blocks);
+    CubArgs ca;
+    ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
+    ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu; ca.lam = (float)m->lam;
+    ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
+    ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
+    ca.stride = w.cub_stride; ca.ns = ns; ca.eval_flag = w.eval_flag;
+    launch_cubature(s, ca);
+    // delta_{L-1} = W_L^T a  (dense rows + cubature rows)
+    const Layer& top = d->layers[L - 1];
+    const int K = top.n_in;
+    const int kb = (K + 1023) / 1024;
+    WtaArgs wa;
+    wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.K = K; wa.a = w.a;
+    wa.fe_w = w.fe_w; wa.fe_dof = w.fe_dof; wa.n_pairs = 12 * P.n_cub; wa.dt2 = P.dt * P.dt;
+    wa.nsplit_dense = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * sm + kb - 1) / kb)));
+    wa.nsplit_pairs = std::max(1, std::min(64, (wa.n_pairs + 95) / 96));
+    wa.part = w.bwd_part[0]; wa.ns = ns;
+    launch_wta(s, wa);
+    int in_split = wa.nsplit_dense + wa.nsplit_pairs, in_ncol = 1, cur = 0;
+    for (int l = L - 2; l >= 0; --l) {
+        BwdArgs ba;
+        ba.W = d->layers[l].W; ba.ld = d->layers[l].ld;
+        ba.n_o = d->widths[l + 1]; ba.n_i = d->widths[l]; ba.r = r;
+        ba.in_part = w.bwd_part[cur]; ba.in_split = in_split; ba.in_ncol = in_ncol;
+        ba.S1 = w.S1[l]; ba.T = w.T[l]; ba.g = w.gbuf;
+        int mb = (ba.n_i + 127) / 128;
+        ba.out_split = std::max(1, std::min((2 * sm + mb - 1) / mb, std::max(1, ba.n_o / 32)));
+        ba.out_part = w.bwd_part[cur ^ 1];
+        ba.ns = ns;
+        launch_bwd(s, ba);
+        cur ^= 1;
+        in_split = ba.out_split;
+        in_ncol = 1 + r;
+    }
+    if (L == 1)
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "a decoder needs at least one hidden layer");
+    AsmArgs aa;
+    aa.r = r; aa.dt = P.dt; aa.h = P.h;
+    aa.row_part = w.row_part; aa.n_row_blocks = w.n_row_blocks; aa.row_stride = w.row_stride;
+    aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = P.n_cub;
+    aa.cub_stride = w.cub_stride;
+    aa.bwd_part = w.bwd_part[cur]; aa.bwd_split = in_split;
+    aa.red = w.red; aa.ns = ns; aa.control = P.control;
+    if (P.opts) {
+        aa.tol = P.opts->tol; aa.c_armijo = P.opts->c_armijo; aa.max_iter = P.opts->max_iter;
+        aa.max_halvings = P.opts->max_halvings; aa.max_evals = P.opts->max_evals;
+    } else {
+        aa.tol = 0; aa.c_armijo = 0; aa.max_iter = 0; aa.max_halvings = 0; aa.max_evals = 0;
+    }
+    aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+    launch_assemble(s, aa);
+    CU(ctx, cudaGetLastError());
+    return DAE_OK;
+}
+
+dae_status check_common(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* m) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    if (!dec || dec->ctx != ctx) return fail(ctx, DAE_ERR_INVALID_ARG, "decoder missing or from another context");
+    if (m) {
+        if (m->ctx != ctx) return fail(ctx, DAE_ERR_INVALID_ARG, "mesh from another context");
+        if (3 * m->n_vert != dec->N)
+            return fail(ctx, DAE_ERR_INVALID_ARG, "decoder output %d != 3 x %d mesh vertices", dec->N, m->n_vert);
+    }
+    CU(ctx, cudaSetDevice(ctx->device));
+    return DAE_OK;
+}
+
+void to_report(const NewtonState& s, dae_newton_report* rep) {
+    rep->iters = s.iters;
+    rep->evals = s.evals;
+    rep->converged = s.converged;
+    rep->status = s.status;
+    rep->phi_norm0 = s.phi_norm0;
+    rep->phi_norm = std::sqrt(s.merit_acc);
+    rep->energy = s.energy;
+    rep->alpha = s.alpha;
+}
+
+void fill_opts(const dae_newton_opts* in, dae_newton_opts* o) {
+    dae_default_newton_opts(o);
+    if (in) *o = *in;
+    if (o->max_evals <= 0) o->max_evals = o->max_iter + 3;
+    if (o->h_cs <= 0) o->h_cs = std::ldexp(1.0, -20);
+}
+
+dae_status stage_cubature(dae_decoder* d, Stage& st, int n_cub, const int* cub_tets,
+                          const float* cub_w, int n_w, const int** dt_out, const float** dw_out) {
+    TRY(ensure_cubature(d, n_cub, n_w));
+    dae_ctx* ctx = d->ctx;
+    if (n_cub > 0) {
+        CU(ctx, cudaMemcpyAsync(d->ws.cub_tets, cub_tets, (size_t)n_cub * sizeof(int),
+                                cudaMemcpyDefault, ctx->stream));
+        CU(ctx, cudaMemcpyAsync(d->ws.cub_w, cub_w, (size_t)n_w * sizeof(float), cudaMemcpyDefault,
+                                ctx->stream));
+    }
+    *dt_out = d->ws.cub_tets;
+    *dw_out = d->ws.cub_w;
+    (void)st;
+    return DAE_OK;
+}
+
+dae_status stage_fext(dae_decoder* d, const float* f_ext, const float** out) {
+    dae_ctx* ctx = d->ctx;
+    if (!f_ext) {
+        *out = nullptr;
+        return DAE_OK;
+    }
+    CU(ctx, cudaMemcpyAsync(d->ws.f_ext, f_ext, (size_t)d->N * sizeof(float), cudaMemcpyDefault,
+                            ctx->stream));
+    *out = d->ws.f_ext;
+    return DAE_OK;
+}
+
+dae_status validate_cub(dae_ctx* ctx, const dae_mesh* m, int n_cub, const int* cub_tets,
+                        const float* cub_w) {
+    if (n_cub < 0) return fail(ctx, DAE_ERR_INVALID_ARG, "n_cub < 0");
+    if (n_cub > 0 && (!cub_tets || !cub_w))
+        return fail(ctx, DAE_ERR_INVALID_ARG, "cubature arrays missing");
+    if (n_cub > 0 && !on_device(cub_tets)) {
+        for (int i = 0; i < n_cub; ++i)
+            if (cub_tets[i] < 0 || cub_tets[i] >= m->n_tet)
+                return fail(ctx, DAE_ERR_INVALID_ARG, "cubature tet %d out of range", cub_tets[i]);
+    }
+    return DAE_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI ====
+extern "C" {
+
+int dae_version(void) { return DAE_VERSION; }
+
+const char* dae_status_string(dae_status s) {
+    switch (s) {
+        case DAE_OK: return "DAE_OK";
+        case DAE_ERR_INVALID_ARG: return "DAE_ERR_INVALID_ARG";
+        case DAE_ERR_CUDA: return "DAE_ERR_CUDA";
+        case DAE_ERR_OOM: return "DAE_ERR_OOM";
+        case DAE_ERR_NOT_CONVERGED: return "DAE_ERR_NOT_CONVERGED";
+        case DAE_ERR_NONFINITE: return "DAE_ERR_NONFINITE";
+        case DAE_ERR_SINGULAR: return "DAE_ERR_SINGULAR";
+        case DAE_ERR_INVERTED: return "DAE_ERR_INVERTED";
+        case DAE_ERR_TIMEOUT: return "DAE_ERR_TIMEOUT";
+        case DAE_ERR_UNSUPPORTED: return "DAE_ERR_UNSUPPORTED";
+    }
+    return "unknown";
+}
+
+void dae_default_newton_opts(dae_newton_opts* o) {
+    if (!o) return;
+    o->max_iter = 5;
+    o->max_evals = 8;
+    o->max_halvings = 8;
+    o->tol = 1e-8;
+    o->c_armijo = 1e-4;
+    o->h_cs = std::ldexp(1.0, -20);
+}
+
+dae_status dae_create(dae_ctx** out, int device, void* stream) {
+    if (!out) return DAE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return DAE_ERR_CUDA;
+    }
+    dae_ctx* ctx = new dae_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return DAE_ERR_CUDA; }
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess) { delete ctx; return DAE_ERR_OOM; }
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+    *out = ctx;
+    return DAE_OK;
+}
+
+dae_status dae_destroy(dae_ctx* ctx) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    dfree(ctx->d_status);
+    dfree(ctx->dstage);
+    delete ctx;
+    return DAE_OK;
+}
+
+const char* dae_last_error(const dae_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dae_status dae_sync(dae_ctx* ctx) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    CU(ctx, cudaSetDevice(ctx->device));
+    return check_device_status(ctx);
+}
+
+dae_status dae_load_decoder(dae_ctx* ctx, int n_layers, const int* widths, const float* const* W,
+                            const float* const* b, dae_act act, dae_prec prec, dae_decoder** out) {
+    if (!ctx || !out) return DAE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_layers < 2 || !widths || !W || !b)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "need >= 2 layers and widths/W/b arrays");
+    for (int l = 0; l <= n_layers; ++l)
+        if (widths[l] <= 0) return fail(ctx, DAE_ERR_INVALID_ARG, "width %d is %d", l, widths[l]);
+    if (widths[0] > kMaxR) return fail(ctx, DAE_ERR_UNSUPPORTED, "latent size %d > %d", widths[0], kMaxR);
+    if (act < DAE_ACT_TANH || act > DAE_ACT_LINEAR) return fail(ctx, DAE_ERR_INVALID_ARG, "bad activation");
+    if (prec < DAE_FP32 || prec > DAE_BF16X3) return fail(ctx, DAE_ERR_INVALID_ARG, "bad precision");
+    CU(ctx, cudaSetDevice(ctx->device));
+    dae_decoder* d = new dae_decoder();
+    d->ctx = ctx;
+    d->L = n_layers;
+    d->r = widths[0];
+    d->N = widths[n_layers];
+    d->widths.assign(widths, widths + n_layers + 1);
+    d->act = act;
+    d->prec = DAE_FP32;
+    d->layers.resize(n_layers);
+    auto cleanup = [&](dae_status st) {
+        dae_free_decoder(d);
+        return st;
+    };
+    for (int l = 0; l < n_layers; ++l) {
+        Layer& ly = d->layers[l];
+        ly.n_in = widths[l];
+        ly.n_out = widths[l + 1];
+        ly.ld = (int)round_up(ly.n_in, kKPad);
+        ly.m_pad = (int)round_up(ly.n_out, kRowTile);
+        if (!W[l] || !b[l]) return cleanup(fail(ctx, DAE_ERR_INVALID_ARG, "layer %d arrays missing", l));
+        dae_status st = dmalloc(ctx, &ly.W, (size_t)ly.m_pad * ly.ld);
+        if (st) return cleanup(st);
+        st = dmalloc(ctx, &ly.b, (size_t)ly.n_out);
+        if (st) return cleanup(st);
+        cudaError_t e = cudaMemcpy2DAsync(ly.W, (size_t)ly.ld * sizeof(float), W[l],
+                                          (size_t)ly.n_in * sizeof(float), (size_t)ly.n_in * sizeof(float),
+                                          ly.n_out, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ly.b, b[l], (size_t)ly.n_out * sizeof(float), cudaMemcpyDefault, ctx->stream);
+        if (e != cudaSuccess)
+            return cleanup(fail(ctx, DAE_ERR_CUDA, "weight upload: %s", cudaGetErrorString(e)));
+    }
+    dae_status st = alloc_workspace(d);
+    if (st) return cleanup(st);
+    st = dae_decoder_set_precision(d, prec);
+    if (st) return cleanup(st);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return cleanup(fail(ctx, DAE_ERR_CUDA, "decoder upload failed"));
+    *out = d;
+    return DAE_OK;
+}
+
+dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = d->ctx;
+    if (prec < DAE_FP32 || prec > DAE_BF16X3) return fail(ctx, DAE_ERR_INVALID_ARG, "bad precision");
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (prec == DAE_BF16 || prec == DAE_BF16X3) {
+        for (auto& ly : d->layers) {
+            size_t n = (size_t)ly.m_pad * ly.ld;
+            if (!ly.Wh) TRY(dmalloc(ctx, &ly.Wh, n));
+            if (prec == DAE_BF16X3 && !ly.Wl) TRY(dmalloc(ctx, &ly.Wl, n));
+            launch_split_bf16(ctx->stream, ly.W, ly.Wh, prec == DAE_BF16X3 ? ly.Wl : nullptr, n);
+        }
+    }
+    CU(ctx, cudaGetLastError());
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    d->prec = prec;
+    return DAE_OK;
+}
+
+dae_status dae_free_decoder(dae_decoder* d) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    cudaSetDevice(d->ctx->device);
+    cudaStreamSynchronize(d->ctx->stream);
+    for (auto& ly : d->layers) { dfree(ly.W); dfree(ly.b); dfree(ly.Wh); dfree(ly.Wl); }
+    free_workspace(d->ws);
+    delete d;
+    return DAE_OK;
+}
+
+dae_status dae_load_mesh(dae_ctx* ctx, int n_vert, const double* X, int n_tet, const int* tets,
+                         const double* vmass, dae_material material, double E, double nu,
+                         dae_mesh** out) {
+    if (!ctx || !out) return DAE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_vert <= 0 || n_tet <= 0 || !X || !tets || !vmass)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "empty mesh or missing arrays");
+    if (!(nu > -1.0 && nu < 0.5) || !(E > 0))
+        return fail(ctx, DAE_ERR_INVALID_ARG, "material parameters out of range");
+    if (material != DAE_STVK && material != DAE_NEOHOOKEAN)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "bad material");
+    CU(ctx, cudaSetDevice(ctx->device));
+    // bring host copies for the precomputation
+    std::vector<double> hX(3 * (size_t)n_vert), hm(n_vert);
+    std::vector<int> ht(4 * (size_t)n_tet);
+    CU(ctx, cudaMemcpy(hX.data(), X, hX.size() * sizeof(double), cudaMemcpyDefault));
+    CU(ctx, cudaMemcpy(ht.data(), tets, ht.size() * sizeof(int), cudaMemcpyDefault));
+    CU(ctx, cudaMemcpy(hm.data(), vmass, hm.size() * sizeof(double), cudaMemcpyDefault));
+    std::vector<float> Bm(9 * (size_t)n_tet), vol(n_tet), mdof(3 * (size_t)n_vert);
+    for (int e = 0; e < n_tet; ++e) {
+        int v[4];
+        for (int a = 0; a < 4; ++a) {
+            v[a] = ht[4 * (size_t)e + a];
+            if (v[a] < 0 || v[a] >= n_vert)
+                return fail(ctx, DAE_ERR_INVALID_ARG, "tet %d vertex index %d out of range", e, v[a]);
+        }
+        double Dm[9];
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) Dm[d * 3 + c] = hX[3 * v[c + 1] + d] - hX[3 * v[0] + d];
+        double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                     Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+        if (!(std::fabs(det) > 0))
+            return fail(ctx, DAE_ERR_INVALID_ARG, "tet %d is degenerate at rest", e);
+        double inv[9];
+        inv[0] = (Dm[4] * Dm[8] - Dm[5] * Dm[7]) / det;
+        inv[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / det;
+        inv[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / det;
+        inv[3] = (Dm[5] * Dm[6] - Dm[3] * Dm[8]) / det;
+        inv[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / det;
+        inv[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / det;
+        inv[6] = (Dm[3] * Dm[7] - Dm[4] * Dm[6]) / det;
+        inv[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / det;
+        inv[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / det;
+        for (int i = 0; i < 9; ++i) Bm[9 * (size_t)e + i] = (float)inv[i];
+        vol[e] = (float)(std::fabs(det) / 6.0);
+    }
+    for (int v = 0; v < n_vert; ++v)
+        for (int d = 0; d < 3; ++d) mdof[3 * (size_t)v + d] = (float)hm[v];
+    dae_mesh* m = new dae_mesh();
+    m->ctx = ctx;
+    m->n_vert = n_vert;
+    m->n_tet = n_tet;
+    m->material = material;
+    m->mu = E / (2.0 * (1.0 + nu));
+    m->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    dae_status st = DAE_OK;
+    if (!st) st = dmalloc(ctx, &m->X, hX.size());
+    if (!st) st = dmalloc(ctx, &m->tets, ht.size());
+    if (!st) st = dmalloc(ctx, &m->Bm, Bm.size());
+    if (!st) st = dmalloc(ctx, &m->vol, vol.size());
+    if (!st) st = dmalloc(ctx, &m->mdof, mdof.size());
+    if (st) { dae_free_mesh(m); return st; }
+    cudaMemcpy(m->X, hX.data(), hX.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->tets, ht.data(), ht.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->Bm, Bm.data(), Bm.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->vol, vol.data(), vol.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(m->mdof, mdof.data(), mdof.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { dae_free_mesh(m); return fail(ctx, DAE_ERR_CUDA, "mesh upload failed"); }
+    *out = m;
+    return DAE_OK;
+}
+
+dae_status dae_free_mesh(dae_mesh* m) {
+    if (!m) return DAE_ERR_INVALID_ARG;
+    cudaSetDevice(m->ctx->device);
+    cudaStreamSynchronize(m->ctx->stream);
+    dfree(m->X); dfree(m->tets); dfree(m->Bm); dfree(m->vol); dfree(m->mdof);
+    delete m;
+    return DAE_OK;
+}
+
+dae_status dae_eval_derivs(dae_ctx* ctx, const dae_decoder* dec_c, const double* q,
+                           const double* qbar, const double* qbar_dot, double dt, float* u,
+                           float* J, float* Hqq, float* dJ, float* Hw, float* Sdd) {
+    TRY(check_common(ctx, dec_c, nullptr));
+    dae_decoder* d = const_cast<dae_decoder*>(dec_c);
+    if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
+    if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
+    const int r = d->r;
+    const size_t N = d->N;
+    Stage st(ctx);
+    st.need(q, r * 8); st.need(u, N * 4); st.need(J, N * r * 4); st.need(Hqq, N * 4);
+    st.need(dJ, N * r * 4); st.need(Hw, N * r * 4); st.need(Sdd, N * r * 4);
+    TRY(st.reserve(st.plan));
+    const double* dq;
+    float *du, *dJo, *dHqq, *ddJ, *dHw, *dSdd;
+    TRY(st.in(q, r, &dq));
+    TRY(st.inout(u, N, &du, false));
+    TRY(st.inout(J, N * r, &dJo, false));
+    TRY(st.inout(Hqq, N, &dHqq, false));
+    TRY(st.inout(dJ, N * r, &ddJ, false));
+    TRY(st.inout(Hw, N * r, &dHw, false));
+    TRY(st.inout(Sdd, N * r, &dSdd, false));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar, qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar_dot, qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    const double h = std::ldexp(1.0, -20);
+    Outs o;
+    o.u = du; o.J = dJo; o.Hqq = dHqq; o.dJ = ddJ;
+    if (du || dJo || dHqq || ddJ) TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_FULL, o));
+    if (dHw) {
+        Outs o2;
+        o2.dJ = dHw;
+        TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_HW, o2));
+    }
+    if (dSdd) {
+        Outs o3;
+        o3.dJ = dSdd;
+        TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_SDD, o3));
+    }
+    TRY(st.finish());
+    if (st.any_host) return check_device_status(ctx);
+    return DAE_OK;
+}
+
+dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m,
+                                int n_cub, const int* cub_tets, const float* cub_w, const double* q,
+                                const double* qbar, const double* qbar_dot, double dt,
+                                const float* f_ext, double* phi, double* A, double* energy,
+                                double* terms) {
+    TRY(check_common(ctx, dec_c, m));
+    if (!m) return fail(ctx, DAE_ERR_INVALID_ARG, "mesh required");
+    dae_decoder* d = const_cast<dae_decoder*>(dec_c);
+    if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
+    if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    const int r = d->r;
+    Stage st(ctx);
+    st.need(q, r * 8);
+    TRY(st.reserve(st.plan));
+    const double* dq;
+    TRY(st.in(q, r, &dq));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar, qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar_dot, qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    const int* dct;
+    const float* dcw;
+    TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
+    const float* dfe;
+    TRY(stage_fext(d, f_ext, &dfe));
+    EvalParams P;
+    P.dt = dt; P.h = std::ldexp(1.0, -20); P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
+    P.f_ext = dfe; P.control = 0; P.opts = nullptr;
+    TRY(enqueue_eval(d, m, nullptr, dq, P));
+    const double* red = d->ws.red;
+    const size_t rr = (size_t)r * r;
+    if (phi) CU(ctx, cudaMemcpyAsync(phi, red, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    if (A) CU(ctx, cudaMemcpyAsync(A, red + r, rr * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    if (energy) CU(ctx, cudaMemcpyAsync(energy, red + r + rr, sizeof(double), cudaMemcpyDefault, ctx->stream));
+    if (terms) CU(ctx, cudaMemcpyAsync(terms, red + r + rr + 1, (4 * rr + r) * sizeof(double),
+                                       cudaMemcpyDefault, ctx->stream));
+    bool host_out = (phi && !on_device(phi)) || (A && !on_device(A)) ||
+                    (energy && !on_device(energy)) || (terms && !on_device(terms));
+    TRY(st.finish());
+    if (host_out || st.any_host) return check_device_status(ctx);
+    return DAE_OK;
+}
+
+dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m, int n_cub,
+                           const int* cub_tets, const float* cub_w, double* q, const double* qbar,
+                           const double* qbar_dot, double dt, const float* f_ext,
+                           const dae_newton_opts* opts_in, dae_newton_report* rep) {
+    TRY(check_common(ctx, dec_c, m));
+    if (!m) return fail(ctx, DAE_ERR_INVALID_ARG, "mesh required");
+    dae_decoder* d = const_cast<dae_decoder*>(dec_c);
+    if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
+    if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    dae_newton_opts opts;
+    fill_opts(opts_in, &opts);
+    if (opts.max_iter < 0 || opts.max_evals < 1) return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
+    const int r = d->r;
+    Stage st(ctx);
+    st.need(q, r * 8);
+    TRY(st.reserve(st.plan));
+    double* dq;
+    TRY(st.inout(q, r, &dq, true));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar, qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(d->ws.qbar_dot, qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    const int* dct;
+    const float* dcw;
+    TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
+    const float* dfe;
+    TRY(stage_fext(d, f_ext, &dfe));
+    EvalParams P;
+    P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
+    P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    launch_frame_begin(ctx->stream, d->ws.ns, dq, r, 0);
+    for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, d->ws.ns, nullptr, P));
+    launch_frame_end(ctx->stream, d->ws.ns, dq, nullptr, nullptr, dt, r, nullptr, nullptr, 0);
+    CU(ctx, cudaGetLastError());
+    ctx->last_ns = d->ws.ns;
+    TRY(st.finish());
+    if (rep) return dae_last_report(ctx, rep);
+    return DAE_OK;
+}
+
+dae_status dae_last_report(dae_ctx* ctx, dae_newton_report* rep) {
+    if (!ctx || !rep) return DAE_ERR_INVALID_ARG;
+    if (!ctx->last_ns) return fail(ctx, DAE_ERR_INVALID_ARG, "no Newton step has run");
+    NewtonState s;
+    CU(ctx, cudaMemcpyAsync(&s, ctx->last_ns, sizeof s, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(check_device_status(ctx));
+    to_report(s, rep);
+    if (s.status != 0) return fail(ctx, (dae_status)s.status, "Newton frame failed: %s", dae_status_string((dae_status)s.status));
+    return DAE_OK;
+}
+
+dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m, int n_cub,
+                       const int* cub_tets, const float* cub_w, int n_frames, double* q,
+                       double* qdot, double dt, const float* f_ext, const dae_newton_opts* opts_in,
+                       double* q_traj, dae_newton_report* reports) {
+    TRY(check_common(ctx, dec_c, m));
+    if (!m) return fail(ctx, DAE_ERR_INVALID_ARG, "mesh required");
+    dae_decoder* d = const_cast<dae_decoder*>(dec_c);
+    if (!q || !qdot || n_frames < 0) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qdot required, n_frames >= 0");
+    if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    dae_newton_opts opts;
+    fill_opts(opts_in, &opts);
+    const int r = d->r;
+    Stage st(ctx);
+    st.need(q, r * 8); st.need(qdot, r * 8);
+    st.need(q_traj, (size_t)n_frames * r * 8);
+    TRY(st.reserve(st.plan));
+    double *dq, *dqd, *dtraj;
+    TRY(st.inout(q, r, &dq, true));
+    TRY(st.inout(qdot, r, &dqd, true));
+    TRY(st.inout(q_traj, (size_t)n_frames * r, &dtraj, false));
+    Workspace& w = d->ws;
+    if (n_frames > w.hist_cap) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.hist);
+        TRY(dmalloc(ctx, &w.hist, (size_t)n_frames));
+        w.hist_cap = n_frames;
+    }
+    CU(ctx, cudaMemcpyAsync(w.qbar, dq, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(w.qbar_dot, dqd, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    const int* dct;
+    const float* dcw;
+    TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub * n_frames, &dct, &dcw));
+    const float* dfe;
+    TRY(stage_fext(d, f_ext, &dfe));
+    for (int f = 0; f < n_frames; ++f) {
+        EvalParams P;
+        P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw + (size_t)f * n_cub;
+        P.n_cub = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+        launch_predict(ctx->stream, w.q0, w.qbar, w.qbar_dot, dt, r);
+        launch_frame_begin(ctx->stream, w.ns, w.q0, r, f);
+        for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, w.ns, nullptr, P));
+        launch_frame_end(ctx->stream, w.ns, nullptr, w.qbar, w.qbar_dot, dt, r,
+                         dtraj ? dtraj + (size_t)f * r : nullptr, w.hist + f, 1);
+    }
+    CU(ctx, cudaGetLastError());
+    CU(ctx, cudaMemcpyAsync(dq, w.qbar, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(dqd, w.qbar_dot, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->last_ns = w.ns;
+    TRY(st.finish());
+    if (reports && n_frames > 0) {
+        std::vector<NewtonState> hs(n_frames);
+        CU(ctx, cudaMemcpyAsync(hs.data(), w.hist, n_frames * sizeof(NewtonState),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+        TRY(check_device_status(ctx));
+        int worst = 0;
+        for (int f = 0; f < n_frames; ++f) {
+            to_report(hs[f], &reports[f]);
+            if (hs[f].status && !worst) worst = hs[f].status;
+        }
+        if (worst) return fail(ctx, (dae_status)worst, "a rollout frame failed: %s", dae_status_string((dae_status)worst));
+    }
+    return DAE_OK;
+}
+
+}  // extern "C"

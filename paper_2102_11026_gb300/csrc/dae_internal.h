@@ -1,0 +1,243 @@
+// Internal declarations of the sm_103a library behind include/dae.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "dae.h"
+
+namespace dae {
+
+// Stacked component columns of one complex-step forward pass (Sec. 4.3).
+// The network input is the multicomplex vector
+//     q* = q + h e_j i1 + h c i2 + h c i3 + h^2 g i2i3          (one j per group)
+// with c = Delta and g = w by default.  Components shared by every j are stored
+// once; the i2 and i3 parts are equal (same seed), so are the i1i2 and i1i3 parts:
+//   col 0        real part                     -> u
+//   col 1        i2 (= i3) part                -> h   J c
+//   col 2        i2i3 part                     -> h^2 (J g + H[c,c])
+//   col 3        i2i3 part of the group without the g seed -> h^2 H[c,c]
+//   col 4+3j     i1 part of group j            -> h   J e_j
+//   col 5+3j     i1i2 (= i1i3) part of group j -> h^2 H[e_j, c]
+//   col 6+3j     i1i2i3 part of group j        -> h^3 (S[e_j,c,c] + H[e_j,g])  (= dJ e_j, Eq. 12)
+constexpr int kShared = 4;
+__host__ __device__ inline int n_cols(int r) { return kShared + 3 * r; }
+__host__ __device__ inline int pad_cols(int r) { return (n_cols(r) + 15) / 16 * 16; }
+constexpr int kMaxR = 32;
+constexpr int kRowTile = 128;     // output rows per tile (tcgen05 M, SIMT uses 64)
+constexpr int kKPad = 64;         // K padding (128 bytes of BF16)
+
+enum SeedMode { SEED_FULL = 0, SEED_SDD = 1, SEED_HW = 2 };
+
+struct Layer {
+    int n_in = 0, n_out = 0;
+    int ld = 0;            // padded row stride of W (elements), multiple of kKPad
+    int m_pad = 0;         // n_out padded to kRowTile
+    float* W = nullptr;    // [m_pad][ld] FP32, zero padded
+    float* b = nullptr;    // [n_out]
+    __nv_bfloat16* Wh = nullptr;   // BF16 hi split [m_pad][ld]
+    __nv_bfloat16* Wl = nullptr;   // BF16 lo split (W - hi)
+};
+
+// Device-resident Newton control state of one frame.
+struct NewtonState {
+    double q_acc[kMaxR];     // last accepted iterate
+    double q_trial[kMaxR];   // iterate being evaluated
+    double delta[kMaxR];     // Newton direction from q_acc
+    double phi[kMaxR];       // phi at q_trial
+    double merit_acc;        // |phi|^2 at q_acc
+    double phi_norm0;
+    double alpha;
+    double energy;
+    int halvings;
+    int iters;
+    int evals;
+    int done;                // 1: the remaining evaluations of the frame are skipped
+    int converged;
+    int status;              // dae_status of the frame
+    int frame;
+    int pad_;
+};
+
+// Per-decoder workspace (sized for the decoder's widths and latent size).
+struct Workspace {
+    int Cp = 0, C = 0;
+    size_t ldx_max = 0;            // max padded width over all layer inputs/outputs
+    float* X[2] = {nullptr, nullptr};             // FP32 activations [Cp][ld]
+    __nv_bfloat16* Xh[2] = {nullptr, nullptr};    // BF16 hi [Cp][ld]
+    __nv_bfloat16* Xl[2] = {nullptr, nullptr};    // BF16 lo [Cp][ld]
+    std::vector<float*> S1;        // per hidden layer: act'(z) [n]
+    std::vector<float*> T;         // per hidden layer: act''(z) * (i1 part of z)/h  [r][n]
+    // last-layer outputs (internal copies)
+    float* u = nullptr;            // [N]
+    float* J = nullptr;            // [r][N]
+    float* dJ = nullptr;           // [r][N]
+    float* HDD = nullptr;          // [N]  H[Delta,Delta]
+    float* a = nullptr;            // [N]  dense part of the BP seed: M(Jz+HDD) - dt^2 f_ext
+    // per-tile partial sums of the row reductions (FP32)
+    float* row_part = nullptr;     // [n_row_blocks][row_stride]
+    int n_row_blocks = 0, row_stride = 0;
+    // reverse pass partials [nsplit][1+r][width]
+    float* bwd_part[2] = {nullptr, nullptr};
+    size_t bwd_part_elems = 0;
+    float* gbuf = nullptr;         // [1+r][max width] reverse-pass seed of one layer
+    int max_split = 0;
+    // cubature scratch (grown on demand)
+    int cub_cap = 0;
+    float* fe_w = nullptr;          // [cap][12] w_e f_e
+    int* fe_dof = nullptr;          // [cap][12] DOF index
+    float* cub_part = nullptr;      // [cap][cub_stride]
+    double* cub_energy = nullptr;   // [cap]
+    int cub_stride = 0;
+    // reduced system (FP64)
+    double* red = nullptr;          // phi | A | energy | terms (see dae_assemble_reduced)
+    NewtonState* ns = nullptr;
+    double* qbar = nullptr;         // [r]
+    double* qbar_dot = nullptr;     // [r]
+    float* zvec = nullptr;          // [r] z = Delta - dt qbar_dot (FP32 copy)
+    int* cub_tets = nullptr;        // staged cubature indices
+    float* cub_w = nullptr;         // staged weights (per frame)
+    int cub_w_cap = 0;
+    float* f_ext = nullptr;         // staged f_ext [N] (zero if absent)
+    double* q0 = nullptr;           // [r] first iterate of a rollout frame
+    int* eval_flag = nullptr;       // per-evaluation cubature flag
+    NewtonState* hist = nullptr;    // per-frame states of a rollout (grown on demand)
+    int hist_cap = 0;
+};
+
+}  // namespace dae
+
+struct dae_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int* d_status = nullptr;         // device status word (first error wins)
+    void* pinned = nullptr;          // host staging
+    size_t pinned_bytes = 0;
+    void* dstage = nullptr;          // device staging for host arguments
+    size_t dstage_bytes = 0;
+    int sm_count = 0;
+    dae::NewtonState* last_ns = nullptr;   // state of the most recent newton step
+};
+
+struct dae_decoder {
+    dae_ctx* ctx = nullptr;
+    int L = 0, r = 0, N = 0;
+    std::vector<int> widths;
+    dae_act act = DAE_ACT_TANH;
+    dae_prec prec = DAE_FP32;
+    std::vector<dae::Layer> layers;
+    dae::Workspace ws;
+};
+
+struct dae_mesh {
+    dae_ctx* ctx = nullptr;
+    int n_vert = 0, n_tet = 0;
+    dae_material material = DAE_STVK;
+    double mu = 0, lam = 0;
+    double* X = nullptr;       // [3V] rest positions
+    int* tets = nullptr;       // [4T]
+    float* Bm = nullptr;       // [T][9] Dm^{-1}, row-major
+    float* vol = nullptr;      // [T] rest volumes
+    float* mdof = nullptr;     // [3V] lumped mass per DOF
+};
+
+namespace dae {
+
+// ----------------------------------------------------------------- kernels --
+// Arguments shared by the forward epilogues.
+struct FwdArgs {
+    const float* W; int ld;                 // FP32 weights [m_pad][ld]
+    const __nv_bfloat16* Wh; const __nv_bfloat16* Wl;
+    const float* bias;
+    const float* X; const __nv_bfloat16* Xh; const __nv_bfloat16* Xl;   // input [Cp][ld]
+    int n_in, n_out, m_pad, r, Cp;
+    int act;                                 // dae_act (hidden layers)
+    int last;                                // 1: output layer
+    // hidden-layer outputs
+    float* Y; __nv_bfloat16* Yh; __nv_bfloat16* Yl; int ldy;   // next activations [Cp][ldy]
+    int out_bf16;                            // 0 none, 1 hi, 2 hi+lo
+    float* S1; float* T;                     // reverse-pass data
+    // output-layer outputs (any may be null)
+    float* u; float* J; float* dJ; float* HDD; float* Hqq;
+    double inv_h, inv_h2, inv_h3, inv_dt2;
+    const NewtonState* ns;                   // early exit when ns->done (may be null)
+    int* status;
+};
+
+void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,
+                 const double* qbar, const double* qbar_dot, double dt, double h, int mode,
+                 int r, int Cp, int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
+                 int out_bf16, float* zvec);
+void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
+bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
+
+struct RowArgs {
+    const float* J; const float* dJ; const float* HDD; const float* mdof; const float* f_ext;
+    const float* zvec; float* a; float* part; int N, r, stride; double dt;
+    const NewtonState* ns;
+};
+void launch_row_reduce(cudaStream_t s, const RowArgs& a, int n_blocks);
+
+struct CubArgs {
+    const float* u; const float* J; int N, r;
+    const double* X; const int* tets; const float* Bm; const float* vol; int n_tet;
+    int material; float mu, lam;
+    const int* cub_tets; const float* cub_w; int n_cub;
+    float* fe_w; int* fe_dof; float* part; double* energy; int stride;
+    const NewtonState* ns; int* eval_flag;   // set when a Neo-Hookean tet is inverted
+};
+void launch_cubature(cudaStream_t s, const CubArgs& a);
+
+struct WtaArgs {
+    const float* W; int ld, N, K;           // output layer weights [m_pad][ld], K = n_in
+    const float* a;                          // dense seed [N]
+    const float* fe_w; const int* fe_dof; int n_pairs; double dt2;
+    float* part; int nsplit_dense, nsplit_pairs;   // out [nsplit_dense + nsplit_pairs][K]
+    const NewtonState* ns;
+};
+void launch_wta(cudaStream_t s, const WtaArgs& a);
+
+struct BwdArgs {
+    const float* W; int ld;                  // layer weights [m_pad][ld], rows = n_o, cols = n_i
+    int n_o, n_i, r;
+    const float* in_part; int in_split; int in_ncol;  // incoming delta partials [in_split][in_ncol][n_o]
+    const float* S1; const float* T;         // layer derivative data
+    float* g;                                // scratch [1+r][n_o]
+    float* out_part; int out_split;          // [out_split][1+r][n_i]
+    const NewtonState* ns;
+};
+void launch_bwd(cudaStream_t s, const BwdArgs& a);
+
+struct AsmArgs {
+    int r; double dt, h;
+    const float* row_part; int n_row_blocks, row_stride;
+    const float* cub_part; const double* cub_energy; int n_cub, cub_stride;
+    const float* bwd_part; int bwd_split;   // [split][1+r][r]
+    double* red;                             // out: phi | A | energy | terms
+    NewtonState* ns;                         // null: assemble only
+    int control;                             // 1: Newton control step
+    double tol, c_armijo; int max_iter, max_halvings, max_evals;
+    int* eval_flag;                          // per-evaluation flag of the cubature kernel
+    int* status;                             // sticky device status (assemble-only mode)
+};
+void launch_assemble(cudaStream_t s, const AsmArgs& a);
+// doubles of the reduced-system buffer: outputs, terms and reduction scratch
+inline size_t red_size(int r) {
+    size_t nsym = (size_t)r * (r + 1) / 2;
+    return (size_t)r + r * r + 1 + 4 * (size_t)r * r + r + (r + nsym + (size_t)r * r) + (r + nsym) +
+           (size_t)(1 + r) * r + 1;
+}
+
+void launch_frame_begin(cudaStream_t s, NewtonState* ns, const double* q0, int r, int frame);
+void launch_frame_end(cudaStream_t s, NewtonState* ns, double* q, double* qbar, double* qbar_dot,
+                      double dt, int r, double* traj_row, NewtonState* hist, int advance);
+void launch_predict(cudaStream_t s, double* q0, const double* qbar, const double* qbar_dot,
+                    double dt, int r);
+void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                       size_t n);
+
+}  // namespace dae

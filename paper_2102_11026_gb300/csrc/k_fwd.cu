@@ -1,0 +1,201 @@
+// Forward pass of the stacked complex-step batch: seed columns, CUDA-core FP32
+// layer GEMM with the fused multicomplex activation / output epilogue.
+#include "dae_internal.h"
+#include "epilogue.cuh"
+
+namespace dae {
+
+// ------------------------------------------------------------------- seed --
+// Input components of q* = q + h e_j i1 + h c i2 + h c i3 + h^2 g i2i3 (Sec. 4.3),
+// c = Delta (0 in SEED_HW), g = w (0 in SEED_SDD); column layout in dae_internal.h.
+__global__ void k_seed(const NewtonState* ns, const double* q_override, const double* qbar,
+                       const double* qbar_dot, double dt, double h, int mode, int r, int Cp,
+                       int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
+                       float* zvec) {
+    if (ns && ns->done) return;
+    const double* q = q_override ? q_override : ns->q_trial;
+    const int C = n_cols(r);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Cp * ld0;
+         idx += gridDim.x * blockDim.x) {
+        int c = idx / ld0, k = idx % ld0;
+        double v = 0.0;
+        if (k < r && c < C) {
+            double D = q[k] - qbar[k];
+            double w = 3.0 * D - dt * qbar_dot[k];
+            if (c == 0) v = q[k];
+            else if (c == 1) v = (mode == SEED_HW) ? 0.0 : h * D;
+            else if (c == 2) v = (mode == SEED_SDD) ? 0.0 : h * h * w;
+            else if (c >= kShared && (c - kShared) % 3 == 0) v = ((c - kShared) / 3 == k) ? h : 0.0;
+        }
+        store_act((float)v, X, Xh, Xl, (size_t)c * ld0 + k, out_bf16);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < r && zvec) {
+        int k = threadIdx.x;
+        zvec[k] = (float)((q[k] - qbar[k]) - dt * qbar_dot[k]);
+    }
+}
+
+void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,
+                 const double* qbar, const double* qbar_dot, double dt, double h, int mode,
+                 int r, int Cp, int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
+                 int out_bf16, float* zvec) {
+    int n = Cp * ld0;
+    k_seed<<<(n + 255) / 256, 256, 0, s>>>(ns, q_override, qbar, qbar_dot, dt, h, mode, r, Cp,
+                                          ld0, X, Xh, Xl, out_bf16, zvec);
+}
+
+// ------------------------------------------------------- CUDA-core GEMM --
+// Tile: 64 output rows x Cp component columns, K step 32, 256 threads; thread
+// (ty, tx) accumulates rows 4ty..4ty+3 and columns tx + 16 i.
+constexpr int SB_M = 64, SB_K = 32;
+
+template <int NC>
+struct SimtSmem {
+    static constexpr int CP = 16 * NC;
+    union {
+        struct {
+            float Ws[SB_K][SB_M + 4];
+            float Xs[SB_K][CP + 4];
+        } mm;
+        float tile[SB_M][CP + 1];
+    };
+};
+
+// Row epilogue on a tile in shared memory: thread t handles row t%64 and the
+// component groups j = t/64, t/64 + 4, ...
+template <int NC>
+__device__ void simt_epilogue(const FwdArgs& A, float (*tile)[16 * NC + 1], int m0) {
+    const int t = threadIdx.x;
+    const int row = t & (SB_M - 1), grp = t >> 6;
+    const int n = m0 + row;
+    const int r = A.r, C = n_cols(r);
+    const float* v = tile[row];
+    if (!A.last) {
+        if (n >= A.ldy) return;
+        const size_t ldy = A.ldy;
+        if (n >= A.n_out) {   // zero padding rows of the next layer's input
+            for (int c = grp; c < A.Cp; c += 4) store_act(0.f, A.Y, A.Yh, A.Yl, c * ldy + n, A.out_bf16);
+            return;
+        }
+        ActD D = act_d(A.act, v[0] + A.bias[n]);
+        const float c = v[1], gw = v[2];
+        if (grp == 0) {
+            float oc, ogw, og0;
+            mc_shared(D, c, gw, v[3], oc, ogw, og0);
+            store_act(D.s0, A.Y, A.Yh, A.Yl, 0 * ldy + n, A.out_bf16);
+            store_act(oc, A.Y, A.Yh, A.Yl, 1 * ldy + n, A.out_bf16);
+            store_act(ogw, A.Y, A.Yh, A.Yl, 2 * ldy + n, A.out_bf16);
+            store_act(og0, A.Y, A.Yh, A.Yl, 3 * ldy + n, A.out_bf16);
+            for (int cc = C; cc < A.Cp; ++cc) store_act(0.f, A.Y, A.Yh, A.Yl, cc * ldy + n, A.out_bf16);
+            if (A.S1) A.S1[n] = D.s1;
+        }
+        for (int j = grp; j < r; j += 4) {
+            const int cb = kShared + 3 * j;
+            float ob, od, oh;
+            mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
+            store_act(ob, A.Y, A.Yh, A.Yl, (size_t)cb * ldy + n, A.out_bf16);
+            store_act(od, A.Y, A.Yh, A.Yl, (size_t)(cb + 1) * ldy + n, A.out_bf16);
+            store_act(oh, A.Y, A.Yh, A.Yl, (size_t)(cb + 2) * ldy + n, A.out_bf16);
+            if (A.T) A.T[(size_t)j * A.n_out + n] = D.s2 * v[cb];
+        }
+    } else {
+        if (n >= A.n_out) return;
+        const size_t N = A.n_out;
+        if (grp == 0) {
+            if (A.u) A.u[n] = v[0] + A.bias[n];
+            float hdd = (float)(v[3] * A.inv_h2);
+            if (A.HDD) A.HDD[n] = hdd;
+            if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
+        }
+        for (int j = grp; j < r; j += 4) {
+            const int cb = kShared + 3 * j;
+            if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb] * A.inv_h);
+            if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 2] * A.inv_h3);
+        }
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_fwd_simt(FwdArgs A) {
+    if (A.ns && A.ns->done) return;
+    __shared__ SimtSmem<NC> sm;
+    constexpr int CP = 16 * NC;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * SB_M;
+    float acc[4][NC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[i][j] = 0.f;
+    const int K = A.ld;
+    for (int k0 = 0; k0 < K; k0 += SB_K) {
+        for (int i = tid; i < SB_M * (SB_K / 4); i += 256) {
+            int row = i >> 3, kq = i & 7;
+            float4 w = *reinterpret_cast<const float4*>(A.W + (size_t)(m0 + row) * A.ld + k0 + kq * 4);
+            sm.mm.Ws[kq * 4 + 0][row] = w.x;
+            sm.mm.Ws[kq * 4 + 1][row] = w.y;
+            sm.mm.Ws[kq * 4 + 2][row] = w.z;
+            sm.mm.Ws[kq * 4 + 3][row] = w.w;
+        }
+        for (int i = tid; i < CP * (SB_K / 4); i += 256) {
+            int c = i >> 3, kq = i & 7;
+            float4 x = *reinterpret_cast<const float4*>(A.X + (size_t)c * A.ld + k0 + kq * 4);
+            sm.mm.Xs[kq * 4 + 0][c] = x.x;
+            sm.mm.Xs[kq * 4 + 1][c] = x.y;
+            sm.mm.Xs[kq * 4 + 2][c] = x.z;
+            sm.mm.Xs[kq * 4 + 3][c] = x.w;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < SB_K; ++kk) {
+            float4 w4 = *reinterpret_cast<const float4*>(&sm.mm.Ws[kk][ty * 4]);
+            float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+            float xv[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) xv[j] = sm.mm.Xs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < NC; ++j) acc[i][j] = fmaf(wv[i], xv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) sm.tile[ty * 4 + i][tx + 16 * j] = acc[i][j];
+    __syncthreads();
+    simt_epilogue<NC>(A, sm.tile, m0);
+}
+
+void launch_fwd_simt(cudaStream_t s, const FwdArgs& a) {
+    dim3 grid(a.m_pad / SB_M);
+    switch (a.Cp / 16) {
+        case 1: k_fwd_simt<1><<<grid, 256, 0, s>>>(a); break;
+        case 2: k_fwd_simt<2><<<grid, 256, 0, s>>>(a); break;
+        case 3: k_fwd_simt<3><<<grid, 256, 0, s>>>(a); break;
+        case 4: k_fwd_simt<4><<<grid, 256, 0, s>>>(a); break;
+        case 5: k_fwd_simt<5><<<grid, 256, 0, s>>>(a); break;
+        case 6: k_fwd_simt<6><<<grid, 256, 0, s>>>(a); break;
+        case 7: k_fwd_simt<7><<<grid, 256, 0, s>>>(a); break;
+        default: break;
+    }
+}
+
+// ------------------------------------------------------------ BF16 split --
+__global__ void k_split_bf16(const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float v = W[i];
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                       size_t n) {
+    k_split_bf16<<<1024, 256, 0, s>>>(W, hi, lo, n);
+}
+
+}  // namespace dae

@@ -1,0 +1,412 @@
+// Reduced-system kernels: row reductions of the output layer (J^T M J,
+// J^T M dJ, J^T a), warp-per-tet cubature (Sec. 5), W_L^T a, the complex-step
+// reverse pass (Sec. 4.4) and the FP64 assembly / LU / Newton control.
+#include "dae_internal.h"
+#include "epilogue.cuh"
+
+namespace dae {
+
+// ------------------------------------------------------- row reductions --
+// Per block of 128 output rows n (lumped mass m_n on each DOF, Sec. 3.1):
+//   y_n = sum_j J_nj z_j + H[Delta,Delta]_n,  a_n = m_n y_n - dt^2 f_ext,n
+//   phi_i += J_ni a_n,  Mr_ij += m_n J_ni J_nj (i <= j),  B_ij += m_n J_ni dJ_nj
+// Partial layout per block: [phi (r) | Mr upper (r(r+1)/2, row-major i<=j) | B (r*r, i*r+j)].
+constexpr int RR_ROWS = 128;
+
+__global__ void __launch_bounds__(256) k_row_reduce(RowArgs A) {
+    if (A.ns && A.ns->done) return;
+    __shared__ float Js[kMaxR][RR_ROWS + 1];
+    __shared__ float dJs[kMaxR][RR_ROWS + 1];
+    __shared__ float ms[RR_ROWS], as[RR_ROWS];
+    const int r = A.r, t = threadIdx.x;
+    const int n0 = blockIdx.x * RR_ROWS;
+    if (t < RR_ROWS) {
+        const int n = n0 + t;
+        float m = 0.f, a = 0.f;
+        if (n < A.N) {
+            m = A.mdof[n];
+            float y = A.HDD[n];
+            for (int j = 0; j < r; ++j) {
+                float Jv = A.J[(size_t)j * A.N + n];
+                Js[j][t] = Jv;
+                dJs[j][t] = A.dJ[(size_t)j * A.N + n];
+                y = fmaf(Jv, A.zvec[j], y);
+            }
+            a = (float)((double)m * y - A.dt * A.dt * (A.f_ext ? (double)A.f_ext[n] : 0.0));
+            A.a[n] = a;
+        } else {
+            for (int j = 0; j < r; ++j) { Js[j][t] = 0.f; dJs[j][t] = 0.f; }
+        }
+        ms[t] = m;
+        as[t] = a;
+    }
+    __syncthreads();
+    const int nsym = r * (r + 1) / 2;
+    const int n_ent = r + nsym + r * r;
+    float* out = A.part + (size_t)blockIdx.x * A.stride;
+    for (int e = t; e < n_ent; e += blockDim.x) {
+        float acc = 0.f;
+        if (e < r) {
+            for (int k = 0; k < RR_ROWS; ++k) acc = fmaf(Js[e][k], as[k], acc);
+        } else if (e < r + nsym) {
+            int p = e - r, i = 0;
+            while (p >= r - i) { p -= r - i; ++i; }
+            int j = i + p;
+            for (int k = 0; k < RR_ROWS; ++k) acc = fmaf(ms[k] * Js[i][k], Js[j][k], acc);
+        } else {
+            int p = e - r - nsym, i = p / r, j = p % r;
+            for (int k = 0; k < RR_ROWS; ++k) acc = fmaf(ms[k] * Js[i][k], dJs[j][k], acc);
+        }
+        out[e] = acc;
+    }
+}
+
+void launch_row_reduce(cudaStream_t s, const RowArgs& a, int n_blocks) {
+    k_row_reduce<<<n_blocks, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------------------- cubature --
+// One warp per cubature tet e (Sec. 5), displacement gradient G = dU Dm^{-1}
+// (F = I + G, formed from differences so small strains keep their accuracy):
+//   StVK: E = (G + G^T + G^T G)/2, S = 2 mu E + lam tr(E) I, P = F S,
+//         Psi = mu tr(E^2) + lam/2 tr(E)^2
+//   NH:   P = mu (F - F^{-T}) + lam ln(J) F^{-T},
+//         Psi = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2
+//   f_e = V_e P Dm^{-T} (nodes 1..3; node 0 = minus their sum)
+// Lane j < r takes the displacement direction of J's column j on the tet's 12
+// DOFs, dG_j, and its stress differential dP_j = dP[dG_j]; then
+//   g_j  = V_e P : dG_j            (= (J_e^T f_e)_j)
+//   K_ij = V_e dG_i : dP_j         (= (J_e^T K_e J_e)_ij)
+// Partial per slot: [w g (r) | w K upper (r(r+1)/2)], energy w V Psi (FP64).
+__device__ __forceinline__ void mat3_mul(const double* A, const double* B, double* C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[i * 3 + j] = A[i * 3 + 0] * B[0 * 3 + j] + A[i * 3 + 1] * B[1 * 3 + j] +
+                           A[i * 3 + 2] * B[2 * 3 + j];
+}
+
+__global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
+    if (A.ns && A.ns->done) return;
+    __shared__ float sdG[8][kMaxR][9];
+    __shared__ float sdP[8][kMaxR][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * 8 + warp;
+    if (slot >= A.n_cub) return;
+    const int r = A.r;
+    const int nsym = r * (r + 1) / 2;
+    float* part = A.part + (size_t)slot * A.stride;
+    const int tet = A.cub_tets[slot];
+    const float wgt = A.cub_w[slot];
+    if (tet < 0 || tet >= A.n_tet) {   // index checked here too: device arrays skip the host check
+        if (lane == 0) {
+            if (A.eval_flag) atomicExch(A.eval_flag, 2);
+            A.energy[slot] = 0.0;
+        }
+        for (int e = lane; e < r + nsym; e += 32) part[e] = 0.f;
+        if (lane < 12) { A.fe_w[slot * 12 + lane] = 0.f; A.fe_dof[slot * 12 + lane] = 0; }
+        return;
+    }
+    int v[4];
+    for (int a = 0; a < 4; ++a) v[a] = A.tets[4 * tet + a];
+    const float* Bmf = A.Bm + 9 * (size_t)tet;
+    double Bm[9];
+    for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
+    const double V = A.vol[tet];
+    // dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
+    double dU[9];
+    for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d)
+            dU[d * 3 + c] = (double)A.u[3 * v[c + 1] + d] - (double)A.u[3 * v[0] + d];
+    double G[9], F[9], P[9], psi;
+    mat3_mul(dU, Bm, G);
+    for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.0 : 0.0);
+    const double mu = A.mu, lam = A.lam;
+    double Finv_T[9], lnJ = 0.0, Sst[9];
+    bool bad = false;
+    if (A.material == DAE_STVK) {
+        double E[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double gg = 0.0;
+                for (int k = 0; k < 3; ++k) gg += G[k * 3 + i] * G[k * 3 + j];
+                E[i * 3 + j] = 0.5 * (G[i * 3 + j] + G[j * 3 + i] + gg);
+            }
+        double trE = E[0] + E[4] + E[8];
+        double trE2 = 0.0;
+        for (int i = 0; i < 9; ++i) trE2 += E[i] * E[i];
+        for (int i = 0; i < 9; ++i) Sst[i] = 2.0 * mu * E[i] + ((i % 4) == 0 ? lam * trE : 0.0);
+        mat3_mul(F, Sst, P);
+        psi = mu * trE2 + 0.5 * lam * trE * trE;
+    } else {
+        // J - 1 = tr G + (principal 2x2 minors of G) + det G
+        double trG = G[0] + G[4] + G[8];
+        double m2 = G[0] * G[4] - G[1] * G[3] + G[0] * G[8] - G[2] * G[6] + G[4] * G[8] - G[5] * G[7];
+        double detG = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                    G[2] * (G[3] * G[7] - G[4] * G[6]);
+        double Jm1 = trG + m2 + detG;
+        double Jd = 1.0 + Jm1;
+        if (!(Jd > 0.0)) {
+            bad = true;
+            psi = 0.0;
+            for (int i = 0; i < 9; ++i) P[i] = 0.0;
+        } else {
+            lnJ = log1p(Jm1);
+            // F^{-T} = cof(F) / J
+            double cof[9];
+            cof[0] = F[4] * F[8] - F[5] * F[7];
+            cof[1] = F[5] * F[6] - F[3] * F[8];
+            cof[2] = F[3] * F[7] - F[4] * F[6];
+            cof[3] = F[2] * F[7] - F[1] * F[8];
+            cof[4] = F[0] * F[8] - F[2] * F[6];
+            cof[5] = F[1] * F[6] - F[0] * F[7];
+            cof[6] = F[1] * F[5] - F[2] * F[4];
+            cof[7] = F[2] * F[3] - F[0] * F[5];
+            cof[8] = F[0] * F[4] - F[1] * F[3];
+            for (int i = 0; i < 9; ++i) Finv_T[i] = cof[i] / Jd;
+            for (int i = 0; i < 9; ++i) P[i] = mu * (F[i] - Finv_T[i]) + lam * lnJ * Finv_T[i];
+            double gg = 0.0;
+            for (int i = 0; i < 9; ++i) gg += G[i] * G[i];
+            // tr F^T F - 3 = 2 tr G + |G|^2
+            psi = 0.5 * mu * (2.0 * trG + gg) - mu * lnJ + 0.5 * lam * lnJ * lnJ;
+        }
+    }
+    if (bad) {
+        if (lane == 0) {
+            if (A.eval_flag) atomicExch(A.eval_flag, 1);
+            A.energy[slot] = 0.0;
+        }
+        for (int e = lane; e < r + nsym; e += 32) part[e] = 0.f;
+        if (lane < 12) { A.fe_w[slot * 12 + lane] = 0.f; A.fe_dof[slot * 12 + lane] = 0; }
+        return;
+    }
+    // nodal forces: H = V P Bm^T, f(node c+1, d) = H[d][c], f(node 0) = -sum
+    if (lane < 12) {
+        int node = lane / 3, d = lane % 3;
+        double f = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double Hdc = 0.0;
+            for (int k = 0; k < 3; ++k) Hdc += P[d * 3 + k] * Bm[c * 3 + k];
+            Hdc *= V;
+            if (node == 0) f -= Hdc;
+            else if (c == node - 1) f = Hdc;
+        }
+        A.fe_w[slot * 12 + lane] = (float)(wgt * f);
+        A.fe_dof[slot * 12 + lane] = 3 * v[node] + d;
+    }
+    if (lane == 0) A.energy[slot] = (double)wgt * V * psi;
+    // directional quantities per column j
+    float g_j = 0.f;
+    if (lane < r) {
+        const float* Jc = A.J + (size_t)lane * A.N;
+        float dUj[9], dGj[9], dPj[9];
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d)
+                dUj[d * 3 + c] = Jc[3 * v[c + 1] + d] - Jc[3 * v[0] + d];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                dGj[i * 3 + j] = dUj[i * 3 + 0] * (float)Bm[0 * 3 + j] +
+                                 dUj[i * 3 + 1] * (float)Bm[1 * 3 + j] +
+                                 dUj[i * 3 + 2] * (float)Bm[2 * 3 + j];
+        if (A.material == DAE_STVK) {
+            // dE = (dG^T F + F^T dG)/2, dS = 2 mu dE + lam tr(dE) I, dP = dG S + F dS
+            float dE[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    float s = 0.f;
+                    for (int k = 0; k < 3; ++k)
+                        s += dGj[k * 3 + i] * (float)F[k * 3 + j] + (float)F[k * 3 + i] * dGj[k * 3 + j];
+                    dE[i * 3 + j] = 0.5f * s;
+                }
+            float trdE = dE[0] + dE[4] + dE[8];
+            float dS[9];
+            for (int i = 0; i < 9; ++i) dS[i] = 2.f * (float)mu * dE[i] + ((i % 4) == 0 ? (float)lam * trdE : 0.f);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    float s = 0.f;
+                    for (int k = 0; k < 3; ++k)
+                        s += dGj[i * 3 + k] * (float)Sst[k * 3 + j] + (float)F[i * 3 + k] * dS[k * 3 + j];
+                    dPj[i * 3 + j] = s;
+                }
+        } else {
+            // dP = mu dG + (mu - lam lnJ) F^{-T} dG^T F^{-T} + lam (F^{-T}:dG) F^{-T}
+            float FiT[9];
+            for (int i = 0; i < 9; ++i) FiT[i] = (float)Finv_T[i];
+            float tr = 0.f;
+            for (int i = 0; i < 9; ++i) tr += FiT[i] * dGj[i];
+            float M1[9];   // F^{-T} dG^T
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    float s = 0.f;
+                    for (int k = 0; k < 3; ++k) s += FiT[i * 3 + k] * dGj[j * 3 + k];
+                    M1[i * 3 + j] = s;
+                }
+            const float c1 = (float)(mu - lam * lnJ);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    float s = 0.f;
+                    for (int k = 0; k < 3; ++k) s += M1[i * 3 + k] * FiT[k * 3 + j];
+                    dPj[i * 3 + j] = (float)mu * dGj[i * 3 + j] + c1 * s + (float)lam * tr * FiT[i * 3 + j];
+                }
+        }
+        float gs = 0.f;
+        for (int i = 0; i < 9; ++i) gs += (float)P[i] * dGj[i];
+        g_j = (float)(V * gs);
+        for (int i = 0; i < 9; ++i) { sdG[warp][lane][i] = dGj[i]; sdP[warp][lane][i] = dPj[i]; }
+    }
+    __syncwarp();
+    if (lane < r) part[lane] = wgt * g_j;
+    const float wV = (float)(wgt * V);
+    for (int e = lane; e < nsym; e += 32) {
+        int p = e, i = 0;
+        while (p >= r - i) { p -= r - i; ++i; }
+        int j = i + p;
+        float s = 0.f;
+        for (int k = 0; k < 9; ++k) s = fmaf(sdG[warp][i][k], sdP[warp][j][k], s);
+        part[r + e] = wV * s;
+    }
+}
+
+void launch_cubature(cudaStream_t s, const CubArgs& a) {
+    if (a.n_cub <= 0) return;
+    k_cubature<<<(a.n_cub + 7) / 8, 256, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------- W_L^T a GEMV --
+// part[s][k] = sum_{n in split s} W[n][k] a_n                       (s < nsplit_dense)
+// part[nsplit_dense + t][k] = dt^2 sum_{p in pair split t} W[dof_p][k] (w f)_p
+// (the cubature rows; pairs may repeat a DOF, which only adds).
+// Thread = 4 consecutive k (float4), 4 rows in flight.
+__device__ __forceinline__ void fma4(float4& acc, const float4& w, float a) {
+    acc.x = fmaf(w.x, a, acc.x);
+    acc.y = fmaf(w.y, a, acc.y);
+    acc.z = fmaf(w.z, a, acc.z);
+    acc.w = fmaf(w.w, a, acc.w);
+}
+
+__global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
+    if (A.ns && A.ns->done) return;
+    const int k4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (k4 >= A.K) return;
+    const int s = blockIdx.y;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < A.nsplit_dense) {
+        const int per = (A.N + A.nsplit_dense - 1) / A.nsplit_dense;
+        const int n0 = s * per, n1 = min(A.N, n0 + per);
+        int n = n0;
+        for (; n + 4 <= n1; n += 4) {
+            float4 w[4];
+            float av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = __ldg(reinterpret_cast<const float4*>(A.W + (size_t)(n + u) * A.ld + k4));
+                av[u] = __ldg(A.a + n + u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fma4(acc, w[u], av[u]);
+        }
+        for (; n < n1; ++n)
+            fma4(acc, __ldg(reinterpret_cast<const float4*>(A.W + (size_t)n * A.ld + k4)),
+                 __ldg(A.a + n));
+    } else {
+        const int t = s - A.nsplit_dense;
+        const int per = (A.n_pairs + A.nsplit_pairs - 1) / A.nsplit_pairs;
+        const int p0 = t * per, p1 = min(A.n_pairs, p0 + per);
+        for (int p = p0; p < p1; ++p) {
+            const int n = A.fe_dof[p];
+            const float av = (float)(A.dt2 * A.fe_w[p]);
+            fma4(acc, __ldg(reinterpret_cast<const float4*>(A.W + (size_t)n * A.ld + k4)), av);
+        }
+    }
+    // scalar stores: the partial rows have stride K, which need not keep 16-byte alignment
+    float* out = A.part + (size_t)s * A.K + k4;
+    const float v[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (k4 + u < A.K) out[u] = v[u];
+}
+
+void launch_wta(cudaStream_t s, const WtaArgs& a) {
+    dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs);
+    k_wta<<<grid, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------- complex-step reverse --
+// Complex-step backpropagation of g(q) = a . D(q) (Sec. 4.4): the forward pass
+// carried q + h e_j i1 for every j; delta has a real column and one i1 column
+// per j.  Through the activation of layer l (pre-activation a + b_j i1):
+//   Re(g)   = Re(delta) act'(a)
+//   Im_j(g) = Im_j(delta) act'(a) + Re(delta) act''(a) b_j
+// (terms of relative order h^2 dropped as in the forward pass), then
+// delta_{l-1} = W_l^T g.  At the input Re = J^T a and Im_j / h = (a^T H)[:, j].
+// Incoming partials [in_split][in_ncol][n_o] are summed in a fixed order.
+constexpr int BW_THREADS = 128, BW_CHUNK = 32;
+
+// g[c][k] for k < n_o from the incoming partials (fixed summation order).
+__global__ void k_bwd_prep(BwdArgs A) {
+    if (A.ns && A.ns->done) return;
+    const int ncol = 1 + A.r;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncol * A.n_o;
+         e += gridDim.x * blockDim.x) {
+        const int c = e / A.n_o, k = e % A.n_o;
+        float re = 0.f;
+        for (int s = 0; s < A.in_split; ++s) re += A.in_part[((size_t)s * A.in_ncol) * A.n_o + k];
+        float v;
+        if (c == 0) {
+            v = re * A.S1[k];
+        } else {
+            float im = 0.f;
+            if (A.in_ncol > 1)
+                for (int s = 0; s < A.in_split; ++s)
+                    im += A.in_part[((size_t)s * A.in_ncol + c) * A.n_o + k];
+            v = fmaf(im, A.S1[k], re * A.T[(size_t)(c - 1) * A.n_o + k]);
+        }
+        A.g[e] = v;
+    }
+}
+
+// out_part[s][c][m] = sum_{k in split s} W[k][m] g[c][k]
+template <int NCOL>
+__global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
+    if (A.ns && A.ns->done) return;
+    __shared__ float gs[BW_CHUNK][NCOL];
+    const int m = blockIdx.x * BW_THREADS + threadIdx.x;
+    const int ncol = 1 + A.r;
+    const int per = (A.n_o + A.out_split - 1) / A.out_split;
+    const int k0 = blockIdx.y * per, k1 = min(A.n_o, k0 + per);
+    float acc[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) acc[c] = 0.f;
+    for (int kc = k0; kc < k1; kc += BW_CHUNK) {
+        const int kn = min(BW_CHUNK, k1 - kc);
+        __syncthreads();
+        for (int e = threadIdx.x; e < BW_CHUNK * NCOL; e += BW_THREADS) {
+            int kk = e / NCOL, c = e % NCOL;
+            gs[kk][c] = (kk < kn && c < ncol) ? A.g[(size_t)c * A.n_o + kc + kk] : 0.f;
+        }
+        __syncthreads();
+        if (m < A.n_i) {
+            for (int kk = 0; kk < kn; ++kk) {
+                float w = __ldg(A.W + (size_t)(kc + kk) * A.ld + m);
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) acc[c] = fmaf(w, gs[kk][c], acc[c]);
+            }
+        }
+    }
+    if (m < A.n_i) {
+        for (int c = 0; c < ncol; ++c)
+            A.out_part[((size_t)blockIdx.y * ncol + c) * A.n_i + m] = acc[c];
+    }
+}
+
+void launch_bwd(cudaStream_t s, const BwdArgs& a) {
+    int ncol = 1 + a.r;
+    int n = ncol * a.n_o;
+    k_bwd_prep<<<(n + 255) / 256, 256, 0, s>>>(a);
+    dim3 grid((a.n_i + BW_THREADS - 1) / BW_THREADS, a.out_split);
+    if (ncol <= 8) k_bwd<8><<<grid, BW_THREADS, 0, s>>>(a);
+    else if (ncol <= 16) k_bwd<16><<<grid, BW_THREADS, 0, s>>>(a);
+    else if (ncol <= 24) k_bwd<24><<<grid, BW_THREADS, 0, s>>>(a);
+    else k_bwd<33><<<grid, BW_THREADS, 0, s>>>(a);
+}
+
+}  // namespace dae

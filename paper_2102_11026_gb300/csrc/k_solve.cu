@@ -1,0 +1,309 @@
+// FP64 assembly of the reduced system (Eqs. 10-11 with n_p = 0), the dense
+// LU solve of the Newton step and the device-side Newton / line-search control.
+#include <math.h>
+#include "dae_internal.h"
+#include "epilogue.cuh"
+
+namespace dae {
+
+// out[e] = sum_p part[p * stride + e] for e < n_ent, in FP64; 32 threads per entry
+// with a fixed summation tree (bitwise reproducible).
+__global__ void k_colsum(const float* part, int n_parts, int stride, int n_ent, double* out,
+                         const NewtonState* ns) {
+    if (ns && ns->done) return;
+    const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= n_ent) return;
+    double acc = 0.0;
+    for (int p = lane; p < n_parts; p += 32) acc += (double)part[(size_t)p * stride + e];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[e] = acc;
+}
+
+__global__ void k_dsum(const double* x, int n, double* out, const NewtonState* ns) {
+    if (ns && ns->done) return;
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) acc += x[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+static inline void colsum(cudaStream_t st, const float* part, int n_parts, int stride, int n_ent,
+                          double* out, const NewtonState* ns) {
+    k_colsum<<<(n_ent + 7) / 8, 256, 0, st>>>(part, n_parts, stride, n_ent, out, ns);
+}
+
+__device__ __forceinline__ int upper_idx(int i, int j, int r) {
+    if (i > j) { int t = i; i = j; j = t; }
+    return i * r - i * (i - 1) / 2 + (j - i);
+}
+
+// Solve A x = b (r <= 32, A column-major in global memory) with LU and partial
+// pivoting, one warp.  Returns 0, or DAE_ERR_SINGULAR.
+__device__ int warp_lu_solve(const double* A, const double* b, double* x, int r,
+                             double (*M)[kMaxR + 1], double* rhs) {
+    const int lane = threadIdx.x & 31;
+    double amax = 0.0;
+    for (int i = 0; i < r; ++i) {
+        if (lane < r) {
+            M[i][lane] = A[i + lane * r];
+            amax = fmax(amax, fabs(M[i][lane]));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane < r) rhs[lane] = b[lane];
+    __syncwarp();
+    int sing = 0;
+    for (int k = 0; k < r; ++k) {
+        double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
+        int p = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+            if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+        }
+        if (!(v > 1e-14 * amax) || !isfinite(v)) { sing = 1; break; }
+        if (p != k) {
+            if (lane < r) { double t = M[k][lane]; M[k][lane] = M[p][lane]; M[p][lane] = t; }
+            if (lane == 0) { double t = rhs[k]; rhs[k] = rhs[p]; rhs[p] = t; }
+        }
+        __syncwarp();
+        const double piv = M[k][k];
+        if (lane > k && lane < r) {
+            const double l = M[lane][k] / piv;
+            for (int j = k + 1; j < r; ++j) M[lane][j] -= l * M[k][j];
+            rhs[lane] -= l * rhs[k];
+            M[lane][k] = 0.0;
+        }
+        __syncwarp();
+    }
+    if (sing) return DAE_ERR_SINGULAR;
+    if (lane == 0) {
+        for (int i = r - 1; i >= 0; --i) {
+            double s = rhs[i];
+            for (int j = i + 1; j < r; ++j) s -= M[i][j] * x[j];
+            x[i] = s / M[i][i];
+        }
+    }
+    __syncwarp();
+    return 0;
+}
+
+// Combine the reductions into phi, A, energy and the separate terms, then (if
+// control) take one step of the Newton / Armijo control.
+//   rowsum  [phi_dense (r) | Mr upper | B (i*r+j)]
+//   cubsum  [g_int (r) | K_r upper]
+//   bwdsum  [(1+r) x r]: column 0 = J^T a, column 1+j = h (a^T H)[:, j]
+//   red     [phi (r) | A (r*r col-major) | energy | aH | Mr | B | Kr | g_int]
+struct CtlArgs {
+    int r; double dt, h;
+    const double* rowsum; const double* cubsum; const double* bwdsum; const double* esum;
+    int have_cub;
+    double* red;
+    NewtonState* ns; int control;
+    double tol, c_armijo; int max_iter, max_halvings, max_evals;
+    int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
+    int* status;
+};
+
+__global__ void k_control(CtlArgs C) {
+    if (C.ns && C.ns->done) return;
+    __shared__ double M[kMaxR][kMaxR + 1];
+    __shared__ double rhs[kMaxR];
+    __shared__ double x[kMaxR];
+    __shared__ int nonfinite;
+    const int r = C.r, t = threadIdx.x;
+    const double dt2 = C.dt * C.dt;
+    const int nsym = r * (r + 1) / 2;
+    double* phi = C.red;
+    double* A = C.red + r;
+    double* energy = C.red + r + r * r;
+    double* aH = energy + 1;
+    double* Mr = aH + r * r;
+    double* Bm = Mr + r * r;
+    double* Kr = Bm + r * r;
+    double* gint = Kr + r * r;
+    if (t == 0) nonfinite = 0;
+    __syncthreads();
+    for (int e = t; e < r * r; e += blockDim.x) {
+        const int i = e % r, j = e / r;   // column-major (i, j)
+        const double ah = 0.5 * (C.bwdsum[(1 + j) * r + i] + C.bwdsum[(1 + i) * r + j]) / C.h;
+        const double mr = C.rowsum[r + upper_idx(i, j, r)];
+        const double b = C.rowsum[r + nsym + i * r + j];
+        const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
+        const double a = ah + mr + b + dt2 * kr;
+        aH[e] = ah; Mr[e] = mr; Bm[e] = b; Kr[e] = kr;
+        A[e] = a;
+        if (!isfinite(a)) nonfinite = 1;
+    }
+    for (int i = t; i < r; i += blockDim.x) {
+        const double g = C.have_cub ? C.cubsum[i] : 0.0;
+        gint[i] = g;
+        const double p = C.rowsum[i] + dt2 * g;
+        phi[i] = p;
+        if (!isfinite(p)) nonfinite = 1;
+    }
+    if (t == 0) *energy = C.have_cub ? *C.esum : 0.0;
+    __syncthreads();
+    const int flag = C.eval_flag ? *C.eval_flag : 0;   // 1 inverted tet, 2 bad cubature index
+    const int inverted = flag != 0;
+    if (!C.control) {
+        if (t == 0) {
+            if (flag == 2) set_status(C.status, DAE_ERR_INVALID_ARG);
+            else if (inverted) set_status(C.status, DAE_ERR_INVERTED);
+            else if (nonfinite) set_status(C.status, DAE_ERR_NONFINITE);
+            if (C.eval_flag) *C.eval_flag = 0;
+        }
+        return;
+    }
+    if (t >= 32) return;
+    NewtonState* ns = C.ns;
+    __shared__ int decision;   // 0 reject, 1 accept-and-continue, 2 accept-and-stop, 3 stop
+    if (t == 0) {
+        ns->evals += 1;
+        double merit = 0.0;
+        for (int i = 0; i < r; ++i) merit += phi[i] * phi[i];
+        const bool bad = inverted || nonfinite || !isfinite(merit);
+        int dec;
+        if (ns->evals == 1) {
+            if (bad) {
+                ns->status = flag == 2 ? DAE_ERR_INVALID_ARG
+                           : (inverted ? DAE_ERR_INVERTED : DAE_ERR_NONFINITE);
+                dec = 3;
+            } else {
+                ns->phi_norm0 = sqrt(merit);
+                dec = 1;
+            }
+        } else {
+            const bool ok = !bad && merit <= (1.0 - 2.0 * C.c_armijo * ns->alpha) * ns->merit_acc;
+            dec = ok ? 1 : 0;
+        }
+        if (dec == 1) {
+            for (int i = 0; i < r; ++i) { ns->q_acc[i] = ns->q_trial[i]; ns->phi[i] = phi[i]; }
+            ns->merit_acc = merit;
+            ns->energy = *energy;
+            if (ns->evals > 1) ns->iters += 1;
+            const double pn = sqrt(merit);
+            if (pn <= C.tol * fmax(1.0, ns->phi_norm0)) { ns->converged = 1; dec = 2; }
+            else if (ns->iters >= C.max_iter) dec = 2;
+        } else if (dec == 0) {
+            if (ns->halvings >= C.max_halvings) dec = 3;
+        }
+        if (dec != 3 && dec != 2 && ns->evals >= C.max_evals) dec = 3;
+        decision = dec;
+    }
+    __syncwarp();
+    const int dec = decision;
+    if (dec == 1) {
+        for (int i = t; i < r; i += 32) rhs[i] = -phi[i];
+        __syncwarp();
+        int st = warp_lu_solve(A, rhs, x, r, M, rhs);
+        __syncwarp();
+        if (t == 0) {
+            if (st) {
+                ns->status = st;
+                ns->done = 1;
+            } else {
+                for (int i = 0; i < r; ++i) {
+                    ns->delta[i] = x[i];
+                    ns->q_trial[i] = ns->q_acc[i] + x[i];
+                }
+                ns->alpha = 1.0;
+                ns->halvings = 0;
+            }
+        }
+    } else if (dec == 0) {
+        if (t == 0) {
+            ns->alpha *= 0.5;
+            ns->halvings += 1;
+            for (int i = 0; i < r; ++i) ns->q_trial[i] = ns->q_acc[i] + ns->alpha * ns->delta[i];
+        }
+    } else if (t == 0) {
+        ns->done = 1;
+    }
+    if (t == 0 && C.eval_flag) *C.eval_flag = 0;
+}
+
+void launch_assemble(cudaStream_t s, const AsmArgs& a) {
+    const int r = a.r;
+    const int nsym = r * (r + 1) / 2;
+    // scratch doubles live after the terms block of red
+    double* base = a.red + (r + r * r + 1 + 4 * r * r + r);
+    double* rowsum = base;
+    double* cubsum = rowsum + (r + nsym + r * r);
+    double* bwdsum = cubsum + (r + nsym);
+    double* esum = bwdsum + (1 + r) * r;
+    colsum(s, a.row_part, a.n_row_blocks, a.row_stride, r + nsym + r * r, rowsum, a.ns);
+    if (a.n_cub > 0) {
+        colsum(s, a.cub_part, a.n_cub, a.cub_stride, r + nsym, cubsum, a.ns);
+        k_dsum<<<1, 256, 0, s>>>(a.cub_energy, a.n_cub, esum, a.ns);
+    }
+    colsum(s, a.bwd_part, a.bwd_split, (1 + r) * r, (1 + r) * r, bwdsum, a.ns);
+    CtlArgs c;
+    c.r = r; c.dt = a.dt; c.h = a.h;
+    c.rowsum = rowsum; c.cubsum = cubsum; c.bwdsum = bwdsum; c.esum = esum;
+    c.have_cub = a.n_cub > 0;
+    c.red = a.red; c.ns = a.ns; c.control = a.control;
+    c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_iter = a.max_iter;
+    c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
+    c.eval_flag = a.eval_flag; c.status = a.status;
+    k_control<<<1, 256, 0, s>>>(c);
+}
+
+// --------------------------------------------------------- frame control --
+__global__ void k_frame_begin(NewtonState* ns, const double* q0, int r, int frame) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < r; ++i) { ns->q_trial[i] = q0[i]; ns->q_acc[i] = q0[i]; ns->delta[i] = 0.0; }
+        ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
+        ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
+        ns->status = 0; ns->frame = frame;
+    }
+}
+
+void launch_frame_begin(cudaStream_t s, NewtonState* ns, const double* q0, int r, int frame) {
+    k_frame_begin<<<1, 32, 0, s>>>(ns, q0, r, frame);
+}
+
+// q <- accepted iterate; with advance: qbar_dot <- (q - qbar)/dt, qbar <- q (Sec. 3.2).
+__global__ void k_frame_end(NewtonState* ns, double* q, double* qbar, double* qbar_dot, double dt,
+                            int r, double* traj_row, NewtonState* hist, int advance) {
+    const int i = threadIdx.x;
+    if (i < r) {
+        const double qn = ns->q_acc[i];
+        if (q) q[i] = qn;
+        if (advance) {
+            qbar_dot[i] = (qn - qbar[i]) / dt;
+            qbar[i] = qn;
+        }
+        if (traj_row) traj_row[i] = qn;
+    }
+    __syncthreads();
+    if (i == 0) {
+        ns->done = 1;
+        if (hist) *hist = *ns;
+    }
+}
+
+void launch_frame_end(cudaStream_t s, NewtonState* ns, double* q, double* qbar, double* qbar_dot,
+                      double dt, int r, double* traj_row, NewtonState* hist, int advance) {
+    k_frame_end<<<1, 32, 0, s>>>(ns, q, qbar, qbar_dot, dt, r, traj_row, hist, advance);
+}
+
+// q0 = qbar + dt * qbar_dot (the first Newton iterate of a rollout frame)
+__global__ void k_predict(double* q0, const double* qbar, const double* qbar_dot, double dt, int r) {
+    const int i = threadIdx.x;
+    if (i < r) q0[i] = qbar[i] + dt * qbar_dot[i];
+}
+
+void launch_predict(cudaStream_t s, double* q0, const double* qbar, const double* qbar_dot,
+                    double dt, int r) {
+    k_predict<<<1, 32, 0, s>>>(q0, qbar, qbar_dot, dt, r);
+}
+
+}  // namespace dae
