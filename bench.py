@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: reduced implicit-Euler Newton iterations per second on one GB300.
+
+Workload (default "paper"): latent r = 30, ten-layer tanh decoder
+30-128-256-512-1024-2048-2048-2048-4096-4096-60000 (282 M weights), 20x20x50
+vertex grid (88 445 tets), Neo-Hookean E = 5e5, nu = 0.45, 500 cubature tets
+with per-frame weights in [0.5, 2], gravity, dt = 1/60, at most 5 Newton
+updates per frame.  All inputs are seeded and synthetic (the paper ships no
+meshes or trained decoders).
+
+A step is one implicit-Euler frame: every evaluation of the frame runs the whole
+hot path (stacked complex-step forward, output-layer reductions, cubature,
+complex-step reverse pass, FP64 assembly, LU and line-search control).
+``value`` = Newton evaluations (iterations incl. the final residual check) per
+second over the timed frames, device-resident inputs; ``e2e`` = the same metric
+through the public C ABI with host buffers, one ``dae_rollout`` call per frame.
+
+--impl reference times the FP64 CPU oracle (the baseline this library is
+checked against) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    from paper_2102_11026_gb300 import synth
+    return synth.paper() if name == "paper" else synth.small()
+
+
+def frame_weights(wl, n_frames, seed, start=0):
+    from paper_2102_11026_gb300 import synth
+    return np.concatenate([synth.make_cubature(wl.mesh.n_tet, wl.cub_tets.size, seed, frame=f)[1]
+                           for f in range(start, start + n_frames)]).astype(np.float32)
+
+
+# --------------------------------------------------------------- roofline --
+def out_layer_bytes(wl, prec):
+    """Algorithmic DRAM bytes of one output-layer launch: weights once, the stacked
+    activations once, the written outputs (u, H[D,D], J, dJ)."""
+    d = wl.dec
+    N, K, r = d.n_out, d.widths[-2], d.r
+    C = 4 + 3 * r
+    wbytes = {"fp32": 4, "tf32": 4, "bf16": 2, "bf16x3": 4}[prec]
+    return N * K * wbytes + C * K * wbytes + N * (2 + 2 * r) * 4
+
+
+def algorithmic_flops(wl):
+    """2 [P C_f + sum_{hidden} P_l (1 + r) + P_L]: stacked forward over all C_f = 3r + 4
+    columns, complex reverse pass through the hidden layers, W_L^T a."""
+    d = wl.dec
+    r = d.r
+    P = [w.size for w in d.W]
+    return 2.0 * (sum(P) * (3 * r + 4) + sum(P[:-1]) * (1 + r) + P[-1])
+
+
+# ---------------------------------------------------------------- oracle --
+def oracle_sample(wl, budget_s):
+    """Time the FP64 oracle on a bounded sample of one Newton evaluation and scale.
+
+    One oracle evaluation = 2r full-decoder jet passes (u, J, H[D,.], dJ), r(r+1)/2
+    hidden-only second-order passes (a^T H), W_L^T a and the cubature FEM.  The
+    sample runs one batch of T full passes (T = OpenMP threads) and one batch of T
+    hidden passes, then scales each batch to its count per evaluation."""
+    import oracle
+    dec, r = wl.dec, wl.dec.r
+    T = oracle.num_threads()
+    q = wl.state.qbar + wl.state.dt * wl.state.qbar_dot
+    E = np.eye(r)[np.arange(T) % r]
+    t0 = time.perf_counter()
+    oracle.decoder_jets(dec, q, E)
+    t_full = time.perf_counter() - t0
+    L = len(dec.W)
+    t0 = time.perf_counter()
+    oracle.decoder_jets(dec, q, E, E, n_run=L - 1)
+    t_hid = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    u = oracle.decode(dec, q)
+    oracle.tets_fk(wl.mesh, u, wl.cub_tets)
+    t_fem = time.perf_counter() - t0
+    n_full, n_hid = 2 * r, r * (r + 1) // 2
+    t_eval = n_full / T * t_full + n_hid / T * t_hid + t_fem
+    sample = ("one batch of %d full-decoder first-order jet passes (%.2f s) and %d hidden-layer "
+              "second-order passes (%.2f s) + decode + %d-tet FEM (%.2f s), scaled to %d full + "
+              "%d hidden passes per evaluation" % (T, t_full, T, t_hid, wl.cub_tets.size, t_fem,
+                                                   n_full, n_hid))
+    return 1.0 / t_eval, T, sample, t_full + t_hid + t_fem
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        v, T, sample, spent = oracle_sample(wl, args.cpu_seconds)
+        if i >= args.warmup:
+            vals.append(v)
+            times.append(spent)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "reduced Newton iterations/s", "value": value,
+        "unit": "iterations/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s decoder + tet grid, one Newton evaluation" % args.workload,
+                   "oracle": "FP64 hyper-dual CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": T, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------- ours --
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2102_11026_gb300 import dae
+
+    wl = make_workload(args.workload)
+    d, m = wl.dec, wl.mesh
+    stream = torch.cuda.Stream()
+    ctx = dae.dae_create(torch.cuda.current_device(), stream.cuda_stream)
+    dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, args.prec)
+    mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass, m.material,
+                             m.E, m.nu)
+    dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+    W, K = args.warmup, args.steps
+    n = wl.cub_tets.size
+    seed = 2 + rank
+    cw_all = frame_weights(wl, W + K, seed)
+    cub_t = dev(wl.cub_tets, torch.int32)
+    cub_w = dev(cw_all, torch.float32)
+    f_ext = dev(wl.f_ext, torch.float32)
+    q = dev(wl.state.qbar, torch.float64)
+    qd = dev(wl.state.qbar_dot, torch.float64)
+    opts = dae.dae_default_newton_opts()
+    opts.max_iter = 5
+
+    with torch.cuda.stream(stream):
+        # warm-up frames (untimed)
+        dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[:W * n], W, q, qd, wl.state.dt, f_ext, opts)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        dae.dae_profile_read(ctx)
+        dae.dae_profile_enable(ctx, True)
+        launches0 = dae.dae_launch_count(ctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        reps = dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[W * n:(W + K) * n], K, q, qd,
+                               wl.state.dt, f_ext, opts)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = dae.dae_launch_count(ctx) - launches0
+        dae.dae_profile_enable(ctx, False)
+        prof = dae.dae_profile_read(ctx)
+        clocks = sampler.stop()
+    evals = sum(rp.evals for rp in reps)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(evals)], device="cuda", dtype=torch.float64)
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        te = t[1:].clone()
+        dist.all_reduce(te, op=dist.ReduceOp.SUM)
+        ms, evals_all = float(tm.item()), float(te.item())
+    else:
+        evals_all = evals
+    value = evals_all / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (output-layer GEMM), timed live
+    peaks, peak_src = load_peaks()
+    t_out, c_out = prof["fwd_out"]
+    # performed output-layer launches = performed evaluations (skipped ones exit at once)
+    avg_out_ms = t_out / max(evals, 1)
+    bytes_out = out_layer_bytes(wl, args.prec)
+    achieved = bytes_out / (avg_out_ms / 1e3) / 1e9
+    hbm = peaks["hbm_gbs"]
+    traffic = load_traffic(args.workload, args.prec)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic,
+            "kernel": "output-layer GEMM + epilogue (%s)" % args.prec,
+            "peak_source": "%s hbm_gbs" % peak_src,
+            "avg_launch_ms": avg_out_ms, "algorithmic_bytes_per_launch": bytes_out}
+    phase_share = {k: round(v[0] / max(ms, 1e-9), 4) for k, v in prof.items()}
+    flops = algorithmic_flops(wl)
+
+    # ---- end to end through the C ABI with host buffers (one dae_rollout per frame)
+    e2e = None
+    if not args.no_e2e:
+        qh = wl.state.qbar.copy()
+        qdh = wl.state.qbar_dot.copy()
+        cwh = frame_weights(wl, K, seed, start=W)
+        ev_tot = 0
+        dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, cwh[:n], 1, qh, qdh, wl.state.dt, wl.f_ext,
+                        opts)
+        qh = wl.state.qbar.copy()
+        qdh = wl.state.qbar_dot.copy()
+        t0 = time.perf_counter()
+        for f in range(K):
+            rp = dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, cwh[f * n:(f + 1) * n], 1, qh, qdh,
+                                 wl.state.dt, wl.f_ext, opts)
+            ev_tot += rp[0].evals
+        te = time.perf_counter() - t0
+        r = d.r
+        h2d = 2 * r * 8 + n * 4 + n * 4 + wl.f_ext.nbytes
+        d2h = 2 * r * 8 + 40 * 8 + 8 * 8 * 4
+        e2e = {"value": ev_tot / te, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    dae.dae_free_decoder(dec)
+    dae.dae_free_mesh(mesh)
+    dae.dae_destroy(ctx)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        v, T, sample, _ = oracle_sample(wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": "iterations/s", "cores": T, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": "reduced Newton iterations/s", "value": value, "unit": "iterations/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": ("paper-scale decoder r=30, 30-128-256-512-1024-2048-2048-2048-"
+                                "4096-4096-60000 tanh, 20x20x50 grid (88445 tets), Neo-Hookean, "
+                                "500 cubature tets, gravity, dt=1/60, <=5 Newton updates/frame")
+                   if args.workload == "paper" else "small decoder r=5 5-64-256-1024-3000",
+                   "step": "one implicit-Euler frame", "frames": K,
+                   "evaluations": int(evals_all), "l2": "inputs larger than L2 (decoder weights "
+                   "%.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "algorithmic_gflop_per_evaluation": flops / 1e9,
+                   "derivative_pass_tflops": flops * evals_all / (ms / 1e3) / 1e12},
+        "roofline": roof, "phase_share": phase_share, "clocks": clocks,
+        "gpu_launches": int(launches), "cpu_baseline": cpu, "e2e": e2e,
+    }
+    print(json.dumps(line))
+
+
+def load_traffic(workload, prec):
+    """DRAM bytes per output-layer launch from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("%s/%s" % (workload, prec))
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

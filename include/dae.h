@@ -230,6 +230,28 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------------ instrumentation -- */
+/* Not part of the paper's method: device timing of the phases of every
+ * evaluation, for benchmarks and profiles. */
+typedef enum {
+    DAE_PHASE_FWD_HIDDEN = 0,  /* hidden-layer GEMMs + multicomplex activation */
+    DAE_PHASE_FWD_OUT = 1,     /* output-layer GEMM + output epilogue */
+    DAE_PHASE_ROWS = 2,        /* J^T M J, J^T M dJ, J^T a row reductions */
+    DAE_PHASE_CUBATURE = 3,    /* cubature forces and stiffness */
+    DAE_PHASE_WTA = 4,         /* W_L^T a */
+    DAE_PHASE_BWD = 5,         /* complex-step reverse pass through the hidden layers */
+    DAE_PHASE_ASSEMBLE = 6,    /* FP64 reductions, assembly, LU and Newton control */
+    DAE_N_PHASES = 7
+} dae_phase;
+
+/* on != 0: record a CUDA event pair around every phase enqueued on ctx. */
+dae_status dae_profile_enable(dae_ctx* ctx, int on);
+/* Synchronize, then return per phase the summed device time (ms) and the number of
+ * recorded phase instances since the previous read (arrays of DAE_N_PHASES). */
+dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count);
+/* Number of kernels enqueued on ctx since it was created. */
+long long dae_launch_count(const dae_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

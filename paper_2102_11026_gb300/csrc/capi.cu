@@ -138,6 +138,37 @@ dae_status check_device_status(dae_ctx* ctx) {
     return DAE_OK;
 }
 
+// Records a CUDA event pair around one phase when profiling is on.
+struct Phase {
+    dae_ctx* c;
+    int ph;
+    cudaEvent_t a = nullptr;
+    static cudaEvent_t get(dae_ctx* c) {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    Phase(dae_ctx* ctx, int phase, int n_kernels) : c(ctx), ph(phase) {
+        c->launches += n_kernels;
+        if (c->prof_on) {
+            a = get(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~Phase() {
+        if (c->prof_on && a) {
+            cudaEvent_t b = get(c);
+            cudaEventRecord(b, c->stream);
+            c->recs.push_back({ph, a, b});
+        }
+    }
+};
+
 int out_bf16_of(dae_prec p) { return p == DAE_BF16 ? 1 : (p == DAE_BF16X3 ? 2 : 0); }
 
 // ----------------------------------------------------------- workspace --
@@ -243,8 +274,11 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     const int r = d->r, L = d->L;
     const int ob = out_bf16_of(d->prec);
     const int ld0 = (int)round_up(r, kKPad);
-    launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0], w.Xh[0],
-                w.Xl[0], ob, w.zvec);
+    {
+        Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
+        launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0],
+                    w.Xh[0], w.Xl[0], ob, w.zvec);
+    }
     for (int l = 0; l < L; ++l) {
         const Layer& ly = d->layers[l];
         FwdArgs a;
@@ -266,6 +300,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         } else {
             a.u = o.u; a.J = o.J; a.dJ = o.dJ; a.HDD = o.HDD; a.Hqq = o.Hqq;
         }
+        Phase p(ctx, a.last ? DAE_PHASE_FWD_OUT : DAE_PHASE_FWD_HIDDEN, 1);
         if (d->prec == DAE_FP32) {
             launch_fwd_simt(s, a);
         } else if (!launch_fwd_tc(s, a, d->prec, ctx->sm_count)) {
@@ -298,14 +333,20 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     ra.J = w.J; ra.dJ = w.dJ; ra.HDD = w.HDD; ra.mdof = m->mdof; ra.f_ext = P.f_ext;
     ra.zvec = w.zvec; ra.a = w.a; ra.part = w.row_part; ra.N = N; ra.r = r;
     ra.stride = w.row_stride; ra.dt = P.dt; ra.ns = ns;
-    launch_row_reduce(s, ra, w.n_row_blocks);
+    {
+        Phase p(ctx, DAE_PHASE_ROWS, 1);
+        launch_row_reduce(s, ra, w.n_row_blocks);
+    }
     CubArgs ca;
     ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
     ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu; ca.lam = (float)m->lam;
     ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
     ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
     ca.stride = w.cub_stride; ca.ns = ns; ca.eval_flag = w.eval_flag;
-    launch_cubature(s, ca);
+    {
+        Phase p(ctx, DAE_PHASE_CUBATURE, P.n_cub > 0 ? 1 : 0);
+        launch_cubature(s, ca);
+    }
     // delta_{L-1} = W_L^T a  (dense rows + cubature rows)
     const Layer& top = d->layers[L - 1];
     const int K = top.n_in;
@@ -316,7 +357,10 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     wa.nsplit_dense = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * sm + kb - 1) / kb)));
     wa.nsplit_pairs = std::max(1, std::min(64, (wa.n_pairs + 95) / 96));
     wa.part = w.bwd_part[0]; wa.ns = ns;
-    launch_wta(s, wa);
+    {
+        Phase p(ctx, DAE_PHASE_WTA, 1);
+        launch_wta(s, wa);
+    }
     int in_split = wa.nsplit_dense + wa.nsplit_pairs, in_ncol = 1, cur = 0;
     for (int l = L - 2; l >= 0; --l) {
         BwdArgs ba;
@@ -328,7 +372,10 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         ba.out_split = std::max(1, std::min((2 * sm + mb - 1) / mb, std::max(1, ba.n_o / 32)));
         ba.out_part = w.bwd_part[cur ^ 1];
         ba.ns = ns;
-        launch_bwd(s, ba);
+        {
+            Phase p(ctx, DAE_PHASE_BWD, 2);
+            launch_bwd(s, ba);
+        }
         cur ^= 1;
         in_split = ba.out_split;
         in_ncol = 1 + r;
@@ -349,7 +396,10 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         aa.tol = 0; aa.c_armijo = 0; aa.max_iter = 0; aa.max_halvings = 0; aa.max_evals = 0;
     }
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
-    launch_assemble(s, aa);
+    {
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, P.n_cub > 0 ? 5 : 3);
+        launch_assemble(s, aa);
+    }
     CU(ctx, cudaGetLastError());
     return DAE_OK;
 }
@@ -483,6 +533,8 @@ dae_status dae_destroy(dae_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_status);
     dfree(ctx->dstage);
+    for (auto& rec : ctx->recs) { cudaEventDestroy(rec.a); cudaEventDestroy(rec.b); }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
     return DAE_OK;
 }
@@ -773,6 +825,7 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    ctx->launches += 2;
     launch_frame_begin(ctx->stream, d->ws.ns, dq, r, 0);
     for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, d->ws.ns, nullptr, P));
     launch_frame_end(ctx->stream, d->ws.ns, dq, nullptr, nullptr, dt, r, nullptr, nullptr, 0);
@@ -833,6 +886,7 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
         EvalParams P;
         P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw + (size_t)f * n_cub;
         P.n_cub = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+        ctx->launches += 3;
         launch_predict(ctx->stream, w.q0, w.qbar, w.qbar_dot, dt, r);
         launch_frame_begin(ctx->stream, w.ns, w.q0, r, f);
         for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, w.ns, nullptr, P));
@@ -858,5 +912,37 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     }
     return DAE_OK;
 }
+
+dae_status dae_profile_enable(dae_ctx* ctx, int on) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    ctx->prof_on = on ? 1 : 0;
+    return DAE_OK;
+}
+
+dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double> acc(DAE_N_PHASES, 0.0);
+    std::vector<long long> cnt(DAE_N_PHASES, 0);
+    for (auto& rec : ctx->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, rec.a, rec.b) == cudaSuccess) {
+            acc[rec.phase] += t;
+            cnt[rec.phase] += 1;
+        }
+        ctx->ev_pool.push_back(rec.a);
+        ctx->ev_pool.push_back(rec.b);
+    }
+    cudaGetLastError();
+    ctx->recs.clear();
+    for (int i = 0; i < DAE_N_PHASES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (count) count[i] = cnt[i];
+    }
+    return DAE_OK;
+}
+
+long long dae_launch_count(const dae_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 }  // extern "C"

@@ -121,6 +121,12 @@ struct dae_ctx {
     size_t dstage_bytes = 0;
     int sm_count = 0;
     dae::NewtonState* last_ns = nullptr;   // state of the most recent newton step
+    // instrumentation
+    int prof_on = 0;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
 };
 
 struct dae_decoder {

@@ -69,6 +69,9 @@ SIGNATURES = {
     "dae_newton_step": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp,
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
+    "dae_profile_enable": ([_vp, _i], _i),
+    "dae_profile_read": ([_vp, _vp, _vp], _i),
+    "dae_launch_count": ([_vp], ctypes.c_longlong),
     "dae_rollout": ([_vp, _vp, _vp, _i, _vp, _vp, _i, _vp, _vp, _d, _vp,
                      ctypes.POINTER(dae_newton_opts), _vp, ctypes.POINTER(dae_newton_report)], _i),
 }
@@ -189,7 +192,7 @@ def dae_load_mesh(ctx, X, tets, vmass, material="stvk", E=1e5, nu=0.4):
     tets = np.ascontiguousarray(tets, dtype=np.int32) if isinstance(tets, np.ndarray) else tets
     vmass = np.ascontiguousarray(vmass, dtype=np.float64) if isinstance(vmass, np.ndarray) else vmass
     nv = vmass.shape[0]
-    nt = tets.shape[0]
+    nt = (tets.numel() if hasattr(tets, "numel") else tets.size) // 4
     h = _vp()
     _check(ctx, lib().dae_load_mesh(ctx, nv, _ptr(X, np.float64, 3 * nv), nt,
                                     _ptr(tets, np.int32, 4 * nt), _ptr(vmass, np.float64, nv),
@@ -247,3 +250,22 @@ def dae_rollout(ctx, dec, mesh, cub_tets, cub_w, n_frames, q, qdot, dt, f_ext=No
         ctypes.byref(opts) if opts is not None else None, _ptr(q_traj, np.float64),
         ctypes.cast(reps, ctypes.POINTER(dae_newton_report)) if reps is not None else None))
     return list(reps)[:n_frames] if reps is not None else None
+
+
+PHASES = ["fwd_hidden", "fwd_out", "rows", "cubature", "wta", "bwd", "assemble"]
+
+
+def dae_profile_enable(ctx, on=True):
+    _check(ctx, lib().dae_profile_enable(ctx, 1 if on else 0))
+
+
+def dae_profile_read(ctx):
+    """{phase: (total_ms, count)} since the previous read (synchronizes)."""
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), np.int64)
+    _check(ctx, lib().dae_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data))
+    return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def dae_launch_count(ctx):
+    return int(lib().dae_launch_count(ctx))
