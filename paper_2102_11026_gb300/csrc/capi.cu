@@ -288,6 +288,8 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = r; a.Cp = w.Cp;
         a.act = d->act;
         a.last = (l == L - 1);
+        a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32);
+        a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
         a.ns = ns;
         a.status = ctx->d_status;
         a.inv_h = 1.0 / h; a.inv_h2 = 1.0 / (h * h); a.inv_h3 = 1.0 / (h * h * h);
@@ -616,6 +618,27 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     }
     CU(ctx, cudaGetLastError());
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (prec != DAE_FP32) {
+        // TMA descriptors of every layer: A = weights [m_pad][ld], B = input activations [Cp][ld]
+        const bool f32 = (prec == DAE_TF32);
+        for (int l = 0; l < d->L; ++l) {
+            Layer& ly = d->layers[l];
+            const int buf = l & 1;
+            bool ok = make_tmap(&ly.tm[0], f32 ? (const void*)ly.W : (const void*)ly.Wh, f32, ly.ld,
+                                ly.m_pad, 128);
+            ok = ok && make_tmap(&ly.tm[2], f32 ? (const void*)d->ws.X[buf] : (const void*)d->ws.Xh[buf],
+                                 f32, ly.ld, d->ws.Cp, d->ws.Cp);
+            if (prec == DAE_BF16X3) {
+                ok = ok && make_tmap(&ly.tm[1], ly.Wl, false, ly.ld, ly.m_pad, 128);
+                ok = ok && make_tmap(&ly.tm[3], d->ws.Xl[buf], false, ly.ld, d->ws.Cp, d->ws.Cp);
+            } else {
+                ly.tm[1] = ly.tm[0];
+                ly.tm[3] = ly.tm[2];
+            }
+            ly.tm_ok = ok;
+            if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "tensor map encoding failed for layer %d", l);
+        }
+    }
     d->prec = prec;
     return DAE_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a library behind include/dae.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -40,6 +41,8 @@ struct Layer {
     float* b = nullptr;    // [n_out]
     __nv_bfloat16* Wh = nullptr;   // BF16 hi split [m_pad][ld]
     __nv_bfloat16* Wl = nullptr;   // BF16 lo split (W - hi)
+    CUtensorMap tm[4];             // TMA maps: A (W or W hi), A lo, B (input activations), B lo
+    bool tm_ok = false;
 };
 
 // Device-resident Newton control state of one frame.
@@ -166,6 +169,8 @@ struct FwdArgs {
     // hidden-layer outputs
     float* Y; __nv_bfloat16* Yh; __nv_bfloat16* Yl; int ldy;   // next activations [Cp][ldy]
     int out_bf16;                            // 0 none, 1 hi, 2 hi+lo
+    int out_f32;                             // write FP32 activations (FP32 / TF32 inputs)
+    const void* tmaps;                       // 4 CUtensorMap (tensor-core path)
     float* S1; float* T;                     // reverse-pass data
     // output-layer outputs (any may be null)
     float* u; float* J; float* dJ; float* HDD; float* Hqq;
@@ -243,6 +248,7 @@ void launch_frame_end(cudaStream_t s, NewtonState* ns, double* q, double* qbar, 
                       double dt, int r, double* traj_row, NewtonState* hist, int advance);
 void launch_predict(cudaStream_t s, double* q0, const double* qbar, const double* qbar_dot,
                     double dt, int r);
+bool make_tmap(void* out, const void* base, bool fp32, int ld, int rows, int box_rows);
 void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
                        size_t n);
 

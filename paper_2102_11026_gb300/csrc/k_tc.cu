@@ -1,8 +1,427 @@
-// Tensor-core (tcgen05) forward GEMMs: added in a following change.
+// Tensor-core forward GEMMs of the stacked complex-step batch (Sec. 4.3, Sec. 6
+// "CR formulation": real weights act on every stacked component column, so each
+// layer is one dense real GEMM).  sm_103a: TMA tile loads into 128B-swizzled
+// shared memory, tcgen05.mma (one issuing thread) accumulating in TMEM,
+// epilogue warps reading TMEM with tcgen05.ld and applying the multicomplex
+// activation / output epilogue of epilogue.cuh.
+//
+// Tile: 128 output rows (TMEM lanes) x Cp component columns (TMEM columns), the
+// whole K loop in one CTA.  Warp 0: TMA producer; warp 1: TMEM owner + MMA
+// issuer; warps 2-5: epilogue.  Every mbarrier wait is bounded (2 s of
+// %globaltimer); a wait that gives up records DAE_ERR_TIMEOUT and the CTA
+// drains its copies, frees TMEM and exits.
+#include <cuda.h>
 #include "dae_internal.h"
+#include "epilogue.cuh"
 
 namespace dae {
 
-bool launch_fwd_tc(cudaStream_t, const FwdArgs&, dae_prec, int) { return false; }
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s
+
+// Bounded wait for the phase of `bar` with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, rows of 128 bytes with the
+// 128-byte swizzle, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused with 128B swizzle, K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (PREC == DAE_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One output row held in registers (all Cp columns): the same per-row math as the
+// CUDA-core kernel's epilogue, with compile-time column indices.
+template <int NC>
+__device__ __forceinline__ void row_epilogue(const FwdArgs& A, int n, const float* v) {
+    constexpr int CP = 16 * NC;
+    constexpr int JMAX = (CP - kShared) / 3;
+    const int r = A.r;
+    if (!A.last) {
+        if (n >= A.ldy) return;
+        const size_t ldy = A.ldy;
+        auto put = [&](int c, float x) {
+            const size_t idx = (size_t)c * ldy + n;
+            if (A.out_f32) A.Y[idx] = x;
+            if (A.out_bf16) {
+                __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                A.Yh[idx] = hi;
+                if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+        };
+        if (n >= A.n_out) {
+#pragma unroll
+            for (int c = 0; c < CP; ++c) put(c, 0.f);
+            return;
+        }
+        const ActD D = act_d(A.act, v[0] + A.bias[n]);
+        const float c = v[1], gw = v[2];
+        float oc, ogw, og0;
+        mc_shared(D, c, gw, v[3], oc, ogw, og0);
+        put(0, D.s0);
+        put(1, oc);
+        put(2, ogw);
+        put(3, og0);
+        if (A.S1) A.S1[n] = D.s1;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            const int cb = kShared + 3 * j;
+            if (j < r) {
+                float ob, od, oh;
+                mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
+                put(cb, ob);
+                put(cb + 1, od);
+                put(cb + 2, oh);
+                if (A.T) A.T[(size_t)j * A.n_out + n] = D.s2 * v[cb];
+            } else {
+                put(cb, 0.f);
+                put(cb + 1, 0.f);
+                put(cb + 2, 0.f);
+            }
+        }
+#pragma unroll
+        for (int cc = kShared + 3 * JMAX; cc < CP; ++cc) put(cc, 0.f);
+    } else {
+        if (n >= A.n_out) return;
+        const size_t N = A.n_out;
+        if (A.u) A.u[n] = v[0] + A.bias[n];
+        if (A.HDD) A.HDD[n] = (float)(v[3] * A.inv_h2);
+        if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            if (j < r) {
+                const int cb = kShared + 3 * j;
+                if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb] * A.inv_h);
+                if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 2] * A.inv_h3);
+            }
+        }
+    }
+}
+
+constexpr int kMaxStages = 8;
+constexpr int kThreads = 192;
+
+template <int NC, int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+             const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
+             FwdArgs A, int nk, int stages) {
+    constexpr int CP = 16 * NC;
+    constexpr bool X3 = (PREC == DAE_BF16X3);
+    constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;         // K elements per 128-byte row
+    constexpr uint32_t A_BYTES = 128 * 128;
+    constexpr uint32_t B_BYTES = CP * 128;
+    constexpr uint32_t STAGE = (A_BYTES + B_BYTES) * (X3 ? 2 : 1);
+    constexpr uint32_t TMEM_COLS = (CP <= 32) ? 32 : (CP <= 64 ? 64 : 128);
+    constexpr uint32_t ID = idesc(PREC == DAE_TF32 ? 2u : 1u, 128, CP);
+
+    if (A.ns && A.ns->done) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull;
+    __shared__ uint32_t tmem_base;
+    __shared__ int fail;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * 128;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&tfull, 1);
+        fail = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_base, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % stages;
+                const uint32_t ph = (kb / stages) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1)) { fail = 1; break; }
+                mbar_expect_tx(&full[s], STAGE);
+                uint8_t* base = smem + (size_t)s * STAGE;
+                tma_load_2d(base, &tmA, &full[s], kb * KB, m0);
+                tma_load_2d(base + A_BYTES, &tmB, &full[s], kb * KB, 0);
+                if constexpr (X3) {
+                    tma_load_2d(base + A_BYTES + B_BYTES, &tmAlo, &full[s], kb * KB, m0);
+                    tma_load_2d(base + 2 * A_BYTES + B_BYTES, &tmBlo, &full[s], kb * KB, 0);
+                }
+                ++issued;
+            }
+            // drain: the last load of every stage has landed before the CTA may exit
+            for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb) {
+                if (!mbar_wait(&full[kb % stages], (kb / stages) & 1)) fail = 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % stages;
+                const uint32_t ph = (kb / stages) & 1;
+                if (!mbar_wait(&full[s], ph)) { ok = false; fail = 1; break; }
+                tc_fence_after();
+                const uint32_t base = smem_u32(smem + (size_t)s * STAGE);
+                const uint64_t da = sdesc(base), db = sdesc(base + A_BYTES);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t acc = (kb | k) != 0;
+                    mma<PREC>(tmem, da + 2 * k, db + 2 * k, ID, acc);
+                    if constexpr (X3) {
+                        const uint64_t dal = sdesc(base + A_BYTES + B_BYTES);
+                        const uint64_t dbl = sdesc(base + 2 * A_BYTES + B_BYTES);
+                        mma<PREC>(tmem, da + 2 * k, dbl + 2 * k, ID, 1u);
+                        mma<PREC>(tmem, dal + 2 * k, db + 2 * k, ID, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+            mma_commit(&tfull);
+            (void)ok;
+        }
+    } else {
+        const bool ok = mbar_wait(&tfull, 0);
+        tc_fence_after();
+        const int lane_base = 32 * (warp & 3);
+        const int n = m0 + lane_base + lane;
+        float v[CP];
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 16 * c, v + 16 * c);
+            tmem_wait_ld();
+            row_epilogue<NC>(A, n, v);
+        } else {
+            fail = 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && fail && A.status) atomicCAS(A.status, 0, (int)DAE_ERR_TIMEOUT);
+}
+
+template <int NC, int PREC>
+bool launch_inst(cudaStream_t s, const FwdArgs& a) {
+    constexpr int CP = 16 * NC;
+    constexpr bool X3 = (PREC == DAE_BF16X3);
+    constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
+    int stages = (int)((200 * 1024) / STAGE);
+    stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
+    const size_t smem = (size_t)stages * STAGE + 1024;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_fwd_tc<NC, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return false;
+        configured = true;
+    }
+    const int KB = (PREC == DAE_TF32) ? 32 : 64;
+    const int nk = a.ld / KB;
+    const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(a.tmaps);
+    k_fwd_tc<NC, PREC><<<a.m_pad / 128, kThreads, smem, s>>>(tm[0], tm[1], tm[2], tm[3], a, nk,
+                                                             stages);
+    return cudaPeekAtLastError() == cudaSuccess;
+}
+
+template <int PREC>
+bool launch_prec(cudaStream_t s, const FwdArgs& a) {
+    switch (a.Cp / 16) {
+        case 1: return launch_inst<1, PREC>(s, a);
+        case 2: return launch_inst<2, PREC>(s, a);
+        case 3: return launch_inst<3, PREC>(s, a);
+        case 4: return launch_inst<4, PREC>(s, a);
+        case 5: return launch_inst<5, PREC>(s, a);
+        case 6: return launch_inst<6, PREC>(s, a);
+        case 7: return launch_inst<7, PREC>(s, a);
+    }
+    return false;
+}
+
+}  // namespace
+
+bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int) {
+    if (!a.tmaps || a.m_pad % 128 != 0) return false;
+    switch (prec) {
+        case DAE_TF32: return launch_prec<DAE_TF32>(s, a);
+        case DAE_BF16: return launch_prec<DAE_BF16>(s, a);
+        case DAE_BF16X3: return launch_prec<DAE_BF16X3>(s, a);
+        default: return false;
+    }
+}
+
+// ------------------------------------------------------------ tensor maps --
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D row-major matrix [rows][ld] of `elem` bytes, box {box_k elements, box_rows}, 128B swizzle.
+bool make_tmap(void* out, const void* base, bool fp32, int ld, int rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || !base) return false;
+    const int esz = fp32 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(out),
+                    fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 }  // namespace dae
