@@ -244,8 +244,9 @@ typedef enum {
     DAE_N_PHASES = 7
 } dae_phase;
 
-/* on != 0: record a CUDA event pair around every phase enqueued on ctx. */
-dae_status dae_profile_enable(dae_ctx* ctx, int on);
+/* Record a CUDA event pair around every enqueued phase p with bit (1 << p) set in
+ * mask (0 = off; (1 << DAE_N_PHASES) - 1 = all phases). */
+dae_status dae_profile_enable(dae_ctx* ctx, unsigned mask);
 /* Synchronize, then return per phase the summed device time (ms) and the number of
  * recorded phase instances since the previous read (arrays of DAE_N_PHASES). */
 dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count);

@@ -59,7 +59,7 @@ def build(force=False, verbose=False):
     with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
         f.write("\n".join(logs))
     tmp = LIB + ".tmp"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *[r[1] for r in results], "-lcudart"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *[r[1] for r in results], "-lcudart", "-lcublas"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n" + p.stdout + p.stderr)

@@ -7,9 +7,14 @@
 #include <cmath>
 #include <vector>
 
+#include <atomic>
+#include <cublas_v2.h>
+
 #include "dae_internal.h"
 
 using namespace dae;
+
+static std::atomic<unsigned long long> g_mesh_ids{1};
 
 #define DAE_VERSION 10000
 
@@ -155,13 +160,13 @@ struct Phase {
     }
     Phase(dae_ctx* ctx, int phase, int n_kernels) : c(ctx), ph(phase) {
         c->launches += n_kernels;
-        if (c->prof_on) {
+        if (c->prof_on & (1u << phase)) {
             a = get(c);
             cudaEventRecord(a, c->stream);
         }
     }
     ~Phase() {
-        if (c->prof_on && a) {
+        if (a) {
             cudaEvent_t b = get(c);
             cudaEventRecord(b, c->stream);
             c->recs.push_back({ph, a, b});
@@ -204,12 +209,10 @@ dae_status alloc_workspace(dae_decoder* d) {
     // reverse-pass partials: the largest of the W_L^T a splits and the hidden splits
     const int sm = ctx->sm_count;
     const int K = d->widths[L - 1];
-    size_t need = (size_t)(128 + 64) * K;
+    size_t need = (size_t)(128 + 64 + 1) * K;   // dense + pair + f_ext splits
     for (int l = L - 2; l >= 0; --l) {
         int n_o = d->widths[l + 1], n_i = d->widths[l];
-        int mb = (n_i + 127) / 128;
-        int split = std::max(1, std::min((2 * sm + mb - 1) / mb, std::max(1, n_o / 32)));
-        need = std::max(need, (size_t)split * (1 + r) * n_i);
+        need = std::max(need, (size_t)bwd_split(n_i, n_o, sm) * (1 + r) * n_i);
     }
     w.bwd_part_elems = need;
     TRY(dmalloc(ctx, &w.bwd_part[0], need));
@@ -234,6 +237,7 @@ void free_workspace(Workspace& w) {
     dfree(w.gbuf); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
+    dfree(w.G); dfree(w.xy); dfree(w.pext); dfree(w.fext_prev); dfree(w.pext_flag); dfree(w.pext_part);
 }
 
 dae_status ensure_cubature(dae_decoder* d, int n_cub, int n_w) {
@@ -288,7 +292,8 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = r; a.Cp = w.Cp;
         a.act = d->act;
         a.last = (l == L - 1);
-        a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32);
+        // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
+        a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
         a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
         a.ns = ns;
         a.status = ctx->d_status;
@@ -310,6 +315,88 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         }
     }
     CU(ctx, cudaGetLastError());
+    return DAE_OK;
+}
+
+bool use_gram(const dae_decoder* d) {
+    const size_t K = d->widths[d->L - 1];
+    return 2 * K <= (size_t)d->N;
+}
+
+// G = W_L^T diag(m) W_L (set-up, once per decoder/mesh pair; cuBLAS SGEMM in FP32 over row chunks)
+dae_status ensure_gram(dae_decoder* d, const dae_mesh* m) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    if (w.G && w.G_mesh == m->id) return DAE_OK;
+    const Layer& top = d->layers[d->L - 1];
+    const int K = top.n_in, N = top.n_out;
+    if (!w.G) {
+        w.ldG = (int)round_up(K, kKPad);
+        TRY(dmalloc(ctx, &w.G, (size_t)K * w.ldG));
+        TRY(dmalloc(ctx, &w.xy, (size_t)w.ldG));
+    }
+    if (!ctx->cublas) {
+        cublasHandle_t hnd;
+        if (cublasCreate(&hnd) != CUBLAS_STATUS_SUCCESS) return fail(ctx, DAE_ERR_CUDA, "cublasCreate failed");
+        ctx->cublas = hnd;
+    }
+    cublasHandle_t hnd = (cublasHandle_t)ctx->cublas;
+    cublasSetStream(hnd, ctx->stream);
+    cublasSetMathMode(hnd, CUBLAS_DEFAULT_MATH);
+    const int CH = 4096;
+    float* tmp = nullptr;
+    TRY(dmalloc(ctx, &tmp, (size_t)CH * top.ld));
+    for (int n0 = 0; n0 < N; n0 += CH) {
+        const int rows = std::min(CH, N - n0);
+        launch_scale_rows(ctx->stream, top.W + (size_t)n0 * top.ld, top.ld, m->mdof + n0, rows, tmp);
+        const float one = 1.f, beta = n0 == 0 ? 0.f : 1.f;
+        // column-major view: Wc = W^T (K x rows, ld), G += Wc (Wc diag(m))^T
+        cublasStatus_t st = cublasSgemm(hnd, CUBLAS_OP_N, CUBLAS_OP_T, K, K, rows, &one,
+                                        top.W + (size_t)n0 * top.ld, top.ld, tmp, top.ld, &beta,
+                                        w.G, w.ldG);
+        if (st != CUBLAS_STATUS_SUCCESS) {
+            cudaFree(tmp);
+            return fail(ctx, DAE_ERR_CUDA, "cublasSgemm failed (%d)", (int)st);
+        }
+    }
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(tmp);
+    w.G_mesh = m->id;
+    return DAE_OK;
+}
+
+// W_L^T f_ext, recomputed on the device only when f_ext differs from the cached copy.
+dae_status prepare_pext(dae_decoder* d, const float* f_ext_dev) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    if (!f_ext_dev) return DAE_OK;
+    const Layer& top = d->layers[d->L - 1];
+    const int K = top.n_in, N = top.n_out;
+    const int kb = (K + 1023) / 1024;
+    const int splits = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * ctx->sm_count + kb - 1) / kb)));
+    if (!w.pext) {
+        TRY(dmalloc(ctx, &w.pext, (size_t)K + 4));
+        TRY(dmalloc(ctx, &w.fext_prev, (size_t)N));
+        TRY(dmalloc(ctx, &w.pext_flag, 1));
+        TRY(dmalloc(ctx, &w.pext_part, (size_t)splits * K));
+        w.pext_splits = splits;
+    }
+    if (!w.pext_valid) {
+        const int one = 1;
+        CU(ctx, cudaMemcpyAsync(w.pext_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->launches += 4;
+    launch_fext_check(ctx->stream, f_ext_dev, w.fext_prev, N, w.pext_flag);
+    WtaArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.K = K; wa.a = f_ext_dev;
+    wa.nsplit_dense = w.pext_splits; wa.nsplit_pairs = 0; wa.run_flag = w.pext_flag;
+    wa.part = w.pext_part;
+    launch_wta(ctx->stream, wa);
+    launch_pext_finish(ctx->stream, w.pext_part, w.pext_splits, K, w.pext, f_ext_dev, w.fext_prev, N,
+                       w.pext_flag);
+    CU(ctx, cudaGetLastError());
+    w.pext_valid = true;
     return DAE_OK;
 }
 
@@ -349,29 +436,40 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         Phase p(ctx, DAE_PHASE_CUBATURE, P.n_cub > 0 ? 1 : 0);
         launch_cubature(s, ca);
     }
-    // delta_{L-1} = W_L^T a  (dense rows + cubature rows)
+    // delta_{L-1} = W_L^T a = W_L^T M y - dt^2 W_L^T f_ext + dt^2 W_L^T f_C:
+    // with the Gram matrix, W_L^T M y = G x_y (y = W_L x_y) and W_L^T f_ext is cached,
+    // so only the cubature rows of W_L are read again.
     const Layer& top = d->layers[L - 1];
     const int K = top.n_in;
     const int kb = (K + 1023) / 1024;
+    const bool gram = w.G && w.G_mesh == m->id;
     WtaArgs wa;
-    wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.K = K; wa.a = w.a;
+    memset(&wa, 0, sizeof wa);
     wa.fe_w = w.fe_w; wa.fe_dof = w.fe_dof; wa.n_pairs = 12 * P.n_cub; wa.dt2 = P.dt * P.dt;
-    wa.nsplit_dense = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * sm + kb - 1) / kb)));
+    wa.Wp = top.W; wa.ldp = top.ld; wa.K = K;
+    if (gram) {
+        wa.W = w.G; wa.ld = w.ldG; wa.N = K; wa.a = w.xy;
+        wa.pext = P.f_ext ? w.pext : nullptr;
+        wa.pext_scale = (float)(-P.dt * P.dt);
+    } else {
+        wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.a = w.a;
+    }
+    wa.nsplit_dense = std::max(1, std::min(128, std::min((wa.N + 63) / 64, (4 * sm + kb - 1) / kb)));
     wa.nsplit_pairs = std::max(1, std::min(64, (wa.n_pairs + 95) / 96));
     wa.part = w.bwd_part[0]; wa.ns = ns;
     {
-        Phase p(ctx, DAE_PHASE_WTA, 1);
+        Phase p(ctx, DAE_PHASE_WTA, gram ? 2 : 1);
+        if (gram) launch_xy(s, w.X[(L - 1) & 1], top.ld, K, r, w.zvec, P.h, w.xy, ns);
         launch_wta(s, wa);
     }
-    int in_split = wa.nsplit_dense + wa.nsplit_pairs, in_ncol = 1, cur = 0;
+    int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0), in_ncol = 1, cur = 0;
     for (int l = L - 2; l >= 0; --l) {
         BwdArgs ba;
         ba.W = d->layers[l].W; ba.ld = d->layers[l].ld;
         ba.n_o = d->widths[l + 1]; ba.n_i = d->widths[l]; ba.r = r;
         ba.in_part = w.bwd_part[cur]; ba.in_split = in_split; ba.in_ncol = in_ncol;
         ba.S1 = w.S1[l]; ba.T = w.T[l]; ba.g = w.gbuf;
-        int mb = (ba.n_i + 127) / 128;
-        ba.out_split = std::max(1, std::min((2 * sm + mb - 1) / mb, std::max(1, ba.n_o / 32)));
+        ba.out_split = bwd_split(ba.n_i, ba.n_o, sm);
         ba.out_part = w.bwd_part[cur ^ 1];
         ba.ns = ns;
         {
@@ -535,6 +633,7 @@ dae_status dae_destroy(dae_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_status);
     dfree(ctx->dstage);
+    if (ctx->cublas) cublasDestroy((cublasHandle_t)ctx->cublas);
     for (auto& rec : ctx->recs) { cudaEventDestroy(rec.a); cudaEventDestroy(rec.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
@@ -703,6 +802,7 @@ dae_status dae_load_mesh(dae_ctx* ctx, int n_vert, const double* X, int n_tet, c
         for (int d = 0; d < 3; ++d) mdof[3 * (size_t)v + d] = (float)hm[v];
     dae_mesh* m = new dae_mesh();
     m->ctx = ctx;
+    m->id = g_mesh_ids.fetch_add(1);
     m->n_vert = n_vert;
     m->n_tet = n_tet;
     m->material = material;
@@ -801,6 +901,10 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
     const float* dfe;
     TRY(stage_fext(d, f_ext, &dfe));
+    if (use_gram(d)) {
+        TRY(ensure_gram(d, m));
+        TRY(prepare_pext(d, dfe));
+    }
     EvalParams P;
     P.dt = dt; P.h = std::ldexp(1.0, -20); P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.f_ext = dfe; P.control = 0; P.opts = nullptr;
@@ -845,6 +949,10 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
     const float* dfe;
     TRY(stage_fext(d, f_ext, &dfe));
+    if (use_gram(d)) {
+        TRY(ensure_gram(d, m));
+        TRY(prepare_pext(d, dfe));
+    }
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.f_ext = dfe; P.control = 1; P.opts = &opts;
@@ -905,6 +1013,10 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub * n_frames, &dct, &dcw));
     const float* dfe;
     TRY(stage_fext(d, f_ext, &dfe));
+    if (use_gram(d)) {
+        TRY(ensure_gram(d, m));
+        TRY(prepare_pext(d, dfe));
+    }
     for (int f = 0; f < n_frames; ++f) {
         EvalParams P;
         P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw + (size_t)f * n_cub;
@@ -936,9 +1048,9 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     return DAE_OK;
 }
 
-dae_status dae_profile_enable(dae_ctx* ctx, int on) {
+dae_status dae_profile_enable(dae_ctx* ctx, unsigned mask) {
     if (!ctx) return DAE_ERR_INVALID_ARG;
-    ctx->prof_on = on ? 1 : 0;
+    ctx->prof_on = mask;
     return DAE_OK;
 }
 

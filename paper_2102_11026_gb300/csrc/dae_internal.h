@@ -109,6 +109,18 @@ struct Workspace {
     int* eval_flag = nullptr;       // per-evaluation cubature flag
     NewtonState* hist = nullptr;    // per-frame states of a rollout (grown on demand)
     int hist_cap = 0;
+    // Gram matrix G = W_L^T M W_L of the output layer for the mesh masses (W_L^T M y = G x_y)
+    float* G = nullptr;             // [K][ldG]
+    int ldG = 0;
+    unsigned long long G_mesh = 0;  // id of the mesh G was formed for
+    float* xy = nullptr;            // [K] x_y: y = J z + H[D,D] = W_L x_y
+    // W_L^T f_ext, recomputed only when f_ext changes
+    float* pext = nullptr;          // [K]
+    float* fext_prev = nullptr;     // [N]
+    int* pext_flag = nullptr;       // 1: recompute
+    bool pext_valid = false;
+    float* pext_part = nullptr;     // [splits][K]
+    int pext_splits = 0;
 };
 
 }  // namespace dae
@@ -123,9 +135,10 @@ struct dae_ctx {
     void* dstage = nullptr;          // device staging for host arguments
     size_t dstage_bytes = 0;
     int sm_count = 0;
+    void* cublas = nullptr;          // cublasHandle_t (set-up GEMMs only)
     dae::NewtonState* last_ns = nullptr;   // state of the most recent newton step
     // instrumentation
-    int prof_on = 0;
+    unsigned prof_on = 0;          // bit mask of instrumented phases
     long long launches = 0;
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int phase; cudaEvent_t a, b; };
@@ -144,6 +157,7 @@ struct dae_decoder {
 
 struct dae_mesh {
     dae_ctx* ctx = nullptr;
+    unsigned long long id = 0;      // unique per upload
     int n_vert = 0, n_tet = 0;
     dae_material material = DAE_STVK;
     double mu = 0, lam = 0;
@@ -204,13 +218,22 @@ struct CubArgs {
 void launch_cubature(cudaStream_t s, const CubArgs& a);
 
 struct WtaArgs {
-    const float* W; int ld, N, K;           // output layer weights [m_pad][ld], K = n_in
+    const float* W; int ld, N, K;           // dense matrix [N][ld] (W_L, or G with N = K)
     const float* a;                          // dense seed [N]
+    const float* Wp; int ldp;                // matrix of the cubature pair rows (W_L)
+    const float* pext; float pext_scale;     // extra split: pext_scale * pext (or null)
+    const int* run_flag;                     // skip when *run_flag == 0 (or null)
     const float* fe_w; const int* fe_dof; int n_pairs; double dt2;
     float* part; int nsplit_dense, nsplit_pairs;   // out [nsplit_dense + nsplit_pairs][K]
     const NewtonState* ns;
 };
 void launch_wta(cudaStream_t s, const WtaArgs& a);
+void launch_xy(cudaStream_t s, const float* X, int ld, int K, int r, const float* zvec, double h,
+               float* xy, const NewtonState* ns);
+void launch_scale_rows(cudaStream_t s, const float* W, int ld, const float* m, int rows, float* out);
+void launch_fext_check(cudaStream_t s, const float* f, const float* prev, int N, int* flag);
+void launch_pext_finish(cudaStream_t s, const float* part, int splits, int K, float* pext,
+                        const float* f, float* prev, int N, int* flag);
 
 struct BwdArgs {
     const float* W; int ld;                  // layer weights [m_pad][ld], rows = n_o, cols = n_i
@@ -222,6 +245,7 @@ struct BwdArgs {
     const NewtonState* ns;
 };
 void launch_bwd(cudaStream_t s, const BwdArgs& a);
+int bwd_split(int n_i, int n_o, int sm);
 
 struct AsmArgs {
     int r; double dt, h;

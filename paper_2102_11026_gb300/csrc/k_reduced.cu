@@ -3,6 +3,7 @@
 // reverse pass (Sec. 4.4) and the FP64 assembly / LU / Newton control.
 #include "dae_internal.h"
 #include "epilogue.cuh"
+#include <algorithm>
 
 namespace dae {
 
@@ -285,6 +286,7 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& w, float a) {
 
 __global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
     if (A.ns && A.ns->done) return;
+    if (A.run_flag && *A.run_flag == 0) return;
     const int k4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (k4 >= A.K) return;
     const int s = blockIdx.y;
@@ -307,14 +309,20 @@ __global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
         for (; n < n1; ++n)
             fma4(acc, __ldg(reinterpret_cast<const float4*>(A.W + (size_t)n * A.ld + k4)),
                  __ldg(A.a + n));
-    } else {
+    } else if (s < A.nsplit_dense + A.nsplit_pairs) {
         const int t = s - A.nsplit_dense;
         const int per = (A.n_pairs + A.nsplit_pairs - 1) / A.nsplit_pairs;
         const int p0 = t * per, p1 = min(A.n_pairs, p0 + per);
         for (int p = p0; p < p1; ++p) {
             const int n = A.fe_dof[p];
             const float av = (float)(A.dt2 * A.fe_w[p]);
-            fma4(acc, __ldg(reinterpret_cast<const float4*>(A.W + (size_t)n * A.ld + k4)), av);
+            fma4(acc, __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4)), av);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float v = (k4 + u < A.K) ? A.pext_scale * A.pext[k4 + u] : 0.f;
+            if (u == 0) acc.x = v; else if (u == 1) acc.y = v; else if (u == 2) acc.z = v; else acc.w = v;
         }
     }
     // scalar stores: the partial rows have stride K, which need not keep 16-byte alignment
@@ -326,8 +334,72 @@ __global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
 }
 
 void launch_wta(cudaStream_t s, const WtaArgs& a) {
-    dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs);
+    dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs + (a.pext ? 1 : 0));
     k_wta<<<grid, 256, 0, s>>>(a);
+}
+
+// x_y[k] = sum_j X[b_j][k] z_j / h + X[g0][k] / h^2 over the output layer's input
+// activations (stacked columns, see dae_internal.h), so that J z + H[D,D] = W_L x_y.
+__global__ void k_xy(const float* X, int ld, int K, int r, const float* zvec, double h, float* xy,
+                     const NewtonState* ns) {
+    if (ns && ns->done) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const float ih = (float)(1.0 / h), ih2 = (float)(1.0 / (h * h));
+    float acc = X[(size_t)3 * ld + k] * ih2;
+    for (int j = 0; j < r; ++j) acc = fmaf(X[(size_t)(kShared + 3 * j) * ld + k] * ih, zvec[j], acc);
+    xy[k] = acc;
+}
+
+void launch_xy(cudaStream_t s, const float* X, int ld, int K, int r, const float* zvec, double h,
+               float* xy, const NewtonState* ns) {
+    k_xy<<<(K + 255) / 256, 256, 0, s>>>(X, ld, K, r, zvec, h, xy, ns);
+}
+
+// out[i][k] = m[i] * W[i][k] for i < rows, k < ld (set-up of G).
+__global__ void k_scale_rows(const float* W, int ld, const float* m, int rows, float* out) {
+    const size_t n = (size_t)rows * ld;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = W[i] * m[i / ld];
+}
+
+void launch_scale_rows(cudaStream_t s, const float* W, int ld, const float* m, int rows, float* out) {
+    k_scale_rows<<<1024, 256, 0, s>>>(W, ld, m, rows, out);
+}
+
+// flag |= (f != prev) anywhere
+__global__ void k_fext_check(const float* f, const float* prev, int N, int* flag) {
+    int diff = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        diff |= (__float_as_uint(f[i]) != __float_as_uint(prev[i]));
+    diff = __syncthreads_or(diff);
+    if (threadIdx.x == 0 && diff) atomicOr(flag, 1);
+}
+
+void launch_fext_check(cudaStream_t s, const float* f, const float* prev, int N, int* flag) {
+    k_fext_check<<<64, 256, 0, s>>>(f, prev, N, flag);
+}
+
+// pext = sum of the split partials; remember f; clear the flag (only when flagged)
+__global__ void k_pext_finish(const float* part, int splits, int K, float* pext, const float* f,
+                              float* prev, int N, int* flag) {
+    if (*flag == 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < K) {
+        float acc = 0.f;
+        for (int s = 0; s < splits; ++s) acc += part[(size_t)s * K + i];
+        pext[i] = acc;
+    }
+    for (int j = i; j < N; j += gridDim.x * blockDim.x) prev[j] = f[j];
+}
+
+__global__ void k_clear_flag(int* flag) { *flag = 0; }
+
+void launch_pext_finish(cudaStream_t s, const float* part, int splits, int K, float* pext,
+                        const float* f, float* prev, int N, int* flag) {
+    k_pext_finish<<<(K + 255) / 256, 256, 0, s>>>(part, splits, K, pext, f, prev, N, flag);
+    k_clear_flag<<<1, 1, 0, s>>>(flag);
 }
 
 // ------------------------------------------------- complex-step reverse --
@@ -341,72 +413,94 @@ void launch_wta(cudaStream_t s, const WtaArgs& a) {
 // Incoming partials [in_split][in_ncol][n_o] are summed in a fixed order.
 constexpr int BW_THREADS = 128, BW_CHUNK = 32;
 
-// g[c][k] for k < n_o from the incoming partials (fixed summation order).
+// g[c][k] for k < n_o from the incoming partials (fixed summation order); one
+// thread per k forms the real part once and every i1 column from it.
 __global__ void k_bwd_prep(BwdArgs A) {
     if (A.ns && A.ns->done) return;
-    const int ncol = 1 + A.r;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncol * A.n_o;
-         e += gridDim.x * blockDim.x) {
-        const int c = e / A.n_o, k = e % A.n_o;
-        float re = 0.f;
-        for (int s = 0; s < A.in_split; ++s) re += A.in_part[((size_t)s * A.in_ncol) * A.n_o + k];
-        float v;
-        if (c == 0) {
-            v = re * A.S1[k];
-        } else {
-            float im = 0.f;
-            if (A.in_ncol > 1)
-                for (int s = 0; s < A.in_split; ++s)
-                    im += A.in_part[((size_t)s * A.in_ncol + c) * A.n_o + k];
-            v = fmaf(im, A.S1[k], re * A.T[(size_t)(c - 1) * A.n_o + k]);
-        }
-        A.g[e] = v;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.n_o) return;
+    const int r = A.r;
+    const size_t stride = (size_t)A.in_ncol * A.n_o;
+    float re = 0.f;
+    for (int s = 0; s < A.in_split; ++s) re += A.in_part[(size_t)s * stride + k];
+    const float s1 = A.S1[k];
+    A.g[k] = re * s1;
+    for (int c = 1; c <= r; ++c) {
+        float im = 0.f;
+        if (A.in_ncol > 1)
+            for (int s = 0; s < A.in_split; ++s) im += A.in_part[(size_t)s * stride + (size_t)c * A.n_o + k];
+        A.g[(size_t)c * A.n_o + k] = fmaf(im, s1, re * A.T[(size_t)(c - 1) * A.n_o + k]);
     }
 }
 
-// out_part[s][c][m] = sum_{k in split s} W[k][m] g[c][k]
+// out_part[s][c][m] = sum_{k in split s} W[k][m] g[c][k]; a thread owns two
+// consecutive m (one 8-byte weight load per k), g is staged in shared memory
+// and read as float4 over c.
 template <int NCOL>
 __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
     if (A.ns && A.ns->done) return;
-    __shared__ float gs[BW_CHUNK][NCOL];
-    const int m = blockIdx.x * BW_THREADS + threadIdx.x;
+    __shared__ __align__(16) float gs[BW_CHUNK][NCOL];
+    const int m = (blockIdx.x * BW_THREADS + threadIdx.x) * 2;
     const int ncol = 1 + A.r;
     const int per = (A.n_o + A.out_split - 1) / A.out_split;
     const int k0 = blockIdx.y * per, k1 = min(A.n_o, k0 + per);
-    float acc[NCOL];
+    float acc0[NCOL], acc1[NCOL];
 #pragma unroll
-    for (int c = 0; c < NCOL; ++c) acc[c] = 0.f;
+    for (int c = 0; c < NCOL; ++c) { acc0[c] = 0.f; acc1[c] = 0.f; }
+    const bool active = m < A.n_i;
     for (int kc = k0; kc < k1; kc += BW_CHUNK) {
         const int kn = min(BW_CHUNK, k1 - kc);
         __syncthreads();
         for (int e = threadIdx.x; e < BW_CHUNK * NCOL; e += BW_THREADS) {
-            int kk = e / NCOL, c = e % NCOL;
+            const int kk = e / NCOL, c = e % NCOL;
             gs[kk][c] = (kk < kn && c < ncol) ? A.g[(size_t)c * A.n_o + kc + kk] : 0.f;
         }
         __syncthreads();
-        if (m < A.n_i) {
+        if (active) {
+#pragma unroll 4
             for (int kk = 0; kk < kn; ++kk) {
-                float w = __ldg(A.W + (size_t)(kc + kk) * A.ld + m);
+                const float2 w = __ldg(reinterpret_cast<const float2*>(A.W + (size_t)(kc + kk) * A.ld + m));
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) acc[c] = fmaf(w, gs[kk][c], acc[c]);
+                for (int c4 = 0; c4 < NCOL / 4; ++c4) {
+                    const float4 g = *reinterpret_cast<const float4*>(&gs[kk][4 * c4]);
+                    acc0[4 * c4 + 0] = fmaf(w.x, g.x, acc0[4 * c4 + 0]);
+                    acc0[4 * c4 + 1] = fmaf(w.x, g.y, acc0[4 * c4 + 1]);
+                    acc0[4 * c4 + 2] = fmaf(w.x, g.z, acc0[4 * c4 + 2]);
+                    acc0[4 * c4 + 3] = fmaf(w.x, g.w, acc0[4 * c4 + 3]);
+                    acc1[4 * c4 + 0] = fmaf(w.y, g.x, acc1[4 * c4 + 0]);
+                    acc1[4 * c4 + 1] = fmaf(w.y, g.y, acc1[4 * c4 + 1]);
+                    acc1[4 * c4 + 2] = fmaf(w.y, g.z, acc1[4 * c4 + 2]);
+                    acc1[4 * c4 + 3] = fmaf(w.y, g.w, acc1[4 * c4 + 3]);
+                }
             }
         }
     }
-    if (m < A.n_i) {
-        for (int c = 0; c < ncol; ++c)
-            A.out_part[((size_t)blockIdx.y * ncol + c) * A.n_i + m] = acc[c];
+    if (active) {
+        float* out = A.out_part + (size_t)blockIdx.y * ncol * A.n_i;
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+            if (c < ncol) {
+                out[(size_t)c * A.n_i + m] = acc0[c];
+                if (m + 1 < A.n_i) out[(size_t)c * A.n_i + m + 1] = acc1[c];
+            }
+        }
     }
 }
 
+int bwd_split(int n_i, int n_o, int sm) {
+    const int mb = (n_i + 2 * BW_THREADS - 1) / (2 * BW_THREADS);
+    return std::max(1, std::min((3 * sm + mb - 1) / mb, std::max(1, n_o / 32)));
+}
+
 void launch_bwd(cudaStream_t s, const BwdArgs& a) {
-    int ncol = 1 + a.r;
-    int n = ncol * a.n_o;
-    k_bwd_prep<<<(n + 255) / 256, 256, 0, s>>>(a);
-    dim3 grid((a.n_i + BW_THREADS - 1) / BW_THREADS, a.out_split);
+    const int ncol = 1 + a.r;
+    k_bwd_prep<<<(a.n_o + 255) / 256, 256, 0, s>>>(a);
+    dim3 grid((a.n_i + 2 * BW_THREADS - 1) / (2 * BW_THREADS), a.out_split);
     if (ncol <= 8) k_bwd<8><<<grid, BW_THREADS, 0, s>>>(a);
     else if (ncol <= 16) k_bwd<16><<<grid, BW_THREADS, 0, s>>>(a);
     else if (ncol <= 24) k_bwd<24><<<grid, BW_THREADS, 0, s>>>(a);
-    else k_bwd<33><<<grid, BW_THREADS, 0, s>>>(a);
+    else if (ncol <= 32) k_bwd<32><<<grid, BW_THREADS, 0, s>>>(a);
+    else k_bwd<36><<<grid, BW_THREADS, 0, s>>>(a);
 }
 
 }  // namespace dae

@@ -117,7 +117,10 @@ __global__ void k_control(CtlArgs C) {
     __shared__ double M[kMaxR][kMaxR + 1];
     __shared__ double rhs[kMaxR];
     __shared__ double x[kMaxR];
+    __shared__ double sphi[kMaxR];
     __shared__ int nonfinite;
+    __shared__ int decision;   // 0 reject, 1 accept-and-continue, 2 accept-and-stop, 3 stop
+    __shared__ __align__(8) NewtonState S;
     const int r = C.r, t = threadIdx.x;
     const double dt2 = C.dt * C.dt;
     const int nsym = r * (r + 1) / 2;
@@ -130,6 +133,12 @@ __global__ void k_control(CtlArgs C) {
     double* Kr = Bm + r * r;
     double* gint = Kr + r * r;
     if (t == 0) nonfinite = 0;
+    if (C.control) {
+        // stage the Newton state in shared memory (coalesced copy)
+        const int nw = sizeof(NewtonState) / sizeof(int);
+        for (int i = t; i < nw; i += blockDim.x)
+            reinterpret_cast<int*>(&S)[i] = reinterpret_cast<const int*>(C.ns)[i];
+    }
     __syncthreads();
     for (int e = t; e < r * r; e += blockDim.x) {
         const int i = e % r, j = e / r;   // column-major (i, j)
@@ -147,9 +156,11 @@ __global__ void k_control(CtlArgs C) {
         gint[i] = g;
         const double p = C.rowsum[i] + dt2 * g;
         phi[i] = p;
+        sphi[i] = p;
         if (!isfinite(p)) nonfinite = 1;
     }
-    if (t == 0) *energy = C.have_cub ? *C.esum : 0.0;
+    const double en = C.have_cub ? *C.esum : 0.0;
+    if (t == 0) *energy = en;
     __syncthreads();
     const int flag = C.eval_flag ? *C.eval_flag : 0;   // 1 inverted tet, 2 bad cubature index
     const int inverted = flag != 0;
@@ -163,71 +174,75 @@ __global__ void k_control(CtlArgs C) {
         return;
     }
     if (t >= 32) return;
-    NewtonState* ns = C.ns;
-    __shared__ int decision;   // 0 reject, 1 accept-and-continue, 2 accept-and-stop, 3 stop
     if (t == 0) {
-        ns->evals += 1;
+        S.evals += 1;
         double merit = 0.0;
-        for (int i = 0; i < r; ++i) merit += phi[i] * phi[i];
+        for (int i = 0; i < r; ++i) merit += sphi[i] * sphi[i];
         const bool bad = inverted || nonfinite || !isfinite(merit);
         int dec;
-        if (ns->evals == 1) {
+        if (S.evals == 1) {
             if (bad) {
-                ns->status = flag == 2 ? DAE_ERR_INVALID_ARG
-                           : (inverted ? DAE_ERR_INVERTED : DAE_ERR_NONFINITE);
+                S.status = flag == 2 ? DAE_ERR_INVALID_ARG
+                         : (inverted ? DAE_ERR_INVERTED : DAE_ERR_NONFINITE);
                 dec = 3;
             } else {
-                ns->phi_norm0 = sqrt(merit);
+                S.phi_norm0 = sqrt(merit);
                 dec = 1;
             }
         } else {
-            const bool ok = !bad && merit <= (1.0 - 2.0 * C.c_armijo * ns->alpha) * ns->merit_acc;
+            const bool ok = !bad && merit <= (1.0 - 2.0 * C.c_armijo * S.alpha) * S.merit_acc;
             dec = ok ? 1 : 0;
         }
         if (dec == 1) {
-            for (int i = 0; i < r; ++i) { ns->q_acc[i] = ns->q_trial[i]; ns->phi[i] = phi[i]; }
-            ns->merit_acc = merit;
-            ns->energy = *energy;
-            if (ns->evals > 1) ns->iters += 1;
+            for (int i = 0; i < r; ++i) { S.q_acc[i] = S.q_trial[i]; S.phi[i] = sphi[i]; }
+            S.merit_acc = merit;
+            S.energy = en;
+            if (S.evals > 1) S.iters += 1;
             const double pn = sqrt(merit);
-            if (pn <= C.tol * fmax(1.0, ns->phi_norm0)) { ns->converged = 1; dec = 2; }
-            else if (ns->iters >= C.max_iter) dec = 2;
+            if (pn <= C.tol * fmax(1.0, S.phi_norm0)) { S.converged = 1; dec = 2; }
+            else if (S.iters >= C.max_iter) dec = 2;
         } else if (dec == 0) {
-            if (ns->halvings >= C.max_halvings) dec = 3;
+            if (S.halvings >= C.max_halvings) dec = 3;
         }
-        if (dec != 3 && dec != 2 && ns->evals >= C.max_evals) dec = 3;
+        if (dec != 3 && dec != 2 && S.evals >= C.max_evals) dec = 3;
         decision = dec;
     }
     __syncwarp();
     const int dec = decision;
     if (dec == 1) {
-        for (int i = t; i < r; i += 32) rhs[i] = -phi[i];
+        for (int i = t; i < r; i += 32) rhs[i] = -sphi[i];
         __syncwarp();
-        int st = warp_lu_solve(A, rhs, x, r, M, rhs);
+        const int st = warp_lu_solve(A, rhs, x, r, M, rhs);
         __syncwarp();
         if (t == 0) {
             if (st) {
-                ns->status = st;
-                ns->done = 1;
+                S.status = st;
+                S.done = 1;
             } else {
-                for (int i = 0; i < r; ++i) {
-                    ns->delta[i] = x[i];
-                    ns->q_trial[i] = ns->q_acc[i] + x[i];
-                }
-                ns->alpha = 1.0;
-                ns->halvings = 0;
+                S.alpha = 1.0;
+                S.halvings = 0;
             }
         }
+        __syncwarp();
+        if (!st)
+            for (int i = t; i < r; i += 32) {
+                S.delta[i] = x[i];
+                S.q_trial[i] = S.q_acc[i] + x[i];
+            }
     } else if (dec == 0) {
         if (t == 0) {
-            ns->alpha *= 0.5;
-            ns->halvings += 1;
-            for (int i = 0; i < r; ++i) ns->q_trial[i] = ns->q_acc[i] + ns->alpha * ns->delta[i];
+            S.alpha *= 0.5;
+            S.halvings += 1;
         }
+        __syncwarp();
+        for (int i = t; i < r; i += 32) S.q_trial[i] = S.q_acc[i] + S.alpha * S.delta[i];
     } else if (t == 0) {
-        ns->done = 1;
+        S.done = 1;
     }
     if (t == 0 && C.eval_flag) *C.eval_flag = 0;
+    __syncwarp();
+    const int nw = sizeof(NewtonState) / sizeof(int);
+    for (int i = t; i < nw; i += 32) reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
 }
 
 void launch_assemble(cudaStream_t s, const AsmArgs& a) {

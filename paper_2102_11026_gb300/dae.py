@@ -69,7 +69,7 @@ SIGNATURES = {
     "dae_newton_step": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp,
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
-    "dae_profile_enable": ([_vp, _i], _i),
+    "dae_profile_enable": ([_vp, ctypes.c_uint], _i),
     "dae_profile_read": ([_vp, _vp, _vp], _i),
     "dae_launch_count": ([_vp], ctypes.c_longlong),
     "dae_rollout": ([_vp, _vp, _vp, _i, _vp, _vp, _i, _vp, _vp, _d, _vp,
@@ -255,8 +255,17 @@ def dae_rollout(ctx, dec, mesh, cub_tets, cub_w, n_frames, q, qdot, dt, f_ext=No
 PHASES = ["fwd_hidden", "fwd_out", "rows", "cubature", "wta", "bwd", "assemble"]
 
 
-def dae_profile_enable(ctx, on=True):
-    _check(ctx, lib().dae_profile_enable(ctx, 1 if on else 0))
+def dae_profile_enable(ctx, phases=None):
+    """phases: None/True = all, False/() = off, or an iterable of phase names."""
+    if phases is None or phases is True:
+        mask = (1 << len(PHASES)) - 1
+    elif phases is False:
+        mask = 0
+    else:
+        mask = 0
+        for p in phases:
+            mask |= 1 << PHASES.index(p)
+    _check(ctx, lib().dae_profile_enable(ctx, mask))
 
 
 def dae_profile_read(ctx):
