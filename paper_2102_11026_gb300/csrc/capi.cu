@@ -183,6 +183,7 @@ dae_status alloc_workspace(dae_decoder* d) {
     const int r = d->r, L = d->L, N = d->N;
     w.C = n_cols(r);
     w.Cp = pad_cols(r);
+    const int sm = ctx->sm_count;
     size_t ldmax = 0, wmax = 0;
     for (int l = 0; l <= L - 1; ++l) ldmax = std::max(ldmax, round_up(d->widths[l], kKPad));
     for (int l = 1; l < L; ++l) wmax = std::max(wmax, (size_t)d->widths[l]);
@@ -207,7 +208,6 @@ dae_status alloc_workspace(dae_decoder* d) {
     w.row_stride = r + r * (r + 1) / 2 + r * r;
     TRY(dmalloc(ctx, &w.row_part, (size_t)w.n_row_blocks * w.row_stride));
     // reverse-pass partials: the largest of the W_L^T a splits and the hidden splits
-    const int sm = ctx->sm_count;
     const int K = d->widths[L - 1];
     size_t need = (size_t)(128 + 64 + 1) * K;   // dense + pair + f_ext splits
     for (int l = L - 2; l >= 0; --l) {
@@ -218,6 +218,19 @@ dae_status alloc_workspace(dae_decoder* d) {
     TRY(dmalloc(ctx, &w.bwd_part[0], need));
     TRY(dmalloc(ctx, &w.bwd_part[1], need));
     TRY(dmalloc(ctx, &w.gbuf, (size_t)(1 + r) * std::max(wmax, (size_t)1)));
+    {
+        // split-K scratch for the hidden tensor-core layers (largest tiles x split x Cp x 128)
+        size_t part = 0, tiles_max = 0;
+        for (int l = 0; l < L - 1; ++l) {
+            const int m_pad = (int)round_up(d->widths[l + 1], kRowTile);
+            const int ldl = (int)round_up(d->widths[l], kKPad);
+            const int sp = std::max(tc_split(m_pad, ldl, DAE_BF16, sm), tc_split(m_pad, ldl, DAE_TF32, sm));
+            part = std::max(part, (size_t)(m_pad / 128) * sp * w.Cp * 128);
+            tiles_max = std::max(tiles_max, (size_t)(m_pad / 128));
+        }
+        TRY(dmalloc(ctx, &w.split_part, std::max(part, (size_t)1)));
+        TRY(dmalloc(ctx, &w.split_cnt, std::max(tiles_max, (size_t)1)));
+    }
     TRY(dmalloc(ctx, &w.red, red_size(r)));
     TRY(dmalloc(ctx, &w.ns, 1));
     TRY(dmalloc(ctx, &w.qbar, (size_t)r));
@@ -234,9 +247,11 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
-    dfree(w.gbuf); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
+    dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
+    if (w.gexec) cudaGraphExecDestroy(w.gexec);
+    dfree(w.traj); dfree(w.qout); dfree(w.rc);
     dfree(w.G); dfree(w.xy); dfree(w.pext); dfree(w.fext_prev); dfree(w.pext_flag); dfree(w.pext_part);
 }
 
@@ -295,6 +310,8 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
         a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
         a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
+        a.split_part = w.split_part;
+        a.split_cnt = w.split_cnt;
         a.ns = ns;
         a.status = ctx->d_status;
         a.inv_h = 1.0 / h; a.inv_h2 = 1.0 / (h * h); a.inv_h3 = 1.0 / (h * h * h);
@@ -403,9 +420,14 @@ dae_status prepare_pext(dae_decoder* d, const float* f_ext_dev) {
 struct EvalParams {
     double dt, h;
     const int* cub_tets; const float* cub_w; int n_cub;
+    int w_stride;             // cubature weights per frame
     const float* f_ext;       // device, may be null
     int control;
     const dae_newton_opts* opts;
+    cudaGraphConditionalHandle hcond = 0;
+    int use_cond = 0;
+    unsigned long long* kcount = nullptr;
+    int kpe = 0;
 };
 
 dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
@@ -427,6 +449,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         launch_row_reduce(s, ra, w.n_row_blocks);
     }
     CubArgs ca;
+    ca.w_stride = P.w_stride;
     ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
     ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu; ca.lam = (float)m->lam;
     ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
@@ -496,11 +519,184 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         aa.tol = 0; aa.c_armijo = 0; aa.max_iter = 0; aa.max_halvings = 0; aa.max_evals = 0;
     }
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+    aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
     {
         Phase p(ctx, DAE_PHASE_ASSEMBLE, P.n_cub > 0 ? 5 : 3);
         launch_assemble(s, aa);
     }
     CU(ctx, cudaGetLastError());
+    return DAE_OK;
+}
+
+dae_status ensure_frames(dae_decoder* d, int n_frames) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    if (!w.rc) {
+        TRY(dmalloc(ctx, &w.rc, 1));
+        TRY(dmalloc(ctx, &w.qout, (size_t)d->r));
+    }
+    if (n_frames > w.hist_cap) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.hist);
+        dfree(w.traj);
+        const int cap = std::max(n_frames, 16);
+        TRY(dmalloc(ctx, &w.hist, (size_t)cap));
+        TRY(dmalloc(ctx, &w.traj, (size_t)cap * d->r));
+        w.hist_cap = cap;
+        w.graph_ok = false;
+    }
+    return DAE_OK;
+}
+
+void drop_graph(Workspace& w) {
+    if (w.gexec) cudaGraphExecDestroy(w.gexec);
+    w.gexec = nullptr;
+    w.graph_ok = false;
+}
+
+// Add a WHILE conditional node to g after dep (may be null); returns its body graph.
+dae_status add_while(dae_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* dep,
+                     cudaGraphConditionalHandle h, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    CU(ctx, cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &p));
+    *body = p.conditional.phGraph_out[0];
+    return DAE_OK;
+}
+
+dae_status sole_sink(dae_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* out) {
+    size_t n = 0;
+    CU(ctx, cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CU(ctx, cudaGraphGetNodes(g, nodes.data(), &n));
+    for (auto nd : nodes) {
+        size_t nout = 0;
+        CU(ctx, cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout));
+        if (nout == 0) { *out = nd; return DAE_OK; }
+    }
+    return fail(ctx, DAE_ERR_CUDA, "graph has no sink node");
+}
+
+// Capture: init -> WHILE(frames) { frame_start -> WHILE(evals) { evaluation } -> frame_finish }
+dae_status build_graph(dae_decoder* d, const dae_mesh* m, EvalParams P) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    drop_graph(w);
+    // capture on a private stream (the caller's stream may be the legacy default stream,
+    // which cannot be captured); the executable graph is launched on the caller's stream
+    if (!ctx->cap_stream) CU(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t saved_stream = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    cudaStream_t s = ctx->cap_stream;
+    const unsigned saved_prof = ctx->prof_on;
+    ctx->prof_on = 0;
+    cudaGraph_t g = nullptr;
+    CU(ctx, cudaGraphCreate(&g, 0));
+    dae_status st = DAE_OK;
+    const int r = d->r;
+    do {
+        cudaGraphConditionalHandle hout, hin;
+        if (cudaGraphConditionalHandleCreate(&hout, g, 0, 0) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        if (cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        launch_roll_init(s, w.rc, hout, 1, ctx->d_kcount);
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        cudaGraphNode_t a, outer, sn, inner;
+        if ((st = sole_sink(ctx, g, &a))) break;
+        cudaGraph_t bo, bi;
+        if ((st = add_while(ctx, g, &a, hout, &outer, &bo))) break;
+        if (cudaGraphConditionalHandleCreate(&hin, bo, 0, 0) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        if (cudaStreamBeginCaptureToGraph(s, bo, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        launch_frame_start(s, w.rc, w.ns, w.qbar, w.qbar_dot, P.dt, r, hin, 1, ctx->d_kcount);
+        if (cudaStreamEndCapture(s, &bo) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        if ((st = sole_sink(ctx, bo, &sn))) break;
+        if ((st = add_while(ctx, bo, &sn, hin, &inner, &bi))) break;
+        // evaluation body
+        if (cudaStreamBeginCaptureToGraph(s, bi, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        const long long l0 = ctx->launches;
+        P.hcond = hin; P.use_cond = 1; P.kcount = ctx->d_kcount;
+        dae_status es = enqueue_eval(d, m, w.ns, nullptr, P);
+        const int kpe = (int)(ctx->launches - l0);
+        ctx->launches = l0;
+        cudaGraph_t bi2 = bi;
+        cudaError_t ce = cudaStreamEndCapture(s, &bi2);
+        if (es) { st = es; break; }
+        if (ce != cudaSuccess) { st = fail(ctx, DAE_ERR_CUDA, "capture failed: %s", cudaGetErrorString(ce)); break; }
+        w.kpe = kpe;
+        if (cudaStreamBeginCaptureToGraph(s, bo, &inner, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        launch_frame_finish(s, w.rc, w.ns, w.qbar, w.qbar_dot, P.dt, r, w.traj, w.hist, w.qout, hout,
+                            1, ctx->d_kcount);
+        if (cudaStreamEndCapture(s, &bo) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        cudaError_t ie = cudaGraphInstantiate(&w.gexec, g, 0);
+        if (ie != cudaSuccess) { st = fail(ctx, DAE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie)); break; }
+    } while (0);
+    ctx->prof_on = saved_prof;
+    ctx->stream = saved_stream;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st) {
+        if (ctx->err.empty()) fail(ctx, st, "frame graph construction failed");
+        w.gexec = nullptr;
+        return st;
+    }
+    w.graph_ok = true;
+    return DAE_OK;
+}
+
+// Run n_frames implicit-Euler frames on the device (Newton evaluations until the
+// device control marks each frame done).  The kernels executed per evaluation are
+// patched into the counter by k_control when the kpe field is known, so the graph
+// needs it at capture time: captured with kpe from a dry count.
+dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_frames, int given_q0,
+                      int advance, const double* q_in_dev) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    cudaStream_t s = ctx->stream;
+    const int r = d->r;
+    TRY(ensure_frames(d, n_frames));
+    ctx->launches += 1;
+    launch_roll_setup(s, w.rc, n_frames, given_q0, advance, q_in_dev, r);
+    if (ctx->prof_on) {
+        // explicit launches, host checks each frame's done flag after every evaluation
+        drop_graph(w);
+        ctx->launches += 1;
+        launch_roll_init(s, w.rc, 0, 0, nullptr);
+        for (int f = 0; f < n_frames; ++f) {
+            ctx->launches += 1;
+            launch_frame_start(s, w.rc, w.ns, w.qbar, w.qbar_dot, P.dt, r, 0, 0, nullptr);
+            for (int e = 0; e < P.opts->max_evals; ++e) {
+                TRY(enqueue_eval(d, m, w.ns, nullptr, P));
+                int done = 0;
+                CU(ctx, cudaMemcpyAsync(&done, &w.ns->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CU(ctx, cudaStreamSynchronize(s));
+                if (done) break;
+            }
+            ctx->launches += 1;
+            launch_frame_finish(s, w.rc, w.ns, w.qbar, w.qbar_dot, P.dt, r, w.traj, w.hist, w.qout,
+                                0, 0, nullptr);
+        }
+        CU(ctx, cudaGetLastError());
+        return DAE_OK;
+    }
+    GraphKey key;
+    memset(&key, 0, sizeof key);
+    key.mesh_id = m->id; key.cub_w = P.cub_w; key.cub_tets = P.cub_tets; key.fe_w = w.fe_w;
+    key.hist = w.hist; key.traj = w.traj; key.fext = P.f_ext; key.n_cub = P.n_cub;
+    key.gram = w.G && w.G_mesh == m->id; key.prec = d->prec;
+    key.max_iter = P.opts->max_iter; key.max_halvings = P.opts->max_halvings;
+    key.max_evals = P.opts->max_evals; key.dt = P.dt; key.h = P.h; key.tol = P.opts->tol;
+    key.c_armijo = P.opts->c_armijo;
+    if (!w.graph_ok || memcmp(&key, &w.gkey, sizeof key) != 0) {
+        // kernels per evaluation: count once with a dry capture so k_control can add them
+        P.kpe = 0;
+        TRY(build_graph(d, m, P));
+        P.kpe = w.kpe;
+        TRY(build_graph(d, m, P));
+        w.gkey = key;
+    }
+    CU(ctx, cudaGraphLaunch(w.gexec, s));
     return DAE_OK;
 }
 
@@ -623,6 +819,8 @@ dae_status dae_create(dae_ctx** out, int device, void* stream) {
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess) { delete ctx; return DAE_ERR_OOM; }
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+    if (cudaMalloc(&ctx->d_kcount, sizeof(unsigned long long)) != cudaSuccess) { delete ctx; return DAE_ERR_OOM; }
+    cudaMemsetAsync(ctx->d_kcount, 0, sizeof(unsigned long long), ctx->stream);
     *out = ctx;
     return DAE_OK;
 }
@@ -632,7 +830,9 @@ dae_status dae_destroy(dae_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_status);
+    dfree(ctx->d_kcount);
     dfree(ctx->dstage);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cublas) cublasDestroy((cublasHandle_t)ctx->cublas);
     for (auto& rec : ctx->recs) { cudaEventDestroy(rec.a); cudaEventDestroy(rec.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -907,7 +1107,7 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     }
     EvalParams P;
     P.dt = dt; P.h = std::ldexp(1.0, -20); P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
-    P.f_ext = dfe; P.control = 0; P.opts = nullptr;
+    P.w_stride = 0; P.f_ext = dfe; P.control = 0; P.opts = nullptr;
     TRY(enqueue_eval(d, m, nullptr, dq, P));
     const double* red = d->ws.red;
     const size_t rr = (size_t)r * r;
@@ -935,7 +1135,8 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
     dae_newton_opts opts;
     fill_opts(opts_in, &opts);
-    if (opts.max_iter < 0 || opts.max_evals < 1) return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
+    if (opts.max_iter < 0 || opts.max_evals < 1 || opts.max_evals > 1000)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
     const int r = d->r;
     Stage st(ctx);
     st.need(q, r * 8);
@@ -955,13 +1156,10 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     }
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
-    P.f_ext = dfe; P.control = 1; P.opts = &opts;
-    ctx->launches += 2;
-    launch_frame_begin(ctx->stream, d->ws.ns, dq, r, 0);
-    for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, d->ws.ns, nullptr, P));
-    launch_frame_end(ctx->stream, d->ws.ns, dq, nullptr, nullptr, dt, r, nullptr, nullptr, 0);
-    CU(ctx, cudaGetLastError());
-    ctx->last_ns = d->ws.ns;
+    P.w_stride = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    TRY(run_frames(d, m, P, 1, 1, 0, dq));
+    CU(ctx, cudaMemcpyAsync(dq, d->ws.qout, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->last_ns = d->ws.hist;
     TRY(st.finish());
     if (rep) return dae_last_report(ctx, rep);
     return DAE_OK;
@@ -1000,12 +1198,7 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     TRY(st.inout(qdot, r, &dqd, true));
     TRY(st.inout(q_traj, (size_t)n_frames * r, &dtraj, false));
     Workspace& w = d->ws;
-    if (n_frames > w.hist_cap) {
-        CU(ctx, cudaStreamSynchronize(ctx->stream));
-        dfree(w.hist);
-        TRY(dmalloc(ctx, &w.hist, (size_t)n_frames));
-        w.hist_cap = n_frames;
-    }
+    TRY(ensure_frames(d, n_frames));
     CU(ctx, cudaMemcpyAsync(w.qbar, dq, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     CU(ctx, cudaMemcpyAsync(w.qbar_dot, dqd, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     const int* dct;
@@ -1017,21 +1210,17 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
         TRY(ensure_gram(d, m));
         TRY(prepare_pext(d, dfe));
     }
-    for (int f = 0; f < n_frames; ++f) {
-        EvalParams P;
-        P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw + (size_t)f * n_cub;
-        P.n_cub = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
-        ctx->launches += 3;
-        launch_predict(ctx->stream, w.q0, w.qbar, w.qbar_dot, dt, r);
-        launch_frame_begin(ctx->stream, w.ns, w.q0, r, f);
-        for (int e = 0; e < opts.max_evals; ++e) TRY(enqueue_eval(d, m, w.ns, nullptr, P));
-        launch_frame_end(ctx->stream, w.ns, nullptr, w.qbar, w.qbar_dot, dt, r,
-                         dtraj ? dtraj + (size_t)f * r : nullptr, w.hist + f, 1);
-    }
+    EvalParams P;
+    P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
+    P.w_stride = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    if (n_frames > 0) TRY(run_frames(d, m, P, n_frames, 0, 1, nullptr));
     CU(ctx, cudaGetLastError());
     CU(ctx, cudaMemcpyAsync(dq, w.qbar, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     CU(ctx, cudaMemcpyAsync(dqd, w.qbar_dot, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    ctx->last_ns = w.ns;
+    if (dtraj && n_frames > 0)
+        CU(ctx, cudaMemcpyAsync(dtraj, w.traj, (size_t)n_frames * r * sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->last_ns = n_frames > 0 ? w.hist + (n_frames - 1) : nullptr;
     TRY(st.finish());
     if (reports && n_frames > 0) {
         std::vector<NewtonState> hs(n_frames);
@@ -1078,6 +1267,16 @@ dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count) {
     return DAE_OK;
 }
 
-long long dae_launch_count(const dae_ctx* ctx) { return ctx ? ctx->launches : -1; }
+long long dae_launch_count(const dae_ctx* ctx) {
+    if (!ctx) return -1;
+    unsigned long long k = 0;
+    cudaSetDevice(ctx->device);
+    if (cudaMemcpyAsync(&k, ctx->d_kcount, sizeof k, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return ctx->launches + (long long)k;
+}
 
 }  // extern "C"

@@ -65,6 +65,24 @@ struct NewtonState {
     int pad_;
 };
 
+// Device-resident control of a sequence of frames (rollout or single Newton step).
+struct RollCtl {
+    int n_frames;
+    int frame;
+    int given_q0;            // 1: first iterate from q_in; 0: qbar + dt qbar_dot
+    int advance;             // 1: qbar_dot <- (q - qbar)/dt, qbar <- q after each frame
+    double q_in[kMaxR];
+};
+
+// Everything a captured frame graph bakes into its kernel parameters.
+struct GraphKey {
+    unsigned long long mesh_id;
+    const void* cub_w; const void* cub_tets; const void* fe_w; const void* hist; const void* traj;
+    const void* fext;
+    int n_cub, gram, prec, max_iter, max_halvings, max_evals;
+    double dt, h, tol, c_armijo;
+};
+
 // Per-decoder workspace (sized for the decoder's widths and latent size).
 struct Workspace {
     int Cp = 0, C = 0;
@@ -87,6 +105,8 @@ struct Workspace {
     float* bwd_part[2] = {nullptr, nullptr};
     size_t bwd_part_elems = 0;
     float* gbuf = nullptr;         // [1+r][max width] reverse-pass seed of one layer
+    float* split_part = nullptr;   // split-K partial tiles of the hidden tensor-core GEMMs
+    int* split_cnt = nullptr;      // per-tile counters
     int max_split = 0;
     // cubature scratch (grown on demand)
     int cub_cap = 0;
@@ -109,6 +129,14 @@ struct Workspace {
     int* eval_flag = nullptr;       // per-evaluation cubature flag
     NewtonState* hist = nullptr;    // per-frame states of a rollout (grown on demand)
     int hist_cap = 0;
+    double* traj = nullptr;         // [hist_cap][r] accepted iterate of every frame
+    double* qout = nullptr;         // [r] result of the last frame
+    RollCtl* rc = nullptr;
+    // cached frame graph
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    int kpe = 0;                    // kernels per evaluation
+    bool graph_ok = false;
     // Gram matrix G = W_L^T M W_L of the output layer for the mesh masses (W_L^T M y = G x_y)
     float* G = nullptr;             // [K][ldG]
     int ldG = 0;
@@ -128,6 +156,7 @@ struct Workspace {
 struct dae_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     std::string err;
     int* d_status = nullptr;         // device status word (first error wins)
     void* pinned = nullptr;          // host staging
@@ -139,7 +168,8 @@ struct dae_ctx {
     dae::NewtonState* last_ns = nullptr;   // state of the most recent newton step
     // instrumentation
     unsigned prof_on = 0;          // bit mask of instrumented phases
-    long long launches = 0;
+    long long launches = 0;             // kernels enqueued explicitly
+    unsigned long long* d_kcount = nullptr;   // kernels executed inside graphs (device counter)
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int phase; cudaEvent_t a, b; };
     std::vector<Rec> recs;
@@ -185,6 +215,8 @@ struct FwdArgs {
     int out_bf16;                            // 0 none, 1 hi, 2 hi+lo
     int out_f32;                             // write FP32 activations (FP32 / TF32 inputs)
     const void* tmaps;                       // 4 CUtensorMap (tensor-core path)
+    float* split_part;                       // split-K partial tiles [tiles][split][Cp][128]
+    int* split_cnt;                          // per-tile arrival counters (kept at zero)
     float* S1; float* T;                     // reverse-pass data
     // output-layer outputs (any may be null)
     float* u; float* J; float* dJ; float* HDD; float* Hqq;
@@ -199,6 +231,8 @@ void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override
                  int out_bf16, float* zvec);
 void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
+constexpr int kMaxSplit = 16;
+int tc_split(int m_pad, int ld, dae_prec prec, int sm_count);
 
 struct RowArgs {
     const float* J; const float* dJ; const float* HDD; const float* mdof; const float* f_ext;
@@ -208,6 +242,7 @@ struct RowArgs {
 void launch_row_reduce(cudaStream_t s, const RowArgs& a, int n_blocks);
 
 struct CubArgs {
+    int w_stride;                            // weights per frame (cub_w + frame * w_stride)
     const float* u; const float* J; int N, r;
     const double* X; const int* tets; const float* Bm; const float* vol; int n_tet;
     int material; float mu, lam;
@@ -258,6 +293,8 @@ struct AsmArgs {
     double tol, c_armijo; int max_iter, max_halvings, max_evals;
     int* eval_flag;                          // per-evaluation flag of the cubature kernel
     int* status;                             // sticky device status (assemble-only mode)
+    cudaGraphConditionalHandle hcond; int use_cond;
+    unsigned long long* kcount; int kpe;
 };
 void launch_assemble(cudaStream_t s, const AsmArgs& a);
 // doubles of the reduced-system buffer: outputs, terms and reduction scratch
@@ -267,11 +304,17 @@ inline size_t red_size(int r) {
            (size_t)(1 + r) * r + 1;
 }
 
-void launch_frame_begin(cudaStream_t s, NewtonState* ns, const double* q0, int r, int frame);
-void launch_frame_end(cudaStream_t s, NewtonState* ns, double* q, double* qbar, double* qbar_dot,
-                      double dt, int r, double* traj_row, NewtonState* hist, int advance);
-void launch_predict(cudaStream_t s, double* q0, const double* qbar, const double* qbar_dot,
-                    double dt, int r);
+void launch_roll_setup(cudaStream_t s, RollCtl* rc, int n_frames, int given_q0, int advance,
+                       const double* q_in, int r);
+void launch_roll_init(cudaStream_t s, RollCtl* rc, cudaGraphConditionalHandle h, int use,
+                      unsigned long long* kcount);
+void launch_frame_start(cudaStream_t s, RollCtl* rc, NewtonState* ns, const double* qbar,
+                        const double* qbar_dot, double dt, int r, cudaGraphConditionalHandle h,
+                        int use, unsigned long long* kcount);
+void launch_frame_finish(cudaStream_t s, RollCtl* rc, NewtonState* ns, double* qbar,
+                         double* qbar_dot, double dt, int r, double* traj, NewtonState* hist,
+                         double* q_out, cudaGraphConditionalHandle h, int use,
+                         unsigned long long* kcount);
 bool make_tmap(void* out, const void* base, bool fp32, int ld, int rows, int box_rows);
 void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
                        size_t n);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     const int nsym = r * (r + 1) / 2;
     float* part = A.part + (size_t)slot * A.stride;
     const int tet = A.cub_tets[slot];
-    const float wgt = A.cub_w[slot];
+    const float wgt = A.cub_w[(A.ns ? (size_t)A.ns->frame * A.w_stride : 0) + slot];
     if (tet < 0 || tet >= A.n_tet) {   // index checked here too: device arrays skip the host check
         if (lane == 0) {
             if (A.eval_flag) atomicExch(A.eval_flag, 2);

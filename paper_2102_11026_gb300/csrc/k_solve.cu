@@ -102,6 +102,8 @@ __device__ int warp_lu_solve(const double* A, const double* b, double* x, int r,
 //   bwdsum  [(1+r) x r]: column 0 = J^T a, column 1+j = h (a^T H)[:, j]
 //   red     [phi (r) | A (r*r col-major) | energy | aH | Mr | B | Kr | g_int]
 struct CtlArgs {
+    cudaGraphConditionalHandle hcond; int use_cond;   // evaluation loop of a graph frame
+    unsigned long long* kcount; int kpe;              // executed-kernel counter
     int r; double dt, h;
     const double* rowsum; const double* cubsum; const double* bwdsum; const double* esum;
     int have_cub;
@@ -113,7 +115,11 @@ struct CtlArgs {
 };
 
 __global__ void k_control(CtlArgs C) {
-    if (C.ns && C.ns->done) return;
+    if (C.ns && C.ns->done) {
+        // a finished frame never re-enters the evaluation loop
+        if (C.use_cond && threadIdx.x == 0) cudaGraphSetConditional(C.hcond, 0u);
+        return;
+    }
     __shared__ double M[kMaxR][kMaxR + 1];
     __shared__ double rhs[kMaxR];
     __shared__ double x[kMaxR];
@@ -239,7 +245,11 @@ __global__ void k_control(CtlArgs C) {
     } else if (t == 0) {
         S.done = 1;
     }
-    if (t == 0 && C.eval_flag) *C.eval_flag = 0;
+    if (t == 0) {
+        if (C.eval_flag) *C.eval_flag = 0;
+        if (C.kcount) atomicAdd(C.kcount, (unsigned long long)C.kpe);
+        if (C.use_cond) cudaGraphSetConditional(C.hcond, S.done ? 0u : 1u);
+    }
     __syncwarp();
     const int nw = sizeof(NewtonState) / sizeof(int);
     for (int i = t; i < nw; i += 32) reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
@@ -268,57 +278,97 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_iter = a.max_iter;
     c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
     c.eval_flag = a.eval_flag; c.status = a.status;
+    c.hcond = a.hcond; c.use_cond = a.use_cond; c.kcount = a.kcount; c.kpe = a.kpe;
     k_control<<<1, 256, 0, s>>>(c);
 }
 
 // --------------------------------------------------------- frame control --
-__global__ void k_frame_begin(NewtonState* ns, const double* q0, int r, int frame) {
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < r; ++i) { ns->q_trial[i] = q0[i]; ns->q_acc[i] = q0[i]; ns->delta[i] = 0.0; }
-        ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
-        ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
-        ns->status = 0; ns->frame = frame;
+// A frame (Sec. 3.2 implicit Euler): first iterate q0 = qbar + dt qbar_dot (or a
+// given q), Newton evaluations until k_control marks it done, then the update
+// qbar_dot <- (q - qbar)/dt, qbar <- q.  Inside a graph the two loops are
+// conditional WHILE nodes driven by these kernels and k_control.
+__global__ void k_roll_setup(RollCtl* rc, int n_frames, int given_q0, int advance,
+                             const double* q_in, int r) {
+    const int i = threadIdx.x;
+    if (i < r) rc->q_in[i] = given_q0 ? q_in[i] : 0.0;
+    if (i == 0) {
+        rc->n_frames = n_frames;
+        rc->frame = 0;
+        rc->given_q0 = given_q0;
+        rc->advance = advance;
     }
 }
 
-void launch_frame_begin(cudaStream_t s, NewtonState* ns, const double* q0, int r, int frame) {
-    k_frame_begin<<<1, 32, 0, s>>>(ns, q0, r, frame);
+__global__ void k_roll_init(RollCtl* rc, cudaGraphConditionalHandle h, int use,
+                            unsigned long long* kcount) {
+    rc->frame = 0;
+    if (kcount) atomicAdd(kcount, 1ull);
+    if (use) cudaGraphSetConditional(h, rc->n_frames > 0 ? 1u : 0u);
 }
 
-// q <- accepted iterate; with advance: qbar_dot <- (q - qbar)/dt, qbar <- q (Sec. 3.2).
-__global__ void k_frame_end(NewtonState* ns, double* q, double* qbar, double* qbar_dot, double dt,
-                            int r, double* traj_row, NewtonState* hist, int advance) {
+__global__ void k_frame_start(RollCtl* rc, NewtonState* ns, const double* qbar,
+                              const double* qbar_dot, double dt, int r,
+                              cudaGraphConditionalHandle h, int use, unsigned long long* kcount) {
     const int i = threadIdx.x;
     if (i < r) {
-        const double qn = ns->q_acc[i];
-        if (q) q[i] = qn;
-        if (advance) {
-            qbar_dot[i] = (qn - qbar[i]) / dt;
-            qbar[i] = qn;
+        const double q0 = rc->given_q0 ? rc->q_in[i] : qbar[i] + dt * qbar_dot[i];
+        ns->q_trial[i] = q0;
+        ns->q_acc[i] = q0;
+        ns->delta[i] = 0.0;
+        ns->phi[i] = 0.0;
+    }
+    if (i == 0) {
+        ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
+        ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
+        ns->status = 0; ns->frame = rc->frame;
+        if (kcount) atomicAdd(kcount, 1ull);
+        if (use) cudaGraphSetConditional(h, 1u);
+    }
+}
+
+__global__ void k_frame_finish(RollCtl* rc, NewtonState* ns, double* qbar, double* qbar_dot,
+                               double dt, int r, double* traj, NewtonState* hist, double* q_out,
+                               cudaGraphConditionalHandle h, int use, unsigned long long* kcount) {
+    const int i = threadIdx.x;
+    const int f = rc->frame;
+    if (i < r) {
+        const double q = ns->q_acc[i];
+        q_out[i] = q;
+        if (rc->advance) {
+            qbar_dot[i] = (q - qbar[i]) / dt;
+            qbar[i] = q;
         }
-        if (traj_row) traj_row[i] = qn;
+        if (traj) traj[(size_t)f * r + i] = q;
     }
     __syncthreads();
     if (i == 0) {
         ns->done = 1;
-        if (hist) *hist = *ns;
+        if (hist) hist[f] = *ns;
+        rc->frame = f + 1;
+        if (kcount) atomicAdd(kcount, 1ull);
+        if (use) cudaGraphSetConditional(h, (f + 1 < rc->n_frames) ? 1u : 0u);
     }
 }
 
-void launch_frame_end(cudaStream_t s, NewtonState* ns, double* q, double* qbar, double* qbar_dot,
-                      double dt, int r, double* traj_row, NewtonState* hist, int advance) {
-    k_frame_end<<<1, 32, 0, s>>>(ns, q, qbar, qbar_dot, dt, r, traj_row, hist, advance);
+void launch_roll_setup(cudaStream_t s, RollCtl* rc, int n_frames, int given_q0, int advance,
+                       const double* q_in, int r) {
+    k_roll_setup<<<1, 32, 0, s>>>(rc, n_frames, given_q0, advance, q_in, r);
 }
-
-// q0 = qbar + dt * qbar_dot (the first Newton iterate of a rollout frame)
-__global__ void k_predict(double* q0, const double* qbar, const double* qbar_dot, double dt, int r) {
-    const int i = threadIdx.x;
-    if (i < r) q0[i] = qbar[i] + dt * qbar_dot[i];
+void launch_roll_init(cudaStream_t s, RollCtl* rc, cudaGraphConditionalHandle h, int use,
+                      unsigned long long* kcount) {
+    k_roll_init<<<1, 1, 0, s>>>(rc, h, use, kcount);
 }
-
-void launch_predict(cudaStream_t s, double* q0, const double* qbar, const double* qbar_dot,
-                    double dt, int r) {
-    k_predict<<<1, 32, 0, s>>>(q0, qbar, qbar_dot, dt, r);
+void launch_frame_start(cudaStream_t s, RollCtl* rc, NewtonState* ns, const double* qbar,
+                        const double* qbar_dot, double dt, int r, cudaGraphConditionalHandle h,
+                        int use, unsigned long long* kcount) {
+    k_frame_start<<<1, 32, 0, s>>>(rc, ns, qbar, qbar_dot, dt, r, h, use, kcount);
+}
+void launch_frame_finish(cudaStream_t s, RollCtl* rc, NewtonState* ns, double* qbar,
+                         double* qbar_dot, double dt, int r, double* traj, NewtonState* hist,
+                         double* q_out, cudaGraphConditionalHandle h, int use,
+                         unsigned long long* kcount) {
+    k_frame_finish<<<1, 32, 0, s>>>(rc, ns, qbar, qbar_dot, dt, r, traj, hist, q_out, h, use,
+                                    kcount);
 }
 
 }  // namespace dae

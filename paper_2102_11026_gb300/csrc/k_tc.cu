@@ -11,6 +11,7 @@
 // %globaltimer); a wait that gives up records DAE_ERR_TIMEOUT and the CTA
 // drains its copies, frees TMEM and exits.
 #include <cuda.h>
+#include <algorithm>
 #include "dae_internal.h"
 #include "epilogue.cuh"
 
@@ -224,7 +225,7 @@ template <int NC, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
-             FwdArgs A, int nk, int stages) {
+             FwdArgs A, int nk, int stages, int split) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;         // K elements per 128-byte row
@@ -244,6 +245,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * 128;
+    // split-K: this CTA takes k-blocks [kb0, kb1)
+    const int kb0 = (int)((long long)nk * blockIdx.y / split);
+    const int kb1 = (int)((long long)nk * (blockIdx.y + 1) / split);
+    const int nkl = kb1 - kb0;
+    __shared__ int is_last;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -266,17 +272,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int issued = 0;
-            for (int kb = 0; kb < nk; ++kb) {
+            for (int kb = 0; kb < nkl; ++kb) {
                 const int s = kb % stages;
                 const uint32_t ph = (kb / stages) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1)) { fail = 1; break; }
                 mbar_expect_tx(&full[s], STAGE);
                 uint8_t* base = smem + (size_t)s * STAGE;
-                tma_load_2d(base, &tmA, &full[s], kb * KB, m0);
-                tma_load_2d(base + A_BYTES, &tmB, &full[s], kb * KB, 0);
+                const int kx = (kb0 + kb) * KB;
+                tma_load_2d(base, &tmA, &full[s], kx, m0);
+                tma_load_2d(base + A_BYTES, &tmB, &full[s], kx, 0);
                 if constexpr (X3) {
-                    tma_load_2d(base + A_BYTES + B_BYTES, &tmAlo, &full[s], kb * KB, m0);
-                    tma_load_2d(base + 2 * A_BYTES + B_BYTES, &tmBlo, &full[s], kb * KB, 0);
+                    tma_load_2d(base + A_BYTES + B_BYTES, &tmAlo, &full[s], kx, m0);
+                    tma_load_2d(base + 2 * A_BYTES + B_BYTES, &tmBlo, &full[s], kx, 0);
                 }
                 ++issued;
             }
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = true;
-            for (int kb = 0; kb < nk; ++kb) {
+            for (int kb = 0; kb < nkl; ++kb) {
                 const int s = kb % stages;
                 const uint32_t ph = (kb / stages) & 1;
                 if (!mbar_wait(&full[s], ph)) { ok = false; fail = 1; break; }
@@ -317,14 +324,43 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int lane_base = 32 * (warp & 3);
         const int n = m0 + lane_base + lane;
         float v[CP];
-        if (ok) {
+        const bool wok = __all_sync(0xffffffffu, ok);
+        if (wok) {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
                 tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 16 * c, v + 16 * c);
             tmem_wait_ld();
-            row_epilogue<NC>(A, n, v);
         } else {
             fail = 1;
+        }
+        if (split == 1) {
+            if (wok) row_epilogue<NC>(A, n, v);
+        } else {
+            // write this split's partial tile [tile][split][c][128 rows]; the last CTA of the
+            // tile (atomic count, no waiting) sums the partials in split order and finishes
+            const int row = lane_base + lane;
+            float* part = A.split_part + ((size_t)blockIdx.x * split + blockIdx.y) * CP * 128;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) part[(size_t)c * 128 + row] = wok ? v[c] : 0.f;
+            __threadfence();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (warp == 2 && lane == 0) {
+                const int old = atomicAdd(A.split_cnt + blockIdx.x, 1);
+                is_last = (old == split - 1);
+                if (is_last) A.split_cnt[blockIdx.x] = 0;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (is_last) {
+                __threadfence();
+                const float* tp = A.split_part + (size_t)blockIdx.x * split * CP * 128;
+#pragma unroll
+                for (int c = 0; c < CP; ++c) v[c] = 0.f;
+                for (int s = 0; s < split; ++s) {
+#pragma unroll
+                    for (int c = 0; c < CP; ++c) v[c] += __ldcg(tp + ((size_t)s * CP + c) * 128 + row);
+                }
+                row_epilogue<NC>(A, n, v);
+            }
         }
     }
     tc_fence_before();
@@ -337,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int NC, int PREC>
-bool launch_inst(cudaStream_t s, const FwdArgs& a) {
+bool launch_inst(cudaStream_t s, const FwdArgs& a, int split) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
@@ -354,33 +390,47 @@ bool launch_inst(cudaStream_t s, const FwdArgs& a) {
     const int KB = (PREC == DAE_TF32) ? 32 : 64;
     const int nk = a.ld / KB;
     const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(a.tmaps);
-    k_fwd_tc<NC, PREC><<<a.m_pad / 128, kThreads, smem, s>>>(tm[0], tm[1], tm[2], tm[3], a, nk,
-                                                             stages);
+    dim3 grid(a.m_pad / 128, split);
+    k_fwd_tc<NC, PREC><<<grid, kThreads, smem, s>>>(tm[0], tm[1], tm[2], tm[3], a, nk, stages,
+                                                   split);
     return cudaPeekAtLastError() == cudaSuccess;
 }
 
 template <int PREC>
-bool launch_prec(cudaStream_t s, const FwdArgs& a) {
+bool launch_prec(cudaStream_t s, const FwdArgs& a, int split) {
     switch (a.Cp / 16) {
-        case 1: return launch_inst<1, PREC>(s, a);
-        case 2: return launch_inst<2, PREC>(s, a);
-        case 3: return launch_inst<3, PREC>(s, a);
-        case 4: return launch_inst<4, PREC>(s, a);
-        case 5: return launch_inst<5, PREC>(s, a);
-        case 6: return launch_inst<6, PREC>(s, a);
-        case 7: return launch_inst<7, PREC>(s, a);
+        case 1: return launch_inst<1, PREC>(s, a, split);
+        case 2: return launch_inst<2, PREC>(s, a, split);
+        case 3: return launch_inst<3, PREC>(s, a, split);
+        case 4: return launch_inst<4, PREC>(s, a, split);
+        case 5: return launch_inst<5, PREC>(s, a, split);
+        case 6: return launch_inst<6, PREC>(s, a, split);
+        case 7: return launch_inst<7, PREC>(s, a, split);
     }
     return false;
 }
 
 }  // namespace
 
-bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int) {
+// Split-K factor: fill about one CTA per SM with at least 4 k-blocks per split;
+// the output layer (and any layer with enough row tiles) runs unsplit.
+int tc_split(int m_pad, int ld, dae_prec prec, int sm_count) {
+    const int tiles = m_pad / 128;
+    const int nk = ld / (prec == DAE_TF32 ? 32 : 64);
+    int split = sm_count / tiles;
+    split = std::min(split, nk / 4);
+    split = std::min(split, kMaxSplit);
+    return split < 2 ? 1 : split;
+}
+
+bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count) {
     if (!a.tmaps || a.m_pad % 128 != 0) return false;
+    int split = a.last ? 1 : tc_split(a.m_pad, a.ld, prec, sm_count);
+    if (!a.split_part || !a.split_cnt) split = 1;
     switch (prec) {
-        case DAE_TF32: return launch_prec<DAE_TF32>(s, a);
-        case DAE_BF16: return launch_prec<DAE_BF16>(s, a);
-        case DAE_BF16X3: return launch_prec<DAE_BF16X3>(s, a);
+        case DAE_TF32: return launch_prec<DAE_TF32>(s, a, split);
+        case DAE_BF16: return launch_prec<DAE_BF16>(s, a, split);
+        case DAE_BF16X3: return launch_prec<DAE_BF16X3>(s, a, split);
         default: return false;
     }
 }
