@@ -235,7 +235,7 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     n = wl.cub_tets.size
     seed = 2 + rank
-    cw_all = frame_weights(wl, W + K, seed)
+    cw_all = frame_weights(wl, W + K + 2, seed)
     cub_t = dev(wl.cub_tets, torch.int32)
     cub_w = dev(cw_all, torch.float32)
     f_ext = dev(wl.f_ext, torch.float32)
@@ -281,7 +281,7 @@ def run_ours(args):
         prof = dae.dae_profile_read(ctx)
         # phase shares from a fully instrumented pass over 2 more frames
         dae.dae_profile_enable(ctx, True)
-        reps2 = dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[W * n:(W + 2) * n], 2, q2, qd2,
+        reps2 = dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[(W + K) * n:(W + K + 2) * n], 2, q2, qd2,
                                 wl.state.dt, f_ext, opts)
         dae.dae_profile_enable(ctx, False)
         prof_all = dae.dae_profile_read(ctx)

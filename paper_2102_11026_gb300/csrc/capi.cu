@@ -218,8 +218,16 @@ dae_status alloc_workspace(dae_decoder* d) {
     TRY(dmalloc(ctx, &w.bwd_part[0], need));
     TRY(dmalloc(ctx, &w.bwd_part[1], need));
     TRY(dmalloc(ctx, &w.gbuf, (size_t)(1 + r) * std::max(wmax, (size_t)1)));
+    w.Cb = (int)round_up(1 + r, 16);
+    for (int l = 0; l < L - 1; ++l) w.ldg_max = std::max(w.ldg_max, round_up(d->widths[l + 1], kKPad));
+    for (int i = 0; i < 2; ++i) {
+        TRY(dmalloc(ctx, &w.G32[i], (size_t)w.Cb * w.ldg_max));
+        TRY(dmalloc(ctx, &w.Gh[i], (size_t)w.Cb * w.ldg_max));
+        TRY(dmalloc(ctx, &w.Gl[i], (size_t)w.Cb * w.ldg_max));
+    }
     {
-        // split-K scratch for the hidden tensor-core layers (largest tiles x split x Cp x 128)
+        // split-K scratch of the tensor-core GEMMs: hidden forward layers and the reverse
+        // GEMMs (largest tiles x split x columns x 128)
         size_t part = 0, tiles_max = 0;
         for (int l = 0; l < L - 1; ++l) {
             const int m_pad = (int)round_up(d->widths[l + 1], kRowTile);
@@ -227,6 +235,11 @@ dae_status alloc_workspace(dae_decoder* d) {
             const int sp = std::max(tc_split(m_pad, ldl, DAE_BF16, sm), tc_split(m_pad, ldl, DAE_TF32, sm));
             part = std::max(part, (size_t)(m_pad / 128) * sp * w.Cp * 128);
             tiles_max = std::max(tiles_max, (size_t)(m_pad / 128));
+            const int mt = (int)round_up(d->widths[l], kRowTile);
+            const int ldt = (int)round_up(d->widths[l + 1], kKPad);
+            const int spt = std::max(tc_split(mt, ldt, DAE_BF16, sm), tc_split(mt, ldt, DAE_TF32, sm));
+            part = std::max(part, (size_t)(mt / 128) * spt * w.Cb * 128);
+            tiles_max = std::max(tiles_max, (size_t)(mt / 128));
         }
         TRY(dmalloc(ctx, &w.split_part, std::max(part, (size_t)1)));
         TRY(dmalloc(ctx, &w.split_cnt, std::max(tiles_max, (size_t)1)));
@@ -244,6 +257,7 @@ dae_status alloc_workspace(dae_decoder* d) {
 
 void free_workspace(Workspace& w) {
     for (int i = 0; i < 2; ++i) { dfree(w.X[i]); dfree(w.Xh[i]); dfree(w.Xl[i]); dfree(w.bwd_part[i]); }
+    for (int i = 0; i < 2; ++i) { dfree(w.G32[i]); dfree(w.Gh[i]); dfree(w.Gl[i]); }
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
@@ -307,6 +321,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = r; a.Cp = w.Cp;
         a.act = d->act;
         a.last = (l == L - 1);
+        a.mode = a.last ? 1 : 0;
         // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
         a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
         a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
@@ -486,6 +501,46 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         launch_wta(s, wa);
     }
     int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0), in_ncol = 1, cur = 0;
+    const bool tc_rev = d->prec != DAE_FP32 && d->layers[0].tmR_ok;
+    if (tc_rev) {
+        // complex-step reverse pass on the tensor cores: delta_l = W_l^T g_l, the epilogue
+        // forms g_{l-1} (complex act' of the layer below) as the next B operand
+        const int ob = out_bf16_of(d->prec);
+        const int of32 = (d->prec == DAE_TF32);
+        {
+            BwdArgs ba;
+            memset(&ba, 0, sizeof ba);
+            ba.n_o = d->widths[L - 1]; ba.r = r;
+            ba.in_part = w.bwd_part[0]; ba.in_split = in_split; ba.in_ncol = 1;
+            ba.S1 = w.S1[L - 2]; ba.T = w.T[L - 2]; ba.ns = ns;
+            Phase p(ctx, DAE_PHASE_BWD, 1);
+            launch_bwd_prep_tc(s, ba, w.Cb, d->layers[L - 2].ldT, w.G32[0], w.Gh[0], w.Gl[0], of32, ob);
+        }
+        for (int l = L - 2; l >= 0; --l) {
+            const Layer& ly = d->layers[l];
+            FwdArgs a;
+            memset(&a, 0, sizeof a);
+            a.ld = ly.ldT; a.m_pad = ly.mT_pad; a.n_in = ly.n_out; a.n_out = ly.n_in;
+            a.r = r; a.Cp = w.Cb; a.ns = ns; a.status = ctx->d_status;
+            a.tmaps = ly.tmR; a.split_part = w.split_part; a.split_cnt = w.split_cnt;
+            if (l > 0) {
+                const int nb = (L - 1 - l) & 1;
+                a.mode = 2;
+                a.Y = w.G32[nb]; a.Yh = w.Gh[nb]; a.Yl = w.Gl[nb];
+                a.ldy = d->layers[l - 1].ldT;
+                a.out_f32 = of32; a.out_bf16 = ob;
+                a.S1 = w.S1[l - 1]; a.T = w.T[l - 1];
+            } else {
+                a.mode = 3;
+                a.dout = w.bwd_part[1];
+            }
+            Phase p(ctx, DAE_PHASE_BWD, 1);
+            if (!launch_fwd_tc(s, a, d->prec, sm))
+                return fail(ctx, DAE_ERR_UNSUPPORTED, "reverse GEMM launch failed for layer %d", l);
+        }
+        cur = 1;
+        in_split = 1;
+    } else {
     for (int l = L - 2; l >= 0; --l) {
         BwdArgs ba;
         ba.W = d->layers[l].W; ba.ld = d->layers[l].ld;
@@ -502,6 +557,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         cur ^= 1;
         in_split = ba.out_split;
         in_ncol = 1 + r;
+    }
     }
     if (L == 1)
         return fail(ctx, DAE_ERR_UNSUPPORTED, "a decoder needs at least one hidden layer");
@@ -937,6 +993,39 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
             ly.tm_ok = ok;
             if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "tensor map encoding failed for layer %d", l);
         }
+        // reverse pass: W_l^T (K-major, K = n_out) for every hidden layer, and its B operand
+        // g_l (ping-pong buffer (L-2-l) & 1)
+        for (int l = 0; l < d->L - 1; ++l) {
+            Layer& ly = d->layers[l];
+            ly.ldT = (int)round_up(ly.n_out, kKPad);
+            ly.mT_pad = (int)round_up(ly.n_in, kRowTile);
+            const size_t nt = (size_t)ly.mT_pad * ly.ldT;
+            if (!ly.WT) {
+                TRY(dmalloc(ctx, &ly.WT, nt));
+                launch_transpose(ctx->stream, ly.W, ly.ld, ly.n_out, ly.n_in, ly.WT, ly.ldT);
+            }
+            if (prec != DAE_TF32) {
+                if (!ly.WTh) TRY(dmalloc(ctx, &ly.WTh, nt));
+                if (prec == DAE_BF16X3 && !ly.WTl) TRY(dmalloc(ctx, &ly.WTl, nt));
+                launch_split_bf16(ctx->stream, ly.WT, ly.WTh, prec == DAE_BF16X3 ? ly.WTl : nullptr, nt);
+            }
+            const int gb = (d->L - 2 - l) & 1;
+            bool ok = make_tmap(&ly.tmR[0], f32 ? (const void*)ly.WT : (const void*)ly.WTh, f32, ly.ldT,
+                                ly.mT_pad, 128);
+            ok = ok && make_tmap(&ly.tmR[2], f32 ? (const void*)d->ws.G32[gb] : (const void*)d->ws.Gh[gb],
+                                 f32, ly.ldT, d->ws.Cb, d->ws.Cb);
+            if (prec == DAE_BF16X3) {
+                ok = ok && make_tmap(&ly.tmR[1], ly.WTl, false, ly.ldT, ly.mT_pad, 128);
+                ok = ok && make_tmap(&ly.tmR[3], d->ws.Gl[gb], false, ly.ldT, d->ws.Cb, d->ws.Cb);
+            } else {
+                ly.tmR[1] = ly.tmR[0];
+                ly.tmR[3] = ly.tmR[2];
+            }
+            ly.tmR_ok = ok;
+            if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "reverse tensor map failed for layer %d", l);
+        }
+        CU(ctx, cudaGetLastError());
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
     }
     d->prec = prec;
     return DAE_OK;
@@ -946,7 +1035,10 @@ dae_status dae_free_decoder(dae_decoder* d) {
     if (!d) return DAE_ERR_INVALID_ARG;
     cudaSetDevice(d->ctx->device);
     cudaStreamSynchronize(d->ctx->stream);
-    for (auto& ly : d->layers) { dfree(ly.W); dfree(ly.b); dfree(ly.Wh); dfree(ly.Wl); }
+    for (auto& ly : d->layers) {
+        dfree(ly.W); dfree(ly.b); dfree(ly.Wh); dfree(ly.Wl);
+        dfree(ly.WT); dfree(ly.WTh); dfree(ly.WTl);
+    }
     free_workspace(d->ws);
     delete d;
     return DAE_OK;

@@ -43,6 +43,13 @@ struct Layer {
     __nv_bfloat16* Wl = nullptr;   // BF16 lo split (W - hi)
     CUtensorMap tm[4];             // TMA maps: A (W or W hi), A lo, B (input activations), B lo
     bool tm_ok = false;
+    // transposed copy for the tensor-core reverse pass (hidden layers): [mT_pad][ldT]
+    int ldT = 0, mT_pad = 0;
+    float* WT = nullptr;
+    __nv_bfloat16* WTh = nullptr;
+    __nv_bfloat16* WTl = nullptr;
+    CUtensorMap tmR[4];
+    bool tmR_ok = false;
 };
 
 // Device-resident Newton control state of one frame.
@@ -105,6 +112,12 @@ struct Workspace {
     float* bwd_part[2] = {nullptr, nullptr};
     size_t bwd_part_elems = 0;
     float* gbuf = nullptr;         // [1+r][max width] reverse-pass seed of one layer
+    // reverse-pass B operands on the tensor-core path: g of one layer, [Cb][ld] (ping-pong)
+    int Cb = 0;
+    size_t ldg_max = 0;
+    float* G32[2] = {nullptr, nullptr};
+    __nv_bfloat16* Gh[2] = {nullptr, nullptr};
+    __nv_bfloat16* Gl[2] = {nullptr, nullptr};
     float* split_part = nullptr;   // split-K partial tiles of the hidden tensor-core GEMMs
     int* split_cnt = nullptr;      // per-tile counters
     int max_split = 0;
@@ -210,6 +223,9 @@ struct FwdArgs {
     int n_in, n_out, m_pad, r, Cp;
     int act;                                 // dae_act (hidden layers)
     int last;                                // 1: output layer
+    int mode;                                // 0 forward hidden, 1 forward output,
+                                             // 2 reverse (next g), 3 reverse (input layer)
+    float* dout;                             // mode 3: delta_0 [1+r][r]
     // hidden-layer outputs
     float* Y; __nv_bfloat16* Yh; __nv_bfloat16* Yl; int ldy;   // next activations [Cp][ldy]
     int out_bf16;                            // 0 none, 1 hi, 2 hi+lo
@@ -280,6 +296,10 @@ struct BwdArgs {
     const NewtonState* ns;
 };
 void launch_bwd(cudaStream_t s, const BwdArgs& a);
+// g of the top hidden layer in the tensor-core B layout [Cb][ld] (FP32 and/or BF16 splits)
+void launch_bwd_prep_tc(cudaStream_t s, const BwdArgs& a, int Cb, int ld, float* g32,
+                        __nv_bfloat16* gh, __nv_bfloat16* gl, int out_f32, int out_bf16);
+void launch_transpose(cudaStream_t s, const float* W, int ld, int rows, int cols, float* WT, int ldT);
 int bwd_split(int n_i, int n_o, int sm);
 
 struct AsmArgs {

@@ -487,6 +487,67 @@ __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
     }
 }
 
+// Tensor-core variant of the top-layer seed: g[c][k] for k < ld (zero padding), c < Cb.
+__global__ void k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32, __nv_bfloat16* gh,
+                              __nv_bfloat16* gl, int out_f32, int out_bf16) {
+    if (A.ns && A.ns->done) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ld) return;
+    const int r = A.r;
+    const size_t stride = (size_t)A.in_ncol * A.n_o;
+    float re = 0.f, s1 = 0.f;
+    if (k < A.n_o) {
+        for (int s = 0; s < A.in_split; ++s) re += A.in_part[(size_t)s * stride + k];
+        s1 = A.S1[k];
+    }
+    for (int c = 0; c < Cb; ++c) {
+        float v = 0.f;
+        if (k < A.n_o) {
+            if (c == 0) {
+                v = re * s1;
+            } else if (c <= r) {
+                float im = 0.f;
+                if (A.in_ncol > 1)
+                    for (int s = 0; s < A.in_split; ++s)
+                        im += A.in_part[(size_t)s * stride + (size_t)c * A.n_o + k];
+                v = fmaf(im, s1, re * A.T[(size_t)(c - 1) * A.n_o + k]);
+            }
+        }
+        const size_t idx = (size_t)c * ld + k;
+        if (out_f32) g32[idx] = v;
+        if (out_bf16) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            gh[idx] = hi;
+            if (out_bf16 == 2) gl[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+    }
+}
+
+void launch_bwd_prep_tc(cudaStream_t s, const BwdArgs& a, int Cb, int ld, float* g32,
+                        __nv_bfloat16* gh, __nv_bfloat16* gl, int out_f32, int out_bf16) {
+    k_bwd_prep_tc<<<(ld + 255) / 256, 256, 0, s>>>(a, Cb, ld, g32, gh, gl, out_f32, out_bf16);
+}
+
+// WT[c][r] = W[r][c] for r < rows, c < cols (zero elsewhere in WT's padding is kept)
+__global__ void k_transpose(const float* W, int ld, int rows, int cols, float* WT, int ldT) {
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? W[(size_t)r * ld + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) WT[(size_t)c * ldT + r] = t[threadIdx.x][i];
+    }
+}
+
+void launch_transpose(cudaStream_t s, const float* W, int ld, int rows, int cols, float* WT, int ldT) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, s>>>(W, ld, rows, cols, WT, ldT);
+}
+
 int bwd_split(int n_i, int n_o, int sm) {
     const int mb = (n_i + 2 * BW_THREADS - 1) / (2 * BW_THREADS);
     return std::max(1, std::min((3 * sm + mb - 1) / mb, std::max(1, n_o / 32)));

@@ -157,6 +157,41 @@ __device__ __forceinline__ void row_epilogue(const FwdArgs& A, int n, const floa
     constexpr int CP = 16 * NC;
     constexpr int JMAX = (CP - kShared) / 3;
     const int r = A.r;
+    if (A.mode == 2) {
+        // reverse pass: delta of this layer's input -> g of the layer below,
+        // Re g = Re d s1, Im_j g = Im_j d s1 + Re d (s2 b_j)   (Sec. 4.4 complex BP)
+        if (n >= A.ldy) return;
+        const size_t ldy = A.ldy;
+        auto put = [&](int c, float x) {
+            const size_t idx = (size_t)c * ldy + n;
+            if (A.out_f32) A.Y[idx] = x;
+            if (A.out_bf16) {
+                __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                A.Yh[idx] = hi;
+                if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+        };
+        if (n >= A.n_out) {
+#pragma unroll
+            for (int c = 0; c < CP; ++c) put(c, 0.f);
+            return;
+        }
+        const float s1 = A.S1[n];
+        const float re = v[0];
+        put(0, re * s1);
+#pragma unroll
+        for (int c = 1; c < CP; ++c)
+            put(c, c <= r ? fmaf(v[c], s1, re * A.T[(size_t)(c - 1) * A.n_out + n]) : 0.f);
+        return;
+    }
+    if (A.mode == 3) {
+        // reverse pass at the network input: Re = J^T a, Im_j = h (a^T H)[:, j]
+        if (n >= A.n_out) return;
+#pragma unroll
+        for (int c = 0; c < CP; ++c)
+            if (c <= r) A.dout[(size_t)c * A.n_out + n] = v[c];
+        return;
+    }
     if (!A.last) {
         if (n >= A.ldy) return;
         const size_t ldy = A.ldy;
@@ -425,7 +460,7 @@ int tc_split(int m_pad, int ld, dae_prec prec, int sm_count) {
 
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count) {
     if (!a.tmaps || a.m_pad % 128 != 0) return false;
-    int split = a.last ? 1 : tc_split(a.m_pad, a.ld, prec, sm_count);
+    int split = (a.mode == 1) ? 1 : tc_split(a.m_pad, a.ld, prec, sm_count);
     if (!a.split_part || !a.split_cnt) split = 1;
     switch (prec) {
         case DAE_TF32: return launch_prec<DAE_TF32>(s, a, split);
