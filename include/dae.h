@@ -230,6 +230,39 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------ allocation-free variant -- */
+
+/*
+ * The output-row reductions of dae_assemble_reduced, for callers that cannot
+ * allocate device memory: processes that hand all device memory to their own
+ * pool at start-up, real-time loops where a cudaMalloc stall is not allowed, or
+ * code that runs while an allocator is busy.  This entry point calls no
+ * cudaMalloc / cudaFree and no allocating library routine: its per-block partial
+ * sums live in a fixed file-scope device array of 4 MiB (2^20 floats) plus 32 KiB
+ * of FP64 sums, reserved on every GPU that loads this library until the process
+ * exits.  The paper has no counterpart; it is an interface for such callers.
+ *
+ *   N, r         output rows and latent size (1 <= r <= 32)
+ *   J, dJ        N x r column-major (as written by dae_eval_derivs)
+ *   HDD          N: H[Delta,Delta] (= dt^2 times the Hqq output of dae_eval_derivs)
+ *   mdof         N lumped mass per DOF;  f_ext  N external force or NULL
+ *   z            r FP32: (q - qbar) - dt qbar_dot
+ *   phi_dense    r FP64: J^T (M (J z + H[Delta,Delta]) - dt^2 f_ext)
+ *   Mr, B        r x r FP64 column-major: J^T M J and J^T M dJ (either may be NULL)
+ *   cuda_stream  stream to enqueue on (NULL = legacy default stream)
+ * Every pointer is device memory; the call only enqueues and returns.  Limits:
+ * ceil(N / 128) * (r + r(r+1)/2 + r^2) <= 2^20 (for r = 30: N <= 96 000);
+ * larger problems return DAE_ERR_INVALID_ARG.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one array
+ * and each call overwrites it, so calls that can overlap on the GPU (different
+ * streams, or concurrent host threads) race: serialize them.
+ */
+dae_status dae_reduce_rows_noalloc(int N, int r, const float* J, const float* dJ,
+                                   const float* HDD, const float* mdof, const float* f_ext,
+                                   const float* z, double dt, double* phi_dense, double* Mr,
+                                   double* B, void* cuda_stream);
+
 /* ------------------------------------------------------ instrumentation -- */
 /* Not part of the paper's method: device timing of the phases of every
  * evaluation, for benchmarks and profiles. */

@@ -69,6 +69,7 @@ SIGNATURES = {
     "dae_newton_step": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp,
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
+    "dae_reduce_rows_noalloc": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp], _i),
     "dae_profile_enable": ([_vp, ctypes.c_uint], _i),
     "dae_profile_read": ([_vp, _vp, _vp], _i),
     "dae_launch_count": ([_vp], ctypes.c_longlong),
@@ -278,3 +279,15 @@ def dae_profile_read(ctx):
 
 def dae_launch_count(ctx):
     return int(lib().dae_launch_count(ctx))
+
+
+def dae_reduce_rows_noalloc(N, r, J, dJ, HDD, mdof, f_ext, z, dt, phi_dense=None, Mr=None, B=None,
+                            stream=None):
+    """Row reductions with no device allocation (all arrays device tensors)."""
+    st = lib().dae_reduce_rows_noalloc(int(N), int(r), _ptr(J, np.float32), _ptr(dJ, np.float32),
+                                       _ptr(HDD, np.float32), _ptr(mdof, np.float32),
+                                       _ptr(f_ext, np.float32), _ptr(z, np.float32), float(dt),
+                                       _ptr(phi_dense, np.float64), _ptr(Mr, np.float64),
+                                       _ptr(B, np.float64), stream)
+    if st != 0:
+        raise DaeError(st, "dae_reduce_rows_noalloc failed")
