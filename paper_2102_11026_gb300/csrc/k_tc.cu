@@ -150,106 +150,82 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One output row held in registers (all Cp columns): the same per-row math as the
-// CUDA-core kernel's epilogue, with compile-time column indices.
-template <int NC>
-__device__ __forceinline__ void row_epilogue(const FwdArgs& A, int n, const float* v) {
-    constexpr int CP = 16 * NC;
-    constexpr int JMAX = (CP - kShared) / 3;
-    const int r = A.r;
+// Epilogue of one output row whose Cp accumulator columns sit in shared memory
+// (v[c], stride 1).  Runtime loops keep the executed code small: the kernel runs
+// each epilogue once per CTA, so straight-line unrolled code would be fetched
+// cold from memory.
+__device__ __forceinline__ void put_act(const FwdArgs& A, size_t idx, float x) {
+    if (A.out_f32) A.Y[idx] = x;
+    if (A.out_bf16) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        A.Yh[idx] = hi;
+        if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+__device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const float* v) {
+    const int r = A.r, CP = A.Cp, C = n_cols(r);
     if (A.mode == 2) {
         // reverse pass: delta of this layer's input -> g of the layer below,
         // Re g = Re d s1, Im_j g = Im_j d s1 + Re d (s2 b_j)   (Sec. 4.4 complex BP)
         if (n >= A.ldy) return;
         const size_t ldy = A.ldy;
-        auto put = [&](int c, float x) {
-            const size_t idx = (size_t)c * ldy + n;
-            if (A.out_f32) A.Y[idx] = x;
-            if (A.out_bf16) {
-                __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                A.Yh[idx] = hi;
-                if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
-        };
         if (n >= A.n_out) {
-#pragma unroll
-            for (int c = 0; c < CP; ++c) put(c, 0.f);
+            for (int c = 0; c < CP; ++c) put_act(A, (size_t)c * ldy + n, 0.f);
             return;
         }
         const float s1 = A.S1[n];
         const float re = v[0];
-        put(0, re * s1);
-#pragma unroll
+        put_act(A, n, re * s1);
         for (int c = 1; c < CP; ++c)
-            put(c, c <= r ? fmaf(v[c], s1, re * A.T[(size_t)(c - 1) * A.n_out + n]) : 0.f);
+            put_act(A, (size_t)c * ldy + n,
+                    c <= r ? fmaf(v[c], s1, re * A.T[(size_t)(c - 1) * A.n_out + n]) : 0.f);
         return;
     }
     if (A.mode == 3) {
         // reverse pass at the network input: Re = J^T a, Im_j = h (a^T H)[:, j]
         if (n >= A.n_out) return;
-#pragma unroll
-        for (int c = 0; c < CP; ++c)
-            if (c <= r) A.dout[(size_t)c * A.n_out + n] = v[c];
+        for (int c = 0; c <= r; ++c) A.dout[(size_t)c * A.n_out + n] = v[c];
         return;
     }
-    if (!A.last) {
+    if (A.mode == 0) {
         if (n >= A.ldy) return;
         const size_t ldy = A.ldy;
-        auto put = [&](int c, float x) {
-            const size_t idx = (size_t)c * ldy + n;
-            if (A.out_f32) A.Y[idx] = x;
-            if (A.out_bf16) {
-                __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                A.Yh[idx] = hi;
-                if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
-        };
         if (n >= A.n_out) {
-#pragma unroll
-            for (int c = 0; c < CP; ++c) put(c, 0.f);
+            for (int c = 0; c < CP; ++c) put_act(A, (size_t)c * ldy + n, 0.f);
             return;
         }
         const ActD D = act_d(A.act, v[0] + A.bias[n]);
         const float c = v[1], gw = v[2];
         float oc, ogw, og0;
         mc_shared(D, c, gw, v[3], oc, ogw, og0);
-        put(0, D.s0);
-        put(1, oc);
-        put(2, ogw);
-        put(3, og0);
+        put_act(A, n, D.s0);
+        put_act(A, ldy + n, oc);
+        put_act(A, 2 * ldy + n, ogw);
+        put_act(A, 3 * ldy + n, og0);
         if (A.S1) A.S1[n] = D.s1;
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
+        for (int j = 0; j < r; ++j) {
             const int cb = kShared + 3 * j;
-            if (j < r) {
-                float ob, od, oh;
-                mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
-                put(cb, ob);
-                put(cb + 1, od);
-                put(cb + 2, oh);
-                if (A.T) A.T[(size_t)j * A.n_out + n] = D.s2 * v[cb];
-            } else {
-                put(cb, 0.f);
-                put(cb + 1, 0.f);
-                put(cb + 2, 0.f);
-            }
+            float ob, od, oh;
+            mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
+            put_act(A, (size_t)cb * ldy + n, ob);
+            put_act(A, (size_t)(cb + 1) * ldy + n, od);
+            put_act(A, (size_t)(cb + 2) * ldy + n, oh);
+            if (A.T) A.T[(size_t)j * A.n_out + n] = D.s2 * v[cb];
         }
-#pragma unroll
-        for (int cc = kShared + 3 * JMAX; cc < CP; ++cc) put(cc, 0.f);
-    } else {
-        if (n >= A.n_out) return;
-        const size_t N = A.n_out;
-        if (A.u) A.u[n] = v[0] + A.bias[n];
-        if (A.HDD) A.HDD[n] = (float)(v[3] * A.inv_h2);
-        if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-            if (j < r) {
-                const int cb = kShared + 3 * j;
-                if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb] * A.inv_h);
-                if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 2] * A.inv_h3);
-            }
-        }
+        for (int cc = C; cc < CP; ++cc) put_act(A, (size_t)cc * ldy + n, 0.f);
+        return;
+    }
+    // mode 1: output layer
+    if (n >= A.n_out) return;
+    const size_t N = A.n_out;
+    if (A.u) A.u[n] = v[0] + A.bias[n];
+    if (A.HDD) A.HDD[n] = (float)(v[3] * A.inv_h2);
+    if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
+    for (int j = 0; j < r; ++j) {
+        const int cb = kShared + 3 * j;
+        if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb] * A.inv_h);
+        if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 2] * A.inv_h3);
     }
 }
 
@@ -357,26 +333,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool ok = mbar_wait(&tfull, 0);
         tc_fence_after();
         const int lane_base = 32 * (warp & 3);
-        const int n = m0 + lane_base + lane;
-        float v[CP];
+        const int row = lane_base + lane;
+        const int n = m0 + row;
+        // the pipeline buffers are idle once the accumulator is complete: stage the
+        // tile there, one row per thread (odd stride: conflict-free)
+        constexpr int TS = CP + 1;
+        float* tile = reinterpret_cast<float*>(smem);
+        float* vrow = tile + (size_t)row * TS;
         const bool wok = __all_sync(0xffffffffu, ok);
         if (wok) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 16 * c, v + 16 * c);
-            tmem_wait_ld();
+            for (int c = 0; c < NC; ++c) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 16 * c, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) vrow[16 * c + i] = v[i];
+            }
         } else {
             fail = 1;
+            for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
         }
         if (split == 1) {
-            if (wok) row_epilogue<NC>(A, n, v);
+            if (wok) row_epilogue(A, n, vrow);
         } else {
             // write this split's partial tile [tile][split][c][128 rows]; the last CTA of the
             // tile (atomic count, no waiting) sums the partials in split order and finishes
-            const int row = lane_base + lane;
             float* part = A.split_part + ((size_t)blockIdx.x * split + blockIdx.y) * CP * 128;
-#pragma unroll
-            for (int c = 0; c < CP; ++c) part[(size_t)c * 128 + row] = wok ? v[c] : 0.f;
+            for (int c = 0; c < CP; ++c) part[(size_t)c * 128 + row] = vrow[c];
             __threadfence();
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (warp == 2 && lane == 0) {
@@ -388,13 +372,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (is_last) {
                 __threadfence();
                 const float* tp = A.split_part + (size_t)blockIdx.x * split * CP * 128;
-#pragma unroll
-                for (int c = 0; c < CP; ++c) v[c] = 0.f;
-                for (int s = 0; s < split; ++s) {
-#pragma unroll
-                    for (int c = 0; c < CP; ++c) v[c] += __ldcg(tp + ((size_t)s * CP + c) * 128 + row);
+                for (int c = 0; c < CP; ++c) {
+                    float acc = 0.f;
+                    for (int s = 0; s < split; ++s) acc += __ldcg(tp + ((size_t)s * CP + c) * 128 + row);
+                    vrow[c] = acc;
                 }
-                row_epilogue<NC>(A, n, v);
+                row_epilogue(A, n, vrow);
             }
         }
     }
