@@ -261,6 +261,7 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
+    dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.gbar); dfree(w.chain_part);
     dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
@@ -299,6 +300,98 @@ struct Outs {
     float *u = nullptr, *J = nullptr, *dJ = nullptr, *HDD = nullptr, *Hqq = nullptr;
 };
 
+// Forward-pass arguments of layer l that do not change between calls.
+void fill_fwd_args(const dae_decoder* d, int l, FwdArgs& a) {
+    const Workspace& w = d->ws;
+    const Layer& ly = d->layers[l];
+    const int L = d->L;
+    memset(&a, 0, sizeof a);
+    a.W = ly.W; a.ld = ly.ld; a.Wh = ly.Wh; a.Wl = ly.Wl; a.bias = ly.b;
+    a.X = w.X[l & 1]; a.Xh = w.Xh[l & 1]; a.Xl = w.Xl[l & 1];
+    a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = d->r; a.Cp = w.Cp;
+    a.act = d->act;
+    a.last = (l == L - 1);
+    a.mode = a.last ? 1 : 0;
+    // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
+    a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
+    a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
+    a.split_part = w.split_part;
+    a.split_cnt = w.split_cnt;
+    if (!a.last) {
+        a.Y = w.X[(l + 1) & 1]; a.Yh = w.Xh[(l + 1) & 1]; a.Yl = w.Xl[(l + 1) & 1];
+        a.ldy = (int)round_up(ly.n_out, kKPad);
+        a.out_bf16 = out_bf16_of(d->prec);
+        a.S1 = w.S1[l]; a.T = w.T[l];
+    }
+}
+
+// Reverse-pass arguments of hidden layer l (tensor-core path).
+void fill_rev_args(const dae_decoder* d, int l, FwdArgs& a) {
+    const Workspace& w = d->ws;
+    const Layer& ly = d->layers[l];
+    const int L = d->L;
+    memset(&a, 0, sizeof a);
+    a.ld = ly.ldT; a.m_pad = ly.mT_pad; a.n_in = ly.n_out; a.n_out = ly.n_in;
+    a.r = d->r; a.Cp = w.Cb;
+    a.tmaps = ly.tmR; a.split_part = w.split_part; a.split_cnt = w.split_cnt;
+    if (l > 0) {
+        const int nb = (L - 1 - l) & 1;
+        a.mode = 2;
+        a.Y = w.G32[nb]; a.Yh = w.Gh[nb]; a.Yl = w.Gl[nb];
+        a.ldy = d->layers[l - 1].ldT;
+        a.out_f32 = (d->prec == DAE_TF32);
+        a.out_bf16 = out_bf16_of(d->prec);
+        a.S1 = w.S1[l - 1]; a.T = w.T[l - 1];
+    } else {
+        a.mode = 3;
+        a.dout = w.bwd_part[1];
+    }
+}
+
+// Job lists of the persistent layer-chain kernel (both directions).
+dae_status build_chains(dae_decoder* d) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    const int L = d->L, G = ctx->sm_count;
+    const int KB = d->prec == DAE_TF32 ? 32 : 64;
+    std::vector<ChainJob> fj(L - 1), rj(L - 1);
+    size_t part = 1;
+    for (int l = 0; l < L - 1; ++l) {
+        const Layer& ly = d->layers[l];
+        ChainJob& j = fj[l];
+        memset(&j, 0, sizeof j);
+        memcpy(j.tm, ly.tm, sizeof j.tm);
+        fill_fwd_args(d, l, j.a);
+        j.tiles = ly.m_pad / 128;
+        j.nk = ly.ld / KB;
+        j.split = chain_split(j.tiles, j.nk, G);
+        part = std::max(part, (size_t)j.tiles * j.split * w.Cp * 128);
+    }
+    for (int i = 0; i < L - 1; ++i) {
+        const int l = L - 2 - i;
+        const Layer& ly = d->layers[l];
+        ChainJob& j = rj[i];
+        memset(&j, 0, sizeof j);
+        memcpy(j.tm, ly.tmR, sizeof j.tm);
+        fill_rev_args(d, l, j.a);
+        j.tiles = ly.mT_pad / 128;
+        j.nk = ly.ldT / KB;
+        j.split = chain_split(j.tiles, j.nk, G);
+        part = std::max(part, (size_t)j.tiles * j.split * w.Cb * 128);
+    }
+    if (!w.fwd_jobs) {
+        CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * (L - 1)));
+        CU(ctx, cudaMalloc(&w.rev_jobs, sizeof(ChainJob) * (L - 1)));
+        TRY(dmalloc(ctx, &w.gbar, 1));
+    }
+    dfree(w.chain_part);
+    TRY(dmalloc(ctx, &w.chain_part, part));
+    CU(ctx, cudaMemcpy(w.fwd_jobs, fj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
+    CU(ctx, cudaMemcpy(w.rev_jobs, rj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
+    w.chain_ok = true;
+    return DAE_OK;
+}
+
 dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* q_override,
                            double dt, double h, int mode, const Outs& o) {
     dae_ctx* ctx = d->ctx;
@@ -312,31 +405,24 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0],
                     w.Xh[0], w.Xl[0], ob, w.zvec);
     }
-    for (int l = 0; l < L; ++l) {
-        const Layer& ly = d->layers[l];
+    const bool chain = d->ws.chain_ok;
+    if (chain) {
+        // hidden layers: one persistent cooperative launch for the whole chain
+        ChainLaunch cl;
+        cl.jobs = w.fwd_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
+        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+        Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
+        if (!launch_chain(s, cl, d->prec))
+            return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    for (int l = chain ? L - 1 : 0; l < L; ++l) {
         FwdArgs a;
-        memset(&a, 0, sizeof a);
-        a.W = ly.W; a.ld = ly.ld; a.Wh = ly.Wh; a.Wl = ly.Wl; a.bias = ly.b;
-        a.X = w.X[l & 1]; a.Xh = w.Xh[l & 1]; a.Xl = w.Xl[l & 1];
-        a.n_in = ly.n_in; a.n_out = ly.n_out; a.m_pad = ly.m_pad; a.r = r; a.Cp = w.Cp;
-        a.act = d->act;
-        a.last = (l == L - 1);
-        a.mode = a.last ? 1 : 0;
-        // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
-        a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
-        a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
-        a.split_part = w.split_part;
-        a.split_cnt = w.split_cnt;
+        fill_fwd_args(d, l, a);
         a.ns = ns;
         a.status = ctx->d_status;
         a.inv_h = 1.0 / h; a.inv_h2 = 1.0 / (h * h); a.inv_h3 = 1.0 / (h * h * h);
         a.inv_dt2 = 1.0 / (dt * dt);
-        if (!a.last) {
-            a.Y = w.X[(l + 1) & 1]; a.Yh = w.Xh[(l + 1) & 1]; a.Yl = w.Xl[(l + 1) & 1];
-            a.ldy = (int)round_up(ly.n_out, kKPad);
-            a.out_bf16 = ob;
-            a.S1 = w.S1[l]; a.T = w.T[l];
-        } else {
+        if (a.last) {
             a.u = o.u; a.J = o.J; a.dJ = o.dJ; a.HDD = o.HDD; a.Hqq = o.Hqq;
         }
         Phase p(ctx, a.last ? DAE_PHASE_FWD_OUT : DAE_PHASE_FWD_HIDDEN, 1);
@@ -516,27 +602,23 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
             Phase p(ctx, DAE_PHASE_BWD, 1);
             launch_bwd_prep_tc(s, ba, w.Cb, d->layers[L - 2].ldT, w.G32[0], w.Gh[0], w.Gl[0], of32, ob);
         }
-        for (int l = L - 2; l >= 0; --l) {
-            const Layer& ly = d->layers[l];
-            FwdArgs a;
-            memset(&a, 0, sizeof a);
-            a.ld = ly.ldT; a.m_pad = ly.mT_pad; a.n_in = ly.n_out; a.n_out = ly.n_in;
-            a.r = r; a.Cp = w.Cb; a.ns = ns; a.status = ctx->d_status;
-            a.tmaps = ly.tmR; a.split_part = w.split_part; a.split_cnt = w.split_cnt;
-            if (l > 0) {
-                const int nb = (L - 1 - l) & 1;
-                a.mode = 2;
-                a.Y = w.G32[nb]; a.Yh = w.Gh[nb]; a.Yl = w.Gl[nb];
-                a.ldy = d->layers[l - 1].ldT;
-                a.out_f32 = of32; a.out_bf16 = ob;
-                a.S1 = w.S1[l - 1]; a.T = w.T[l - 1];
-            } else {
-                a.mode = 3;
-                a.dout = w.bwd_part[1];
-            }
+        if (w.chain_ok) {
+            ChainLaunch cl;
+            cl.jobs = w.rev_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cb; cl.grid = ctx->sm_count;
+            cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
             Phase p(ctx, DAE_PHASE_BWD, 1);
-            if (!launch_fwd_tc(s, a, d->prec, sm))
-                return fail(ctx, DAE_ERR_UNSUPPORTED, "reverse GEMM launch failed for layer %d", l);
+            if (!launch_chain(s, cl, d->prec))
+                return fail(ctx, DAE_ERR_CUDA, "reverse layer-chain launch failed");
+        } else {
+            for (int l = L - 2; l >= 0; --l) {
+                FwdArgs a;
+                fill_rev_args(d, l, a);
+                a.ns = ns;
+                a.status = ctx->d_status;
+                Phase p(ctx, DAE_PHASE_BWD, 1);
+                if (!launch_fwd_tc(s, a, d->prec, sm))
+                    return fail(ctx, DAE_ERR_UNSUPPORTED, "reverse GEMM launch failed for layer %d", l);
+            }
         }
         cur = 1;
         in_split = 1;
@@ -1027,6 +1109,9 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
         CU(ctx, cudaGetLastError());
         CU(ctx, cudaStreamSynchronize(ctx->stream));
     }
+    d->prec = prec;
+    d->ws.chain_ok = false;
+    if (prec != DAE_FP32) TRY(build_chains(d));
     d->prec = prec;
     return DAE_OK;
 }

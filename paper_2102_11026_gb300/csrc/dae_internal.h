@@ -72,6 +72,9 @@ struct NewtonState {
     int pad_;
 };
 
+struct ChainJob;
+struct GridBar;
+
 // Device-resident control of a sequence of frames (rollout or single Newton step).
 struct RollCtl {
     int n_frames;
@@ -118,6 +121,12 @@ struct Workspace {
     float* G32[2] = {nullptr, nullptr};
     __nv_bfloat16* Gh[2] = {nullptr, nullptr};
     __nv_bfloat16* Gl[2] = {nullptr, nullptr};
+    // persistent layer-chain jobs (tensor-core precisions)
+    ChainJob* fwd_jobs = nullptr;  // hidden forward layers 0..L-2 (device)
+    ChainJob* rev_jobs = nullptr;  // reverse layers L-2..0 (device)
+    GridBar* gbar = nullptr;
+    float* chain_part = nullptr;   // split-K partial tiles of the chains
+    bool chain_ok = false;
     float* split_part = nullptr;   // split-K partial tiles of the hidden tensor-core GEMMs
     int* split_cnt = nullptr;      // per-tile counters
     int max_split = 0;
@@ -247,6 +256,20 @@ void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override
                  int out_bf16, float* zvec);
 void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
+
+// Persistent layer-chain kernel (k_chain.cu): one job per GEMM layer.
+struct ChainJob {
+    CUtensorMap tm[4];           // A, A lo, B, B lo
+    FwdArgs a;                   // epilogue (mode 0, 2 or 3)
+    int tiles, split, nk, pad_;
+};
+struct GridBar { unsigned count; unsigned gen; };
+struct ChainLaunch {
+    const ChainJob* jobs; int n_jobs; int Cp; int grid;
+    GridBar* gb; const NewtonState* ns; int* status; float* split_part;
+};
+bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
+int chain_split(int tiles, int nk, int grid);
 constexpr int kMaxSplit = 16;
 int tc_split(int m_pad, int ld, dae_prec prec, int sm_count);
 
