@@ -144,92 +144,104 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 // Epilogue of one output row whose Cp accumulator columns sit in shared memory
-// (v[c], stride 1).  Runtime loops keep the executed code small: the kernel runs
-// each epilogue once per CTA, so straight-line unrolled code would be fetched
-// cold from memory.
-__device__ __forceinline__ void put_act(const FwdArgs& A, size_t idx, float x) {
-    if (A.out_f32) A.Y[idx] = x;
-    if (A.out_bf16) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        A.Yh[idx] = hi;
-        if (A.out_bf16 == 2) A.Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+// (v[c], stride 1).  Runtime loops keep the executed code small; every argument
+// is read once into a register-resident local (the stores below cannot alias
+// them), so the loops issue stores back to back.
+struct ActOut {
+    float* __restrict__ Y;
+    __nv_bfloat16* __restrict__ Yh;
+    __nv_bfloat16* __restrict__ Yl;
+    int f32, bf16;
+    __device__ __forceinline__ void put(size_t idx, float x) const {
+        if (f32) Y[idx] = x;
+        if (bf16) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            Yh[idx] = hi;
+            if (bf16 == 2) Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
     }
-}
+};
 
 static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const float* v) {
-    const int r = A.r, CP = A.Cp, C = n_cols(r);
-    if (A.mode == 2) {
+    const int mode = A.mode, r = A.r, CP = A.Cp, C = n_cols(r);
+    const int n_out = A.n_out;
+    if (mode == 3) {
+        // reverse pass at the network input: Re = J^T a, Im_j = h (a^T H)[:, j]
+        if (n >= n_out) return;
+        float* __restrict__ dout = A.dout;
+        for (int c = 0; c <= r; ++c) dout[(size_t)c * n_out + n] = v[c];
+        return;
+    }
+    if (mode == 1) {
+        if (n >= n_out) return;
+        const size_t N = n_out;
+        float* __restrict__ u = A.u;
+        float* __restrict__ J = A.J;
+        float* __restrict__ dJ = A.dJ;
+        float* __restrict__ HDD = A.HDD;
+        float* __restrict__ Hqq = A.Hqq;
+        const double ih = A.inv_h, ih2 = A.inv_h2, ih3 = A.inv_h3, idt2 = A.inv_dt2;
+        if (u) u[n] = v[0] + A.bias[n];
+        if (HDD) HDD[n] = (float)(v[3] * ih2);
+        if (Hqq) Hqq[n] = (float)(v[3] * ih2 * idt2);
+        for (int j = 0; j < r; ++j) {
+            const int cb = kShared + 3 * j;
+            if (J) J[(size_t)j * N + n] = (float)(v[cb] * ih);
+            if (dJ) dJ[(size_t)j * N + n] = (float)(v[cb + 2] * ih3);
+        }
+        return;
+    }
+    const ActOut o{A.Y, A.Yh, A.Yl, A.out_f32, A.out_bf16};
+    const int ldy_i = A.ldy;
+    if (n >= ldy_i) return;
+    const size_t ldy = ldy_i;
+    if (n >= n_out) {
+        for (int c = 0; c < CP; ++c) o.put((size_t)c * ldy + n, 0.f);
+        return;
+    }
+    const float* __restrict__ T = A.T;
+    if (mode == 2) {
         // reverse pass: delta of this layer's input -> g of the layer below,
         // Re g = Re d s1, Im_j g = Im_j d s1 + Re d (s2 b_j)   (Sec. 4.4 complex BP)
-        if (n >= A.ldy) return;
-        const size_t ldy = A.ldy;
-        if (n >= A.n_out) {
-            for (int c = 0; c < CP; ++c) put_act(A, (size_t)c * ldy + n, 0.f);
-            return;
-        }
         const float s1 = A.S1[n];
         const float re = v[0];
-        put_act(A, n, re * s1);
+        o.put(n, re * s1);
         for (int c0 = 1; c0 < CP; c0 += 8) {
             float tv[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                tv[i] = (c0 + i <= r) ? A.T[(size_t)(c0 + i - 1) * A.n_out + n] : 0.f;
+                tv[i] = (c0 + i <= r) ? T[(size_t)(c0 + i - 1) * n_out + n] : 0.f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int c = c0 + i;
-                if (c < CP) put_act(A, (size_t)c * ldy + n, c <= r ? fmaf(v[c], s1, re * tv[i]) : 0.f);
+                if (c < CP) o.put((size_t)c * ldy + n, c <= r ? fmaf(v[c], s1, re * tv[i]) : 0.f);
             }
         }
         return;
     }
-    if (A.mode == 3) {
-        // reverse pass at the network input: Re = J^T a, Im_j = h (a^T H)[:, j]
-        if (n >= A.n_out) return;
-        for (int c = 0; c <= r; ++c) A.dout[(size_t)c * A.n_out + n] = v[c];
-        return;
-    }
-    if (A.mode == 0) {
-        if (n >= A.ldy) return;
-        const size_t ldy = A.ldy;
-        if (n >= A.n_out) {
-            for (int c = 0; c < CP; ++c) put_act(A, (size_t)c * ldy + n, 0.f);
-            return;
-        }
-        const ActD D = act_d(A.act, v[0] + A.bias[n]);
-        const float c = v[1], gw = v[2];
-        float oc, ogw, og0;
-        mc_shared(D, c, gw, v[3], oc, ogw, og0);
-        put_act(A, n, D.s0);
-        put_act(A, ldy + n, oc);
-        put_act(A, 2 * ldy + n, ogw);
-        put_act(A, 3 * ldy + n, og0);
-        if (A.S1) A.S1[n] = D.s1;
-        for (int j = 0; j < r; ++j) {
-            const int cb = kShared + 3 * j;
-            float ob, od, oh;
-            mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
-            put_act(A, (size_t)cb * ldy + n, ob);
-            put_act(A, (size_t)(cb + 1) * ldy + n, od);
-            put_act(A, (size_t)(cb + 2) * ldy + n, oh);
-            if (A.T) A.T[(size_t)j * A.n_out + n] = D.s2 * v[cb];
-        }
-        for (int cc = C; cc < CP; ++cc) put_act(A, (size_t)cc * ldy + n, 0.f);
-        return;
-    }
-    // mode 1: output layer
-    if (n >= A.n_out) return;
-    const size_t N = A.n_out;
-    if (A.u) A.u[n] = v[0] + A.bias[n];
-    if (A.HDD) A.HDD[n] = (float)(v[3] * A.inv_h2);
-    if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
+    // mode 0: hidden layer, multicomplex activation (epilogue.cuh)
+    float* __restrict__ S1 = A.S1;
+    float* __restrict__ Tw = A.T;
+    const ActD D = act_d(A.act, v[0] + A.bias[n]);
+    const float c = v[1], gw = v[2];
+    float oc, ogw, og0;
+    mc_shared(D, c, gw, v[3], oc, ogw, og0);
+    o.put(n, D.s0);
+    o.put(ldy + n, oc);
+    o.put(2 * ldy + n, ogw);
+    o.put(3 * ldy + n, og0);
+    if (S1) S1[n] = D.s1;
     for (int j = 0; j < r; ++j) {
         const int cb = kShared + 3 * j;
-        if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb] * A.inv_h);
-        if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 2] * A.inv_h3);
+        float ob, od, oh;
+        mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
+        o.put((size_t)cb * ldy + n, ob);
+        o.put((size_t)(cb + 1) * ldy + n, od);
+        o.put((size_t)(cb + 2) * ldy + n, oh);
+        if (Tw) Tw[(size_t)j * n_out + n] = D.s2 * v[cb];
     }
+    for (int cc = C; cc < CP; ++cc) o.put((size_t)cc * ldy + n, 0.f);
 }
-
 
 }  // namespace tc
 }  // namespace dae
