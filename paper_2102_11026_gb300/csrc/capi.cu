@@ -298,6 +298,9 @@ dae_status ensure_cubature(dae_decoder* d, int n_cub, int n_w) {
 // ----------------------------------------------------------- evaluation --
 struct Outs {
     float *u = nullptr, *J = nullptr, *dJ = nullptr, *HDD = nullptr, *Hqq = nullptr;
+    // fused row reductions of the output layer (tensor-core path)
+    float* row_part = nullptr; int row_stride = 0;
+    const float* mdof = nullptr; const float* f_ext = nullptr; float* a_out = nullptr;
 };
 
 // Forward-pass arguments of layer l that do not change between calls.
@@ -424,6 +427,10 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         a.inv_dt2 = 1.0 / (dt * dt);
         if (a.last) {
             a.u = o.u; a.J = o.J; a.dJ = o.dJ; a.HDD = o.HDD; a.Hqq = o.Hqq;
+            if (d->prec != DAE_FP32 && o.row_part) {
+                a.row_part = o.row_part; a.row_stride = o.row_stride;
+                a.mdof = o.mdof; a.f_ext = o.f_ext; a.zvec = w.zvec; a.dt = dt; a.a_out = o.a_out;
+            }
         }
         Phase p(ctx, a.last ? DAE_PHASE_FWD_OUT : DAE_PHASE_FWD_HIDDEN, 1);
         if (d->prec == DAE_FP32) {
@@ -540,7 +547,13 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     const int sm = ctx->sm_count;
     Outs o;
     o.u = w.u; o.J = w.J; o.dJ = w.dJ; o.HDD = w.HDD;
+    const bool fused_rows = d->prec != DAE_FP32;
+    if (fused_rows) {
+        o.row_part = w.row_part; o.row_stride = w.row_stride;
+        o.mdof = m->mdof; o.f_ext = P.f_ext; o.a_out = w.a;
+    }
     TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o));
+    if (!fused_rows) {
     RowArgs ra;
     ra.J = w.J; ra.dJ = w.dJ; ra.HDD = w.HDD; ra.mdof = m->mdof; ra.f_ext = P.f_ext;
     ra.zvec = w.zvec; ra.a = w.a; ra.part = w.row_part; ra.N = N; ra.r = r;
@@ -548,6 +561,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     {
         Phase p(ctx, DAE_PHASE_ROWS, 1);
         launch_row_reduce(s, ra, w.n_row_blocks);
+    }
     }
     CubArgs ca;
     ca.w_stride = P.w_stride;

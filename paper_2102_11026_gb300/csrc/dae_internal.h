@@ -235,6 +235,10 @@ struct FwdArgs {
     int mode;                                // 0 forward hidden, 1 forward output,
                                              // 2 reverse (next g), 3 reverse (input layer)
     float* dout;                             // mode 3: delta_0 [1+r][r]
+    // mode 1, fused row reductions (null row_part: not fused)
+    float* row_part; int row_stride;         // per-tile [J^T a | Mr upper | B] partials
+    const float* mdof; const float* f_ext; const float* zvec; double dt;
+    float* a_out;                            // dense a_n (may be null)
     // hidden-layer outputs
     float* Y; __nv_bfloat16* Yh; __nv_bfloat16* Yl; int ldy;   // next activations [Cp][ldy]
     int out_bf16;                            // 0 none, 1 hi, 2 hi+lo

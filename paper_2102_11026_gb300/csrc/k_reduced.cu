@@ -110,72 +110,92 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     int v[4];
     for (int a = 0; a < 4; ++a) v[a] = A.tets[4 * tet + a];
     const float* Bmf = A.Bm + 9 * (size_t)tet;
-    double Bm[9];
-    for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
-    const double V = A.vol[tet];
-    // dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
-    double dU[9];
-    for (int c = 0; c < 3; ++c)
-        for (int d = 0; d < 3; ++d)
-            dU[d * 3 + c] = (double)A.u[3 * v[c + 1] + d] - (double)A.u[3 * v[0] + d];
-    double G[9], F[9], P[9], psi;
-    mat3_mul(dU, Bm, G);
-    for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.0 : 0.0);
-    const double mu = A.mu, lam = A.lam;
-    double Finv_T[9], lnJ = 0.0, Sst[9];
-    bool bad = false;
-    if (A.material == DAE_STVK) {
-        double E[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                double gg = 0.0;
-                for (int k = 0; k < 3; ++k) gg += G[k * 3 + i] * G[k * 3 + j];
-                E[i * 3 + j] = 0.5 * (G[i * 3 + j] + G[j * 3 + i] + gg);
-            }
-        double trE = E[0] + E[4] + E[8];
-        double trE2 = 0.0;
-        for (int i = 0; i < 9; ++i) trE2 += E[i] * E[i];
-        for (int i = 0; i < 9; ++i) Sst[i] = 2.0 * mu * E[i] + ((i % 4) == 0 ? lam * trE : 0.0);
-        mat3_mul(F, Sst, P);
-        psi = mu * trE2 + 0.5 * lam * trE * trE;
-    } else {
-        // J - 1 = tr G + (principal 2x2 minors of G) + det G
-        double trG = G[0] + G[4] + G[8];
-        double m2 = G[0] * G[4] - G[1] * G[3] + G[0] * G[8] - G[2] * G[6] + G[4] * G[8] - G[5] * G[7];
-        double detG = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
-                    G[2] * (G[3] * G[7] - G[4] * G[6]);
-        double Jm1 = trG + m2 + detG;
-        double Jd = 1.0 + Jm1;
-        if (!(Jd > 0.0)) {
-            bad = true;
-            psi = 0.0;
-            for (int i = 0; i < 9; ++i) P[i] = 0.0;
+    const float Vf = A.vol[tet];
+    // per-tet FP64 part (F, P, Psi) once per warp: FP64 throughput is a small fraction
+    // of FP32 on this part, so the 31 other lanes wait and then read the results
+    __shared__ float sF[8][9], sS[8][9], sFiT[8][9], sP[8][9], sLnJ[8];
+    __shared__ int sBad[8];
+    if (lane == 0) {
+        double Bm[9];
+        for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
+        const double V = Vf;
+        // dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
+        double dU[9];
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d)
+                dU[d * 3 + c] = (double)A.u[3 * v[c + 1] + d] - (double)A.u[3 * v[0] + d];
+        double G[9], F[9], P[9], psi = 0.0, Finv_T[9], lnJ = 0.0, Sst[9];
+        mat3_mul(dU, Bm, G);
+        for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.0 : 0.0);
+        const double mu = A.mu, lam = A.lam;
+        int bad = 0;
+        for (int i = 0; i < 9; ++i) { Finv_T[i] = 0.0; Sst[i] = 0.0; }
+        if (A.material == DAE_STVK) {
+            double E[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double gg = 0.0;
+                    for (int kk = 0; kk < 3; ++kk) gg += G[kk * 3 + i] * G[kk * 3 + j];
+                    E[i * 3 + j] = 0.5 * (G[i * 3 + j] + G[j * 3 + i] + gg);
+                }
+            const double trE = E[0] + E[4] + E[8];
+            double trE2 = 0.0;
+            for (int i = 0; i < 9; ++i) trE2 += E[i] * E[i];
+            for (int i = 0; i < 9; ++i) Sst[i] = 2.0 * mu * E[i] + ((i % 4) == 0 ? lam * trE : 0.0);
+            mat3_mul(F, Sst, P);
+            psi = mu * trE2 + 0.5 * lam * trE * trE;
         } else {
-            lnJ = log1p(Jm1);
-            // F^{-T} = cof(F) / J
-            double cof[9];
-            cof[0] = F[4] * F[8] - F[5] * F[7];
-            cof[1] = F[5] * F[6] - F[3] * F[8];
-            cof[2] = F[3] * F[7] - F[4] * F[6];
-            cof[3] = F[2] * F[7] - F[1] * F[8];
-            cof[4] = F[0] * F[8] - F[2] * F[6];
-            cof[5] = F[1] * F[6] - F[0] * F[7];
-            cof[6] = F[1] * F[5] - F[2] * F[4];
-            cof[7] = F[2] * F[3] - F[0] * F[5];
-            cof[8] = F[0] * F[4] - F[1] * F[3];
-            for (int i = 0; i < 9; ++i) Finv_T[i] = cof[i] / Jd;
-            for (int i = 0; i < 9; ++i) P[i] = mu * (F[i] - Finv_T[i]) + lam * lnJ * Finv_T[i];
-            double gg = 0.0;
-            for (int i = 0; i < 9; ++i) gg += G[i] * G[i];
-            // tr F^T F - 3 = 2 tr G + |G|^2
-            psi = 0.5 * mu * (2.0 * trG + gg) - mu * lnJ + 0.5 * lam * lnJ * lnJ;
+            // J - 1 = tr G + (principal 2x2 minors of G) + det G
+            const double trG = G[0] + G[4] + G[8];
+            const double m2 = G[0] * G[4] - G[1] * G[3] + G[0] * G[8] - G[2] * G[6] + G[4] * G[8] - G[5] * G[7];
+            const double detG = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                                G[2] * (G[3] * G[7] - G[4] * G[6]);
+            const double Jm1 = trG + m2 + detG;
+            const double Jd = 1.0 + Jm1;
+            if (!(Jd > 0.0)) {
+                bad = 1;
+                for (int i = 0; i < 9; ++i) P[i] = 0.0;
+            } else {
+                lnJ = log1p(Jm1);
+                // F^{-T} = cof(F) / J
+                double cof[9];
+                cof[0] = F[4] * F[8] - F[5] * F[7];
+                cof[1] = F[5] * F[6] - F[3] * F[8];
+                cof[2] = F[3] * F[7] - F[4] * F[6];
+                cof[3] = F[2] * F[7] - F[1] * F[8];
+                cof[4] = F[0] * F[8] - F[2] * F[6];
+                cof[5] = F[1] * F[6] - F[0] * F[7];
+                cof[6] = F[1] * F[5] - F[2] * F[4];
+                cof[7] = F[2] * F[3] - F[0] * F[5];
+                cof[8] = F[0] * F[4] - F[1] * F[3];
+                for (int i = 0; i < 9; ++i) Finv_T[i] = cof[i] / Jd;
+                for (int i = 0; i < 9; ++i) P[i] = mu * (F[i] - Finv_T[i]) + lam * lnJ * Finv_T[i];
+                double gg = 0.0;
+                for (int i = 0; i < 9; ++i) gg += G[i] * G[i];
+                // tr F^T F - 3 = 2 tr G + |G|^2
+                psi = 0.5 * mu * (2.0 * trG + gg) - mu * lnJ + 0.5 * lam * lnJ * lnJ;
+            }
         }
+        for (int i = 0; i < 9; ++i) {
+            sF[warp][i] = (float)F[i]; sS[warp][i] = (float)Sst[i];
+            sFiT[warp][i] = (float)Finv_T[i]; sP[warp][i] = (float)P[i];
+        }
+        sLnJ[warp] = (float)lnJ;
+        sBad[warp] = bad;
+        A.energy[slot] = bad ? 0.0 : (double)wgt * V * psi;
     }
+    __syncwarp();
+    const bool bad = sBad[warp] != 0;
+    float F[9], Sst[9], Finv_T[9], P[9], Bm[9];
+    for (int i = 0; i < 9; ++i) {
+        F[i] = sF[warp][i]; Sst[i] = sS[warp][i]; Finv_T[i] = sFiT[warp][i]; P[i] = sP[warp][i];
+        Bm[i] = Bmf[i];
+    }
+    const float lnJ = sLnJ[warp];
+    const float V = Vf;
+    const float mu = A.mu, lam = A.lam;
     if (bad) {
-        if (lane == 0) {
-            if (A.eval_flag) atomicExch(A.eval_flag, 1);
-            A.energy[slot] = 0.0;
-        }
+        if (lane == 0 && A.eval_flag) atomicExch(A.eval_flag, 1);
         for (int e = lane; e < r + nsym; e += 32) part[e] = 0.f;
         if (lane < 12) { A.fe_w[slot * 12 + lane] = 0.f; A.fe_dof[slot * 12 + lane] = 0; }
         return;
@@ -183,18 +203,17 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     // nodal forces: H = V P Bm^T, f(node c+1, d) = H[d][c], f(node 0) = -sum
     if (lane < 12) {
         int node = lane / 3, d = lane % 3;
-        double f = 0.0;
+        float f = 0.f;
         for (int c = 0; c < 3; ++c) {
-            double Hdc = 0.0;
-            for (int k = 0; k < 3; ++k) Hdc += P[d * 3 + k] * Bm[c * 3 + k];
+            float Hdc = 0.f;
+            for (int kk = 0; kk < 3; ++kk) Hdc += P[d * 3 + kk] * Bm[c * 3 + kk];
             Hdc *= V;
             if (node == 0) f -= Hdc;
             else if (c == node - 1) f = Hdc;
         }
-        A.fe_w[slot * 12 + lane] = (float)(wgt * f);
+        A.fe_w[slot * 12 + lane] = wgt * f;
         A.fe_dof[slot * 12 + lane] = 3 * v[node] + d;
     }
-    if (lane == 0) A.energy[slot] = (double)wgt * V * psi;
     // directional quantities per column j
     float g_j = 0.f;
     if (lane < r) {
@@ -313,7 +332,20 @@ __global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
         const int t = s - A.nsplit_dense;
         const int per = (A.n_pairs + A.nsplit_pairs - 1) / A.nsplit_pairs;
         const int p0 = t * per, p1 = min(A.n_pairs, p0 + per);
-        for (int p = p0; p < p1; ++p) {
+        int p = p0;
+        for (; p + 4 <= p1; p += 4) {
+            float4 w[4];
+            float av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int n = A.fe_dof[p + u];
+                av[u] = (float)(A.dt2 * A.fe_w[p + u]);
+                w[u] = __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fma4(acc, w[u], av[u]);
+        }
+        for (; p < p1; ++p) {
             const int n = A.fe_dof[p];
             const float av = (float)(A.dt2 * A.fe_w[p]);
             fma4(acc, __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4)), av);
@@ -353,7 +385,7 @@ __global__ void k_xy(const float* X, int ld, int K, int r, const float* zvec, do
 
 void launch_xy(cudaStream_t s, const float* X, int ld, int K, int r, const float* zvec, double h,
                float* xy, const NewtonState* ns) {
-    k_xy<<<(K + 255) / 256, 256, 0, s>>>(X, ld, K, r, zvec, h, xy, ns);
+    k_xy<<<(K + 63) / 64, 64, 0, s>>>(X, ld, K, r, zvec, h, xy, ns);
 }
 
 // out[i][k] = m[i] * W[i][k] for i < rows, k < ld (set-up of G).
@@ -525,7 +557,7 @@ __global__ void k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32, __nv_bfloat
 
 void launch_bwd_prep_tc(cudaStream_t s, const BwdArgs& a, int Cb, int ld, float* g32,
                         __nv_bfloat16* gh, __nv_bfloat16* gl, int out_f32, int out_bf16) {
-    k_bwd_prep_tc<<<(ld + 255) / 256, 256, 0, s>>>(a, Cb, ld, g32, gh, gl, out_f32, out_bf16);
+    k_bwd_prep_tc<<<(ld + 63) / 64, 64, 0, s>>>(a, Cb, ld, g32, gh, gl, out_f32, out_bf16);
 }
 
 // WT[c][r] = W[r][c] for r < rows, c < cols (zero elsewhere in WT's padding is kept)

@@ -149,6 +149,59 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (split == 1) {
             if (wok) row_epilogue(A, n, vrow);
+            if (A.mode == 1 && A.row_part) {
+                // fused output-row reductions over this tile's 128 rows (the same sums
+                // as k_row_reduce):  y_n = sum_j J_nj z_j + H[D,D]_n,
+                // a_n = m_n y_n - dt^2 f_ext,n;  J^T a, J^T M J (upper), J^T M dJ
+                const int r = A.r, N = A.n_out;
+                const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
+                (void)ih2;
+                float* ms = tile + (size_t)128 * TS;
+                float* as = ms + 128;
+                float m = 0.f, av = 0.f;
+                if (wok && n < N) {
+                    m = A.mdof[n];
+                    // this row's J and dJ in physical units (in place: the outputs are written)
+                    for (int j = 0; j < r; ++j) {
+                        vrow[kShared + 3 * j] *= ih;
+                        vrow[kShared + 3 * j + 2] *= ih3;
+                    }
+                    float y = vrow[3] * ih2;
+                    for (int j = 0; j < r; ++j) y = fmaf(vrow[kShared + 3 * j], A.zvec[j], y);
+                    av = (float)((double)m * y - A.dt * A.dt * (A.f_ext ? (double)A.f_ext[n] : 0.0));
+                    if (A.a_out) A.a_out[n] = av;
+                } else if (!wok) {
+                    for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
+                } else {
+                    // rows past N hold zeros of the padded weights; keep them out of the sums
+                    for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
+                }
+                ms[row] = m;
+                as[row] = av;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                const int nsym = r * (r + 1) / 2;
+                const int n_ent = r + nsym + r * r;
+                float* out = A.row_part + (size_t)blockIdx.x * A.row_stride;
+                for (int e = row; e < n_ent; e += 128) {
+                    float acc = 0.f;
+                    if (e < r) {
+                        const int ci = kShared + 3 * e;
+                        for (int k = 0; k < 128; ++k) acc = fmaf(tile[k * TS + ci], as[k], acc);
+                    } else if (e < r + nsym) {
+                        int p = e - r, i = 0;
+                        while (p >= r - i) { p -= r - i; ++i; }
+                        const int ci = kShared + 3 * i, cj = kShared + 3 * (i + p);
+                        for (int k = 0; k < 128; ++k)
+                            acc = fmaf(ms[k] * tile[k * TS + ci], tile[k * TS + cj], acc);
+                    } else {
+                        const int q = e - r - nsym, i = q / r, jj = q % r;
+                        const int ci = kShared + 3 * i, cj = kShared + 3 * jj + 2;
+                        for (int k = 0; k < 128; ++k)
+                            acc = fmaf(ms[k] * tile[k * TS + ci], tile[k * TS + cj], acc);
+                    }
+                    out[e] = acc;
+                }
+            }
         } else {
             // write this split's partial tile [tile][split][c][128 rows]; the last CTA of the
             // tile (atomic count, no waiting) sums the partials in split order and finishes
