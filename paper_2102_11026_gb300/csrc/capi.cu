@@ -414,6 +414,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         ChainLaunch cl;
         cl.jobs = w.fwd_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
         cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+        cl.split_cnt = w.split_cnt;
         Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
         if (!launch_chain(s, cl, d->prec))
             return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -620,6 +621,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
             ChainLaunch cl;
             cl.jobs = w.rev_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cb; cl.grid = ctx->sm_count;
             cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+            cl.split_cnt = w.split_cnt;
             Phase p(ctx, DAE_PHASE_BWD, 1);
             if (!launch_chain(s, cl, d->prec))
                 return fail(ctx, DAE_ERR_CUDA, "reverse layer-chain launch failed");

@@ -270,7 +270,7 @@ struct ChainJob {
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
     const ChainJob* jobs; int n_jobs; int Cp; int grid;
-    GridBar* gb; const NewtonState* ns; int* status; float* split_part;
+    GridBar* gb; const NewtonState* ns; int* status; float* split_part; int* split_cnt;
 };
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
 int chain_split(int tiles, int nk, int grid);

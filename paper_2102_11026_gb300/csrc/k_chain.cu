@@ -59,7 +59,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 template <int NC, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_chain(const ChainJob* __restrict__ jobs, int n_jobs, GridBar* gb, const NewtonState* ns,
-            int* status, float* split_part, int stages) {
+            int* status, float* split_part, int* split_cnt, int stages) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull, tempty;
     __shared__ uint32_t tmem_base;
     __shared__ int fail;
+    __shared__ int is_last;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~(uintptr_t)1023);
     float* tile = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
@@ -115,6 +116,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap* tmBlo = &Jb.tm[3];
         if (warp == 0) {
             if (lane == 0 && !fail) {
+                if ((int)blockIdx.x < items) {
+                    prefetch_tmap(tmA);
+                    prefetch_tmap(tmB);
+                    if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
+                }
                 for (int item = blockIdx.x; item < items && !fail; item += G) {
                     const int tl = item / split, ks = item % split;
                     const int kb0 = (int)((long long)nk * ks / split);
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int tl = item / split, ks = item % split;
                 const bool ok = mbar_wait(&tfull, it & 1);
                 tc_fence_after();
-                const bool wok = __all_sync(0xffffffffu, ok);
+                const bool wok = epi_all(ok);
                 if (wok) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
@@ -192,9 +198,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (split == 1) {
                     row_epilogue(Jb.a, tl * 128 + row, vrow);
                 } else {
+                    // K-split partial tile; the last CTA to finish this tile (atomic count,
+                    // no waiting) sums the partials in split order and runs the epilogue
                     float* part = split_part + ((size_t)tl * split + ks) * CP * 128;
 #pragma unroll 8
                     for (int c = 0; c < CP; ++c) part[(size_t)c * 128 + row] = vrow[c];
+                    __threadfence();
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (warp == 2 && lane == 0) {
+                        const int old = atomicAdd(split_cnt + tl, 1);
+                        is_last = (old == split - 1);
+                        if (is_last) split_cnt[tl] = 0;
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (is_last) {
+                        __threadfence();
+                        const float* tp = split_part + (size_t)tl * split * CP * 128 + row;
+                        for (int c0 = 0; c0 < CP; c0 += 8) {
+                            float acc[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+                            for (int s = 0; s < split; ++s) {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i)
+                                    acc[i] += __ldcg(tp + ((size_t)s * CP + c0 + i) * 128);
+                            }
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) vrow[c0 + i] = acc[i];
+                        }
+                        row_epilogue(Jb.a, tl * 128 + row, vrow);
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");   // is_last reused next item
                 }
             }
             fence_proxy_async_global();       // epilogue stores feed the next layer's TMA
@@ -203,33 +237,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (threadIdx.x == 0 && !grid_barrier(gb, G, gen)) fail = 1;
         __syncthreads();
         if (fail) break;
-        if (split > 1) {
-            if (warp >= 2) {
-                const int row = 32 * (warp & 3) + lane;
-                float* vrow = tile + (size_t)row * TS;
-                for (int tl = blockIdx.x; tl < tiles; tl += G) {
-                    const float* tp = split_part + (size_t)tl * split * CP * 128 + row;
-                    for (int c0 = 0; c0 < CP; c0 += 8) {
-                        float acc[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-                        for (int s = 0; s < split; ++s) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                acc[i] += __ldcg(tp + ((size_t)s * CP + c0 + i) * 128);
-                        }
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) vrow[c0 + i] = acc[i];
-                    }
-                    row_epilogue(Jb.a, tl * 128 + row, vrow);
-                }
-                fence_proxy_async_global();
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && !grid_barrier(gb, G, gen)) fail = 1;
-            __syncthreads();
-            if (fail) break;
-        }
     }
     // drain: nothing in flight may outlive the CTA
     if (warp == 0 && lane == 0) {
@@ -273,7 +280,7 @@ bool launch_chain_inst(cudaStream_t s, const ChainLaunch& c) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_chain<NC, PREC>, c.jobs, c.n_jobs, c.gb, c.ns, c.status,
-                              c.split_part, stages) == cudaSuccess;
+                              c.split_part, c.split_cnt, stages) == cudaSuccess;
 }
 
 template <int PREC>

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         constexpr int TS = CP + 1;
         float* tile = reinterpret_cast<float*>(smem);
         float* vrow = tile + (size_t)row * TS;
-        const bool wok = __all_sync(0xffffffffu, ok);
+        const bool wok = epi_all(ok);
         if (wok) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
