@@ -411,7 +411,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     const bool chain = d->ws.chain_ok;
     if (chain) {
         // hidden layers: one persistent cooperative launch for the whole chain
-        ChainLaunch cl;
+        ChainLaunch cl = {};
         cl.jobs = w.fwd_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
         cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
         cl.split_cnt = w.split_cnt;
@@ -618,7 +618,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
             launch_bwd_prep_tc(s, ba, w.Cb, d->layers[L - 2].ldT, w.G32[0], w.Gh[0], w.Gl[0], of32, ob);
         }
         if (w.chain_ok) {
-            ChainLaunch cl;
+            ChainLaunch cl = {};
             cl.jobs = w.rev_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cb; cl.grid = ctx->sm_count;
             cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
             cl.split_cnt = w.split_cnt;

@@ -26,7 +26,7 @@ constexpr int kMaxStages = 8;
 constexpr int kThreads = 192;
 
 template <int NC, int PREC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
              FwdArgs A, int nk, int stages, int split) {
@@ -180,26 +180,60 @@ __global__ void __launch_bounds__(kThreads, 1)
                 as[row] = av;
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 const int nsym = r * (r + 1) / 2;
-                const int n_ent = r + nsym + r * r;
                 float* out = A.row_part + (size_t)blockIdx.x * A.row_stride;
-                for (int e = row; e < n_ent; e += 128) {
-                    float acc = 0.f;
-                    if (e < r) {
-                        const int ci = kShared + 3 * e;
-                        for (int k = 0; k < 128; ++k) acc = fmaf(tile[k * TS + ci], as[k], acc);
-                    } else if (e < r + nsym) {
-                        int p = e - r, i = 0;
-                        while (p >= r - i) { p -= r - i; ++i; }
-                        const int ci = kShared + 3 * i, cj = kShared + 3 * (i + p);
-                        for (int k = 0; k < 128; ++k)
-                            acc = fmaf(ms[k] * tile[k * TS + ci], tile[k * TS + cj], acc);
-                    } else {
-                        const int q = e - r - nsym, i = q / r, jj = q % r;
-                        const int ci = kShared + 3 * i, cj = kShared + 3 * jj + 2;
-                        for (int k = 0; k < 128; ++k)
-                            acc = fmaf(ms[k] * tile[k * TS + ci], tile[k * TS + cj], acc);
+                // 4x4 register blocks: threads 0-63 own blocks of J^T M J, 64-127 of
+                // J^T M dJ; threads with bj == 0 of the first half also form J^T a
+                const int mat = row >> 6, blk = row & 63, bi = blk >> 3, bj = blk & 7;
+                int ci[4], cj[4];
+                bool vi[4], vj[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * bi + q, j = 4 * bj + q;
+                    vi[q] = i < r;
+                    vj[q] = j < r;
+                    ci[q] = kShared + 3 * (vi[q] ? i : 0);
+                    cj[q] = kShared + 3 * (vj[q] ? j : 0) + (mat ? 2 : 0);
+                }
+                float acc[4][4], accp[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    accp[p] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+                }
+                const bool do_phi = (mat == 0 && bj == 0);
+                for (int k = 0; k < 128; ++k) {
+                    const float* tk = tile + k * TS;
+                    const float mk = ms[k], ak = as[k];
+                    float Ji[4], Xj[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { Ji[q] = tk[ci[q]]; Xj[q] = tk[cj[q]]; }
+                    if (do_phi) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) accp[p] = fmaf(Ji[p], ak, accp[p]);
                     }
-                    out[e] = acc;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float mJ = mk * Ji[p];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(mJ, Xj[q], acc[p][q]);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int i = 4 * bi + p;
+                    if (!vi[p]) continue;
+                    if (do_phi) out[i] = accp[p];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = 4 * bj + q;
+                        if (!vj[q]) continue;
+                        if (mat == 0) {
+                            if (i <= j) out[r + i * r - i * (i - 1) / 2 + (j - i)] = acc[p][q];
+                        } else {
+                            out[r + nsym + i * r + j] = acc[p][q];
+                        }
+                    }
                 }
             }
         } else {
@@ -241,15 +275,20 @@ bool launch_inst(cudaStream_t s, const FwdArgs& a, int split) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
-    int stages = (int)((200 * 1024) / STAGE);
+    // the output layer streams many tiles: two CTAs per SM (about 110 KB each) so one
+    // CTA's epilogue overlaps the other's loads; single-tile layers take deep pipelines
+    const size_t budget = (a.mode == 1) ? 110 * 1024 : 200 * 1024;
+    int stages = (int)(budget / STAGE);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
+    const size_t tile_need = (size_t)128 * (CP + 1) * 4 + 256 * 4;
+    while ((size_t)stages * STAGE < tile_need) ++stages;
     const size_t smem = (size_t)stages * STAGE + 1024;
-    static bool configured = false;
-    if (!configured) {
+    static size_t configured = 0;
+    if (smem > configured) {
         if (cudaFuncSetAttribute(k_fwd_tc<NC, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+                                 (int)std::max(smem, (size_t)200 * 1024 + 1024)) != cudaSuccess)
             return false;
-        configured = true;
+        configured = std::max(smem, (size_t)200 * 1024 + 1024);
     }
     const int KB = (PREC == DAE_TF32) ? 32 : 64;
     const int nk = a.ld / KB;
