@@ -150,6 +150,34 @@ def algorithmic_flops(wl):
     return 2.0 * (sum(P) * (3 * r + 4) + sum(P[:-1]) * (1 + r) + P[-1])
 
 
+def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
+    """The config block shared by both arms of the benchmark."""
+    d = wl.dec
+    cfg = {"workload": ("paper-scale decoder r=30, 30-128-256-512-1024-2048-2048-2048-"
+                        "4096-4096-60000 tanh, 20x20x50 grid (88445 tets), Neo-Hookean, "
+                        "500 cubature tets, gravity, dt=1/60, <=5 Newton updates/frame")
+           if args.workload == "paper" else "small decoder r=5 5-64-256-1024-3000",
+           "step": "one implicit-Euler frame", "frames": K,
+           "l2": "inputs larger than L2 (decoder weights %.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    if evals_all is not None:
+        cfg["evaluations"] = int(evals_all)
+        cfg["algorithmic_gflop_per_evaluation"] = flops / 1e9
+        cfg["derivative_pass_tflops"] = flops * evals_all / (ms / 1e3) / 1e12
+    return cfg
+
+
+def reduce_over_ranks(ms, evals, device):
+    """Max of the timed region and sum of the evaluations over all ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 # ---------------------------------------------------------------- oracle --
 def oracle_sample(wl, budget_s):
     """Time the FP64 oracle on a bounded sample of one Newton evaluation and scale.
@@ -202,8 +230,7 @@ def run_reference(args):
         "unit": "iterations/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%s decoder + tet grid, one Newton evaluation" % args.workload,
-                   "oracle": "FP64 hyper-dual CPU oracle"},
+        "config": workload_config(args, wl, args.steps),
         "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": T, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
@@ -288,13 +315,7 @@ def run_ours(args):
         evals2 = max(1, sum(rp.evals for rp in reps2))
     evals = sum(rp.evals for rp in reps)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(evals)], device="cuda", dtype=torch.float64)
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        te = t[1:].clone()
-        dist.all_reduce(te, op=dist.ReduceOp.SUM)
-        ms, evals_all = float(tm.item()), float(te.item())
+        ms, evals_all = reduce_over_ranks(ms, evals, "cuda")
     else:
         evals_all = evals
     value = evals_all / (ms / 1e3)
@@ -355,16 +376,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": ("paper-scale decoder r=30, 30-128-256-512-1024-2048-2048-2048-"
-                                "4096-4096-60000 tanh, 20x20x50 grid (88445 tets), Neo-Hookean, "
-                                "500 cubature tets, gravity, dt=1/60, <=5 Newton updates/frame")
-                   if args.workload == "paper" else "small decoder r=5 5-64-256-1024-3000",
-                   "step": "one implicit-Euler frame", "frames": K,
-                   "evaluations": int(evals_all), "l2": "inputs larger than L2 (decoder weights "
-                   "%.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "algorithmic_gflop_per_evaluation": flops / 1e9,
-                   "derivative_pass_tflops": flops * evals_all / (ms / 1e3) / 1e12},
+        "config": workload_config(args, wl, K, evals_all, flops, ms, world),
         "newton": {"evals_per_frame": evals / K, "iters_per_frame": sum(rp.iters for rp in reps) / K,
                    "converged_frames": sum(rp.converged for rp in reps),
                    "phi_norm0_first": reps[0].phi_norm0, "phi_norm_first": reps[0].phi_norm,

@@ -261,7 +261,7 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
-    dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.gbar); dfree(w.chain_part);
+    dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part);
     dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
@@ -385,6 +385,7 @@ dae_status build_chains(dae_decoder* d) {
     if (!w.fwd_jobs) {
         CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * (L - 1)));
         CU(ctx, cudaMalloc(&w.rev_jobs, sizeof(ChainJob) * (L - 1)));
+        CU(ctx, cudaMalloc(&w.out_job, sizeof(ChainJob)));
         TRY(dmalloc(ctx, &w.gbar, 1));
     }
     dfree(w.chain_part);
@@ -419,7 +420,36 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         if (!launch_chain(s, cl, d->prec))
             return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    for (int l = chain ? L - 1 : 0; l < L; ++l) {
+    if (chain) {
+        // output layer: a one-job persistent launch, its epilogue (outputs and the fused
+        // row reductions) overlapping the next tile's loads and MMAs
+        ChainJob job;
+        memset(&job, 0, sizeof job);
+        const Layer& ly = d->layers[L - 1];
+        memcpy(job.tm, ly.tm, sizeof job.tm);
+        fill_fwd_args(d, L - 1, job.a);
+        job.a.inv_h = 1.0 / h; job.a.inv_h2 = 1.0 / (h * h); job.a.inv_h3 = 1.0 / (h * h * h);
+        job.a.inv_dt2 = 1.0 / (dt * dt);
+        job.a.u = o.u; job.a.J = o.J; job.a.dJ = o.dJ; job.a.HDD = o.HDD; job.a.Hqq = o.Hqq;
+        if (o.row_part) {
+            job.a.row_part = o.row_part; job.a.row_stride = o.row_stride;
+            job.a.mdof = o.mdof; job.a.f_ext = o.f_ext; job.a.zvec = w.zvec; job.a.dt = dt;
+            job.a.a_out = o.a_out;
+        }
+        job.tiles = ly.m_pad / 128;
+        job.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
+        job.split = 1;
+        ctx->launches += 1;
+        launch_store_job(s, w.out_job, job);
+        ChainLaunch cl = {};
+        cl.jobs = w.out_job; cl.n_jobs = 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
+        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+        cl.split_cnt = w.split_cnt;
+        Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
+        if (!launch_chain(s, cl, d->prec))
+            return fail(ctx, DAE_ERR_CUDA, "output-layer launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    for (int l = chain ? L : 0; l < L; ++l) {
         FwdArgs a;
         fill_fwd_args(d, l, a);
         a.ns = ns;

@@ -124,6 +124,7 @@ struct Workspace {
     // persistent layer-chain jobs (tensor-core precisions)
     ChainJob* fwd_jobs = nullptr;  // hidden forward layers 0..L-2 (device)
     ChainJob* rev_jobs = nullptr;  // reverse layers L-2..0 (device)
+    ChainJob* out_job = nullptr;   // output layer, rewritten per call (device)
     GridBar* gbar = nullptr;
     float* chain_part = nullptr;   // split-K partial tiles of the chains
     bool chain_ok = false;
@@ -273,6 +274,7 @@ struct ChainLaunch {
     GridBar* gb; const NewtonState* ns; int* status; float* split_part; int* split_cnt;
 };
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
+void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);
 int chain_split(int tiles, int nk, int grid);
 constexpr int kMaxSplit = 16;
 int tc_split(int m_pad, int ld, dae_prec prec, int sm_count);

@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!wok) break;
                 if (split == 1) {
                     row_epilogue(Jb.a, tl * 128 + row, vrow);
+                    if (Jb.a.mode == 1 && Jb.a.row_part)
+                        fused_row_reduce(Jb.a, tile, TS, row, tl * 128 + row, true, tl);
                 } else {
                     // K-split partial tile; the last CTA to finish this tile (atomic count,
                     // no waiting) sums the partials in split order and runs the epilogue
@@ -257,7 +259,7 @@ bool launch_chain_inst(cudaStream_t s, const ChainLaunch& c) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
-    const size_t tile_bytes = (size_t)128 * (CP + 1) * 4;
+    const size_t tile_bytes = (size_t)128 * (CP + 1) * 4 + 256 * 4;
     const size_t budget = 220 * 1024 - tile_bytes - 1024;
     int stages = (int)(budget / STAGE);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
@@ -298,6 +300,18 @@ bool launch_chain_prec(cudaStream_t s, const ChainLaunch& c) {
 }
 
 }  // namespace
+
+// Writes one job into device memory (stream-ordered; the job travels as a kernel
+// parameter, so the caller's copy may change right after the launch).
+__global__ void k_store_job(ChainJob* dst, ChainJob job) {
+    const int n = sizeof(ChainJob) / sizeof(int);
+    const int* src = reinterpret_cast<const int*>(&job);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) reinterpret_cast<int*>(dst)[i] = src[i];
+}
+
+void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job) {
+    k_store_job<<<1, 128, 0, s>>>(dst, job);
+}
 
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec) {
     switch (prec) {

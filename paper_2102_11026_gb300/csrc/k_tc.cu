@@ -26,7 +26,7 @@ constexpr int kMaxStages = 8;
 constexpr int kThreads = 192;
 
 template <int NC, int PREC>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     k_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
              FwdArgs A, int nk, int stages, int split) {
@@ -149,93 +149,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         if (split == 1) {
             if (wok) row_epilogue(A, n, vrow);
-            if (A.mode == 1 && A.row_part) {
-                // fused output-row reductions over this tile's 128 rows (the same sums
-                // as k_row_reduce):  y_n = sum_j J_nj z_j + H[D,D]_n,
-                // a_n = m_n y_n - dt^2 f_ext,n;  J^T a, J^T M J (upper), J^T M dJ
-                const int r = A.r, N = A.n_out;
-                const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
-                (void)ih2;
-                float* ms = tile + (size_t)128 * TS;
-                float* as = ms + 128;
-                float m = 0.f, av = 0.f;
-                if (wok && n < N) {
-                    m = A.mdof[n];
-                    // this row's J and dJ in physical units (in place: the outputs are written)
-                    for (int j = 0; j < r; ++j) {
-                        vrow[kShared + 3 * j] *= ih;
-                        vrow[kShared + 3 * j + 2] *= ih3;
-                    }
-                    float y = vrow[3] * ih2;
-                    for (int j = 0; j < r; ++j) y = fmaf(vrow[kShared + 3 * j], A.zvec[j], y);
-                    av = (float)((double)m * y - A.dt * A.dt * (A.f_ext ? (double)A.f_ext[n] : 0.0));
-                    if (A.a_out) A.a_out[n] = av;
-                } else if (!wok) {
-                    for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
-                } else {
-                    // rows past N hold zeros of the padded weights; keep them out of the sums
-                    for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
-                }
-                ms[row] = m;
-                as[row] = av;
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                const int nsym = r * (r + 1) / 2;
-                float* out = A.row_part + (size_t)blockIdx.x * A.row_stride;
-                // 4x4 register blocks: threads 0-63 own blocks of J^T M J, 64-127 of
-                // J^T M dJ; threads with bj == 0 of the first half also form J^T a
-                const int mat = row >> 6, blk = row & 63, bi = blk >> 3, bj = blk & 7;
-                int ci[4], cj[4];
-                bool vi[4], vj[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int i = 4 * bi + q, j = 4 * bj + q;
-                    vi[q] = i < r;
-                    vj[q] = j < r;
-                    ci[q] = kShared + 3 * (vi[q] ? i : 0);
-                    cj[q] = kShared + 3 * (vj[q] ? j : 0) + (mat ? 2 : 0);
-                }
-                float acc[4][4], accp[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    accp[p] = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
-                }
-                const bool do_phi = (mat == 0 && bj == 0);
-                for (int k = 0; k < 128; ++k) {
-                    const float* tk = tile + k * TS;
-                    const float mk = ms[k], ak = as[k];
-                    float Ji[4], Xj[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) { Ji[q] = tk[ci[q]]; Xj[q] = tk[cj[q]]; }
-                    if (do_phi) {
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) accp[p] = fmaf(Ji[p], ak, accp[p]);
-                    }
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const float mJ = mk * Ji[p];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(mJ, Xj[q], acc[p][q]);
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int i = 4 * bi + p;
-                    if (!vi[p]) continue;
-                    if (do_phi) out[i] = accp[p];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * bj + q;
-                        if (!vj[q]) continue;
-                        if (mat == 0) {
-                            if (i <= j) out[r + i * r - i * (i - 1) / 2 + (j - i)] = acc[p][q];
-                        } else {
-                            out[r + nsym + i * r + j] = acc[p][q];
-                        }
-                    }
-                }
-            }
+            if (A.mode == 1 && A.row_part) fused_row_reduce(A, tile, TS, row, n, wok, blockIdx.x);
         } else {
             // write this split's partial tile [tile][split][c][128 rows]; the last CTA of the
             // tile (atomic count, no waiting) sums the partials in split order and finishes
@@ -277,7 +191,7 @@ bool launch_inst(cudaStream_t s, const FwdArgs& a, int split) {
     constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
     // the output layer streams many tiles: two CTAs per SM (about 110 KB each) so one
     // CTA's epilogue overlaps the other's loads; single-tile layers take deep pipelines
-    const size_t budget = (a.mode == 1) ? 110 * 1024 : 200 * 1024;
+    const size_t budget = 200 * 1024;
     int stages = (int)(budget / STAGE);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
     const size_t tile_need = (size_t)128 * (CP + 1) * 4 + 256 * 4;

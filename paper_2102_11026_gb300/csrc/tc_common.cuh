@@ -262,5 +262,102 @@ static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const 
     for (int cc = C; cc < CP; ++cc) o.put((size_t)cc * ldy + n, 0.f);
 }
 
+
+// Output-row reductions fused into the output layer's epilogue, over one tile's
+// 128 rows held in shared memory (row stride TS):  y_n = sum_j J_nj z_j + H[D,D]_n,
+// a_n = m_n y_n - dt^2 f_ext,n;  partials [J^T a | J^T M J (upper) | J^T M dJ] of
+// tile `tl` go to A.row_part (the layout of k_row_reduce).  All 128 epilogue
+// threads call this together (named barrier 1); `tile` needs 128*TS + 256 floats.
+static __device__ __noinline__ void fused_row_reduce(const FwdArgs& A, float* tile, int TS,
+                                                     int row, int n, bool wok, int tl) {
+    const int r = A.r, N = A.n_out, CP = A.Cp;
+    const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
+    const float* __restrict__ mdof = A.mdof;
+    const float* __restrict__ zvec = A.zvec;
+    const float* __restrict__ f_ext = A.f_ext;
+    float* __restrict__ a_out = A.a_out;
+    float* __restrict__ out = A.row_part + (size_t)tl * A.row_stride;
+    const double dt2 = A.dt * A.dt;
+    float* vrow = tile + (size_t)row * TS;
+    float* ms = tile + (size_t)128 * TS;
+    float* as = ms + 128;
+    float m = 0.f, av = 0.f;
+    if (wok && n < N) {
+        m = mdof[n];
+        // this row's J and dJ in physical units (in place: the outputs are written)
+        float y = vrow[3] * ih2;
+        for (int j = 0; j < r; ++j) {
+            const float Jv = vrow[kShared + 3 * j] * ih;
+            vrow[kShared + 3 * j] = Jv;
+            vrow[kShared + 3 * j + 2] *= ih3;
+            y = fmaf(Jv, zvec[j], y);
+        }
+        av = (float)((double)m * y - dt2 * (f_ext ? (double)f_ext[n] : 0.0));
+        if (a_out) a_out[n] = av;
+    } else {
+        // failed tile, or rows past N (zero rows of the padded weights): no contribution
+        for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
+    }
+    ms[row] = m;
+    as[row] = av;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const int nsym = r * (r + 1) / 2;
+    // 4x4 register blocks: threads 0-63 own blocks of J^T M J, 64-127 of J^T M dJ;
+    // threads with bj == 0 of the first half also form J^T a
+    const int mat = row >> 6, blk = row & 63, bi = blk >> 3, bj = blk & 7;
+    int ci[4], cj[4];
+    bool vi[4], vj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = 4 * bi + q, j = 4 * bj + q;
+        vi[q] = i < r;
+        vj[q] = j < r;
+        ci[q] = kShared + 3 * (vi[q] ? i : 0);
+        cj[q] = kShared + 3 * (vj[q] ? j : 0) + (mat ? 2 : 0);
+    }
+    float acc[4][4], accp[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        accp[p] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+    }
+    const bool do_phi = (mat == 0 && bj == 0);
+    for (int k = 0; k < 128; ++k) {
+        const float* tk = tile + k * TS;
+        const float mk = ms[k], ak = as[k];
+        float Ji[4], Xj[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { Ji[q] = tk[ci[q]]; Xj[q] = tk[cj[q]]; }
+        if (do_phi) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) accp[p] = fmaf(Ji[p], ak, accp[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const float mJ = mk * Ji[p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(mJ, Xj[q], acc[p][q]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = 4 * bi + p;
+        if (!vi[p]) continue;
+        if (do_phi) out[i] = accp[p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * bj + q;
+            if (!vj[q]) continue;
+            if (mat == 0) {
+                if (i <= j) out[r + i * r - i * (i - 1) / 2 + (j - i)] = acc[p][q];
+            } else {
+                out[r + nsym + i * r + j] = acc[p][q];
+            }
+        }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");   // the tile is reused afterwards
+}
+
 }  // namespace tc
 }  // namespace dae
