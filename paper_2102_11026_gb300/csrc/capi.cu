@@ -209,7 +209,7 @@ dae_status alloc_workspace(dae_decoder* d) {
     TRY(dmalloc(ctx, &w.row_part, (size_t)w.n_row_blocks * w.row_stride));
     // reverse-pass partials: the largest of the W_L^T a splits and the hidden splits
     const int K = d->widths[L - 1];
-    size_t need = (size_t)(128 + 64 + 1) * K;   // dense + pair + f_ext splits
+    size_t need = (size_t)(128 + kMaxPairSplits + 1) * K;   // dense + pair + f_ext splits
     for (int l = L - 2; l >= 0; --l) {
         int n_o = d->widths[l + 1], n_i = d->widths[l];
         need = std::max(need, (size_t)bwd_split(n_i, n_o, sm) * (1 + r) * n_i);
@@ -624,7 +624,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.a = w.a;
     }
     wa.nsplit_dense = std::max(1, std::min(128, std::min((wa.N + 63) / 64, (4 * sm + kb - 1) / kb)));
-    wa.nsplit_pairs = std::max(1, std::min(64, (wa.n_pairs + 95) / 96));
+    wa.nsplit_pairs = std::max(1, std::min(kMaxPairSplits, (wa.n_pairs + 15) / 16));
     wa.part = w.bwd_part[0]; wa.ns = ns;
     {
         Phase p(ctx, DAE_PHASE_WTA, gram ? 2 : 1);

@@ -30,6 +30,7 @@ __host__ __device__ inline int pad_cols(int r) { return (n_cols(r) + 15) / 16 * 
 constexpr int kMaxR = 32;
 constexpr int kRowTile = 128;     // output rows per tile (tcgen05 M, SIMT uses 64)
 constexpr int kKPad = 64;         // K padding (128 bytes of BF16)
+constexpr int kMaxPairSplits = 512;   // cubature-row splits of the W_L^T a GEMV
 
 enum SeedMode { SEED_FULL = 0, SEED_SDD = 1, SEED_HW = 2 };
 

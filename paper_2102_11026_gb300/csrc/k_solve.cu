@@ -45,53 +45,74 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
 }
 
 // Solve A x = b (r <= 32, A column-major in global memory) with LU and partial
-// pivoting, one warp.  Returns 0, or DAE_ERR_SINGULAR.
-__device__ int warp_lu_solve(const double* A, const double* b, double* x, int r,
-                             double (*M)[kMaxR + 1], double* rhs) {
-    const int lane = threadIdx.x & 31;
-    double amax = 0.0;
-    for (int i = 0; i < r; ++i) {
-        if (lane < r) {
-            M[i][lane] = A[i + lane * r];
-            amax = fmax(amax, fabs(M[i][lane]));
-        }
+// pivoting, all threads of the block (FP64 throughput is low on this part, so the
+// trailing updates are spread over the block and each pivot costs one reciprocal).
+// Returns 0, or DAE_ERR_SINGULAR (uniform over the block).
+__device__ int block_lu_solve(const double* A, const double* b, double* x, int r,
+                              double (*M)[kMaxR + 1], double* rhs) {
+    __shared__ double amax_s, piv_inv;
+    __shared__ int piv_row, sing;
+    __shared__ double dinv[kMaxR];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int lane = t & 31, warp = t >> 5;
+    for (int e = t; e < r * r; e += nt) {
+        const int i = e % r, j = e / r;
+        M[i][j] = A[e];
     }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane < r) rhs[lane] = b[lane];
-    __syncwarp();
-    int sing = 0;
+    for (int i = t; i < r; i += nt) rhs[i] = b[i];
+    if (t == 0) sing = 0;
+    __syncthreads();
+    if (warp == 0) {
+        double am = 0.0;
+        for (int e = lane; e < r * r; e += 32) am = fmax(am, fabs(M[e % r][e / r]));
+        for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+        if (lane == 0) amax_s = am;
+    }
+    __syncthreads();
     for (int k = 0; k < r; ++k) {
-        double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
-        int p = lane;
-        for (int o = 16; o > 0; o >>= 1) {
-            double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            int p2 = __shfl_xor_sync(0xffffffffu, p, o);
-            if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+        if (warp == 0) {
+            double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
+            int p = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+                if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+            }
+            if (lane == 0) {
+                piv_row = p;
+                if (!(v > 1e-14 * amax_s) || !isfinite(v)) sing = 1;
+            }
         }
-        if (!(v > 1e-14 * amax) || !isfinite(v)) { sing = 1; break; }
+        __syncthreads();
+        if (sing) return DAE_ERR_SINGULAR;
+        const int p = piv_row;
         if (p != k) {
-            if (lane < r) { double t = M[k][lane]; M[k][lane] = M[p][lane]; M[p][lane] = t; }
-            if (lane == 0) { double t = rhs[k]; rhs[k] = rhs[p]; rhs[p] = t; }
+            for (int j = t; j < r; j += nt) {
+                const double tmp = M[k][j]; M[k][j] = M[p][j]; M[p][j] = tmp;
+            }
+            if (t == 0) { const double tmp = rhs[k]; rhs[k] = rhs[p]; rhs[p] = tmp; }
         }
-        __syncwarp();
-        const double piv = M[k][k];
-        if (lane > k && lane < r) {
-            const double l = M[lane][k] / piv;
-            for (int j = k + 1; j < r; ++j) M[lane][j] -= l * M[k][j];
-            rhs[lane] -= l * rhs[k];
-            M[lane][k] = 0.0;
+        __syncthreads();
+        if (t == 0) piv_inv = 1.0 / M[k][k];
+        __syncthreads();
+        const int m = r - k - 1;
+        for (int i = k + 1 + t; i < r; i += nt) M[i][k] *= piv_inv;
+        __syncthreads();
+        for (int e = t; e < m * m; e += nt) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            M[i][j] = fma(-M[i][k], M[k][j], M[i][j]);
         }
-        __syncwarp();
+        for (int i = k + 1 + t; i < r; i += nt) rhs[i] = fma(-M[i][k], rhs[k], rhs[i]);
+        __syncthreads();
     }
-    if (sing) return DAE_ERR_SINGULAR;
-    if (lane == 0) {
-        for (int i = r - 1; i >= 0; --i) {
-            double s = rhs[i];
-            for (int j = i + 1; j < r; ++j) s -= M[i][j] * x[j];
-            x[i] = s / M[i][i];
-        }
+    for (int i = t; i < r; i += nt) dinv[i] = 1.0 / M[i][i];
+    __syncthreads();
+    for (int i = r - 1; i >= 0; --i) {
+        if (t == 0) x[i] = rhs[i] * dinv[i];
+        __syncthreads();
+        for (int j = t; j < i; j += nt) rhs[j] = fma(-M[j][i], x[i], rhs[j]);
+        __syncthreads();
     }
-    __syncwarp();
     return 0;
 }
 
@@ -179,7 +200,6 @@ __global__ void k_control(CtlArgs C) {
         }
         return;
     }
-    if (t >= 32) return;
     if (t == 0) {
         S.evals += 1;
         double merit = 0.0;
@@ -213,13 +233,13 @@ __global__ void k_control(CtlArgs C) {
         if (dec != 3 && dec != 2 && S.evals >= C.max_evals) dec = 3;
         decision = dec;
     }
-    __syncwarp();
+    __syncthreads();
     const int dec = decision;
     if (dec == 1) {
-        for (int i = t; i < r; i += 32) rhs[i] = -sphi[i];
-        __syncwarp();
-        const int st = warp_lu_solve(A, rhs, x, r, M, rhs);
-        __syncwarp();
+        for (int i = t; i < r; i += blockDim.x) rhs[i] = -sphi[i];
+        __syncthreads();
+        const int st = block_lu_solve(A, rhs, x, r, M, rhs);
+        __syncthreads();
         if (t == 0) {
             if (st) {
                 S.status = st;
@@ -229,9 +249,8 @@ __global__ void k_control(CtlArgs C) {
                 S.halvings = 0;
             }
         }
-        __syncwarp();
         if (!st)
-            for (int i = t; i < r; i += 32) {
+            for (int i = t; i < r; i += blockDim.x) {
                 S.delta[i] = x[i];
                 S.q_trial[i] = S.q_acc[i] + x[i];
             }
@@ -240,19 +259,20 @@ __global__ void k_control(CtlArgs C) {
             S.alpha *= 0.5;
             S.halvings += 1;
         }
-        __syncwarp();
-        for (int i = t; i < r; i += 32) S.q_trial[i] = S.q_acc[i] + S.alpha * S.delta[i];
+        __syncthreads();
+        for (int i = t; i < r; i += blockDim.x) S.q_trial[i] = S.q_acc[i] + S.alpha * S.delta[i];
     } else if (t == 0) {
         S.done = 1;
     }
+    __syncthreads();
     if (t == 0) {
         if (C.eval_flag) *C.eval_flag = 0;
         if (C.kcount) atomicAdd(C.kcount, (unsigned long long)C.kpe);
         if (C.use_cond) cudaGraphSetConditional(C.hcond, S.done ? 0u : 1u);
     }
-    __syncwarp();
     const int nw = sizeof(NewtonState) / sizeof(int);
-    for (int i = t; i < nw; i += 32) reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
+    for (int i = t; i < nw; i += blockDim.x)
+        reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
 }
 
 void launch_assemble(cudaStream_t s, const AsmArgs& a) {
