@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper", choices=["paper", "small"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -283,6 +283,12 @@ dae_status dae_profile_enable(dae_ctx* ctx, unsigned mask);
 /* Synchronize, then return per phase the summed device time (ms) and the number of
  * recorded phase instances since the previous read (arrays of DAE_N_PHASES). */
 dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count);
+/* Self-test of the device-side bounded waits: launches a kernel whose mbarrier wait
+ * and grid-barrier spin can never complete (nothing arrives) and checks that both
+ * give up after their limit (2 s each) instead of hanging.  Synchronizes; the
+ * context stays usable.  Returns DAE_OK when both waits gave up, DAE_ERR_TIMEOUT if
+ * one did not report it. */
+dae_status dae_selftest_bounded_waits(dae_ctx* ctx);
 /* Number of kernels enqueued on ctx since it was created. */
 long long dae_launch_count(const dae_ctx* ctx);
 

@@ -1490,6 +1490,29 @@ dae_status dae_profile_read(dae_ctx* ctx, double* ms, long long* count) {
     return DAE_OK;
 }
 
+dae_status dae_selftest_bounded_waits(dae_ctx* ctx) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    CU(ctx, cudaSetDevice(ctx->device));
+    GridBar* gb = nullptr;
+    int* out = nullptr;
+    const int nb = 2;
+    TRY(dmalloc(ctx, &gb, 1));
+    TRY(dmalloc(ctx, &out, nb));
+    ctx->launches += 1;
+    if (run_wait_selftest(ctx->stream, gb, out, nb)) {
+        dfree(gb); dfree(out);
+        return fail(ctx, DAE_ERR_CUDA, "self-test launch failed");
+    }
+    int h[nb] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(gb); dfree(out);
+    if (e != cudaSuccess) return fail(ctx, DAE_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+    for (int i = 0; i < nb; ++i)
+        if (h[i] != 1) return fail(ctx, DAE_ERR_TIMEOUT, "a bounded wait did not give up as expected");
+    return DAE_OK;
+}
+
 long long dae_launch_count(const dae_ctx* ctx) {
     if (!ctx) return -1;
     unsigned long long k = 0;

@@ -276,6 +276,7 @@ struct ChainLaunch {
 };
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);
+int run_wait_selftest(cudaStream_t s, GridBar* gb, int* out, int nblocks);
 int chain_split(int tiles, int nk, int grid);
 constexpr int kMaxSplit = 16;
 int tc_split(int m_pad, int ld, dae_prec prec, int sm_count);

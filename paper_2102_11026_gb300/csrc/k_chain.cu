@@ -301,6 +301,29 @@ bool launch_chain_prec(cudaStream_t s, const ChainLaunch& c) {
 
 }  // namespace
 
+// Self-test of the bounded waits: an mbarrier that nothing arrives on and a grid
+// barrier that expects one CTA more than the grid has.  Both must give up within
+// their limit; out[b] = 1 when CTA b saw both time out.
+__global__ void k_wait_selftest(GridBar* gb, int* out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool mb = mbar_wait(&bar, 0);               // no arrival: must time out
+        unsigned gen = *(volatile unsigned*)&gb->gen;
+        const bool gbok = grid_barrier(gb, gridDim.x + 1, gen);   // one CTA short: times out
+        out[blockIdx.x] = (!mb && !gbok) ? 1 : 0;
+    }
+}
+
+int run_wait_selftest(cudaStream_t s, GridBar* gb, int* out, int nblocks) {
+    k_wait_selftest<<<nblocks, 32, 0, s>>>(gb, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 // Writes one job into device memory (stream-ordered; the job travels as a kernel
 // parameter, so the caller's copy may change right after the launch).
 __global__ void k_store_job(ChainJob* dst, ChainJob job) {

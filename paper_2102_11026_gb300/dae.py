@@ -73,6 +73,7 @@ SIGNATURES = {
     "dae_profile_enable": ([_vp, ctypes.c_uint], _i),
     "dae_profile_read": ([_vp, _vp, _vp], _i),
     "dae_launch_count": ([_vp], ctypes.c_longlong),
+    "dae_selftest_bounded_waits": ([_vp], _i),
     "dae_rollout": ([_vp, _vp, _vp, _i, _vp, _vp, _i, _vp, _vp, _d, _vp,
                      ctypes.POINTER(dae_newton_opts), _vp, ctypes.POINTER(dae_newton_report)], _i),
 }
@@ -275,6 +276,10 @@ def dae_profile_read(ctx):
     cnt = np.zeros(len(PHASES), np.int64)
     _check(ctx, lib().dae_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data))
     return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def dae_selftest_bounded_waits(ctx):
+    _check(ctx, lib().dae_selftest_bounded_waits(ctx))
 
 
 def dae_launch_count(ctx):
