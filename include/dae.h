@@ -74,7 +74,7 @@ typedef enum { DAE_ACT_TANH = 0, DAE_ACT_SIN = 1, DAE_ACT_LINEAR = 2 } dae_act;
 
 /* Arithmetic of the decoder GEMMs (accumulation is always FP32):
  *   FP32    CUDA-core FFMA tiles
- *   TF32    tcgen05 kind::tf32 tensor cores
+ *   TF32    tcgen05 kind::tf32 tensor cores (operands rounded to the nearest TF32)
  *   BF16    tcgen05 kind::f16 with BF16 operands
  *   BF16X3  three BF16 products (hi*hi + hi*lo + lo*hi) per split operand pair */
 typedef enum { DAE_FP32 = 0, DAE_TF32 = 1, DAE_BF16 = 2, DAE_BF16X3 = 3 } dae_prec;
@@ -91,13 +91,17 @@ typedef struct {
     double tol;          /* stop when |phi| <= tol * max(1, |phi_0|)  (1e-8) */
     double c_armijo;     /* |phi(alpha)|^2 <= (1 - 2 c alpha) |phi|^2  (1e-4) */
     double h_cs;         /* complex-step size; a power of two keeps the scaling exact (2^-20) */
+    double max_step;     /* first trial step of an update capped at |alpha delta|_inf <= max_step
+                            (0.5, in latent units; 0 = no cap) */
+    double xtol;         /* also stop when the next Newton step is negligible:
+                            |delta|_inf <= xtol * max(1, |q|_inf)  (1e-6; 0 = off) */
 } dae_newton_opts;
 
 /* Per-frame outcome of dae_newton_step / dae_rollout. */
 typedef struct {
     int iters;           /* accepted Newton updates */
     int evals;           /* full evaluations (derivatives + cubature + assembly) */
-    int converged;       /* 1 if |phi| reached tol */
+    int converged;       /* 1 if |phi| reached tol or the next step fell below xtol */
     int status;          /* dae_status of the frame (device-side errors included) */
     double phi_norm0;    /* |phi| at the first iterate */
     double phi_norm;     /* |phi| at the returned iterate */

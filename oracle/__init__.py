@@ -345,12 +345,15 @@ def phi_only(wl, q, qbar=None, qbar_dot=None, dt=None, cub_w=None):
 
 
 def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvings=8,
-                 cub_w=None, qbar=None, qbar_dot=None, dt=None):
+                 cub_w=None, qbar=None, qbar_dot=None, dt=None, max_step=0.5, xtol=1e-6):
     """Implicit-Euler Newton iteration on phi(q) = 0 (Eq. 7) with A from Eq. 11.
 
     Each iteration solves A delta = -phi (LU, partial pivoting) and backtracks
-    on |phi|^2 (Armijo).  Stops when |phi| <= tol * max(1, |phi_0|).
-    Returns (q, report dict).
+    on |phi|^2 (Armijo), starting from the step length alpha = min(1,
+    max_step / |delta|_inf) (no cap when max_step is 0).  Stops when
+    |phi| <= tol * max(1, |phi_0|), or when the next step is negligible,
+    |delta|_inf <= xtol * max(1, |q|_inf) (q is then the solution; xtol = 0 turns
+    this test off).  Returns (q, report dict).
     """
     st = wl.state
     qbar = st.qbar if qbar is None else qbar
@@ -367,7 +370,11 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
     while not converged and it < max_iter:
         delta = np.linalg.solve(rs["A"], -rs["phi"])
         m0 = float(rs["phi"] @ rs["phi"])
-        alpha = 1.0
+        dn = float(np.max(np.abs(delta)))
+        if xtol > 0 and dn <= xtol * max(1.0, float(np.max(np.abs(q)))):
+            converged = True
+            break
+        alpha = max_step / dn if (max_step > 0 and dn > max_step) else 1.0
         for _ in range(max_halvings + 1):
             qt = q + alpha * delta
             try:

@@ -316,7 +316,8 @@ void fill_fwd_args(const dae_decoder* d, int l, FwdArgs& a) {
     a.last = (l == L - 1);
     a.mode = a.last ? 1 : 0;
     // FP32 activations feed the FP32/TF32 GEMMs and (for the output layer's input) x_y
-    a.out_f32 = (d->prec == DAE_FP32 || d->prec == DAE_TF32 || l == L - 2);
+    // (rounded to TF32 when they feed the tf32 GEMMs)
+    a.out_f32 = d->prec == DAE_TF32 ? 2 : ((d->prec == DAE_FP32 || l == L - 2) ? 1 : 0);
     a.tmaps = ly.tm_ok ? (const void*)ly.tm : nullptr;
     a.split_part = w.split_part;
     a.split_cnt = w.split_cnt;
@@ -342,7 +343,7 @@ void fill_rev_args(const dae_decoder* d, int l, FwdArgs& a) {
         a.mode = 2;
         a.Y = w.G32[nb]; a.Yh = w.Gh[nb]; a.Yl = w.Gl[nb];
         a.ldy = d->layers[l - 1].ldT;
-        a.out_f32 = (d->prec == DAE_TF32);
+        a.out_f32 = (d->prec == DAE_TF32) ? 2 : 0;
         a.out_bf16 = out_bf16_of(d->prec);
         a.S1 = w.S1[l - 1]; a.T = w.T[l - 1];
     } else {
@@ -407,7 +408,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     {
         Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
         launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0],
-                    w.Xh[0], w.Xl[0], ob, w.zvec);
+                    w.Xh[0], w.Xl[0], d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec);
     }
     const bool chain = d->ws.chain_ok;
     if (chain) {
@@ -637,7 +638,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         // complex-step reverse pass on the tensor cores: delta_l = W_l^T g_l, the epilogue
         // forms g_{l-1} (complex act' of the layer below) as the next B operand
         const int ob = out_bf16_of(d->prec);
-        const int of32 = (d->prec == DAE_TF32);
+        const int of32 = (d->prec == DAE_TF32) ? 2 : 0;
         {
             BwdArgs ba;
             memset(&ba, 0, sizeof ba);
@@ -698,9 +699,11 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     aa.red = w.red; aa.ns = ns; aa.control = P.control;
     if (P.opts) {
         aa.tol = P.opts->tol; aa.c_armijo = P.opts->c_armijo; aa.max_iter = P.opts->max_iter;
+        aa.max_step = P.opts->max_step; aa.xtol = P.opts->xtol;
         aa.max_halvings = P.opts->max_halvings; aa.max_evals = P.opts->max_evals;
     } else {
         aa.tol = 0; aa.c_armijo = 0; aa.max_iter = 0; aa.max_halvings = 0; aa.max_evals = 0;
+        aa.max_step = 0; aa.xtol = 0;
     }
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
     aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
@@ -871,7 +874,8 @@ dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_fra
     key.gram = w.G && w.G_mesh == m->id; key.prec = d->prec;
     key.max_iter = P.opts->max_iter; key.max_halvings = P.opts->max_halvings;
     key.max_evals = P.opts->max_evals; key.dt = P.dt; key.h = P.h; key.tol = P.opts->tol;
-    key.c_armijo = P.opts->c_armijo;
+    key.c_armijo = P.opts->c_armijo; key.max_step = P.opts->max_step;
+    key.xtol = P.opts->xtol;
     if (!w.graph_ok || memcmp(&key, &w.gkey, sizeof key) != 0) {
         // kernels per evaluation: count once with a dry capture so k_control can add them
         P.kpe = 0;
@@ -986,6 +990,8 @@ void dae_default_newton_opts(dae_newton_opts* o) {
     o->tol = 1e-8;
     o->c_armijo = 1e-4;
     o->h_cs = std::ldexp(1.0, -20);
+    o->max_step = 0.5;
+    o->xtol = 1e-6;
 }
 
 dae_status dae_create(dae_ctx** out, int device, void* stream) {
@@ -1099,6 +1105,13 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
             launch_split_bf16(ctx->stream, ly.W, ly.Wh, prec == DAE_BF16X3 ? ly.Wl : nullptr, n);
         }
     }
+    if (prec == DAE_TF32) {
+        for (auto& ly : d->layers) {
+            size_t n = (size_t)ly.m_pad * ly.ld;
+            if (!ly.Wr) TRY(dmalloc(ctx, &ly.Wr, n));
+            launch_round_tf32(ctx->stream, ly.W, ly.Wr, n);
+        }
+    }
     CU(ctx, cudaGetLastError());
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (prec != DAE_FP32) {
@@ -1107,7 +1120,7 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
         for (int l = 0; l < d->L; ++l) {
             Layer& ly = d->layers[l];
             const int buf = l & 1;
-            bool ok = make_tmap(&ly.tm[0], f32 ? (const void*)ly.W : (const void*)ly.Wh, f32, ly.ld,
+            bool ok = make_tmap(&ly.tm[0], f32 ? (const void*)ly.Wr : (const void*)ly.Wh, f32, ly.ld,
                                 ly.m_pad, 128);
             ok = ok && make_tmap(&ly.tm[2], f32 ? (const void*)d->ws.X[buf] : (const void*)d->ws.Xh[buf],
                                  f32, ly.ld, d->ws.Cp, d->ws.Cp);
@@ -1132,13 +1145,16 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
                 TRY(dmalloc(ctx, &ly.WT, nt));
                 launch_transpose(ctx->stream, ly.W, ly.ld, ly.n_out, ly.n_in, ly.WT, ly.ldT);
             }
-            if (prec != DAE_TF32) {
+            if (prec == DAE_TF32) {
+                if (!ly.WTr) TRY(dmalloc(ctx, &ly.WTr, nt));
+                launch_round_tf32(ctx->stream, ly.WT, ly.WTr, nt);
+            } else {
                 if (!ly.WTh) TRY(dmalloc(ctx, &ly.WTh, nt));
                 if (prec == DAE_BF16X3 && !ly.WTl) TRY(dmalloc(ctx, &ly.WTl, nt));
                 launch_split_bf16(ctx->stream, ly.WT, ly.WTh, prec == DAE_BF16X3 ? ly.WTl : nullptr, nt);
             }
             const int gb = (d->L - 2 - l) & 1;
-            bool ok = make_tmap(&ly.tmR[0], f32 ? (const void*)ly.WT : (const void*)ly.WTh, f32, ly.ldT,
+            bool ok = make_tmap(&ly.tmR[0], f32 ? (const void*)ly.WTr : (const void*)ly.WTh, f32, ly.ldT,
                                 ly.mT_pad, 128);
             ok = ok && make_tmap(&ly.tmR[2], f32 ? (const void*)d->ws.G32[gb] : (const void*)d->ws.Gh[gb],
                                  f32, ly.ldT, d->ws.Cb, d->ws.Cb);
@@ -1167,8 +1183,8 @@ dae_status dae_free_decoder(dae_decoder* d) {
     cudaSetDevice(d->ctx->device);
     cudaStreamSynchronize(d->ctx->stream);
     for (auto& ly : d->layers) {
-        dfree(ly.W); dfree(ly.b); dfree(ly.Wh); dfree(ly.Wl);
-        dfree(ly.WT); dfree(ly.WTh); dfree(ly.WTl);
+        dfree(ly.W); dfree(ly.b); dfree(ly.Wh); dfree(ly.Wl); dfree(ly.Wr);
+        dfree(ly.WT); dfree(ly.WTh); dfree(ly.WTl); dfree(ly.WTr);
     }
     free_workspace(d->ws);
     delete d;

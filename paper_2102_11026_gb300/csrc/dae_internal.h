@@ -33,6 +33,8 @@ constexpr int kKPad = 64;         // K padding (128 bytes of BF16)
 constexpr int kMaxPairSplits = 512;   // cubature-row splits of the W_L^T a GEMV
 
 enum SeedMode { SEED_FULL = 0, SEED_SDD = 1, SEED_HW = 2 };
+// activation store mode (after 0 FP32, 1 + BF16 hi, 2 + BF16 hi/lo): FP32 rounded to TF32
+constexpr int kStoreTF32 = 3;
 
 struct Layer {
     int n_in = 0, n_out = 0;
@@ -42,6 +44,7 @@ struct Layer {
     float* b = nullptr;    // [n_out]
     __nv_bfloat16* Wh = nullptr;   // BF16 hi split [m_pad][ld]
     __nv_bfloat16* Wl = nullptr;   // BF16 lo split (W - hi)
+    float* Wr = nullptr;           // W rounded to TF32 (operand of the tf32 GEMMs)
     CUtensorMap tm[4];             // TMA maps: A (W or W hi), A lo, B (input activations), B lo
     bool tm_ok = false;
     // transposed copy for the tensor-core reverse pass (hidden layers): [mT_pad][ldT]
@@ -49,6 +52,7 @@ struct Layer {
     float* WT = nullptr;
     __nv_bfloat16* WTh = nullptr;
     __nv_bfloat16* WTl = nullptr;
+    float* WTr = nullptr;          // W^T rounded to TF32
     CUtensorMap tmR[4];
     bool tmR_ok = false;
 };
@@ -91,7 +95,7 @@ struct GraphKey {
     const void* cub_w; const void* cub_tets; const void* fe_w; const void* hist; const void* traj;
     const void* fext;
     int n_cub, gram, prec, max_iter, max_halvings, max_evals;
-    double dt, h, tol, c_armijo;
+    double dt, h, tol, c_armijo, max_step, xtol;
 };
 
 // Per-decoder workspace (sized for the decoder's widths and latent size).
@@ -341,7 +345,7 @@ struct AsmArgs {
     double* red;                             // out: phi | A | energy | terms
     NewtonState* ns;                         // null: assemble only
     int control;                             // 1: Newton control step
-    double tol, c_armijo; int max_iter, max_halvings, max_evals;
+    double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
     int* eval_flag;                          // per-evaluation flag of the cubature kernel
     int* status;                             // sticky device status (assemble-only mode)
     cudaGraphConditionalHandle hcond; int use_cond;
@@ -369,5 +373,6 @@ void launch_frame_finish(cudaStream_t s, RollCtl* rc, NewtonState* ns, double* q
 bool make_tmap(void* out, const void* base, bool fp32, int ld, int rows, int box_rows);
 void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
                        size_t n);
+void launch_round_tf32(cudaStream_t s, const float* W, float* out, size_t n);
 
 }  // namespace dae

@@ -2,7 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
-#include "dae.h"
+#include "dae_internal.h"
 
 namespace dae {
 
@@ -62,8 +62,24 @@ __device__ __forceinline__ void mc_group(const ActD& D, float c, float gw, float
     oh = fmaf(D.s1, hh, fmaf(D.s2, fmaf(b, gw, 2.0f * c * dd), D.s3 * b * c * c));
 }
 
+// FP32 value rounded to the nearest TF32 value (10 explicit mantissa bits, ties away
+// from zero), returned as an FP32 bit pattern.  The tf32 tensor-core path reads the
+// low 13 mantissa bits as zero, so rounding here replaces a biased truncation.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+
+// out_bf16: 0 FP32 only, 1 FP32 + BF16 hi, 2 FP32 + BF16 hi + lo, kStoreTF32 FP32
+// rounded to TF32 (the operand of the tf32 tensor-core GEMMs).
+
 __device__ __forceinline__ void store_act(float v, float* Y, __nv_bfloat16* Yh,
                                           __nv_bfloat16* Yl, size_t idx, int out_bf16) {
+    if (out_bf16 == kStoreTF32) {
+        Y[idx] = tf32_rna(v);
+        return;
+    }
     Y[idx] = v;
     if (out_bf16) {
         __nv_bfloat16 hi = __float2bfloat16_rn(v);

@@ -198,4 +198,15 @@ void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_b
     k_split_bf16<<<1024, 256, 0, s>>>(W, hi, lo, n);
 }
 
+// ------------------------------------------------------------ TF32 copy --
+__global__ void k_round_tf32(const float* W, float* out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = tf32_rna(W[i]);
+}
+
+void launch_round_tf32(cudaStream_t s, const float* W, float* out, size_t n) {
+    k_round_tf32<<<1024, 256, 0, s>>>(W, out, n);
+}
+
 }  // namespace dae

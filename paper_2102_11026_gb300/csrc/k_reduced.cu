@@ -546,7 +546,7 @@ __global__ void k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32, __nv_bfloat
             }
         }
         const size_t idx = (size_t)c * ld + k;
-        if (out_f32) g32[idx] = v;
+        if (out_f32) g32[idx] = (out_f32 == 2) ? tf32_rna(v) : v;
         if (out_bf16) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
             gh[idx] = hi;

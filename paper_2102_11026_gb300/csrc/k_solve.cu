@@ -130,7 +130,7 @@ struct CtlArgs {
     int have_cub;
     double* red;
     NewtonState* ns; int control;
-    double tol, c_armijo; int max_iter, max_halvings, max_evals;
+    double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
     int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
     int* status;
 };
@@ -245,14 +245,27 @@ __global__ void k_control(CtlArgs C) {
                 S.status = st;
                 S.done = 1;
             } else {
-                S.alpha = 1.0;
-                S.halvings = 0;
+                double xn = 0.0, qn = 0.0;
+                for (int i = 0; i < r; ++i) {
+                    xn = fmax(xn, fabs(x[i]));
+                    qn = fmax(qn, fabs(S.q_acc[i]));
+                }
+                if (C.xtol > 0.0 && xn <= C.xtol * fmax(1.0, qn)) {
+                    // the remaining correction is negligible: q_acc is the solution
+                    S.converged = 1;
+                    S.done = 1;
+                } else {
+                    // the first trial step is capped at max_step in the max-norm
+                    S.alpha = (C.max_step > 0.0 && xn > C.max_step) ? C.max_step / xn : 1.0;
+                    S.halvings = 0;
+                }
             }
         }
-        if (!st)
+        __syncthreads();
+        if (!st && !S.done)
             for (int i = t; i < r; i += blockDim.x) {
                 S.delta[i] = x[i];
-                S.q_trial[i] = S.q_acc[i] + x[i];
+                S.q_trial[i] = S.q_acc[i] + S.alpha * x[i];
             }
     } else if (dec == 0) {
         if (t == 0) {
@@ -295,7 +308,7 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     c.rowsum = rowsum; c.cubsum = cubsum; c.bwdsum = bwdsum; c.esum = esum;
     c.have_cub = a.n_cub > 0;
     c.red = a.red; c.ns = a.ns; c.control = a.control;
-    c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_iter = a.max_iter;
+    c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_step = a.max_step; c.xtol = a.xtol; c.max_iter = a.max_iter;
     c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
     c.eval_flag = a.eval_flag; c.status = a.status;
     c.hcond = a.hcond; c.use_cond = a.use_cond; c.kcount = a.kcount; c.kpe = a.kpe;

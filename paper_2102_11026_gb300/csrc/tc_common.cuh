@@ -170,9 +170,9 @@ struct ActOut {
     float* __restrict__ Y;
     __nv_bfloat16* __restrict__ Yh;
     __nv_bfloat16* __restrict__ Yl;
-    int f32, bf16;
+    int f32, bf16;   // f32: 1 FP32, 2 FP32 rounded to TF32; bf16: 1 hi, 2 hi + lo
     __device__ __forceinline__ void put(size_t idx, float x) const {
-        if (f32) Y[idx] = x;
+        if (f32) Y[idx] = (f32 == 2) ? tf32_rna(x) : x;
         if (bf16) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(x);
             Yh[idx] = hi;

@@ -33,7 +33,8 @@ class DaeError(RuntimeError):
 class dae_newton_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("max_evals", ctypes.c_int),
                 ("max_halvings", ctypes.c_int), ("tol", ctypes.c_double),
-                ("c_armijo", ctypes.c_double), ("h_cs", ctypes.c_double)]
+                ("c_armijo", ctypes.c_double), ("h_cs", ctypes.c_double),
+                ("max_step", ctypes.c_double), ("xtol", ctypes.c_double)]
 
 
 class dae_newton_report(ctypes.Structure):

@@ -326,7 +326,7 @@ def test_newton_converges_quadratically(material):
     wl = synth.custom([3, 8, 8, 3 * 27], (3, 3, 3), 12, 3, "tanh", material, 1e3, 0.3, True)
     wl.state.dt = 1.0 / 60.0
     wl.state.qbar_dot = wl.state.qbar_dot * 20
-    q, rep = oracle.newton_solve(wl, max_iter=12, tol=1e-12)
+    q, rep = oracle.newton_solve(wl, max_iter=12, tol=1e-12, xtol=0.0)
     assert rep["converged"], rep["phi_hist"]
     h = rep["phi_hist"]
     assert np.linalg.norm(oracle.phi_only(wl, q)) <= 1e-12 * max(1, h[0])
@@ -343,3 +343,29 @@ def test_small_workload_shapes():
     assert wl.mesh.n_tet == 3645 and wl.dec.n_out == 3 * wl.mesh.n_vert
     assert len(set(wl.cub_tets.tolist())) == 64
     assert wl.cub_w.min() >= 0.5 and wl.cub_w.max() <= 2.0
+
+
+def test_newton_step_cap_and_step_tolerance():
+    """max_step caps the first trial of an update in the max-norm (the accepted
+    iterate lies on the Newton direction at distance max_step); the xtol stop ends
+    at an iterate whose remaining Newton correction is below xtol, which is that
+    close to the tightly converged solution."""
+    wl = synth.custom([3, 8, 8, 3 * 27], (3, 3, 3), 12, 3, "tanh", "stvk", 1e3, 0.3, True)
+    wl.state.qbar_dot = wl.state.qbar_dot * 20
+    q0 = synth.newton_start(wl.state)
+    rs = oracle.reduced_system(wl, q0)
+    delta = np.linalg.solve(rs["A"], -rs["phi"])
+    cap = 0.25 * np.abs(delta).max()
+    q1, rep1 = oracle.newton_solve(wl, q0=q0, max_iter=1, max_step=cap, xtol=0.0)
+    step = q1 - q0
+    assert abs(np.abs(step).max() - cap) <= 1e-12 * cap
+    assert np.allclose(step, cap * delta / np.abs(delta).max(), rtol=1e-10, atol=0)
+    # no cap: the full Newton step is taken
+    qf, _ = oracle.newton_solve(wl, q0=q0, max_iter=1, max_step=0.0, xtol=0.0)
+    assert np.allclose(qf - q0, delta, rtol=1e-10, atol=1e-14)
+    # step tolerance against the tightly converged solution
+    qt, rt = oracle.newton_solve(wl, q0=q0, max_iter=20, tol=1e-13, xtol=0.0)
+    qx, rx = oracle.newton_solve(wl, q0=q0, max_iter=20, tol=0.0, xtol=1e-6)
+    assert rt["converged"] and rx["converged"]
+    assert np.abs(qx - qt).max() <= 2e-6 * max(1.0, np.abs(qt).max())
+    assert rx["iters"] <= rt["iters"]
