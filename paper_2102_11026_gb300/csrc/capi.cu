@@ -261,7 +261,7 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
-    dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part);
+    dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part); dfree(w.chain_cnt);
     dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
@@ -359,7 +359,7 @@ dae_status build_chains(dae_decoder* d) {
     const int L = d->L, G = ctx->sm_count;
     const int KB = d->prec == DAE_TF32 ? 32 : 64;
     std::vector<ChainJob> fj(L - 1), rj(L - 1);
-    size_t part = 1;
+    size_t part = 1, cnt_f = 0, cnt_r = 0;
     for (int l = 0; l < L - 1; ++l) {
         const Layer& ly = d->layers[l];
         ChainJob& j = fj[l];
@@ -368,8 +368,10 @@ dae_status build_chains(dae_decoder* d) {
         fill_fwd_args(d, l, j.a);
         j.tiles = ly.m_pad / 128;
         j.nk = ly.ld / KB;
-        j.split = chain_split(j.tiles, j.nk, G);
-        part = std::max(part, (size_t)j.tiles * j.split * w.Cp * 128);
+        chain_plan(j, G);
+        j.cnt_off = (int)cnt_f;
+        cnt_f += j.tiles;
+        part = std::max(part, (size_t)j.tiles * j.split * (w.Cp + 1) * 128);
     }
     for (int i = 0; i < L - 1; ++i) {
         const int l = L - 2 - i;
@@ -380,8 +382,10 @@ dae_status build_chains(dae_decoder* d) {
         fill_rev_args(d, l, j.a);
         j.tiles = ly.mT_pad / 128;
         j.nk = ly.ldT / KB;
-        j.split = chain_split(j.tiles, j.nk, G);
-        part = std::max(part, (size_t)j.tiles * j.split * w.Cb * 128);
+        chain_plan(j, G);
+        j.cnt_off = (int)cnt_r;
+        cnt_r += j.tiles;
+        part = std::max(part, (size_t)j.tiles * j.split * (w.Cb + 1) * 128);
     }
     if (!w.fwd_jobs) {
         CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * (L - 1)));
@@ -391,6 +395,8 @@ dae_status build_chains(dae_decoder* d) {
     }
     dfree(w.chain_part);
     TRY(dmalloc(ctx, &w.chain_part, part));
+    dfree(w.chain_cnt);
+    TRY(dmalloc(ctx, &w.chain_cnt, std::max(cnt_f, cnt_r) + 1));
     CU(ctx, cudaMemcpy(w.fwd_jobs, fj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
     CU(ctx, cudaMemcpy(w.rev_jobs, rj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
     w.chain_ok = true;
@@ -416,7 +422,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         ChainLaunch cl = {};
         cl.jobs = w.fwd_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
         cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
-        cl.split_cnt = w.split_cnt;
+        cl.split_cnt = w.chain_cnt;
         Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
         if (!launch_chain(s, cl, d->prec))
             return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -440,12 +446,13 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         job.tiles = ly.m_pad / 128;
         job.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
         job.split = 1;
+        job.rep = 1;
         ctx->launches += 1;
         launch_store_job(s, w.out_job, job);
         ChainLaunch cl = {};
         cl.jobs = w.out_job; cl.n_jobs = 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
         cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
-        cl.split_cnt = w.split_cnt;
+        cl.split_cnt = w.chain_cnt;
         Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
         if (!launch_chain(s, cl, d->prec))
             return fail(ctx, DAE_ERR_CUDA, "output-layer launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -652,7 +659,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
             ChainLaunch cl = {};
             cl.jobs = w.rev_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cb; cl.grid = ctx->sm_count;
             cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
-            cl.split_cnt = w.split_cnt;
+            cl.split_cnt = w.chain_cnt;
             Phase p(ctx, DAE_PHASE_BWD, 1);
             if (!launch_chain(s, cl, d->prec))
                 return fail(ctx, DAE_ERR_CUDA, "reverse layer-chain launch failed");

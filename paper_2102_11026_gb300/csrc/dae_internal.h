@@ -132,6 +132,7 @@ struct Workspace {
     ChainJob* out_job = nullptr;   // output layer, rewritten per call (device)
     GridBar* gbar = nullptr;
     float* chain_part = nullptr;   // split-K partial tiles of the chains
+    unsigned long long* chain_cnt = nullptr;   // per-tile arrival counters of the chains
     bool chain_ok = false;
     float* split_part = nullptr;   // split-K partial tiles of the hidden tensor-core GEMMs
     int* split_cnt = nullptr;      // per-tile counters
@@ -268,20 +269,28 @@ void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
 
 // Persistent layer-chain kernel (k_chain.cu): one job per GEMM layer.
+// A layer of a chain is cut into tiles x P items (P = max(split, rep)): item (tile,
+// ks) covers K chunk ks of `split` (split-K; the split CTAs of a tile exchange
+// partial tiles and each finishes 128/split rows), or the whole K loop
+// replicated `rep` times (short K; each copy finishes 128/rep rows).
 struct ChainJob {
     CUtensorMap tm[4];           // A, A lo, B, B lo
-    FwdArgs a;                   // epilogue (mode 0, 2 or 3)
-    int tiles, split, nk, pad_;
+    FwdArgs a;                   // epilogue (mode 0, 1, 2 or 3)
+    int tiles, split, nk, rep;
+    int cnt_off;                 // first per-tile arrival counter of this job (split > 1)
+    int pad_[3];
 };
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
     const ChainJob* jobs; int n_jobs; int Cp; int grid;
-    GridBar* gb; const NewtonState* ns; int* status; float* split_part; int* split_cnt;
+    GridBar* gb; const NewtonState* ns; int* status; float* split_part;
+    unsigned long long* split_cnt;   // per-tile arrival counters tagged with the barrier generation
 };
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);
 int run_wait_selftest(cudaStream_t s, GridBar* gb, int* out, int nblocks);
-int chain_split(int tiles, int nk, int grid);
+// Work decomposition of one chain layer: sets job.split and job.rep.
+void chain_plan(ChainJob& job, int grid);
 constexpr int kMaxSplit = 16;
 int tc_split(int m_pad, int ld, dae_prec prec, int sm_count);
 

@@ -1,19 +1,25 @@
-// Persistent tensor-core kernel for a chain of small GEMM layers: the hidden
-// layers of the stacked complex-step forward pass (Sec. 4.3) and the hidden
-// layers of the complex-step reverse pass (Sec. 4.4).
+// Persistent tensor-core kernel for a chain of GEMM layers: the hidden layers of
+// the stacked complex-step forward pass (Sec. 4.3), the hidden layers of the
+// complex-step reverse pass (Sec. 4.4), and (as a one-job chain) the output layer.
 //
-// One CTA per SM for the whole chain (cooperative launch): barriers, TMEM and
-// the instruction stream are set up once instead of once per layer.  Each layer
-// ("job") is split into work items (128-row tile x K chunk) dealt round-robin to
-// the CTAs; a grid-wide barrier separates the layers (the next layer's TMA reads
-// the activations the previous layer's epilogue wrote).  K-split partial tiles go
-// to global scratch and are reduced, in split order, after a second barrier.
+// One CTA per SM for the whole chain (cooperative launch): barriers, TMEM and the
+// instruction stream are set up once instead of once per layer.  Each layer
+// ("job") is cut into items (128-row tile x K range) dealt round-robin to the CTAs;
+// a grid-wide barrier separates the layers (the next layer's TMA reads the
+// activations the previous layer's epilogue wrote).
 //
-// Roles as in k_tc.cu: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer,
-// warps 2-5 epilogue.  The accumulator is staged through a shared-memory tile so
-// the MMA of the next item can start while the epilogue runs.  Every wait
-// (mbarrier or grid barrier) is bounded; a wait that gives up records
-// DAE_ERR_TIMEOUT, and the CTA stops issuing work, drains and exits.
+// Short-K layers replicate the whole K loop on `rep` CTAs per tile; long-K layers
+// split K over `split` CTAs per tile, which publish their partial tiles (one bulk
+// copy each), wait for one another and sum them.  Either way each of the P CTAs of
+// a tile finishes 128/P rows, so the activation epilogue of a layer is spread over
+// tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue runs, the
+// producer prefetches the next layer's weight tiles into L2.
+//
+// Roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5 epilogue.
+// The accumulator is staged through a shared-memory tile so the MMA of the next
+// item can start while the epilogue runs.  Every wait (mbarrier, partner tiles,
+// grid barrier) is bounded; a wait that gives up records DAE_ERR_TIMEOUT, and the
+// CTA stops issuing work, drains and exits.
 #include <algorithm>
 #include "tc_common.cuh"
 
@@ -29,6 +35,12 @@ constexpr int kMaxStages = 8;
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -55,11 +67,76 @@ __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& gen) {
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16) from shared to global memory, waited for.
+__device__ __forceinline__ void bulk_store_wait(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16) from global to shared memory, completing on
+// the transaction count of `bar`.
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_l2_2d(const CUtensorMap* map, int c0, int c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1)
+                 : "memory");
+}
+
+// Arrival at the counter of a split tile for barrier generation g: the counter holds
+// (g << 8) | arrivals, so counters left by earlier layers or launches never need
+// resetting.
+__device__ __forceinline__ void split_arrive(unsigned long long* cnt, unsigned g) {
+    const unsigned long long tag = (unsigned long long)g << 8;
+    unsigned long long old = *(volatile unsigned long long*)cnt;
+    while (true) {
+        const unsigned long long want = ((old >> 8) == (unsigned long long)g) ? old + 1 : (tag | 1ull);
+        const unsigned long long prev = atomicCAS(cnt, old, want);
+        if (prev == old) break;
+        old = prev;
+    }
+}
+
+struct Item {
+    int tl, ks, kb0, kb1;
+};
+
+__device__ __forceinline__ Item item_of(int item, int P, int split, int nk) {
+    Item it;
+    it.tl = item / P;
+    it.ks = item % P;
+    if (split > 1) {
+        it.kb0 = (int)((long long)nk * it.ks / split);
+        it.kb1 = (int)((long long)nk * (it.ks + 1) / split);
+    } else {
+        it.kb0 = 0;
+        it.kb1 = nk;
+    }
+    return it;
+}
 
 template <int NC, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_chain(const ChainJob* __restrict__ jobs, int n_jobs, GridBar* gb, const NewtonState* ns,
-            int* status, float* split_part, int* split_cnt, int stages) {
+            int* status, float* split_part, unsigned long long* split_cnt, int stages) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;
@@ -69,14 +146,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t TMEM_COLS = (CP <= 32) ? 32 : (CP <= 64 ? 64 : 128);
     constexpr uint32_t ID = idesc(PREC == DAE_TF32 ? 2u : 1u, 128, CP);
     constexpr int TS = CP + 1;
+    constexpr uint32_t TILE_BYTES = 128u * TS * 4u;   // a partial tile as staged (multiple of 16)
 
     if (ns && ns->done) return;   // uniform: every CTA reads the same flag
 
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull, tempty;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull, tempty, rbar;
     __shared__ uint32_t tmem_base;
     __shared__ int fail;
-    __shared__ int is_last;
+    __shared__ unsigned s_gen;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~(uintptr_t)1023);
     float* tile = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
@@ -90,7 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(&tfull, 1);
         mbar_init(&tempty, 128);
+        mbar_init(&rbar, 1);
         fail = 0;
+        s_gen = *(volatile unsigned*)&gb->gen;
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -101,15 +181,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    unsigned gen = 0;
-    if (threadIdx.x == 0) gen = *(volatile unsigned*)&gb->gen;
+    unsigned gen = s_gen;
 
     uint32_t pk = 0;   // stage-ring position (producer and MMA walk it identically)
     uint32_t it = 0;   // items taken by this CTA (tfull / tempty phases)
+    uint32_t nred = 0; // split reductions of this CTA (rbar phases)
     for (int j = 0; j < n_jobs; ++j) {
         const ChainJob& Jb = jobs[j];
+        const unsigned jg = s_gen;   // barrier generation of this job (tags split counters)
         const int tiles = Jb.tiles, split = Jb.split, nk = Jb.nk;
-        const int items = tiles * split;
+        const int P = split > Jb.rep ? split : Jb.rep;
+        const int items = tiles * P;
         const CUtensorMap* tmA = &Jb.tm[0];
         const CUtensorMap* tmAlo = &Jb.tm[1];
         const CUtensorMap* tmB = &Jb.tm[2];
@@ -122,20 +204,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
                 }
                 for (int item = blockIdx.x; item < items && !fail; item += G) {
-                    const int tl = item / split, ks = item % split;
-                    const int kb0 = (int)((long long)nk * ks / split);
-                    const int kb1 = (int)((long long)nk * (ks + 1) / split);
-                    for (int kb = kb0; kb < kb1; ++kb, ++pk) {
+                    const Item I = item_of(item, P, split, nk);
+                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
                         if (!mbar_wait(&empty[s], ph ^ 1)) { fail = 1; break; }
                         mbar_expect_tx(&full[s], STAGE);
                         uint8_t* base = smem + (size_t)s * STAGE;
-                        tma_load_2d(base, tmA, &full[s], kb * KB, tl * 128);
+                        tma_load_2d(base, tmA, &full[s], kb * KB, I.tl * 128);
                         tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
                         if constexpr (X3) {
-                            tma_load_2d(base + A_BYTES + B_BYTES, tmAlo, &full[s], kb * KB, tl * 128);
+                            tma_load_2d(base + A_BYTES + B_BYTES, tmAlo, &full[s], kb * KB, I.tl * 128);
                             tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
+                        }
+                    }
+                }
+                // the next layer's weight tiles of this CTA's items into L2 (they do not
+                // depend on this layer's output)
+                if (j + 1 < n_jobs && !fail) {
+                    const ChainJob& Nb = jobs[j + 1];
+                    const int Pn = Nb.split > Nb.rep ? Nb.split : Nb.rep;
+                    const int items_n = Nb.tiles * Pn;
+                    for (int item = blockIdx.x; item < items_n; item += G) {
+                        const Item I = item_of(item, Pn, Nb.split, Nb.nk);
+                        for (int kb = I.kb0; kb < I.kb1; ++kb) {
+                            prefetch_l2_2d(&Nb.tm[0], kb * KB, I.tl * 128);
+                            if constexpr (X3) prefetch_l2_2d(&Nb.tm[1], kb * KB, I.tl * 128);
                         }
                     }
                 }
@@ -143,12 +237,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else if (warp == 1) {
             if (lane == 0 && !fail) {
                 for (int item = blockIdx.x; item < items && !fail; item += G, ++it) {
-                    const int ks = item % split;
-                    const int kb0 = (int)((long long)nk * ks / split);
-                    const int kb1 = (int)((long long)nk * (ks + 1) / split);
+                    const Item I = item_of(item, P, split, nk);
                     if (!mbar_wait(&tempty, (it & 1) ^ 1)) { fail = 1; break; }
                     tc_fence_after();
-                    for (int kb = kb0; kb < kb1; ++kb, ++pk) {
+                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
                         if (!mbar_wait(&full[s], ph)) { fail = 1; break; }
@@ -157,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t da = sdesc(base), db = sdesc(base + A_BYTES);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+                            const uint32_t acc = (kb > I.kb0 || k > 0) ? 1u : 0u;
                             mma<PREC>(tmem, da + 2 * k, db + 2 * k, ID, acc);
                             if constexpr (X3) {
                                 const uint64_t dal = sdesc(base + A_BYTES + B_BYTES);
@@ -172,14 +264,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         } else {
-            const int lane_base = 32 * (warp & 3);
+            const int et = threadIdx.x - 64;          // epilogue thread 0..127
+            const int lane_base = 32 * (warp & 3);    // TMEM lane quarter of this warp
             const int row = lane_base + lane;
             float* vrow = tile + (size_t)row * TS;
+            const int R = 128 / P;
             for (int item = blockIdx.x; item < items; item += G, ++it) {
-                const int tl = item / split, ks = item % split;
+                const Item I = item_of(item, P, split, nk);
+                if (et == 0 && Jb.a.mode != 1) {
+                    // this slice's epilogue inputs into L2 while the MMAs run
+                    const int n0 = I.tl * 128 + I.ks * R;
+                    const int n1 = min(n0 + R, Jb.a.n_out);
+                    const int n_out = Jb.a.n_out;
+                    if (Jb.a.mode == 2 && n0 < n1) {
+                        prefetch_line_l2(Jb.a.S1 + n0);
+                        for (int c = 0; c < Jb.a.r; ++c)
+                            for (int nn = n0; nn < n1; nn += 32)
+                                prefetch_line_l2(Jb.a.T + (size_t)c * n_out + nn);
+                    } else if (Jb.a.mode == 0 && n0 < n1) {
+                        prefetch_line_l2(Jb.a.bias + n0);
+                    }
+                }
                 const bool ok = mbar_wait(&tfull, it & 1);
                 tc_fence_after();
-                const bool wok = epi_all(ok);
+                bool wok = epi_all(ok);
                 if (wok) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
@@ -195,48 +303,80 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 mbar_arrive(&tempty);          // TMEM may be overwritten by the next item
                 if (!wok) break;
-                if (split == 1) {
-                    row_epilogue(Jb.a, tl * 128 + row, vrow);
-                    if (Jb.a.mode == 1 && Jb.a.row_part)
-                        fused_row_reduce(Jb.a, tile, TS, row, tl * 128 + row, true, tl);
-                } else {
-                    // K-split partial tile; the last CTA to finish this tile (atomic count,
-                    // no waiting) sums the partials in split order and runs the epilogue
-                    float* part = split_part + ((size_t)tl * split + ks) * CP * 128;
-#pragma unroll 8
-                    for (int c = 0; c < CP; ++c) part[(size_t)c * 128 + row] = vrow[c];
-                    __threadfence();
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (warp == 2 && lane == 0) {
-                        const int old = atomicAdd(split_cnt + tl, 1);
-                        is_last = (old == split - 1);
-                        if (is_last) split_cnt[tl] = 0;
-                    }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (is_last) {
-                        __threadfence();
-                        const float* tp = split_part + (size_t)tl * split * CP * 128 + row;
-                        for (int c0 = 0; c0 < CP; c0 += 8) {
-                            float acc[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-                            for (int s = 0; s < split; ++s) {
-#pragma unroll
-                                for (int i = 0; i < 8; ++i)
-                                    acc[i] += __ldcg(tp + ((size_t)s * CP + c0 + i) * 128);
-                            }
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) vrow[c0 + i] = acc[i];
-                        }
-                        row_epilogue(Jb.a, tl * 128 + row, vrow);
-                    }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");   // is_last reused next item
+                if (Jb.a.mode == 1) {
+                    // output layer (one row per thread, fused row reductions)
+                    row_epilogue(Jb.a, I.tl * 128 + row, vrow);
+                    if (Jb.a.row_part)
+                        fused_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl);
+                    continue;
                 }
+                if (split > 1) {
+                    // publish this K chunk's partial tile, wait for the tile's other
+                    // chunks, then sum rows [ks R, ks R + R) of all chunks in order
+                    fence_proxy_async_smem();
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    unsigned long long* cnt = split_cnt + Jb.cnt_off + I.tl;
+                    bool got = true;
+                    if (et == 0) {
+                        float* dst = split_part + ((size_t)I.tl * split + I.ks) * (TILE_BYTES / 4);
+                        bulk_store_wait(dst, tile, TILE_BYTES);
+                        fence_proxy_async_global();
+                        __threadfence();
+                        split_arrive(cnt, jg);
+                        const unsigned long long want =
+                            ((unsigned long long)jg << 8) | (unsigned long long)split;
+                        const uint64_t t0 = globaltimer();
+                        while (ld_acquire64(cnt) != want) {
+                            if (globaltimer() - t0 > kWaitNs) { got = false; break; }
+                        }
+                        __threadfence();
+                    }
+                    // the other chunks' rows [r0, r0 + R) into the idle stage buffers (every
+                    // MMA of this item has completed; a split layer gives a CTA one item)
+                    const int r0 = I.ks * R;
+                    const uint32_t slice_f = (uint32_t)R * TS;   // floats of one chunk's slice
+                    float* scratch = reinterpret_cast<float*>(smem);
+                    const float* src = split_part + (size_t)I.tl * split * (TILE_BYTES / 4) + (size_t)r0 * TS;
+                    if (et == 0 && got) {
+                        mbar_expect_tx(&rbar, (uint32_t)(split - 1) * slice_f * 4u);
+                        for (int s = 0, q = 0; s < split; ++s) {
+                            if (s == I.ks) continue;
+                            bulk_load(scratch + (size_t)q * slice_f, src + (size_t)s * (TILE_BYTES / 4),
+                                      slice_f * 4u, &rbar);
+                            ++q;
+                        }
+                    }
+                    wok = epi_all(got || et != 0);
+                    if (!wok) { fail = 1; break; }
+                    wok = epi_all(mbar_wait(&rbar, nred & 1));
+                    ++nred;
+                    if (!wok) { fail = 1; break; }
+                    // sum in chunk order (bitwise reproducible)
+                    float* own = tile + (size_t)r0 * TS;
+                    for (int e = et; e < (int)slice_f; e += 128) {
+                        float acc = 0.f;
+                        for (int s = 0, q = 0; s < split; ++s) {
+                            if (s == I.ks) {
+                                acc += own[e];
+                            } else {
+                                acc += scratch[(size_t)q * slice_f + e];
+                                ++q;
+                            }
+                        }
+                        own[e] = acc;
+                    }
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                slice_epilogue<PREC>(Jb.a, tile, TS, I.tl, I.ks * R, R, et);
+                asm volatile("bar.sync 1, 128;" ::: "memory");   // the tile is reused next item
             }
             fence_proxy_async_global();       // epilogue stores feed the next layer's TMA
         }
         __syncthreads();
-        if (threadIdx.x == 0 && !grid_barrier(gb, G, gen)) fail = 1;
+        if (threadIdx.x == 0) {
+            if (!grid_barrier(gb, G, gen)) fail = 1;
+            s_gen = gen;
+        }
         __syncthreads();
         if (fail) break;
     }
@@ -345,13 +485,22 @@ bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec) {
     }
 }
 
-// Items per job: enough K chunks that tiles x split covers the grid, at least
-// 4 k-blocks per chunk.
-int chain_split(int tiles, int nk, int grid) {
-    int split = grid / std::max(tiles, 1);
-    split = std::min(split, nk / 4);
-    split = std::min(split, kMaxSplit);
-    return split < 2 ? 1 : split;
+// Items of a layer: P = max(split, rep) CTAs per 128-row tile with tiles x P <= grid
+// and P a power of two <= 8 (each finishes 128/P rows).  K loops of at most 8
+// k-blocks are replicated (the weights are a few hundred KB, read from L2 by each
+// copy); longer ones are split, at least 4 k-blocks per chunk.
+void chain_plan(ChainJob& job, int grid) {
+    job.split = 1;
+    job.rep = 1;
+    int pmax = 1;
+    while (pmax * 2 <= 8 && job.tiles * pmax * 2 <= grid) pmax *= 2;
+    if (job.nk <= 8) {
+        job.rep = pmax;
+    } else {
+        int s = 1;
+        while (s * 2 <= pmax && job.nk / (s * 2) >= 4) s *= 2;
+        job.split = s;
+    }
 }
 
 }  // namespace dae

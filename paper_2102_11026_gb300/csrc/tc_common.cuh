@@ -263,6 +263,92 @@ static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const 
 }
 
 
+// Output store of the layer-chain epilogue: BF16 hi (and lo for the split form) by
+// precision, FP32 (rounded to TF32 for the tf32 form) when f32 is set.
+template <int PREC>
+struct SliceOut {
+    float* __restrict__ Y;
+    __nv_bfloat16* __restrict__ Yh;
+    __nv_bfloat16* __restrict__ Yl;
+    int f32;
+    __device__ __forceinline__ void put(size_t idx, float x) const {
+        if constexpr (PREC == DAE_TF32) {
+            Y[idx] = tf32_rna(x);
+        } else {
+            if (f32) Y[idx] = x;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            Yh[idx] = hi;
+            if constexpr (PREC == DAE_BF16X3) Yl[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+    }
+};
+
+// Epilogue of rows [r0, r0 + R) of tile `tl` (R divides 128) whose accumulator
+// columns sit in shared memory (row stride TS), by the 128 epilogue threads: thread
+// t takes row r0 + t % R (consecutive threads, consecutive rows: coalesced stores)
+// and every (128/R)-th column group from t / R.  Modes 0 (hidden layer,
+// multicomplex activation), 2 (reverse pass, next g) and 3 (reverse pass at the
+// network input); see row_epilogue for the arithmetic of each.
+template <int PREC>
+static __device__ __noinline__ void slice_epilogue(const FwdArgs& A, const float* __restrict__ tile,
+                                                   int TS, int tl, int r0, int R, int t) {
+    const int tpr = 128 / R, rl = t % R, sub = t / R;
+    const int n = tl * 128 + r0 + rl;
+    const float* __restrict__ v = tile + (size_t)(r0 + rl) * TS;
+    const int mode = A.mode, r = A.r, CP = A.Cp, n_out = A.n_out;
+    if (mode == 3) {
+        if (n >= n_out) return;
+        float* __restrict__ dout = A.dout;
+        for (int c = sub; c <= r; c += tpr) dout[(size_t)c * n_out + n] = v[c];
+        return;
+    }
+    const SliceOut<PREC> o{A.Y, A.Yh, A.Yl, A.out_f32};
+    const int ldy_i = A.ldy;
+    if (n >= ldy_i) return;
+    const size_t ldy = ldy_i;
+    if (n >= n_out) {
+        for (int c = sub; c < CP; c += tpr) o.put((size_t)c * ldy + n, 0.f);
+        return;
+    }
+    const float* __restrict__ T = A.T;
+    if (mode == 2) {
+        const float s1 = A.S1[n];
+        const float re = v[0];
+#pragma unroll 4
+        for (int c = sub; c < CP; c += tpr) {
+            float x = 0.f;
+            if (c == 0) x = re * s1;
+            else if (c <= r) x = fmaf(v[c], s1, re * T[(size_t)(c - 1) * n_out + n]);
+            o.put((size_t)c * ldy + n, x);
+        }
+        return;
+    }
+    // mode 0
+    const ActD D = act_d(A.act, v[0] + A.bias[n]);
+    const float c = v[1], gw = v[2];
+    if (sub == 0) {
+        float oc, ogw, og0;
+        mc_shared(D, c, gw, v[3], oc, ogw, og0);
+        o.put(n, D.s0);
+        o.put(ldy + n, oc);
+        o.put(2 * ldy + n, ogw);
+        o.put(3 * ldy + n, og0);
+        if (A.S1) A.S1[n] = D.s1;
+    }
+    float* __restrict__ Tw = A.T;
+#pragma unroll 2
+    for (int j = sub; j < r; j += tpr) {
+        const int cb = kShared + 3 * j;
+        float ob, od, oh;
+        mc_group(D, c, gw, v[cb], v[cb + 1], v[cb + 2], ob, od, oh);
+        o.put((size_t)cb * ldy + n, ob);
+        o.put((size_t)(cb + 1) * ldy + n, od);
+        o.put((size_t)(cb + 2) * ldy + n, oh);
+        if (Tw) Tw[(size_t)j * n_out + n] = D.s2 * v[cb];
+    }
+    for (int cc = n_cols(r) + sub; cc < CP; cc += tpr) o.put((size_t)cc * ldy + n, 0.f);
+}
+
 // Output-row reductions fused into the output layer's epilogue, over one tile's
 // 128 rows held in shared memory (row stride TS):  y_n = sum_j J_nj z_j + H[D,D]_n,
 // a_n = m_n y_n - dt^2 f_ext,n;  partials [J^T a | J^T M J (upper) | J^T M dJ] of
