@@ -138,6 +138,8 @@ dae_status check_device_status(dae_ctx* ctx) {
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (st != 0) {
         CU(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        // a bounded wait that gave up can leave grid-barrier and split counters mid-count
+        if (st == DAE_ERR_TIMEOUT) ctx->timeout_epoch += 1;
         return fail(ctx, (dae_status)st, "device reported %s", dae_status_string((dae_status)st));
     }
     return DAE_OK;
@@ -393,10 +395,14 @@ dae_status build_chains(dae_decoder* d) {
         CU(ctx, cudaMalloc(&w.out_job, sizeof(ChainJob)));
         TRY(dmalloc(ctx, &w.gbar, 1));
     }
+    // the output layer's stream pieces: two partial tiles per CTA, a counter per tile
+    const Layer& top = d->layers[L - 1];
+    part = std::max(part, (size_t)G * 2 * (w.Cp + 1) * 128);
     dfree(w.chain_part);
     TRY(dmalloc(ctx, &w.chain_part, part));
     dfree(w.chain_cnt);
-    TRY(dmalloc(ctx, &w.chain_cnt, std::max(cnt_f, cnt_r) + 1));
+    w.chain_cnt_n = std::max(std::max(cnt_f, cnt_r), (size_t)(top.m_pad / 128)) + 1;
+    TRY(dmalloc(ctx, &w.chain_cnt, w.chain_cnt_n));
     CU(ctx, cudaMemcpy(w.fwd_jobs, fj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
     CU(ctx, cudaMemcpy(w.rev_jobs, rj.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
     w.chain_ok = true;
@@ -447,6 +453,10 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         job.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
         job.split = 1;
         job.rep = 1;
+        // stream the output layer's tiles x nk k-blocks in equal ranges per CTA when the
+        // tiles do not divide evenly over the grid
+        job.stream = (job.tiles > ctx->sm_count) ? 1 : 0;
+        job.cnt_off = 0;
         ctx->launches += 1;
         launch_store_job(s, w.out_job, job);
         ChainLaunch cl = {};
@@ -898,6 +908,14 @@ dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_fra
 dae_status check_common(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* m) {
     if (!ctx) return DAE_ERR_INVALID_ARG;
     if (!dec || dec->ctx != ctx) return fail(ctx, DAE_ERR_INVALID_ARG, "decoder missing or from another context");
+    if (dec->ws.sync_epoch != ctx->timeout_epoch) {
+        // zero the layer-chain synchronisation state after a timed-out launch
+        Workspace& w = const_cast<dae_decoder*>(dec)->ws;
+        CU(ctx, cudaSetDevice(ctx->device));
+        if (w.gbar) CU(ctx, cudaMemsetAsync(w.gbar, 0, sizeof(GridBar), ctx->stream));
+        if (w.chain_cnt) CU(ctx, cudaMemsetAsync(w.chain_cnt, 0, w.chain_cnt_n * sizeof(unsigned), ctx->stream));
+        w.sync_epoch = ctx->timeout_epoch;
+    }
     if (m) {
         if (m->ctx != ctx) return fail(ctx, DAE_ERR_INVALID_ARG, "mesh from another context");
         if (3 * m->n_vert != dec->N)

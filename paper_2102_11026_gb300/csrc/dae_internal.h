@@ -132,7 +132,9 @@ struct Workspace {
     ChainJob* out_job = nullptr;   // output layer, rewritten per call (device)
     GridBar* gbar = nullptr;
     float* chain_part = nullptr;   // split-K partial tiles of the chains
-    unsigned long long* chain_cnt = nullptr;   // per-tile arrival counters of the chains
+    unsigned* chain_cnt = nullptr;  // per-tile arrival counters of the chains (zero between launches)
+    size_t chain_cnt_n = 0;
+    unsigned long long sync_epoch = 0;   // ctx->timeout_epoch when gbar / chain_cnt were last valid
     bool chain_ok = false;
     float* split_part = nullptr;   // split-K partial tiles of the hidden tensor-core GEMMs
     int* split_cnt = nullptr;      // per-tile counters
@@ -195,6 +197,7 @@ struct dae_ctx {
     int sm_count = 0;
     void* cublas = nullptr;          // cublasHandle_t (set-up GEMMs only)
     dae::NewtonState* last_ns = nullptr;   // state of the most recent newton step
+    unsigned long long timeout_epoch = 0;  // bumped when the device reports DAE_ERR_TIMEOUT
     // instrumentation
     unsigned prof_on = 0;          // bit mask of instrumented phases
     long long launches = 0;             // kernels enqueued explicitly
@@ -277,14 +280,16 @@ struct ChainJob {
     CUtensorMap tm[4];           // A, A lo, B, B lo
     FwdArgs a;                   // epilogue (mode 0, 1, 2 or 3)
     int tiles, split, nk, rep;
-    int cnt_off;                 // first per-tile arrival counter of this job (split > 1)
-    int pad_[3];
+    int cnt_off;                 // first per-tile arrival counter of this job (split > 1);
+                                 // the chain zeroes a layer's counters once past it
+    int stream;                  // 1: equal k-block ranges per CTA (output layer, mode 1)
+    int pad_[2];
 };
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
     const ChainJob* jobs; int n_jobs; int Cp; int grid;
     GridBar* gb; const NewtonState* ns; int* status; float* split_part;
-    unsigned long long* split_cnt;   // per-tile arrival counters tagged with the barrier generation
+    unsigned* split_cnt;   // per-tile arrival counters of split layers (zero between launches)
 };
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);

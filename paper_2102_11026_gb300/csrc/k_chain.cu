@@ -38,11 +38,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // Sense-reversing grid barrier, thread 0 of each CTA; false on timeout.
 __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& gen) {
@@ -101,19 +96,6 @@ __device__ __forceinline__ void prefetch_l2_2d(const CUtensorMap* map, int c0, i
                  : "memory");
 }
 
-// Arrival at the counter of a split tile for barrier generation g: the counter holds
-// (g << 8) | arrivals, so counters left by earlier layers or launches never need
-// resetting.
-__device__ __forceinline__ void split_arrive(unsigned long long* cnt, unsigned g) {
-    const unsigned long long tag = (unsigned long long)g << 8;
-    unsigned long long old = *(volatile unsigned long long*)cnt;
-    while (true) {
-        const unsigned long long want = ((old >> 8) == (unsigned long long)g) ? old + 1 : (tag | 1ull);
-        const unsigned long long prev = atomicCAS(cnt, old, want);
-        if (prev == old) break;
-        old = prev;
-    }
-}
 
 struct Item {
     int tl, ks, kb0, kb1;
@@ -133,17 +115,92 @@ __device__ __forceinline__ Item item_of(int item, int P, int split, int nk) {
     return it;
 }
 
+// The items of one job for CTA c.  Split / replicated jobs: items (tile, ks) dealt
+// round-robin.  Stream jobs: the CTA takes the contiguous range [c T / G, (c+1) T / G)
+// of the job's T = tiles x nk k-blocks, so every CTA streams the same number of
+// k-blocks.  The range is cut at tile edges into a head piece (end of a tile begun by
+// the previous CTA), a tail piece (start of a tile the next CTA ends) and whole
+// tiles, taken as head, one whole tile, tail, the other whole tiles: both pieces of a
+// cut tile are streamed early by their CTAs, so the CTA that finishes the tile does
+// so early, the pieces' epilogues overlap whole-tile MMAs, and every CTA ends on
+// whole tiles.
+struct Walk {
+    int P, split, nk, items, stream, G;
+    long long T, g0, g1, hb, tb, cur;
+    int item, stage;
+    __device__ Walk(const ChainJob& J, int c, int G_) {
+        split = J.split;
+        P = split > J.rep ? split : J.rep;
+        nk = J.nk;
+        items = J.tiles * P;
+        stream = J.stream;
+        G = G_;
+        T = (long long)J.tiles * nk;
+        g0 = T * c / G;
+        g1 = T * (c + 1) / G;
+        hb = (g0 + nk - 1) / nk * nk;   // first tile edge at or after g0
+        tb = g1 / nk * nk;              // last tile edge at or before g1
+        cur = hb;
+        stage = 0;
+        item = c;
+    }
+    __device__ void seg(Item& I, long long a, long long b) const {
+        I.tl = (int)(a / nk);
+        I.ks = 0;
+        I.kb0 = (int)(a - (long long)I.tl * nk);
+        I.kb1 = I.kb0 + (int)(b - a);
+    }
+    __device__ bool next(Item& I) {
+        if (stream) {
+            if (g0 >= g1) return false;
+            if (hb > g1) {                       // the range lies inside one tile
+                if (stage++ > 0) return false;
+                seg(I, g0, g1);
+                return true;
+            }
+            if (stage == 0) {                    // head piece
+                stage = 1;
+                if (g0 < hb) { seg(I, g0, hb); return true; }
+            }
+            if (stage == 1) {                    // first whole tile
+                stage = 2;
+                if (cur < tb) { seg(I, cur, cur + nk); cur += nk; return true; }
+            }
+            if (stage == 2) {                    // tail piece
+                stage = 3;
+                if (tb < g1 && tb >= hb) { seg(I, tb, g1); return true; }
+            }
+            if (cur < tb) {                      // other whole tiles
+                seg(I, cur, cur + nk);
+                cur += nk;
+                return true;
+            }
+            return false;
+        }
+        if (item >= items) return false;
+        I = item_of(item, P, split, nk);
+        item += G;
+        return true;
+    }
+};
+
+// CTA of a stream job whose k-block range holds global k-block g.
+__device__ __forceinline__ int stream_cta(long long g, long long T, int G) {
+    return (int)(((g + 1) * G + T - 1) / T) - 1;
+}
+
 template <int NC, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_chain(const ChainJob* __restrict__ jobs, int n_jobs, GridBar* gb, const NewtonState* ns,
-            int* status, float* split_part, unsigned long long* split_cnt, int stages) {
+            int* status, float* split_part, unsigned* split_cnt, int stages) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;
     constexpr uint32_t A_BYTES = 128 * 128;
     constexpr uint32_t B_BYTES = CP * 128;
     constexpr uint32_t STAGE = (A_BYTES + B_BYTES) * (X3 ? 2 : 1);
-    constexpr uint32_t TMEM_COLS = (CP <= 32) ? 32 : (CP <= 64 ? 64 : 128);
+    constexpr uint32_t ACC_COLS = (CP <= 32) ? 32 : (CP <= 64 ? 64 : 128);
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // two accumulators: MMA runs one item ahead
     constexpr uint32_t ID = idesc(PREC == DAE_TF32 ? 2u : 1u, 128, CP);
     constexpr int TS = CP + 1;
     constexpr uint32_t TILE_BYTES = 128u * TS * 4u;   // a partial tile as staged (multiple of 16)
@@ -151,10 +208,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (ns && ns->done) return;   // uniform: every CTA reads the same flag
 
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull, tempty, rbar;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2], rbar;
     __shared__ uint32_t tmem_base;
     __shared__ int fail;
-    __shared__ unsigned s_gen;
+    __shared__ int s_last;
+    __shared__ float s_z[kMaxR];   // z of the fused row reductions (output layer)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~(uintptr_t)1023);
     float* tile = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
@@ -166,11 +224,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&tfull, 1);
-        mbar_init(&tempty, 128);
+        mbar_init(&tfull[0], 1);
+        mbar_init(&tfull[1], 1);
+        mbar_init(&tempty[0], 128);
+        mbar_init(&tempty[1], 128);
         mbar_init(&rbar, 1);
         fail = 0;
-        s_gen = *(volatile unsigned*)&gb->gen;
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -181,14 +240,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    unsigned gen = s_gen;
+    unsigned gen = 0;   // grid-barrier generation (thread 0)
+    if (threadIdx.x == 0) gen = *(volatile unsigned*)&gb->gen;
 
     uint32_t pk = 0;   // stage-ring position (producer and MMA walk it identically)
-    uint32_t it = 0;   // items taken by this CTA (tfull / tempty phases)
+    uint32_t it = 0;   // items taken by this CTA: accumulator it & 1, its use it >> 1
     uint32_t nred = 0; // split reductions of this CTA (rbar phases)
     for (int j = 0; j < n_jobs; ++j) {
         const ChainJob& Jb = jobs[j];
-        const unsigned jg = s_gen;   // barrier generation of this job (tags split counters)
+        if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+            // the previous layer's split counters are no longer read: zero them for the
+            // next launch (counters of one launch are disjoint per layer)
+            const ChainJob& Pb = jobs[j - 1];
+            if (Pb.split > 1)
+                for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
+        }
         const int tiles = Jb.tiles, split = Jb.split, nk = Jb.nk;
         const int P = split > Jb.rep ? split : Jb.rep;
         const int items = tiles * P;
@@ -203,8 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     prefetch_tmap(tmB);
                     if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
                 }
-                for (int item = blockIdx.x; item < items && !fail; item += G) {
-                    const Item I = item_of(item, P, split, nk);
+                Walk W(Jb, blockIdx.x, G);
+                Item I;
+                while (!fail && W.next(I)) {
                     for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
@@ -223,10 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // depend on this layer's output)
                 if (j + 1 < n_jobs && !fail) {
                     const ChainJob& Nb = jobs[j + 1];
-                    const int Pn = Nb.split > Nb.rep ? Nb.split : Nb.rep;
-                    const int items_n = Nb.tiles * Pn;
-                    for (int item = blockIdx.x; item < items_n; item += G) {
-                        const Item I = item_of(item, Pn, Nb.split, Nb.nk);
+                    Walk Wn(Nb, blockIdx.x, G);
+                    while (Wn.next(I)) {
                         for (int kb = I.kb0; kb < I.kb1; ++kb) {
                             prefetch_l2_2d(&Nb.tm[0], kb * KB, I.tl * 128);
                             if constexpr (X3) prefetch_l2_2d(&Nb.tm[1], kb * KB, I.tl * 128);
@@ -236,9 +301,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp == 1) {
             if (lane == 0 && !fail) {
-                for (int item = blockIdx.x; item < items && !fail; item += G, ++it) {
-                    const Item I = item_of(item, P, split, nk);
-                    if (!mbar_wait(&tempty, (it & 1) ^ 1)) { fail = 1; break; }
+                Walk W(Jb, blockIdx.x, G);
+                Item I;
+                for (; !fail && W.next(I); ++it) {
+                    const uint32_t ab = it & 1, au = (it >> 1) & 1;
+                    const uint32_t dacc = tmem + ab * ACC_COLS;
+                    if (!mbar_wait(&tempty[ab], au ^ 1)) { fail = 1; break; }
                     tc_fence_after();
                     for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
@@ -250,17 +318,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const uint32_t acc = (kb > I.kb0 || k > 0) ? 1u : 0u;
-                            mma<PREC>(tmem, da + 2 * k, db + 2 * k, ID, acc);
+                            mma<PREC>(dacc, da + 2 * k, db + 2 * k, ID, acc);
                             if constexpr (X3) {
                                 const uint64_t dal = sdesc(base + A_BYTES + B_BYTES);
                                 const uint64_t dbl = sdesc(base + 2 * A_BYTES + B_BYTES);
-                                mma<PREC>(tmem, da + 2 * k, dbl + 2 * k, ID, 1u);
-                                mma<PREC>(tmem, dal + 2 * k, db + 2 * k, ID, 1u);
+                                mma<PREC>(dacc, da + 2 * k, dbl + 2 * k, ID, 1u);
+                                mma<PREC>(dacc, dal + 2 * k, db + 2 * k, ID, 1u);
                             }
                         }
                         mma_commit(&empty[s]);
                     }
-                    mma_commit(&tfull);
+                    mma_commit(&tfull[ab]);
                 }
             }
         } else {
@@ -269,8 +337,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int row = lane_base + lane;
             float* vrow = tile + (size_t)row * TS;
             const int R = 128 / P;
-            for (int item = blockIdx.x; item < items; item += G, ++it) {
-                const Item I = item_of(item, P, split, nk);
+            if (Jb.a.mode == 1 && Jb.a.row_part) {
+                if (et < Jb.a.r) s_z[et] = Jb.a.zvec[et];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+            Walk W(Jb, blockIdx.x, G);
+            Item I;
+            for (; W.next(I); ++it) {
                 if (et == 0 && Jb.a.mode != 1) {
                     // this slice's epilogue inputs into L2 while the MMAs run
                     const int n0 = I.tl * 128 + I.ks * R;
@@ -285,14 +358,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         prefetch_line_l2(Jb.a.bias + n0);
                     }
                 }
-                const bool ok = mbar_wait(&tfull, it & 1);
+                const uint32_t ab = it & 1;
+                const bool ok = mbar_wait(&tfull[ab], (it >> 1) & 1);
                 tc_fence_after();
                 bool wok = epi_all(ok);
                 if (wok) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         float v[16];
-                        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 16 * c, v);
+                        tmem_ld16(tmem + ab * ACC_COLS + ((uint32_t)lane_base << 16) + 16 * c, v);
                         tmem_wait_ld();
 #pragma unroll
                         for (int i = 0; i < 16; ++i) vrow[16 * c + i] = v[i];
@@ -301,13 +375,68 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fail = 1;
                 }
                 tc_fence_before();
-                mbar_arrive(&tempty);          // TMEM may be overwritten by the next item
+                mbar_arrive(&tempty[ab]);      // this accumulator may be overwritten
                 if (!wok) break;
                 if (Jb.a.mode == 1) {
                     // output layer (one row per thread, fused row reductions)
+                    if (Jb.stream && (I.kb0 > 0 || I.kb1 < nk)) {
+                        // a tile cut between CTAs: publish this piece; the last of the
+                        // tile's CTAs sums the pieces in CTA order and finishes the tile
+                        const long long Tt = (long long)tiles * nk;
+                        const int cf = stream_cta((long long)I.tl * nk, Tt, G);
+                        const int cl = stream_cta((long long)(I.tl + 1) * nk - 1, Tt, G);
+                        auto slot_of = [&](int cc) {
+                            return (int)((Tt * cc / G) / nk) == I.tl ? 0 : 1;
+                        };
+                        fence_proxy_async_smem();
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (et == 0) {
+                            float* dst = split_part + ((size_t)blockIdx.x * 2 + slot_of(blockIdx.x)) * (TILE_BYTES / 4);
+                            bulk_store_wait(dst, tile, TILE_BYTES);
+                            fence_proxy_async_global();
+                            __threadfence();
+                            unsigned* cnt = split_cnt + Jb.cnt_off + I.tl;
+                            const unsigned old = atomicAdd(cnt, 1u);
+                            s_last = (old + 1 == (unsigned)(cl - cf + 1));
+                            if (s_last) *cnt = 0u;
+                            __threadfence();
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (!s_last) continue;
+                        float4* own4 = reinterpret_cast<float4*>(tile);
+                        constexpr int NE = (int)(TILE_BYTES / 16);
+                        for (int e0 = et; e0 < NE; e0 += 128 * 8) {
+                            // eight float4 of every piece in flight at once
+                            float4 acc[8];
+                            for (int cc = cf; cc <= cl; ++cc) {
+                                float4 v[8];
+                                const float4* src = reinterpret_cast<const float4*>(
+                                    split_part + ((size_t)cc * 2 + slot_of(cc)) * (TILE_BYTES / 4));
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const int e = e0 + u * 128;
+                                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                    if (e < NE) v[u] = (cc == (int)blockIdx.x) ? own4[e] : __ldcg(src + e);
+                                }
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    if (cc == cf) {
+                                        acc[u] = v[u];
+                                    } else {
+                                        acc[u].x += v[u].x; acc[u].y += v[u].y;
+                                        acc[u].z += v[u].z; acc[u].w += v[u].w;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (e0 + u * 128 < NE) own4[e0 + u * 128] = acc[u];
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    }
                     row_epilogue(Jb.a, I.tl * 128 + row, vrow);
                     if (Jb.a.row_part)
-                        fused_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl);
+                        fused_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl, s_z);
                     continue;
                 }
                 if (split > 1) {
@@ -315,18 +444,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // chunks, then sum rows [ks R, ks R + R) of all chunks in order
                     fence_proxy_async_smem();
                     asm volatile("bar.sync 1, 128;" ::: "memory");
-                    unsigned long long* cnt = split_cnt + Jb.cnt_off + I.tl;
+                    unsigned* cnt = split_cnt + Jb.cnt_off + I.tl;
                     bool got = true;
                     if (et == 0) {
                         float* dst = split_part + ((size_t)I.tl * split + I.ks) * (TILE_BYTES / 4);
                         bulk_store_wait(dst, tile, TILE_BYTES);
                         fence_proxy_async_global();
                         __threadfence();
-                        split_arrive(cnt, jg);
-                        const unsigned long long want =
-                            ((unsigned long long)jg << 8) | (unsigned long long)split;
+                        atomicAdd(cnt, 1u);
                         const uint64_t t0 = globaltimer();
-                        while (ld_acquire64(cnt) != want) {
+                        while (ld_acquire(cnt) != (unsigned)split) {
                             if (globaltimer() - t0 > kWaitNs) { got = false; break; }
                         }
                         __threadfence();
@@ -351,18 +478,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     wok = epi_all(mbar_wait(&rbar, nred & 1));
                     ++nred;
                     if (!wok) { fail = 1; break; }
-                    // sum in chunk order (bitwise reproducible)
+                    // sum in chunk order (bitwise reproducible); split <= 8, the eight
+                    // loads of an element issue together
                     float* own = tile + (size_t)r0 * TS;
+#pragma unroll 2
                     for (int e = et; e < (int)slice_f; e += 128) {
-                        float acc = 0.f;
-                        for (int s = 0, q = 0; s < split; ++s) {
-                            if (s == I.ks) {
-                                acc += own[e];
-                            } else {
-                                acc += scratch[(size_t)q * slice_f + e];
-                                ++q;
-                            }
+                        float v[8];
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) {
+                            const int q = s < I.ks ? s : s - 1;
+                            v[s] = (s >= split) ? 0.f
+                                 : (s == I.ks ? own[e] : scratch[(size_t)q * slice_f + e]);
                         }
+                        float acc = v[0];
+#pragma unroll
+                        for (int s = 1; s < 8; ++s) acc += v[s];
                         own[e] = acc;
                     }
                 }
@@ -375,10 +505,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             if (!grid_barrier(gb, G, gen)) fail = 1;
-            s_gen = gen;
         }
         __syncthreads();
         if (fail) break;
+    }
+    if (!fail && n_jobs > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        const ChainJob& Pb = jobs[n_jobs - 1];
+        if (Pb.split > 1)
+            for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
     }
     // drain: nothing in flight may outlive the CTA
     if (warp == 0 && lane == 0) {

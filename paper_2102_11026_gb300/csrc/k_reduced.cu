@@ -520,28 +520,46 @@ __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
 }
 
 // Tensor-core variant of the top-layer seed: g[c][k] for k < ld (zero padding), c < Cb.
-__global__ void k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32, __nv_bfloat16* gh,
-                              __nv_bfloat16* gl, int out_f32, int out_bf16) {
+// A block takes 32 consecutive k; its 8 warps sum every 8th incoming split partial
+// (coalesced over k), combine the 8 sums in a fixed order, then write the columns
+// c = warp, warp + 8, ...
+__global__ void __launch_bounds__(256) k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32,
+                                                     __nv_bfloat16* gh, __nv_bfloat16* gl,
+                                                     int out_f32, int out_bf16) {
     if (A.ns && A.ns->done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ld) return;
+    __shared__ float part[8][kMaxR + 1][33];
+    __shared__ float sre[32];
+    const int tx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + tx;
     const int r = A.r;
     const size_t stride = (size_t)A.in_ncol * A.n_o;
-    float re = 0.f, s1 = 0.f;
-    if (k < A.n_o) {
-        for (int s = 0; s < A.in_split; ++s) re += A.in_part[(size_t)s * stride + k];
-        s1 = A.S1[k];
+    const bool valid = k < A.n_o;
+    const int ncol = A.in_ncol > 1 ? r + 1 : 1;
+    for (int c = 0; c < ncol; ++c) {
+        float acc = 0.f;
+        if (valid)
+            for (int s = sy; s < A.in_split; s += 8) acc += A.in_part[(size_t)s * stride + (size_t)c * A.n_o + k];
+        part[sy][c][tx] = acc;
     }
-    for (int c = 0; c < Cb; ++c) {
+    __syncthreads();
+    if (sy == 0) {
         float v = 0.f;
-        if (k < A.n_o) {
+        for (int q = 0; q < 8; ++q) v += part[q][0][tx];
+        sre[tx] = v;
+    }
+    __syncthreads();
+    if (k >= ld) return;
+    const float re = sre[tx];
+    const float s1 = valid ? A.S1[k] : 0.f;
+    for (int c = sy; c < Cb; c += 8) {
+        float v = 0.f;
+        if (valid) {
             if (c == 0) {
                 v = re * s1;
             } else if (c <= r) {
                 float im = 0.f;
                 if (A.in_ncol > 1)
-                    for (int s = 0; s < A.in_split; ++s)
-                        im += A.in_part[(size_t)s * stride + (size_t)c * A.n_o + k];
+                    for (int q = 0; q < 8; ++q) im += part[q][c][tx];
                 v = fmaf(im, s1, re * A.T[(size_t)(c - 1) * A.n_o + k]);
             }
         }
@@ -557,7 +575,7 @@ __global__ void k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32, __nv_bfloat
 
 void launch_bwd_prep_tc(cudaStream_t s, const BwdArgs& a, int Cb, int ld, float* g32,
                         __nv_bfloat16* gh, __nv_bfloat16* gl, int out_f32, int out_bf16) {
-    k_bwd_prep_tc<<<(ld + 63) / 64, 64, 0, s>>>(a, Cb, ld, g32, gh, gl, out_f32, out_bf16);
+    k_bwd_prep_tc<<<(ld + 31) / 32, 256, 0, s>>>(a, Cb, ld, g32, gh, gl, out_f32, out_bf16);
 }
 
 // WT[c][r] = W[r][c] for r < rows, c < cols (zero elsewhere in WT's padding is kept)

@@ -149,7 +149,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (split == 1) {
             if (wok) row_epilogue(A, n, vrow);
-            if (A.mode == 1 && A.row_part) fused_row_reduce(A, tile, TS, row, n, wok, blockIdx.x);
+            if (A.mode == 1 && A.row_part) {
+                __shared__ float s_z[kMaxR];
+                if (row < A.r) s_z[row] = A.zvec[row];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                fused_row_reduce(A, tile, TS, row, n, wok, blockIdx.x, s_z);
+            }
         } else {
             // write this split's partial tile [tile][split][c][128 rows]; the last CTA of the
             // tile (atomic count, no waiting) sums the partials in split order and finishes

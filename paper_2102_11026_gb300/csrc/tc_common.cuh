@@ -181,7 +181,7 @@ struct ActOut {
     }
 };
 
-static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const float* v) {
+static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const float* __restrict__ v) {
     const int mode = A.mode, r = A.r, CP = A.Cp, C = n_cols(r);
     const int n_out = A.n_out;
     if (mode == 3) {
@@ -199,14 +199,26 @@ static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const 
         float* __restrict__ dJ = A.dJ;
         float* __restrict__ HDD = A.HDD;
         float* __restrict__ Hqq = A.Hqq;
-        const double ih = A.inv_h, ih2 = A.inv_h2, ih3 = A.inv_h3, idt2 = A.inv_dt2;
+        const double ih2 = A.inv_h2, idt2 = A.inv_dt2;
+        // 1/h and 1/h^3 in FP32 (exact for the power-of-two steps the library uses)
+        const float fh = (float)A.inv_h, fh3 = (float)A.inv_h3;
         if (u) u[n] = v[0] + A.bias[n];
         if (HDD) HDD[n] = (float)(v[3] * ih2);
         if (Hqq) Hqq[n] = (float)(v[3] * ih2 * idt2);
-        for (int j = 0; j < r; ++j) {
-            const int cb = kShared + 3 * j;
-            if (J) J[(size_t)j * N + n] = (float)(v[cb] * ih);
-            if (dJ) dJ[(size_t)j * N + n] = (float)(v[cb + 2] * ih3);
+        if (J && dJ) {
+#pragma unroll 5
+            for (int j = 0; j < r; ++j) {
+                const int cb = kShared + 3 * j;
+                const float a = v[cb], b = v[cb + 2];
+                J[(size_t)j * N + n] = a * fh;
+                dJ[(size_t)j * N + n] = b * fh3;
+            }
+        } else {
+            for (int j = 0; j < r; ++j) {
+                const int cb = kShared + 3 * j;
+                if (J) J[(size_t)j * N + n] = v[cb] * fh;
+                if (dJ) dJ[(size_t)j * N + n] = v[cb + 2] * fh3;
+            }
         }
         return;
     }
@@ -354,12 +366,13 @@ static __device__ __noinline__ void slice_epilogue(const FwdArgs& A, const float
 // a_n = m_n y_n - dt^2 f_ext,n;  partials [J^T a | J^T M J (upper) | J^T M dJ] of
 // tile `tl` go to A.row_part (the layout of k_row_reduce).  All 128 epilogue
 // threads call this together (named barrier 1); `tile` needs 128*TS + 256 floats.
-static __device__ __noinline__ void fused_row_reduce(const FwdArgs& A, float* tile, int TS,
-                                                     int row, int n, bool wok, int tl) {
+// zs: z = (q - qbar) - dt qbar_dot (r floats) staged in shared memory by the caller.
+static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float* tile, int TS,
+                                                     int row, int n, bool wok, int tl,
+                                                     const float* zs) {
     const int r = A.r, N = A.n_out, CP = A.Cp;
     const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
     const float* __restrict__ mdof = A.mdof;
-    const float* __restrict__ zvec = A.zvec;
     const float* __restrict__ f_ext = A.f_ext;
     float* __restrict__ a_out = A.a_out;
     float* __restrict__ out = A.row_part + (size_t)tl * A.row_stride;
@@ -370,15 +383,29 @@ static __device__ __noinline__ void fused_row_reduce(const FwdArgs& A, float* ti
     float m = 0.f, av = 0.f;
     if (wok && n < N) {
         m = mdof[n];
-        // this row's J and dJ in physical units (in place: the outputs are written)
+        const float fe = f_ext ? f_ext[n] : 0.f;
+        // this row's J and dJ in physical units (in place: the outputs are written);
+        // eight columns' loads issue before their stores
         float y = vrow[3] * ih2;
-        for (int j = 0; j < r; ++j) {
-            const float Jv = vrow[kShared + 3 * j] * ih;
-            vrow[kShared + 3 * j] = Jv;
-            vrow[kShared + 3 * j + 2] *= ih3;
-            y = fmaf(Jv, zvec[j], y);
+        for (int j0 = 0; j0 < r; j0 += 8) {
+            float Jv[8], dv[8], z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u < r ? j0 + u : r - 1;
+                Jv[u] = vrow[kShared + 3 * j] * ih;
+                dv[u] = vrow[kShared + 3 * j + 2] * ih3;
+                z[u] = zs[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (j0 + u < r) {
+                    vrow[kShared + 3 * (j0 + u)] = Jv[u];
+                    vrow[kShared + 3 * (j0 + u) + 2] = dv[u];
+                    y = fmaf(Jv[u], z[u], y);
+                }
+            }
         }
-        av = (float)((double)m * y - dt2 * (f_ext ? (double)f_ext[n] : 0.0));
+        av = (float)((double)m * y - dt2 * (double)fe);
         if (a_out) a_out[n] = av;
     } else {
         // failed tile, or rows past N (zero rows of the padded weights): no contribution
@@ -409,6 +436,7 @@ static __device__ __noinline__ void fused_row_reduce(const FwdArgs& A, float* ti
         for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
     }
     const bool do_phi = (mat == 0 && bj == 0);
+#pragma unroll 4
     for (int k = 0; k < 128; ++k) {
         const float* tk = tile + k * TS;
         const float mk = ms[k], ak = as[k];
