@@ -86,12 +86,14 @@ __device__ __forceinline__ void mat3_mul(const double* A, const double* B, doubl
                            A[i * 3 + 2] * B[2 * 3 + j];
 }
 
-__global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
+constexpr int kCubWarps = 4;   // tets per block (one warp each): more SMs, one warp per scheduler
+
+__global__ void __launch_bounds__(32 * kCubWarps) k_cubature(CubArgs A) {
     if (A.ns && A.ns->done) return;
-    __shared__ float sdG[8][kMaxR][9];
-    __shared__ float sdP[8][kMaxR][9];
+    __shared__ float sdG[kCubWarps][kMaxR][9];
+    __shared__ float sdP[kCubWarps][kMaxR][9];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * 8 + warp;
+    const int slot = blockIdx.x * kCubWarps + warp;
     if (slot >= A.n_cub) return;
     const int r = A.r;
     const int nsym = r * (r + 1) / 2;
@@ -113,8 +115,19 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     const float Vf = A.vol[tet];
     // per-tet FP64 part (F, P, Psi) once per warp: FP64 throughput is a small fraction
     // of FP32 on this part, so the 31 other lanes wait and then read the results
-    __shared__ float sF[8][9], sS[8][9], sFiT[8][9], sP[8][9], sLnJ[8];
-    __shared__ int sBad[8];
+    __shared__ float sF[kCubWarps][9], sS[kCubWarps][9], sFiT[kCubWarps][9], sP[kCubWarps][9],
+        sLnJ[kCubWarps];
+    __shared__ int sBad[kCubWarps];
+    // lane j < r gathers column j of J on the tet's 12 DOFs now, so the loads are in
+    // flight while lane 0 forms the per-tet FP64 quantities
+    float Jg[12];
+    if (lane < r) {
+        const float* Jc = A.J + (size_t)lane * A.N;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Jg[3 * a + d] = Jc[3 * v[a] + d];
+    }
     if (lane == 0) {
         double Bm[9];
         for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
@@ -217,11 +230,10 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     // directional quantities per column j
     float g_j = 0.f;
     if (lane < r) {
-        const float* Jc = A.J + (size_t)lane * A.N;
         float dUj[9], dGj[9], dPj[9];
         for (int c = 0; c < 3; ++c)
             for (int d = 0; d < 3; ++d)
-                dUj[d * 3 + c] = Jc[3 * v[c + 1] + d] - Jc[3 * v[0] + d];
+                dUj[d * 3 + c] = Jg[3 * (c + 1) + d] - Jg[d];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
                 dGj[i * 3 + j] = dUj[i * 3 + 0] * (float)Bm[0 * 3 + j] +
@@ -276,10 +288,13 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
     __syncwarp();
     if (lane < r) part[lane] = wgt * g_j;
     const float wV = (float)(wgt * V);
+    // (i, j) of upper-triangle entry e (row-major, i <= j), advanced 32 entries a step
+    int ui = 0, up = lane;
+    while (ui < r && up >= r - ui) { up -= r - ui; ++ui; }
     for (int e = lane; e < nsym; e += 32) {
-        int p = e, i = 0;
-        while (p >= r - i) { p -= r - i; ++i; }
-        int j = i + p;
+        const int i = ui, j = ui + up;
+        up += 32;
+        while (ui < r && up >= r - ui) { up -= r - ui; ++ui; }
         float s = 0.f;
         for (int k = 0; k < 9; ++k) s = fmaf(sdG[warp][i][k], sdP[warp][j][k], s);
         part[r + e] = wV * s;
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(256) k_cubature(CubArgs A) {
 
 void launch_cubature(cudaStream_t s, const CubArgs& a) {
     if (a.n_cub <= 0) return;
-    k_cubature<<<(a.n_cub + 7) / 8, 256, 0, s>>>(a);
+    k_cubature<<<(a.n_cub + kCubWarps - 1) / kCubWarps, 32 * kCubWarps, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------- W_L^T a GEMV --

@@ -8,16 +8,36 @@ namespace dae {
 
 // out[e] = sum_p part[p * stride + e] for e < n_ent, in FP64; 32 threads per entry
 // with a fixed summation tree (bitwise reproducible).
-__global__ void k_colsum(const float* part, int n_parts, int stride, int n_ent, double* out,
-                         const NewtonState* ns) {
+// out[e] = sum_p part[p][e].  A block takes 32 consecutive entries (the lanes,
+// coalesced loads); warp w of 16 sums the parts p = w (mod 16): each group of four
+// of its terms is summed in FP32 and added to an FP64 accumulator (FP64 adds are
+// scarce on this part), then the 16 warp sums are added in warp order (fixed order:
+// bitwise reproducible).
+__global__ void __launch_bounds__(512) k_colsum(const float* part, int n_parts, int stride,
+                                                int n_ent, double* out, const NewtonState* ns) {
     if (ns && ns->done) return;
-    const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (e >= n_ent) return;
+    __shared__ double ws[16][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
     double acc = 0.0;
-    for (int p = lane; p < n_parts; p += 32) acc += (double)part[(size_t)p * stride + e];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[e] = acc;
+    if (e < n_ent) {
+        int p = w;
+        for (; p + 48 < n_parts; p += 64) {
+            const float a = part[(size_t)p * stride + e];
+            const float b = part[(size_t)(p + 16) * stride + e];
+            const float c = part[(size_t)(p + 32) * stride + e];
+            const float d = part[(size_t)(p + 48) * stride + e];
+            acc += (double)((a + b) + (c + d));
+        }
+        for (; p < n_parts; p += 16) acc += (double)part[(size_t)p * stride + e];
+    }
+    ws[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && e < n_ent) {
+        double s = 0.0;
+        for (int q = 0; q < 16; ++q) s += ws[q][lane];
+        out[e] = s;
+    }
 }
 
 __global__ void k_dsum(const double* x, int n, double* out, const NewtonState* ns) {
@@ -36,7 +56,7 @@ __global__ void k_dsum(const double* x, int n, double* out, const NewtonState* n
 
 static inline void colsum(cudaStream_t st, const float* part, int n_parts, int stride, int n_ent,
                           double* out, const NewtonState* ns) {
-    k_colsum<<<(n_ent + 7) / 8, 256, 0, st>>>(part, n_parts, stride, n_ent, out, ns);
+    k_colsum<<<(n_ent + 31) / 32, 512, 0, st>>>(part, n_parts, stride, n_ent, out, ns);
 }
 
 __device__ __forceinline__ int upper_idx(int i, int j, int r) {
@@ -45,74 +65,57 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
 }
 
 // Solve A x = b (r <= 32, A column-major in global memory) with LU and partial
-// pivoting, all threads of the block (FP64 throughput is low on this part, so the
-// trailing updates are spread over the block and each pivot costs one reciprocal).
-// Returns 0, or DAE_ERR_SINGULAR (uniform over the block).
-__device__ int block_lu_solve(const double* A, const double* b, double* x, int r,
-                              double (*M)[kMaxR + 1], double* rhs) {
-    __shared__ double amax_s, piv_inv;
-    __shared__ int piv_row, sing;
-    __shared__ double dinv[kMaxR];
-    const int t = threadIdx.x, nt = blockDim.x;
-    const int lane = t & 31, warp = t >> 5;
-    for (int e = t; e < r * r; e += nt) {
-        const int i = e % r, j = e / r;
-        M[i][j] = A[e];
-    }
-    for (int i = t; i < r; i += nt) rhs[i] = b[i];
-    if (t == 0) sing = 0;
-    __syncthreads();
-    if (warp == 0) {
-        double am = 0.0;
-        for (int e = lane; e < r * r; e += 32) am = fmax(am, fabs(M[e % r][e / r]));
-        for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
-        if (lane == 0) amax_s = am;
-    }
-    __syncthreads();
+// pivoting in one warp: the matrix sits in shared memory, each elimination step
+// spreads its trailing update over the 32 lanes, and nothing waits on a block-wide
+// barrier (the steps are latency-bound; FP64 issue is the only throughput limit).
+// Call with all 32 lanes of one warp.  Returns 0, or DAE_ERR_SINGULAR when a pivot is
+// below 1e-14 max|A| (uniform over the warp).
+__device__ int warp_lu_solve(const double* A, const double* b, double* x, int r,
+                             double (*M)[kMaxR + 1], double* rhs) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    for (int e = lane; e < r * r; e += 32) M[e % r][e / r] = A[e];
+    if (lane < r) rhs[lane] = b[lane];
+    __syncwarp();
+    double am = 0.0;
+    for (int e = lane; e < r * r; e += 32) am = fmax(am, fabs(M[e % r][e / r]));
+    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(full, am, o));
     for (int k = 0; k < r; ++k) {
-        if (warp == 0) {
-            double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
-            int p = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
-                if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
-            }
-            if (lane == 0) {
-                piv_row = p;
-                if (!(v > 1e-14 * amax_s) || !isfinite(v)) sing = 1;
-            }
+        double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
+        int p = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(full, v, o);
+            const int p2 = __shfl_xor_sync(full, p, o);
+            if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
         }
-        __syncthreads();
-        if (sing) return DAE_ERR_SINGULAR;
-        const int p = piv_row;
+        if (!(v > 1e-14 * am) || !isfinite(v)) return DAE_ERR_SINGULAR;
         if (p != k) {
-            for (int j = t; j < r; j += nt) {
-                const double tmp = M[k][j]; M[k][j] = M[p][j]; M[p][j] = tmp;
+            if (lane < r) {
+                const double tmp = M[k][lane]; M[k][lane] = M[p][lane]; M[p][lane] = tmp;
             }
-            if (t == 0) { const double tmp = rhs[k]; rhs[k] = rhs[p]; rhs[p] = tmp; }
+            if (lane == 0) { const double tmp = rhs[k]; rhs[k] = rhs[p]; rhs[p] = tmp; }
         }
-        __syncthreads();
-        if (t == 0) piv_inv = 1.0 / M[k][k];
-        __syncthreads();
+        __syncwarp();
+        const double piv_inv = 1.0 / M[k][k];
+        if (lane > k && lane < r) M[lane][k] *= piv_inv;
+        __syncwarp();
         const int m = r - k - 1;
-        for (int i = k + 1 + t; i < r; i += nt) M[i][k] *= piv_inv;
-        __syncthreads();
-        for (int e = t; e < m * m; e += nt) {
+#pragma unroll 4
+        for (int e = lane; e < m * m; e += 32) {
             const int i = k + 1 + e / m, j = k + 1 + e % m;
             M[i][j] = fma(-M[i][k], M[k][j], M[i][j]);
         }
-        for (int i = k + 1 + t; i < r; i += nt) rhs[i] = fma(-M[i][k], rhs[k], rhs[i]);
-        __syncthreads();
+        if (lane > k && lane < r) rhs[lane] = fma(-M[lane][k], rhs[k], rhs[lane]);
+        __syncwarp();
     }
-    for (int i = t; i < r; i += nt) dinv[i] = 1.0 / M[i][i];
-    __syncthreads();
+    // back substitution: lane j holds rhs[j]; x[i] is broadcast by a shuffle
+    double rv = lane < r ? rhs[lane] : 0.0;
     for (int i = r - 1; i >= 0; --i) {
-        if (t == 0) x[i] = rhs[i] * dinv[i];
-        __syncthreads();
-        for (int j = t; j < i; j += nt) rhs[j] = fma(-M[j][i], x[i], rhs[j]);
-        __syncthreads();
+        const double xi = __shfl_sync(full, rv, i) / M[i][i];
+        if (lane == i) x[i] = xi;
+        if (lane < i) rv = fma(-M[lane][i], xi, rv);
     }
+    __syncwarp();
     return 0;
 }
 
@@ -238,8 +241,13 @@ __global__ void k_control(CtlArgs C) {
     if (dec == 1) {
         for (int i = t; i < r; i += blockDim.x) rhs[i] = -sphi[i];
         __syncthreads();
-        const int st = block_lu_solve(A, rhs, x, r, M, rhs);
+        __shared__ int lu_st;
+        if (t < 32) {
+            const int st0 = warp_lu_solve(A, rhs, x, r, M, rhs);
+            if (t == 0) lu_st = st0;
+        }
         __syncthreads();
+        const int st = lu_st;
         if (t == 0) {
             if (st) {
                 S.status = st;
