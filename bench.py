@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "medium"],
+                    help="medium: the paper-scale hidden layers onto a 20x20x17 grid, for "
+                         "profiler captures")
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -121,7 +123,7 @@ class ClockSampler:
 
 def make_workload(name):
     from paper_2102_11026_gb300 import synth
-    return synth.paper() if name == "paper" else synth.small()
+    return {"paper": synth.paper, "small": synth.small, "medium": synth.medium}[name]()
 
 
 def frame_weights(wl, n_frames, seed, start=0):
@@ -156,7 +158,9 @@ def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
     cfg = {"workload": ("paper-scale decoder r=30, 30-128-256-512-1024-2048-2048-2048-"
                         "4096-4096-60000 tanh, 20x20x50 grid (88445 tets), Neo-Hookean, "
                         "500 cubature tets, gravity, dt=1/60, <=5 Newton updates/frame")
-           if args.workload == "paper" else "small decoder r=5 5-64-256-1024-3000",
+           if args.workload == "paper" else
+           ("paper-scale hidden layers r=30, 30-...-4096-20400 tanh, 20x20x17 grid, Neo-Hookean"
+            if args.workload == "medium" else "small decoder r=5 5-64-256-1024-3000"),
            "step": "one implicit-Euler frame", "frames": K,
            "l2": "inputs larger than L2 (decoder weights %.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
            "parallelism": "replicas" if world > 1 else "single GPU"}

@@ -64,58 +64,124 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
     return i * r - i * (i - 1) / 2 + (j - i);
 }
 
-// Solve A x = b (r <= 32, A column-major in global memory) with LU and partial
-// pivoting in one warp: the matrix sits in shared memory, each elimination step
-// spreads its trailing update over the 32 lanes, and nothing waits on a block-wide
-// barrier (the steps are latency-bound; FP64 issue is the only throughput limit).
-// Call with all 32 lanes of one warp.  Returns 0, or DAE_ERR_SINGULAR when a pivot is
-// below 1e-14 max|A| (uniform over the warp).
-__device__ int warp_lu_solve(const double* A, const double* b, double* x, int r,
-                             double (*M)[kMaxR + 1], double* rhs) {
-    const int lane = threadIdx.x & 31;
+// Solve A x = b in FP64 accuracy (r <= 32, A column-major FP64 in global memory) by
+// mixed-precision iterative refinement (Wilkinson; Moler 1967): LU with partial
+// pivoting of the FP32-rounded A, then x <- x + U^{-1} L^{-1} P (b - A x) with the
+// residual formed in FP64.  Each correction shrinks the error by about
+// kappa(A) r eps_32, so kRefine corrections reach FP64 rounding for the reduced
+// Newton matrices (kappa ~ 1e1 - 1e3).  FP64 issue is scarce on this part (each
+// dependent FP64 operation costs ~100 cycles; an FP64 LU took ~60 us of latency),
+// while the FP32 factorisation is one warp with no barriers.
+//   LU: lane i of warp 0 holds row i in registers; per column k the warp picks the
+//   pivot row among the rows not yet used (largest |.|, lowest index on ties)
+//   without swapping rows, broadcasts it lane to lane, stores the multipliers in
+//   place and updates its row (fully unrolled over the <= 32 columns).
+// Called by the 128 threads of warps 0-3.  Returns 0, or DAE_ERR_SINGULAR when an
+// FP32 pivot is below 2^-20 max|A| (such A are beyond what the FP32 factors resolve).
+constexpr int kRefine = 3;
+
+__device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
+    __shared__ int perm[kMaxR];
+    __shared__ float rinv[kMaxR], dsol[kMaxR];
+    __shared__ double res[kMaxR], part[4][kMaxR];
+    __shared__ int s_sing;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const unsigned full = 0xffffffffu;
-    for (int e = lane; e < r * r; e += 32) M[e % r][e / r] = A[e];
-    if (lane < r) rhs[lane] = b[lane];
-    __syncwarp();
-    double am = 0.0;
-    for (int e = lane; e < r * r; e += 32) am = fmax(am, fabs(M[e % r][e / r]));
-    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(full, am, o));
-    for (int k = 0; k < r; ++k) {
-        double v = (lane >= k && lane < r) ? fabs(M[lane][k]) : -1.0;
-        int p = lane;
-        for (int o = 16; o > 0; o >>= 1) {
-            const double v2 = __shfl_xor_sync(full, v, o);
-            const int p2 = __shfl_xor_sync(full, p, o);
-            if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+    float row[kMaxR];   // warp 0: row `lane` of the FP32 factors (L left of its pivot step, U from it)
+    int ps = -1;        // warp 0: the elimination step at which row `lane` was the pivot
+    if (t < r) { x[t] = 0.0; res[t] = b[t]; }
+    if (warp == 0) {
+        float am = 0.f;
+#pragma unroll
+        for (int j = 0; j < kMaxR; ++j) {
+            row[j] = (lane < r && j < r) ? (float)A[(size_t)j * r + lane] : 0.f;
+            am = fmaxf(am, fabsf(row[j]));
         }
-        if (!(v > 1e-14 * am) || !isfinite(v)) return DAE_ERR_SINGULAR;
-        if (p != k) {
-            if (lane < r) {
-                const double tmp = M[k][lane]; M[k][lane] = M[p][lane]; M[p][lane] = tmp;
+        for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(full, am, o));
+        unsigned used = 0u;
+        int sing = 0;
+        // k runs in a rolled loop: row[k] is read and written through unrolled selects,
+        // so the row stays in registers
+        for (int k = 0; k < r && !sing; ++k) {
+            float rk = 0.f;
+#pragma unroll
+            for (int j = 0; j < kMaxR; ++j)
+                if (j == k) rk = row[j];
+            float v = (lane < r && !((used >> lane) & 1u)) ? fabsf(rk) : -1.f;
+            int p = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(full, v, o);
+                const int p2 = __shfl_xor_sync(full, p, o);
+                if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
             }
-            if (lane == 0) { const double tmp = rhs[k]; rhs[k] = rhs[p]; rhs[p] = tmp; }
+            if (!(v > 0x1p-20f * am) || !isfinite(v)) {
+                sing = 1;
+                break;
+            }
+            const float inv = 1.0f / __shfl_sync(full, rk, p);
+            used |= 1u << p;
+            if (lane == p) ps = k;
+            if (lane == 0) { perm[k] = p; rinv[k] = inv; }
+            const bool act = lane < r && !((used >> lane) & 1u);
+            const float l = rk * inv;
+            // branch-free: all 32 broadcasts issue back to back, updates are selects
+            float pr[kMaxR];
+#pragma unroll
+            for (int j = 0; j < kMaxR; ++j) pr[j] = __shfl_sync(full, row[j], p);
+#pragma unroll
+            for (int j = 0; j < kMaxR; ++j) {
+                const float upd = fmaf(-l, pr[j], row[j]);
+                row[j] = (act && j > k) ? upd : ((act && j == k) ? l : row[j]);
+            }
         }
-        __syncwarp();
-        const double piv_inv = 1.0 / M[k][k];
-        if (lane > k && lane < r) M[lane][k] *= piv_inv;
-        __syncwarp();
-        const int m = r - k - 1;
-#pragma unroll 4
-        for (int e = lane; e < m * m; e += 32) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            M[i][j] = fma(-M[i][k], M[k][j], M[i][j]);
+        if (lane == 0) s_sing = sing;
+    }
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    if (s_sing) return DAE_ERR_SINGULAR;
+    for (int it = 0; it <= kRefine; ++it) {
+        if (warp == 0) {
+            // d = U^{-1} L^{-1} P res in FP32; lane i holds the right-hand side of row i.
+            // Branch-free chains: steps past r are no-ops (perm 0, multiplier 0).
+            float bv = lane < r ? (float)res[lane] : 0.f;
+            int pk[kMaxR];
+            float rk[kMaxR];
+#pragma unroll
+            for (int k = 0; k < kMaxR; ++k) {
+                pk[k] = k < r ? perm[k] : 0;
+                rk[k] = k < r ? rinv[k] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kMaxR; ++k) {
+                const float bp = __shfl_sync(full, bv, pk[k]);
+                const float m = (k < r && ps > k) ? row[k] : 0.f;
+                bv = fmaf(-m, bp, bv);
+            }
+            float d = 0.f;
+#pragma unroll
+            for (int k = kMaxR - 1; k >= 0; --k) {
+                const float xk = __shfl_sync(full, bv, pk[k]) * rk[k];
+                if (lane == k) d = xk;
+                const float m = (k < r && ps >= 0 && ps < k) ? row[k] : 0.f;
+                bv = fmaf(-m, xk, bv);
+            }
+            if (lane < r) dsol[lane] = d;
         }
-        if (lane > k && lane < r) rhs[lane] = fma(-M[lane][k], rhs[k], rhs[lane]);
-        __syncwarp();
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (t < r) x[t] += (double)dsol[t];
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (it == kRefine) break;
+        // res = b - A x in FP64: thread (i, c) sums the columns j = c (mod 4) of row i
+        {
+            const int i = lane, c = warp;
+            double sacc = 0.0;
+            if (i < r)
+                for (int j = c; j < r; j += 4) sacc = fma(A[(size_t)j * r + i], x[j], sacc);
+            part[c][i] = sacc;
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (t < r) res[t] = b[t] - ((part[0][t] + part[1][t]) + (part[2][t] + part[3][t]));
+        asm volatile("bar.sync 2, 128;" ::: "memory");
     }
-    // back substitution: lane j holds rhs[j]; x[i] is broadcast by a shuffle
-    double rv = lane < r ? rhs[lane] : 0.0;
-    for (int i = r - 1; i >= 0; --i) {
-        const double xi = __shfl_sync(full, rv, i) / M[i][i];
-        if (lane == i) x[i] = xi;
-        if (lane < i) rv = fma(-M[lane][i], xi, rv);
-    }
-    __syncwarp();
     return 0;
 }
 
@@ -144,7 +210,6 @@ __global__ void k_control(CtlArgs C) {
         if (C.use_cond && threadIdx.x == 0) cudaGraphSetConditional(C.hcond, 0u);
         return;
     }
-    __shared__ double M[kMaxR][kMaxR + 1];
     __shared__ double rhs[kMaxR];
     __shared__ double x[kMaxR];
     __shared__ double sphi[kMaxR];
@@ -154,6 +219,7 @@ __global__ void k_control(CtlArgs C) {
     const int r = C.r, t = threadIdx.x;
     const double dt2 = C.dt * C.dt;
     const int nsym = r * (r + 1) / 2;
+    const double inv_h = 1.0 / C.h;   // one divide (exact for power-of-two steps)
     double* phi = C.red;
     double* A = C.red + r;
     double* energy = C.red + r + r * r;
@@ -172,7 +238,7 @@ __global__ void k_control(CtlArgs C) {
     __syncthreads();
     for (int e = t; e < r * r; e += blockDim.x) {
         const int i = e % r, j = e / r;   // column-major (i, j)
-        const double ah = 0.5 * (C.bwdsum[(1 + j) * r + i] + C.bwdsum[(1 + i) * r + j]) / C.h;
+        const double ah = 0.5 * inv_h * (C.bwdsum[(1 + j) * r + i] + C.bwdsum[(1 + i) * r + j]);
         const double mr = C.rowsum[r + upper_idx(i, j, r)];
         const double b = C.rowsum[r + nsym + i * r + j];
         const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
@@ -203,10 +269,17 @@ __global__ void k_control(CtlArgs C) {
         }
         return;
     }
+    // |phi|^2 by a warp reduction (serial FP64 chains are slow on this part)
+    __shared__ double s_merit;
+    if (t < 32) {
+        double m2 = t < r ? sphi[t] * sphi[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        if (t == 0) s_merit = m2;
+    }
+    __syncthreads();
     if (t == 0) {
         S.evals += 1;
-        double merit = 0.0;
-        for (int i = 0; i < r; ++i) merit += sphi[i] * sphi[i];
+        const double merit = s_merit;
         const bool bad = inverted || nonfinite || !isfinite(merit);
         int dec;
         if (S.evals == 1) {
@@ -241,23 +314,29 @@ __global__ void k_control(CtlArgs C) {
     if (dec == 1) {
         for (int i = t; i < r; i += blockDim.x) rhs[i] = -sphi[i];
         __syncthreads();
+        __shared__ double s_xn, s_qn;
         __shared__ int lu_st;
-        if (t < 32) {
-            const int st0 = warp_lu_solve(A, rhs, x, r, M, rhs);
+        if (t < 128) {
+            const int st0 = mixed_solve(A, rhs, x, r);
             if (t == 0) lu_st = st0;
         }
         __syncthreads();
         const int st = lu_st;
+        if (t < 32) {
+            double xn = t < r ? fabs(x[t]) : 0.0, qn = t < r ? fabs(S.q_acc[t]) : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                xn = fmax(xn, __shfl_xor_sync(0xffffffffu, xn, o));
+                qn = fmax(qn, __shfl_xor_sync(0xffffffffu, qn, o));
+            }
+            if (t == 0) { s_xn = xn; s_qn = qn; }
+        }
+        __syncthreads();
         if (t == 0) {
             if (st) {
                 S.status = st;
                 S.done = 1;
             } else {
-                double xn = 0.0, qn = 0.0;
-                for (int i = 0; i < r; ++i) {
-                    xn = fmax(xn, fabs(x[i]));
-                    qn = fmax(qn, fabs(S.q_acc[i]));
-                }
+                const double xn = s_xn, qn = s_qn;
                 if (C.xtol > 0.0 && xn <= C.xtol * fmax(1.0, qn)) {
                     // the remaining correction is negligible: q_acc is the solution
                     S.converged = 1;

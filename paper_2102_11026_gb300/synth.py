@@ -198,6 +198,19 @@ def paper(seed=2, act="tanh"):
     return Workload("paper", dec, mesh, cub, w, st, gravity_force(mesh.vmass))
 
 
+def medium(seed=2, act="tanh"):
+    """The paper-scale decoder's hidden layers with a 20x20x17 grid (N = 20400 output
+    DOFs, 160 output tiles, 334 MB of output-layer weights: larger than L2), for
+    profiler captures that must stay small; material, cubature, gravity and start
+    state as in ``paper``."""
+    widths = PAPER_WIDTHS[:-1] + [3 * 20 * 20 * 17]
+    dec = make_decoder(widths, seed, act, bias=False)
+    mesh = make_grid_mesh(20, 20, 17, seed, "neohookean", 5e5, 0.45)
+    cub, w = make_cubature(mesh.n_tet, 500, seed)
+    st = make_state(dec.r, seed, q_std=PAPER_Q_STD)
+    return Workload("medium", dec, mesh, cub, w, st, gravity_force(mesh.vmass))
+
+
 def custom(widths, grid, n_cub, seed, act="tanh", material="stvk", E=1e5, nu=0.4,
            gravity=False):
     """Arbitrary-shape workload for parity sweeps; ``widths[-1]`` must equal

@@ -177,6 +177,50 @@ def test_inverted_neohookean_tet_reports_inverted():
         g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_latent_the_decoder_ignores_reports_singular(prec):
+    """With column 0 of the first layer zero the decoder does not depend on q_0: row
+    and column 0 of A vanish (J e_0 = 0, H[., e_0] = 0, dJ e_0 = 0) while phi stays
+    nonzero, so the Newton step must report DAE_ERR_SINGULAR instead of a step."""
+    from paper_2102_11026_gb300 import dae
+    wl = odd_workload(4)
+    wl.dec.W[0][:, 0] = 0.0
+    g = Gpu(wl, prec)
+    try:
+        q0 = synth.newton_start(wl.state)
+        try:
+            _, rep = g.newton(q0)
+            status = rep.status
+        except dae.DaeError as e:
+            status = e.status
+        assert status == -6
+    finally:
+        g.close()
+
+
+def test_newton_step_solves_reduced_system():
+    """The device Newton step solves A delta = -phi to FP64 accuracy: one update from
+    q0 with the line search off equals q0 + A^{-1}(-phi) formed on the host from the
+    same library's A and phi."""
+    from paper_2102_11026_gb300 import dae
+    wl = odd_workload(7, seed=11)
+    g = Gpu(wl)
+    try:
+        q0 = synth.newton_start(wl.state)
+        rs = g.reduced(q0)
+        delta = np.linalg.solve(rs["A"], -rs["phi"])
+        opts = dae.dae_default_newton_opts()
+        opts.max_iter = 1
+        opts.max_step = 0.0
+        opts.xtol = 0.0
+        opts.c_armijo = -1e30       # accept the full step
+        q, rep = g.newton(q0, opts)
+        assert rep.iters == 1
+        assert np.linalg.norm(q - (q0 + delta)) <= 1e-12 * np.linalg.norm(delta)
+    finally:
+        g.close()
+
+
 def test_rollout_frames_restart_parity():
     """Two implicit-Euler frames on the device; each frame's solution matches the
     oracle restarted from the GPU's state at the start of that frame."""
