@@ -199,6 +199,72 @@ def derivs(dec, q, qbar, qbar_dot, dt, rows=None):
     return dict(u=u, J=J, HDe=HDe, Hw=Hw, Sdd=Sdd, dJ=Sdd + Hw, HDD=HDD, Hqq=HDD / dt ** 2)
 
 
+def _act_d2(act, z):
+    """act(z), act'(z), act''(z) by their plain definitions (FP64)."""
+    if act == "tanh":
+        t = np.tanh(z)
+        s1 = 1.0 - t * t
+        return t, s1, -2.0 * t * s1
+    if act == "sin":
+        return np.sin(z), np.cos(z), -np.sin(z)
+    return z, np.ones_like(z), np.zeros_like(z)
+
+
+def decoder_uJ_vjp(dec, Q, gu, gJ):
+    """Gradient of the scalar
+
+        L = sum_s [ gu_s . u(q_s) + sum_j gJ_s[:, j] . J(q_s) e_j ]
+
+    with respect to every latent q_s and every decoder weight W_l and bias b_l, in
+    FP64.  u = D(q) and J = dD/dq are formed by first-order forward differentiation
+    (a value and r tangents per layer, Sec. 3.5's MLP); the gradient is the reverse
+    sweep of the chain rule through that computation (the backpropagation Sec. 4.4
+    builds on).  Per layer z = W x + b, zt_j = W xt_j, and for hidden layers
+    a = act(z), at_j = act'(z) zt_j; the reverse of the activation is
+        gz = act'(z) ga + act''(z) sum_j zt_j gat_j,   gzt_j = act'(z) gat_j.
+
+    Q (B, r), gu (B, N), gJ (B, N, r).  Returns gq (B, r), gW (list of (n_out, n_in)),
+    gb (list of (n_out,)).
+    """
+    W = [np.asarray(w, np.float64) for w in dec.W]
+    bb = [np.asarray(x, np.float64) for x in dec.b]
+    L = len(W)
+    Q = np.atleast_2d(np.asarray(Q, np.float64))
+    B, r = Q.shape
+    gu = np.asarray(gu, np.float64).reshape(B, -1)
+    gJ = np.asarray(gJ, np.float64).reshape(B, -1, r)
+    xs, xts, zs, zts = [], [], [], []
+    x = Q.copy()
+    xt = np.repeat(np.eye(r)[None], B, 0)          # (B, r, n): tangent j of sample s
+    for l in range(L):
+        xs.append(x)
+        xts.append(xt)
+        z = x @ W[l].T + bb[l]
+        zt = xt @ W[l].T
+        zs.append(z)
+        zts.append(zt)
+        if l < L - 1:
+            a, s1, _ = _act_d2(dec.act, z)
+            x = a
+            xt = s1[:, None, :] * zt
+    gz = gu.copy()
+    gzt = np.transpose(gJ, (0, 2, 1)).copy()       # (B, r, N)
+    gW, gb = [None] * L, [None] * L
+    gq = None
+    for l in range(L - 1, -1, -1):
+        gW[l] = gz.T @ xs[l] + np.einsum("bjo,bji->oi", gzt, xts[l])
+        gb[l] = gz.sum(0)
+        gx = gz @ W[l]
+        gxt = gzt @ W[l]
+        if l > 0:
+            _, s1, s2 = _act_d2(dec.act, zs[l - 1])
+            gz = s1 * gx + s2 * np.einsum("bjn,bjn->bn", zts[l - 1], gxt)
+            gzt = s1[:, None, :] * gxt
+        else:
+            gq = gx
+    return gq, gW, gb
+
+
 def aTH(dec, q, a):
     """(a^T H)[i,j] = sum_n a_n H[n,i,j]: the plain definition, one second-order
     jet per pair (i <= j) over all N outputs."""

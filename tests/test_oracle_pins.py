@@ -369,3 +369,86 @@ def test_newton_step_cap_and_step_tolerance():
     assert rt["converged"] and rx["converged"]
     assert np.abs(qx - qt).max() <= 2e-6 * max(1.0, np.abs(qt).max())
     assert rx["iters"] <= rt["iters"]
+
+
+# --------------------------------------------- decoder backward (u, J) ---
+
+def _uJ_loss(dec, Q, gu, gJ):
+    """L = sum_s gu_s . u(q_s) + sum_{s,j} gJ_s[:, j] . J(q_s) e_j, with u and J from
+    the hyper-dual jets (independent of the reverse sweep)."""
+    r = dec.r
+    tot = 0.0
+    for s in range(Q.shape[0]):
+        jet = oracle.decoder_jets(dec, Q[s], np.eye(r))
+        u = jet[0, :, 0]
+        J = jet[:, :, 1].T
+        tot += gu[s] @ u + np.sum(gJ[s] * J)
+    return tot
+
+
+@pytest.mark.parametrize("act", ["tanh", "sin", "linear"])
+def test_uJ_vjp_against_central_differences(act):
+    """Every latent gradient and a sample of weight / bias gradients against FP64
+    central differences of the jet-evaluated loss: h = 1e-6 on the FP64 latents,
+    h = 2^-12 on the weights and biases (stored in FP32 by the decoder, so the step
+    must be exactly representable next to them)."""
+    import copy
+    dec = tiny_net([3, 5, 6, 9], 21, act)
+    rng = np.random.default_rng(4)
+    B, r, N = 2, 3, 9
+    Q = rng.normal(0, 0.6, (B, r))
+    gu = rng.normal(size=(B, N))
+    gJ = rng.normal(size=(B, N, r))
+    gq, gW, gb = oracle.decoder_uJ_vjp(dec, Q, gu, gJ)
+    h = 1e-6
+    fd = np.zeros_like(Q)
+    for s in range(B):
+        for j in range(r):
+            Qp, Qm = Q.copy(), Q.copy()
+            Qp[s, j] += h
+            Qm[s, j] -= h
+            fd[s, j] = (_uJ_loss(dec, Qp, gu, gJ) - _uJ_loss(dec, Qm, gu, gJ)) / (2 * h)
+    assert relerr(gq, fd) < 1e-6
+    hw = np.float32(2.0 ** -12)
+    for l in range(3):
+        for (i, k) in [(0, 0), (1, 2), (dec.W[l].shape[0] - 1, dec.W[l].shape[1] - 1)]:
+            dp, dm = copy.deepcopy(dec), copy.deepcopy(dec)
+            dp.W[l][i, k] += hw
+            dm.W[l][i, k] -= hw
+            step = float(dp.W[l][i, k]) - float(dm.W[l][i, k])
+            g = (_uJ_loss(dp, Q, gu, gJ) - _uJ_loss(dm, Q, gu, gJ)) / step
+            assert abs(gW[l][i, k] - g) <= 1e-6 * max(1.0, abs(g)), (l, i, k, gW[l][i, k], g)
+        dp, dm = copy.deepcopy(dec), copy.deepcopy(dec)
+        dp.b[l][1] += hw
+        dm.b[l][1] -= hw
+        step = float(dp.b[l][1]) - float(dm.b[l][1])
+        g = (_uJ_loss(dp, Q, gu, gJ) - _uJ_loss(dm, Q, gu, gJ)) / step
+        assert abs(gb[l][1] - g) <= 1e-6 * max(1.0, abs(g))
+
+
+def test_uJ_vjp_one_hidden_layer_closed_form():
+    """u = W2 t + b2, J = W2 diag(t') W1 with t = tanh(W1 q + b1); the gradients written
+    out by hand: dL/dW2 = gu t^T + sum_j gJ_j (t' * W1 e_j)^T, dL/db2 = gu,
+    dL/dz = t' (W2^T gu) + t'' sum_j (W1 e_j) (W2^T gJ_j),
+    dL/dW1 = dL/dz q^T + sum_j (t' W2^T gJ_j) e_j^T, dL/db1 = dL/dz, dL/dq = W1^T dL/dz."""
+    r, K, N = 4, 7, 9
+    dec = tiny_net([r, K, N], 12, "tanh")
+    W1, W2 = dec.W[0].astype(np.float64), dec.W[1].astype(np.float64)
+    b1 = dec.b[0].astype(np.float64)
+    rng = np.random.default_rng(8)
+    q = rng.normal(0, .5, r)
+    gu = rng.normal(size=N)
+    gJ = rng.normal(size=(N, r))
+    z = W1 @ q + b1
+    t = np.tanh(z)
+    t1 = 1 - t ** 2
+    t2 = -2 * t * t1
+    gW2 = np.outer(gu, t) + sum(np.outer(gJ[:, j], t1 * W1[:, j]) for j in range(r))
+    gz = t1 * (W2.T @ gu) + t2 * sum(W1[:, j] * (W2.T @ gJ[:, j]) for j in range(r))
+    gW1 = np.outer(gz, q) + sum(np.outer(t1 * (W2.T @ gJ[:, j]), np.eye(r)[j]) for j in range(r))
+    gq, gW, gb = oracle.decoder_uJ_vjp(dec, q[None], gu[None], gJ[None])
+    assert relerr(gW[1], gW2) < 1e-13
+    assert relerr(gb[1], gu) < 1e-13
+    assert relerr(gW[0], gW1) < 1e-13
+    assert relerr(gb[0], gz) < 1e-13
+    assert relerr(gq[0], W1.T @ gz) < 1e-13
