@@ -234,6 +234,39 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------------- decoder training -- */
+
+/*
+ * Gradients of the decoder's first-order derivatives for fitting a decoder: the
+ * paper trains its autoencoder with backpropagation (Sec. 4.4 builds on it; Sec. 5
+ * fits the networks).  For a batch of B latents q_s the forward gives
+ *     u_s = D(q_s),   J_s = dD/dq (q_s)
+ * and the backward, given cotangents gu_s (N) and gJ_s (N x r) of a scalar loss,
+ * gives dL/dq_s, dL/dW_l and dL/db_l of L = sum_s gu_s.u_s + sum_{s,j} gJ_s[:,j].J_s e_j.
+ * The batch is carried as C = B (1 + r) columns (value and the r tangents of each
+ * sample), so every layer is one dense GEMM on the tensor cores in split BF16x3 with
+ * FP32 accumulation (forward Z = W X, reverse W^T Z̄, weights Z̄ X^T over the C
+ * columns).  The backward recomputes the forward, keeping the pre-activations of
+ * every second hidden layer and recomputing the others.
+ *
+ * Layouts: W[l] row-major widths[l+1] x widths[l] FP32, b[l] widths[l+1] FP32 (the
+ * caller's current parameters, read on every call); q B x r FP64 row-major;
+ * uJ and g_uJ (1 + r) x B x N FP32: block 0 holds u_s (row s), block 1 + j holds
+ * J_s e_j; g_q B x r FP64; g_W[l], g_b[l] like W[l], b[l] (overwritten).  All arrays
+ * must be device memory (these entries do not stage host arrays).  Calls enqueue on
+ * the context's stream and return.  Errors: INVALID_ARG (shapes, B outside
+ * 1..max_batch, host arrays), UNSUPPORTED (r > 32), OOM, CUDA.
+ */
+typedef struct dae_trainer dae_trainer;
+dae_status dae_trainer_create(dae_ctx* ctx, int n_layers, const int* widths, dae_act act,
+                              int max_batch, dae_trainer** out);
+dae_status dae_trainer_free(dae_trainer* t);
+dae_status dae_train_forward(dae_trainer* t, const float* const* W, const float* const* b, int B,
+                             const double* q, float* uJ);
+dae_status dae_train_backward(dae_trainer* t, const float* const* W, const float* const* b, int B,
+                              const double* q, const float* g_uJ, double* g_q,
+                              float* const* g_W, float* const* g_b);
+
 /* ------------------------------------------------ allocation-free variant -- */
 
 /*

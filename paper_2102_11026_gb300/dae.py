@@ -75,6 +75,10 @@ SIGNATURES = {
     "dae_profile_read": ([_vp, _vp, _vp], _i),
     "dae_launch_count": ([_vp], ctypes.c_longlong),
     "dae_selftest_bounded_waits": ([_vp], _i),
+    "dae_trainer_create": ([_vp, _i, _vp, _i, _i, ctypes.POINTER(_vp)], _i),
+    "dae_trainer_free": ([_vp], _i),
+    "dae_train_forward": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
+    "dae_train_backward": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "dae_rollout": ([_vp, _vp, _vp, _i, _vp, _vp, _i, _vp, _vp, _d, _vp,
                      ctypes.POINTER(dae_newton_opts), _vp, ctypes.POINTER(dae_newton_report)], _i),
 }
@@ -297,3 +301,59 @@ def dae_reduce_rows_noalloc(N, r, J, dJ, HDD, mdof, f_ext, z, dt, phi_dense=None
                                        _ptr(B, np.float64), stream)
     if st != 0:
         raise DaeError(st, "dae_reduce_rows_noalloc failed")
+
+
+# ------------------------------------------------------------- training --
+class Trainer:
+    """Handle of a dae_trainer (decoder training pass)."""
+
+    def __init__(self, ctx, handle, widths, act):
+        self.ctx = ctx
+        self.handle = handle
+        self.widths = list(widths)
+        self.act = act
+
+
+def _devptr_array(tensors):
+    arr = (_vp * len(tensors))()
+    for i, t in enumerate(tensors):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous()):
+            raise ValueError("trainer arrays must be contiguous float32 CUDA tensors")
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def dae_trainer_create(ctx, widths, act="tanh", max_batch=256):
+    w = (ctypes.c_int * len(widths))(*[int(x) for x in widths])
+    h = _vp()
+    _check(ctx, lib().dae_trainer_create(ctx, len(widths) - 1, w, ACT[act], int(max_batch),
+                                         ctypes.byref(h)))
+    return Trainer(ctx, h, widths, act)
+
+
+def dae_trainer_free(tr):
+    lib().dae_trainer_free(tr.handle)
+
+
+def _tensor_ptr(t, dtype):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError("expected a contiguous %s CUDA tensor" % dtype)
+    return _vp(t.data_ptr())
+
+
+def dae_train_forward(tr, W, b, q, uJ):
+    """W, b: lists of float32 CUDA tensors; q (B, r) float64; uJ (1 + r, B, N) float32."""
+    import torch
+    B = int(q.shape[0])
+    _check(tr.ctx, lib().dae_train_forward(tr.handle, _devptr_array(W), _devptr_array(b), B,
+                                           _tensor_ptr(q, torch.float64), _tensor_ptr(uJ, torch.float32)))
+
+
+def dae_train_backward(tr, W, b, q, g_uJ, g_q, g_W, g_b):
+    import torch
+    B = int(q.shape[0])
+    _check(tr.ctx, lib().dae_train_backward(
+        tr.handle, _devptr_array(W), _devptr_array(b), B, _tensor_ptr(q, torch.float64),
+        _tensor_ptr(g_uJ, torch.float32),
+        _tensor_ptr(g_q, torch.float64) if g_q is not None else None,
+        _devptr_array(g_W), _devptr_array(g_b)))
