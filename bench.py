@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="newton", choices=["newton", "train"],
+                    help="train: fit a re-seeded small-workload decoder to 4096 rollout poses "
+                         "(batch 256, 100 Adam steps) and time the library's backward pass")
     return ap.parse_args()
 
 
@@ -402,10 +405,128 @@ def load_traffic(workload, prec):
     return None
 
 
+# ------------------------------------------------------------------ train --
+def train_flops(widths, B):
+    """Algorithmic flops of one backward call at batch B: weight gradients of every
+    layer, W^T Z̄ for layers 2..L, and the forward of the hidden layers it needs, each
+    2 n_out n_in C with C = B (1 + r) columns."""
+    P = [widths[l] * widths[l + 1] for l in range(len(widths) - 1)]
+    C = B * (1 + widths[0])
+    return 2.0 * C * (sum(P) + sum(P[1:]) + sum(P[:-1]))
+
+
+def run_train(args):
+    import torch
+    from paper_2102_11026_gb300 import dae, synth
+    from paper_2102_11026_gb300.autograd import decoder_uJ
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = synth.small()
+    d, m = wl.dec, wl.mesh
+    r, n = d.r, wl.cub_tets.size
+    stream = torch.cuda.current_stream()
+    ctx = dae.dae_create(torch.cuda.current_device(), stream.cuda_stream)
+    # 4096 poses: 64 implicit-Euler rollouts of 64 frames of the small workload from
+    # seeded start states
+    dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, "bf16x3")
+    mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass, m.material, m.E, m.nu)
+    opts = dae.dae_default_newton_opts()
+    poses = []
+    for k in range(64):
+        st = synth.make_state(r, 1000 + k)
+        qh, qdh = st.qbar.copy(), st.qbar_dot.copy()
+        traj = np.zeros((64, r))
+        dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, frame_weights(wl, 64, 1000 + k), 64, qh, qdh,
+                        st.dt, wl.f_ext, opts, traj)
+        poses.append(traj)
+    dae.dae_free_decoder(dec)
+    dae.dae_free_mesh(mesh)
+    poses = torch.as_tensor(np.concatenate(poses), device="cuda")
+    Bt = 256
+    tr = dae.dae_trainer_create(ctx, d.widths, d.act, max_batch=Bt)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    teacher = []
+    for w, x in zip(d.W, d.b):
+        teacher += [dev(w), dev(x)]
+    st_dec = synth.make_decoder(d.widths, 77, d.act)
+    params = []
+    for w, x in zip(st_dec.W, st_dec.b):
+        params += [dev(w).requires_grad_(True), dev(x).requires_grad_(True)]
+    with torch.no_grad():
+        tU, tJ = [], []
+        for i in range(0, poses.shape[0], Bt):
+            u, J = decoder_uJ(tr, poses[i:i + Bt], teacher)
+            tU.append(u)
+            tJ.append(J)
+        tU, tJ = torch.cat(tU), torch.cat(tJ)
+    opt = torch.optim.Adam(params, lr=1e-3)
+    n_steps = 100
+    losses = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for step in range(n_steps):
+        i = (step * Bt) % poses.shape[0]
+        u, J = decoder_uJ(tr, poses[i:i + Bt], params)
+        loss = ((u - tU[i:i + Bt]) ** 2).mean() + ((J - tJ[i:i + Bt]) ** 2).mean()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    e1.record()
+    torch.cuda.synchronize()
+    fit_ms = e0.elapsed_time(e1)
+    losses = [float(x) for x in losses]
+    # the backward pass alone, timed over K calls after W warm-up calls
+    W_, b_ = [p.detach() for p in params[0::2]], [p.detach() for p in params[1::2]]
+    qb = poses[:Bt].contiguous()
+    g_uJ = torch.randn((1 + r, Bt, d.n_out), device="cuda")
+    gq = torch.empty((Bt, r), dtype=torch.float64, device="cuda")
+    gW = [torch.empty_like(w) for w in W_]
+    gb = [torch.empty_like(x) for x in b_]
+    for _ in range(args.warmup):
+        dae.dae_train_backward(tr, W_, b_, qb, g_uJ, gq, gW, gb)
+    torch.cuda.synchronize()
+    l0 = dae.dae_launch_count(ctx)
+    e0.record()
+    for _ in range(args.steps):
+        dae.dae_train_backward(tr, W_, b_, qb, g_uJ, gq, gW, gb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = dae.dae_launch_count(ctx) - l0
+    flops = train_flops(d.widths, Bt)
+    peaks, src = load_peaks()
+    tf = flops / (ms / 1e3) / 1e12
+    dae.dae_trainer_free(tr)
+    dae.dae_destroy(ctx)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "decoder backward-pass TFLOP/s", "value": tf, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+        "data": "synthetic",
+        "config": {"workload": "small decoder 5-64-256-1024-3000 tanh: backward of u and J w.r.t. "
+                               "latents, weights and biases, batch 256 (1536 columns)",
+                   "poses": "4096 from 64 rollouts x 64 frames of the small workload",
+                   "gflop_per_backward": flops / 1e9},
+        "roofline": {"bound": "tensor", "achieved": tf * 3, "peak": peaks["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": tf * 3 / peaks["bf16_tflops"], "traffic": None,
+                     "note": "achieved counts the three BF16 MMAs of each split-BF16x3 product; "
+                             "peak: %s bf16 burst" % src},
+        "fit": {"steps": n_steps, "batch": Bt, "loss_first": losses[0], "loss_last": losses[-1],
+                "ms_per_adam_step": fit_ms / n_steps},
+        "gpu_launches": int(launches),
+    }))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "train":
+        run_train(args)
     else:
         run_ours(args)
 
