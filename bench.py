@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="newton", choices=["newton", "train"],
+    ap.add_argument("--n-strings", type=int, default=320)
+    ap.add_argument("--mode", default="newton", choices=["newton", "train", "strings"],
                     help="train: fit a re-seeded small-workload decoder to 4096 rollout poses "
                          "(batch 256, 100 Adam steps) and time the library's backward pass")
     return ap.parse_args()
@@ -521,12 +522,135 @@ def run_train(args):
     }))
 
 
+# -------------------------------------------------------- grouped strings --
+def run_strings(args):
+    """One implicit-Euler Newton step of every string of the substructured model
+    (320 independent strings, depth-8 decoders) per bench step: the grouped entry point
+    (all strings in one graph) against per-string dae_newton_step calls."""
+    import torch
+    from paper_2102_11026_gb300 import dae, synth
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    wls = synth.strings(args.n_strings)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    ctx = dae.dae_create(0, stream.cuda_stream)
+    loaded = []
+    for wl in wls:
+        d, m = wl.dec, wl.mesh
+        loaded.append((dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, args.prec),
+                       dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass,
+                                         m.material, m.E, m.nu)))
+    dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+    n = len(wls)
+    R = 32
+    q0_all = torch.zeros(n, R, dtype=torch.float64, device="cuda")
+    for i, wl in enumerate(wls):
+        q0_all[i, :wl.dec.r] = dev(synth.newton_start(wl.state), torch.float64)
+    q_all = q0_all.clone()
+    systems = []
+    for i, (wl, (dec, mesh)) in enumerate(zip(wls, loaded)):
+        systems.append(dict(dec=dec, mesh=mesh, cub_tets=dev(wl.cub_tets, torch.int32),
+                            cub_w=dev(wl.cub_w, torch.float32), q=q_all[i],
+                            qbar=dev(wl.state.qbar, torch.float64),
+                            qbar_dot=dev(wl.state.qbar_dot, torch.float64)))
+    dt = wls[0].state.dt
+    opts = dae.dae_default_newton_opts()
+    opts.max_iter = 5
+    W, K = args.warmup, args.steps
+    with torch.cuda.stream(stream):
+        q_all.copy_(q0_all)
+        reps = dae.dae_newton_step_batched(ctx, systems, dt, opts)
+        evals = [rp.evals for rp in reps]
+        for _ in range(W):
+            q_all.copy_(q0_all)
+            dae.dae_newton_step_batched(ctx, systems, dt, opts, want_reports=False)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(K):
+            q_all.copy_(q0_all)
+            dae.dae_newton_step_batched(ctx, systems, dt, opts, want_reports=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        clocks = sampler.stop()
+        q_grouped = q_all.cpu().numpy().copy()
+        # per-string launches: the same steps through dae_newton_step, one string at a time
+        Kp = max(1, min(K, 3))
+        for y in systems[:4]:
+            dae.dae_newton_step(ctx, y["dec"], y["mesh"], y["cub_tets"], y["cub_w"], y["q"],
+                                y["qbar"], y["qbar_dot"], dt, None, opts, want_report=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(Kp):
+            q_all.copy_(q0_all)
+            for y in systems:
+                dae.dae_newton_step(ctx, y["dec"], y["mesh"], y["cub_tets"], y["cub_w"], y["q"],
+                                    y["qbar"], y["qbar_dot"], dt, None, opts, want_report=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_single = ev0.elapsed_time(ev1) / Kp
+        q_single = q_all.cpu().numpy()
+    diff = 0.0
+    for i, wl in enumerate(wls):
+        r = wl.dec.r
+        step = np.linalg.norm(q_grouped[i, :r] - q0_all[i, :r].cpu().numpy())
+        diff = max(diff, float(np.linalg.norm(q_grouped[i, :r] - q_single[i, :r]) / max(step, 1e-30)))
+    # grouped launches per step: copy in, the graph (begin, per evaluation 12 kernels, end),
+    # copy out
+    max_ev = max(evals)
+    launches_step = 2 + 2 + 12 * max_ev
+    for dec, mesh in loaded:
+        dae.dae_free_decoder(dec)
+        dae.dae_free_mesh(mesh)
+    dae.dae_destroy(ctx)
+    ev_step = float(sum(evals))
+    value = ev_step * K / (ms / 1e3)
+    params = [sum(w.size for w in wl.dec.W) for wl in wls]
+    bpe = {"bf16x3": 4, "bf16": 2, "tf32": 4}[args.prec]
+    # every evaluation of a string streams its decoder's weights twice (forward chain and
+    # transposed reverse chain)
+    bytes_step = float(sum(e * 2 * p * bpe for e, p in zip(evals, params)))
+    peaks, peak_src = load_peaks()
+    achieved = bytes_step / (ms / K / 1e3) / 1e9
+    line = {
+        "metric": "string Newton iterations/s (320 strings, grouped)", "value": value,
+        "unit": "iterations/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": "%d strings, depth-8 decoders r-32-64-128-256-256-256-256-3V, "
+                               "r ~ U{3..15}, V ~ U[200,2000], 2x2xV/4 grids, StVK, 32 cubature "
+                               "tets each; one implicit-Euler Newton step of every string per "
+                               "step" % n, "params_total": int(sum(params)),
+                   "evals_per_step": ev_step, "max_evals": max_ev,
+                   "l2": "weights %.2f GB > L2" % (sum(params) * bpe / 1e9),
+                   "synth_seconds": round(t_gen, 1)},
+        "per_string_launches": {"ms_per_step": ms_single, "value": ev_step / (ms_single / 1e3),
+                                "grouped_speedup": ms_single / (ms / K),
+                                "max_rel_diff_vs_grouped": diff},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "whole grouped step (weights streamed twice per string evaluation)",
+                     "peak_source": "%s hbm_gbs" % peak_src},
+        "clocks": clocks, "gpu_launches": int(launches_step * K),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "train":
         run_train(args)
+    elif args.mode == "strings":
+        run_strings(args)
     else:
         run_ours(args)
 

@@ -234,6 +234,49 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------------ grouped systems -- */
+
+/*
+ * One independent reduced system of a grouped Newton step: its own decoder, mesh,
+ * cubature set, state and external force (a domain of a substructured model with
+ * no coupling between domains; the puffer ball's 320 strings, each with its own
+ * depth-8 decoder, in the paper's Sec. 6 "Extensions and More Results").  Arrays as
+ * in dae_newton_step (host or device memory):
+ *   q          in: first iterate; out: solution (r FP64)
+ *   qbar, qbar_dot  r FP64;  cub_tets, cub_w  n_cub each;  f_ext  N FP32 or NULL
+ */
+typedef struct dae_system {
+    const dae_decoder* dec;
+    const dae_mesh* mesh;
+    int n_cub;
+    const int* cub_tets;
+    const float* cub_w;
+    double* q;
+    const double* qbar;
+    const double* qbar_dot;
+    const float* f_ext;
+} dae_system;
+
+/*
+ * One implicit-Euler Newton step (as dae_newton_step) of n_sys independent systems
+ * at once: each kernel of a Newton evaluation runs once for all systems that are
+ * still iterating (the decoder layers of all systems as the stages of one
+ * persistent tensor-core launch), and the evaluation loop repeats on the device
+ * until every system is done.  Each system keeps its own Newton control (tol,
+ * line search, max_evals from opts, shared by all systems).
+ *   Requirements: every decoder on ctx, in one tensor-core precision (TF32, BF16
+ *   or BF16X3), appearing in at most one system (workspaces are per decoder).
+ *   reports  n_sys reports or NULL (then the call does not synchronize when every
+ *            array is on the device).
+ * The launch plan and graph are cached while the systems' decoders, meshes, cubature
+ * counts, f_ext presence, dt and opts stay the same.
+ * Errors: INVALID_ARG, UNSUPPORTED (FP32 decoder), CUDA; with reports, the first
+ * failing system's INVERTED / NONFINITE / SINGULAR status.
+ */
+dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* systems,
+                                   double dt, const dae_newton_opts* opts,
+                                   dae_newton_report* reports);
+
 /* ------------------------------------------------------- decoder training -- */
 
 /*

@@ -15,6 +15,7 @@
 using namespace dae;
 
 static std::atomic<unsigned long long> g_mesh_ids{1};
+static std::atomic<unsigned long long> g_dec_ids{1};
 
 #define DAE_VERSION 10000
 
@@ -354,22 +355,60 @@ void fill_rev_args(const dae_decoder* d, int l, FwdArgs& a) {
     }
 }
 
+// Chain job of hidden forward layer l (whole K loop per 128-row tile).
+void make_fwd_job(const dae_decoder* d, int l, ChainJob& j) {
+    const Layer& ly = d->layers[l];
+    memset(&j, 0, sizeof j);
+    memcpy(j.tm, ly.tm, sizeof j.tm);
+    fill_fwd_args(d, l, j.a);
+    j.tiles = ly.m_pad / 128;
+    j.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
+    j.split = 1;
+    j.rep = 1;
+}
+
+// Chain job of the reverse pass through hidden layer l.
+void make_rev_job(const dae_decoder* d, int l, ChainJob& j) {
+    const Layer& ly = d->layers[l];
+    memset(&j, 0, sizeof j);
+    memcpy(j.tm, ly.tmR, sizeof j.tm);
+    fill_rev_args(d, l, j.a);
+    j.tiles = ly.mT_pad / 128;
+    j.nk = ly.ldT / (d->prec == DAE_TF32 ? 32 : 64);
+    j.split = 1;
+    j.rep = 1;
+}
+
+// Chain job of the output layer (outputs and fused row reductions per call).
+void make_out_job(const dae_decoder* d, const Outs& o, double dt, double h, ChainJob& job) {
+    const Layer& ly = d->layers[d->L - 1];
+    memset(&job, 0, sizeof job);
+    memcpy(job.tm, ly.tm, sizeof job.tm);
+    fill_fwd_args(d, d->L - 1, job.a);
+    job.a.inv_h = 1.0 / h; job.a.inv_h2 = 1.0 / (h * h); job.a.inv_h3 = 1.0 / (h * h * h);
+    job.a.inv_dt2 = 1.0 / (dt * dt);
+    job.a.u = o.u; job.a.J = o.J; job.a.dJ = o.dJ; job.a.HDD = o.HDD; job.a.Hqq = o.Hqq;
+    if (o.row_part) {
+        job.a.row_part = o.row_part; job.a.row_stride = o.row_stride;
+        job.a.mdof = o.mdof; job.a.f_ext = o.f_ext; job.a.zvec = d->ws.zvec; job.a.dt = dt;
+        job.a.a_out = o.a_out;
+    }
+    job.tiles = ly.m_pad / 128;
+    job.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
+    job.split = 1;
+    job.rep = 1;
+}
+
 // Job lists of the persistent layer-chain kernel (both directions).
 dae_status build_chains(dae_decoder* d) {
     dae_ctx* ctx = d->ctx;
     Workspace& w = d->ws;
     const int L = d->L, G = ctx->sm_count;
-    const int KB = d->prec == DAE_TF32 ? 32 : 64;
     std::vector<ChainJob> fj(L - 1), rj(L - 1);
     size_t part = 1, cnt_f = 0, cnt_r = 0;
     for (int l = 0; l < L - 1; ++l) {
-        const Layer& ly = d->layers[l];
         ChainJob& j = fj[l];
-        memset(&j, 0, sizeof j);
-        memcpy(j.tm, ly.tm, sizeof j.tm);
-        fill_fwd_args(d, l, j.a);
-        j.tiles = ly.m_pad / 128;
-        j.nk = ly.ld / KB;
+        make_fwd_job(d, l, j);
         chain_plan(j, G);
         j.cnt_off = (int)cnt_f;
         cnt_f += j.tiles;
@@ -377,13 +416,8 @@ dae_status build_chains(dae_decoder* d) {
     }
     for (int i = 0; i < L - 1; ++i) {
         const int l = L - 2 - i;
-        const Layer& ly = d->layers[l];
         ChainJob& j = rj[i];
-        memset(&j, 0, sizeof j);
-        memcpy(j.tm, ly.tmR, sizeof j.tm);
-        fill_rev_args(d, l, j.a);
-        j.tiles = ly.mT_pad / 128;
-        j.nk = ly.ldT / KB;
+        make_rev_job(d, l, j);
         chain_plan(j, G);
         j.cnt_off = (int)cnt_r;
         cnt_r += j.tiles;
@@ -437,22 +471,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         // output layer: a one-job persistent launch, its epilogue (outputs and the fused
         // row reductions) overlapping the next tile's loads and MMAs
         ChainJob job;
-        memset(&job, 0, sizeof job);
-        const Layer& ly = d->layers[L - 1];
-        memcpy(job.tm, ly.tm, sizeof job.tm);
-        fill_fwd_args(d, L - 1, job.a);
-        job.a.inv_h = 1.0 / h; job.a.inv_h2 = 1.0 / (h * h); job.a.inv_h3 = 1.0 / (h * h * h);
-        job.a.inv_dt2 = 1.0 / (dt * dt);
-        job.a.u = o.u; job.a.J = o.J; job.a.dJ = o.dJ; job.a.HDD = o.HDD; job.a.Hqq = o.Hqq;
-        if (o.row_part) {
-            job.a.row_part = o.row_part; job.a.row_stride = o.row_stride;
-            job.a.mdof = o.mdof; job.a.f_ext = o.f_ext; job.a.zvec = w.zvec; job.a.dt = dt;
-            job.a.a_out = o.a_out;
-        }
-        job.tiles = ly.m_pad / 128;
-        job.nk = ly.ld / (d->prec == DAE_TF32 ? 32 : 64);
-        job.split = 1;
-        job.rep = 1;
+        make_out_job(d, o, dt, h, job);
         // stream the output layer's tiles x nk k-blocks in equal ranges per CTA when the
         // tiles do not divide evenly over the grid
         job.stream = (job.tiles > ctx->sm_count) ? 1 : 0;
@@ -539,6 +558,22 @@ dae_status ensure_gram(dae_decoder* d, const dae_mesh* m) {
     return DAE_OK;
 }
 
+dae_status ensure_pext_bufs(dae_decoder* d) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    if (w.pext) return DAE_OK;
+    const Layer& top = d->layers[d->L - 1];
+    const int K = top.n_in, N = top.n_out;
+    const int kb = (K + 1023) / 1024;
+    const int splits = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * ctx->sm_count + kb - 1) / kb)));
+    TRY(dmalloc(ctx, &w.pext, (size_t)K + 4));
+    TRY(dmalloc(ctx, &w.fext_prev, (size_t)N));
+    TRY(dmalloc(ctx, &w.pext_flag, 1));
+    TRY(dmalloc(ctx, &w.pext_part, (size_t)splits * K));
+    w.pext_splits = splits;
+    return DAE_OK;
+}
+
 // W_L^T f_ext, recomputed on the device only when f_ext differs from the cached copy.
 dae_status prepare_pext(dae_decoder* d, const float* f_ext_dev) {
     dae_ctx* ctx = d->ctx;
@@ -546,15 +581,7 @@ dae_status prepare_pext(dae_decoder* d, const float* f_ext_dev) {
     if (!f_ext_dev) return DAE_OK;
     const Layer& top = d->layers[d->L - 1];
     const int K = top.n_in, N = top.n_out;
-    const int kb = (K + 1023) / 1024;
-    const int splits = std::max(1, std::min(128, std::min((N + 63) / 64, (4 * ctx->sm_count + kb - 1) / kb)));
-    if (!w.pext) {
-        TRY(dmalloc(ctx, &w.pext, (size_t)K + 4));
-        TRY(dmalloc(ctx, &w.fext_prev, (size_t)N));
-        TRY(dmalloc(ctx, &w.pext_flag, 1));
-        TRY(dmalloc(ctx, &w.pext_part, (size_t)splits * K));
-        w.pext_splits = splits;
-    }
+    TRY(ensure_pext_bufs(d));
     if (!w.pext_valid) {
         const int one = 1;
         CU(ctx, cudaMemcpyAsync(w.pext_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -984,6 +1011,327 @@ dae_status validate_cub(dae_ctx* ctx, const dae_mesh* m, int n_cub, const int* c
     return DAE_OK;
 }
 
+// ------------------------------------------------------- batched systems --
+// One Newton step of many independent systems (dae_newton_step_batched): every
+// kernel of an evaluation runs once for all systems (grouped launches), inside one
+// graph whose evaluation loop runs while any system is not done.
+struct BatchKey {
+    unsigned long long dec_id, mesh_id;
+    const void* cub_tets; const void* cub_w; const void* fe_w; const void* G; const void* pext;
+    int n_cub, has_fext;
+};
+
+struct BatchPlan {
+    std::vector<BatchKey> key;
+    double dt = 0;
+    dae_newton_opts opts;
+    int prec = -1;
+    int n = 0;
+    unsigned long long epoch = 0;
+    // device argument arrays (one allocation)
+    char* dev = nullptr;
+    SeedArgs* seed = nullptr; CubArgs* cub = nullptr; XyArgs* xy = nullptr; WtaArgs* wta = nullptr;
+    PrepArgs* prep = nullptr; ColsumArgs* cs = nullptr; DsumArgs* ds = nullptr; CtlArgs* ctl = nullptr;
+    FrameArgs* frame = nullptr;
+    double* q0 = nullptr; double* qout = nullptr;   // [n][kMaxR]
+    NewtonState* ns_out = nullptr;                  // [n] report copies
+    ChainJob* jobs = nullptr; int* stage_off = nullptr;
+    GridBar* gb = nullptr;
+    struct Chain { size_t job0; size_t st0; int n_stages; int Cp; };
+    std::vector<Chain> fwd, rev;
+    int max_elems = 0, max_cub = 0, max_K = 0, max_splits = 1, max_ld = 0, max_ent = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t staged = nullptr;   // host staging buffer free again
+};
+
+void free_batch(dae_ctx* ctx) {
+    BatchPlan* b = (BatchPlan*)ctx->batch;
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->dev) cudaFree(b->dev);
+    if (b->staged) cudaEventDestroy(b->staged);
+    delete b;
+    ctx->batch = nullptr;
+}
+
+dae_status ensure_pinned(dae_ctx* ctx, size_t bytes) {
+    if (ctx->pinned_bytes >= bytes) return DAE_OK;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    const size_t nb = std::max(bytes, (size_t)1 << 20);
+    CU(ctx, cudaHostAlloc(&ctx->pinned, nb, cudaHostAllocDefault));
+    ctx->pinned_bytes = nb;
+    return DAE_OK;
+}
+
+// Grouped chain launches: stage t of a chain holds layer t (forward) or reverse job t
+// of each system of a group of at most kMaxGroupJobs systems.  B-operand maps are
+// re-encoded with the launch's column count as box height (rows past a system's own
+// columns read as zero).
+dae_status batch_chain_jobs(dae_ctx* ctx, const std::vector<dae_decoder*>& ds, bool fwd,
+                            const std::vector<Outs>& outs, double dt, double h,
+                            std::vector<ChainJob>& jobs, std::vector<int>& stage_off,
+                            std::vector<BatchPlan::Chain>& chains) {
+    const int n = (int)ds.size();
+    for (int g0 = 0; g0 < n; g0 += kMaxGroupJobs) {
+        const int g1 = std::min(n, g0 + kMaxGroupJobs);
+        int CP = 16, n_st = 0;
+        for (int i = g0; i < g1; ++i) {
+            CP = std::max(CP, fwd ? ds[i]->ws.Cp : ds[i]->ws.Cb);
+            n_st = std::max(n_st, fwd ? ds[i]->L : ds[i]->L - 1);
+        }
+        if (CP > 112) return fail(ctx, DAE_ERR_UNSUPPORTED, "column count %d too large", CP);
+        BatchPlan::Chain c;
+        c.job0 = jobs.size();
+        c.st0 = stage_off.size();
+        c.n_stages = n_st;
+        c.Cp = CP;
+        for (int t = 0; t < n_st; ++t) {
+            stage_off.push_back((int)(jobs.size() - c.job0));
+            int base = 0;
+            for (int i = g0; i < g1; ++i) {
+                const dae_decoder* d = ds[i];
+                const Workspace& w = d->ws;
+                const int L = d->L;
+                ChainJob j;
+                if (fwd) {
+                    if (t >= L) continue;
+                    if (t == L - 1) make_out_job(d, outs[i], dt, h, j);
+                    else make_fwd_job(d, t, j);
+                    if (w.Cp != CP) {
+                        const Layer& ly = d->layers[t];
+                        const bool f32 = d->prec == DAE_TF32;
+                        const int buf = t & 1;
+                        bool ok = make_tmap(&j.tm[2], f32 ? (const void*)w.X[buf] : (const void*)w.Xh[buf],
+                                            f32, ly.ld, w.Cp, CP);
+                        if (d->prec == DAE_BF16X3) ok = ok && make_tmap(&j.tm[3], w.Xl[buf], false, ly.ld, w.Cp, CP);
+                        else j.tm[3] = j.tm[2];
+                        if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "tensor map encoding failed");
+                    }
+                } else {
+                    if (t >= L - 1) continue;
+                    const int l = L - 2 - t;
+                    make_rev_job(d, l, j);
+                    if (w.Cb != CP) {
+                        const Layer& ly = d->layers[l];
+                        const bool f32 = d->prec == DAE_TF32;
+                        const int gb = (L - 2 - l) & 1;
+                        bool ok = make_tmap(&j.tm[2], f32 ? (const void*)w.G32[gb] : (const void*)w.Gh[gb],
+                                            f32, ly.ldT, w.Cb, CP);
+                        if (d->prec == DAE_BF16X3) ok = ok && make_tmap(&j.tm[3], w.Gl[gb], false, ly.ldT, w.Cb, CP);
+                        else j.tm[3] = j.tm[2];
+                        if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "tensor map encoding failed");
+                    }
+                }
+                j.a.ns = w.ns;
+                j.item_base = base;
+                base += j.tiles;
+                jobs.push_back(j);
+            }
+        }
+        stage_off.push_back((int)(jobs.size() - c.job0));
+        chains.push_back(c);
+    }
+    return DAE_OK;
+}
+
+// Argument arrays, chain jobs and the graph of one batch (cached while the systems'
+// decoders, meshes, staging buffers and the options stay the same).
+dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder*>& ds,
+                       const std::vector<const dae_mesh*>& ms, const std::vector<int>& ncub,
+                       const std::vector<int>& hasf, double dt, const dae_newton_opts& opts) {
+    const int n = (int)ds.size();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (b->dev) cudaFree(b->dev);
+    b->dev = nullptr;
+    b->fwd.clear();
+    b->rev.clear();
+    const double h = opts.h_cs;
+    std::vector<SeedArgs> seed(n); std::vector<CubArgs> cub(n); std::vector<XyArgs> xy(n);
+    std::vector<WtaArgs> wta(n); std::vector<PrepArgs> prep(n); std::vector<ColsumArgs> cs(3 * n);
+    std::vector<DsumArgs> dsum(n); std::vector<CtlArgs> ctl(n); std::vector<FrameArgs> frame(n);
+    std::vector<Outs> outs(n);
+    b->max_elems = b->max_cub = b->max_K = b->max_ld = b->max_ent = 0;
+    b->max_splits = 1;
+    for (int i = 0; i < n; ++i) {
+        dae_decoder* d = ds[i];
+        const dae_mesh* m = ms[i];
+        Workspace& w = d->ws;
+        const int r = d->r, L = d->L, N = d->N;
+        const int ob = out_bf16_of(d->prec);
+        const int ld0 = (int)round_up(r, kKPad);
+        seed[i] = SeedArgs{w.ns, w.qbar, w.qbar_dot, dt, h, r, w.Cp, ld0, w.X[0], w.Xh[0], w.Xl[0],
+                           d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec};
+        b->max_elems = std::max(b->max_elems, w.Cp * ld0);
+        Outs& o = outs[i];
+        o.u = w.u; o.J = w.J; o.dJ = w.dJ; o.HDD = w.HDD;
+        o.row_part = w.row_part; o.row_stride = w.row_stride;
+        o.mdof = m->mdof; o.f_ext = hasf[i] ? w.f_ext : nullptr; o.a_out = w.a;
+        CubArgs& ca = cub[i];
+        memset(&ca, 0, sizeof ca);
+        ca.w_stride = ncub[i];
+        ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
+        ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu;
+        ca.lam = (float)m->lam; ca.cub_tets = w.cub_tets; ca.cub_w = w.cub_w; ca.n_cub = ncub[i];
+        ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
+        ca.stride = w.cub_stride; ca.ns = w.ns; ca.eval_flag = w.eval_flag;
+        b->max_cub = std::max(b->max_cub, ncub[i]);
+        const Layer& top = d->layers[L - 1];
+        const int K = top.n_in;
+        const int kb = (K + 1023) / 1024;
+        const bool gram = w.G && w.G_mesh == m->id;
+        WtaArgs& wa = wta[i];
+        memset(&wa, 0, sizeof wa);
+        wa.fe_w = w.fe_w; wa.fe_dof = w.fe_dof; wa.n_pairs = 12 * ncub[i]; wa.dt2 = dt * dt;
+        wa.Wp = top.W; wa.ldp = top.ld; wa.K = K;
+        memset(&xy[i], 0, sizeof xy[i]);
+        if (gram) {
+            wa.W = w.G; wa.ld = w.ldG; wa.N = K; wa.a = w.xy;
+            wa.pext = hasf[i] ? w.pext : nullptr;
+            wa.pext_scale = (float)(-dt * dt);
+            xy[i] = XyArgs{w.X[(L - 1) & 1], top.ld, K, r, w.zvec, h, w.xy, w.ns};
+        } else {
+            wa.W = top.W; wa.ld = top.ld; wa.N = N; wa.a = w.a;
+        }
+        wa.nsplit_dense = std::max(1, std::min(128, std::min((wa.N + 63) / 64, (4 * ctx->sm_count + kb - 1) / kb)));
+        wa.nsplit_pairs = std::max(1, std::min(kMaxPairSplits, (wa.n_pairs + 15) / 16));
+        wa.part = w.bwd_part[0]; wa.ns = w.ns;
+        const int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0);
+        b->max_K = std::max(b->max_K, K);
+        b->max_splits = std::max(b->max_splits, in_split);
+        PrepArgs& pa = prep[i];
+        memset(&pa, 0, sizeof pa);
+        pa.a.n_o = d->widths[L - 1]; pa.a.r = r;
+        pa.a.in_part = w.bwd_part[0]; pa.a.in_split = in_split; pa.a.in_ncol = 1;
+        pa.a.S1 = w.S1[L - 2]; pa.a.T = w.T[L - 2]; pa.a.ns = w.ns;
+        pa.Cb = w.Cb; pa.ld = d->layers[L - 2].ldT;
+        pa.g32 = w.G32[0]; pa.gh = w.Gh[0]; pa.gl = w.Gl[0];
+        pa.out_f32 = (d->prec == DAE_TF32) ? 2 : 0; pa.out_bf16 = ob;
+        b->max_ld = std::max(b->max_ld, pa.ld);
+        AsmArgs aa;
+        memset(&aa, 0, sizeof aa);
+        aa.r = r; aa.dt = dt; aa.h = h;
+        aa.row_part = w.row_part; aa.n_row_blocks = w.n_row_blocks; aa.row_stride = w.row_stride;
+        aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = ncub[i];
+        aa.cub_stride = w.cub_stride;
+        aa.bwd_part = w.bwd_part[1]; aa.bwd_split = 1;
+        aa.red = w.red; aa.ns = w.ns; aa.control = 1;
+        aa.tol = opts.tol; aa.c_armijo = opts.c_armijo; aa.max_iter = opts.max_iter;
+        aa.max_step = opts.max_step; aa.xtol = opts.xtol;
+        aa.max_halvings = opts.max_halvings; aa.max_evals = opts.max_evals;
+        aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+        assemble_parts(aa, &cs[3 * i], dsum[i], ctl[i]);
+        for (int k = 0; k < 3; ++k) b->max_ent = std::max(b->max_ent, cs[3 * i + k].n_ent);
+    }
+    std::vector<ChainJob> jobs;
+    std::vector<int> stage_off;
+    TRY(batch_chain_jobs(ctx, ds, true, outs, dt, h, jobs, stage_off, b->fwd));
+    TRY(batch_chain_jobs(ctx, ds, false, outs, dt, h, jobs, stage_off, b->rev));
+    // one device allocation for everything the graph reads
+    size_t off = 0;
+    auto place = [&](size_t bytes) { size_t o = off; off += round_up(bytes, 256); return o; };
+    const size_t o_seed = place(n * sizeof(SeedArgs)), o_cub = place(n * sizeof(CubArgs));
+    const size_t o_xy = place(n * sizeof(XyArgs)), o_wta = place(n * sizeof(WtaArgs));
+    const size_t o_prep = place(n * sizeof(PrepArgs)), o_cs = place(3 * n * sizeof(ColsumArgs));
+    const size_t o_ds = place(n * sizeof(DsumArgs)), o_ctl = place(n * sizeof(CtlArgs));
+    const size_t o_fr = place(n * sizeof(FrameArgs));
+    const size_t o_q0 = place((size_t)n * kMaxR * sizeof(double));
+    const size_t o_qo = place((size_t)n * kMaxR * sizeof(double));
+    const size_t o_ns = place((size_t)n * sizeof(NewtonState));
+    const size_t o_jobs = place(jobs.size() * sizeof(ChainJob));
+    const size_t o_st = place(stage_off.size() * sizeof(int));
+    const size_t o_gb = place(sizeof(GridBar));
+    CU(ctx, cudaMalloc(&b->dev, off));
+    char* D = b->dev;
+    b->seed = (SeedArgs*)(D + o_seed); b->cub = (CubArgs*)(D + o_cub); b->xy = (XyArgs*)(D + o_xy);
+    b->wta = (WtaArgs*)(D + o_wta); b->prep = (PrepArgs*)(D + o_prep); b->cs = (ColsumArgs*)(D + o_cs);
+    b->ds = (DsumArgs*)(D + o_ds); b->ctl = (CtlArgs*)(D + o_ctl); b->frame = (FrameArgs*)(D + o_fr);
+    b->q0 = (double*)(D + o_q0); b->qout = (double*)(D + o_qo); b->ns_out = (NewtonState*)(D + o_ns);
+    b->jobs = (ChainJob*)(D + o_jobs); b->stage_off = (int*)(D + o_st); b->gb = (GridBar*)(D + o_gb);
+    for (int i = 0; i < n; ++i)
+        frame[i] = FrameArgs{ds[i]->ws.ns, b->q0 + (size_t)i * kMaxR, b->qout + (size_t)i * kMaxR, ds[i]->r};
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    CU(ctx, up(b->seed, seed.data(), n * sizeof(SeedArgs)));
+    CU(ctx, up(b->cub, cub.data(), n * sizeof(CubArgs)));
+    CU(ctx, up(b->xy, xy.data(), n * sizeof(XyArgs)));
+    CU(ctx, up(b->wta, wta.data(), n * sizeof(WtaArgs)));
+    CU(ctx, up(b->prep, prep.data(), n * sizeof(PrepArgs)));
+    CU(ctx, up(b->cs, cs.data(), 3 * n * sizeof(ColsumArgs)));
+    CU(ctx, up(b->ds, dsum.data(), n * sizeof(DsumArgs)));
+    CU(ctx, up(b->ctl, ctl.data(), n * sizeof(CtlArgs)));
+    CU(ctx, up(b->frame, frame.data(), n * sizeof(FrameArgs)));
+    CU(ctx, up(b->jobs, jobs.data(), jobs.size() * sizeof(ChainJob)));
+    CU(ctx, up(b->stage_off, stage_off.data(), stage_off.size() * sizeof(int)));
+    CU(ctx, cudaMemset(b->gb, 0, sizeof(GridBar)));
+    b->epoch = ctx->timeout_epoch;
+
+    // graph: begin -> WHILE(any system running) { evaluation of all systems } -> end
+    if (!ctx->cap_stream) CU(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t s = ctx->cap_stream;
+    const dae_prec prec = ds[0]->prec;
+    cudaGraph_t g = nullptr;
+    CU(ctx, cudaGraphCreate(&g, 0));
+    dae_status st = DAE_OK;
+    do {
+        cudaGraphConditionalHandle hc;
+        if (cudaGraphConditionalHandleCreate(&hc, g, 0, 0) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        if (cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        launch_frame_begin_batched(s, b->frame, n, hc);
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        cudaGraphNode_t a, loop;
+        cudaGraph_t body;
+        if ((st = sole_sink(ctx, g, &a))) break;
+        if ((st = add_while(ctx, g, &a, hc, &loop, &body))) break;
+        if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        bool ok = true;
+        launch_seed_batched(s, b->seed, n, b->max_elems);
+        for (const auto& c : b->fwd) {
+            ChainLaunch cl = {};
+            cl.jobs = b->jobs + c.job0; cl.n_jobs = 0; cl.Cp = c.Cp; cl.grid = ctx->sm_count;
+            cl.gb = b->gb; cl.status = ctx->d_status;
+            cl.stage_off = b->stage_off + c.st0; cl.n_stages = c.n_stages;
+            ok = ok && launch_chain(s, cl, prec);
+        }
+        launch_cubature_batched(s, b->cub, n, b->max_cub);
+        launch_xy_batched(s, b->xy, n, b->max_K);
+        launch_wta_batched(s, b->wta, n, b->max_K, b->max_splits);
+        launch_bwd_prep_tc_batched(s, b->prep, n, b->max_ld);
+        for (const auto& c : b->rev) {
+            ChainLaunch cl = {};
+            cl.jobs = b->jobs + c.job0; cl.n_jobs = 0; cl.Cp = c.Cp; cl.grid = ctx->sm_count;
+            cl.gb = b->gb; cl.status = ctx->d_status;
+            cl.stage_off = b->stage_off + c.st0; cl.n_stages = c.n_stages;
+            ok = ok && launch_chain(s, cl, prec);
+        }
+        launch_assemble_batched(s, b->cs, b->ds, b->ctl, n, b->max_ent);
+        launch_batch_cond(s, b->frame, n, hc);
+        cudaGraph_t body2 = body;
+        const cudaError_t ce = cudaStreamEndCapture(s, &body2);
+        if (!ok) { st = fail(ctx, DAE_ERR_CUDA, "grouped chain launch failed"); break; }
+        if (ce != cudaSuccess) { st = fail(ctx, DAE_ERR_CUDA, "capture failed: %s", cudaGetErrorString(ce)); break; }
+        if (cudaStreamBeginCaptureToGraph(s, g, &loop, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        launch_frame_end_batched(s, b->frame, n);
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
+        const cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+        if (ie != cudaSuccess) { st = fail(ctx, DAE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie)); break; }
+    } while (0);
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st) {
+        if (ctx->err.empty()) fail(ctx, st, "batch graph construction failed");
+        b->gexec = nullptr;
+        b->key.clear();
+        return st;
+    }
+    return DAE_OK;
+}
+
 }  // namespace
 
 // =============================================================== C ABI ====
@@ -1047,6 +1395,8 @@ dae_status dae_destroy(dae_ctx* ctx) {
     dfree(ctx->d_status);
     dfree(ctx->d_kcount);
     dfree(ctx->dstage);
+    free_batch(ctx);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cublas) cublasDestroy((cublasHandle_t)ctx->cublas);
     for (auto& rec : ctx->recs) { cudaEventDestroy(rec.a); cudaEventDestroy(rec.b); }
@@ -1197,6 +1547,7 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
         CU(ctx, cudaStreamSynchronize(ctx->stream));
     }
     d->prec = prec;
+    d->id = g_dec_ids++;   // cached grouped plans of the old form no longer match
     d->ws.chain_ok = false;
     if (prec != DAE_FP32) TRY(build_chains(d));
     d->prec = prec;
@@ -1426,6 +1777,163 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     ctx->last_ns = d->ws.hist;
     TRY(st.finish());
     if (rep) return dae_last_report(ctx, rep);
+    return DAE_OK;
+}
+
+dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sys, double dt,
+                                   const dae_newton_opts* opts_in, dae_newton_report* reps) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    if (n_sys < 0 || (n_sys > 0 && !sys)) return fail(ctx, DAE_ERR_INVALID_ARG, "bad system list");
+    if (n_sys == 0) return DAE_OK;
+    if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
+    dae_newton_opts opts;
+    fill_opts(opts_in, &opts);
+    if (opts.max_iter < 0 || opts.max_evals < 1 || opts.max_evals > 1000)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
+    std::vector<dae_decoder*> ds(n_sys);
+    std::vector<const dae_mesh*> ms(n_sys);
+    std::vector<int> ncub(n_sys), hasf(n_sys);
+    std::vector<const dae_decoder*> seen;
+    for (int i = 0; i < n_sys; ++i) {
+        const dae_system& y = sys[i];
+        TRY(check_common(ctx, y.dec, y.mesh));
+        if (!y.mesh) return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: mesh required", i);
+        if (!y.q || !y.qbar || !y.qbar_dot)
+            return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: q, qbar, qbar_dot required", i);
+        TRY(validate_cub(ctx, y.mesh, y.n_cub, y.cub_tets, y.cub_w));
+        dae_decoder* d = const_cast<dae_decoder*>(y.dec);
+        if (d->prec == DAE_FP32 || !d->ws.chain_ok || !d->layers[0].tmR_ok)
+            return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: the grouped step needs a tensor-core precision", i);
+        if (d->prec != sys[0].dec->prec)
+            return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: all decoders must share one precision", i);
+        if (d->L < 2) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: a decoder needs a hidden layer", i);
+        ds[i] = d;
+        ms[i] = y.mesh;
+        ncub[i] = y.n_cub;
+        hasf[i] = y.f_ext ? 1 : 0;
+        seen.push_back(y.dec);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return fail(ctx, DAE_ERR_INVALID_ARG, "a decoder appears in two systems (its workspace is per decoder)");
+    // per-system set-up that is cached across calls
+    for (int i = 0; i < n_sys; ++i) {
+        TRY(ensure_cubature(ds[i], ncub[i], ncub[i]));
+        if (use_gram(ds[i])) TRY(ensure_gram(ds[i], ms[i]));
+    }
+    BatchPlan* b = (BatchPlan*)ctx->batch;
+    if (!b) {
+        b = new BatchPlan();
+        ctx->batch = b;
+        CU(ctx, cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
+    }
+    for (int i = 0; i < n_sys; ++i)
+        if (hasf[i] && use_gram(ds[i])) TRY(ensure_pext_bufs(ds[i]));
+    std::vector<BatchKey> key(n_sys);
+    for (int i = 0; i < n_sys; ++i) {
+        const Workspace& w = ds[i]->ws;
+        key[i] = BatchKey{ds[i]->id, ms[i]->id, w.cub_tets, w.cub_w, w.fe_w, w.G, w.pext, ncub[i], hasf[i]};
+    }
+    const bool same = b->gexec && b->n == n_sys && b->dt == dt && b->prec == (int)ds[0]->prec &&
+                      memcmp(&b->opts, &opts, sizeof opts) == 0 &&
+                      memcmp(b->key.data(), key.data(), n_sys * sizeof(BatchKey)) == 0;
+    if (!same) {
+        TRY(build_batch(ctx, b, ds, ms, ncub, hasf, dt, opts));
+        b->key = key;
+        b->n = n_sys;
+        b->dt = dt;
+        b->prec = (int)ds[0]->prec;
+        b->opts = opts;
+    }
+    if (b->epoch != ctx->timeout_epoch) {
+        CU(ctx, cudaMemsetAsync(b->gb, 0, sizeof(GridBar), ctx->stream));
+        b->epoch = ctx->timeout_epoch;
+    }
+    // inputs into the systems' workspaces and the results out: host arrays through one
+    // pinned buffer and one upload (with the copy lists), then one grouped device copy
+    // each way
+    struct HostIn { const void* src; size_t n; void* dst; };
+    std::vector<CopyDesc> cin, cout;
+    std::vector<HostIn> hin;
+    size_t hbytes = 0;
+    auto add = [&](const void* src, void* dst, size_t nb) {
+        if (!src || nb == 0) return;
+        if (on_device(src)) {
+            cin.push_back(CopyDesc{src, dst, (unsigned long long)nb});
+        } else {
+            hin.push_back(HostIn{src, nb, dst});
+            hbytes += round_up(nb, 16);
+        }
+    };
+    std::vector<int> host_q;
+    for (int i = 0; i < n_sys; ++i) {
+        const dae_system& y = sys[i];
+        Workspace& w = ds[i]->ws;
+        const int r = ds[i]->r;
+        add(y.q, b->q0 + (size_t)i * kMaxR, r * sizeof(double));
+        add(y.qbar, w.qbar, r * sizeof(double));
+        add(y.qbar_dot, w.qbar_dot, r * sizeof(double));
+        add(y.cub_tets, w.cub_tets, (size_t)ncub[i] * sizeof(int));
+        add(y.cub_w, w.cub_w, (size_t)ncub[i] * sizeof(float));
+        add(y.f_ext, w.f_ext, (size_t)ds[i]->N * sizeof(float));
+        if (on_device(y.q))
+            cout.push_back(CopyDesc{b->qout + (size_t)i * kMaxR, y.q, (unsigned long long)(r * sizeof(double))});
+        else
+            host_q.push_back(i);
+        if (reps) cout.push_back(CopyDesc{w.ns, b->ns_out + i, (unsigned long long)sizeof(NewtonState)});
+    }
+    const size_t n_in = hin.size() + cin.size();
+    const size_t o_cin = hbytes, o_cout = round_up(o_cin + n_in * sizeof(CopyDesc), 16);
+    const size_t total = o_cout + cout.size() * sizeof(CopyDesc);
+    Stage stg(ctx);
+    TRY(stg.reserve(total));
+    CU(ctx, cudaEventSynchronize(b->staged));   // the previous call's upload has completed
+    TRY(ensure_pinned(ctx, total));
+    char* P = (char*)ctx->pinned;
+    char* D = (char*)ctx->dstage;
+    size_t o = 0;
+    for (const HostIn& h : hin) {
+        memcpy(P + o, h.src, h.n);
+        cin.push_back(CopyDesc{D + o, h.dst, (unsigned long long)h.n});
+        o += round_up(h.n, 16);
+    }
+    memcpy(P + o_cin, cin.data(), cin.size() * sizeof(CopyDesc));
+    memcpy(P + o_cout, cout.data(), cout.size() * sizeof(CopyDesc));
+    CU(ctx, cudaMemcpyAsync(D, P, total, cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaEventRecord(b->staged, ctx->stream));
+    ctx->launches += 2;
+    launch_copy_batch(ctx->stream, (const CopyDesc*)(D + o_cin), (int)cin.size());
+    for (int i = 0; i < n_sys; ++i)
+        if (hasf[i] && use_gram(ds[i])) TRY(prepare_pext(ds[i], ds[i]->ws.f_ext));
+    CU(ctx, cudaGraphLaunch(b->gexec, ctx->stream));
+    launch_copy_batch(ctx->stream, (const CopyDesc*)(D + o_cout), (int)cout.size());
+    ctx->last_ns = ds[n_sys - 1]->ws.ns;
+    std::vector<NewtonState> hs;
+    if (!host_q.empty() || reps) {
+        std::vector<double> qh;
+        if (!host_q.empty()) {
+            qh.resize((size_t)n_sys * kMaxR);
+            CU(ctx, cudaMemcpyAsync(qh.data(), b->qout, qh.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (reps) {
+            hs.resize(n_sys);
+            CU(ctx, cudaMemcpyAsync(hs.data(), b->ns_out, n_sys * sizeof(NewtonState), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int i : host_q) memcpy(sys[i].q, qh.data() + (size_t)i * kMaxR, ds[i]->r * sizeof(double));
+    }
+    CU(ctx, cudaGetLastError());
+    if (reps) {
+        TRY(check_device_status(ctx));
+        int worst = -1;
+        for (int i = 0; i < n_sys; ++i) {
+            to_report(hs[i], &reps[i]);
+            if (hs[i].status && worst < 0) worst = i;
+        }
+        if (worst >= 0)
+            return fail(ctx, (dae_status)hs[worst].status, "system %d failed: %s", worst,
+                        dae_status_string((dae_status)hs[worst].status));
+    }
     return DAE_OK;
 }
 

@@ -205,10 +205,12 @@ struct dae_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int phase; cudaEvent_t a, b; };
     std::vector<Rec> recs;
+    void* batch = nullptr;               // cached plan of dae_newton_step_batched
 };
 
 struct dae_decoder {
     dae_ctx* ctx = nullptr;
+    unsigned long long id = 0;      // unique per upload and precision change
     int L = 0, r = 0, N = 0;
     std::vector<int> widths;
     dae_act act = DAE_ACT_TANH;
@@ -283,14 +285,22 @@ struct ChainJob {
     int cnt_off;                 // first per-tile arrival counter of this job (split > 1);
                                  // the chain zeroes a layer's counters once past it
     int stream;                  // 1: equal k-block ranges per CTA (output layer, mode 1)
-    int pad_[2];
+    int item_base;               // grouped stage: position of this job's first tile in the
+                                 // stage's item list (jobs of one stage are consecutive)
+    int pad_;
 };
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
     const ChainJob* jobs; int n_jobs; int Cp; int grid;
     GridBar* gb; const NewtonState* ns; int* status; float* split_part;
     unsigned* split_cnt;   // per-tile arrival counters of split layers (zero between launches)
+    // Grouped launch (many decoders in one chain): stage t runs jobs
+    // [stage_off[t], stage_off[t+1]) with no grid barrier between them, one item per
+    // 128-row tile (no split, replication or streaming), and skips the jobs whose
+    // a.ns is done.  stage_off == nullptr: one job per stage (a single decoder).
+    const int* stage_off; int n_stages;
 };
+constexpr int kMaxGroupJobs = 512;   // jobs of one grouped stage
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);
 int run_wait_selftest(cudaStream_t s, GridBar* gb, int* out, int nblocks);
@@ -366,6 +376,56 @@ struct AsmArgs {
     unsigned long long* kcount; int kpe;
 };
 void launch_assemble(cudaStream_t s, const AsmArgs& a);
+
+// ------------------------------------------------ grouped (batched) launches --
+// The kernels of one Newton evaluation run for many independent systems (decoder +
+// mesh + Newton state each) in one launch: blockIdx.z selects the system's argument
+// record in a device array; a system whose Newton state is done returns at once.
+struct CtlArgs {
+    cudaGraphConditionalHandle hcond; int use_cond;   // evaluation loop of a graph frame
+    unsigned long long* kcount; int kpe;              // executed-kernel counter
+    int r; double dt, h;
+    const double* rowsum; const double* cubsum; const double* bwdsum; const double* esum;
+    int have_cub;
+    double* red;
+    NewtonState* ns; int control;
+    double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
+    int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
+    int* status;
+};
+struct SeedArgs {
+    const NewtonState* ns; const double* qbar; const double* qbar_dot; double dt, h;
+    int r, Cp, ld0; float* X; __nv_bfloat16* Xh; __nv_bfloat16* Xl; int out_bf16; float* zvec;
+};
+struct XyArgs {
+    const float* X; int ld, K, r; const float* zvec; double h; float* xy; const NewtonState* ns;
+};
+struct PrepArgs {
+    BwdArgs a; int Cb, ld; float* g32; __nv_bfloat16* gh; __nv_bfloat16* gl; int out_f32, out_bf16;
+};
+struct ColsumArgs {
+    const float* part; int n_parts, stride, n_ent; double* out; const NewtonState* ns;
+};
+struct DsumArgs { const double* x; int n; double* out; const NewtonState* ns; };
+struct FrameArgs {
+    NewtonState* ns; const double* q0; double* q_out; int r;
+};
+// The three column sums, the energy sum and the control step of launch_assemble.
+void assemble_parts(const AsmArgs& a, ColsumArgs cs[3], DsumArgs& ds, CtlArgs& c);
+void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems);
+void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_cub);
+void launch_xy_batched(cudaStream_t s, const XyArgs* d_args, int n_sys, int max_K);
+void launch_wta_batched(cudaStream_t s, const WtaArgs* d_args, int n_sys, int max_K, int max_splits);
+void launch_bwd_prep_tc_batched(cudaStream_t s, const PrepArgs* d_args, int n_sys, int max_ld);
+void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
+                             const CtlArgs* c, int n_sys, int max_ent);
+void launch_frame_begin_batched(cudaStream_t s, const FrameArgs* f, int n_sys,
+                                cudaGraphConditionalHandle h);
+void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys);
+void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h);
+// copy[i]: n bytes from src to dst (device memory), one block per copy
+struct CopyDesc { const void* src; void* dst; unsigned long long n; };
+void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);
 // doubles of the reduced-system buffer: outputs, terms and reduction scratch
 inline size_t red_size(int r) {
     size_t nsym = (size_t)r * (r + 1) / 2;

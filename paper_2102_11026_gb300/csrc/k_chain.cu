@@ -189,10 +189,51 @@ __device__ __forceinline__ int stream_cta(long long g, long long T, int G) {
     return (int)(((g + 1) * G + T - 1) / T) - 1;
 }
 
+// The items of one stage for CTA c.  A single-decoder stage is one job walked by
+// Walk.  A grouped stage is the list of its jobs' tiles (job t's tiles start at
+// base[t], a table in shared memory), dealt round-robin over the grid; the tiles of
+// jobs marked in skip are passed over.  Every role of a CTA walks the same sequence.
+struct StageWalk {
+    Walk w;
+    const ChainJob* jobs;
+    const int* base;
+    const unsigned char* skip;
+    int nj, total, item, G;
+    bool grouped;
+    __device__ StageWalk(const ChainJob* jobs_, int j0, int nj_, bool grouped_, const int* base_,
+                         const unsigned char* skip_, int c, int G_)
+        : w(jobs_[j0], c, G_), jobs(jobs_ + j0), base(base_), skip(skip_), nj(nj_),
+          total(grouped_ ? base_[nj_] : 0), item(c), G(G_), grouped(grouped_) {}
+    __device__ bool next(const ChainJob*& J, Item& I) {
+        if (!grouped) {
+            J = jobs;
+            return w.next(I);
+        }
+        while (item < total) {
+            const int i = item;
+            item += G;
+            int lo = 0, hi = nj - 1;   // last job whose first tile is at or before i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (base[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            if (skip[lo]) continue;
+            J = jobs + lo;
+            I.tl = i - base[lo];
+            I.ks = 0;
+            I.kb0 = 0;
+            I.kb1 = J->nk;
+            return true;
+        }
+        return false;
+    }
+};
+
 template <int NC, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_chain(const ChainJob* __restrict__ jobs, int n_jobs, GridBar* gb, const NewtonState* ns,
-            int* status, float* split_part, unsigned* split_cnt, int stages) {
+            int* status, float* split_part, unsigned* split_cnt, int stages,
+            const int* __restrict__ stage_off, int n_stages) {
     constexpr int CP = 16 * NC;
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr int KB = (PREC == DAE_TF32) ? 32 : 64;
@@ -213,6 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int fail;
     __shared__ int s_last;
     __shared__ float s_z[kMaxR];   // z of the fused row reductions (output layer)
+    __shared__ int s_base[kMaxGroupJobs + 1];           // grouped stage: first tile per job
+    __shared__ unsigned char s_skip[kMaxGroupJobs];     // grouped stage: job skipped
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~(uintptr_t)1023);
     float* tile = reinterpret_cast<float*>(smem + (size_t)stages * STAGE);
@@ -246,32 +289,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t pk = 0;   // stage-ring position (producer and MMA walk it identically)
     uint32_t it = 0;   // items taken by this CTA: accumulator it & 1, its use it >> 1
     uint32_t nred = 0; // split reductions of this CTA (rbar phases)
-    for (int j = 0; j < n_jobs; ++j) {
-        const ChainJob& Jb = jobs[j];
-        if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool grouped = stage_off != nullptr;
+    const int n_st = grouped ? n_stages : n_jobs;
+    for (int st = 0; st < n_st; ++st) {
+        const int j0 = grouped ? stage_off[st] : st;
+        const int nj = grouped ? stage_off[st + 1] - j0 : 1;
+        if (grouped) {
+            // the stage's job table (the done flags are not written during the launch)
+            for (int t = threadIdx.x; t < nj; t += blockDim.x) {
+                const ChainJob& Jt = jobs[j0 + t];
+                s_base[t] = Jt.item_base;
+                s_skip[t] = (Jt.a.ns && *(volatile const int*)&Jt.a.ns->done) ? 1 : 0;
+            }
+            if (threadIdx.x == 0) s_base[nj] = jobs[j0 + nj - 1].item_base + jobs[j0 + nj - 1].tiles;
+            __syncthreads();
+        } else if (st > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
             // the previous layer's split counters are no longer read: zero them for the
             // next launch (counters of one launch are disjoint per layer)
-            const ChainJob& Pb = jobs[j - 1];
+            const ChainJob& Pb = jobs[st - 1];
             if (Pb.split > 1)
                 for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
         }
-        const int tiles = Jb.tiles, split = Jb.split, nk = Jb.nk;
-        const int P = split > Jb.rep ? split : Jb.rep;
-        const int items = tiles * P;
-        const CUtensorMap* tmA = &Jb.tm[0];
-        const CUtensorMap* tmAlo = &Jb.tm[1];
-        const CUtensorMap* tmB = &Jb.tm[2];
-        const CUtensorMap* tmBlo = &Jb.tm[3];
         if (warp == 0) {
             if (lane == 0 && !fail) {
-                if ((int)blockIdx.x < items) {
-                    prefetch_tmap(tmA);
-                    prefetch_tmap(tmB);
-                    if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
-                }
-                Walk W(Jb, blockIdx.x, G);
+                StageWalk W(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
+                const ChainJob* Jp;
+                const ChainJob* Jlast = nullptr;
                 Item I;
-                while (!fail && W.next(I)) {
+                while (!fail && W.next(Jp, I)) {
+                    const CUtensorMap* tmA = &Jp->tm[0];
+                    const CUtensorMap* tmAlo = &Jp->tm[1];
+                    const CUtensorMap* tmB = &Jp->tm[2];
+                    const CUtensorMap* tmBlo = &Jp->tm[3];
+                    if (Jp != Jlast) {
+                        prefetch_tmap(tmA);
+                        prefetch_tmap(tmB);
+                        if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
+                        Jlast = Jp;
+                    }
                     for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
@@ -288,8 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 // the next layer's weight tiles of this CTA's items into L2 (they do not
                 // depend on this layer's output)
-                if (j + 1 < n_jobs && !fail) {
-                    const ChainJob& Nb = jobs[j + 1];
+                if (!grouped && st + 1 < n_jobs && !fail) {
+                    const ChainJob& Nb = jobs[st + 1];
                     Walk Wn(Nb, blockIdx.x, G);
                     while (Wn.next(I)) {
                         for (int kb = I.kb0; kb < I.kb1; ++kb) {
@@ -301,9 +356,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp == 1) {
             if (lane == 0 && !fail) {
-                Walk W(Jb, blockIdx.x, G);
+                StageWalk W(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
+                const ChainJob* Jp;
                 Item I;
-                for (; !fail && W.next(I); ++it) {
+                for (; !fail && W.next(Jp, I); ++it) {
                     const uint32_t ab = it & 1, au = (it >> 1) & 1;
                     const uint32_t dacc = tmem + ab * ACC_COLS;
                     if (!mbar_wait(&tempty[ab], au ^ 1)) { fail = 1; break; }
@@ -336,14 +392,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int lane_base = 32 * (warp & 3);    // TMEM lane quarter of this warp
             const int row = lane_base + lane;
             float* vrow = tile + (size_t)row * TS;
-            const int R = 128 / P;
-            if (Jb.a.mode == 1 && Jb.a.row_part) {
-                if (et < Jb.a.r) s_z[et] = Jb.a.zvec[et];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-            }
-            Walk W(Jb, blockIdx.x, G);
+            StageWalk W(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
+            const ChainJob* Jp;
+            const ChainJob* Jlast = nullptr;
             Item I;
-            for (; W.next(I); ++it) {
+            for (; W.next(Jp, I); ++it) {
+                const ChainJob& Jb = *Jp;
+                const int tiles = Jb.tiles, split = Jb.split, nk = Jb.nk;
+                const int P = split > Jb.rep ? split : Jb.rep;
+                const int R = 128 / P;
+                if (Jp != Jlast) {
+                    if (Jb.a.mode == 1 && Jb.a.row_part) {
+                        // z of this job's fused row reductions (the previous job's
+                        // reductions are done once every epilogue thread is here)
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (et < Jb.a.r) s_z[et] = Jb.a.zvec[et];
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    }
+                    Jlast = Jp;
+                }
                 if (et == 0 && Jb.a.mode != 1) {
                     // this slice's epilogue inputs into L2 while the MMAs run
                     const int n0 = I.tl * 128 + I.ks * R;
@@ -534,6 +601,8 @@ bool launch_chain_inst(cudaStream_t s, const ChainLaunch& c) {
     constexpr bool X3 = (PREC == DAE_BF16X3);
     constexpr uint32_t STAGE = (128 * 128 + CP * 128) * (X3 ? 2 : 1);
     const size_t tile_bytes = (size_t)128 * (CP + 1) * 4 + 256 * 4;
+    // dynamic shared memory <= 220 KB: with the static part (barriers, z, the grouped
+    // stage's job table, < 3 KB) within the 227 KB a CTA may hold
     const size_t budget = 220 * 1024 - tile_bytes - 1024;
     int stages = (int)(budget / STAGE);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
@@ -556,7 +625,7 @@ bool launch_chain_inst(cudaStream_t s, const ChainLaunch& c) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_chain<NC, PREC>, c.jobs, c.n_jobs, c.gb, c.ns, c.status,
-                              c.split_part, c.split_cnt, stages) == cudaSuccess;
+                              c.split_part, c.split_cnt, stages, c.stage_off, c.n_stages) == cudaSuccess;
 }
 
 template <int PREC>

@@ -8,10 +8,11 @@ namespace dae {
 // ------------------------------------------------------------------- seed --
 // Input components of q* = q + h e_j i1 + h c i2 + h c i3 + h^2 g i2i3 (Sec. 4.3),
 // c = Delta (0 in SEED_HW), g = w (0 in SEED_SDD); column layout in dae_internal.h.
-__global__ void k_seed(const NewtonState* ns, const double* q_override, const double* qbar,
-                       const double* qbar_dot, double dt, double h, int mode, int r, int Cp,
-                       int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
-                       float* zvec) {
+__device__ __forceinline__ void seed_impl(const NewtonState* ns, const double* q_override,
+                                          const double* qbar, const double* qbar_dot, double dt,
+                                          double h, int mode, int r, int Cp, int ld0, float* X,
+                                          __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
+                                          float* zvec) {
     if (ns && ns->done) return;
     const double* q = q_override ? q_override : ns->q_trial;
     const int C = n_cols(r);
@@ -33,6 +34,26 @@ __global__ void k_seed(const NewtonState* ns, const double* q_override, const do
         int k = threadIdx.x;
         zvec[k] = (float)((q[k] - qbar[k]) - dt * qbar_dot[k]);
     }
+}
+
+__global__ void k_seed(const NewtonState* ns, const double* q_override, const double* qbar,
+                       const double* qbar_dot, double dt, double h, int mode, int r, int Cp,
+                       int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
+                       float* zvec) {
+    seed_impl(ns, q_override, qbar, qbar_dot, dt, h, mode, r, Cp, ld0, X, Xh, Xl, out_bf16, zvec);
+}
+
+// Grouped form (z = system): the full seed at each system's trial iterate.
+__global__ void k_seed_b(const SeedArgs* __restrict__ args) {
+    const SeedArgs& a = args[blockIdx.z];
+    seed_impl(a.ns, nullptr, a.qbar, a.qbar_dot, a.dt, a.h, SEED_FULL, a.r, a.Cp, a.ld0, a.X,
+              a.Xh, a.Xl, a.out_bf16, a.zvec);
+}
+
+void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems) {
+    if (n_sys <= 0) return;
+    const int bx = (max_elems + 255) / 256;
+    k_seed_b<<<dim3(bx < 1 ? 1 : bx, 1, n_sys), 256, 0, s>>>(d_args);
 }
 
 void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,

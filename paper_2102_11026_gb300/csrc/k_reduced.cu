@@ -88,7 +88,7 @@ __device__ __forceinline__ void mat3_mul(const double* A, const double* B, doubl
 
 constexpr int kCubWarps = 4;   // tets per block (one warp each): more SMs, one warp per scheduler
 
-__global__ void __launch_bounds__(32 * kCubWarps) k_cubature(CubArgs A) {
+__device__ __forceinline__ void cubature_impl(const CubArgs& A) {
     if (A.ns && A.ns->done) return;
     __shared__ float sdG[kCubWarps][kMaxR][9];
     __shared__ float sdP[kCubWarps][kMaxR][9];
@@ -301,6 +301,18 @@ __global__ void __launch_bounds__(32 * kCubWarps) k_cubature(CubArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(32 * kCubWarps) k_cubature(CubArgs A) { cubature_impl(A); }
+
+// Grouped form: z = system.
+__global__ void __launch_bounds__(32 * kCubWarps) k_cubature_b(const CubArgs* __restrict__ args) {
+    cubature_impl(args[blockIdx.z]);
+}
+
+void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_cub) {
+    if (n_sys <= 0 || max_cub <= 0) return;
+    k_cubature_b<<<dim3((max_cub + kCubWarps - 1) / kCubWarps, 1, n_sys), 32 * kCubWarps, 0, s>>>(d_args);
+}
+
 void launch_cubature(cudaStream_t s, const CubArgs& a) {
     if (a.n_cub <= 0) return;
     k_cubature<<<(a.n_cub + kCubWarps - 1) / kCubWarps, 32 * kCubWarps, 0, s>>>(a);
@@ -318,12 +330,13 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& w, float a) {
     acc.w = fmaf(w.w, a, acc.w);
 }
 
-__global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
+__device__ __forceinline__ void wta_impl(const WtaArgs& A) {
     if (A.ns && A.ns->done) return;
     if (A.run_flag && *A.run_flag == 0) return;
     const int k4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (k4 >= A.K) return;
     const int s = blockIdx.y;
+    if (s >= A.nsplit_dense + A.nsplit_pairs + (A.pext ? 1 : 0)) return;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (s < A.nsplit_dense) {
         const int per = (A.N + A.nsplit_dense - 1) / A.nsplit_dense;
@@ -380,6 +393,18 @@ __global__ void __launch_bounds__(256) k_wta(WtaArgs A) {
         if (k4 + u < A.K) out[u] = v[u];
 }
 
+__global__ void __launch_bounds__(256) k_wta(WtaArgs A) { wta_impl(A); }
+
+// Grouped form: z = system.
+__global__ void __launch_bounds__(256) k_wta_b(const WtaArgs* __restrict__ args) {
+    wta_impl(args[blockIdx.z]);
+}
+
+void launch_wta_batched(cudaStream_t s, const WtaArgs* d_args, int n_sys, int max_K, int max_splits) {
+    if (n_sys <= 0) return;
+    k_wta_b<<<dim3((max_K + 1023) / 1024, max_splits, n_sys), 256, 0, s>>>(d_args);
+}
+
 void launch_wta(cudaStream_t s, const WtaArgs& a) {
     dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs + (a.pext ? 1 : 0));
     k_wta<<<grid, 256, 0, s>>>(a);
@@ -387,8 +412,8 @@ void launch_wta(cudaStream_t s, const WtaArgs& a) {
 
 // x_y[k] = sum_j X[b_j][k] z_j / h + X[g0][k] / h^2 over the output layer's input
 // activations (stacked columns, see dae_internal.h), so that J z + H[D,D] = W_L x_y.
-__global__ void k_xy(const float* X, int ld, int K, int r, const float* zvec, double h, float* xy,
-                     const NewtonState* ns) {
+__device__ __forceinline__ void xy_impl(const float* X, int ld, int K, int r, const float* zvec,
+                                        double h, float* xy, const NewtonState* ns) {
     if (ns && ns->done) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
@@ -396,6 +421,21 @@ __global__ void k_xy(const float* X, int ld, int K, int r, const float* zvec, do
     float acc = X[(size_t)3 * ld + k] * ih2;
     for (int j = 0; j < r; ++j) acc = fmaf(X[(size_t)(kShared + 3 * j) * ld + k] * ih, zvec[j], acc);
     xy[k] = acc;
+}
+
+__global__ void k_xy(const float* X, int ld, int K, int r, const float* zvec, double h, float* xy,
+                     const NewtonState* ns) {
+    xy_impl(X, ld, K, r, zvec, h, xy, ns);
+}
+
+__global__ void k_xy_b(const XyArgs* __restrict__ args) {
+    const XyArgs& a = args[blockIdx.z];
+    xy_impl(a.X, a.ld, a.K, a.r, a.zvec, a.h, a.xy, a.ns);
+}
+
+void launch_xy_batched(cudaStream_t s, const XyArgs* d_args, int n_sys, int max_K) {
+    if (n_sys <= 0 || max_K <= 0) return;
+    k_xy_b<<<dim3((max_K + 63) / 64, 1, n_sys), 64, 0, s>>>(d_args);
 }
 
 void launch_xy(cudaStream_t s, const float* X, int ld, int K, int r, const float* zvec, double h,
@@ -538,10 +578,11 @@ __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
 // A block takes 32 consecutive k; its 8 warps sum every 8th incoming split partial
 // (coalesced over k), combine the 8 sums in a fixed order, then write the columns
 // c = warp, warp + 8, ...
-__global__ void __launch_bounds__(256) k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32,
-                                                     __nv_bfloat16* gh, __nv_bfloat16* gl,
-                                                     int out_f32, int out_bf16) {
+__device__ __forceinline__ void bwd_prep_tc_impl(const BwdArgs& A, int Cb, int ld, float* g32,
+                                                 __nv_bfloat16* gh, __nv_bfloat16* gl,
+                                                 int out_f32, int out_bf16) {
     if (A.ns && A.ns->done) return;
+    if ((int)blockIdx.x * 32 >= ld) return;
     __shared__ float part[8][kMaxR + 1][33];
     __shared__ float sre[32];
     const int tx = threadIdx.x & 31, sy = threadIdx.x >> 5;
@@ -586,6 +627,22 @@ __global__ void __launch_bounds__(256) k_bwd_prep_tc(BwdArgs A, int Cb, int ld, 
             if (out_bf16 == 2) gl[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_bwd_prep_tc(BwdArgs A, int Cb, int ld, float* g32,
+                                                     __nv_bfloat16* gh, __nv_bfloat16* gl,
+                                                     int out_f32, int out_bf16) {
+    bwd_prep_tc_impl(A, Cb, ld, g32, gh, gl, out_f32, out_bf16);
+}
+
+__global__ void __launch_bounds__(256) k_bwd_prep_tc_b(const PrepArgs* __restrict__ args) {
+    const PrepArgs& p = args[blockIdx.z];
+    bwd_prep_tc_impl(p.a, p.Cb, p.ld, p.g32, p.gh, p.gl, p.out_f32, p.out_bf16);
+}
+
+void launch_bwd_prep_tc_batched(cudaStream_t s, const PrepArgs* d_args, int n_sys, int max_ld) {
+    if (n_sys <= 0) return;
+    k_bwd_prep_tc_b<<<dim3((max_ld + 31) / 32, 1, n_sys), 256, 0, s>>>(d_args);
 }
 
 void launch_bwd_prep_tc(cudaStream_t s, const BwdArgs& a, int Cb, int ld, float* g32,

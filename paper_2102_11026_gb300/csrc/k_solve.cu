@@ -1,6 +1,7 @@
 // FP64 assembly of the reduced system (Eqs. 10-11 with n_p = 0), the dense
 // LU solve of the Newton step and the device-side Newton / line-search control.
 #include <math.h>
+#include <string.h>
 #include "dae_internal.h"
 #include "epilogue.cuh"
 
@@ -13,8 +14,8 @@ namespace dae {
 // of its terms is summed in FP32 and added to an FP64 accumulator (FP64 adds are
 // scarce on this part), then the 16 warp sums are added in warp order (fixed order:
 // bitwise reproducible).
-__global__ void __launch_bounds__(512) k_colsum(const float* part, int n_parts, int stride,
-                                                int n_ent, double* out, const NewtonState* ns) {
+__device__ __forceinline__ void colsum_impl(const float* part, int n_parts, int stride,
+                                            int n_ent, double* out, const NewtonState* ns) {
     if (ns && ns->done) return;
     __shared__ double ws[16][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -40,7 +41,13 @@ __global__ void __launch_bounds__(512) k_colsum(const float* part, int n_parts, 
     }
 }
 
-__global__ void k_dsum(const double* x, int n, double* out, const NewtonState* ns) {
+__global__ void __launch_bounds__(512) k_colsum(const float* part, int n_parts, int stride,
+                                                int n_ent, double* out, const NewtonState* ns) {
+    colsum_impl(part, n_parts, stride, n_ent, out, ns);
+}
+
+__device__ __forceinline__ void dsum_impl(const double* x, int n, double* out,
+                                          const NewtonState* ns) {
     if (ns && ns->done) return;
     __shared__ double s[256];
     double acc = 0.0;
@@ -52,6 +59,10 @@ __global__ void k_dsum(const double* x, int n, double* out, const NewtonState* n
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void k_dsum(const double* x, int n, double* out, const NewtonState* ns) {
+    dsum_impl(x, n, out, ns);
 }
 
 static inline void colsum(cudaStream_t st, const float* part, int n_parts, int stride, int n_ent,
@@ -191,20 +202,9 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
 //   cubsum  [g_int (r) | K_r upper]
 //   bwdsum  [(1+r) x r]: column 0 = J^T a, column 1+j = h (a^T H)[:, j]
 //   red     [phi (r) | A (r*r col-major) | energy | aH | Mr | B | Kr | g_int]
-struct CtlArgs {
-    cudaGraphConditionalHandle hcond; int use_cond;   // evaluation loop of a graph frame
-    unsigned long long* kcount; int kpe;              // executed-kernel counter
-    int r; double dt, h;
-    const double* rowsum; const double* cubsum; const double* bwdsum; const double* esum;
-    int have_cub;
-    double* red;
-    NewtonState* ns; int control;
-    double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
-    int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
-    int* status;
-};
 
-__global__ void k_control(CtlArgs C) {
+
+__device__ __forceinline__ void control_impl(const CtlArgs& C) {
     if (C.ns && C.ns->done) {
         // a finished frame never re-enters the evaluation loop
         if (C.use_cond && threadIdx.x == 0) cudaGraphSetConditional(C.hcond, 0u);
@@ -375,7 +375,9 @@ __global__ void k_control(CtlArgs C) {
         reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
 }
 
-void launch_assemble(cudaStream_t s, const AsmArgs& a) {
+__global__ void k_control(CtlArgs C) { control_impl(C); }
+
+void assemble_parts(const AsmArgs& a, ColsumArgs cs[3], DsumArgs& ds, CtlArgs& c) {
     const int r = a.r;
     const int nsym = r * (r + 1) / 2;
     // scratch doubles live after the terms block of red
@@ -384,13 +386,11 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     double* cubsum = rowsum + (r + nsym + r * r);
     double* bwdsum = cubsum + (r + nsym);
     double* esum = bwdsum + (1 + r) * r;
-    colsum(s, a.row_part, a.n_row_blocks, a.row_stride, r + nsym + r * r, rowsum, a.ns);
-    if (a.n_cub > 0) {
-        colsum(s, a.cub_part, a.n_cub, a.cub_stride, r + nsym, cubsum, a.ns);
-        k_dsum<<<1, 256, 0, s>>>(a.cub_energy, a.n_cub, esum, a.ns);
-    }
-    colsum(s, a.bwd_part, a.bwd_split, (1 + r) * r, (1 + r) * r, bwdsum, a.ns);
-    CtlArgs c;
+    cs[0] = ColsumArgs{a.row_part, a.n_row_blocks, a.row_stride, r + nsym + r * r, rowsum, a.ns};
+    cs[1] = ColsumArgs{a.cub_part, a.n_cub, a.cub_stride, a.n_cub > 0 ? r + nsym : 0, cubsum, a.ns};
+    cs[2] = ColsumArgs{a.bwd_part, a.bwd_split, (1 + r) * r, (1 + r) * r, bwdsum, a.ns};
+    ds = DsumArgs{a.cub_energy, a.n_cub, esum, a.ns};
+    memset(&c, 0, sizeof c);
     c.r = r; c.dt = a.dt; c.h = a.h;
     c.rowsum = rowsum; c.cubsum = cubsum; c.bwdsum = bwdsum; c.esum = esum;
     c.have_cub = a.n_cub > 0;
@@ -399,7 +399,42 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
     c.eval_flag = a.eval_flag; c.status = a.status;
     c.hcond = a.hcond; c.use_cond = a.use_cond; c.kcount = a.kcount; c.kpe = a.kpe;
+}
+
+void launch_assemble(cudaStream_t s, const AsmArgs& a) {
+    ColsumArgs cs[3];
+    DsumArgs ds;
+    CtlArgs c;
+    assemble_parts(a, cs, ds, c);
+    colsum(s, cs[0].part, cs[0].n_parts, cs[0].stride, cs[0].n_ent, cs[0].out, a.ns);
+    if (a.n_cub > 0) {
+        colsum(s, cs[1].part, cs[1].n_parts, cs[1].stride, cs[1].n_ent, cs[1].out, a.ns);
+        k_dsum<<<1, 256, 0, s>>>(ds.x, ds.n, ds.out, a.ns);
+    }
+    colsum(s, cs[2].part, cs[2].n_parts, cs[2].stride, cs[2].n_ent, cs[2].out, a.ns);
     k_control<<<1, 256, 0, s>>>(c);
+}
+
+// Grouped form: z = system; the three column sums in y (an empty sum skips), then the
+// energy sum and the control step, one block per system.
+__global__ void __launch_bounds__(512) k_colsum_b(const ColsumArgs* __restrict__ cs) {
+    const ColsumArgs& a = cs[blockIdx.z * 3 + blockIdx.y];
+    if ((int)blockIdx.x * 32 >= a.n_ent) return;
+    colsum_impl(a.part, a.n_parts, a.stride, a.n_ent, a.out, a.ns);
+}
+__global__ void k_dsum_b(const DsumArgs* __restrict__ ds) {
+    const DsumArgs& a = ds[blockIdx.x];
+    if (a.n <= 0) return;
+    dsum_impl(a.x, a.n, a.out, a.ns);
+}
+__global__ void k_control_b(const CtlArgs* __restrict__ c) { control_impl(c[blockIdx.x]); }
+
+void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
+                             const CtlArgs* c, int n_sys, int max_ent) {
+    if (n_sys <= 0) return;
+    k_colsum_b<<<dim3((max_ent + 31) / 32, 3, n_sys), 512, 0, s>>>(cs);
+    k_dsum_b<<<n_sys, 256, 0, s>>>(ds);
+    k_control_b<<<n_sys, 256, 0, s>>>(c);
 }
 
 // --------------------------------------------------------- frame control --
@@ -489,6 +524,75 @@ void launch_frame_finish(cudaStream_t s, RollCtl* rc, NewtonState* ns, double* q
                          unsigned long long* kcount) {
     k_frame_finish<<<1, 32, 0, s>>>(rc, ns, qbar, qbar_dot, dt, r, traj, hist, q_out, h, use,
                                     kcount);
+}
+
+// Grouped single-frame control: one block per system.  Begin: Newton state from the
+// given first iterate (and the evaluation loop's condition set); end: the accepted
+// iterate out.  The condition kernel keeps the loop going while any system runs.
+__global__ void k_frame_begin_b(const FrameArgs* __restrict__ f, cudaGraphConditionalHandle h,
+                                int use) {
+    const FrameArgs& a = f[blockIdx.x];
+    NewtonState* ns = a.ns;
+    const int i = threadIdx.x;
+    if (i < a.r) {
+        const double q0 = a.q0[i];
+        ns->q_trial[i] = q0;
+        ns->q_acc[i] = q0;
+        ns->delta[i] = 0.0;
+        ns->phi[i] = 0.0;
+    }
+    if (i == 0) {
+        ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
+        ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
+        ns->status = 0; ns->frame = 0;
+        if (use && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
+    }
+}
+
+__global__ void k_frame_end_b(const FrameArgs* __restrict__ f) {
+    const FrameArgs& a = f[blockIdx.x];
+    const int i = threadIdx.x;
+    if (i < a.r) a.q_out[i] = a.ns->q_acc[i];
+    __syncthreads();
+    if (i == 0) a.ns->done = 1;
+}
+
+__global__ void k_batch_cond(const FrameArgs* __restrict__ f, int n_sys,
+                             cudaGraphConditionalHandle h) {
+    int run = 0;
+    for (int i = threadIdx.x; i < n_sys; i += blockDim.x) run |= f[i].ns->done ? 0 : 1;
+    run = __syncthreads_or(run);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+void launch_frame_begin_batched(cudaStream_t s, const FrameArgs* f, int n_sys,
+                                cudaGraphConditionalHandle h) {
+    k_frame_begin_b<<<n_sys, 32, 0, s>>>(f, h, h != 0 ? 1 : 0);
+}
+void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys) {
+    k_frame_end_b<<<n_sys, 32, 0, s>>>(f);
+}
+void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h) {
+    k_batch_cond<<<1, 256, 0, s>>>(f, n_sys, h);
+}
+
+// One block per copy; 16-byte vectors where both ends and the size allow it.
+__global__ void k_copy_batch(const CopyDesc* __restrict__ d) {
+    const CopyDesc c = d[blockIdx.x];
+    const uintptr_t a = (uintptr_t)c.src | (uintptr_t)c.dst | (uintptr_t)c.n;
+    if ((a & 15) == 0) {
+        const uint4* src = reinterpret_cast<const uint4*>(c.src);
+        uint4* dst = reinterpret_cast<uint4*>(c.dst);
+        for (unsigned long long i = threadIdx.x; i < c.n / 16; i += blockDim.x) dst[i] = src[i];
+    } else {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(c.src);
+        unsigned char* dst = reinterpret_cast<unsigned char*>(c.dst);
+        for (unsigned long long i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n) {
+    if (n > 0) k_copy_batch<<<n, 256, 0, s>>>(d);
 }
 
 }  // namespace dae

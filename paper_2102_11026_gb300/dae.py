@@ -51,6 +51,13 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
 
+class dae_system(ctypes.Structure):
+    _fields_ = [("dec", ctypes.c_void_p), ("mesh", ctypes.c_void_p), ("n_cub", ctypes.c_int),
+                ("cub_tets", ctypes.c_void_p), ("cub_w", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("qbar", ctypes.c_void_p), ("qbar_dot", ctypes.c_void_p),
+                ("f_ext", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "dae_version": ([], _i),
     "dae_status_string": ([_i], ctypes.c_char_p),
@@ -70,6 +77,8 @@ SIGNATURES = {
     "dae_newton_step": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp,
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
+    "dae_newton_step_batched": ([_vp, _i, ctypes.POINTER(dae_system), _d,
+                                 ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_reduce_rows_noalloc": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp], _i),
     "dae_profile_enable": ([_vp, ctypes.c_uint], _i),
     "dae_profile_read": ([_vp, _vp, _vp], _i),
@@ -239,6 +248,25 @@ def dae_newton_step(ctx, dec, mesh, cub_tets, cub_w, q, qbar, qbar_dot, dt, f_ex
         _ptr(f_ext, np.float32), ctypes.byref(opts) if opts is not None else None,
         ctypes.byref(rep) if rep is not None else None))
     return rep
+
+
+def dae_newton_step_batched(ctx, systems, dt, opts=None, want_reports=True):
+    """systems: list of dicts with keys dec, mesh, cub_tets, cub_w, q, qbar, qbar_dot and
+    optionally f_ext (arrays as for dae_newton_step; q is updated in place)."""
+    n = len(systems)
+    arr = (dae_system * max(n, 1))()
+    for i, y in enumerate(systems):
+        ct = y.get("cub_tets")
+        nc = int(ct.shape[0]) if ct is not None else 0
+        arr[i] = dae_system(y["dec"], y["mesh"], nc, _ptr(ct, np.int32),
+                            _ptr(y.get("cub_w"), np.float32, nc), _ptr(y["q"], np.float64),
+                            _ptr(y["qbar"], np.float64), _ptr(y["qbar_dot"], np.float64),
+                            _ptr(y.get("f_ext"), np.float32))
+    reps = (dae_newton_report * max(n, 1))() if want_reports else None
+    _check(ctx, lib().dae_newton_step_batched(
+        ctx, n, arr, float(dt), ctypes.byref(opts) if opts is not None else None,
+        ctypes.cast(reps, ctypes.POINTER(dae_newton_report)) if reps is not None else None))
+    return list(reps)[:n] if reps is not None else None
 
 
 def dae_last_report(ctx):

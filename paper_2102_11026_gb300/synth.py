@@ -211,6 +211,33 @@ def medium(seed=2, act="tanh"):
     return Workload("medium", dec, mesh, cub, w, st, gravity_force(mesh.vmass))
 
 
+STRING_HIDDEN = [32, 64, 128, 256, 256, 256, 256]
+STRING_Q_STD = 0.1
+
+
+def strings(n_strings=320, seed=4, act="tanh", r_range=(3, 15), v_range=(200, 2000),
+            n_cub=32):
+    """Substructured model of independent strings (the puffer ball's 320 strings): string
+    s has latent r_s ~ U{r_range}, V_s ~ U[v_range] vertices (rounded down to a multiple
+    of 4) on a 2 x 2 x V_s/4 grid, a bias-free depth-8 decoder
+    r_s-32-64-128-256-256-256-256-3V_s, StVK (E = 1e5, nu = 0.4), ``n_cub`` cubature tets,
+    start qbar ~ N(0, 0.1^2), qbar_dot ~ N(0, 0.1^2), no external force.  Returns a list of
+    workloads (string s seeded from seed and s)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 32452843))
+    rs = rng.integers(r_range[0], r_range[1] + 1, n_strings)
+    vs = rng.integers(v_range[0], v_range[1] + 1, n_strings) // 4 * 4
+    out = []
+    for s in range(n_strings):
+        r, V = int(rs[s]), int(vs[s])
+        ss = seed * 100003 + s
+        dec = make_decoder([r] + STRING_HIDDEN + [3 * V], ss, act, bias=False)
+        mesh = make_grid_mesh(2, 2, V // 4, ss, "stvk", 1e5, 0.4)
+        cub, w = make_cubature(mesh.n_tet, n_cub, ss)
+        st = make_state(r, ss, q_std=STRING_Q_STD)
+        out.append(Workload("string%d" % s, dec, mesh, cub, w, st, np.zeros(dec.n_out, np.float32)))
+    return out
+
+
 def custom(widths, grid, n_cub, seed, act="tanh", material="stvk", E=1e5, nu=0.4,
            gravity=False):
     """Arbitrary-shape workload for parity sweeps; ``widths[-1]`` must equal
