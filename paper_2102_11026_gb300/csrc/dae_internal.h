@@ -93,7 +93,7 @@ struct RollCtl {
 struct GraphKey {
     unsigned long long mesh_id;
     const void* cub_w; const void* cub_tets; const void* fe_w; const void* hist; const void* traj;
-    const void* fext;
+    const void* fext; const void* gs;
     int n_cub, gram, prec, max_iter, max_halvings, max_evals;
     double dt, h, tol, c_armijo, max_step, xtol;
 };
@@ -180,6 +180,20 @@ struct Workspace {
     bool pext_valid = false;
     float* pext_part = nullptr;     // [splits][K]
     int pext_splits = 0;
+    // Gram form of the Newton path's output layer (tensor-core precisions, with G): one
+    // stacked operand [G (Gt*128 rows) ; W_L rows of the cubature DOFs (Rt*128 rows)],
+    // [rows][ldGs] in the precision's operand form (TF32-rounded FP32, or BF16 hi / lo).
+    // Its G tiles give the row reductions over K (J^T M J = X_J^T G X_J, ...), its other
+    // tiles the output rows the cubature reads.
+    float* Gs32 = nullptr;
+    __nv_bfloat16* Gsh = nullptr;
+    __nv_bfloat16* Gsl = nullptr;
+    int Gt = 0, Rt = 0, ldGs = 0, gs_rows_cap = 0;
+    unsigned long long gs_G_mesh = 0;   // mesh id the G tiles were filled for
+    int* cub_rows = nullptr;        // [gs_rows_cap] DOF of each cubature row (-1: none)
+    CUtensorMap tmGs[2];
+    bool gs_ok = false;             // stacked operand ready (G part current)
+    float* gy = nullptr;            // [K] G x_y, written by the G tiles' epilogue
 };
 
 }  // namespace dae
@@ -264,6 +278,14 @@ struct FwdArgs {
     double inv_h, inv_h2, inv_h3, inv_dt2;
     const NewtonState* ns;                   // early exit when ns->done (may be null)
     int* status;
+    // mode 1 over the stacked Gram operand: tiles < gram_tiles are rows k < K of G X
+    // (reductions into row_part, G x_y into gy); a later tile's row i is output row
+    // row_map[i] (skipped when negative or i >= n_map)
+    int gram_tiles, K;
+    const int* row_map; int n_map;
+    const float* Xg; int ldxg;               // FP32 input activations of the output layer [Cp][ldxg]
+    const float* pext;                       // W_L^T f_ext [K] or null
+    float* gy;                               // out: G x_y [K]
 };
 
 void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,
@@ -332,6 +354,7 @@ struct WtaArgs {
     const float* a;                          // dense seed [N]
     const float* Wp; int ldp;                // matrix of the cubature pair rows (W_L)
     const float* pext; float pext_scale;     // extra split: pext_scale * pext (or null)
+    const float* gy;                         // extra split: gy (or null), after pext
     const int* run_flag;                     // skip when *run_flag == 0 (or null)
     const float* fe_w; const int* fe_dof; int n_pairs; double dt2;
     float* part; int nsplit_dense, nsplit_pairs;   // out [nsplit_dense + nsplit_pairs][K]
@@ -420,9 +443,11 @@ void launch_bwd_prep_tc_batched(cudaStream_t s, const PrepArgs* d_args, int n_sy
 void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
                              const CtlArgs* c, int n_sys, int max_ent);
 void launch_frame_begin_batched(cudaStream_t s, const FrameArgs* f, int n_sys,
-                                cudaGraphConditionalHandle h);
+                                cudaGraphConditionalHandle h, int use);
 void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys);
-void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h);
+// sets the graph condition h (flag == nullptr) or writes *flag: 1 while any system runs
+void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h,
+                       int* flag);
 // copy[i]: n bytes from src to dst (device memory), one block per copy
 struct CopyDesc { const void* src; void* dst; unsigned long long n; };
 void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);
@@ -448,5 +473,17 @@ bool make_tmap(void* out, const void* base, bool fp32, int ld, int rows, int box
 void launch_split_bf16(cudaStream_t s, const float* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
                        size_t n);
 void launch_round_tf32(cudaStream_t s, const float* W, float* out, size_t n);
+// Rows of the stacked Gram operand for the cubature DOFs: row i < 12 n_cub is output-layer
+// row dof(i) = 3 tets[4 cub_tets[i/12] + (i%12)/3] + i%3 (the order of the element
+// force pairs), copied from the output layer's operand arrays (src32 or srch/srcl,
+// [*][ld]) into dst rows [row0 + i]; rows i in [12 n_cub, n_rows) are zeroed; map[i] = dof
+// or -1.
+struct GatherArgs {
+    const int* cub_tets; const int* tets; int n_cub, n_rows, ld, row0;
+    const float* src32; const __nv_bfloat16* srch; const __nv_bfloat16* srcl;
+    float* dst32; __nv_bfloat16* dsth; __nv_bfloat16* dstl; int* map;
+};
+void launch_gather_cub_rows(cudaStream_t s, const GatherArgs* d_args, const GatherArgs& host_args,
+                            int n_sys);
 
 }  // namespace dae

@@ -116,9 +116,9 @@ __device__ __forceinline__ Item item_of(int item, int P, int split, int nk) {
 }
 
 // The items of one job for CTA c.  Split / replicated jobs: items (tile, ks) dealt
-// round-robin.  Stream jobs: the CTA takes the contiguous range [c T / G, (c+1) T / G)
-// of the job's T = tiles x nk k-blocks, so every CTA streams the same number of
-// k-blocks.  The range is cut at tile edges into a head piece (end of a tile begun by
+// round-robin.  Stream jobs (T >= G): the CTA takes the contiguous range
+// [c T / G, (c+1) T / G) of the job's T = tiles x nk k-blocks, so every CTA streams the
+// same number (at least one) of k-blocks.  The range is cut at tile edges into a head piece (end of a tile begun by
 // the previous CTA), a tail piece (start of a tile the next CTA ends) and whole
 // tiles, taken as head, one whole tile, tail, the other whole tiles: both pieces of a
 // cut tile are streamed early by their CTAs, so the CTA that finishes the tile does
@@ -501,9 +501,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         asm volatile("bar.sync 1, 128;" ::: "memory");
                     }
-                    row_epilogue(Jb.a, I.tl * 128 + row, vrow);
-                    if (Jb.a.row_part)
-                        fused_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl, s_z);
+                    if (I.tl < Jb.a.gram_tiles) {
+                        // Gram rows: reductions over K (and G x_y)
+                        gram_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl, s_z);
+                    } else if (Jb.a.row_map) {
+                        // output rows of the cubature DOFs
+                        const int i = (I.tl - Jb.a.gram_tiles) * 128 + row;
+                        const int n = i < Jb.a.n_map ? Jb.a.row_map[i] : -1;
+                        row_epilogue(Jb.a, n < 0 ? Jb.a.n_out : n, vrow);
+                    } else {
+                        row_epilogue(Jb.a, I.tl * 128 + row, vrow);
+                        if (Jb.a.row_part)
+                            fused_row_reduce(Jb.a, tile, TS, row, I.tl * 128 + row, true, I.tl, s_z);
+                    }
                     continue;
                 }
                 if (split > 1) {

@@ -230,4 +230,50 @@ void launch_round_tf32(cudaStream_t s, const float* W, float* out, size_t n) {
     k_round_tf32<<<1024, 256, 0, s>>>(W, out, n);
 }
 
+// ---------------------------------------------------- cubature-row gather --
+__device__ __forceinline__ void gather_row_impl(const GatherArgs& A, int i) {
+    if (i >= A.n_rows) return;
+    int dof = -1;
+    if (i < 12 * A.n_cub) {
+        const int e = A.cub_tets[i / 12], a = (i % 12) / 3, d = i % 3;
+        dof = 3 * A.tets[4 * e + a] + d;
+    }
+    if (threadIdx.x == 0) A.map[i] = dof;
+    const size_t dst = (size_t)(A.row0 + i) * A.ld;
+    if (A.dst32) {
+        const uint4* src = reinterpret_cast<const uint4*>(A.src32 + (size_t)(dof < 0 ? 0 : dof) * A.ld);
+        uint4* out = reinterpret_cast<uint4*>(A.dst32 + dst);
+        for (int c = threadIdx.x; c < A.ld / 4; c += blockDim.x)
+            out[c] = dof < 0 ? make_uint4(0, 0, 0, 0) : src[c];
+    }
+    if (A.dsth) {
+        const size_t so = (size_t)(dof < 0 ? 0 : dof) * A.ld;
+        const uint4* sh = reinterpret_cast<const uint4*>(A.srch + so);
+        uint4* oh = reinterpret_cast<uint4*>(A.dsth + dst);
+        for (int c = threadIdx.x; c < A.ld / 8; c += blockDim.x)
+            oh[c] = dof < 0 ? make_uint4(0, 0, 0, 0) : sh[c];
+        if (A.dstl) {
+            const uint4* sl = reinterpret_cast<const uint4*>(A.srcl + so);
+            uint4* ol = reinterpret_cast<uint4*>(A.dstl + dst);
+            for (int c = threadIdx.x; c < A.ld / 8; c += blockDim.x)
+                ol[c] = dof < 0 ? make_uint4(0, 0, 0, 0) : sl[c];
+        }
+    }
+}
+
+__global__ void k_gather_cub_rows(GatherArgs A) { gather_row_impl(A, blockIdx.x); }
+
+__global__ void k_gather_cub_rows_b(const GatherArgs* __restrict__ args) {
+    gather_row_impl(args[blockIdx.z], blockIdx.x);
+}
+
+void launch_gather_cub_rows(cudaStream_t s, const GatherArgs* d_args, const GatherArgs& host_args,
+                            int n_sys) {
+    if (host_args.n_rows <= 0) return;
+    if (d_args)
+        k_gather_cub_rows_b<<<dim3(host_args.n_rows, 1, n_sys), 128, 0, s>>>(d_args);
+    else
+        k_gather_cub_rows<<<host_args.n_rows, 128, 0, s>>>(host_args);
+}
+
 }  // namespace dae

@@ -336,7 +336,7 @@ __device__ __forceinline__ void wta_impl(const WtaArgs& A) {
     const int k4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (k4 >= A.K) return;
     const int s = blockIdx.y;
-    if (s >= A.nsplit_dense + A.nsplit_pairs + (A.pext ? 1 : 0)) return;
+    if (s >= A.nsplit_dense + A.nsplit_pairs + (A.pext ? 1 : 0) + (A.gy ? 1 : 0)) return;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (s < A.nsplit_dense) {
         const int per = (A.N + A.nsplit_dense - 1) / A.nsplit_dense;
@@ -378,6 +378,13 @@ __device__ __forceinline__ void wta_impl(const WtaArgs& A) {
             const float av = (float)(A.dt2 * A.fe_w[p]);
             fma4(acc, __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4)), av);
         }
+    } else if (A.gy && s == A.nsplit_dense + A.nsplit_pairs + (A.pext ? 1 : 0)) {
+        // G x_y from the Gram tiles of the output stage (the dense W_L^T M y)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float v = (k4 + u < A.K) ? A.gy[k4 + u] : 0.f;
+            if (u == 0) acc.x = v; else if (u == 1) acc.y = v; else if (u == 2) acc.z = v; else acc.w = v;
+        }
     } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -406,7 +413,7 @@ void launch_wta_batched(cudaStream_t s, const WtaArgs* d_args, int n_sys, int ma
 }
 
 void launch_wta(cudaStream_t s, const WtaArgs& a) {
-    dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs + (a.pext ? 1 : 0));
+    dim3 grid((a.K + 1023) / 1024, a.nsplit_dense + a.nsplit_pairs + (a.pext ? 1 : 0) + (a.gy ? 1 : 0));
     k_wta<<<grid, 256, 0, s>>>(a);
 }
 

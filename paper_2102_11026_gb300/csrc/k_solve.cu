@@ -558,22 +558,26 @@ __global__ void k_frame_end_b(const FrameArgs* __restrict__ f) {
 }
 
 __global__ void k_batch_cond(const FrameArgs* __restrict__ f, int n_sys,
-                             cudaGraphConditionalHandle h) {
+                             cudaGraphConditionalHandle h, int use, int* flag) {
     int run = 0;
     for (int i = threadIdx.x; i < n_sys; i += blockDim.x) run |= f[i].ns->done ? 0 : 1;
     run = __syncthreads_or(run);
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, run ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        if (use) cudaGraphSetConditional(h, run ? 1u : 0u);
+        if (flag) *flag = run;
+    }
 }
 
 void launch_frame_begin_batched(cudaStream_t s, const FrameArgs* f, int n_sys,
-                                cudaGraphConditionalHandle h) {
-    k_frame_begin_b<<<n_sys, 32, 0, s>>>(f, h, h != 0 ? 1 : 0);
+                                cudaGraphConditionalHandle h, int use) {
+    k_frame_begin_b<<<n_sys, 32, 0, s>>>(f, h, use);
 }
 void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys) {
     k_frame_end_b<<<n_sys, 32, 0, s>>>(f);
 }
-void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h) {
-    k_batch_cond<<<1, 256, 0, s>>>(f, n_sys, h);
+void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h,
+                       int* flag) {
+    k_batch_cond<<<1, 256, 0, s>>>(f, n_sys, h, flag ? 0 : 1, flag);
 }
 
 // One block per copy; 16-byte vectors where both ends and the size allow it.

@@ -362,57 +362,17 @@ static __device__ __noinline__ void slice_epilogue(const FwdArgs& A, const float
 }
 
 // Output-row reductions fused into the output layer's epilogue, over one tile's
-// 128 rows held in shared memory (row stride TS):  y_n = sum_j J_nj z_j + H[D,D]_n,
-// a_n = m_n y_n - dt^2 f_ext,n;  partials [J^T a | J^T M J (upper) | J^T M dJ] of
-// tile `tl` go to A.row_part (the layout of k_row_reduce).  All 128 epilogue
-// threads call this together (named barrier 1); `tile` needs 128*TS + 256 floats.
-// zs: z = (q - qbar) - dt qbar_dot (r floats) staged in shared memory by the caller.
-static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float* tile, int TS,
-                                                     int row, int n, bool wok, int tl,
-                                                     const float* zs) {
-    const int r = A.r, N = A.n_out, CP = A.Cp;
-    const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
-    const float* __restrict__ mdof = A.mdof;
-    const float* __restrict__ f_ext = A.f_ext;
-    float* __restrict__ a_out = A.a_out;
+// Partials of one 128-row block held in shared memory (row stride TS): per row k a
+// left factor L_k,i (column kShared + 3i + xoff), right factors R_k,j (column kShared +
+// 3j: J side; + 2: dJ side), a weight ms[k] and a scalar as[k];
+//   out = [sum_k L_k,i as_k | sum_k ms_k L_k,i R_k,j (upper) | sum_k ms_k L_k,i R'_k,j]
+// in the layout of k_row_reduce, by the 128 epilogue threads (named barrier 1).
+static __device__ __forceinline__ void reduce_row_block(const FwdArgs& A, float* tile, int TS,
+                                                     int row, int tl, int xoff) {
+    const int r = A.r;
     float* __restrict__ out = A.row_part + (size_t)tl * A.row_stride;
-    const double dt2 = A.dt * A.dt;
-    float* vrow = tile + (size_t)row * TS;
     float* ms = tile + (size_t)128 * TS;
     float* as = ms + 128;
-    float m = 0.f, av = 0.f;
-    if (wok && n < N) {
-        m = mdof[n];
-        const float fe = f_ext ? f_ext[n] : 0.f;
-        // this row's J and dJ in physical units (in place: the outputs are written);
-        // eight columns' loads issue before their stores
-        float y = vrow[3] * ih2;
-        for (int j0 = 0; j0 < r; j0 += 8) {
-            float Jv[8], dv[8], z[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + u < r ? j0 + u : r - 1;
-                Jv[u] = vrow[kShared + 3 * j] * ih;
-                dv[u] = vrow[kShared + 3 * j + 2] * ih3;
-                z[u] = zs[j];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (j0 + u < r) {
-                    vrow[kShared + 3 * (j0 + u)] = Jv[u];
-                    vrow[kShared + 3 * (j0 + u) + 2] = dv[u];
-                    y = fmaf(Jv[u], z[u], y);
-                }
-            }
-        }
-        av = (float)((double)m * y - dt2 * (double)fe);
-        if (a_out) a_out[n] = av;
-    } else {
-        // failed tile, or rows past N (zero rows of the padded weights): no contribution
-        for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
-    }
-    ms[row] = m;
-    as[row] = av;
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const int nsym = r * (r + 1) / 2;
     // 4x4 register blocks: threads 0-63 own blocks of J^T M J, 64-127 of J^T M dJ;
@@ -425,7 +385,7 @@ static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float*
         const int i = 4 * bi + q, j = 4 * bj + q;
         vi[q] = i < r;
         vj[q] = j < r;
-        ci[q] = kShared + 3 * (vi[q] ? i : 0);
+        ci[q] = kShared + 3 * (vi[q] ? i : 0) + xoff;
         cj[q] = kShared + 3 * (vj[q] ? j : 0) + (mat ? 2 : 0);
     }
     float acc[4][4], accp[4];
@@ -471,6 +431,113 @@ static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float*
         }
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");   // the tile is reused afterwards
+}
+
+// 128 rows held in shared memory (row stride TS):  y_n = sum_j J_nj z_j + H[D,D]_n,
+// a_n = m_n y_n - dt^2 f_ext,n;  partials [J^T a | J^T M J (upper) | J^T M dJ] of
+// tile `tl` go to A.row_part (the layout of k_row_reduce).  All 128 epilogue
+// threads call this together (named barrier 1); `tile` needs 128*TS + 256 floats.
+// zs: z = (q - qbar) - dt qbar_dot (r floats) staged in shared memory by the caller.
+static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float* tile, int TS,
+                                                     int row, int n, bool wok, int tl,
+                                                     const float* zs) {
+    const int r = A.r, N = A.n_out, CP = A.Cp;
+    const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
+    const float* __restrict__ mdof = A.mdof;
+    const float* __restrict__ f_ext = A.f_ext;
+    float* __restrict__ a_out = A.a_out;
+    const double dt2 = A.dt * A.dt;
+    float* vrow = tile + (size_t)row * TS;
+    float* ms = tile + (size_t)128 * TS;
+    float* as = ms + 128;
+    float m = 0.f, av = 0.f;
+    if (wok && n < N) {
+        m = mdof[n];
+        const float fe = f_ext ? f_ext[n] : 0.f;
+        // this row's J and dJ in physical units (in place: the outputs are written);
+        // eight columns' loads issue before their stores
+        float y = vrow[3] * ih2;
+        for (int j0 = 0; j0 < r; j0 += 8) {
+            float Jv[8], dv[8], z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u < r ? j0 + u : r - 1;
+                Jv[u] = vrow[kShared + 3 * j] * ih;
+                dv[u] = vrow[kShared + 3 * j + 2] * ih3;
+                z[u] = zs[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (j0 + u < r) {
+                    vrow[kShared + 3 * (j0 + u)] = Jv[u];
+                    vrow[kShared + 3 * (j0 + u) + 2] = dv[u];
+                    y = fmaf(Jv[u], z[u], y);
+                }
+            }
+        }
+        av = (float)((double)m * y - dt2 * (double)fe);
+        if (a_out) a_out[n] = av;
+    } else {
+        // failed tile, or rows past N (zero rows of the padded weights): no contribution
+        for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
+    }
+    ms[row] = m;
+    as[row] = av;
+    reduce_row_block(A, tile, TS, row, tl, 0);
+}
+
+// Gram form of the reductions: row k < K of the block holds p = (G X)[k] (G = W_L^T M W_L,
+// X the output layer's input columns).  With the column maps of the output epilogue
+// (J_j = col(kShared+3j)/h, dJ_j = col(kShared+3j+2)/h^3, y = col(3)/h^2 + J z) applied
+// to p and to x = X[:, k], and W_L linear,
+//   J^T M J = sum_k xJ_k pJ_k^T,  J^T M dJ = sum_k xJ_k pdJ_k^T,
+//   J^T (M y - dt^2 f_ext) = sum_k xJ_k (py_k - dt^2 (W_L^T f_ext)_k),
+// the same partials as fused_row_reduce over the N output rows.  py = (G x_y)_k goes to
+// A.gy (the reverse pass's seed W_L^T M y).
+static __device__ __forceinline__ void gram_row_reduce(const FwdArgs& A, float* tile, int TS,
+                                                    int row, int k, bool wok, int tl,
+                                                    const float* zs) {
+    const int r = A.r, K = A.K, CP = A.Cp;
+    const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
+    const double dt2 = A.dt * A.dt;
+    float* vrow = tile + (size_t)row * TS;
+    float* ms = tile + (size_t)128 * TS;
+    float* as = ms + 128;
+    float av = 0.f;
+    if (wok && k < K) {
+        const float* __restrict__ X = A.Xg;
+        const size_t ldx = A.ldxg;
+        float py = vrow[3] * ih2;
+        for (int j0 = 0; j0 < r; j0 += 8) {
+            float pj[8], pd[8], xj[8], z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u < r ? j0 + u : r - 1;
+                const int cb = kShared + 3 * j;
+                pj[u] = vrow[cb] * ih;
+                pd[u] = vrow[cb + 2] * ih3;
+                xj[u] = X[(size_t)cb * ldx + k] * ih;
+                z[u] = zs[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (j0 + u < r) {
+                    const int cb = kShared + 3 * (j0 + u);
+                    vrow[cb] = pj[u];
+                    vrow[cb + 1] = xj[u];
+                    vrow[cb + 2] = pd[u];
+                    py = fmaf(pj[u], z[u], py);
+                }
+            }
+        }
+        if (A.gy) A.gy[k] = py;
+        av = (float)((double)py - (A.pext ? dt2 * (double)A.pext[k] : 0.0));
+    } else {
+        for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
+    }
+    ms[row] = 1.f;
+    as[row] = av;
+    reduce_row_block(A, tile, TS, row, tl, 1);
 }
 
 }  // namespace tc

@@ -111,6 +111,26 @@ def test_batched_finished_strings_are_skipped(strings):
     assert max(r.evals for r in rb) > 2
 
 
+def test_batched_explicit_launches_match_graph(strings):
+    """With phase profiling on, the step runs as explicit launches (host loop over the
+    evaluations) and gives the graph's result bit for bit."""
+    S = strings
+    q0 = S.starts()
+    qa = [q.copy() for q in q0]
+    dae.dae_newton_step_batched(S.ctx, S.systems(qa), S.wls[0].state.dt)
+    dae.dae_profile_read(S.ctx)
+    dae.dae_profile_enable(S.ctx, True)
+    try:
+        qb = [q.copy() for q in q0]
+        rb = dae.dae_newton_step_batched(S.ctx, S.systems(qb), S.wls[0].state.dt)
+    finally:
+        dae.dae_profile_enable(S.ctx, False)
+    prof = dae.dae_profile_read(S.ctx)
+    assert prof["fwd_out"][1] >= max(r.evals for r in rb)
+    for a, b in zip(qa, qb):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
 def test_batched_other_precisions_match_single(prec):
     S = Strings(4, seed=9, prec=prec, v_range=(200, 500))
