@@ -137,23 +137,34 @@ def frame_weights(wl, n_frames, seed, start=0):
 
 
 # --------------------------------------------------------------- roofline --
-def out_layer_bytes(wl, prec):
-    """Algorithmic DRAM bytes of one output-layer launch: weights once, the stacked
-    activations once, the written outputs (u, H[D,D], J, dJ)."""
+def hidden_chain_bytes(wl, prec):
+    """Algorithmic DRAM bytes of one hidden forward chain launch (the dominant kernel):
+    every hidden layer's weights once, its stacked input columns read and output columns
+    written once (operand form), act'(z) and act''(z) b_j written, and the FP32 copy of
+    the output layer's input."""
     d = wl.dec
-    N, K, r = d.n_out, d.widths[-2], d.r
+    r = d.r
     C = 4 + 3 * r
     wbytes = {"fp32": 4, "tf32": 4, "bf16": 2, "bf16x3": 4}[prec]
-    return N * K * wbytes + C * K * wbytes + N * (2 + 2 * r) * 4
+    tot = 0
+    for l in range(len(d.W) - 1):
+        n_out, n_in = d.W[l].shape
+        tot += n_out * n_in * wbytes + C * n_in * wbytes + C * n_out * wbytes + n_out * (1 + r) * 4
+    tot += C * d.widths[-2] * 4
+    return tot
 
 
-def algorithmic_flops(wl):
-    """2 [P C_f + sum_{hidden} P_l (1 + r) + P_L]: stacked forward over all C_f = 3r + 4
-    columns, complex reverse pass through the hidden layers, W_L^T a."""
+def algorithmic_flops(wl, gram=True):
+    """2 [sum_hidden P_l C_f + P_out C_f + sum_hidden P_l (1 + r) + K]: the stacked forward
+    over all C_f = 3r + 4 columns (the output stage in Gram form: K x K of G plus the 12|C|
+    cubature rows of W_L; else all N x K of W_L), the complex reverse pass through the
+    hidden layers, W_L^T a."""
     d = wl.dec
     r = d.r
     P = [w.size for w in d.W]
-    return 2.0 * (sum(P) * (3 * r + 4) + sum(P[:-1]) * (1 + r) + P[-1])
+    K = d.widths[-2]
+    P_out = (K * K + 12 * wl.cub_tets.size * K) if gram else P[-1]
+    return 2.0 * ((sum(P[:-1]) + P_out) * (3 * r + 4) + sum(P[:-1]) * (1 + r) + K)
 
 
 def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
@@ -309,7 +320,7 @@ def run_ours(args):
         qd2.copy_(dev(wl.state.qbar_dot, torch.float64))
         dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[:W * n], W, q2, qd2, wl.state.dt, f_ext, opts)
         dae.dae_profile_read(ctx)
-        dae.dae_profile_enable(ctx, ["fwd_out"])
+        dae.dae_profile_enable(ctx, ["fwd_hidden"])
         reps1 = dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[W * n:(W + K) * n], K, q2, qd2,
                                 wl.state.dt, f_ext, opts)
         dae.dae_profile_enable(ctx, False)
@@ -328,23 +339,24 @@ def run_ours(args):
         evals_all = evals
     value = evals_all / (ms / 1e3)
 
-    # ---- roofline of the dominant kernel (output-layer GEMM), timed live
+    # ---- roofline of the dominant kernel (the persistent hidden forward chain), timed
+    # live with CUDA events around every launch
     peaks, peak_src = load_peaks()
-    t_out, c_out = prof["fwd_out"]
-    avg_out_ms = t_out / max(c_out, 1)
-    bytes_out = out_layer_bytes(wl, args.prec)
-    achieved = bytes_out / (avg_out_ms / 1e3) / 1e9
+    t_hid, c_hid = prof["fwd_hidden"]
+    avg_ms = t_hid / max(c_hid, 1)
+    bytes_hid = hidden_chain_bytes(wl, args.prec)
+    achieved = bytes_hid / (avg_ms / 1e3) / 1e9
     hbm = peaks["hbm_gbs"]
     traffic = load_traffic(args.workload, args.prec)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
-            "kernel": "output-layer GEMM + epilogue (%s)" % args.prec,
+            "kernel": "hidden forward chain (k_chain, %d layers, %s)" % (len(d.W) - 1, args.prec),
             "peak_source": "%s hbm_gbs" % peak_src,
-            "avg_launch_ms": avg_out_ms, "algorithmic_bytes_per_launch": bytes_out}
+            "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_hid}
     tot_ph = sum(v[0] for v in prof_all.values())
     phase_share = {k: round(v[0] / max(tot_ph, 1e-9), 4) for k, v in prof_all.items()}
     phase_ms_per_eval = {k: round(v[0] / evals2, 4) for k, v in prof_all.items()}
-    flops = algorithmic_flops(wl)
+    flops = algorithmic_flops(wl, gram=args.prec != "fp32")
 
     # ---- end to end through the C ABI with host buffers (one dae_rollout per frame)
     e2e = None
@@ -397,7 +409,7 @@ def run_ours(args):
 
 
 def load_traffic(workload, prec):
-    """DRAM bytes per output-layer launch from the committed ncu summary, if any."""
+    """DRAM bytes per hidden forward chain launch from the committed ncu summary, if any."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(p):
         with open(p) as f:
@@ -622,20 +634,22 @@ def run_strings(args):
     value = ev_step * K / (ms / 1e3)
     params = [sum(w.size for w in wl.dec.W) for wl in wls]
     bpe = {"bf16x3": 4, "bf16": 2, "tf32": 4}[args.prec]
-    # every evaluation of a string streams its decoder's weights twice (forward chain and
-    # transposed reverse chain)
-    bytes_step = float(sum(e * 2 * p * bpe for e, p in zip(evals, params)))
     peaks, peak_src = load_peaks()
-    step_gbs = bytes_step / (ms / K / 1e3) / 1e9
-    # dominant kernel: the grouped forward chain; algorithmic bytes = weights of every
-    # evaluated string (once) + its input columns and outputs, over the chain's event time
-    fwd_bytes = 0.0
+    # every evaluation of a string streams its hidden weights twice (forward chain and the
+    # transposed reverse chain) and its stacked Gram operand once ([G ; the W_L rows of its
+    # 12 x 32 cubature DOFs], K = 256)
+    fwd_bytes = bytes_step = 0.0
     for e, wl in zip(evals, wls):
-        r, V3 = wl.dec.r, wl.dec.n_out
+        r, Kw = wl.dec.r, wl.dec.widths[-2]
+        hidden = sum(w.size for w in wl.dec.W[:-1])
+        gram = (Kw + 12 * wl.cub_tets.size) * Kw
         cp = (4 + 3 * r + 15) // 16 * 16
-        act = sum(cp * n * 2 * 2 for n in wl.dec.widths[:-1])
-        outs = V3 * (2 + 2 * r) * 4
-        fwd_bytes += e * (sum(w.size for w in wl.dec.W) * bpe + act + outs)
+        act = sum(cp * n * 2 * bpe // 2 for n in wl.dec.widths[:-1])
+        outs = 12 * wl.cub_tets.size * (2 + 2 * r) * 4
+        # dominant kernel: the grouped forward chain (hidden layers + Gram operand)
+        fwd_bytes += e * ((hidden + gram) * bpe + act + outs)
+        bytes_step += e * ((2 * hidden + gram) * bpe)
+    step_gbs = bytes_step / (ms / K / 1e3) / 1e9
     t_fwd, c_fwd = prof["fwd_out"]
     achieved = fwd_bytes / (t_fwd / 1e3) / 1e9
     tot_ph = sum(v[0] for v in prof.values())

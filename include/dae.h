@@ -354,7 +354,8 @@ typedef enum {
     DAE_PHASE_WTA = 4,         /* W_L^T a */
     DAE_PHASE_BWD = 5,         /* complex-step reverse pass through the hidden layers */
     DAE_PHASE_ASSEMBLE = 6,    /* FP64 reductions, assembly, LU and Newton control */
-    DAE_N_PHASES = 7
+    DAE_PHASE_SEED = 7,        /* input columns of the stacked complex-step batch */
+    DAE_N_PHASES = 8
 } dae_phase;
 
 /* Record a CUDA event pair around every enqueued phase p with bit (1 << p) set in

@@ -454,6 +454,7 @@ dae_status ensure_gs(dae_decoder* d, const dae_mesh* m, int n_cub) {
             }
         }
         TRY(dmalloc(ctx, &w.cub_rows, (size_t)rows));
+        CU(ctx, cudaMemsetAsync(w.cub_rows, 0xff, (size_t)rows * sizeof(int), ctx->stream));
         if (!w.gy) TRY(dmalloc(ctx, &w.gy, (size_t)K));
         w.gs_rows_cap = rows;
         w.ldGs = top.ld;
@@ -563,7 +564,7 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     const int ob = out_bf16_of(d->prec);
     const int ld0 = (int)round_up(r, kKPad);
     {
-        Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
+        Phase p(ctx, DAE_PHASE_SEED, 1);
         launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0],
                     w.Xh[0], w.Xl[0], d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec);
     }
@@ -1276,7 +1277,7 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
     cudaStream_t s = ctx->stream;
     const int n = b->n;
     {
-        Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
+        Phase p(ctx, DAE_PHASE_SEED, 1);
         launch_seed_batched(s, b->seed, n, b->max_elems);
     }
     for (const auto& c : b->fwd) {

@@ -316,6 +316,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const ChainJob* Jp;
                 const ChainJob* Jlast = nullptr;
                 Item I;
+                if (grouped) {
+                    // a grouped stage's items mostly belong to different jobs: fetch all of
+                    // this CTA's descriptors up front so their latencies overlap
+                    StageWalk Wd(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
+                    while (Wd.next(Jp, I)) {
+                        prefetch_tmap(&Jp->tm[0]);
+                        prefetch_tmap(&Jp->tm[2]);
+                        if constexpr (X3) { prefetch_tmap(&Jp->tm[1]); prefetch_tmap(&Jp->tm[3]); }
+                    }
+                }
                 while (!fail && W.next(Jp, I)) {
                     const CUtensorMap* tmA = &Jp->tm[0];
                     const CUtensorMap* tmAlo = &Jp->tm[1];

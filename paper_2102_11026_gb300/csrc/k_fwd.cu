@@ -238,6 +238,11 @@ __device__ __forceinline__ void gather_row_impl(const GatherArgs& A, int i) {
         const int e = A.cub_tets[i / 12], a = (i % 12) / 3, d = i % 3;
         dof = 3 * A.tets[4 * e + a] + d;
     }
+    // a row that already holds this DOF is current: the operand rows change only here
+    // (the map reads -1 after allocation, and no DOF is negative)
+    const bool current = dof >= 0 && A.map[i] == dof;
+    __syncthreads();
+    if (current) return;
     if (threadIdx.x == 0) A.map[i] = dof;
     const size_t dst = (size_t)(A.row0 + i) * A.ld;
     if (A.dst32) {

@@ -287,7 +287,7 @@ def dae_rollout(ctx, dec, mesh, cub_tets, cub_w, n_frames, q, qdot, dt, f_ext=No
     return list(reps)[:n_frames] if reps is not None else None
 
 
-PHASES = ["fwd_hidden", "fwd_out", "rows", "cubature", "wta", "bwd", "assemble"]
+PHASES = ["fwd_hidden", "fwd_out", "rows", "cubature", "wta", "bwd", "assemble", "seed"]
 
 
 def dae_profile_enable(ctx, phases=None):
