@@ -39,15 +39,19 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 
-// Sense-reversing grid barrier, thread 0 of each CTA; false on timeout.
+// Grid barrier, thread 0 of each CTA (after a __syncthreads of its CTA); false on
+// timeout.  The arrival counter only grows: the barrier of generation g completes at
+// (g + 1) * nblocks arrivals, so nothing is reset (count == gen * nblocks between
+// barriers; the host zeroes both after a timed-out launch).  The arrival is a release
+// (it publishes the CTA's writes, ordered before it by the CTA barrier), the wait an
+// acquire.
 __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& gen) {
-    __threadfence();
     const unsigned g = gen;
-    const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
-    if (arrived == nblocks) {
-        gb->count = 0u;
-        __threadfence();
-        atomicExch(&gb->gen, g + 1u);
+    const unsigned target = (g + 1u) * nblocks;
+    unsigned old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+    if (old + 1u == target) {
+        asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(&gb->gen), "r"(g + 1u) : "memory");
     } else {
         const uint64_t t0 = globaltimer();
         while (ld_acquire(&gb->gen) == g) {
@@ -55,7 +59,6 @@ __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& gen) {
         }
     }
     gen = g + 1u;
-    __threadfence();
     return true;
 }
 
@@ -712,12 +715,15 @@ bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec) {
 // and P a power of two <= 8 (each finishes 128/P rows).  K loops of at most 8
 // k-blocks are replicated (the weights are a few hundred KB, read from L2 by each
 // copy); longer ones are split, at least 4 k-blocks per chunk.
+#ifndef DAE_REP_MAX_NK
+#define DAE_REP_MAX_NK 8
+#endif
 void chain_plan(ChainJob& job, int grid) {
     job.split = 1;
     job.rep = 1;
     int pmax = 1;
     while (pmax * 2 <= 8 && job.tiles * pmax * 2 <= grid) pmax *= 2;
-    if (job.nk <= 8) {
+    if (job.nk <= DAE_REP_MAX_NK) {
         job.rep = pmax;
     } else {
         int s = 1;
