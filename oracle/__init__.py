@@ -299,6 +299,20 @@ def aTH_regrouped(dec, q, a):
 
 # -------------------------------------------------------------------- FEM --
 
+def wnet_weights(wnet, dec, q, tet_ids=None):
+    """Cubature weights predicted by the weight network W (Sec. 5, "Weight Prediction"):
+    the latent is decoded to the full displacement u = D(q), then the four FC layers of
+    W follow, sin after each of the first three and a square after the last (the
+    non-negativity constraint).  Returns w_e for the elements tet_ids (all when None).
+    The plain definition: every layer applies to the previous layer's full output."""
+    h = decode(dec, q)
+    L = len(wnet.W)
+    for l in range(L):
+        z = np.asarray(wnet.W[l], np.float64) @ h + np.asarray(wnet.b[l], np.float64)
+        h = np.sin(z) if l < L - 1 else z * z
+    return h if tet_ids is None else h[np.asarray(tet_ids)]
+
+
 def lame(E, nu):
     mu = E / (2.0 * (1.0 + nu))
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))

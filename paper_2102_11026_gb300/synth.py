@@ -111,6 +111,33 @@ def make_decoder(widths, seed, act="tanh", out_scale=0.1, bias=True):
     return Decoder(list(widths), W, b, act)
 
 
+@dataclasses.dataclass
+class WNet:
+    widths: list            # [N, h1, h2, h3, n_tet]
+    W: list                 # float32 (n_out, n_in)
+    b: list                 # float32 (n_out,)
+
+
+def make_wnet(n_in, n_tet, seed, hidden=(64, 64, 64), out_scale=0.3, out_bias=1.0):
+    """Weight network with random weights: Xavier-normal layers n_in-h1-h2-h3-n_tet,
+    U(+-1/sqrt(fan_in)) biases; the last layer scaled by ``out_scale`` with biases
+    ``out_bias``, so the squared outputs sit around 1 (the range of the seeded
+    cubature weights they replace)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 49979687))
+    widths = [n_in] + list(hidden) + [n_tet]
+    W, b = [], []
+    for l in range(len(widths) - 1):
+        fi, fo = widths[l], widths[l + 1]
+        w = rng.standard_normal((fo, fi), dtype=np.float32) * np.float32(np.sqrt(2.0 / (fi + fo)))
+        bb = rng.uniform(-1.0, 1.0, fo).astype(np.float32) / np.float32(np.sqrt(fi))
+        if l == len(widths) - 2:
+            w *= np.float32(out_scale)
+            bb[:] = np.float32(out_bias)
+        W.append(np.ascontiguousarray(w))
+        b.append(np.ascontiguousarray(bb))
+    return WNet(widths, W, b)
+
+
 def make_grid_mesh(nx, ny, nz, seed, material="stvk", E=1e5, nu=0.4, spacing=1.0):
     """Regular vertex grid (nx*ny*nz vertices, spacing 1, origin 0), five tets
     per cube alternating with the parity of (i+j+k), positive orientation,

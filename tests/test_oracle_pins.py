@@ -452,3 +452,62 @@ def test_uJ_vjp_one_hidden_layer_closed_form():
     assert relerr(gW[0], gW1) < 1e-13
     assert relerr(gb[0], gz) < 1e-13
     assert relerr(gq[0], W1.T @ gz) < 1e-13
+
+
+# ------------------------------------------------------------ weight network --
+def _wnet(widths, W, b):
+    return synth.WNet(list(widths), [np.asarray(w, np.float32) for w in W],
+                      [np.asarray(x, np.float32) for x in b])
+
+
+def test_wnet_layer_order_on_selected_dofs():
+    """Sec. 5, Weight Prediction: u = D(q), four FC layers, sin after the first three,
+    a square after the last.  With one-hot first-layer rows picking DOFs d_i and
+    identity layers after it, w_i = sin(sin(sin(u_{d_i})))^2 exactly: a dropped sin, a
+    sin on the last layer or a square in the wrong place fails."""
+    wl = synth.small()
+    dec = wl.dec
+    N = dec.n_out
+    q = synth.newton_start(wl.state)
+    d = np.array([0, 17, 512, N - 1])
+    W1 = np.zeros((4, N), np.float32)
+    W1[np.arange(4), d] = 1.0
+    I4 = np.eye(4, dtype=np.float32)
+    net = _wnet([N, 4, 4, 4, 4], [W1, I4, I4, I4], [np.zeros(4)] * 4)
+    u = oracle.decode(dec, q)
+    want = np.sin(np.sin(np.sin(u[d]))) ** 2
+    got = oracle.wnet_weights(net, dec, q)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    # biases enter before each activation: a zero last-layer row gives b^2
+    net2 = _wnet([N, 4, 4, 4, 2], [W1, I4, I4, np.zeros((2, 4))],
+                 [np.zeros(4), np.zeros(4), np.zeros(4), np.array([0.5, -1.5])])
+    assert np.allclose(oracle.wnet_weights(net2, dec, q), [0.25, 2.25], rtol=1e-7)
+
+
+def test_wnet_at_rest_shape_closed_form():
+    """A bias-free odd decoder maps q = 0 to the rest shape (u = 0 exactly), so the
+    network reduces to its biases: w = (W4 sin(W3 sin(W2 sin(b1) + b2) + b3) + b4)^2."""
+    wl = synth.small()
+    dec = wl.dec
+    net = synth.make_wnet(dec.n_out, wl.mesh.n_tet, 3, hidden=(16, 12, 8))
+    W = [w.astype(np.float64) for w in net.W]
+    b = [x.astype(np.float64) for x in net.b]
+    h = np.sin(b[0])
+    h = np.sin(W[1] @ h + b[1])
+    h = np.sin(W[2] @ h + b[2])
+    want = (W[3] @ h + b[3]) ** 2
+    got = oracle.wnet_weights(net, dec, np.zeros(dec.r))
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
+    sel = np.array([3, 40, 7])
+    assert np.array_equal(oracle.wnet_weights(net, dec, np.zeros(dec.r), sel), got[sel])
+
+
+def test_wnet_weights_are_nonnegative_and_depend_on_q():
+    wl = synth.small()
+    net = synth.make_wnet(wl.dec.n_out, wl.mesh.n_tet, 5)
+    q = synth.newton_start(wl.state)
+    w0 = oracle.wnet_weights(net, wl.dec, q, wl.cub_tets)
+    w1 = oracle.wnet_weights(net, wl.dec, 2.0 * q, wl.cub_tets)
+    assert w0.shape == wl.cub_tets.shape and np.all(w0 >= 0) and np.all(w1 >= 0)
+    assert np.max(np.abs(w1 - w0)) > 1e-6
+    assert 0.2 < np.median(w0) < 5.0
