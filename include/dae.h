@@ -234,6 +234,29 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------------- weight network -- */
+
+/*
+ * Attach a cubature weight network W (Sec. 5, "Weight Prediction") to a decoder:
+ * the latent is decoded to u = D(q), then four FC layers of widths[0..4]
+ * (widths[0] = N, the decoder output; widths[1..3] <= 1024; widths[4] = the mesh's
+ * element count), sin after the first three and a square after the last (weights
+ * >= 0).  W[l]: row-major widths[l+1] x widths[l], b[l]: widths[l+1] (host or device;
+ * copied).  The first layer is composed with the decoder's linear output layer here,
+ * A1 (W_L x + b_L) + b1 = (A1 W_L) x + (A1 b_L + b1), so a prediction never forms u.
+ * Once attached, dae_newton_step / dae_rollout / dae_assemble_reduced accept
+ * cub_w == NULL: the weights of the cubature tets are then predicted at the first
+ * iterate of every frame (at q for dae_assemble_reduced) and held for the frame.
+ * Replaces a previously attached network.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+dae_status dae_decoder_attach_wnet(dae_decoder* dec, const int* widths, const float* const* W,
+                                   const float* const* b);
+
+/* Predicted weights w[i] of the elements tet_ids[i], i < n, at latent q (r FP64);
+ * arrays host or device; synchronizes when w is a host array. */
+dae_status dae_predict_weights(dae_ctx* ctx, const dae_decoder* dec, const double* q, int n,
+                               const int* tet_ids, float* w);
+
 /* ------------------------------------------------------ grouped systems -- */
 
 /*

@@ -272,6 +272,8 @@ void free_workspace(Workspace& w) {
     dfree(w.traj); dfree(w.qout); dfree(w.rc);
     dfree(w.G); dfree(w.xy); dfree(w.pext); dfree(w.fext_prev); dfree(w.pext_flag); dfree(w.pext_part);
     dfree(w.Gs32); dfree(w.Gsh); dfree(w.Gsl); dfree(w.cub_rows); dfree(w.gy);
+    dfree(w.wn_B1); dfree(w.wn_c1); dfree(w.wn_A2); dfree(w.wn_b2); dfree(w.wn_A3); dfree(w.wn_b3);
+    dfree(w.wn_A4); dfree(w.wn_b4); dfree(w.wn_h1); dfree(w.wn_w);
 }
 
 dae_status ensure_cubature(dae_decoder* d, int n_cub, int n_w) {
@@ -727,7 +729,24 @@ struct EvalParams {
     int use_cond = 0;
     unsigned long long* kcount = nullptr;
     int kpe = 0;
+    int wnet = 0;             // predict the cubature weights (first evaluation of a frame)
 };
+
+WnetArgs wnet_args(const dae_decoder* d, const int* tets, int n, float* w_out,
+                   const NewtonState* ns, int first_only) {
+    const Workspace& w = d->ws;
+    const Layer& top = d->layers[d->L - 1];
+    WnetArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = w.X[(d->L - 1) & 1]; a.K = top.n_in; a.ldx = top.ld;
+    a.B1 = w.wn_B1; a.c1 = w.wn_c1; a.H1 = w.wn_H1;
+    a.A2 = w.wn_A2; a.b2 = w.wn_b2; a.H2 = w.wn_H2;
+    a.A3 = w.wn_A3; a.b3 = w.wn_b3; a.H3 = w.wn_H3;
+    a.A4 = w.wn_A4; a.b4 = w.wn_b4;
+    a.tets = tets; a.n = n; a.h1 = w.wn_h1; a.w = w_out;
+    a.ns = ns; a.first_only = first_only;
+    return a;
+}
 
 dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
                         const double* q_override, const EvalParams& P) {
@@ -750,6 +769,12 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         o.pext = P.f_ext ? w.pext : nullptr;
     }
     TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o));
+    if (P.wnet && P.n_cub > 0) {
+        // cubature weights of this frame from the weight network at its first iterate
+        Phase p(ctx, DAE_PHASE_CUBATURE, 2);
+        launch_wnet(s, wnet_args(d, P.cub_tets, P.n_cub, const_cast<float*>(P.cub_w), ns,
+                                 P.control ? 1 : 0));
+    }
     if (!fused_rows) {
     RowArgs ra;
     ra.J = w.J; ra.dJ = w.dJ; ra.HDD = w.HDD; ra.mdof = m->mdof; ra.f_ext = P.f_ext;
@@ -1048,6 +1073,7 @@ dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_fra
     key.c_armijo = P.opts->c_armijo; key.max_step = P.opts->max_step;
     key.xtol = P.opts->xtol;
     key.gs = w.gs_ok ? (w.Gs32 ? (const void*)w.Gs32 : (const void*)w.Gsh) : nullptr;
+    key.wn = P.wnet ? (const void*)w.wn_B1 : nullptr;
     key.gram = (key.gram ? 1 : 0) | (gram_out(d, m) ? 2 : 0);
     if (!w.graph_ok || memcmp(&key, &w.gkey, sizeof key) != 0) {
         // kernels per evaluation: count once with a dry capture so k_control can add them
@@ -1103,14 +1129,26 @@ dae_status stage_cubature(dae_decoder* d, Stage& st, int n_cub, const int* cub_t
                           const float* cub_w, int n_w, const int** dt_out, const float** dw_out) {
     TRY(ensure_cubature(d, n_cub, n_w));
     dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
     if (n_cub > 0) {
-        CU(ctx, cudaMemcpyAsync(d->ws.cub_tets, cub_tets, (size_t)n_cub * sizeof(int),
+        CU(ctx, cudaMemcpyAsync(w.cub_tets, cub_tets, (size_t)n_cub * sizeof(int),
                                 cudaMemcpyDefault, ctx->stream));
-        CU(ctx, cudaMemcpyAsync(d->ws.cub_w, cub_w, (size_t)n_w * sizeof(float), cudaMemcpyDefault,
-                                ctx->stream));
+        if (cub_w)
+            CU(ctx, cudaMemcpyAsync(w.cub_w, cub_w, (size_t)n_w * sizeof(float), cudaMemcpyDefault,
+                                    ctx->stream));
     }
-    *dt_out = d->ws.cub_tets;
-    *dw_out = d->ws.cub_w;
+    *dt_out = w.cub_tets;
+    *dw_out = w.cub_w;
+    if (!cub_w && n_cub > 0) {
+        // weights predicted by the attached weight network (one set per frame)
+        if (w.wn_cap < n_cub) {
+            dfree(w.wn_w);
+            TRY(dmalloc(ctx, &w.wn_w, (size_t)n_cub));
+            w.wn_cap = n_cub;
+            w.graph_ok = false;
+        }
+        *dw_out = w.wn_w;
+    }
     (void)st;
     return DAE_OK;
 }
@@ -1128,10 +1166,14 @@ dae_status stage_fext(dae_decoder* d, const float* f_ext, const float** out) {
 }
 
 dae_status validate_cub(dae_ctx* ctx, const dae_mesh* m, int n_cub, const int* cub_tets,
-                        const float* cub_w) {
+                        const float* cub_w, const dae_decoder* d = nullptr) {
     if (n_cub < 0) return fail(ctx, DAE_ERR_INVALID_ARG, "n_cub < 0");
-    if (n_cub > 0 && (!cub_tets || !cub_w))
-        return fail(ctx, DAE_ERR_INVALID_ARG, "cubature arrays missing");
+    if (n_cub > 0 && !cub_tets) return fail(ctx, DAE_ERR_INVALID_ARG, "cubature tets missing");
+    if (n_cub > 0 && !cub_w && !(d && d->ws.wn_B1))
+        return fail(ctx, DAE_ERR_INVALID_ARG, "cubature weights missing (and no weight network attached)");
+    if (d && d->ws.wn_B1 && !cub_w && d->ws.wn_ntet != m->n_tet)
+        return fail(ctx, DAE_ERR_INVALID_ARG, "weight network has %d outputs for %d elements",
+                    d->ws.wn_ntet, m->n_tet);
     if (n_cub > 0 && !on_device(cub_tets)) {
         for (int i = 0; i < n_cub; ++i)
             if (cub_tets[i] < 0 || cub_tets[i] >= m->n_tet)
@@ -1746,6 +1788,103 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     return DAE_OK;
 }
 
+dae_status dae_decoder_attach_wnet(dae_decoder* d, const int* widths, const float* const* W,
+                                   const float* const* b) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = d->ctx;
+    if (!widths || !W || !b) return fail(ctx, DAE_ERR_INVALID_ARG, "widths, W and b required");
+    for (int l = 0; l < 4; ++l)
+        if (!W[l] || !b[l]) return fail(ctx, DAE_ERR_INVALID_ARG, "weight network layer %d missing", l);
+    if (widths[0] != d->N) return fail(ctx, DAE_ERR_INVALID_ARG, "weight network input %d != decoder output %d", widths[0], d->N);
+    for (int l = 1; l <= 3; ++l)
+        if (widths[l] <= 0 || widths[l] > kMaxWnetWidth)
+            return fail(ctx, DAE_ERR_UNSUPPORTED, "weight network width %d must be in [1, %d]", widths[l], kMaxWnetWidth);
+    if (widths[4] <= 0) return fail(ctx, DAE_ERR_INVALID_ARG, "weight network output width %d", widths[4]);
+    CU(ctx, cudaSetDevice(ctx->device));
+    Workspace& w = d->ws;
+    const int N = d->N, H1 = widths[1], H2 = widths[2], H3 = widths[3], T = widths[4];
+    const Layer& top = d->layers[d->L - 1];
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    dfree(w.wn_B1); dfree(w.wn_c1); dfree(w.wn_A2); dfree(w.wn_b2); dfree(w.wn_A3); dfree(w.wn_b3);
+    dfree(w.wn_A4); dfree(w.wn_b4); dfree(w.wn_h1);
+    w.wn_H1 = w.wn_H2 = w.wn_H3 = w.wn_ntet = 0;
+    float* A1 = nullptr;
+    TRY(dmalloc(ctx, &A1, (size_t)H1 * N));
+    auto up = [&](float* dst, const float* src, size_t n) {
+        return cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDefault, ctx->stream);
+    };
+    dae_status st = DAE_OK;
+    do {
+        if ((st = dmalloc(ctx, &w.wn_B1, (size_t)H1 * top.ld))) break;
+        if ((st = dmalloc(ctx, &w.wn_c1, (size_t)H1))) break;
+        if ((st = dmalloc(ctx, &w.wn_A2, (size_t)H2 * H1))) break;
+        if ((st = dmalloc(ctx, &w.wn_b2, (size_t)H2))) break;
+        if ((st = dmalloc(ctx, &w.wn_A3, (size_t)H3 * H2))) break;
+        if ((st = dmalloc(ctx, &w.wn_b3, (size_t)H3))) break;
+        if ((st = dmalloc(ctx, &w.wn_A4, (size_t)T * H3))) break;
+        if ((st = dmalloc(ctx, &w.wn_b4, (size_t)T))) break;
+        if ((st = dmalloc(ctx, &w.wn_h1, (size_t)H1))) break;
+        if (up(A1, W[0], (size_t)H1 * N) || up(w.wn_c1, b[0], H1) || up(w.wn_A2, W[1], (size_t)H2 * H1) ||
+            up(w.wn_b2, b[1], H2) || up(w.wn_A3, W[2], (size_t)H3 * H2) || up(w.wn_b3, b[2], H3) ||
+            up(w.wn_A4, W[3], (size_t)T * H3) || up(w.wn_b4, b[3], T)) {
+            st = fail(ctx, DAE_ERR_CUDA, "weight network upload failed");
+            break;
+        }
+        if (!ctx->cublas) {
+            cublasHandle_t hnd;
+            if (cublasCreate(&hnd) != CUBLAS_STATUS_SUCCESS) { st = fail(ctx, DAE_ERR_CUDA, "cublasCreate failed"); break; }
+            ctx->cublas = hnd;
+        }
+        cublasHandle_t hnd = (cublasHandle_t)ctx->cublas;
+        cublasSetStream(hnd, ctx->stream);
+        cublasSetMathMode(hnd, CUBLAS_DEFAULT_MATH);
+        // B1 = A1 W_L ([H1][ld], row-major) and c1 = A1 b_L + b1: the first layer composed
+        // with the decoder's linear output layer (column-major view: B1^T = W_L^T A1^T)
+        const float one = 1.f, zero = 0.f;
+        cublasStatus_t cs = cublasSgemm(hnd, CUBLAS_OP_N, CUBLAS_OP_N, top.ld, H1, N, &one, top.W, top.ld,
+                                        A1, N, &zero, w.wn_B1, top.ld);
+        if (cs == CUBLAS_STATUS_SUCCESS)
+            cs = cublasSgemv(hnd, CUBLAS_OP_T, N, H1, &one, A1, N, top.b, 1, &one, w.wn_c1, 1);
+        if (cs != CUBLAS_STATUS_SUCCESS) { st = fail(ctx, DAE_ERR_CUDA, "weight network composition failed (%d)", (int)cs); break; }
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { st = fail(ctx, DAE_ERR_CUDA, "weight network set-up failed"); break; }
+    } while (0);
+    dfree(A1);
+    if (st) return st;
+    w.wn_H1 = H1; w.wn_H2 = H2; w.wn_H3 = H3; w.wn_ntet = T;
+    w.graph_ok = false;
+    return DAE_OK;
+}
+
+dae_status dae_predict_weights(dae_ctx* ctx, const dae_decoder* dec_c, const double* q, int n,
+                               const int* tet_ids, float* w_out) {
+    TRY(check_common(ctx, dec_c, nullptr));
+    dae_decoder* d = const_cast<dae_decoder*>(dec_c);
+    if (!d->ws.wn_B1) return fail(ctx, DAE_ERR_INVALID_ARG, "no weight network attached");
+    if (!q || n < 0 || (n > 0 && (!tet_ids || !w_out))) return fail(ctx, DAE_ERR_INVALID_ARG, "q, tet_ids, w required");
+    if (n > 0 && !on_device(tet_ids))
+        for (int i = 0; i < n; ++i)
+            if (tet_ids[i] < 0 || tet_ids[i] >= d->ws.wn_ntet)
+                return fail(ctx, DAE_ERR_INVALID_ARG, "element %d out of range", tet_ids[i]);
+    if (n == 0) return DAE_OK;
+    const int r = d->r;
+    Stage st(ctx);
+    st.need(q, r * 8); st.need(tet_ids, (size_t)n * 4); st.need(w_out, (size_t)n * 4);
+    TRY(st.reserve(st.plan));
+    const double* dq;
+    const int* dt;
+    float* dw;
+    TRY(st.in(q, r, &dq));
+    TRY(st.in(tet_ids, n, &dt));
+    TRY(st.inout(w_out, n, &dw, false));
+    Outs o;   // hidden layers only matter: no outputs
+    TRY(enqueue_forward(d, nullptr, dq, 1.0, std::ldexp(1.0, -20), SEED_FULL, o));
+    ctx->launches += 2;
+    launch_wnet(ctx->stream, wnet_args(d, dt, n, dw, nullptr, 0));
+    CU(ctx, cudaGetLastError());
+    TRY(st.finish());
+    return DAE_OK;
+}
+
 dae_status dae_free_decoder(dae_decoder* d) {
     if (!d) return DAE_ERR_INVALID_ARG;
     cudaSetDevice(d->ctx->device);
@@ -1894,7 +2033,7 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     dae_decoder* d = const_cast<dae_decoder*>(dec_c);
     if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
     if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
-    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w, d));
     const int r = d->r;
     Stage st(ctx);
     st.need(q, r * 8);
@@ -1915,7 +2054,7 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     }
     EvalParams P;
     P.dt = dt; P.h = std::ldexp(1.0, -20); P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
-    P.w_stride = 0; P.f_ext = dfe; P.control = 0; P.opts = nullptr;
+    P.w_stride = 0; P.f_ext = dfe; P.control = 0; P.opts = nullptr; P.wnet = cub_w ? 0 : 1;
     TRY(enqueue_eval(d, m, nullptr, dq, P));
     const double* red = d->ws.red;
     const size_t rr = (size_t)r * r;
@@ -1940,7 +2079,7 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     dae_decoder* d = const_cast<dae_decoder*>(dec_c);
     if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
     if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
-    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w, d));
     dae_newton_opts opts;
     fill_opts(opts_in, &opts);
     if (opts.max_iter < 0 || opts.max_evals < 1 || opts.max_evals > 1000)
@@ -1965,7 +2104,8 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     }
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
-    P.w_stride = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    P.w_stride = cub_w ? n_cub : 0; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    P.wnet = cub_w ? 0 : 1;
     TRY(run_frames(d, m, P, 1, 1, 0, dq));
     CU(ctx, cudaMemcpyAsync(dq, d->ws.qout, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->last_ns = d->ws.hist;
@@ -2179,7 +2319,7 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     dae_decoder* d = const_cast<dae_decoder*>(dec_c);
     if (!q || !qdot || n_frames < 0) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qdot required, n_frames >= 0");
     if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
-    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w));
+    TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w, d));
     dae_newton_opts opts;
     fill_opts(opts_in, &opts);
     const int r = d->r;
@@ -2207,7 +2347,8 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     }
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
-    P.w_stride = n_cub; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    P.w_stride = cub_w ? n_cub : 0; P.f_ext = dfe; P.control = 1; P.opts = &opts;
+    P.wnet = cub_w ? 0 : 1;
     if (n_frames > 0) TRY(run_frames(d, m, P, n_frames, 0, 1, nullptr));
     CU(ctx, cudaGetLastError());
     CU(ctx, cudaMemcpyAsync(dq, w.qbar, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));

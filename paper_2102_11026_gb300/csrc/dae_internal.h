@@ -93,7 +93,7 @@ struct RollCtl {
 struct GraphKey {
     unsigned long long mesh_id;
     const void* cub_w; const void* cub_tets; const void* fe_w; const void* hist; const void* traj;
-    const void* fext; const void* gs;
+    const void* fext; const void* gs; const void* wn;
     int n_cub, gram, prec, max_iter, max_halvings, max_evals;
     double dt, h, tol, c_armijo, max_step, xtol;
 };
@@ -194,6 +194,17 @@ struct Workspace {
     CUtensorMap tmGs[2];
     bool gs_ok = false;             // stacked operand ready (G part current)
     float* gy = nullptr;            // [K] G x_y, written by the G tiles' epilogue
+    // weight network (cubature weights predicted at run time), first layer composed with
+    // the output layer: h1 = sin(B1 x + c1), x the output layer's input (real column)
+    int wn_H1 = 0, wn_H2 = 0, wn_H3 = 0, wn_ntet = 0;
+    float* wn_B1 = nullptr;         // [H1][ldx] (ldx = the output layer's ld)
+    float* wn_c1 = nullptr;         // [H1]
+    float* wn_A2 = nullptr; float* wn_b2 = nullptr;   // [H2][H1], [H2]
+    float* wn_A3 = nullptr; float* wn_b3 = nullptr;   // [H3][H2], [H3]
+    float* wn_A4 = nullptr; float* wn_b4 = nullptr;   // [n_tet][H3], [n_tet]
+    float* wn_h1 = nullptr;         // [H1] first-layer output
+    float* wn_w = nullptr;          // [wn_cap] predicted weights of the cubature tets
+    int wn_cap = 0;
 };
 
 }  // namespace dae
@@ -448,6 +459,21 @@ void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys);
 // sets the graph condition h (flag == nullptr) or writes *flag: 1 while any system runs
 void launch_batch_cond(cudaStream_t s, const FrameArgs* f, int n_sys, cudaGraphConditionalHandle h,
                        int* flag);
+// Weight network: h1 = sin(B1 x + c1) (x = real column of the output layer's input,
+// stride 1), h2 = sin(A2 h1 + b2), h3 = sin(A3 h2 + b3), w_j = (A4[tets[j]] h3 + b4[tets[j]])^2.
+// With ns: skipped once the frame is done, and after its first evaluation when
+// first_only (the weights hold for the frame).
+constexpr int kMaxWnetWidth = 1024;   // hidden widths of the weight network
+struct WnetArgs {
+    const float* x; int K; int ldx;
+    const float* B1; const float* c1; int H1;
+    const float* A2; const float* b2; int H2;
+    const float* A3; const float* b3; int H3;
+    const float* A4; const float* b4;
+    const int* tets; int n; float* h1; float* w;
+    const NewtonState* ns; int first_only;
+};
+void launch_wnet(cudaStream_t s, const WnetArgs& a);
 // copy[i]: n bytes from src to dst (device memory), one block per copy
 struct CopyDesc { const void* src; void* dst; unsigned long long n; };
 void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);

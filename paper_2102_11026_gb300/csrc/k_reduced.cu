@@ -693,4 +693,66 @@ void launch_bwd(cudaStream_t s, const BwdArgs& a) {
     else k_bwd<36><<<grid, BW_THREADS, 0, s>>>(a);
 }
 
+// ---------------------------------------------------------- weight network --
+// Weight prediction (Sec. 5): the first layer over the output layer's input column
+// (one warp per row, lanes over K), then the small layers and the squared output rows of
+// the cubature tets in one block.
+__device__ __forceinline__ bool wnet_skip(const WnetArgs& a) {
+    return a.ns && (a.ns->done || (a.first_only && a.ns->evals != 0));
+}
+
+__global__ void __launch_bounds__(256) k_wnet_first(WnetArgs a) {
+    if (wnet_skip(a)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + warp;
+    if (i >= a.H1) return;
+    const float* __restrict__ row = a.B1 + (size_t)i * a.ldx;
+    float acc = 0.f;
+    for (int k = lane; k < a.K; k += 32) acc = fmaf(row[k], a.x[k], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.h1[i] = sinf(acc + a.c1[i]);
+}
+
+__device__ __forceinline__ void wnet_layer(const float* __restrict__ A, const float* __restrict__ b,
+                                           const float* in, int n_in, float* out, int n_out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < n_out; i += nw) {
+        float acc = 0.f;
+        for (int k = lane; k < n_in; k += 32) acc = fmaf(A[(size_t)i * n_in + k], in[k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[i] = sinf(acc + b[i]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wnet_rest(WnetArgs a) {
+    if (wnet_skip(a)) return;
+    __shared__ float h1[kMaxWnetWidth], h2[kMaxWnetWidth], h3[kMaxWnetWidth];
+    for (int i = threadIdx.x; i < a.H1; i += blockDim.x) h1[i] = a.h1[i];
+    __syncthreads();
+    wnet_layer(a.A2, a.b2, h1, a.H1, h2, a.H2);
+    __syncthreads();
+    wnet_layer(a.A3, a.b3, h2, a.H2, h3, a.H3);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < a.n; j += nw) {
+        const int t = a.tets[j];
+        const float* __restrict__ row = a.A4 + (size_t)t * a.H3;
+        float acc = 0.f;
+        for (int k = lane; k < a.H3; k += 32) acc = fmaf(row[k], h3[k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const float z = acc + a.b4[t];
+            a.w[j] = z * z;
+        }
+    }
+}
+
+void launch_wnet(cudaStream_t s, const WnetArgs& a) {
+    k_wnet_first<<<(a.H1 + 7) / 8, 256, 0, s>>>(a);
+    k_wnet_rest<<<1, 256, 0, s>>>(a);
+}
+
 }  // namespace dae

@@ -77,6 +77,8 @@ SIGNATURES = {
     "dae_newton_step": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp,
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
+    "dae_decoder_attach_wnet": ([_vp, _vp, _vp, _vp], _i),
+    "dae_predict_weights": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
     "dae_newton_step_batched": ([_vp, _i, ctypes.POINTER(dae_system), _d,
                                  ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_reduce_rows_noalloc": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp], _i),
@@ -267,6 +269,24 @@ def dae_newton_step_batched(ctx, systems, dt, opts=None, want_reports=True):
         ctx, n, arr, float(dt), ctypes.byref(opts) if opts is not None else None,
         ctypes.cast(reps, ctypes.POINTER(dae_newton_report)) if reps is not None else None))
     return list(reps)[:n] if reps is not None else None
+
+
+def dae_decoder_attach_wnet(ctx, dec, widths, W, b):
+    """W, b: lists of 4 row-major float32 arrays (host numpy or device tensors)."""
+    wa = (ctypes.c_int * 5)(*[int(x) for x in widths])
+    Ws = [np.ascontiguousarray(w, np.float32) if not hasattr(w, "data_ptr") else w for w in W]
+    bs = [np.ascontiguousarray(x, np.float32) if not hasattr(x, "data_ptr") else x for x in b]
+    Wp = (ctypes.c_void_p * 4)(*[_ptr(w, np.float32) for w in Ws])
+    bp = (ctypes.c_void_p * 4)(*[_ptr(x, np.float32) for x in bs])
+    _check(ctx, lib().dae_decoder_attach_wnet(dec, wa, Wp, bp))
+
+
+def dae_predict_weights(ctx, dec, q, tet_ids, w=None):
+    n = int(tet_ids.shape[0])
+    out = np.zeros(n, np.float32) if w is None else w
+    _check(ctx, lib().dae_predict_weights(ctx, dec, _ptr(q, np.float64), n, _ptr(tet_ids, np.int32),
+                                          _ptr(out, np.float32, n)))
+    return out
 
 
 def dae_last_report(ctx):
