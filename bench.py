@@ -45,6 +45,8 @@ def parse():
                          "profiler captures")
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--wnet", action="store_true",
+                    help="predict the cubature weights with a weight network (N-64-64-64-n_tet)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n-strings", type=int, default=320)
@@ -177,6 +179,8 @@ def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
            ("paper-scale hidden layers r=30, 30-...-4096-20400 tanh, 20x20x17 grid, Neo-Hookean"
             if args.workload == "medium" else "small decoder r=5 5-64-256-1024-3000"),
            "step": "one implicit-Euler frame", "frames": K,
+           "cubature_weights": ("predicted per frame by a weight network N-64-64-64-n_tet (sin, squared)"
+                                if getattr(args, "wnet", False) else "seeded per frame, U[0.5, 2]"),
            "l2": "inputs larger than L2 (decoder weights %.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
            "parallelism": "replicas" if world > 1 else "single GPU"}
     if evals_all is not None:
@@ -277,6 +281,10 @@ def run_ours(args):
     dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, args.prec)
     mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass, m.material,
                              m.E, m.nu)
+    if args.wnet:
+        from paper_2102_11026_gb300 import synth
+        net = synth.make_wnet(d.n_out, m.n_tet, 7)
+        dae.dae_decoder_attach_wnet(ctx, dec, net.widths, net.W, net.b)
     dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
     W, K = args.warmup, args.steps
     n = wl.cub_tets.size
@@ -284,6 +292,11 @@ def run_ours(args):
     cw_all = frame_weights(wl, W + K + 2, seed)
     cub_t = dev(wl.cub_tets, torch.int32)
     cub_w = dev(cw_all, torch.float32)
+    if args.wnet:
+        class _NoWeights:            # every slice: predicted weights (NULL)
+            def __getitem__(self, k):
+                return None
+        cub_w = _NoWeights()
     f_ext = dev(wl.f_ext, torch.float32)
     q = dev(wl.state.qbar, torch.float64)
     qd = dev(wl.state.qbar_dot, torch.float64)
@@ -365,18 +378,19 @@ def run_ours(args):
         qdh = wl.state.qbar_dot.copy()
         cwh = frame_weights(wl, K, seed, start=W)
         ev_tot = 0
-        dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, cwh[:n], 1, qh, qdh, wl.state.dt, wl.f_ext,
-                        opts)
+        dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, None if args.wnet else cwh[:n], 1, qh, qdh,
+                        wl.state.dt, wl.f_ext, opts)
         qh = wl.state.qbar.copy()
         qdh = wl.state.qbar_dot.copy()
         t0 = time.perf_counter()
         for f in range(K):
-            rp = dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, cwh[f * n:(f + 1) * n], 1, qh, qdh,
+            rp = dae.dae_rollout(ctx, dec, mesh, wl.cub_tets,
+                                 None if args.wnet else cwh[f * n:(f + 1) * n], 1, qh, qdh,
                                  wl.state.dt, wl.f_ext, opts)
             ev_tot += rp[0].evals
         te = time.perf_counter() - t0
         r = d.r
-        h2d = 2 * r * 8 + n * 4 + n * 4 + wl.f_ext.nbytes
+        h2d = 2 * r * 8 + n * 4 + (0 if args.wnet else n * 4) + wl.f_ext.nbytes
         d2h = 2 * r * 8 + 40 * 8 + 8 * 8 * 4
         e2e = {"value": ev_tot / te, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}

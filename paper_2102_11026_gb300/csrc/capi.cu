@@ -771,7 +771,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o));
     if (P.wnet && P.n_cub > 0) {
         // cubature weights of this frame from the weight network at its first iterate
-        Phase p(ctx, DAE_PHASE_CUBATURE, 2);
+        Phase p(ctx, DAE_PHASE_CUBATURE, 3);
         launch_wnet(s, wnet_args(d, P.cub_tets, P.n_cub, const_cast<float*>(P.cub_w), ns,
                                  P.control ? 1 : 0));
     }
@@ -1823,7 +1823,7 @@ dae_status dae_decoder_attach_wnet(dae_decoder* d, const int* widths, const floa
         if ((st = dmalloc(ctx, &w.wn_b3, (size_t)H3))) break;
         if ((st = dmalloc(ctx, &w.wn_A4, (size_t)T * H3))) break;
         if ((st = dmalloc(ctx, &w.wn_b4, (size_t)T))) break;
-        if ((st = dmalloc(ctx, &w.wn_h1, (size_t)H1))) break;
+        if ((st = dmalloc(ctx, &w.wn_h1, (size_t)2 * kMaxWnetWidth))) break;   // h1 | h3
         if (up(A1, W[0], (size_t)H1 * N) || up(w.wn_c1, b[0], H1) || up(w.wn_A2, W[1], (size_t)H2 * H1) ||
             up(w.wn_b2, b[1], H2) || up(w.wn_A3, W[2], (size_t)H3 * H2) || up(w.wn_b3, b[2], H3) ||
             up(w.wn_A4, W[3], (size_t)T * H3) || up(w.wn_b4, b[3], T)) {
@@ -1878,7 +1878,7 @@ dae_status dae_predict_weights(dae_ctx* ctx, const dae_decoder* dec_c, const dou
     TRY(st.inout(w_out, n, &dw, false));
     Outs o;   // hidden layers only matter: no outputs
     TRY(enqueue_forward(d, nullptr, dq, 1.0, std::ldexp(1.0, -20), SEED_FULL, o));
-    ctx->launches += 2;
+    ctx->launches += 3;
     launch_wnet(ctx->stream, wnet_args(d, dt, n, dw, nullptr, 0));
     CU(ctx, cudaGetLastError());
     TRY(st.finish());

@@ -202,7 +202,7 @@ struct Workspace {
     float* wn_A2 = nullptr; float* wn_b2 = nullptr;   // [H2][H1], [H2]
     float* wn_A3 = nullptr; float* wn_b3 = nullptr;   // [H3][H2], [H3]
     float* wn_A4 = nullptr; float* wn_b4 = nullptr;   // [n_tet][H3], [n_tet]
-    float* wn_h1 = nullptr;         // [H1] first-layer output
+    float* wn_h1 = nullptr;         // [2 kMaxWnetWidth] first-layer output | third-layer output
     float* wn_w = nullptr;          // [wn_cap] predicted weights of the cubature tets
     int wn_cap = 0;
 };

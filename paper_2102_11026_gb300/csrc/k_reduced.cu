@@ -701,17 +701,32 @@ __device__ __forceinline__ bool wnet_skip(const WnetArgs& a) {
     return a.ns && (a.ns->done || (a.first_only && a.ns->evals != 0));
 }
 
+// first layer: one block per row, the K products spread over the block's threads
 __global__ void __launch_bounds__(256) k_wnet_first(WnetArgs a) {
     if (wnet_skip(a)) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + warp;
-    if (i >= a.H1) return;
+    __shared__ float red[8];
+    const int i = blockIdx.x;
     const float* __restrict__ row = a.B1 + (size_t)i * a.ldx;
-    float acc = 0.f;
-    for (int k = lane; k < a.K; k += 32) acc = fmaf(row[k], a.x[k], acc);
+    const float* __restrict__ x = a.x;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    int k = threadIdx.x;
+    for (; k + 768 < a.K; k += 1024) {
+        acc0 = fmaf(row[k], x[k], acc0);
+        acc1 = fmaf(row[k + 256], x[k + 256], acc1);
+        acc2 = fmaf(row[k + 512], x[k + 512], acc2);
+        acc3 = fmaf(row[k + 768], x[k + 768], acc3);
+    }
+    for (; k < a.K; k += 256) acc0 = fmaf(row[k], x[k], acc0);
+    float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.h1[i] = sinf(acc + a.c1[i]);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        a.h1[i] = sinf(t + a.c1[i]);
+    }
 }
 
 __device__ __forceinline__ void wnet_layer(const float* __restrict__ A, const float* __restrict__ b,
@@ -726,7 +741,8 @@ __device__ __forceinline__ void wnet_layer(const float* __restrict__ A, const fl
     }
 }
 
-__global__ void __launch_bounds__(256) k_wnet_rest(WnetArgs a) {
+// the two small hidden layers (one block); h3 goes to the h1 buffer's tail
+__global__ void __launch_bounds__(1024) k_wnet_mid(WnetArgs a) {
     if (wnet_skip(a)) return;
     __shared__ float h1[kMaxWnetWidth], h2[kMaxWnetWidth], h3[kMaxWnetWidth];
     for (int i = threadIdx.x; i < a.H1; i += blockDim.x) h1[i] = a.h1[i];
@@ -735,24 +751,31 @@ __global__ void __launch_bounds__(256) k_wnet_rest(WnetArgs a) {
     __syncthreads();
     wnet_layer(a.A3, a.b3, h2, a.H2, h3, a.H3);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = warp; j < a.n; j += nw) {
-        const int t = a.tets[j];
-        const float* __restrict__ row = a.A4 + (size_t)t * a.H3;
-        float acc = 0.f;
-        for (int k = lane; k < a.H3; k += 32) acc = fmaf(row[k], h3[k], acc);
+    for (int i = threadIdx.x; i < a.H3; i += blockDim.x) a.h1[kMaxWnetWidth + i] = h3[i];
+}
+
+// squared output rows of the cubature tets: one warp per tet
+__global__ void __launch_bounds__(256) k_wnet_out(WnetArgs a) {
+    if (wnet_skip(a)) return;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= a.n) return;
+    const int t = a.tets[j];
+    const float* __restrict__ row = a.A4 + (size_t)t * a.H3;
+    const float* __restrict__ h3 = a.h1 + kMaxWnetWidth;
+    float acc = 0.f;
+    for (int k = lane; k < a.H3; k += 32) acc = fmaf(row[k], h3[k], acc);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            const float z = acc + a.b4[t];
-            a.w[j] = z * z;
-        }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const float z = acc + a.b4[t];
+        a.w[j] = z * z;
     }
 }
 
 void launch_wnet(cudaStream_t s, const WnetArgs& a) {
-    k_wnet_first<<<(a.H1 + 7) / 8, 256, 0, s>>>(a);
-    k_wnet_rest<<<1, 256, 0, s>>>(a);
+    k_wnet_first<<<a.H1, 256, 0, s>>>(a);
+    k_wnet_mid<<<1, 1024, 0, s>>>(a);
+    if (a.n > 0) k_wnet_out<<<(a.n + 7) / 8, 256, 0, s>>>(a);
 }
 
 }  // namespace dae

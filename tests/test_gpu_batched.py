@@ -172,3 +172,43 @@ def test_batched_argument_checks(strings):
         dae.dae_newton_step_batched(S.ctx, ys[:2], 0.0)
     assert e.value.status == -1
     assert dae.dae_newton_step_batched(S.ctx, [], 1.0 / 60) == []
+
+
+def test_batched_more_systems_than_one_chain_group():
+    """More systems than one grouped chain stage holds (512 jobs): the step runs as
+    several chain launches per direction and still equals the single-system steps."""
+    wls = []
+    for s in range(520):
+        wl = synth.custom([3, 32, 48, 3 * 2 * 2 * 10], (2, 2, 10), 8, 1000 + s)
+        wl.dec.b = [np.zeros_like(x) for x in wl.dec.b]
+        wls.append(wl)
+    ctx = dae.dae_create(0)
+    loaded = [_load(ctx, wl, "bf16x3") for wl in wls]
+    try:
+        q0 = [synth.newton_start(wl.state) for wl in wls]
+        qs = [q.copy() for q in q0]
+        ys = [dict(dec=dec, mesh=mesh, cub_tets=wl.cub_tets, cub_w=wl.cub_w, q=qs[i],
+                   qbar=wl.state.qbar, qbar_dot=wl.state.qbar_dot)
+              for i, (wl, (dec, mesh)) in enumerate(zip(wls, loaded))]
+        try:
+            reps = dae.dae_newton_step_batched(ctx, ys, wls[0].state.dt)
+        except dae.DaeError:
+            reps = None      # a system's own Newton failure: compared below per system
+        for i in (0, 255, 511, 512, 519):
+            wl = wls[i]
+            dec, mesh = loaded[i]
+            q1 = q0[i].copy()
+            try:
+                r1 = dae.dae_newton_step(ctx, dec, mesh, wl.cub_tets, wl.cub_w, q1, wl.state.qbar,
+                                         wl.state.qbar_dot, wl.state.dt)
+            except dae.DaeError:
+                continue
+            assert r1.status == 0
+            step = np.linalg.norm(q1 - q0[i])
+            assert np.linalg.norm(qs[i] - q1) <= 1e-5 * max(step, 1e-12), (i, qs[i], q1)
+        assert reps is None or sum(rp.evals for rp in reps) >= 520
+    finally:
+        for dec, mesh in loaded:
+            dae.dae_free_decoder(dec)
+            dae.dae_free_mesh(mesh)
+        dae.dae_destroy(ctx)
