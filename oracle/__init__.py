@@ -424,8 +424,63 @@ def phi_only(wl, q, qbar=None, qbar_dot=None, dt=None, cub_w=None):
     return J.T @ (Mdiag * y) + dt ** 2 * (J.T @ fC - J.T @ fext)
 
 
+def _split(U, r):
+    U = np.asarray(U, np.float64)
+    n_p = U.shape[1]
+    r = np.asarray(r, np.float64)
+    return U, n_p, r[:n_p], r[n_p:]
+
+
+def linear_subspace_system(wl, U, r, rbar, rbar_dot, dt=None, cub_w=None, want_A=True):
+    """phi and A of the combined linear + nonlinear subspace (Sec. 3.4, Eqs. 9-11):
+    u = U p + Dt(q) with the filtered decoder Dt = (I - U U^T) D (the filtering layer),
+    generalized coordinate r = [p; q], Jt = [U, (I - U U^T) J] (N x (n_p + n_q)),
+    Ht = diag(0, (I - U U^T) H).  With Delta = r - rbar, z = Delta - dt rbar_dot,
+      y   = U z_p + Jt_q z_q + Ht[Delta_q, Delta_q]
+      phi = Jt^T M y + dt^2 Jt^T (f_C - f_ext)
+      A   = Jt^T M [U, Jt_q + dJt] + diag(0, a^T Ht_q) + dt^2 Jt^T K Jt,
+      a   = M y + dt^2 (f_C - f_ext),
+    dJt the filtered Eq. 12 term of the decoder.  Plain N-row definitions, FP64."""
+    dec, mesh = wl.dec, wl.mesh
+    dt = wl.state.dt if dt is None else dt
+    cw = np.asarray(wl.cub_w if cub_w is None else cub_w, np.float64)
+    U, n_p, p, q = _split(U, r)
+    _, _, pbar, qbar = _split(U, rbar)
+    _, _, pdot, qdot = _split(U, rbar_dot)
+    filt = lambda X: X - U @ (U.T @ X)
+    d = derivs(dec, q, qbar, qbar_dot=qdot, dt=dt)
+    Jq = filt(d["J"])
+    HDD = filt(d["HDD"])
+    dJ = filt(d["dJ"])
+    u = U @ p + filt(d["u"])
+    Jt = np.concatenate([U, Jq], axis=1)
+    zp = (p - pbar) - dt * pdot
+    zq = (q - qbar) - dt * qdot
+    Mdiag = mass_diag(mesh)
+    fext = np.asarray(wl.f_ext, np.float64)
+    en, fe, Ke, stat = tets_fk(mesh, u, wl.cub_tets, want_K=want_A)
+    if np.any(stat == -7):
+        raise Inverted("inverted cubature tet")
+    dofs = tet_dofs(mesh, wl.cub_tets)
+    fC = np.zeros(dec.n_out)
+    np.add.at(fC, dofs.reshape(-1), (cw[:, None] * fe).reshape(-1))
+    y = U @ zp + Jq @ zq + HDD
+    a = Mdiag * y + dt ** 2 * (fC - fext)
+    phi = Jt.T @ (Mdiag * y) + dt ** 2 * (Jt.T @ fC - Jt.T @ fext)
+    out = dict(phi=phi, u=u, Jt=Jt, energy=float(np.sum(cw * en)), a=a)
+    if want_A:
+        n = Jt.shape[1]
+        Je = Jt[dofs]
+        Kr = np.einsum("e,eai,eab,ebj->ij", cw, Je, Ke, Je)
+        right = np.concatenate([U, Jq + dJ], axis=1)
+        aH = np.zeros((n, n))
+        aH[n_p:, n_p:] = aTH(dec, q, filt(a))       # a^T Ht_q = ((I - U U^T) a)^T H
+        out.update(A=Jt.T @ (Mdiag[:, None] * right) + aH + dt ** 2 * Kr, Kr=Kr, aH=aH)
+    return out
+
+
 def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvings=8,
-                 cub_w=None, qbar=None, qbar_dot=None, dt=None, max_step=0.5, xtol=1e-6):
+                 cub_w=None, qbar=None, qbar_dot=None, dt=None, max_step=0.5, xtol=1e-6, U=None):
     """Implicit-Euler Newton iteration on phi(q) = 0 (Eq. 7) with A from Eq. 11.
 
     Each iteration solves A delta = -phi (LU, partial pivoting) and backtracks
@@ -433,7 +488,9 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
     max_step / |delta|_inf) (no cap when max_step is 0).  Stops when
     |phi| <= tol * max(1, |phi_0|), or when the next step is negligible,
     |delta|_inf <= xtol * max(1, |q|_inf) (q is then the solution; xtol = 0 turns
-    this test off).  Returns (q, report dict).
+    this test off).  Returns (q, report dict).  With a linear basis U (N x n_p) the
+    unknown is r = [p; q] and the system is linear_subspace_system (qbar, qbar_dot and
+    q0 are then (n_p + n_q)-vectors).
     """
     st = wl.state
     qbar = st.qbar if qbar is None else qbar
@@ -442,7 +499,12 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
     q = (qbar + dt * qbar_dot) if q0 is None else np.asarray(q0, np.float64).copy()
     max_iter = wl.max_iter if max_iter is None else max_iter
     kw = dict(qbar=qbar, qbar_dot=qbar_dot, dt=dt, cub_w=cub_w)
-    rs = reduced_system(wl, q, **kw)
+
+    def reduced_system_(wl_, x, **k):
+        if U is None:
+            return reduced_system(wl_, x, **k)
+        return linear_subspace_system(wl_, U, x, k["qbar"], k["qbar_dot"], k["dt"], k["cub_w"])
+    rs = reduced_system_(wl, q, **kw)
     phi0 = np.linalg.norm(rs["phi"])
     hist = [phi0]
     it = 0
@@ -458,7 +520,7 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
         for _ in range(max_halvings + 1):
             qt = q + alpha * delta
             try:
-                rt = reduced_system(wl, qt, **kw)
+                rt = reduced_system_(wl, qt, **kw)
                 mt = float(rt["phi"] @ rt["phi"])
                 ok = mt <= (1.0 - 2.0 * c_armijo * alpha) * m0
             except Inverted:

@@ -138,6 +138,20 @@ def make_wnet(n_in, n_tet, seed, hidden=(64, 64, 64), out_scale=0.3, out_bias=1.
     return WNet(widths, W, b)
 
 
+def make_linear_basis(N, n_p, seed):
+    """Orthonormal N x n_p basis (unit, mutually orthogonal columns, as the paper's PCA
+    basis): QR of a seeded Gaussian matrix.  float32."""
+    rng = np.random.Generator(np.random.PCG64(seed + 86028121))
+    Q, _ = np.linalg.qr(rng.standard_normal((N, n_p)))
+    return np.ascontiguousarray(Q.astype(np.float32))
+
+
+def make_linear_state(n_p, seed, p_std=0.5, pdot_std=0.1):
+    """pbar ~ N(0, p_std^2), pbar_dot ~ N(0, pdot_std^2) (float64)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 32452867))
+    return rng.normal(0.0, p_std, n_p), rng.normal(0.0, pdot_std, n_p)
+
+
 def make_grid_mesh(nx, ny, nz, seed, material="stvk", E=1e5, nu=0.4, spacing=1.0):
     """Regular vertex grid (nx*ny*nz vertices, spacing 1, origin 0), five tets
     per cube alternating with the parity of (i+j+k), positive orientation,

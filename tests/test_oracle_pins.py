@@ -511,3 +511,70 @@ def test_wnet_weights_are_nonnegative_and_depend_on_q():
     assert w0.shape == wl.cub_tets.shape and np.all(w0 >= 0) and np.all(w1 >= 0)
     assert np.max(np.abs(w1 - w0)) > 1e-6
     assert 0.2 < np.median(w0) < 5.0
+
+
+# ---------------------------------------------------- linear + nonlinear subspace --
+def _linear_case(n_p=2, material="stvk"):
+    wl = tiny_workload(material=material)
+    U = synth.make_linear_basis(wl.dec.n_out, n_p, 4).astype(np.float64)
+    pb, pd = synth.make_linear_state(n_p, 4, p_std=0.3)
+    rbar = np.concatenate([pb, wl.state.qbar])
+    rdot = np.concatenate([pd, wl.state.qbar_dot])
+    rng = np.random.default_rng(11)
+    r = rbar + wl.state.dt * rdot + rng.normal(0, 0.05, rbar.size)
+    return wl, U, r, rbar, rdot
+
+
+@pytest.mark.parametrize("material", ["stvk", "neohookean"])
+def test_linear_subspace_A_is_jacobian_of_phi(material):
+    """Eq. 11 for r = [p; q]: every block of A (U^T M U, U^T M (J + dJ), J^T M U, the
+    q block with a^T H, dt^2 Jt^T K Jt) equals the central-difference Jacobian of phi."""
+    wl, U, r, rbar, rdot = _linear_case(material=material)
+    rs = oracle.linear_subspace_system(wl, U, r, rbar, rdot)
+    n = r.size
+    eps = 1e-6
+    A_fd = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n); e[k] = eps
+        A_fd[:, k] = (oracle.linear_subspace_system(wl, U, r + e, rbar, rdot, want_A=False)["phi"]
+                      - oracle.linear_subspace_system(wl, U, r - e, rbar, rdot, want_A=False)["phi"]) / (2 * eps)
+    assert relerr(rs["A"], A_fd) < 1e-6
+    # the p block is the linear subspace's own inertia + stiffness
+    n_p = U.shape[1]
+    assert relerr(rs["A"][:n_p, :n_p], U.T @ (oracle.mass_diag(wl.mesh)[:, None] * U)
+                  + wl.state.dt ** 2 * rs["Kr"][:n_p, :n_p]) < 1e-12
+
+
+def test_linear_subspace_without_basis_is_the_decoder_system():
+    wl = tiny_workload()
+    q = synth.newton_start(wl.state)
+    U0 = np.zeros((wl.dec.n_out, 0))
+    a = oracle.linear_subspace_system(wl, U0, q, wl.state.qbar, wl.state.qbar_dot)
+    b = oracle.reduced_system(wl, q)
+    assert relerr(a["phi"], b["phi"]) < 1e-13 and relerr(a["A"], b["A"]) < 1e-13
+
+
+def test_filtered_decoder_is_orthogonal_to_the_linear_subspace():
+    """The filtering layer makes U^T Dt(q) = 0 and U^T Jt_q = 0 (Eq. 9's constraint), and
+    u = U p + Dt(q)."""
+    wl, U, r, rbar, rdot = _linear_case(n_p=3)
+    rs = oracle.linear_subspace_system(wl, U, r, rbar, rdot)
+    n_p = U.shape[1]
+    Dt = rs["u"] - U @ r[:n_p]
+    # U holds FP32 values (orthonormal to ~1e-7): the projector is exact up to that
+    e = np.max(np.abs(U.T @ U - np.eye(n_p)))
+    assert e < 1e-6
+    assert np.max(np.abs(U.T @ Dt)) < 10 * e * np.max(np.abs(Dt))
+    assert np.max(np.abs(U.T @ rs["Jt"][:, n_p:])) < 10 * e * np.max(np.abs(rs["Jt"][:, n_p:]))
+    assert np.allclose(U.T @ rs["u"], (U.T @ U) @ r[:n_p], atol=10 * e * np.max(np.abs(Dt)))
+
+
+def test_linear_subspace_newton_converges_quadratically():
+    wl, U, r, rbar, rdot = _linear_case()
+    r0 = rbar + wl.state.dt * rdot
+    rq, rep = oracle.newton_solve(wl, q0=r0, qbar=rbar, qbar_dot=rdot, U=U, max_iter=6, xtol=0)
+    h = rep["phi_hist"]
+    assert rep["converged"] and len(h) >= 3
+    assert h[-1] < 1e-10 * h[0]
+    ks = [k for k in range(1, len(h) - 1) if h[k] < 1e-2 * h[0] and h[k + 1] > 1e-14]
+    assert all(h[k + 1] <= 10.0 * h[k] ** 2 / h[0] for k in ks)
