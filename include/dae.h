@@ -234,6 +234,23 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
                        const dae_newton_opts* opts, double* q_traj,
                        dae_newton_report* reports);
 
+/* ------------------------------------------------------- linear subspace -- */
+
+/*
+ * Add a linear (PCA) subspace to a decoder (Sec. 3.3-3.4, Eqs. 9-11):
+ * u = U p + (I - U U^T) D(q), the unknown becomes r = [p; q] (np + r entries,
+ * np + r <= 32), Jt = [U, (I - U U^T) J], Ht = diag(0, (I - U U^T) H).
+ *   U  np x N basis, row a = basis vector a (unit, mutually orthogonal; host or
+ *      device; copied).  The filtering layer (I - U U^T) is folded into the output
+ *      layer's weights and bias here, once.
+ * Afterwards dae_newton_step / dae_rollout / dae_assemble_reduced take and return
+ * (np + r)-vectors q = [p; q], qbar, qbar_dot (phi, A, terms are (np + r)-sized) and
+ * need the Gram form (a tensor-core precision and 2K <= N); dae_eval_derivs still
+ * returns the filtered decoder's derivatives (r columns).  Not with a weight network
+ * or in a grouped step.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+dae_status dae_decoder_attach_linear(dae_decoder* dec, int np, const float* U);
+
 /* ------------------------------------------------------- weight network -- */
 
 /*

@@ -274,12 +274,13 @@ void free_workspace(Workspace& w) {
     dfree(w.Gs32); dfree(w.Gsh); dfree(w.Gsl); dfree(w.cub_rows); dfree(w.gy);
     dfree(w.wn_B1); dfree(w.wn_c1); dfree(w.wn_A2); dfree(w.wn_b2); dfree(w.wn_A3); dfree(w.wn_b3);
     dfree(w.wn_A4); dfree(w.wn_b4); dfree(w.wn_h1); dfree(w.wn_w);
+    dfree(w.V); dfree(w.UMU); dfree(w.Uf); dfree(w.zpv); dfree(w.lin_part);
 }
 
 dae_status ensure_cubature(dae_decoder* d, int n_cub, int n_w) {
     dae_ctx* ctx = d->ctx;
     Workspace& w = d->ws;
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     w.cub_stride = r + r * (r + 1) / 2;
     if (n_cub > w.cub_cap) {
         CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -558,7 +559,7 @@ dae_status build_chains(dae_decoder* d) {
 }
 
 dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* q_override,
-                           double dt, double h, int mode, const Outs& o) {
+                           double dt, double h, int mode, const Outs& o, int off = 0) {
     dae_ctx* ctx = d->ctx;
     Workspace& w = d->ws;
     cudaStream_t s = ctx->stream;
@@ -567,8 +568,8 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     const int ld0 = (int)round_up(r, kKPad);
     {
         Phase p(ctx, DAE_PHASE_SEED, 1);
-        launch_seed(s, ns, q_override, w.qbar, w.qbar_dot, dt, h, mode, r, w.Cp, ld0, w.X[0],
-                    w.Xh[0], w.Xl[0], d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec);
+        launch_seed(s, ns, q_override, w.qbar + off, w.qbar_dot + off, dt, h, mode, r, w.Cp, ld0,
+                    w.X[0], w.Xh[0], w.Xl[0], d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec, off);
     }
     const bool chain = d->ws.chain_ok;
     if (chain) {
@@ -634,10 +635,12 @@ bool use_gram(const dae_decoder* d) {
 }
 
 // G = W_L^T diag(m) W_L (set-up, once per decoder/mesh pair; cuBLAS SGEMM in FP32 over row chunks)
+dae_status ensure_linear_terms(dae_decoder* d, const dae_mesh* m);
+
 dae_status ensure_gram(dae_decoder* d, const dae_mesh* m) {
     dae_ctx* ctx = d->ctx;
     Workspace& w = d->ws;
-    if (w.G && w.G_mesh == m->id) return DAE_OK;
+    if (w.G && w.G_mesh == m->id) return ensure_linear_terms(d, m);
     const Layer& top = d->layers[d->L - 1];
     const int K = top.n_in, N = top.n_out;
     if (!w.G) {
@@ -672,6 +675,34 @@ dae_status ensure_gram(dae_decoder* d, const dae_mesh* m) {
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(tmp);
     w.G_mesh = m->id;
+    return ensure_linear_terms(d, m);
+}
+
+// Linear subspace, per mesh: V = W_L^T M U ([ld][np]) and U^T M U ([np][np]), FP32 cuBLAS.
+dae_status ensure_linear_terms(dae_decoder* d, const dae_mesh* m) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    if (d->np == 0 || w.V_mesh == m->id) return DAE_OK;
+    const Layer& top = d->layers[d->L - 1];
+    const int N = d->N, np = d->np;
+    cublasHandle_t hnd = (cublasHandle_t)ctx->cublas;
+    cublasSetStream(hnd, ctx->stream);
+    cublasSetMathMode(hnd, CUBLAS_DEFAULT_MATH);
+    float* MU = nullptr;
+    TRY(dmalloc(ctx, &MU, (size_t)np * N));
+    // MU[a][n] = m_n U[a][n]: U rows are the first np rows of J ([np][N] = column-major N x np)
+    for (int a = 0; a < np; ++a)
+        launch_scale_rows(ctx->stream, w.J + (size_t)a * N, 1, m->mdof, N, MU + (size_t)a * N);
+    const float one = 1.f, zero = 0.f;
+    // V (column-major np x ld, = row-major [ld][np]) = (MU)^T W_L,  U^T M U = (MU)^T U
+    cublasStatus_t cs = cublasSgemm(hnd, CUBLAS_OP_T, CUBLAS_OP_T, np, top.ld, N, &one, MU, N, top.W,
+                                    top.ld, &zero, w.V, np);
+    if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasSgemm(hnd, CUBLAS_OP_T, CUBLAS_OP_N, np, np, N, &one, MU, N, w.J, N, &zero, w.UMU, np);
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(MU);
+    if (cs != CUBLAS_STATUS_SUCCESS) return fail(ctx, DAE_ERR_CUDA, "linear-subspace set-up failed (%d)", (int)cs);
+    w.V_mesh = m->id;
     return DAE_OK;
 }
 
@@ -702,6 +733,15 @@ dae_status prepare_pext(dae_decoder* d, const float* f_ext_dev) {
     if (!w.pext_valid) {
         const int one = 1;
         CU(ctx, cudaMemcpyAsync(w.pext_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (d->np > 0) {
+        // U^T f_ext for the linear subspace's rows of phi
+        const float one = 1.f, zero = 0.f;
+        cublasHandle_t hnd = (cublasHandle_t)ctx->cublas;
+        cublasSetStream(hnd, ctx->stream);
+        if (cublasSgemv(hnd, CUBLAS_OP_T, N, d->np, &one, w.J, N, f_ext_dev, 1, &zero, w.Uf, 1) !=
+            CUBLAS_STATUS_SUCCESS)
+            return fail(ctx, DAE_ERR_CUDA, "U^T f_ext failed");
     }
     ctx->launches += 4;
     launch_fext_check(ctx->stream, f_ext_dev, w.fext_prev, N, w.pext_flag);
@@ -754,9 +794,11 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     Workspace& w = d->ws;
     cudaStream_t s = ctx->stream;
     const int r = d->r, L = d->L, N = d->N;
+    const int np = d->np, n = np + r;   // linear basis size, system size
     const int sm = ctx->sm_count;
     Outs o;
-    o.u = w.u; o.J = w.J; o.dJ = w.dJ; o.HDD = w.HDD;
+    // the decoder's J follows the np rows of the linear basis U in the J buffer
+    o.u = w.u; o.J = w.J + (size_t)np * N; o.dJ = w.dJ; o.HDD = w.HDD;
     const bool fused_rows = d->prec != DAE_FP32;
     const bool gout = gram_out(d, m);
     if (fused_rows) {
@@ -768,7 +810,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         o.n_map = 12 * P.n_cub;
         o.pext = P.f_ext ? w.pext : nullptr;
     }
-    TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o));
+    TRY(enqueue_forward(d, ns, q_override, P.dt, P.h, SEED_FULL, o, np));
     if (P.wnet && P.n_cub > 0) {
         // cubature weights of this frame from the weight network at its first iterate
         Phase p(ctx, DAE_PHASE_CUBATURE, 3);
@@ -785,20 +827,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         launch_row_reduce(s, ra, w.n_row_blocks);
     }
     }
-    CubArgs ca;
-    ca.w_stride = P.w_stride;
-    ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
-    ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu; ca.lam = (float)m->lam;
-    ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
-    ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
-    ca.stride = w.cub_stride; ca.ns = ns; ca.eval_flag = w.eval_flag;
-    {
-        Phase p(ctx, DAE_PHASE_CUBATURE, P.n_cub > 0 ? 1 : 0);
-        launch_cubature(s, ca);
-    }
-    // delta_{L-1} = W_L^T a = W_L^T M y - dt^2 W_L^T f_ext + dt^2 W_L^T f_C:
-    // with the Gram matrix, W_L^T M y = G x_y (y = W_L x_y) and W_L^T f_ext is cached,
-    // so only the cubature rows of W_L are read again.
+    // wta arguments first: the linear-subspace kernel writes one of its seed rows
     const Layer& top = d->layers[L - 1];
     const int K = top.n_in;
     const int kb = (K + 1023) / 1024;
@@ -821,12 +850,38 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         // W_L^T M y = G x_y came out of the output stage
         wa.W = nullptr; wa.nsplit_dense = 0; wa.gy = w.gy;
     }
+    int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0) + (wa.gy ? 1 : 0);
+    if (np > 0) {
+        // V^T X partials (U^T M J, U^T M dJ, U^T M y) and the seed row W_L^T M U z_p
+        LinArgs la;
+        la.X = w.X[(L - 1) & 1]; la.K = K; la.ldx = top.ld; la.r = r; la.np = np;
+        la.V = w.V; la.part = w.lin_part; la.vz = w.bwd_part[0] + (size_t)in_split * K;
+        la.zpv = w.zpv; la.ns = ns; la.q_in = q_override; la.qbar = w.qbar;
+        la.qbar_dot = w.qbar_dot; la.dt = P.dt;
+        Phase p(ctx, DAE_PHASE_CUBATURE, 1);
+        launch_linear(s, la, w.lin_blocks);
+        in_split += 1;
+    }
+    CubArgs ca;
+    ca.w_stride = P.w_stride;
+    ca.np = np; ca.pv = np > 0 ? w.zpv + np : nullptr;
+    ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = n; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
+    ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu; ca.lam = (float)m->lam;
+    ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
+    ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
+    ca.stride = w.cub_stride; ca.ns = ns; ca.eval_flag = w.eval_flag;
+    {
+        Phase p(ctx, DAE_PHASE_CUBATURE, P.n_cub > 0 ? 1 : 0);
+        launch_cubature(s, ca);
+    }
+    // delta_{L-1} = W_L^T a = W_L^T M y - dt^2 W_L^T f_ext + dt^2 W_L^T f_C:
+    // with the Gram matrix, W_L^T M y = G x_y (y = W_L x_y) and W_L^T f_ext is cached,
+    // so only the cubature rows of W_L are read again.
     {
         Phase p(ctx, DAE_PHASE_WTA, (gram && !gout) ? 2 : 1);
         if (gram && !gout) launch_xy(s, w.X[(L - 1) & 1], top.ld, K, r, w.zvec, P.h, w.xy, ns);
         launch_wta(s, wa);
     }
-    int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0) + (wa.gy ? 1 : 0);
     int in_ncol = 1, cur = 0;
     const bool tc_rev = d->prec != DAE_FP32 && d->layers[0].tmR_ok;
     if (tc_rev) {
@@ -886,7 +941,11 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     if (L == 1)
         return fail(ctx, DAE_ERR_UNSUPPORTED, "a decoder needs at least one hidden layer");
     AsmArgs aa;
-    aa.r = r; aa.dt = P.dt; aa.h = P.h;
+    memset(&aa, 0, sizeof aa);
+    aa.r = n; aa.dt = P.dt; aa.h = P.h;
+    aa.rq = r; aa.np = np; aa.lin_part = w.lin_part; aa.lin_blocks = w.lin_blocks;
+    aa.UMU = w.UMU; aa.Uf = P.f_ext ? w.Uf : nullptr; aa.qbar = w.qbar; aa.qbar_dot = w.qbar_dot;
+    aa.q_in = q_override;
     aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
     aa.row_stride = w.row_stride;
     aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = P.n_cub;
@@ -904,7 +963,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
     aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
     {
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, P.n_cub > 0 ? 5 : 3);
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, (P.n_cub > 0 ? 5 : 3) + (np > 0 ? 1 : 0));
         launch_assemble(s, aa);
     }
     CU(ctx, cudaGetLastError());
@@ -916,7 +975,7 @@ dae_status ensure_frames(dae_decoder* d, int n_frames) {
     Workspace& w = d->ws;
     if (!w.rc) {
         TRY(dmalloc(ctx, &w.rc, 1));
-        TRY(dmalloc(ctx, &w.qout, (size_t)d->r));
+        TRY(dmalloc(ctx, &w.qout, (size_t)(d->np + d->r)));
     }
     if (n_frames > w.hist_cap) {
         CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -924,7 +983,7 @@ dae_status ensure_frames(dae_decoder* d, int n_frames) {
         dfree(w.traj);
         const int cap = std::max(n_frames, 16);
         TRY(dmalloc(ctx, &w.hist, (size_t)cap));
-        TRY(dmalloc(ctx, &w.traj, (size_t)cap * d->r));
+        TRY(dmalloc(ctx, &w.traj, (size_t)cap * (d->np + d->r)));
         w.hist_cap = cap;
         w.graph_ok = false;
     }
@@ -979,7 +1038,7 @@ dae_status build_graph(dae_decoder* d, const dae_mesh* m, EvalParams P) {
     cudaGraph_t g = nullptr;
     CU(ctx, cudaGraphCreate(&g, 0));
     dae_status st = DAE_OK;
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     do {
         cudaGraphConditionalHandle hout, hin;
         if (cudaGraphConditionalHandleCreate(&hout, g, 0, 0) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
@@ -1037,7 +1096,7 @@ dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_fra
     dae_ctx* ctx = d->ctx;
     Workspace& w = d->ws;
     cudaStream_t s = ctx->stream;
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     TRY(ensure_frames(d, n_frames));
     ctx->launches += 1;
     launch_roll_setup(s, w.rc, n_frames, given_q0, advance, q_in_dev, r);
@@ -1464,7 +1523,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         aa.max_step = opts.max_step; aa.xtol = opts.xtol;
         aa.max_halvings = opts.max_halvings; aa.max_evals = opts.max_evals;
         aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
-        assemble_parts(aa, &cs[3 * i], dsum[i], ctl[i]);
+        ColsumArgs c4[4];
+        assemble_parts(aa, c4, dsum[i], ctl[i]);
+        for (int k = 0; k < 3; ++k) cs[3 * i + k] = c4[k];
         for (int k = 0; k < 3; ++k) b->max_ent = std::max(b->max_ent, cs[3 * i + k].n_ent);
     }
     std::vector<ChainJob> jobs;
@@ -1796,6 +1857,7 @@ dae_status dae_decoder_attach_wnet(dae_decoder* d, const int* widths, const floa
     for (int l = 0; l < 4; ++l)
         if (!W[l] || !b[l]) return fail(ctx, DAE_ERR_INVALID_ARG, "weight network layer %d missing", l);
     if (widths[0] != d->N) return fail(ctx, DAE_ERR_INVALID_ARG, "weight network input %d != decoder output %d", widths[0], d->N);
+    if (d->np > 0) return fail(ctx, DAE_ERR_UNSUPPORTED, "weight network with a linear subspace");
     for (int l = 1; l <= 3; ++l)
         if (widths[l] <= 0 || widths[l] > kMaxWnetWidth)
             return fail(ctx, DAE_ERR_UNSUPPORTED, "weight network width %d must be in [1, %d]", widths[l], kMaxWnetWidth);
@@ -1853,6 +1915,83 @@ dae_status dae_decoder_attach_wnet(dae_decoder* d, const int* widths, const floa
     w.wn_H1 = H1; w.wn_H2 = H2; w.wn_H3 = H3; w.wn_ntet = T;
     w.graph_ok = false;
     return DAE_OK;
+}
+
+dae_status dae_decoder_attach_linear(dae_decoder* d, int np, const float* U) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = d->ctx;
+    if (!U || np < 1) return fail(ctx, DAE_ERR_INVALID_ARG, "U and np >= 1 required");
+    if (d->np > 0) return fail(ctx, DAE_ERR_INVALID_ARG, "a linear subspace is already attached");
+    if (np + d->r > kMaxR) return fail(ctx, DAE_ERR_UNSUPPORTED, "np + r = %d > %d", np + d->r, kMaxR);
+    if (d->prec == DAE_FP32 || !d->ws.chain_ok)
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the linear subspace needs a tensor-core precision");
+    if (d->ws.wn_B1) return fail(ctx, DAE_ERR_UNSUPPORTED, "weight network with a linear subspace");
+    CU(ctx, cudaSetDevice(ctx->device));
+    Workspace& w = d->ws;
+    Layer& top = d->layers[d->L - 1];
+    const int N = d->N, r = d->r, n = np + r, K = top.n_in;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    float* Ud = nullptr;
+    float* T = nullptr;
+    TRY(dmalloc(ctx, &Ud, (size_t)np * N));
+    TRY(dmalloc(ctx, &T, (size_t)np * top.ld + np));
+    CU(ctx, cudaMemcpyAsync(Ud, U, (size_t)np * N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    if (!ctx->cublas) {
+        cublasHandle_t hnd;
+        if (cublasCreate(&hnd) != CUBLAS_STATUS_SUCCESS) return fail(ctx, DAE_ERR_CUDA, "cublasCreate failed");
+        ctx->cublas = hnd;
+    }
+    cublasHandle_t hnd = (cublasHandle_t)ctx->cublas;
+    cublasSetStream(hnd, ctx->stream);
+    cublasSetMathMode(hnd, CUBLAS_DEFAULT_MATH);
+    // the filtering layer folded into the output layer: W_L <- (I - U U^T) W_L,
+    // b_L <- (I - U U^T) b_L (column-major views: W_L is ld x N, U is N x np)
+    const float one = 1.f, zero = 0.f, mone = -1.f;
+    float* tb = T + (size_t)np * top.ld;
+    cublasStatus_t cs = cublasSgemm(hnd, CUBLAS_OP_N, CUBLAS_OP_N, top.ld, np, N, &one, top.W, top.ld,
+                                    Ud, N, &zero, T, top.ld);
+    if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasSgemm(hnd, CUBLAS_OP_N, CUBLAS_OP_T, top.ld, N, np, &mone, T, top.ld, Ud, N, &one,
+                         top.W, top.ld);
+    if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasSgemv(hnd, CUBLAS_OP_T, N, np, &one, Ud, N, top.b, 1, &zero, tb, 1);
+    if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasSgemv(hnd, CUBLAS_OP_N, N, np, &mone, Ud, N, tb, 1, &one, top.b, 1);
+    if (cs != CUBLAS_STATUS_SUCCESS) {
+        dfree(Ud); dfree(T);
+        return fail(ctx, DAE_ERR_CUDA, "filtering layer failed (%d)", (int)cs);
+    }
+    // system-size buffers: J holds U in its first np rows
+    float* J2 = nullptr;
+    dae_status st = dmalloc(ctx, &J2, (size_t)n * N);
+    if (!st) {
+        CU(ctx, cudaMemcpyAsync(J2, Ud, (size_t)np * N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    dfree(Ud); dfree(T);
+    if (st) return st;
+    dfree(w.J); w.J = J2;
+    dfree(w.red); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0); dfree(w.qout);
+    TRY(dmalloc(ctx, &w.red, red_size(n)));
+    TRY(dmalloc(ctx, &w.qbar, (size_t)n));
+    TRY(dmalloc(ctx, &w.qbar_dot, (size_t)n));
+    TRY(dmalloc(ctx, &w.q0, (size_t)n));
+    if (w.rc) TRY(dmalloc(ctx, &w.qout, (size_t)n));
+    dfree(w.hist); dfree(w.traj); w.hist_cap = 0;
+    dfree(w.fe_w); dfree(w.fe_dof); dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets);
+    w.cub_cap = 0;
+    w.lin_blocks = (K + 63) / 64;
+    TRY(dmalloc(ctx, &w.V, (size_t)top.ld * np));
+    TRY(dmalloc(ctx, &w.UMU, (size_t)np * np));
+    TRY(dmalloc(ctx, &w.Uf, (size_t)np));
+    TRY(dmalloc(ctx, &w.zpv, (size_t)2 * np));
+    TRY(dmalloc(ctx, &w.lin_part, (size_t)w.lin_blocks * np * (1 + 2 * r)));
+    if (w.cub_rows)   // the stacked operand's cubature rows hold unfiltered W_L rows
+        CU(ctx, cudaMemsetAsync(w.cub_rows, 0xff, (size_t)w.gs_rows_cap * sizeof(int), ctx->stream));
+    d->np = np;
+    w.V_mesh = 0; w.G_mesh = 0; w.gs_G_mesh = 0; w.pext_valid = false; w.graph_ok = false;
+    // operand forms of the filtered output layer (splits / rounding, tensor maps, chains)
+    return dae_decoder_set_precision(d, d->prec);
 }
 
 dae_status dae_predict_weights(dae_ctx* ctx, const dae_decoder* dec_c, const double* q, int n,
@@ -2034,7 +2173,7 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     if (!q || !qbar || !qbar_dot) return fail(ctx, DAE_ERR_INVALID_ARG, "q, qbar, qbar_dot required");
     if (!(dt > 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "dt must be > 0");
     TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w, d));
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     Stage st(ctx);
     st.need(q, r * 8);
     TRY(st.reserve(st.plan));
@@ -2052,6 +2191,8 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
         TRY(prepare_pext(d, dfe));
         TRY(prepare_gram_out(d, m, n_cub));
     }
+    if (d->np > 0 && !gram_out(d, m))
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the linear subspace needs the Gram form (2K <= N)");
     EvalParams P;
     P.dt = dt; P.h = std::ldexp(1.0, -20); P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.w_stride = 0; P.f_ext = dfe; P.control = 0; P.opts = nullptr; P.wnet = cub_w ? 0 : 1;
@@ -2084,7 +2225,7 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     fill_opts(opts_in, &opts);
     if (opts.max_iter < 0 || opts.max_evals < 1 || opts.max_evals > 1000)
         return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     Stage st(ctx);
     st.need(q, r * 8);
     TRY(st.reserve(st.plan));
@@ -2102,6 +2243,8 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
         TRY(prepare_pext(d, dfe));
         TRY(prepare_gram_out(d, m, n_cub));
     }
+    if (d->np > 0 && !gram_out(d, m))
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the linear subspace needs the Gram form (2K <= N)");
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.w_stride = cub_w ? n_cub : 0; P.f_ext = dfe; P.control = 1; P.opts = &opts;
@@ -2141,6 +2284,7 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         if (d->prec != sys[0].dec->prec)
             return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: all decoders must share one precision", i);
         if (d->L < 2) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: a decoder needs a hidden layer", i);
+        if (d->np > 0) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: linear subspace in a grouped step", i);
         ds[i] = d;
         ms[i] = y.mesh;
         ncub[i] = y.n_cub;
@@ -2322,7 +2466,7 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     TRY(validate_cub(ctx, m, n_cub, cub_tets, cub_w, d));
     dae_newton_opts opts;
     fill_opts(opts_in, &opts);
-    const int r = d->r;
+    const int r = d->np + d->r;   // system size
     Stage st(ctx);
     st.need(q, r * 8); st.need(qdot, r * 8);
     st.need(q_traj, (size_t)n_frames * r * 8);
@@ -2345,6 +2489,8 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
         TRY(prepare_pext(d, dfe));
         TRY(prepare_gram_out(d, m, n_cub));
     }
+    if (d->np > 0 && !gram_out(d, m))
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the linear subspace needs the Gram form (2K <= N)");
     EvalParams P;
     P.dt = dt; P.h = opts.h_cs; P.cub_tets = dct; P.cub_w = dcw; P.n_cub = n_cub;
     P.w_stride = cub_w ? n_cub : 0; P.f_ext = dfe; P.control = 1; P.opts = &opts;

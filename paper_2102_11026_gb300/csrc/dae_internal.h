@@ -205,6 +205,14 @@ struct Workspace {
     float* wn_h1 = nullptr;         // [2 kMaxWnetWidth] first-layer output | third-layer output
     float* wn_w = nullptr;          // [wn_cap] predicted weights of the cubature tets
     int wn_cap = 0;
+    // linear subspace u = U p + (I - U U^T) D(q): U is stored as the first np rows of J
+    float* V = nullptr;             // [ldK][np] W_L^T M U (filtered W_L; per mesh)
+    float* UMU = nullptr;           // [np][np] U^T M U (per mesh)
+    float* Uf = nullptr;            // [np] U^T f_ext (zero without f_ext)
+    float* zpv = nullptr;           // [2 np] z_p = p - pbar - dt pbar_dot | p (per evaluation)
+    float* lin_part = nullptr;      // [lin_blocks][np (1 + 2r)] partials of V^T X
+    int lin_blocks = 0;
+    unsigned long long V_mesh = 0;
 };
 
 }  // namespace dae
@@ -235,6 +243,7 @@ struct dae_ctx {
 
 struct dae_decoder {
     dae_ctx* ctx = nullptr;
+    int np = 0;                     // linear (PCA) basis size; the system has np + r unknowns
     unsigned long long id = 0;      // unique per upload and precision change
     int L = 0, r = 0, N = 0;
     std::vector<int> widths;
@@ -299,10 +308,12 @@ struct FwdArgs {
     float* gy;                               // out: G x_y [K]
 };
 
+// off: the decoder's coordinates start at entry off of the state (the linear subspace's
+// np coordinates come first); qbar, qbar_dot point at the decoder's entries
 void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,
                  const double* qbar, const double* qbar_dot, double dt, double h, int mode,
                  int r, int Cp, int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
-                 int out_bf16, float* zvec);
+                 int out_bf16, float* zvec, int off = 0);
 void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
 
@@ -357,6 +368,8 @@ struct CubArgs {
     const int* cub_tets; const float* cub_w; int n_cub;
     float* fe_w; int* fe_dof; float* part; double* energy; int stride;
     const NewtonState* ns; int* eval_flag;   // set when a Neo-Hookean tet is inverted
+    // linear subspace: u += U p at the tet's DOFs (U = the first np rows of J, p = pv)
+    int np; const float* pv;
 };
 void launch_cubature(cudaStream_t s, const CubArgs& a);
 
@@ -408,6 +421,12 @@ struct AsmArgs {
     int* status;                             // sticky device status (assemble-only mode)
     cudaGraphConditionalHandle hcond; int use_cond;
     unsigned long long* kcount; int kpe;
+    // linear subspace (np > 0): r above is the system size np + rq
+    int rq, np;
+    const float* lin_part; int lin_blocks;   // V^T X partials
+    const float* UMU; const float* Uf;
+    const double* qbar; const double* qbar_dot;   // full state arrays
+    const double* q_in;                      // evaluation point when ns is null
 };
 void launch_assemble(cudaStream_t s, const AsmArgs& a);
 
@@ -426,6 +445,10 @@ struct CtlArgs {
     double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
     int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
     int* status;
+    int rq, np;                              // decoder latent size, linear basis size (r = np + rq)
+    const double* linsum;                    // [np][1 + 2 rq] sums of V^T X
+    const float* UMU; const float* Uf;
+    const double* qbar; const double* qbar_dot; const double* q_in;
 };
 struct SeedArgs {
     const NewtonState* ns; const double* qbar; const double* qbar_dot; double dt, h;
@@ -445,7 +468,7 @@ struct FrameArgs {
     NewtonState* ns; const double* q0; double* q_out; int r;
 };
 // The three column sums, the energy sum and the control step of launch_assemble.
-void assemble_parts(const AsmArgs& a, ColsumArgs cs[3], DsumArgs& ds, CtlArgs& c);
+void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c);
 void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems);
 void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_cub);
 void launch_xy_batched(cudaStream_t s, const XyArgs* d_args, int n_sys, int max_K);
@@ -474,6 +497,16 @@ struct WnetArgs {
     const NewtonState* ns; int first_only;
 };
 void launch_wnet(cudaStream_t s, const WnetArgs& a);
+// Linear-subspace terms of one evaluation: part[b][a][c] = sum over the 128 rows k of block
+// b of V[k][a] X_c[k] for the columns c = 3 (H[D,D]), kShared+3j (J), kShared+3j+2 (dJ);
+// vz[k] = (V z_p)[k] (a reverse-pass seed split: W_L^T M U z_p); block 0 also writes
+// zpv = [z_p | p] (from ns->q_trial or q_in, and the full qbar / qbar_dot).
+struct LinArgs {
+    const float* X; int K, ldx, r, np;
+    const float* V; float* part; float* vz; float* zpv;
+    const NewtonState* ns; const double* q_in; const double* qbar; const double* qbar_dot; double dt;
+};
+void launch_linear(cudaStream_t s, const LinArgs& a, int n_blocks);
 // copy[i]: n bytes from src to dst (device memory), one block per copy
 struct CopyDesc { const void* src; void* dst; unsigned long long n; };
 void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);
@@ -481,7 +514,7 @@ void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);
 inline size_t red_size(int r) {
     size_t nsym = (size_t)r * (r + 1) / 2;
     return (size_t)r + r * r + 1 + 4 * (size_t)r * r + r + (r + nsym + (size_t)r * r) + (r + nsym) +
-           (size_t)(1 + r) * r + 1;
+           (size_t)(1 + r) * r + 1 + (size_t)r * (1 + 2 * r);
 }
 
 void launch_roll_setup(cudaStream_t s, RollCtl* rc, int n_frames, int given_q0, int advance,

@@ -12,9 +12,9 @@ __device__ __forceinline__ void seed_impl(const NewtonState* ns, const double* q
                                           const double* qbar, const double* qbar_dot, double dt,
                                           double h, int mode, int r, int Cp, int ld0, float* X,
                                           __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
-                                          float* zvec) {
+                                          float* zvec, int off) {
     if (ns && ns->done) return;
-    const double* q = q_override ? q_override : ns->q_trial;
+    const double* q = (q_override ? q_override : ns->q_trial) + off;
     const int C = n_cols(r);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Cp * ld0;
          idx += gridDim.x * blockDim.x) {
@@ -39,15 +39,15 @@ __device__ __forceinline__ void seed_impl(const NewtonState* ns, const double* q
 __global__ void k_seed(const NewtonState* ns, const double* q_override, const double* qbar,
                        const double* qbar_dot, double dt, double h, int mode, int r, int Cp,
                        int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl, int out_bf16,
-                       float* zvec) {
-    seed_impl(ns, q_override, qbar, qbar_dot, dt, h, mode, r, Cp, ld0, X, Xh, Xl, out_bf16, zvec);
+                       float* zvec, int off) {
+    seed_impl(ns, q_override, qbar, qbar_dot, dt, h, mode, r, Cp, ld0, X, Xh, Xl, out_bf16, zvec, off);
 }
 
 // Grouped form (z = system): the full seed at each system's trial iterate.
 __global__ void k_seed_b(const SeedArgs* __restrict__ args) {
     const SeedArgs& a = args[blockIdx.z];
     seed_impl(a.ns, nullptr, a.qbar, a.qbar_dot, a.dt, a.h, SEED_FULL, a.r, a.Cp, a.ld0, a.X,
-              a.Xh, a.Xl, a.out_bf16, a.zvec);
+              a.Xh, a.Xl, a.out_bf16, a.zvec, 0);
 }
 
 void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems) {
@@ -59,10 +59,10 @@ void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int 
 void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override,
                  const double* qbar, const double* qbar_dot, double dt, double h, int mode,
                  int r, int Cp, int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
-                 int out_bf16, float* zvec) {
+                 int out_bf16, float* zvec, int off) {
     int n = Cp * ld0;
     k_seed<<<(n + 255) / 256, 256, 0, s>>>(ns, q_override, qbar, qbar_dot, dt, h, mode, r, Cp,
-                                          ld0, X, Xh, Xl, out_bf16, zvec);
+                                          ld0, X, Xh, Xl, out_bf16, zvec, off);
 }
 
 // ------------------------------------------------------- CUDA-core GEMM --

@@ -128,6 +128,17 @@ __device__ __forceinline__ void cubature_impl(const CubArgs& A) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) Jg[3 * a + d] = Jc[3 * v[a] + d];
     }
+    // linear subspace: (U p) on the tet's 12 DOFs (U = the first np rows of J)
+    __shared__ float sUp[kCubWarps][12];
+    if (A.np > 0) {
+        if (lane < 12) {
+            const int dof = 3 * v[lane / 3] + lane % 3;
+            float acc = 0.f;
+            for (int a = 0; a < A.np; ++a) acc = fmaf(A.J[(size_t)a * A.N + dof], A.pv[a], acc);
+            sUp[warp][lane] = acc;
+        }
+        __syncwarp();
+    }
     if (lane == 0) {
         double Bm[9];
         for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
@@ -135,8 +146,11 @@ __device__ __forceinline__ void cubature_impl(const CubArgs& A) {
         // dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
         double dU[9];
         for (int c = 0; c < 3; ++c)
-            for (int d = 0; d < 3; ++d)
-                dU[d * 3 + c] = (double)A.u[3 * v[c + 1] + d] - (double)A.u[3 * v[0] + d];
+            for (int d = 0; d < 3; ++d) {
+                double u1 = (double)A.u[3 * v[c + 1] + d], u0 = (double)A.u[3 * v[0] + d];
+                if (A.np > 0) { u1 += (double)sUp[warp][3 * (c + 1) + d]; u0 += (double)sUp[warp][d]; }
+                dU[d * 3 + c] = u1 - u0;
+            }
         double G[9], F[9], P[9], psi = 0.0, Finv_T[9], lnJ = 0.0, Sst[9];
         mat3_mul(dU, Bm, G);
         for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.0 : 0.0);
@@ -776,6 +790,53 @@ void launch_wnet(cudaStream_t s, const WnetArgs& a) {
     k_wnet_first<<<a.H1, 256, 0, s>>>(a);
     k_wnet_mid<<<1, 1024, 0, s>>>(a);
     if (a.n > 0) k_wnet_out<<<(a.n + 7) / 8, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------------- linear subspace --
+// V^T X over 64 rows k per block (the Gram-form analogue of U^T M J, U^T M dJ, U^T M y):
+// column c' = 0 -> plane 3 (h^2 H[D,D]), 1 + j -> plane kShared + 3j (h J), 1 + r + j ->
+// plane kShared + 3j + 2 (h^3 dJ); scaled by the control.  vz = V z_p per row.
+constexpr int kLinRows = 64;
+__global__ void __launch_bounds__(kLinRows) k_linear(LinArgs A) {
+    if (A.ns && A.ns->done) return;
+    __shared__ float sx[1 + 2 * kMaxR][kLinRows];
+    __shared__ float sv[kMaxR][kLinRows];
+    __shared__ float szp[kMaxR];
+    const int t = threadIdx.x, np = A.np, r = A.r, nc = 1 + 2 * r;
+    const double* q = A.q_in ? A.q_in : A.ns->q_trial;
+    if (t < np) {
+        const double zp = (q[t] - A.qbar[t]) - A.dt * A.qbar_dot[t];
+        szp[t] = (float)zp;
+        if (blockIdx.x == 0) {
+            A.zpv[t] = (float)zp;
+            A.zpv[np + t] = (float)q[t];
+        }
+    }
+    const int k = blockIdx.x * kLinRows + t;
+    const bool ok = k < A.K;
+    for (int cc = 0; cc < nc; ++cc) {
+        const int c = cc == 0 ? 3 : (cc <= r ? kShared + 3 * (cc - 1) : kShared + 3 * (cc - 1 - r) + 2);
+        sx[cc][t] = ok ? A.X[(size_t)c * A.ldx + k] : 0.f;
+    }
+    for (int a = 0; a < np; ++a) sv[a][t] = ok ? A.V[(size_t)k * np + a] : 0.f;
+    __syncthreads();
+    if (ok) {
+        float acc = 0.f;
+        for (int a = 0; a < np; ++a) acc = fmaf(sv[a][t], szp[a], acc);
+        A.vz[k] = acc;
+    }
+    float* out = A.part + (size_t)blockIdx.x * np * nc;
+    for (int pi = t; pi < np * nc; pi += kLinRows) {
+        const int a = pi / nc, cc = pi % nc;
+        float acc = 0.f;
+#pragma unroll 8
+        for (int kk = 0; kk < kLinRows; ++kk) acc = fmaf(sv[a][kk], sx[cc][kk], acc);
+        out[pi] = acc;
+    }
+}
+
+void launch_linear(cudaStream_t s, const LinArgs& a, int n_blocks) {
+    k_linear<<<n_blocks, kLinRows, 0, s>>>(a);
 }
 
 }  // namespace dae

@@ -236,11 +236,36 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
             reinterpret_cast<int*>(&S)[i] = reinterpret_cast<const int*>(C.ns)[i];
     }
     __syncthreads();
+    // linear subspace (np > 0): unknowns [p; q], decoder partials over rq = r - np
+    const int np = C.np, rq = np > 0 ? C.rq : r, nsq = rq * (rq + 1) / 2, nc = 1 + 2 * rq;
+    const double inv_h3 = inv_h * inv_h * inv_h;
+    __shared__ double szp[kMaxR], szq[kMaxR];
+    if (np > 0) {
+        const double* qe = C.control ? S.q_trial : C.q_in;
+        for (int i = t; i < r; i += blockDim.x) {
+            const double z = (qe[i] - C.qbar[i]) - C.dt * C.qbar_dot[i];
+            if (i < np) szp[i] = z; else szq[i - np] = z;
+        }
+        __syncthreads();
+    }
+    auto umj = [&](int a, int j) { return C.linsum[a * nc + 1 + j] * inv_h; };          // U^T M J
+    auto umdj = [&](int a, int j) { return C.linsum[a * nc + 1 + rq + j] * inv_h3; };   // U^T M dJ
     for (int e = t; e < r * r; e += blockDim.x) {
         const int i = e % r, j = e / r;   // column-major (i, j)
-        const double ah = 0.5 * inv_h * (C.bwdsum[(1 + j) * r + i] + C.bwdsum[(1 + i) * r + j]);
-        const double mr = C.rowsum[r + upper_idx(i, j, r)];
-        const double b = C.rowsum[r + nsym + i * r + j];
+        double ah = 0.0, mr, b = 0.0;
+        if (i >= np && j >= np) {
+            const int qi = i - np, qj = j - np;
+            ah = 0.5 * inv_h * (C.bwdsum[(1 + qj) * rq + qi] + C.bwdsum[(1 + qi) * rq + qj]);
+            mr = C.rowsum[rq + upper_idx(qi, qj, rq)];
+            b = C.rowsum[rq + nsq + qi * rq + qj];
+        } else if (i < np && j < np) {
+            mr = (double)C.UMU[i * np + j];              // U^T M U
+        } else if (i < np) {
+            mr = umj(i, j - np);                         // U^T M [J + dJ]
+            b = umdj(i, j - np);
+        } else {
+            mr = umj(j, i - np);                         // J^T M U
+        }
         const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
         const double a = ah + mr + b + dt2 * kr;
         aH[e] = ah; Mr[e] = mr; Bm[e] = b; Kr[e] = kr;
@@ -250,7 +275,18 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     for (int i = t; i < r; i += blockDim.x) {
         const double g = C.have_cub ? C.cubsum[i] : 0.0;
         gint[i] = g;
-        const double p = C.rowsum[i] + dt2 * g;
+        double p;
+        if (i >= np) {
+            // J^T (M y_q - dt^2 f_ext) + J^T M U z_p + dt^2 J^T f_C
+            const int qi = i - np;
+            p = C.rowsum[qi] + dt2 * g;
+            for (int a = 0; a < np; ++a) p += umj(a, qi) * szp[a];
+        } else {
+            // U^T M U z_p + U^T M (H[D,D] + J z_q) + dt^2 U^T (f_C - f_ext)
+            p = C.linsum[i * nc] * inv_h * inv_h + dt2 * (g - (C.Uf ? (double)C.Uf[i] : 0.0));
+            for (int b = 0; b < np; ++b) p += (double)C.UMU[i * np + b] * szp[b];
+            for (int j = 0; j < rq; ++j) p += umj(i, j) * szq[j];
+        }
         phi[i] = p;
         sphi[i] = p;
         if (!isfinite(p)) nonfinite = 1;
@@ -377,18 +413,22 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
 
 __global__ void k_control(CtlArgs C) { control_impl(C); }
 
-void assemble_parts(const AsmArgs& a, ColsumArgs cs[3], DsumArgs& ds, CtlArgs& c) {
-    const int r = a.r;
-    const int nsym = r * (r + 1) / 2;
+void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c) {
+    const int r = a.r;                       // system size (np + rq)
+    const int np = a.np, rq = np > 0 ? a.rq : r;
+    const int nsym = r * (r + 1) / 2, nsq = rq * (rq + 1) / 2;
     // scratch doubles live after the terms block of red
     double* base = a.red + (r + r * r + 1 + 4 * r * r + r);
     double* rowsum = base;
     double* cubsum = rowsum + (r + nsym + r * r);
     double* bwdsum = cubsum + (r + nsym);
     double* esum = bwdsum + (1 + r) * r;
-    cs[0] = ColsumArgs{a.row_part, a.n_row_blocks, a.row_stride, r + nsym + r * r, rowsum, a.ns};
+    double* linsum = esum + 1;
+    cs[0] = ColsumArgs{a.row_part, a.n_row_blocks, a.row_stride, rq + nsq + rq * rq, rowsum, a.ns};
     cs[1] = ColsumArgs{a.cub_part, a.n_cub, a.cub_stride, a.n_cub > 0 ? r + nsym : 0, cubsum, a.ns};
-    cs[2] = ColsumArgs{a.bwd_part, a.bwd_split, (1 + r) * r, (1 + r) * r, bwdsum, a.ns};
+    cs[2] = ColsumArgs{a.bwd_part, a.bwd_split, (1 + rq) * rq, (1 + rq) * rq, bwdsum, a.ns};
+    cs[3] = ColsumArgs{a.lin_part, a.lin_blocks, np * (1 + 2 * rq), np > 0 ? np * (1 + 2 * rq) : 0,
+                       linsum, a.ns};
     ds = DsumArgs{a.cub_energy, a.n_cub, esum, a.ns};
     memset(&c, 0, sizeof c);
     c.r = r; c.dt = a.dt; c.h = a.h;
@@ -399,10 +439,12 @@ void assemble_parts(const AsmArgs& a, ColsumArgs cs[3], DsumArgs& ds, CtlArgs& c
     c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
     c.eval_flag = a.eval_flag; c.status = a.status;
     c.hcond = a.hcond; c.use_cond = a.use_cond; c.kcount = a.kcount; c.kpe = a.kpe;
+    c.rq = rq; c.np = np; c.linsum = linsum; c.UMU = a.UMU; c.Uf = a.Uf;
+    c.qbar = a.qbar; c.qbar_dot = a.qbar_dot; c.q_in = a.q_in;
 }
 
 void launch_assemble(cudaStream_t s, const AsmArgs& a) {
-    ColsumArgs cs[3];
+    ColsumArgs cs[4];
     DsumArgs ds;
     CtlArgs c;
     assemble_parts(a, cs, ds, c);
@@ -412,6 +454,7 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
         k_dsum<<<1, 256, 0, s>>>(ds.x, ds.n, ds.out, a.ns);
     }
     colsum(s, cs[2].part, cs[2].n_parts, cs[2].stride, cs[2].n_ent, cs[2].out, a.ns);
+    if (a.np > 0) colsum(s, cs[3].part, cs[3].n_parts, cs[3].stride, cs[3].n_ent, cs[3].out, a.ns);
     k_control<<<1, 256, 0, s>>>(c);
 }
 

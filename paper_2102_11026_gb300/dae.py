@@ -78,6 +78,7 @@ SIGNATURES = {
                          ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_last_report": ([_vp, ctypes.POINTER(dae_newton_report)], _i),
     "dae_decoder_attach_wnet": ([_vp, _vp, _vp, _vp], _i),
+    "dae_decoder_attach_linear": ([_vp, _i, _vp], _i),
     "dae_predict_weights": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
     "dae_newton_step_batched": ([_vp, _i, ctypes.POINTER(dae_system), _d,
                                  ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
@@ -269,6 +270,13 @@ def dae_newton_step_batched(ctx, systems, dt, opts=None, want_reports=True):
         ctx, n, arr, float(dt), ctypes.byref(opts) if opts is not None else None,
         ctypes.cast(reps, ctypes.POINTER(dae_newton_report)) if reps is not None else None))
     return list(reps)[:n] if reps is not None else None
+
+
+def dae_decoder_attach_linear(ctx, dec, U):
+    """U: (np, N) float32 rows = basis vectors (host numpy or device tensor)."""
+    Uc = U if hasattr(U, "data_ptr") else np.ascontiguousarray(U, np.float32)
+    n_p = int(Uc.shape[0])
+    _check(ctx, lib().dae_decoder_attach_linear(dec, n_p, _ptr(Uc, np.float32)))
 
 
 def dae_decoder_attach_wnet(ctx, dec, widths, W, b):
