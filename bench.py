@@ -45,6 +45,8 @@ def parse():
                          "profiler captures")
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--np", type=int, default=0,
+                    help="add a linear (PCA-style) subspace of this size to the decoder")
     ap.add_argument("--wnet", action="store_true",
                     help="predict the cubature weights with a weight network (N-64-64-64-n_tet)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -181,6 +183,7 @@ def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
            "step": "one implicit-Euler frame", "frames": K,
            "cubature_weights": ("predicted per frame by a weight network N-64-64-64-n_tet (sin, squared)"
                                 if getattr(args, "wnet", False) else "seeded per frame, U[0.5, 2]"),
+           "linear_subspace": getattr(args, "np", 0),
            "l2": "inputs larger than L2 (decoder weights %.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
            "parallelism": "replicas" if world > 1 else "single GPU"}
     if evals_all is not None:
@@ -285,6 +288,15 @@ def run_ours(args):
         from paper_2102_11026_gb300 import synth
         net = synth.make_wnet(d.n_out, m.n_tet, 7)
         dae.dae_decoder_attach_wnet(ctx, dec, net.widths, net.W, net.b)
+    QBAR0, QDOT0 = wl.state.qbar, wl.state.qbar_dot
+    if args.np > 0:
+        # linear subspace: u = U p + (I - U U^T) D(q), unknown [p; q]
+        from paper_2102_11026_gb300 import synth
+        U = synth.make_linear_basis(d.n_out, args.np, 8)
+        dae.dae_decoder_attach_linear(ctx, dec, np.ascontiguousarray(U.T))
+        pb, pd = synth.make_linear_state(args.np, 8, p_std=0.05, pdot_std=0.02)
+        QBAR0 = np.concatenate([pb, QBAR0])
+        QDOT0 = np.concatenate([pd, QDOT0])
     dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
     W, K = args.warmup, args.steps
     n = wl.cub_tets.size
@@ -298,8 +310,8 @@ def run_ours(args):
                 return None
         cub_w = _NoWeights()
     f_ext = dev(wl.f_ext, torch.float32)
-    q = dev(wl.state.qbar, torch.float64)
-    qd = dev(wl.state.qbar_dot, torch.float64)
+    q = dev(QBAR0, torch.float64)
+    qd = dev(QDOT0, torch.float64)
     opts = dae.dae_default_newton_opts()
     opts.max_iter = 5
 
@@ -329,8 +341,8 @@ def run_ours(args):
         # dominant-kernel time: CUDA events around every output-layer launch of the same
         # frames replayed with explicit launches (events cannot sit inside graph loops)
         q2, qd2 = q.clone(), qd.clone()
-        q2.copy_(dev(wl.state.qbar, torch.float64))
-        qd2.copy_(dev(wl.state.qbar_dot, torch.float64))
+        q2.copy_(dev(QBAR0, torch.float64))
+        qd2.copy_(dev(QDOT0, torch.float64))
         dae.dae_rollout(ctx, dec, mesh, cub_t, cub_w[:W * n], W, q2, qd2, wl.state.dt, f_ext, opts)
         dae.dae_profile_read(ctx)
         dae.dae_profile_enable(ctx, ["fwd_hidden"])
@@ -374,14 +386,14 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (one dae_rollout per frame)
     e2e = None
     if not args.no_e2e:
-        qh = wl.state.qbar.copy()
-        qdh = wl.state.qbar_dot.copy()
+        qh = QBAR0.copy()
+        qdh = QDOT0.copy()
         cwh = frame_weights(wl, K, seed, start=W)
         ev_tot = 0
         dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, None if args.wnet else cwh[:n], 1, qh, qdh,
                         wl.state.dt, wl.f_ext, opts)
-        qh = wl.state.qbar.copy()
-        qdh = wl.state.qbar_dot.copy()
+        qh = QBAR0.copy()
+        qdh = QDOT0.copy()
         t0 = time.perf_counter()
         for f in range(K):
             rp = dae.dae_rollout(ctx, dec, mesh, wl.cub_tets,
@@ -389,7 +401,7 @@ def run_ours(args):
                                  wl.state.dt, wl.f_ext, opts)
             ev_tot += rp[0].evals
         te = time.perf_counter() - t0
-        r = d.r
+        r = d.r + args.np
         h2d = 2 * r * 8 + n * 4 + (0 if args.wnet else n * 4) + wl.f_ext.nbytes
         d2h = 2 * r * 8 + 40 * 8 + 8 * 8 * 4
         e2e = {"value": ev_tot / te, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
