@@ -963,7 +963,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
     aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
     {
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, (P.n_cub > 0 ? 5 : 3) + (np > 0 ? 1 : 0));
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
         launch_assemble(s, aa);
     }
     CU(ctx, cudaGetLastError());

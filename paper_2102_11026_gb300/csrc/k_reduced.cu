@@ -374,22 +374,25 @@ __device__ __forceinline__ void wta_impl(const WtaArgs& A) {
         const int t = s - A.nsplit_dense;
         const int per = (A.n_pairs + A.nsplit_pairs - 1) / A.nsplit_pairs;
         const int p0 = t * per, p1 = min(A.n_pairs, p0 + per);
+        // FP32 scale (the per-pair FP64 product cost more than the row loads); all of
+        // this split's DOFs and weights first, so the row loads issue back to back
+        const float dt2 = (float)A.dt2;
         int p = p0;
-        for (; p + 4 <= p1; p += 4) {
-            float4 w[4];
-            float av[4];
+        for (; p + 8 <= p1; p += 8) {
+            int n[8];
+            float av[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int n = A.fe_dof[p + u];
-                av[u] = (float)(A.dt2 * A.fe_w[p + u]);
-                w[u] = __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4));
-            }
+            for (int u = 0; u < 8; ++u) { n[u] = __ldg(A.fe_dof + p + u); av[u] = dt2 * __ldg(A.fe_w + p + u); }
+            float4 w[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) fma4(acc, w[u], av[u]);
+            for (int u = 0; u < 8; ++u)
+                w[u] = __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n[u] * A.ldp + k4));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) fma4(acc, w[u], av[u]);
         }
         for (; p < p1; ++p) {
             const int n = A.fe_dof[p];
-            const float av = (float)(A.dt2 * A.fe_w[p]);
+            const float av = dt2 * A.fe_w[p];
             fma4(acc, __ldg(reinterpret_cast<const float4*>(A.Wp + (size_t)n * A.ldp + k4)), av);
         }
     } else if (A.gy && s == A.nsplit_dense + A.nsplit_pairs + (A.pext ? 1 : 0)) {

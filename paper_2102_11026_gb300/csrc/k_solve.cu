@@ -443,18 +443,39 @@ void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c
     c.qbar = a.qbar; c.qbar_dot = a.qbar_dot; c.q_in = a.q_in;
 }
 
-void launch_assemble(cudaStream_t s, const AsmArgs& a) {
-    ColsumArgs cs[4];
-    DsumArgs ds;
-    CtlArgs c;
-    assemble_parts(a, cs, ds, c);
-    colsum(s, cs[0].part, cs[0].n_parts, cs[0].stride, cs[0].n_ent, cs[0].out, a.ns);
-    if (a.n_cub > 0) {
-        colsum(s, cs[1].part, cs[1].n_parts, cs[1].stride, cs[1].n_ent, cs[1].out, a.ns);
-        k_dsum<<<1, 256, 0, s>>>(ds.x, ds.n, ds.out, a.ns);
+// The column sums of one evaluation in one launch (y = which sum; an empty sum skips);
+// block (0, 4) forms the energy sum.
+struct ColsumPack { ColsumArgs cs[4]; DsumArgs ds; };
+__global__ void __launch_bounds__(512) k_colsum4(const ColsumPack P) {
+    if (blockIdx.y == 4) {
+        // energy: every thread of the block takes part (tree in shared memory)
+        if (blockIdx.x != 0 || P.ds.n <= 0 || (P.ds.ns && P.ds.ns->done)) return;
+        __shared__ double sd[512];
+        const int t = threadIdx.x;
+        double acc = 0.0;
+        for (int i = t; i < P.ds.n; i += 512) acc += P.ds.x[i];
+        sd[t] = acc;
+        __syncthreads();
+        for (int o = 256; o > 0; o >>= 1) {
+            if (t < o) sd[t] += sd[t + o];
+            __syncthreads();
+        }
+        if (t == 0) *P.ds.out = sd[0];
+        return;
     }
-    colsum(s, cs[2].part, cs[2].n_parts, cs[2].stride, cs[2].n_ent, cs[2].out, a.ns);
-    if (a.np > 0) colsum(s, cs[3].part, cs[3].n_parts, cs[3].stride, cs[3].n_ent, cs[3].out, a.ns);
+    const ColsumArgs& a = P.cs[blockIdx.y];
+    if ((int)blockIdx.x * 32 >= a.n_ent) return;
+    colsum_impl(a.part, a.n_parts, a.stride, a.n_ent, a.out, a.ns);
+}
+
+void launch_assemble(cudaStream_t s, const AsmArgs& a) {
+    ColsumPack P;
+    CtlArgs c;
+    assemble_parts(a, P.cs, P.ds, c);
+    if (a.n_cub <= 0) { P.cs[1].n_ent = 0; P.ds.n = 0; }
+    int max_ent = 1;
+    for (int i = 0; i < 4; ++i) max_ent = P.cs[i].n_ent > max_ent ? P.cs[i].n_ent : max_ent;
+    k_colsum4<<<dim3((max_ent + 31) / 32, 5), 512, 0, s>>>(P);
     k_control<<<1, 256, 0, s>>>(c);
 }
 
