@@ -109,8 +109,8 @@ __device__ __forceinline__ Item item_of(int item, int P, int split, int nk) {
     it.tl = item / P;
     it.ks = item % P;
     if (split > 1) {
-        it.kb0 = (int)((long long)nk * it.ks / split);
-        it.kb1 = (int)((long long)nk * (it.ks + 1) / split);
+        it.kb0 = nk * it.ks / split;          // nk * split < 2^31: 32-bit integer division
+        it.kb1 = nk * (it.ks + 1) / split;
     } else {
         it.kb0 = 0;
         it.kb1 = nk;
@@ -138,14 +138,17 @@ struct Walk {
         items = J.tiles * P;
         stream = J.stream;
         G = G_;
-        T = (long long)J.tiles * nk;
-        g0 = T * c / G;
-        g1 = T * (c + 1) / G;
-        hb = (g0 + nk - 1) / nk * nk;   // first tile edge at or after g0
-        tb = g1 / nk * nk;              // last tile edge at or before g1
-        cur = hb;
         stage = 0;
         item = c;
+        T = g0 = g1 = hb = tb = cur = 0;
+        if (stream) {                   // 64-bit divisions only where the ranges are used
+            T = (long long)J.tiles * nk;
+            g0 = T * c / G;
+            g1 = T * (c + 1) / G;
+            hb = (g0 + nk - 1) / nk * nk;   // first tile edge at or after g0
+            tb = g1 / nk * nk;              // last tile edge at or before g1
+            cur = hb;
+        }
     }
     __device__ void seg(Item& I, long long a, long long b) const {
         I.tl = (int)(a / nk);
@@ -355,9 +358,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 // the next layer's weight tiles of this CTA's items into L2 (they do not
-                // depend on this layer's output)
+                // depend on this layer's output), and its job header into L1 (every
+                // role reads it right after the grid barrier)
                 if (!grouped && st + 1 < n_jobs && !fail) {
                     const ChainJob& Nb = jobs[st + 1];
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(&Nb.tiles));
                     Walk Wn(Nb, blockIdx.x, G);
                     while (Wn.next(I)) {
                         for (int kb = I.kb0; kb < I.kb1; ++kb) {
