@@ -65,10 +65,6 @@ __global__ void k_dsum(const double* x, int n, double* out, const NewtonState* n
     dsum_impl(x, n, out, ns);
 }
 
-static inline void colsum(cudaStream_t st, const float* part, int n_parts, int stride, int n_ent,
-                          double* out, const NewtonState* ns) {
-    k_colsum<<<(n_ent + 31) / 32, 512, 0, st>>>(part, n_parts, stride, n_ent, out, ns);
-}
 
 __device__ __forceinline__ int upper_idx(int i, int j, int r) {
     if (i > j) { int t = i; i = j; j = t; }
@@ -118,18 +114,22 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
 #pragma unroll
             for (int j = 0; j < kMaxR; ++j)
                 if (j == k) rk = row[j];
-            float v = (lane < r && !((used >> lane) & 1u)) ? fabsf(rk) : -1.f;
-            int p = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_xor_sync(full, v, o);
-                const int p2 = __shfl_xor_sync(full, p, o);
-                if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
-            }
+            // pivot: the largest |row[k]| among the unused rows in one warp reduction.  Key:
+            // the bits of |v| (non-negative floats order like unsigned integers) with the
+            // low 5 mantissa bits replaced by 31 - lane, so among values equal to 2^-18
+            // relative the lowest row wins (any of them is a sound partial pivot; the FP64
+            // refinement below fixes the solution's accuracy)
+            const unsigned key = (lane < r && !((used >> lane) & 1u))
+                                     ? ((__float_as_uint(fabsf(rk)) & ~31u) | (31u - (unsigned)lane))
+                                     : 0u;
+            const unsigned best = __reduce_max_sync(full, key);
+            const int p = 31 - (int)(best & 31u);
+            const float v = __uint_as_float(best & ~31u);
             if (!(v > 0x1p-20f * am) || !isfinite(v)) {
                 sing = 1;
                 break;
             }
-            const float inv = 1.0f / __shfl_sync(full, rk, p);
+            const float inv = __frcp_rn(__shfl_sync(full, rk, p));
             used |= 1u << p;
             if (lane == p) ps = k;
             if (lane == 0) { perm[k] = p; rinv[k] = inv; }
@@ -218,7 +218,6 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     __shared__ __align__(8) NewtonState S;
     const int r = C.r, t = threadIdx.x;
     const double dt2 = C.dt * C.dt;
-    const int nsym = r * (r + 1) / 2;
     const double inv_h = 1.0 / C.h;   // one divide (exact for power-of-two steps)
     double* phi = C.red;
     double* A = C.red + r;
