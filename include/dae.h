@@ -305,7 +305,9 @@ typedef struct dae_system {
  * until every system is done.  Each system keeps its own Newton control (tol,
  * line search, max_evals from opts, shared by all systems).
  *   Requirements: every decoder on ctx, in one tensor-core precision (TF32, BF16
- *   or BF16X3), appearing in at most one system (workspaces are per decoder).
+ *   or BF16X3), appearing in at most one system (workspaces are per decoder), without
+ *   a linear subspace.  A system whose decoder has a weight network may pass
+ *   cub_w == NULL (weights predicted at its first evaluation, as in dae_newton_step).
  *   reports  n_sys reports or NULL (then the call does not synchronize when every
  *            array is on the device).
  * The launch plan and graph are cached while the systems' decoders, meshes, cubature

@@ -1248,7 +1248,7 @@ dae_status validate_cub(dae_ctx* ctx, const dae_mesh* m, int n_cub, const int* c
 struct BatchKey {
     unsigned long long dec_id, mesh_id;
     const void* cub_tets; const void* cub_w; const void* fe_w; const void* G; const void* pext;
-    const void* gs;
+    const void* gs; const void* wn;
     int n_cub, has_fext;
 };
 
@@ -1265,6 +1265,7 @@ struct BatchPlan {
     PrepArgs* prep = nullptr; ColsumArgs* cs = nullptr; DsumArgs* ds = nullptr; CtlArgs* ctl = nullptr;
     FrameArgs* frame = nullptr;
     GatherArgs* gather = nullptr; int max_gather = 0;
+    WnetArgs* wnet = nullptr; int max_wn_H1 = 0, max_wn_n = 0;   // predicted weights
     double* q0 = nullptr; double* qout = nullptr;   // [n][kMaxR]
     NewtonState* ns_out = nullptr;                  // [n] report copies
     ChainJob* jobs = nullptr; int* stage_off = nullptr;
@@ -1389,6 +1390,10 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
         if (!launch_chain(s, cl, prec)) return fail(ctx, DAE_ERR_CUDA, "grouped chain launch failed");
     }
+    if (b->max_wn_H1 > 0) {
+        Phase p(ctx, DAE_PHASE_CUBATURE, 3);
+        launch_wnet_batched(s, b->wnet, n, b->max_wn_H1, b->max_wn_n);
+    }
     {
         Phase p(ctx, DAE_PHASE_CUBATURE, 1);
         launch_cubature_batched(s, b->cub, n, b->max_cub);
@@ -1423,7 +1428,8 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
 // decoders, meshes, staging buffers and the options stay the same).
 dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder*>& ds,
                        const std::vector<const dae_mesh*>& ms, const std::vector<int>& ncub,
-                       const std::vector<int>& hasf, double dt, const dae_newton_opts& opts) {
+                       const std::vector<int>& hasf, const std::vector<int>& pred, double dt,
+                       const dae_newton_opts& opts) {
     const int n = (int)ds.size();
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -1437,7 +1443,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     std::vector<DsumArgs> dsum(n); std::vector<CtlArgs> ctl(n); std::vector<FrameArgs> frame(n);
     std::vector<Outs> outs(n);
     std::vector<GatherArgs> gather(n);
+    std::vector<WnetArgs> wnet(n);
     b->max_gather = 0;
+    b->max_wn_H1 = b->max_wn_n = 0;
     b->max_elems = b->max_cub = b->max_K = b->max_ld = b->max_ent = 0;
     b->max_splits = 1;
     for (int i = 0; i < n; ++i) {
@@ -1469,7 +1477,15 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         ca.w_stride = ncub[i];
         ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
         ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu;
-        ca.lam = (float)m->lam; ca.cub_tets = w.cub_tets; ca.cub_w = w.cub_w; ca.n_cub = ncub[i];
+        ca.lam = (float)m->lam; ca.cub_tets = w.cub_tets; ca.cub_w = pred[i] ? w.wn_w : w.cub_w;
+        ca.n_cub = ncub[i];
+        memset(&wnet[i], 0, sizeof(WnetArgs));
+        if (pred[i]) {
+            // cubature weights from the system's weight network at its first evaluation
+            wnet[i] = wnet_args(d, w.cub_tets, ncub[i], w.wn_w, w.ns, 1);
+            b->max_wn_H1 = std::max(b->max_wn_H1, w.wn_H1);
+            b->max_wn_n = std::max(b->max_wn_n, ncub[i]);
+        }
         ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
         ca.stride = w.cub_stride; ca.ns = w.ns; ca.eval_flag = w.eval_flag;
         b->max_cub = std::max(b->max_cub, ncub[i]);
@@ -1541,6 +1557,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     const size_t o_ds = place(n * sizeof(DsumArgs)), o_ctl = place(n * sizeof(CtlArgs));
     const size_t o_fr = place(n * sizeof(FrameArgs));
     const size_t o_ga = place(n * sizeof(GatherArgs));
+    const size_t o_wn = place(n * sizeof(WnetArgs));
     const size_t o_q0 = place((size_t)n * kMaxR * sizeof(double));
     const size_t o_qo = place((size_t)n * kMaxR * sizeof(double));
     const size_t o_ns = place((size_t)n * sizeof(NewtonState));
@@ -1554,6 +1571,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     b->wta = (WtaArgs*)(D + o_wta); b->prep = (PrepArgs*)(D + o_prep); b->cs = (ColsumArgs*)(D + o_cs);
     b->ds = (DsumArgs*)(D + o_ds); b->ctl = (CtlArgs*)(D + o_ctl); b->frame = (FrameArgs*)(D + o_fr);
     b->gather = (GatherArgs*)(D + o_ga);
+    b->wnet = (WnetArgs*)(D + o_wn);
     b->q0 = (double*)(D + o_q0); b->qout = (double*)(D + o_qo); b->ns_out = (NewtonState*)(D + o_ns);
     b->jobs = (ChainJob*)(D + o_jobs); b->stage_off = (int*)(D + o_st); b->gb = (GridBar*)(D + o_gb);
     b->flag = (int*)(D + o_fl);
@@ -1573,6 +1591,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     CU(ctx, up(b->ctl, ctl.data(), n * sizeof(CtlArgs)));
     CU(ctx, up(b->frame, frame.data(), n * sizeof(FrameArgs)));
     CU(ctx, up(b->gather, gather.data(), n * sizeof(GatherArgs)));
+    CU(ctx, up(b->wnet, wnet.data(), n * sizeof(WnetArgs)));
     CU(ctx, up(b->jobs, jobs.data(), jobs.size() * sizeof(ChainJob)));
     CU(ctx, up(b->stage_off, stage_off.data(), stage_off.size() * sizeof(int)));
     CU(ctx, cudaMemset(b->gb, 0, sizeof(GridBar)));
@@ -2269,7 +2288,7 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         return fail(ctx, DAE_ERR_INVALID_ARG, "bad Newton options");
     std::vector<dae_decoder*> ds(n_sys);
     std::vector<const dae_mesh*> ms(n_sys);
-    std::vector<int> ncub(n_sys), hasf(n_sys);
+    std::vector<int> ncub(n_sys), hasf(n_sys), pred(n_sys);
     std::vector<const dae_decoder*> seen;
     for (int i = 0; i < n_sys; ++i) {
         const dae_system& y = sys[i];
@@ -2277,7 +2296,7 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         if (!y.mesh) return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: mesh required", i);
         if (!y.q || !y.qbar || !y.qbar_dot)
             return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: q, qbar, qbar_dot required", i);
-        TRY(validate_cub(ctx, y.mesh, y.n_cub, y.cub_tets, y.cub_w));
+        TRY(validate_cub(ctx, y.mesh, y.n_cub, y.cub_tets, y.cub_w, y.dec));
         dae_decoder* d = const_cast<dae_decoder*>(y.dec);
         if (d->prec == DAE_FP32 || !d->ws.chain_ok || !d->layers[0].tmR_ok)
             return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: the grouped step needs a tensor-core precision", i);
@@ -2289,6 +2308,7 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         ms[i] = y.mesh;
         ncub[i] = y.n_cub;
         hasf[i] = y.f_ext ? 1 : 0;
+        pred[i] = (!y.cub_w && y.n_cub > 0) ? 1 : 0;
         seen.push_back(y.dec);
     }
     std::sort(seen.begin(), seen.end());
@@ -2297,6 +2317,12 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
     // per-system set-up that is cached across calls
     for (int i = 0; i < n_sys; ++i) {
         TRY(ensure_cubature(ds[i], ncub[i], ncub[i]));
+        Workspace& wi = ds[i]->ws;
+        if (pred[i] && wi.wn_cap < ncub[i]) {
+            dfree(wi.wn_w);
+            TRY(dmalloc(ctx, &wi.wn_w, (size_t)ncub[i]));
+            wi.wn_cap = ncub[i];
+        }
         if (use_gram(ds[i])) {
             TRY(ensure_gram(ds[i], ms[i]));
             TRY(ensure_gs(ds[i], ms[i], ncub[i]));
@@ -2315,13 +2341,13 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         const Workspace& w = ds[i]->ws;
         key[i] = BatchKey{ds[i]->id, ms[i]->id, w.cub_tets, w.cub_w, w.fe_w, w.G, w.pext,
                           gram_out(ds[i], ms[i]) ? (w.Gs32 ? (const void*)w.Gs32 : (const void*)w.Gsh) : nullptr,
-                          ncub[i], hasf[i]};
+                          pred[i] ? (const void*)w.wn_w : nullptr, ncub[i], hasf[i]};
     }
     const bool same = b->gexec && b->n == n_sys && b->dt == dt && b->prec == (int)ds[0]->prec &&
                       memcmp(&b->opts, &opts, sizeof opts) == 0 &&
                       memcmp(b->key.data(), key.data(), n_sys * sizeof(BatchKey)) == 0;
     if (!same) {
-        TRY(build_batch(ctx, b, ds, ms, ncub, hasf, dt, opts));
+        TRY(build_batch(ctx, b, ds, ms, ncub, hasf, pred, dt, opts));
         b->key = key;
         b->n = n_sys;
         b->dt = dt;

@@ -497,6 +497,7 @@ struct WnetArgs {
     const NewtonState* ns; int first_only;
 };
 void launch_wnet(cudaStream_t s, const WnetArgs& a);
+void launch_wnet_batched(cudaStream_t s, const WnetArgs* d_args, int n_sys, int max_H1, int max_n);
 // Linear-subspace terms of one evaluation: part[b][a][c] = sum over the 128 rows k of block
 // b of V[k][a] X_c[k] for the columns c = 3 (H[D,D]), kShared+3j (J), kShared+3j+2 (dJ);
 // vz[k] = (V z_p)[k] (a reverse-pass seed split: W_L^T M U z_p); block 0 also writes

@@ -789,6 +789,65 @@ __global__ void __launch_bounds__(256) k_wnet_out(WnetArgs a) {
     }
 }
 
+// Grouped forms: z = system (systems without a network have H1 = 0 and n = 0).
+__global__ void __launch_bounds__(256) k_wnet_first_b(const WnetArgs* __restrict__ args) {
+    const WnetArgs& a = args[blockIdx.z];
+    if ((int)blockIdx.x >= a.H1) return;
+    if (wnet_skip(a)) return;
+    __shared__ float red[8];
+    const int i = blockIdx.x;
+    const float* __restrict__ row = a.B1 + (size_t)i * a.ldx;
+    const float* __restrict__ x = a.x;
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < a.K; k += 256) acc = fmaf(row[k], x[k], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        a.h1[i] = sinf(t + a.c1[i]);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_wnet_mid_b(const WnetArgs* __restrict__ args) {
+    const WnetArgs& a = args[blockIdx.z];
+    if (a.H1 <= 0 || wnet_skip(a)) return;
+    __shared__ float h1[kMaxWnetWidth], h2[kMaxWnetWidth], h3[kMaxWnetWidth];
+    for (int i = threadIdx.x; i < a.H1; i += blockDim.x) h1[i] = a.h1[i];
+    __syncthreads();
+    wnet_layer(a.A2, a.b2, h1, a.H1, h2, a.H2);
+    __syncthreads();
+    wnet_layer(a.A3, a.b3, h2, a.H2, h3, a.H3);
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.H3; i += blockDim.x) a.h1[kMaxWnetWidth + i] = h3[i];
+}
+
+__global__ void __launch_bounds__(256) k_wnet_out_b(const WnetArgs* __restrict__ args) {
+    const WnetArgs& a = args[blockIdx.z];
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= a.n || wnet_skip(a)) return;
+    const int t = a.tets[j];
+    const float* __restrict__ row = a.A4 + (size_t)t * a.H3;
+    const float* __restrict__ h3 = a.h1 + kMaxWnetWidth;
+    float acc = 0.f;
+    for (int k = lane; k < a.H3; k += 32) acc = fmaf(row[k], h3[k], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const float z = acc + a.b4[t];
+        a.w[j] = z * z;
+    }
+}
+
+void launch_wnet_batched(cudaStream_t s, const WnetArgs* d_args, int n_sys, int max_H1, int max_n) {
+    if (n_sys <= 0 || max_H1 <= 0) return;
+    k_wnet_first_b<<<dim3(max_H1, 1, n_sys), 256, 0, s>>>(d_args);
+    k_wnet_mid_b<<<dim3(1, 1, n_sys), 1024, 0, s>>>(d_args);
+    if (max_n > 0) k_wnet_out_b<<<dim3((max_n + 7) / 8, 1, n_sys), 256, 0, s>>>(d_args);
+}
+
 void launch_wnet(cudaStream_t s, const WnetArgs& a) {
     k_wnet_first<<<a.H1, 256, 0, s>>>(a);
     k_wnet_mid<<<1, 1024, 0, s>>>(a);

@@ -173,7 +173,7 @@ def test_autograd_function_and_short_fit():
             opt.step()
             if first is None:
                 first = float(loss.detach())
-        assert float(loss) < 0.5 * first, (first, float(loss))
+        assert float(loss.detach()) < 0.5 * first, (first, float(loss.detach()))
     finally:
         dae.dae_trainer_free(tr)
         dae.dae_destroy(ctx)

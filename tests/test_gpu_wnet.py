@@ -124,3 +124,42 @@ def test_weight_network_argument_checks():
         assert e.value.status == -1
     finally:
         g.close()
+
+
+def test_grouped_step_with_predicted_weights():
+    """Strings with their own weight networks in one grouped step equal their
+    single-system steps with predicted weights."""
+    wls = synth.strings(4, seed=13, v_range=(200, 500))
+    ctx = dae.dae_create(0)
+    loaded = []
+    try:
+        for k, wl in enumerate(wls):
+            d, m = wl.dec, wl.mesh
+            dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, "bf16x3")
+            mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass,
+                                     m.material, m.E, m.nu)
+            net = synth.make_wnet(d.n_out, m.n_tet, 20 + k)
+            dae.dae_decoder_attach_wnet(ctx, dec, net.widths, net.W, net.b)
+            loaded.append((dec, mesh, net))
+        q0 = [synth.newton_start(wl.state) for wl in wls]
+        qs = [q.copy() for q in q0]
+        ys = [dict(dec=dec, mesh=mesh, cub_tets=wl.cub_tets, cub_w=None, q=qs[i],
+                   qbar=wl.state.qbar, qbar_dot=wl.state.qbar_dot)
+              for i, (wl, (dec, mesh, _)) in enumerate(zip(wls, loaded))]
+        reps = dae.dae_newton_step_batched(ctx, ys, wls[0].state.dt)
+        for i, wl in enumerate(wls):
+            dec, mesh, net = loaded[i]
+            assert reps[i].status == 0
+            q1 = q0[i].copy()
+            dae.dae_newton_step(ctx, dec, mesh, wl.cub_tets, None, q1, wl.state.qbar,
+                                wl.state.qbar_dot, wl.state.dt)
+            step = np.linalg.norm(q1 - q0[i])
+            assert np.linalg.norm(qs[i] - q1) <= 1e-5 * max(step, 1e-12), (i, qs[i], q1)
+            w0 = oracle.wnet_weights(net, wl.dec, q0[i], wl.cub_tets)
+            qo, _ = oracle.newton_solve(wl, q0=q0[i], max_iter=5, cub_w=w0)
+            assert np.linalg.norm(qs[i] - qo) <= 1e-4 * max(np.linalg.norm(qo - q0[i]), 1e-12)
+    finally:
+        for dec, mesh, _ in loaded:
+            dae.dae_free_decoder(dec)
+            dae.dae_free_mesh(mesh)
+        dae.dae_destroy(ctx)
