@@ -245,9 +245,9 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec, const dae_mesh* mes
  *      layer's weights and bias here, once.
  * Afterwards dae_newton_step / dae_rollout / dae_assemble_reduced take and return
  * (np + r)-vectors q = [p; q], qbar, qbar_dot (phi, A, terms are (np + r)-sized) and
- * need the Gram form (a tensor-core precision and 2K <= N); dae_eval_derivs still
- * returns the filtered decoder's derivatives (r columns).  Not with a weight network
- * or in a grouped step.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * need the Gram form (a tensor-core precision and 2K <= N), also in a grouped step;
+ * dae_eval_derivs still returns the filtered decoder's derivatives (r columns).  Not
+ * with a weight network.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  */
 dae_status dae_decoder_attach_linear(dae_decoder* dec, int np, const float* U);
 
@@ -305,9 +305,10 @@ typedef struct dae_system {
  * until every system is done.  Each system keeps its own Newton control (tol,
  * line search, max_evals from opts, shared by all systems).
  *   Requirements: every decoder on ctx, in one tensor-core precision (TF32, BF16
- *   or BF16X3), appearing in at most one system (workspaces are per decoder), without
- *   a linear subspace.  A system whose decoder has a weight network may pass
- *   cub_w == NULL (weights predicted at its first evaluation, as in dae_newton_step).
+ *   or BF16X3), appearing in at most one system (workspaces are per decoder).  A
+ *   system whose decoder has a linear subspace passes (np + r)-vectors q, qbar, qbar_dot
+ *   (as in dae_newton_step); one whose decoder has a weight network may pass
+ *   cub_w == NULL (weights predicted at its first evaluation).
  *   reports  n_sys reports or NULL (then the call does not synchronize when every
  *            array is on the device).
  * The launch plan and graph are cached while the systems' decoders, meshes, cubature

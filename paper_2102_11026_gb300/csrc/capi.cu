@@ -1266,6 +1266,7 @@ struct BatchPlan {
     FrameArgs* frame = nullptr;
     GatherArgs* gather = nullptr; int max_gather = 0;
     WnetArgs* wnet = nullptr; int max_wn_H1 = 0, max_wn_n = 0;   // predicted weights
+    LinArgs* lin = nullptr; int max_lin_blocks = 0;               // linear subspaces
     double* q0 = nullptr; double* qout = nullptr;   // [n][kMaxR]
     NewtonState* ns_out = nullptr;                  // [n] report copies
     ChainJob* jobs = nullptr; int* stage_off = nullptr;
@@ -1394,6 +1395,10 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         Phase p(ctx, DAE_PHASE_CUBATURE, 3);
         launch_wnet_batched(s, b->wnet, n, b->max_wn_H1, b->max_wn_n);
     }
+    if (b->max_lin_blocks > 0) {
+        Phase p(ctx, DAE_PHASE_CUBATURE, 1);
+        launch_linear_batched(s, b->lin, n, b->max_lin_blocks);
+    }
     {
         Phase p(ctx, DAE_PHASE_CUBATURE, 1);
         launch_cubature_batched(s, b->cub, n, b->max_cub);
@@ -1439,11 +1444,13 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     b->rev.clear();
     const double h = opts.h_cs;
     std::vector<SeedArgs> seed(n); std::vector<CubArgs> cub(n); std::vector<XyArgs> xy(n);
-    std::vector<WtaArgs> wta(n); std::vector<PrepArgs> prep(n); std::vector<ColsumArgs> cs(3 * n);
+    std::vector<WtaArgs> wta(n); std::vector<PrepArgs> prep(n); std::vector<ColsumArgs> cs(4 * n);
     std::vector<DsumArgs> dsum(n); std::vector<CtlArgs> ctl(n); std::vector<FrameArgs> frame(n);
     std::vector<Outs> outs(n);
     std::vector<GatherArgs> gather(n);
     std::vector<WnetArgs> wnet(n);
+    std::vector<LinArgs> lin(n);
+    b->max_lin_blocks = 0;
     b->max_gather = 0;
     b->max_wn_H1 = b->max_wn_n = 0;
     b->max_elems = b->max_cub = b->max_K = b->max_ld = b->max_ent = 0;
@@ -1453,14 +1460,15 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         const dae_mesh* m = ms[i];
         Workspace& w = d->ws;
         const int r = d->r, L = d->L, N = d->N;
+        const int np = d->np, nsys = np + r;   // linear subspace size, system size
         const int ob = out_bf16_of(d->prec);
         const int ld0 = (int)round_up(r, kKPad);
-        seed[i] = SeedArgs{w.ns, w.qbar, w.qbar_dot, dt, h, r, w.Cp, ld0, w.X[0], w.Xh[0], w.Xl[0],
-                           d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec};
+        seed[i] = SeedArgs{w.ns, w.qbar + np, w.qbar_dot + np, dt, h, r, w.Cp, ld0, w.X[0], w.Xh[0],
+                           w.Xl[0], d->prec == DAE_TF32 ? kStoreTF32 : ob, w.zvec, np};
         b->max_elems = std::max(b->max_elems, w.Cp * ld0);
         Outs& o = outs[i];
         const bool gout = gram_out(d, m);
-        o.u = w.u; o.J = w.J; o.dJ = w.dJ; o.HDD = w.HDD;
+        o.u = w.u; o.J = w.J + (size_t)np * N; o.dJ = w.dJ; o.HDD = w.HDD;
         o.row_part = w.row_part; o.row_stride = w.row_stride;
         o.mdof = m->mdof; o.f_ext = hasf[i] ? w.f_ext : nullptr; o.a_out = w.a;
         if (gout) {
@@ -1475,7 +1483,8 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         CubArgs& ca = cub[i];
         memset(&ca, 0, sizeof ca);
         ca.w_stride = ncub[i];
-        ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = r; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
+        ca.u = w.u; ca.J = w.J; ca.N = N; ca.r = nsys; ca.X = m->X; ca.tets = m->tets; ca.Bm = m->Bm;
+        ca.np = np; ca.pv = np > 0 ? w.zpv + np : nullptr;
         ca.vol = m->vol; ca.n_tet = m->n_tet; ca.material = m->material; ca.mu = (float)m->mu;
         ca.lam = (float)m->lam; ca.cub_tets = w.cub_tets; ca.cub_w = pred[i] ? w.wn_w : w.cub_w;
         ca.n_cub = ncub[i];
@@ -1514,7 +1523,17 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         wa.nsplit_pairs = std::max(1, std::min(kMaxPairSplits, (wa.n_pairs + 15) / 16));
         wa.part = w.bwd_part[0]; wa.ns = w.ns;
         if (gout) wa.nsplit_dense = 0;
-        const int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0) + (wa.gy ? 1 : 0);
+        int in_split = wa.nsplit_dense + wa.nsplit_pairs + (wa.pext ? 1 : 0) + (wa.gy ? 1 : 0);
+        memset(&lin[i], 0, sizeof(LinArgs));
+        if (np > 0) {
+            LinArgs& la = lin[i];
+            la.X = w.X[(L - 1) & 1]; la.K = K; la.ldx = top.ld; la.r = r; la.np = np;
+            la.V = w.V; la.part = w.lin_part; la.vz = w.bwd_part[0] + (size_t)in_split * K;
+            la.zpv = w.zpv; la.ns = w.ns; la.q_in = nullptr; la.qbar = w.qbar;
+            la.qbar_dot = w.qbar_dot; la.dt = dt;
+            b->max_lin_blocks = std::max(b->max_lin_blocks, w.lin_blocks);
+            in_split += 1;
+        }
         b->max_K = std::max(b->max_K, K);
         b->max_splits = std::max(b->max_splits, in_split);
         PrepArgs& pa = prep[i];
@@ -1528,7 +1547,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         b->max_ld = std::max(b->max_ld, pa.ld);
         AsmArgs aa;
         memset(&aa, 0, sizeof aa);
-        aa.r = r; aa.dt = dt; aa.h = h;
+        aa.r = nsys; aa.dt = dt; aa.h = h;
+        aa.rq = r; aa.np = np; aa.lin_part = w.lin_part; aa.lin_blocks = w.lin_blocks;
+        aa.UMU = w.UMU; aa.Uf = hasf[i] ? w.Uf : nullptr; aa.qbar = w.qbar; aa.qbar_dot = w.qbar_dot;
         aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
         aa.row_stride = w.row_stride;
         aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = ncub[i];
@@ -1539,10 +1560,8 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         aa.max_step = opts.max_step; aa.xtol = opts.xtol;
         aa.max_halvings = opts.max_halvings; aa.max_evals = opts.max_evals;
         aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
-        ColsumArgs c4[4];
-        assemble_parts(aa, c4, dsum[i], ctl[i]);
-        for (int k = 0; k < 3; ++k) cs[3 * i + k] = c4[k];
-        for (int k = 0; k < 3; ++k) b->max_ent = std::max(b->max_ent, cs[3 * i + k].n_ent);
+        assemble_parts(aa, &cs[4 * i], dsum[i], ctl[i]);
+        for (int k = 0; k < 4; ++k) b->max_ent = std::max(b->max_ent, cs[4 * i + k].n_ent);
     }
     std::vector<ChainJob> jobs;
     std::vector<int> stage_off;
@@ -1553,8 +1572,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     auto place = [&](size_t bytes) { size_t o = off; off += round_up(bytes, 256); return o; };
     const size_t o_seed = place(n * sizeof(SeedArgs)), o_cub = place(n * sizeof(CubArgs));
     const size_t o_xy = place(n * sizeof(XyArgs)), o_wta = place(n * sizeof(WtaArgs));
-    const size_t o_prep = place(n * sizeof(PrepArgs)), o_cs = place(3 * n * sizeof(ColsumArgs));
+    const size_t o_prep = place(n * sizeof(PrepArgs)), o_cs = place(4 * n * sizeof(ColsumArgs));
     const size_t o_ds = place(n * sizeof(DsumArgs)), o_ctl = place(n * sizeof(CtlArgs));
+    const size_t o_lin = place(n * sizeof(LinArgs));
     const size_t o_fr = place(n * sizeof(FrameArgs));
     const size_t o_ga = place(n * sizeof(GatherArgs));
     const size_t o_wn = place(n * sizeof(WnetArgs));
@@ -1570,13 +1590,15 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     b->seed = (SeedArgs*)(D + o_seed); b->cub = (CubArgs*)(D + o_cub); b->xy = (XyArgs*)(D + o_xy);
     b->wta = (WtaArgs*)(D + o_wta); b->prep = (PrepArgs*)(D + o_prep); b->cs = (ColsumArgs*)(D + o_cs);
     b->ds = (DsumArgs*)(D + o_ds); b->ctl = (CtlArgs*)(D + o_ctl); b->frame = (FrameArgs*)(D + o_fr);
+    b->lin = (LinArgs*)(D + o_lin);
     b->gather = (GatherArgs*)(D + o_ga);
     b->wnet = (WnetArgs*)(D + o_wn);
     b->q0 = (double*)(D + o_q0); b->qout = (double*)(D + o_qo); b->ns_out = (NewtonState*)(D + o_ns);
     b->jobs = (ChainJob*)(D + o_jobs); b->stage_off = (int*)(D + o_st); b->gb = (GridBar*)(D + o_gb);
     b->flag = (int*)(D + o_fl);
     for (int i = 0; i < n; ++i)
-        frame[i] = FrameArgs{ds[i]->ws.ns, b->q0 + (size_t)i * kMaxR, b->qout + (size_t)i * kMaxR, ds[i]->r};
+        frame[i] = FrameArgs{ds[i]->ws.ns, b->q0 + (size_t)i * kMaxR, b->qout + (size_t)i * kMaxR,
+                             ds[i]->np + ds[i]->r};
     auto up = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
@@ -1586,7 +1608,8 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     CU(ctx, up(b->xy, xy.data(), n * sizeof(XyArgs)));
     CU(ctx, up(b->wta, wta.data(), n * sizeof(WtaArgs)));
     CU(ctx, up(b->prep, prep.data(), n * sizeof(PrepArgs)));
-    CU(ctx, up(b->cs, cs.data(), 3 * n * sizeof(ColsumArgs)));
+    CU(ctx, up(b->cs, cs.data(), 4 * n * sizeof(ColsumArgs)));
+    CU(ctx, up(b->lin, lin.data(), n * sizeof(LinArgs)));
     CU(ctx, up(b->ds, dsum.data(), n * sizeof(DsumArgs)));
     CU(ctx, up(b->ctl, ctl.data(), n * sizeof(CtlArgs)));
     CU(ctx, up(b->frame, frame.data(), n * sizeof(FrameArgs)));
@@ -2303,7 +2326,6 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         if (d->prec != sys[0].dec->prec)
             return fail(ctx, DAE_ERR_INVALID_ARG, "system %d: all decoders must share one precision", i);
         if (d->L < 2) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: a decoder needs a hidden layer", i);
-        if (d->np > 0) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: linear subspace in a grouped step", i);
         ds[i] = d;
         ms[i] = y.mesh;
         ncub[i] = y.n_cub;
@@ -2327,6 +2349,8 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
             TRY(ensure_gram(ds[i], ms[i]));
             TRY(ensure_gs(ds[i], ms[i], ncub[i]));
         }
+        if (ds[i]->np > 0 && !gram_out(ds[i], ms[i]))
+            return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: the linear subspace needs the Gram form", i);
     }
     BatchPlan* b = (BatchPlan*)ctx->batch;
     if (!b) {
@@ -2378,7 +2402,7 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
     for (int i = 0; i < n_sys; ++i) {
         const dae_system& y = sys[i];
         Workspace& w = ds[i]->ws;
-        const int r = ds[i]->r;
+        const int r = ds[i]->np + ds[i]->r;   // system size
         add(y.q, b->q0 + (size_t)i * kMaxR, r * sizeof(double));
         add(y.qbar, w.qbar, r * sizeof(double));
         add(y.qbar_dot, w.qbar_dot, r * sizeof(double));
@@ -2452,7 +2476,8 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
             CU(ctx, cudaMemcpyAsync(hs.data(), b->ns_out, n_sys * sizeof(NewtonState), cudaMemcpyDeviceToHost, ctx->stream));
         }
         CU(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int i : host_q) memcpy(sys[i].q, qh.data() + (size_t)i * kMaxR, ds[i]->r * sizeof(double));
+        for (int i : host_q)
+            memcpy(sys[i].q, qh.data() + (size_t)i * kMaxR, (ds[i]->np + ds[i]->r) * sizeof(double));
     }
     CU(ctx, cudaGetLastError());
     if (reps) {

@@ -453,6 +453,7 @@ struct CtlArgs {
 struct SeedArgs {
     const NewtonState* ns; const double* qbar; const double* qbar_dot; double dt, h;
     int r, Cp, ld0; float* X; __nv_bfloat16* Xh; __nv_bfloat16* Xl; int out_bf16; float* zvec;
+    int off;   // first state entry of the decoder's coordinates (linear subspace size)
 };
 struct XyArgs {
     const float* X; int ld, K, r; const float* zvec; double h; float* xy; const NewtonState* ns;
@@ -508,6 +509,8 @@ struct LinArgs {
     const NewtonState* ns; const double* q_in; const double* qbar; const double* qbar_dot; double dt;
 };
 void launch_linear(cudaStream_t s, const LinArgs& a, int n_blocks);
+// grouped form (z = system; systems without a linear subspace have np = 0)
+void launch_linear_batched(cudaStream_t s, const LinArgs* d_args, int n_sys, int max_blocks);
 // copy[i]: n bytes from src to dst (device memory), one block per copy
 struct CopyDesc { const void* src; void* dst; unsigned long long n; };
 void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);

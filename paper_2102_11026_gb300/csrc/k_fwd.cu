@@ -47,7 +47,7 @@ __global__ void k_seed(const NewtonState* ns, const double* q_override, const do
 __global__ void k_seed_b(const SeedArgs* __restrict__ args) {
     const SeedArgs& a = args[blockIdx.z];
     seed_impl(a.ns, nullptr, a.qbar, a.qbar_dot, a.dt, a.h, SEED_FULL, a.r, a.Cp, a.ld0, a.X,
-              a.Xh, a.Xl, a.out_bf16, a.zvec, 0);
+              a.Xh, a.Xl, a.out_bf16, a.zvec, a.off);
 }
 
 void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems) {

@@ -859,7 +859,7 @@ void launch_wnet(cudaStream_t s, const WnetArgs& a) {
 // column c' = 0 -> plane 3 (h^2 H[D,D]), 1 + j -> plane kShared + 3j (h J), 1 + r + j ->
 // plane kShared + 3j + 2 (h^3 dJ); scaled by the control.  vz = V z_p per row.
 constexpr int kLinRows = 64;
-__global__ void __launch_bounds__(kLinRows) k_linear(LinArgs A) {
+__device__ __forceinline__ void linear_impl(const LinArgs& A) {
     if (A.ns && A.ns->done) return;
     __shared__ float sx[1 + 2 * kMaxR][kLinRows];
     __shared__ float sv[kMaxR][kLinRows];
@@ -897,8 +897,20 @@ __global__ void __launch_bounds__(kLinRows) k_linear(LinArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(kLinRows) k_linear(LinArgs A) { linear_impl(A); }
+
+__global__ void __launch_bounds__(kLinRows) k_linear_b(const LinArgs* __restrict__ args) {
+    const LinArgs& a = args[blockIdx.z];
+    if (a.np <= 0 || (int)blockIdx.x * kLinRows >= a.K) return;
+    linear_impl(a);
+}
+
 void launch_linear(cudaStream_t s, const LinArgs& a, int n_blocks) {
     k_linear<<<n_blocks, kLinRows, 0, s>>>(a);
+}
+
+void launch_linear_batched(cudaStream_t s, const LinArgs* d_args, int n_sys, int max_blocks) {
+    if (n_sys > 0 && max_blocks > 0) k_linear_b<<<dim3(max_blocks, 1, n_sys), kLinRows, 0, s>>>(d_args);
 }
 
 }  // namespace dae

@@ -478,10 +478,10 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     k_control<<<1, 256, 0, s>>>(c);
 }
 
-// Grouped form: z = system; the three column sums in y (an empty sum skips), then the
+// Grouped form: z = system; the four column sums in y (an empty sum skips), then the
 // energy sum and the control step, one block per system.
 __global__ void __launch_bounds__(512) k_colsum_b(const ColsumArgs* __restrict__ cs) {
-    const ColsumArgs& a = cs[blockIdx.z * 3 + blockIdx.y];
+    const ColsumArgs& a = cs[blockIdx.z * 4 + blockIdx.y];
     if ((int)blockIdx.x * 32 >= a.n_ent) return;
     colsum_impl(a.part, a.n_parts, a.stride, a.n_ent, a.out, a.ns);
 }
@@ -495,7 +495,7 @@ __global__ void k_control_b(const CtlArgs* __restrict__ c) { control_impl(c[bloc
 void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
                              const CtlArgs* c, int n_sys, int max_ent) {
     if (n_sys <= 0) return;
-    k_colsum_b<<<dim3((max_ent + 31) / 32, 3, n_sys), 512, 0, s>>>(cs);
+    k_colsum_b<<<dim3((max_ent + 31) / 32, 4, n_sys), 512, 0, s>>>(cs);
     k_dsum_b<<<n_sys, 256, 0, s>>>(ds);
     k_control_b<<<n_sys, 256, 0, s>>>(c);
 }

@@ -114,3 +114,44 @@ def test_linear_subspace_argument_checks():
         assert e.value.status == -1
     finally:
         g.close()
+
+
+def test_grouped_step_with_linear_subspaces():
+    """Strings with and without a linear subspace in one grouped step equal their
+    single-system steps (r = [p; q] for the former)."""
+    wls = synth.strings(4, seed=17, v_range=(200, 500))
+    ctx = dae.dae_create(0)
+    loaded, starts = [], []
+    try:
+        for k, wl in enumerate(wls):
+            d, m = wl.dec, wl.mesh
+            dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, "bf16x3")
+            mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass,
+                                     m.material, m.E, m.nu)
+            rbar, rdot = wl.state.qbar, wl.state.qbar_dot
+            if k % 2 == 0:
+                U = synth.make_linear_basis(d.n_out, 2, 30 + k)
+                dae.dae_decoder_attach_linear(ctx, dec, np.ascontiguousarray(U.T))
+                pb, pd = synth.make_linear_state(2, 30 + k, p_std=0.1)
+                rbar, rdot = np.concatenate([pb, rbar]), np.concatenate([pd, rdot])
+            loaded.append((dec, mesh))
+            starts.append((rbar, rdot))
+        q0 = [rb + wls[0].state.dt * rd for rb, rd in starts]
+        qs = [q.copy() for q in q0]
+        ys = [dict(dec=dec, mesh=mesh, cub_tets=wl.cub_tets, cub_w=wl.cub_w, q=qs[i],
+                   qbar=starts[i][0], qbar_dot=starts[i][1])
+              for i, (wl, (dec, mesh)) in enumerate(zip(wls, loaded))]
+        reps = dae.dae_newton_step_batched(ctx, ys, wls[0].state.dt)
+        for i, wl in enumerate(wls):
+            dec, mesh = loaded[i]
+            assert reps[i].status == 0
+            q1 = q0[i].copy()
+            dae.dae_newton_step(ctx, dec, mesh, wl.cub_tets, wl.cub_w, q1, starts[i][0],
+                                starts[i][1], wl.state.dt)
+            step = np.linalg.norm(q1 - q0[i])
+            assert np.linalg.norm(qs[i] - q1) <= 1e-5 * max(step, 1e-12), (i, qs[i], q1)
+    finally:
+        for dec, mesh in loaded:
+            dae.dae_free_decoder(dec)
+            dae.dae_free_mesh(mesh)
+        dae.dae_destroy(ctx)
