@@ -80,6 +80,12 @@ __device__ __forceinline__ void bulk_store_wait(void* gdst, const void* ssrc, ui
 
 // Bulk copy of `bytes` (multiple of 16) from global to shared memory, completing on
 // the transaction count of `bar`.
+// Counts `bytes` of an mbarrier's expected transactions as done (for loads never issued).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) gen = *(volatile unsigned*)&gb->gen;
 
     uint32_t pk = 0;   // stage-ring position (producer and MMA walk it identically)
+    int pre_n = 0;     // producer: k-blocks of the next stage whose weights are already issued
     uint32_t it = 0;   // items taken by this CTA: accumulator it & 1, its use it >> 1
     uint32_t nred = 0; // split reductions of this CTA (rbar phases)
     const bool grouped = stage_off != nullptr;
@@ -332,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (X3) { prefetch_tmap(&Jp->tm[1]); prefetch_tmap(&Jp->tm[3]); }
                     }
                 }
+                int kc = 0;   // k-blocks of this stage so far
                 while (!fail && W.next(Jp, I)) {
                     const CUtensorMap* tmA = &Jp->tm[0];
                     const CUtensorMap* tmAlo = &Jp->tm[1];
@@ -343,9 +351,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
                         Jlast = Jp;
                     }
-                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
+                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk, ++kc) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
+                        if (kc < pre_n) {
+                            // weights issued ahead, before the grid barrier: the activations only
+                            uint8_t* base = smem + (size_t)s * STAGE;
+                            tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
+                            if constexpr (X3) tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
+                            continue;
+                        }
                         if (!mbar_wait(&empty[s], ph ^ 1)) { fail = 1; break; }
                         mbar_expect_tx(&full[s], STAGE);
                         uint8_t* base = smem + (size_t)s * STAGE;
@@ -357,12 +372,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
+                pre_n = 0;
                 // the next layer's weight tiles of this CTA's items into L2 (they do not
                 // depend on this layer's output), and its job header into L1 (every
                 // role reads it right after the grid barrier)
                 if (!grouped && st + 1 < n_jobs && !fail) {
                     const ChainJob& Nb = jobs[st + 1];
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(&Nb.tiles));
+                    // the first k-blocks of the next layer's weights straight into the free
+                    // ring slots (the epilogue uses no ring slot); their activations follow
+                    // after the grid barrier
+                    {
+                        Walk Wa(Nb, blockIdx.x, G);
+                        Item Ia;
+                        if (Wa.next(Ia)) {
+                            for (int kb = Ia.kb0; kb < Ia.kb1 && pre_n < stages; ++kb) {
+                                const uint32_t kk = pk + (uint32_t)pre_n;
+                                const int s = kk % stages;
+                                if (!mbar_wait(&empty[s], ((kk / stages) & 1) ^ 1)) { fail = 1; break; }
+                                mbar_expect_tx(&full[s], STAGE);
+                                uint8_t* base = smem + (size_t)s * STAGE;
+                                tma_load_2d(base, &Nb.tm[0], &full[s], kb * KB, Ia.tl * 128);
+                                if constexpr (X3)
+                                    tma_load_2d(base + A_BYTES + B_BYTES, &Nb.tm[1], &full[s], kb * KB, Ia.tl * 128);
+                                ++pre_n;
+                            }
+                        }
+                    }
                     Walk Wn(Nb, blockIdx.x, G);
                     while (Wn.next(I)) {
                         for (int kb = I.kb0; kb < I.kb1; ++kb) {
@@ -553,19 +589,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         __threadfence();
                     }
-                    // the other chunks' rows [r0, r0 + R) into the idle stage buffers (every
-                    // MMA of this item has completed; a split layer gives a CTA one item)
+                    // chunk s's rows [r0, r0 + R) into this tile's rows [s R, s R + R): the
+                    // tile is published, its own rows stay in place, and the split * R = 128
+                    // rows hold all chunks (the stage ring stays free for the next layer)
                     const int r0 = I.ks * R;
                     const uint32_t slice_f = (uint32_t)R * TS;   // floats of one chunk's slice
-                    float* scratch = reinterpret_cast<float*>(smem);
                     const float* src = split_part + (size_t)I.tl * split * (TILE_BYTES / 4) + (size_t)r0 * TS;
                     if (et == 0 && got) {
                         mbar_expect_tx(&rbar, (uint32_t)(split - 1) * slice_f * 4u);
-                        for (int s = 0, q = 0; s < split; ++s) {
+                        for (int s = 0; s < split; ++s) {
                             if (s == I.ks) continue;
-                            bulk_load(scratch + (size_t)q * slice_f, src + (size_t)s * (TILE_BYTES / 4),
+                            bulk_load(tile + (size_t)s * slice_f, src + (size_t)s * (TILE_BYTES / 4),
                                       slice_f * 4u, &rbar);
-                            ++q;
                         }
                     }
                     wok = epi_all(got || et != 0);
@@ -580,11 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int e = et; e < (int)slice_f; e += 128) {
                         float v[8];
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) {
-                            const int q = s < I.ks ? s : s - 1;
-                            v[s] = (s >= split) ? 0.f
-                                 : (s == I.ks ? own[e] : scratch[(size_t)q * slice_f + e]);
-                        }
+                        for (int s = 0; s < 8; ++s) v[s] = (s >= split) ? 0.f : tile[(size_t)s * slice_f + e];
                         float acc = v[0];
 #pragma unroll
                         for (int s = 1; s < 8; ++s) acc += v[s];
@@ -609,9 +640,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (Pb.split > 1)
             for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
     }
-    // drain: nothing in flight may outlive the CTA
+    // drain: nothing in flight may outlive the CTA (weights issued ahead for a stage that
+    // did not run have no activation loads: their bytes are counted as done)
     if (warp == 0 && lane == 0) {
-        for (uint32_t k = (pk > (uint32_t)stages ? pk - stages : 0); k < pk; ++k)
+        for (int i = 0; i < pre_n; ++i)
+            mbar_complete_tx(&full[(pk + (uint32_t)i) % stages], B_BYTES * (X3 ? 2u : 1u));
+        const uint32_t end = pk + (uint32_t)pre_n;
+        for (uint32_t k = (end > (uint32_t)stages ? end - stages : 0); k < end; ++k)
             if (!mbar_wait(&full[k % stages], (k / stages) & 1)) fail = 1;
     }
     tc_fence_before();
