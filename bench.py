@@ -564,15 +564,26 @@ def run_train(args):
 def run_strings(args):
     """One implicit-Euler Newton step of every string of the substructured model
     (320 independent strings, depth-8 decoders) per bench step: the grouped entry point
-    (all strings in one graph) against per-string dae_newton_step calls."""
+    (all strings in one graph) against per-string dae_newton_step calls.  Under torchrun
+    each rank steps its own share of the strings (partitioned by cost, no collective on
+    the data path); the timed region is the max over ranks and the evaluations the sum."""
     import torch
-    from paper_2102_11026_gb300 import dae, synth
-    torch.cuda.set_device(0)
+    from paper_2102_11026_gb300 import dae, shard, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > args.n_strings:
+        raise SystemExit("more ranks (%d) than strings (%d)" % (world, args.n_strings))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     t0 = time.perf_counter()
-    wls = synth.strings(args.n_strings)
+    rs, vs = synth.string_shapes(args.n_strings)
+    costs = [shard.string_cost(synth.string_widths(r, V)) for r, V in zip(rs, vs)]
+    mine = shard.shard_by_cost(costs, world)[rank]
+    wls = synth.strings(args.n_strings, only=mine)
     t_gen = time.perf_counter() - t0
     stream = torch.cuda.Stream()
-    ctx = dae.dae_create(0, stream.cuda_stream)
+    ctx = dae.dae_create(torch.cuda.current_device(), stream.cuda_stream)
     loaded = []
     for wl in wls:
         d, m = wl.dec, wl.mesh
@@ -604,6 +615,8 @@ def run_strings(args):
             q_all.copy_(q0_all)
             dae.dae_newton_step_batched(ctx, systems, dt, opts, want_reports=False)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
         time.sleep(0.3)
@@ -615,6 +628,8 @@ def run_strings(args):
             dae.dae_newton_step_batched(ctx, systems, dt, opts, want_reports=False)
         ev1.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         ms = ev0.elapsed_time(ev1)
         clocks = sampler.stop()
         q_grouped = q_all.cpu().numpy().copy()
@@ -657,7 +672,12 @@ def run_strings(args):
         dae.dae_free_mesh(mesh)
     dae.dae_destroy(ctx)
     ev_step = float(sum(evals))
-    value = ev_step * K / (ms / 1e3)
+    ms_rank = ms
+    if world > 1:
+        ms, ev_all = reduce_over_ranks(ms, ev_step, "cuda")
+    else:
+        ev_all = ev_step
+    value = ev_all * K / (ms / 1e3)
     params = [sum(w.size for w in wl.dec.W) for wl in wls]
     bpe = {"bf16x3": 4, "bf16": 2, "tf32": 4}[args.prec]
     peaks, peak_src = load_peaks()
@@ -675,27 +695,34 @@ def run_strings(args):
         # dominant kernel: the grouped forward chain (hidden layers + Gram operand)
         fwd_bytes += e * ((hidden + gram) * bpe + act + outs)
         bytes_step += e * ((2 * hidden + gram) * bpe)
-    step_gbs = bytes_step / (ms / K / 1e3) / 1e9
+    step_gbs = bytes_step / (ms_rank / K / 1e3) / 1e9
     t_fwd, c_fwd = prof["fwd_out"]
     achieved = fwd_bytes / (t_fwd / 1e3) / 1e9
     tot_ph = sum(v[0] for v in prof.values())
     phase_share = {k: round(v[0] / max(tot_ph, 1e-9), 4) for k, v in prof.items()}
     explicit_diff = float(np.max(np.abs(q_explicit - q_grouped)))
+    if rank != 0:
+        return
     line = {
         "metric": "string Newton iterations/s (320 strings, grouped)", "value": value,
-        "unit": "iterations/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "unit": "iterations/s", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None,
         "dtype": {"tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic",
         "config": {"workload": "%d strings, depth-8 decoders r-32-64-128-256-256-256-256-3V, "
                                "r ~ U{3..15}, V ~ U[200,2000], 2x2xV/4 grids, StVK, 32 cubature "
                                "tets each; one implicit-Euler Newton step of every string per "
-                               "step" % n, "params_total": int(sum(params)),
-                   "evals_per_step": ev_step, "max_evals": max_ev,
-                   "l2": "weights %.2f GB > L2" % (sum(params) * bpe / 1e9),
+                               "step" % args.n_strings, "params_total": int(sum(params)),
+                   "evals_per_step": ev_all, "max_evals": max_ev,
+                   "parallelism": ("strings sharded over %d ranks by P*(4r+4), longest "
+                                   "first; rank 0 holds %d" % (world, len(mine)))
+                   if world > 1 else "single GPU",
+                   "l2": "weights %.2f GB > L2%s" % (sum(params) * bpe / 1e9,
+                                                      " (rank 0)" if world > 1 else ""),
                    "synth_seconds": round(t_gen, 1)},
         "per_string_launches": {"ms_per_step": ms_single, "value": ev_step / (ms_single / 1e3),
-                                "grouped_speedup": ms_single / (ms / K),
+                                "grouped_speedup": ms_single / (ms_rank / K),
                                 "max_rel_diff_vs_grouped": diff},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": None,

@@ -256,22 +256,35 @@ STRING_HIDDEN = [32, 64, 128, 256, 256, 256, 256]
 STRING_Q_STD = 0.1
 
 
+def string_shapes(n_strings=320, seed=4, r_range=(3, 15), v_range=(200, 2000)):
+    """Latent sizes r_s ~ U{r_range} and vertex counts V_s ~ U[v_range] (rounded down to a
+    multiple of 4) of the strings made by ``strings`` with the same arguments."""
+    rng = np.random.Generator(np.random.PCG64(seed + 32452843))
+    rs = rng.integers(r_range[0], r_range[1] + 1, n_strings)
+    vs = rng.integers(v_range[0], v_range[1] + 1, n_strings) // 4 * 4
+    return [int(x) for x in rs], [int(x) for x in vs]
+
+
+def string_widths(r, V):
+    """Layer widths of a string's depth-8 decoder."""
+    return [r] + STRING_HIDDEN + [3 * V]
+
+
 def strings(n_strings=320, seed=4, act="tanh", r_range=(3, 15), v_range=(200, 2000),
-            n_cub=32):
+            n_cub=32, only=None):
     """Substructured model of independent strings (the puffer ball's 320 strings): string
     s has latent r_s ~ U{r_range}, V_s ~ U[v_range] vertices (rounded down to a multiple
     of 4) on a 2 x 2 x V_s/4 grid, a bias-free depth-8 decoder
     r_s-32-64-128-256-256-256-256-3V_s, StVK (E = 1e5, nu = 0.4), ``n_cub`` cubature tets,
     start qbar ~ N(0, 0.1^2), qbar_dot ~ N(0, 0.1^2), no external force.  Returns a list of
-    workloads (string s seeded from seed and s)."""
-    rng = np.random.Generator(np.random.PCG64(seed + 32452843))
-    rs = rng.integers(r_range[0], r_range[1] + 1, n_strings)
-    vs = rng.integers(v_range[0], v_range[1] + 1, n_strings) // 4 * 4
+    workloads (string s seeded from seed and s); ``only`` (indices) makes just those
+    strings, each identical to its copy in the full list."""
+    rs, vs = string_shapes(n_strings, seed, r_range, v_range)
     out = []
-    for s in range(n_strings):
-        r, V = int(rs[s]), int(vs[s])
+    for s in (range(n_strings) if only is None else only):
+        r, V = rs[s], vs[s]
         ss = seed * 100003 + s
-        dec = make_decoder([r] + STRING_HIDDEN + [3 * V], ss, act, bias=False)
+        dec = make_decoder(string_widths(r, V), ss, act, bias=False)
         mesh = make_grid_mesh(2, 2, V // 4, ss, "stvk", 1e5, 0.4)
         cub, w = make_cubature(mesh.n_tet, n_cub, ss)
         st = make_state(r, ss, q_std=STRING_Q_STD)
