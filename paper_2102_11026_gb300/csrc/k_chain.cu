@@ -10,10 +10,14 @@
 //
 // Short-K layers replicate the whole K loop on `rep` CTAs per tile; long-K layers
 // split K over `split` CTAs per tile, which publish their partial tiles (one bulk
-// copy each), wait for one another and sum them.  Either way each of the P CTAs of
-// a tile finishes 128/P rows, so the activation epilogue of a layer is spread over
-// tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue runs, the
-// producer prefetches the next layer's weight tiles into L2.
+// copy each), wait for one another and bulk-load the partners' slices of their own
+// rows into the spare rows of the staging tile before summing.  Either way each of
+// the P CTAs of a tile finishes 128/P rows, so the activation epilogue of a layer is
+// spread over tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue
+// runs, the producer prefetches the next layer's weight tiles into L2 and issues the
+// weight half of the next layer's first k-blocks into the free ring slots (weights
+// do not depend on the layer in flight); after the grid barrier it adds only the
+// activation half of those slots.
 //
 // Roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5 epilogue.
 // The accumulator is staged through a shared-memory tile so the MMA of the next
