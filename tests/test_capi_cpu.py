@@ -58,3 +58,22 @@ def test_null_arguments_are_rejected():
     assert L.dae_free_decoder(None) == -1
     assert L.dae_free_mesh(None) == -1
     assert L.dae_sync(None) == -1
+
+
+def test_every_entry_point_rejects_null_handles():
+    """Every call that takes a context, decoder, mesh or trainer handle returns
+    DAE_ERR_INVALID_ARG for NULL handles and NULL arrays (no dereference, no GPU)."""
+    import ctypes
+    L = dae.lib()
+    skip = {"dae_version", "dae_status_string", "dae_default_newton_opts", "dae_last_error"}
+    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_long, ctypes.c_longlong, ctypes.c_size_t)
+    checked = 0
+    for name, (argtypes, _) in dae.SIGNATURES.items():
+        if name in skip:
+            continue
+        vals = [0 if a in ints else 0.0 if a in (ctypes.c_double, ctypes.c_float) else None
+                for a in argtypes]
+        assert getattr(L, name)(*vals) == -1, name
+        checked += 1
+    assert checked >= 25
+    assert L.dae_last_error(None) == b"null context"
