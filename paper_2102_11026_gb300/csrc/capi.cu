@@ -2223,10 +2223,10 @@ dae_status dae_assemble_reduced(dae_ctx* ctx, const dae_decoder* dec_c, const da
     TRY(st.in(q, r, &dq));
     CU(ctx, cudaMemcpyAsync(d->ws.qbar, qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
     CU(ctx, cudaMemcpyAsync(d->ws.qbar_dot, qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
-    const int* dct;
-    const float* dcw;
+    const int* dct = nullptr;
+    const float* dcw = nullptr;
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
-    const float* dfe;
+    const float* dfe = nullptr;
     TRY(stage_fext(d, f_ext, &dfe));
     if (use_gram(d)) {
         TRY(ensure_gram(d, m));
@@ -2275,10 +2275,10 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     TRY(st.inout(q, r, &dq, true));
     CU(ctx, cudaMemcpyAsync(d->ws.qbar, qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
     CU(ctx, cudaMemcpyAsync(d->ws.qbar_dot, qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
-    const int* dct;
-    const float* dcw;
+    const int* dct = nullptr;
+    const float* dcw = nullptr;
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub, &dct, &dcw));
-    const float* dfe;
+    const float* dfe = nullptr;
     TRY(stage_fext(d, f_ext, &dfe));
     if (use_gram(d)) {
         TRY(ensure_gram(d, m));
@@ -2530,10 +2530,10 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     TRY(ensure_frames(d, n_frames));
     CU(ctx, cudaMemcpyAsync(w.qbar, dq, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     CU(ctx, cudaMemcpyAsync(w.qbar_dot, dqd, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    const int* dct;
-    const float* dcw;
+    const int* dct = nullptr;
+    const float* dcw = nullptr;
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub * n_frames, &dct, &dcw));
-    const float* dfe;
+    const float* dfe = nullptr;
     TRY(stage_fext(d, f_ext, &dfe));
     if (use_gram(d)) {
         TRY(ensure_gram(d, m));
