@@ -20,6 +20,12 @@ Notation (r = latent size, N = 3V output DOFs, vertex-major x0,y0,z0,x1,...):
   a      = M (J z + HDD) + dt^2 (f_C - f_ext)
   A      = a^T H + J^T M (J + dJ) + dt^2 K_r,  K_r = sum w_e J_e^T K_e J_e   (Eq. 11, n_p = 0)
 
+Coupled substructures (Sec. 6, deformation substructuring): domains tied by penalty
+springs between interface vertices that coincide at rest (and anchors holding a root's
+base at rest); ``coupled_system`` stacks every domain's Eq. 10 residual with the tie
+force among its forces and adds the ties' Hessian blocks to the global Newton matrix;
+``coupled_newton_solve`` runs the same Newton iteration on the stacked latents.
+
 Readings of the paper taken here (each also listed in the design notes):
   * Eq. 11 prints "- h^2 H^T (f_int - f_ext)"; differentiating Eq. 10 gives "+".
     ``tests/test_oracle_pins.py`` pins A against central differences of phi.
@@ -27,10 +33,14 @@ Readings of the paper taken here (each also listed in the design notes):
     LU with partial pivoting rather than the Cholesky the paper mentions.
   * The paper does not specify a line search; backtracking (Armijo on |phi|^2,
     c = 1e-4, step halving, at most 8 halvings) is used.
+  * The paper defers the coupling of its domains to Barbic & Zhao (2011) and states no
+    formulation; the ties are read as penalty springs (stiffness k_c) between
+    coinciding interface vertices, in one global Newton system over all domains.
 """
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 import subprocess
 import sys
@@ -498,13 +508,23 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
     dt = st.dt if dt is None else dt
     q = (qbar + dt * qbar_dot) if q0 is None else np.asarray(q0, np.float64).copy()
     max_iter = wl.max_iter if max_iter is None else max_iter
-    kw = dict(qbar=qbar, qbar_dot=qbar_dot, dt=dt, cub_w=cub_w)
 
-    def reduced_system_(wl_, x, **k):
+    def system(x):
         if U is None:
-            return reduced_system(wl_, x, **k)
-        return linear_subspace_system(wl_, U, x, k["qbar"], k["qbar_dot"], k["dt"], k["cub_w"])
-    rs = reduced_system_(wl, q, **kw)
+            return reduced_system(wl, x, qbar=qbar, qbar_dot=qbar_dot, dt=dt, cub_w=cub_w)
+        return linear_subspace_system(wl, U, x, qbar, qbar_dot, dt, cub_w)
+    q, rep = newton_iterate(system, q, max_iter, tol, c_armijo, max_halvings, max_step, xtol)
+    rep["qdot"] = (q - qbar) / dt
+    return q, rep
+
+
+def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
+                   max_step=0.5, xtol=1e-6):
+    """The Newton iteration of ``newton_solve`` on any system: ``system(x)`` returns a
+    dict with ``phi`` and its Jacobian ``A`` at x, or raises ``Inverted`` (a trial
+    point the line search then halves away from).  Returns (q, report dict)."""
+    q = np.asarray(q, np.float64).copy()
+    rs = system(q)
     phi0 = np.linalg.norm(rs["phi"])
     hist = [phi0]
     it = 0
@@ -520,7 +540,7 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
         for _ in range(max_halvings + 1):
             qt = q + alpha * delta
             try:
-                rt = reduced_system_(wl, qt, **kw)
+                rt = system(qt)
                 mt = float(rt["phi"] @ rt["phi"])
                 ok = mt <= (1.0 - 2.0 * c_armijo * alpha) * m0
             except Inverted:
@@ -534,5 +554,92 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
         it += 1
         hist.append(float(np.linalg.norm(rs["phi"])))
         converged = hist[-1] <= tol * max(1.0, phi0)
-    return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs,
-                   qdot=(q - qbar) / dt)
+    return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs)
+
+
+# --------------------------------------------------- coupled substructures --
+
+def _v3(i):
+    return slice(3 * int(i), 3 * int(i) + 3)
+
+
+def coupling_energy(cm, us):
+    """Ties between substructures (deformation substructuring, Sec. 6), read as
+    penalty springs of stiffness k_c: every interface pair (d, i, e, j) coincides at
+    rest and every anchor (d, i) holds its vertex at rest, so with displacements u_d
+      E_c = k_c/2 (sum_pairs |u_d[i] - u_e[j]|^2 + sum_anchors |u_d[i]|^2).
+    Returns E_c and the per-domain gradients g_d = dE_c/du_d (N_d each)."""
+    k = float(cm.k_c)
+    g = [np.zeros(np.asarray(u).size) for u in us]
+    E = 0.0
+    for d, i, e, j in cm.pairs:
+        s = us[d][_v3(i)] - us[e][_v3(j)]
+        E += 0.5 * k * float(s @ s)
+        g[d][_v3(i)] += k * s
+        g[e][_v3(j)] -= k * s
+    for d, i in cm.anchors:
+        s = us[d][_v3(i)]
+        E += 0.5 * k * float(s @ s)
+        g[d][_v3(i)] += k * s
+    return E, g
+
+
+def _offsets(cm):
+    return np.concatenate([[0], np.cumsum([wl.dec.r for wl in cm.domains])]).astype(int)
+
+
+def coupled_system(cm, Q, Qbar, Qdot, dt=None, cub_w=None):
+    """phi and A of one implicit-Euler step of the coupled domains, unknown the stacked
+    latents Q = [q_1; ...; q_D].  Domain d's rows are its own Eq. 10 residual with the
+    tie force -g_d among its forces (g_d joins f_C in phi and in a, hence in a^T H), and
+    with the Hessian of E_c (k_c [[I, -I], [-I, I]] per pair, k_c I per anchor):
+      A_dd = A_d(with g_d) + dt^2 k_c (sum_{pairs at d} J_d[i]^T J_d[i]
+                                       + sum_{anchors at d} J_d[i]^T J_d[i]),
+      A_de = -dt^2 k_c sum_{pairs (d,i,e,j)} J_d[i]^T J_e[j],
+    J_d[i] the 3 rows of J_d at vertex i.  ``cub_w`` is one weight array per domain."""
+    off = _offsets(cm)
+    dt = cm.domains[0].state.dt if dt is None else dt
+    Q, Qbar, Qdot = (np.asarray(x, np.float64) for x in (Q, Qbar, Qdot))
+    sl = [slice(off[d], off[d + 1]) for d in range(len(cm.domains))]
+    us = [decode(wl.dec, Q[sl[d]]) for d, wl in enumerate(cm.domains)]
+    Ec, g = coupling_energy(cm, us)
+    n = off[-1]
+    phi = np.zeros(n)
+    A = np.zeros((n, n))
+    Js = []
+    energy = Ec
+    for d, wl in enumerate(cm.domains):
+        tied = dataclasses.replace(wl, f_ext=np.asarray(wl.f_ext, np.float64) - g[d])
+        rs = reduced_system(tied, Q[sl[d]], qbar=Qbar[sl[d]], qbar_dot=Qdot[sl[d]], dt=dt,
+                            cub_w=None if cub_w is None else cub_w[d])
+        phi[sl[d]] = rs["phi"]
+        A[sl[d], sl[d]] = rs["A"]
+        Js.append(rs["J"])
+        energy += rs["energy"]
+    c = dt * dt * float(cm.k_c)
+    for d, i, e, j in cm.pairs:
+        Ji, Jj = Js[d][_v3(i)], Js[e][_v3(j)]
+        A[sl[d], sl[d]] += c * Ji.T @ Ji
+        A[sl[e], sl[e]] += c * Jj.T @ Jj
+        A[sl[d], sl[e]] -= c * Ji.T @ Jj
+        A[sl[e], sl[d]] -= c * Jj.T @ Ji
+    for d, i in cm.anchors:
+        Ji = Js[d][_v3(i)]
+        A[sl[d], sl[d]] += c * Ji.T @ Ji
+    return dict(phi=phi, A=A, energy=energy, coupling_energy=Ec, u=us, g=g, J=Js)
+
+
+def coupled_newton_solve(cm, Q0=None, Qbar=None, Qdot=None, dt=None, max_iter=None,
+                         cub_w=None, **kw):
+    """The Newton iteration of ``newton_solve`` on the coupled system (one global LU
+    solve per iteration over all domains' latents).  Defaults: Qbar, Qdot stacked from
+    the domains' states, Q0 = Qbar + dt Qdot."""
+    dt = cm.domains[0].state.dt if dt is None else dt
+    Qbar = np.concatenate([wl.state.qbar for wl in cm.domains]) if Qbar is None else Qbar
+    Qdot = np.concatenate([wl.state.qbar_dot for wl in cm.domains]) if Qdot is None else Qdot
+    Q0 = Qbar + dt * Qdot if Q0 is None else Q0
+    max_iter = cm.domains[0].max_iter if max_iter is None else max_iter
+    Q, rep = newton_iterate(lambda x: coupled_system(cm, x, Qbar, Qdot, dt, cub_w), Q0,
+                            max_iter, **kw)
+    rep["qdot"] = (Q - Qbar) / dt
+    return Q, rep

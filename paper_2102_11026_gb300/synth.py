@@ -292,6 +292,56 @@ def strings(n_strings=320, seed=4, act="tanh", r_range=(3, 15), v_range=(200, 20
     return out
 
 
+@dataclasses.dataclass
+class Coupled:
+    """Substructured body: domains joined at interfaces.  A row (d, i, e, j) of
+    ``pairs`` says vertex i of domain d and vertex j of domain e coincide at rest; a
+    row (d, i) of ``anchors`` holds vertex i of domain d at its rest position; ``k_c``
+    is the stiffness of both ties; ``parents[d]`` is the domain d hangs from (-1 for
+    an anchored root)."""
+    domains: list
+    parents: list
+    pairs: np.ndarray       # int32 (P, 4)
+    anchors: np.ndarray     # int32 (Q, 2)
+    k_c: float
+
+
+def string_faces(V):
+    """Vertex ids of the base face (k = 0) and the tip face (k = V/4 - 1) of a
+    2 x 2 x V/4 string grid, in the same (i, j) order."""
+    nz = V // 4
+    base = [(i * 2 + j) * nz for i in range(2) for j in range(2)]
+    return base, [b + nz - 1 for b in base]
+
+
+def coupled_strings(parents, seed=6, r=3, V=16, hidden=(16, 32), act="tanh", bias=False,
+                    out_scale=0.1, material="stvk", E=1e5, nu=0.4, k_c=1e5, n_cub=8,
+                    q_std=0.05, gravity=True):
+    """Strings joined into a tree (the cactus's domain hierarchy; a chain is a tree
+    with one child per domain): domain d is a 2 x 2 x V/4 string with decoder
+    r-hidden-3V, and its base face coincides at rest with the tip face of domain
+    parents[d] (a root's base face is anchored).  Bias-free decoders by default, so
+    every domain is at rest at its latent origin and the ties start slack there.
+    Seeded per domain from seed and d."""
+    base, tip = string_faces(V)
+    domains, pairs, anchors = [], [], []
+    for d, p in enumerate(parents):
+        ss = seed * 100003 + d
+        dec = make_decoder([r, *hidden, 3 * V], ss, act, out_scale=out_scale, bias=bias)
+        mesh = make_grid_mesh(2, 2, V // 4, ss, material, E, nu)
+        cub, w = make_cubature(mesh.n_tet, min(n_cub, mesh.n_tet), ss)
+        st = make_state(r, ss, q_std=q_std)
+        f = gravity_force(mesh.vmass) if gravity else np.zeros(dec.n_out, np.float32)
+        domains.append(Workload("domain%d" % d, dec, mesh, cub, w, st, f))
+        if p < 0:
+            anchors += [(d, b) for b in base]
+        else:
+            assert p < d, "a parent precedes its children"
+            pairs += [(d, b, p, t) for b, t in zip(base, tip)]
+    return Coupled(domains, list(parents), np.asarray(pairs, np.int32).reshape(-1, 4),
+                   np.asarray(anchors, np.int32).reshape(-1, 2), float(k_c))
+
+
 def custom(widths, grid, n_cub, seed, act="tanh", material="stvk", E=1e5, nu=0.4,
            gravity=False):
     """Arbitrary-shape workload for parity sweeps; ``widths[-1]`` must equal
