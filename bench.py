@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n-strings", type=int, default=320)
-    ap.add_argument("--mode", default="newton", choices=["newton", "train", "strings"],
+    ap.add_argument("--cub-sizes", default="64,500,6600,11400,88445",
+                    help="cubsweep: cubature set sizes |C| (88445 = every tet of the mesh)")
+    ap.add_argument("--mode", default="newton", choices=["newton", "train", "strings", "cubsweep"],
                     help="train: fit a re-seeded small-workload decoder to 4096 rollout poses "
                          "(batch 256, 100 Adam steps) and time the library's backward pass")
     return ap.parse_args()
@@ -737,6 +739,84 @@ def run_strings(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------ cubature |C| sweep --
+def cubature_bytes(n_cub, r):
+    """Algorithmic bytes of one cubature launch (k_cubature, warp per tet): per tet the
+    decoded u and the r columns of J at its 12 DOFs, its 4 vertex ids, Dm^-1 (9 floats),
+    rest volume, id and weight read, and its weighted force and DOF ids (12 + 12, read
+    again by W_L^T a) written.  The per-tet J_e^T f_e / J_e^T K_e J_e partials and
+    energies the kernel writes for the column sums (r + r(r+1)/2 + 2 words per tet) are
+    an intermediate of this design, not counted: they show as traffic above these bytes."""
+    read = 12 * 4 * (1 + r) + 4 * 4 + 9 * 4 + 4 + 4 + 4
+    write = 12 * 4 + 12 * 4
+    return n_cub * (read + write)
+
+
+def run_cubsweep(args):
+    """Achieved HBM bandwidth of the cubature kernel against the cubature set size on the
+    paper-scale mesh (20 x 20 x 50 grid, 88445 tets, Neo-Hookean, latent 30): the
+    decoder is the paper's latent and output widths with one hidden layer of 256 (the
+    cubature kernel sees only u and J at the cubature DOFs), bias-free, at a latent
+    near rest.  Each size: one warm-up dae_assemble_reduced, then CUDA events around
+    every cubature launch of ``--steps`` more."""
+    import torch
+    from paper_2102_11026_gb300 import dae, synth
+    torch.cuda.set_device(0)
+    sizes = [int(x) for x in args.cub_sizes.split(",") if x]
+    seed = 2
+    dec_w = synth.make_decoder([30, 256, 60000], seed, "tanh", bias=False)
+    mesh_w = synth.make_grid_mesh(20, 20, 50, seed, "neohookean", 5e5, 0.45)
+    if max(sizes) > mesh_w.n_tet:
+        raise SystemExit("|C| > %d tets" % mesh_w.n_tet)
+    stream = torch.cuda.Stream()
+    ctx = dae.dae_create(0, stream.cuda_stream)
+    dec = dae.dae_load_decoder(ctx, dec_w.widths, dec_w.W, dec_w.b, dec_w.act, args.prec)
+    mesh = dae.dae_load_mesh(ctx, mesh_w.X.reshape(-1), mesh_w.tets.reshape(-1), mesh_w.vmass,
+                             mesh_w.material, mesh_w.E, mesh_w.nu)
+    rng = np.random.default_rng(seed)
+    r = dec_w.r
+    q = rng.normal(0.0, 0.05, r)
+    qbar = np.zeros(r)
+    qdot = np.zeros(r)
+    dt = 1.0 / 60.0
+    f_ext = synth.gravity_force(mesh_w.vmass)
+    phi, A, en = np.zeros(r), np.zeros(r * r), np.zeros(1)
+    peaks, peak_src = load_peaks()
+    rows = []
+    with torch.cuda.stream(stream):
+        for C in sizes:
+            cub, w = synth.make_cubature(mesh_w.n_tet, C, seed)
+            ct = torch.as_tensor(cub, device="cuda")
+            cw = torch.as_tensor(w, device="cuda")
+            dae.dae_assemble_reduced(ctx, dec, mesh, ct, cw, q, qbar, qdot, dt, f_ext, phi, A, en)
+            dae.dae_profile_read(ctx)
+            dae.dae_profile_enable(ctx, ["cubature"])
+            for _ in range(args.steps):
+                dae.dae_assemble_reduced(ctx, dec, mesh, ct, cw, q, qbar, qdot, dt, f_ext, phi, A,
+                                         en)
+            dae.dae_profile_enable(ctx, False)
+            t, c = dae.dae_profile_read(ctx)["cubature"]
+            us = 1e3 * t / max(c, 1)
+            b = cubature_bytes(C, r)
+            gbs = b / (us / 1e6) / 1e9
+            rows.append({"n_cub": C, "us_per_launch": round(us, 2), "launches": c,
+                         "algorithmic_bytes": b, "gbs": round(gbs, 1),
+                         "frac": round(gbs / peaks["hbm_gbs"], 4),
+                         "energy": float(en[0])})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    dae.dae_free_decoder(dec)
+    dae.dae_free_mesh(mesh)
+    dae.dae_destroy(ctx)
+    print(json.dumps({
+        "metric": "cubature kernel achieved GB/s vs |C|", "unit": "GB/s",
+        "dtype": {"tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3", "fp32": "f32"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": "20x20x50 grid (88445 tets, Neo-Hookean E=5e5 nu=0.45), "
+                               "decoder 30-256-60000 bias-free, q ~ N(0, 0.05^2)",
+                   "launches_per_size": args.steps},
+        "peak": peaks["hbm_gbs"], "peak_source": "%s hbm_gbs" % peak_src, "sweep": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -745,6 +825,8 @@ def main():
         run_train(args)
     elif args.mode == "strings":
         run_strings(args)
+    elif args.mode == "cubsweep":
+        run_cubsweep(args)
     else:
         run_ours(args)
 
