@@ -467,12 +467,16 @@ dae_status ensure_gs(dae_decoder* d, const dae_mesh* m, int n_cub) {
         if (x3) ok = ok && make_tmap(&w.tmGs[1], w.Gsl, false, w.ldGs, rows, 128);
         else w.tmGs[1] = w.tmGs[0];
         if (!ok) return fail(ctx, DAE_ERR_UNSUPPORTED, "tensor map encoding failed (Gram operand)");
-        if (w.chain_cnt_n < (size_t)(Gt + Rt + 1)) {
-            dfree(w.chain_cnt);
-            w.chain_cnt_n = Gt + Rt + 1;
-            TRY(dmalloc(ctx, &w.chain_cnt, w.chain_cnt_n));
-            CU(ctx, cudaMemsetAsync(w.chain_cnt, 0, w.chain_cnt_n * sizeof(unsigned), ctx->stream));
-        }
+        w.graph_ok = false;
+    }
+    // one arrival counter per output tile of the stacked operand; checked on every call,
+    // since rebuilding the layer chains (a precision change) resizes the counters to the
+    // hidden layers' and the row form's needs only
+    if (w.chain_cnt_n < (size_t)(Gt + Rt + 1)) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.chain_cnt);
+        w.chain_cnt_n = Gt + Rt + 1;
+        TRY(dmalloc(ctx, &w.chain_cnt, w.chain_cnt_n));
         w.graph_ok = false;
     }
     if (w.gs_G_mesh != m->id) {
