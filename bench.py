@@ -8,15 +8,21 @@ with per-frame weights in [0.5, 2], gravity, dt = 1/60, at most 5 Newton
 updates per frame.  All inputs are seeded and synthetic (the paper ships no
 meshes or trained decoders).
 
-A step is one implicit-Euler frame: every evaluation of the frame runs the whole
-hot path (stacked complex-step forward, output-layer reductions, cubature,
-complex-step reverse pass, FP64 assembly, LU and line-search control).
-``value`` = Newton evaluations (iterations incl. the final residual check) per
-second over the timed frames, device-resident inputs; ``e2e`` = the same metric
-through the public C ABI with host buffers, one ``dae_rollout`` call per frame.
+A step is one implicit-Euler frame: the device Newton control evaluates the
+stacked complex-step forward pass, the output-layer reductions, the cubature and
+phi at every iterate; an accepted iterate that starts a new Newton step also runs
+the complex-step reverse pass, forms A (Eq. 11) and solves A delta = -phi (LU);
+rejected, converged or stopped trials are phi-only evaluations.
+``value`` = reduced Newton iterations per second: accepted Newton updates (an
+A-assembly, a solve and the line-search trials until one is accepted) over the
+timed frames, device-resident inputs; evaluations/s and frames/s are reported
+beside it.  ``e2e`` = the same metric through the public C ABI with host buffers,
+one ``dae_rollout`` call per frame.  ``forms`` = every precision form on the
+paper-scale and the small workload: iterations/s and the normwise relative error
+of u, J, H[qdot,qdot], dJ, phi and A against the FP64 oracle at the first iterate.
 
 --impl reference times the FP64 CPU oracle (the baseline this library is
-checked against) on a bounded sample of the same workload.
+checked against): one whole Newton iteration of the same workload per step.
 """
 from __future__ import annotations
 
@@ -50,7 +56,10 @@ def parse():
     ap.add_argument("--wnet", action="store_true",
                     help="predict the cubature weights with a weight network (N-64-64-64-n_tet)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the per-precision-form rates and oracle errors")
+    ap.add_argument("--form-frames", type=int, default=20,
+                    help="timed frames per precision form (the small workload runs 5x more)")
     ap.add_argument("--n-strings", type=int, default=320)
     ap.add_argument("--cub-sizes", default="64,500,6600,11400,88445",
                     help="cubsweep: cubature set sizes |C| (88445 = every tet of the mesh)")
@@ -189,9 +198,9 @@ def workload_config(args, wl, K, evals_all=None, flops=None, ms=None, world=1):
            "l2": "inputs larger than L2 (decoder weights %.0f MB)" % (sum(w.nbytes for w in d.W) / 1e6),
            "parallelism": "replicas" if world > 1 else "single GPU"}
     if evals_all is not None:
-        cfg["evaluations"] = int(evals_all)
-        cfg["algorithmic_gflop_per_evaluation"] = flops / 1e9
-        cfg["derivative_pass_tflops"] = flops * evals_all / (ms / 1e3) / 1e12
+        cfg["full_evaluations"] = int(evals_all)
+        cfg["algorithmic_gflop_per_full_evaluation"] = flops / 1e9
+        cfg["derivative_pass_tflops_over_step"] = flops * evals_all / (ms / 1e3) / 1e12
     return cfg
 
 
@@ -207,62 +216,66 @@ def reduce_over_ranks(ms, evals, device):
 
 
 # ---------------------------------------------------------------- oracle --
-def oracle_sample(wl, budget_s):
-    """Time the FP64 oracle on a bounded sample of one Newton evaluation and scale.
+ORACLE_SAMPLE = ("one whole Newton iteration of the FP64 oracle from the frame's first "
+                 "iterate q0 = qbar + dt qbar_dot: reduced_system (phi and A: hyper-dual "
+                 "derivative passes of the full decoder, a^T H, cubature FEM, assembly), "
+                 "the LU solve of A delta = -phi and phi_only at the first trial point")
 
-    One oracle evaluation = 2r full-decoder jet passes (u, J, H[D,.], dJ), r(r+1)/2
-    hidden-only second-order passes (a^T H), W_L^T a and the cubature FEM.  The
-    sample runs one batch of T full passes (T = OpenMP threads) and one batch of T
-    hidden passes, then scales each batch to its count per evaluation."""
+
+def oracle_iteration(wl, max_step=0.5):
+    """Time one Newton iteration of the FP64 oracle at q0, the unit of the metric:
+    the reduced system (phi and A), the solve and phi at the line search's first
+    trial.  Returns (seconds, OpenMP threads, the reduced system at q0)."""
     import oracle
-    dec, r = wl.dec, wl.dec.r
-    T = oracle.num_threads()
-    q = wl.state.qbar + wl.state.dt * wl.state.qbar_dot
-    E = np.eye(r)[np.arange(T) % r]
+    from paper_2102_11026_gb300 import synth
+    q0 = synth.newton_start(wl.state)
     t0 = time.perf_counter()
-    oracle.decoder_jets(dec, q, E)
-    t_full = time.perf_counter() - t0
-    L = len(dec.W)
-    t0 = time.perf_counter()
-    oracle.decoder_jets(dec, q, E, E, n_run=L - 1)
-    t_hid = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    u = oracle.decode(dec, q)
-    oracle.tets_fk(wl.mesh, u, wl.cub_tets)
-    t_fem = time.perf_counter() - t0
-    n_full, n_hid = 2 * r, r * (r + 1) // 2
-    t_eval = n_full / T * t_full + n_hid / T * t_hid + t_fem
-    sample = ("one batch of %d full-decoder first-order jet passes (%.2f s) and %d hidden-layer "
-              "second-order passes (%.2f s) + decode + %d-tet FEM (%.2f s), scaled to %d full + "
-              "%d hidden passes per evaluation" % (T, t_full, T, t_hid, wl.cub_tets.size, t_fem,
-                                                   n_full, n_hid))
-    return 1.0 / t_eval, T, sample, t_full + t_hid + t_fem
+    rs = oracle.reduced_system(wl, q0)
+    delta = np.linalg.solve(rs["A"], -rs["phi"])
+    dn = float(np.max(np.abs(delta)))
+    alpha = max_step / dn if (max_step > 0 and dn > max_step) else 1.0
+    oracle.phi_only(wl, q0 + alpha * delta)
+    t = time.perf_counter() - t0
+    return t, oracle.num_threads(), rs
 
 
 def run_reference(args):
+    """The oracle arm: each timed step is one whole oracle Newton iteration of the
+    workload (``oracle_iteration``); each warm-up step one phi-only evaluation of it
+    (touches the whole decoder and the cubature, warming caches and the thread pool)."""
     rank, world, local = dist_env()
     if rank != 0:
         return
     wl = make_workload(args.workload)
     import oracle
+    from paper_2102_11026_gb300 import synth
     oracle.build()
-    times, vals = [], []
-    for i in range(args.warmup + args.steps):
-        v, T, sample, spent = oracle_sample(wl, args.cpu_seconds)
-        if i >= args.warmup:
-            vals.append(v)
-            times.append(spent)
-    value = float(np.median(vals))
+    q0 = synth.newton_start(wl.state)
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle.phi_only(wl, q0)
+    times = []
+    T = oracle.num_threads()
+    for _ in range(args.steps):
+        t, T, _ = oracle_iteration(wl)
+        times.append(t)
+    total = time.perf_counter() - t_all
+    ms = 1e3 * float(np.sum(times)) / len(times)
+    value = 1e3 / ms
     line = {
         "impl": "reference", "metric": "reduced Newton iterations/s", "value": value,
         "unit": "iterations/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, wl, args.steps),
         "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": T, "kind": "oracle",
-                         "sample": sample},
+                         "sample": ORACLE_SAMPLE + "; one per timed step (warm-up steps: "
+                                   "phi_only at q0)"},
         "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        "step_seconds": {"min": float(np.min(times)), "median": float(np.median(times)),
+                         "max": float(np.max(times))},
+        "wall_seconds": total,
     }
     print(json.dumps(line))
 
@@ -359,12 +372,17 @@ def run_ours(args):
         dae.dae_profile_enable(ctx, False)
         prof_all = dae.dae_profile_read(ctx)
         evals2 = max(1, sum(rp.evals for rp in reps2))
+        full2 = max(1, sum(rp.full_evals for rp in reps2))
     evals = sum(rp.evals for rp in reps)
+    iters = sum(rp.iters for rp in reps)
+    full = sum(rp.full_evals for rp in reps)
     if world > 1:
-        ms, evals_all = reduce_over_ranks(ms, evals, "cuda")
+        ms, iters_all = reduce_over_ranks(ms, iters, "cuda")
+        _, evals_all = reduce_over_ranks(ms, evals, "cuda")
+        _, full_all = reduce_over_ranks(ms, full, "cuda")
     else:
-        evals_all = evals
-    value = evals_all / (ms / 1e3)
+        iters_all, evals_all, full_all = iters, evals, full
+    value = iters_all / (ms / 1e3)
 
     # ---- roofline of the dominant kernel (the persistent hidden forward chain), timed
     # live with CUDA events around every launch
@@ -375,6 +393,10 @@ def run_ours(args):
     achieved = bytes_hid / (avg_ms / 1e3) / 1e9
     hbm = peaks["hbm_gbs"]
     traffic = load_traffic(args.workload, args.prec)
+    tc = args.prec != "fp32"
+    flops_hid = hidden_chain_flops(wl)
+    tf_hid = flops_hid / (avg_ms / 1e3) / 1e12
+    tpeak = tensor_peak(peaks, args.prec)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
             "kernel": "hidden forward chain (k_chain, %d layers, %s)" % (len(d.W) - 1, args.prec),
@@ -383,7 +405,22 @@ def run_ours(args):
     tot_ph = sum(v[0] for v in prof_all.values())
     phase_share = {k: round(v[0] / max(tot_ph, 1e-9), 4) for k, v in prof_all.items()}
     phase_ms_per_eval = {k: round(v[0] / evals2, 4) for k, v in prof_all.items()}
-    flops = algorithmic_flops(wl, gram=args.prec != "fp32")
+    flops = algorithmic_flops(wl, gram=tc)
+    # the derivative pass (hidden chain, output stage, reverse pass) of a full evaluation
+    t_der = (prof_all["fwd_hidden"][0] + prof_all["fwd_out"][0] + prof_all["bwd"][0] +
+             prof_all["wta"][0])
+    tf_der = flops * full2 / max(t_der / 1e3, 1e-12) / 1e12
+    if tpeak is not None:
+        roof["tensor"] = {
+            "unit": "TFLOP/s", "peak": tpeak["peak"], "peak_source": "%s %s" % (peak_src, tpeak["src"]),
+            "hidden_chain": {"achieved": tf_hid, "frac": tf_hid / tpeak["peak"],
+                             "algorithmic_flops_per_launch": flops_hid,
+                             "executed_frac": tf_hid * tpeak["mma_per_product"] / tpeak["peak"]},
+            "derivative_pass": {"achieved": tf_der, "frac": tf_der / tpeak["peak"],
+                                "algorithmic_flops_per_full_evaluation": flops,
+                                "executed_frac": tf_der * tpeak["mma_per_product"] / tpeak["peak"]},
+            "note": "algorithmic flops (one product per weight and stacked column); split-BF16x3 "
+                    "executes %d MMAs per product (executed_frac)" % tpeak["mma_per_product"]}
 
     # ---- end to end through the C ABI with host buffers (one dae_rollout per frame)
     e2e = None
@@ -391,7 +428,7 @@ def run_ours(args):
         qh = QBAR0.copy()
         qdh = QDOT0.copy()
         cwh = frame_weights(wl, K, seed, start=W)
-        ev_tot = 0
+        it_tot = 0
         dae.dae_rollout(ctx, dec, mesh, wl.cub_tets, None if args.wnet else cwh[:n], 1, qh, qdh,
                         wl.state.dt, wl.f_ext, opts)
         qh = QBAR0.copy()
@@ -401,39 +438,152 @@ def run_ours(args):
             rp = dae.dae_rollout(ctx, dec, mesh, wl.cub_tets,
                                  None if args.wnet else cwh[f * n:(f + 1) * n], 1, qh, qdh,
                                  wl.state.dt, wl.f_ext, opts)
-            ev_tot += rp[0].evals
+            it_tot += rp[0].iters
         te = time.perf_counter() - t0
         r = d.r + args.np
         h2d = 2 * r * 8 + n * 4 + (0 if args.wnet else n * 4) + wl.f_ext.nbytes
-        d2h = 2 * r * 8 + 40 * 8 + 8 * 8 * 4
-        e2e = {"value": ev_tot / te, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
+        d2h = 2 * r * 8 + ctypes_report_bytes()
+        e2e = {"value": it_tot / te, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+
+    # ---- the FP64 oracle: one whole Newton iteration at q0 on the host cores (also the
+    # reference values of the precision forms below)
+    cpu, ref_paper = None, None
+    if rank == 0 and world == 1 and not (args.no_cpu and args.no_forms):
+        t_or, T, ref_paper = oracle_iteration(wl)
+        if not args.no_cpu:
+            cpu = {"value": 1.0 / t_or, "unit": "iterations/s", "cores": T, "kind": "oracle",
+                   "sample": ORACLE_SAMPLE + " (%.2f s)" % t_or}
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms and args.np == 0 and not args.wnet:
+        with torch.cuda.stream(stream):
+            forms = {args.workload: measure_forms(ctx, stream, wl, dec, mesh, ref_paper, args,
+                                                  args.form_frames)}
+            if args.workload != "small":
+                from paper_2102_11026_gb300 import synth
+                ws = synth.small()
+                import oracle
+                ref_small = oracle.reduced_system(ws, synth.newton_start(ws.state))
+                ds, msh = ws.dec, ws.mesh
+                dec_s = dae.dae_load_decoder(ctx, ds.widths, ds.W, ds.b, ds.act, "fp32")
+                mesh_s = dae.dae_load_mesh(ctx, msh.X.reshape(-1), msh.tets.reshape(-1),
+                                           msh.vmass, msh.material, msh.E, msh.nu)
+                forms["small"] = measure_forms(ctx, stream, ws, dec_s, mesh_s, ref_small, args,
+                                               5 * args.form_frames)
+                dae.dae_free_decoder(dec_s)
+                dae.dae_free_mesh(mesh_s)
+        for wk, fm in forms.items():
+            base = fm["fp32"]["iterations_per_s"]
+            for pr, rec in fm.items():
+                rec["vs_fp32"] = rec["iterations_per_s"] / base if base > 0 else None
 
     dae.dae_free_decoder(dec)
     dae.dae_free_mesh(mesh)
     dae.dae_destroy(ctx)
     if rank != 0:
         return
-    cpu = None
-    if not args.no_cpu and world == 1:
-        v, T, sample, _ = oracle_sample(wl, args.cpu_seconds)
-        cpu = {"value": v, "unit": "iterations/s", "cores": T, "kind": "oracle", "sample": sample}
     line = {
         "metric": "reduced Newton iterations/s", "value": value, "unit": "iterations/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic",
-        "config": workload_config(args, wl, K, evals_all, flops, ms, world),
-        "newton": {"evals_per_frame": evals / K, "iters_per_frame": sum(rp.iters for rp in reps) / K,
+        "config": workload_config(args, wl, K, full_all, flops, ms, world),
+        "rates": {"newton_iterations_per_s": value, "evaluations_per_s": evals_all / (ms / 1e3),
+                  "full_evaluations_per_s": full_all / (ms / 1e3),
+                  "frames_per_s": K * world / (ms / 1e3)},
+        "newton": {"evals_per_frame": evals / K, "full_evals_per_frame": full / K,
+                   "iters_per_frame": iters / K,
                    "converged_frames": sum(rp.converged for rp in reps),
                    "phi_norm0_first": reps[0].phi_norm0, "phi_norm_first": reps[0].phi_norm,
                    "status": sorted(set(rp.status for rp in reps))},
         "roofline": roof, "phase_share": phase_share, "phase_ms_per_evaluation": phase_ms_per_eval,
         "clocks": clocks,
-        "gpu_launches": int(launches), "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches), "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
     }
     print(json.dumps(line))
+
+
+def ctypes_report_bytes():
+    from paper_2102_11026_gb300 import dae
+    import ctypes
+    return ctypes.sizeof(dae.dae_newton_report)
+
+
+def tensor_peak(peaks, prec):
+    """Dense tensor-core peak for the precision form: the measured BF16 burst peak (the
+    kernels are timed alone inside a ~1 ms frame, well below the power cap); TF32 at the
+    nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); split-BF16x3 executes three BF16 MMAs
+    per product."""
+    bf = peaks.get("bf16_tflops")
+    if bf is None or prec == "fp32":
+        return None
+    if prec == "tf32":
+        return {"peak": bf * 1.1 / 2.25, "src": "bf16_tflops x 1.1/2.25 (nominal TF32/BF16)",
+                "mma_per_product": 1}
+    return {"peak": bf, "src": "bf16_tflops (burst)", "mma_per_product": 3 if prec == "bf16x3" else 1}
+
+
+def hidden_chain_flops(wl):
+    """Algorithmic flops of one hidden forward chain launch: 2 P_l (3r + 4) per hidden
+    layer (every stacked complex-step column of the shared-column form)."""
+    d = wl.dec
+    return 2.0 * sum(w.size for w in d.W[:-1]) * (3 * d.r + 4)
+
+
+def measure_forms(ctx, stream, wl, dec, mesh, ref, args, n_frames):
+    """Every precision form of the decoder GEMMs on one workload: Newton iterations/s
+    over ``n_frames`` frames (device buffers, CUDA events on the context's stream, after
+    two warm-up frames) and the normwise relative error of u, J, H[qdot,qdot], dJ, phi
+    and A at the first iterate q0 against the FP64 oracle's values there (``ref``)."""
+    import torch
+    from paper_2102_11026_gb300 import dae, synth
+    d = wl.dec
+    r, N, n = d.r, d.n_out, wl.cub_tets.size
+    q0 = synth.newton_start(wl.state)
+    dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+    cw = dev(frame_weights(wl, n_frames + 2, 11), torch.float32)
+    cub_t = dev(wl.cub_tets, torch.int32)
+    f_ext = dev(wl.f_ext, torch.float32)
+    opts = dae.dae_default_newton_opts()
+    opts.max_iter = 5
+    rel = lambda x, y: float(np.linalg.norm(np.asarray(x, np.float64) - y) /
+                             max(np.linalg.norm(y), 1e-300))
+    out = {}
+    for prec in ("fp32", "tf32", "bf16", "bf16x3"):
+        dae.dae_decoder_set_precision(ctx, dec, prec)
+        u = np.zeros(N, np.float32)
+        J = np.zeros((r, N), np.float32)
+        Hqq = np.zeros(N, np.float32)
+        dJ = np.zeros((r, N), np.float32)
+        dae.dae_eval_derivs(ctx, dec, q0, wl.state.qbar, wl.state.qbar_dot, wl.state.dt,
+                            u=u, J=J, Hqq=Hqq, dJ=dJ)
+        phi, A = np.zeros(r), np.zeros(r * r)
+        dae.dae_assemble_reduced(ctx, dec, mesh, wl.cub_tets, wl.cub_w, q0, wl.state.qbar,
+                                 wl.state.qbar_dot, wl.state.dt, wl.f_ext, phi, A)
+        err = {"u": rel(u, ref["u"]), "J": rel(J.T, ref["J"]), "Hqq": rel(Hqq, ref["Hqq"]),
+               "dJ": rel(dJ.T, ref["dJ"]), "phi": rel(phi, ref["phi"]),
+               "A": rel(A.reshape(r, r).T, ref["A"])}
+        q = dev(wl.state.qbar, torch.float64)
+        qd = dev(wl.state.qbar_dot, torch.float64)
+        dae.dae_rollout(ctx, dec, mesh, cub_t, cw[:2 * n], 2, q, qd, wl.state.dt, f_ext, opts)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        reps = dae.dae_rollout(ctx, dec, mesh, cub_t, cw[2 * n:], n_frames, q, qd, wl.state.dt,
+                               f_ext, opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        it = sum(rp.iters for rp in reps)
+        ev = sum(rp.evals for rp in reps)
+        out[prec] = {"iterations_per_s": it / (ms / 1e3), "evaluations_per_s": ev / (ms / 1e3),
+                     "frames_per_s": n_frames / (ms / 1e3), "evals_per_frame": ev / n_frames,
+                     "iters_per_frame": it / n_frames,
+                     "status": sorted(set(rp.status for rp in reps)), "rel_err": err}
+    dae.dae_decoder_set_precision(ctx, dec, args.prec)
+    return out
 
 
 def load_traffic(workload, prec):
@@ -741,12 +891,11 @@ def run_strings(args):
 
 # ------------------------------------------------------ cubature |C| sweep --
 def cubature_bytes(n_cub, r):
-    """Algorithmic bytes of one cubature launch (k_cubature, warp per tet): per tet the
-    decoded u and the r columns of J at its 12 DOFs, its 4 vertex ids, Dm^-1 (9 floats),
-    rest volume, id and weight read, and its weighted force and DOF ids (12 + 12, read
-    again by W_L^T a) written.  The per-tet J_e^T f_e / J_e^T K_e J_e partials and
-    energies the kernel writes for the column sums (r + r(r+1)/2 + 2 words per tet) are
-    an intermediate of this design, not counted: they show as traffic above these bytes."""
+    """Algorithmic bytes of one cubature launch (k_cubature): per tet the decoded u and
+    the r columns of J at its 12 DOFs, its 4 vertex ids, Dm^-1 (9 floats), rest volume,
+    id and weight read, and its weighted force and DOF ids (12 + 12, read again by
+    W_L^T a) written.  The block-summed J_e^T f_e / J_e^T K_e J_e partials (one row of
+    r + r(r+1)/2 words and one energy per block of tets) are not counted."""
     read = 12 * 4 * (1 + r) + 4 * 4 + 9 * 4 + 4 + 4 + 4
     write = 12 * 4 + 12 * 4
     return n_cub * (read + write)

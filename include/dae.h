@@ -100,13 +100,17 @@ typedef struct {
 /* Per-frame outcome of dae_newton_step / dae_rollout. */
 typedef struct {
     int iters;           /* accepted Newton updates */
-    int evals;           /* full evaluations (derivatives + cubature + assembly) */
+    int evals;           /* evaluations of phi (the derivative pass, cubature, phi); those
+                            of trials that start no new Newton step (rejected, converged or
+                            stopped) skip the reverse pass and the Newton matrix */
     int converged;       /* 1 if |phi| reached tol or the next step fell below xtol */
     int status;          /* dae_status of the frame (device-side errors included) */
     double phi_norm0;    /* |phi| at the first iterate */
     double phi_norm;     /* |phi| at the returned iterate */
     double energy;       /* cubature elastic energy sum w_e V_e Psi_e at the returned iterate */
     double alpha;        /* last accepted step length */
+    int full_evals;      /* evaluations that also formed the Newton matrix A and solved
+                            A delta = -phi (complex-step reverse pass included) */
 } dae_newton_report;
 
 /* ---------------------------------------------------------------- context -- */

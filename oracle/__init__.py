@@ -527,6 +527,10 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
     rs = system(q)
     phi0 = np.linalg.norm(rs["phi"])
     hist = [phi0]
+    # the line search's trail, for comparing control decisions: every trial as
+    # (iteration, alpha, |phi(trial)|^2 / Armijo threshold, or None for an inverted
+    # trial), the accepted step lengths, and the number of system evaluations
+    trials, alphas, evals = [], [], 1
     it = 0
     converged = phi0 <= tol * max(1.0, phi0)
     while not converged and it < max_iter:
@@ -539,12 +543,16 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
         alpha = max_step / dn if (max_step > 0 and dn > max_step) else 1.0
         for _ in range(max_halvings + 1):
             qt = q + alpha * delta
+            evals += 1
             try:
                 rt = system(qt)
                 mt = float(rt["phi"] @ rt["phi"])
-                ok = mt <= (1.0 - 2.0 * c_armijo * alpha) * m0
+                thr = (1.0 - 2.0 * c_armijo * alpha) * m0
+                ok = mt <= thr
+                trials.append((it, alpha, mt / thr if thr > 0 else np.inf))
             except Inverted:
                 ok = False
+                trials.append((it, alpha, None))
             if ok:
                 break
             alpha *= 0.5
@@ -552,9 +560,11 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
             break
         q, rs = qt, rt
         it += 1
+        alphas.append(alpha)
         hist.append(float(np.linalg.norm(rs["phi"])))
         converged = hist[-1] <= tol * max(1.0, phi0)
-    return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs)
+    return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs,
+                   trials=trials, alphas=alphas, evals=evals)
 
 
 # --------------------------------------------------- coupled substructures --

@@ -17,7 +17,7 @@ using namespace dae;
 static std::atomic<unsigned long long> g_mesh_ids{1};
 static std::atomic<unsigned long long> g_dec_ids{1};
 
-#define DAE_VERSION 10000
+#define DAE_VERSION 10100
 
 namespace {
 
@@ -271,7 +271,7 @@ void free_workspace(Workspace& w) {
     if (w.gexec) cudaGraphExecDestroy(w.gexec);
     dfree(w.traj); dfree(w.qout); dfree(w.rc);
     dfree(w.G); dfree(w.xy); dfree(w.pext); dfree(w.fext_prev); dfree(w.pext_flag); dfree(w.pext_part);
-    dfree(w.Gs32); dfree(w.Gsh); dfree(w.Gsl); dfree(w.cub_rows); dfree(w.gy);
+    dfree(w.Gs32); dfree(w.Gsh); dfree(w.Gsl); dfree(w.cub_rows); dfree(w.gy); dfree(w.Jc);
     dfree(w.wn_B1); dfree(w.wn_c1); dfree(w.wn_A2); dfree(w.wn_b2); dfree(w.wn_A3); dfree(w.wn_b3);
     dfree(w.wn_A4); dfree(w.wn_b4); dfree(w.wn_h1); dfree(w.wn_w);
     dfree(w.V); dfree(w.UMU); dfree(w.Uf); dfree(w.zpv); dfree(w.lin_part);
@@ -419,6 +419,8 @@ void make_out_job(const dae_decoder* d, const Outs& o, double dt, double h, Chai
         job.a.pext = o.pext;
         job.a.gy = w.gy;
         job.a.a_out = nullptr;
+        job.a.Jc = w.Jc;
+        job.a.ldc = w.Rt * 128;
     }
 }
 
@@ -479,6 +481,15 @@ dae_status ensure_gs(dae_decoder* d, const dae_mesh* m, int n_cub) {
         TRY(dmalloc(ctx, &w.chain_cnt, w.chain_cnt_n));
         w.graph_ok = false;
     }
+    // the cubature rows' u and J in compact form (written by the output stage)
+    const size_t jc = (size_t)(1 + d->r) * Rt * 128;
+    if (jc > w.Jc_cap) {
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.Jc);
+        TRY(dmalloc(ctx, &w.Jc, jc));
+        w.Jc_cap = jc;
+        w.graph_ok = false;
+    }
     if (w.gs_G_mesh != m->id) {
         const size_t n = (size_t)K * w.ldGs;   // G is [K][ldG], ldG = ldGs
         if (f32) launch_round_tf32(ctx->stream, w.G, w.Gs32, n);
@@ -518,17 +529,32 @@ dae_status prepare_gram_out(dae_decoder* d, const dae_mesh* m, int n_cub) {
     return DAE_OK;
 }
 
-// Job lists of the persistent layer-chain kernel (both directions).
-dae_status build_chains(dae_decoder* d) {
-    dae_ctx* ctx = d->ctx;
-    Workspace& w = d->ws;
-    const int L = d->L, G = ctx->sm_count;
-    std::vector<ChainJob> fj(L - 1), rj(L - 1);
-    size_t part = 1, cnt_f = 0, cnt_r = 0;
+// Plan of chain layer l (direction dir): the decoder's stored plan for its precision,
+// else the fixed heuristic.
+void apply_plan(const dae_decoder* d, int dir, int l, ChainJob& j, int grid) {
+    const auto& sp = d->plan_split[dir];
+    if (d->plan_prec == (int)d->prec && (int)sp.size() == d->L - 1) {
+        j.split = sp[l];
+        j.rep = d->plan_rep[dir][l];
+    } else {
+        chain_plan(j, grid);
+    }
+}
+
+// The job lists of both directions with the current plans; part = floats of split-K
+// partial tiles they need, cnt = their per-tile counters.
+void chain_jobs(const dae_decoder* d, std::vector<ChainJob>& fj, std::vector<ChainJob>& rj,
+                size_t& part, size_t& cnt_f, size_t& cnt_r) {
+    const Workspace& w = d->ws;
+    const int L = d->L, G = d->ctx->sm_count;
+    fj.assign(L - 1, ChainJob{});
+    rj.assign(L - 1, ChainJob{});
+    part = 1;
+    cnt_f = cnt_r = 0;
     for (int l = 0; l < L - 1; ++l) {
         ChainJob& j = fj[l];
         make_fwd_job(d, l, j);
-        chain_plan(j, G);
+        apply_plan(d, 0, l, j, G);
         j.cnt_off = (int)cnt_f;
         cnt_f += j.tiles;
         part = std::max(part, (size_t)j.tiles * j.split * (w.Cp + 1) * 128);
@@ -537,11 +563,21 @@ dae_status build_chains(dae_decoder* d) {
         const int l = L - 2 - i;
         ChainJob& j = rj[i];
         make_rev_job(d, l, j);
-        chain_plan(j, G);
+        apply_plan(d, 1, l, j, G);
         j.cnt_off = (int)cnt_r;
         cnt_r += j.tiles;
         part = std::max(part, (size_t)j.tiles * j.split * (w.Cb + 1) * 128);
     }
+}
+
+// Job lists of the persistent layer-chain kernel (both directions).
+dae_status build_chains(dae_decoder* d) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    const int L = d->L, G = ctx->sm_count;
+    std::vector<ChainJob> fj, rj;
+    size_t part, cnt_f, cnt_r;
+    chain_jobs(d, fj, rj, part, cnt_f, cnt_r);
     if (!w.fwd_jobs) {
         CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * (L - 1)));
         CU(ctx, cudaMalloc(&w.rev_jobs, sizeof(ChainJob) * (L - 1)));
@@ -874,9 +910,37 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     ca.cub_tets = P.cub_tets; ca.cub_w = P.cub_w; ca.n_cub = P.n_cub;
     ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
     ca.stride = w.cub_stride; ca.ns = ns; ca.eval_flag = w.eval_flag;
+    ca.Jc = gout ? w.Jc : nullptr; ca.ldc = w.Rt * 128;
+    ca.n_parts = cubature_parts(P.n_cub, sm);
     {
         Phase p(ctx, DAE_PHASE_CUBATURE, P.n_cub > 0 ? 1 : 0);
         launch_cubature(s, ca);
+    }
+    if (L == 1)
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "a decoder needs at least one hidden layer");
+    // phi, the energy and the line-search decision: under Newton control, an iterate that
+    // is not accepted for a new Newton step skips the reverse pass and A below
+    AsmArgs aa;
+    memset(&aa, 0, sizeof aa);
+    aa.r = n; aa.dt = P.dt; aa.h = P.h;
+    aa.rq = r; aa.np = np; aa.lin_part = w.lin_part; aa.lin_blocks = w.lin_blocks;
+    aa.UMU = w.UMU; aa.Uf = P.f_ext ? w.Uf : nullptr; aa.qbar = w.qbar; aa.qbar_dot = w.qbar_dot;
+    aa.q_in = q_override;
+    aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
+    aa.row_stride = w.row_stride;
+    aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = P.n_cub;
+    aa.cub_stride = w.cub_stride; aa.cub_parts = ca.n_parts;
+    aa.red = w.red; aa.ns = ns; aa.control = P.control;
+    if (P.opts) {
+        aa.tol = P.opts->tol; aa.c_armijo = P.opts->c_armijo; aa.max_iter = P.opts->max_iter;
+        aa.max_step = P.opts->max_step; aa.xtol = P.opts->xtol;
+        aa.max_halvings = P.opts->max_halvings; aa.max_evals = P.opts->max_evals;
+    }
+    aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+    aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
+    {
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
+        launch_decide(s, aa);
     }
     // delta_{L-1} = W_L^T a = W_L^T M y - dt^2 W_L^T f_ext + dt^2 W_L^T f_C:
     // with the Gram matrix, W_L^T M y = G x_y (y = W_L x_y) and W_L^T f_ext is cached,
@@ -942,33 +1006,10 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         in_ncol = 1 + r;
     }
     }
-    if (L == 1)
-        return fail(ctx, DAE_ERR_UNSUPPORTED, "a decoder needs at least one hidden layer");
-    AsmArgs aa;
-    memset(&aa, 0, sizeof aa);
-    aa.r = n; aa.dt = P.dt; aa.h = P.h;
-    aa.rq = r; aa.np = np; aa.lin_part = w.lin_part; aa.lin_blocks = w.lin_blocks;
-    aa.UMU = w.UMU; aa.Uf = P.f_ext ? w.Uf : nullptr; aa.qbar = w.qbar; aa.qbar_dot = w.qbar_dot;
-    aa.q_in = q_override;
-    aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
-    aa.row_stride = w.row_stride;
-    aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = P.n_cub;
-    aa.cub_stride = w.cub_stride;
     aa.bwd_part = w.bwd_part[cur]; aa.bwd_split = in_split;
-    aa.red = w.red; aa.ns = ns; aa.control = P.control;
-    if (P.opts) {
-        aa.tol = P.opts->tol; aa.c_armijo = P.opts->c_armijo; aa.max_iter = P.opts->max_iter;
-        aa.max_step = P.opts->max_step; aa.xtol = P.opts->xtol;
-        aa.max_halvings = P.opts->max_halvings; aa.max_evals = P.opts->max_evals;
-    } else {
-        aa.tol = 0; aa.c_armijo = 0; aa.max_iter = 0; aa.max_halvings = 0; aa.max_evals = 0;
-        aa.max_step = 0; aa.xtol = 0;
-    }
-    aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
-    aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
     {
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
-        launch_assemble(s, aa);
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, 1);
+        launch_control(s, aa);
     }
     CU(ctx, cudaGetLastError());
     return DAE_OK;
@@ -1128,7 +1169,7 @@ dae_status run_frames(dae_decoder* d, const dae_mesh* m, EvalParams P, int n_fra
     }
     GraphKey key;
     memset(&key, 0, sizeof key);
-    key.mesh_id = m->id; key.cub_w = P.cub_w; key.cub_tets = P.cub_tets; key.fe_w = w.fe_w;
+    key.mesh_id = m->id; key.dec_id = d->id; key.cub_w = P.cub_w; key.cub_tets = P.cub_tets; key.fe_w = w.fe_w;
     key.hist = w.hist; key.traj = w.traj; key.fext = P.f_ext; key.n_cub = P.n_cub;
     key.gram = w.G && w.G_mesh == m->id; key.prec = d->prec;
     key.max_iter = P.opts->max_iter; key.max_halvings = P.opts->max_halvings;
@@ -1179,6 +1220,7 @@ void to_report(const NewtonState& s, dae_newton_report* rep) {
     rep->phi_norm = std::sqrt(s.merit_acc);
     rep->energy = s.energy;
     rep->alpha = s.alpha;
+    rep->full_evals = s.nfull;
 }
 
 void fill_opts(const dae_newton_opts* in, dae_newton_opts* o) {
@@ -1408,6 +1450,12 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         launch_cubature_batched(s, b->cub, n, b->max_cub);
     }
     {
+        // phi and the decisions: systems whose iterate starts no new Newton step skip the
+        // reverse pass below
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, 3);
+        launch_decide_batched(s, b->cs, b->ds, b->ctl, n, b->max_ent);
+    }
+    {
         Phase p(ctx, DAE_PHASE_WTA, 2);
         launch_xy_batched(s, b->xy, n, b->max_K);
         launch_wta_batched(s, b->wta, n, b->max_K, b->max_splits);
@@ -1425,8 +1473,8 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         if (!launch_chain(s, cl, prec)) return fail(ctx, DAE_ERR_CUDA, "grouped chain launch failed");
     }
     {
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, 4);
-        launch_assemble_batched(s, b->cs, b->ds, b->ctl, n, b->max_ent);
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
+        launch_control_batched(s, b->ctl, n);
         launch_batch_cond(s, b->frame, n, hc, flag);
     }
     CU(ctx, cudaGetLastError());
@@ -1501,7 +1549,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         }
         ca.fe_w = w.fe_w; ca.fe_dof = w.fe_dof; ca.part = w.cub_part; ca.energy = w.cub_energy;
         ca.stride = w.cub_stride; ca.ns = w.ns; ca.eval_flag = w.eval_flag;
-        b->max_cub = std::max(b->max_cub, ncub[i]);
+        ca.Jc = gout ? w.Jc : nullptr; ca.ldc = w.Rt * 128;
+        ca.n_parts = cubature_parts(ncub[i], ctx->sm_count);
+        b->max_cub = std::max(b->max_cub, ca.n_parts);
         const Layer& top = d->layers[L - 1];
         const int K = top.n_in;
         const int kb = (K + 1023) / 1024;
@@ -1557,7 +1607,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
         aa.row_stride = w.row_stride;
         aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = ncub[i];
-        aa.cub_stride = w.cub_stride;
+        aa.cub_stride = w.cub_stride; aa.cub_parts = ca.n_parts;
         aa.bwd_part = w.bwd_part[1]; aa.bwd_split = 1;
         aa.red = w.red; aa.ns = w.ns; aa.control = 1;
         aa.tol = opts.tol; aa.c_armijo = opts.c_armijo; aa.max_iter = opts.max_iter;
@@ -1813,6 +1863,10 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     dae_ctx* ctx = d->ctx;
     if (prec < DAE_FP32 || prec > DAE_BF16X3) return fail(ctx, DAE_ERR_INVALID_ARG, "bad precision");
     CU(ctx, cudaSetDevice(ctx->device));
+    // the cached frame graph bakes the layer chains' job, partial-tile and counter
+    // buffers, which build_chains below frees and reallocates: never replay it again
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_graph(d->ws);
     if (prec == DAE_BF16 || prec == DAE_BF16X3) {
         for (auto& ly : d->layers) {
             size_t n = (size_t)ly.m_pad * ly.ld;

@@ -74,7 +74,10 @@ struct NewtonState {
     int converged;
     int status;              // dae_status of the frame
     int frame;
-    int pad_;
+    int skip_rev;            // 1: this evaluation's trial is not accepted for a new Newton
+                             //    step (rejected, converged or stopped), so the reverse pass
+                             //    and the Newton matrix are skipped (set by k_decide)
+    int nfull;               // evaluations of the frame that formed the Newton matrix
 };
 
 struct ChainJob;
@@ -92,6 +95,7 @@ struct RollCtl {
 // Everything a captured frame graph bakes into its kernel parameters.
 struct GraphKey {
     unsigned long long mesh_id;
+    unsigned long long dec_id;   // bumped by every precision change (the chains are rebuilt)
     const void* cub_w; const void* cub_tets; const void* fe_w; const void* hist; const void* traj;
     const void* fext; const void* gs; const void* wn;
     int n_cub, gram, prec, max_iter, max_halvings, max_evals;
@@ -191,6 +195,8 @@ struct Workspace {
     int Gt = 0, Rt = 0, ldGs = 0, gs_rows_cap = 0;
     unsigned long long gs_G_mesh = 0;   // mesh id the G tiles were filled for
     int* cub_rows = nullptr;        // [gs_rows_cap] DOF of each cubature row (-1: none)
+    float* Jc = nullptr;            // compact cubature rows [1 + r][Rt * 128]: u | J e_j
+    size_t Jc_cap = 0;
     CUtensorMap tmGs[2];
     bool gs_ok = false;             // stacked operand ready (G part current)
     float* gy = nullptr;            // [K] G x_y, written by the G tiles' epilogue
@@ -251,6 +257,12 @@ struct dae_decoder {
     dae_prec prec = DAE_FP32;
     std::vector<dae::Layer> layers;
     dae::Workspace ws;
+    // work decomposition of the persistent layer chains, per hidden layer and direction
+    // (0 forward, 1 reverse; layer order 0..L-2 in both): CTAs per 128-row tile as a K
+    // split or as replicated K loops.  Empty: the fixed heuristic (chain_plan); set by
+    // dae_decoder_autotune / dae_decoder_set_chain_plan for the precision in plan_prec.
+    std::vector<int> plan_split[2], plan_rep[2];
+    int plan_prec = -1;
 };
 
 struct dae_mesh {
@@ -306,6 +318,9 @@ struct FwdArgs {
     const float* Xg; int ldxg;               // FP32 input activations of the output layer [Cp][ldxg]
     const float* pext;                       // W_L^T f_ext [K] or null
     float* gy;                               // out: G x_y [K]
+    // the cubature rows' u and J in compact form instead of at their DOFs (null: at the
+    // DOFs): Jc[0][i] = u, Jc[1 + j][i] = J e_j for stacked row i < n_map, stride ldc
+    float* Jc; int ldc;
 };
 
 // off: the decoder's coordinates start at entry off of the state (the linear subspace's
@@ -370,8 +385,14 @@ struct CubArgs {
     const NewtonState* ns; int* eval_flag;   // set when a Neo-Hookean tet is inverted
     // linear subspace: u += U p at the tet's DOFs (U = the first np rows of J, p = pv)
     int np; const float* pv;
+    // compact cubature rows written by the output stage (null: read u and J at the DOFs):
+    // [1 + r - np][ldc], row 12 slot + 3 a + d, column 0 = u, column 1 + j = J e_j
+    const float* Jc; int ldc;
+    int n_parts;                             // partial rows (blocks): cubature_parts(n_cub)
 };
 void launch_cubature(cudaStream_t s, const CubArgs& a);
+// partial rows of the cubature kernel for n_cub tets (one per block)
+int cubature_parts(int n_cub, int sm_count);
 
 struct WtaArgs {
     const float* W; int ld, N, K;           // dense matrix [N][ld] (W_L, or G with N = K)
@@ -412,6 +433,7 @@ struct AsmArgs {
     int r; double dt, h;
     const float* row_part; int n_row_blocks, row_stride;
     const float* cub_part; const double* cub_energy; int n_cub, cub_stride;
+    int cub_parts;                           // partial rows of the cubature kernel
     const float* bwd_part; int bwd_split;   // [split][1+r][r]
     double* red;                             // out: phi | A | energy | terms
     NewtonState* ns;                         // null: assemble only
@@ -428,7 +450,19 @@ struct AsmArgs {
     const double* qbar; const double* qbar_dot;   // full state arrays
     const double* q_in;                      // evaluation point when ns is null
 };
-void launch_assemble(cudaStream_t s, const AsmArgs& a);
+// One evaluation's FP64 end in two launches around the reverse pass:
+//   launch_decide   column sums of the row, cubature and linear-subspace partials and the
+//                   energy, then phi (Eq. 10) and, under Newton control, the line-search
+//                   decision (k_decide); a trial that is not accepted for a new Newton step
+//                   sets ns->skip_rev, which every reverse-pass kernel honours
+//   launch_control  the Newton matrix A (Eq. 11) from the reverse-pass partials and the
+//                   sums above, the solve A delta = -phi and the next trial (k_control)
+void launch_decide(cudaStream_t s, const AsmArgs& a);
+void launch_control(cudaStream_t s, const AsmArgs& a);
+// true when the reverse pass of this evaluation is skipped (device side)
+__device__ __forceinline__ bool skip_reverse(const NewtonState* ns) {
+    return ns && (ns->done || ns->skip_rev);
+}
 
 // ------------------------------------------------ grouped (batched) launches --
 // The kernels of one Newton evaluation run for many independent systems (decoder +
@@ -438,7 +472,8 @@ struct CtlArgs {
     cudaGraphConditionalHandle hcond; int use_cond;   // evaluation loop of a graph frame
     unsigned long long* kcount; int kpe;              // executed-kernel counter
     int r; double dt, h;
-    const double* rowsum; const double* cubsum; const double* bwdsum; const double* esum;
+    const double* rowsum; const double* cubsum; const double* esum;
+    const float* bwd_part; int bwd_split;             // reverse-pass partials [split][(1+rq) rq]
     int have_cub;
     double* red;
     NewtonState* ns; int control;
@@ -471,12 +506,13 @@ struct FrameArgs {
 // The three column sums, the energy sum and the control step of launch_assemble.
 void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c);
 void launch_seed_batched(cudaStream_t s, const SeedArgs* d_args, int n_sys, int max_elems);
-void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_cub);
+void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_parts);
 void launch_xy_batched(cudaStream_t s, const XyArgs* d_args, int n_sys, int max_K);
 void launch_wta_batched(cudaStream_t s, const WtaArgs* d_args, int n_sys, int max_K, int max_splits);
 void launch_bwd_prep_tc_batched(cudaStream_t s, const PrepArgs* d_args, int n_sys, int max_ld);
-void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
-                             const CtlArgs* c, int n_sys, int max_ent);
+void launch_decide_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
+                           const CtlArgs* c, int n_sys, int max_ent);
+void launch_control_batched(cudaStream_t s, const CtlArgs* c, int n_sys);
 void launch_frame_begin_batched(cudaStream_t s, const FrameArgs* f, int n_sys,
                                 cudaGraphConditionalHandle h, int use);
 void launch_frame_end_batched(cudaStream_t s, const FrameArgs* f, int n_sys);

@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int TS = CP + 1;
     constexpr uint32_t TILE_BYTES = 128u * TS * 4u;   // a partial tile as staged (multiple of 16)
 
-    if (ns && ns->done) return;   // uniform: every CTA reads the same flag
+    // uniform: every CTA reads the same flags; a reverse chain (modes 2, 3) also stops
+    // when this evaluation needs no Newton matrix
+    if (ns && (ns->done || (jobs[0].a.mode >= 2 && ns->skip_rev))) return;
 
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2], rbar;
@@ -316,7 +318,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = threadIdx.x; t < nj; t += blockDim.x) {
                 const ChainJob& Jt = jobs[j0 + t];
                 s_base[t] = Jt.item_base;
-                s_skip[t] = (Jt.a.ns && *(volatile const int*)&Jt.a.ns->done) ? 1 : 0;
+                s_skip[t] = (Jt.a.ns && (*(volatile const int*)&Jt.a.ns->done ||
+                                         (Jt.a.mode >= 2 && *(volatile const int*)&Jt.a.ns->skip_rev)))
+                                ? 1 : 0;
             }
             if (threadIdx.x == 0) s_base[nj] = jobs[j0 + nj - 1].item_base + jobs[j0 + nj - 1].tiles;
             __syncthreads();
@@ -566,7 +570,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // output rows of the cubature DOFs
                         const int i = (I.tl - Jb.a.gram_tiles) * 128 + row;
                         const int n = i < Jb.a.n_map ? Jb.a.row_map[i] : -1;
-                        row_epilogue(Jb.a, n < 0 ? Jb.a.n_out : n, vrow);
+                        if (Jb.a.Jc) {
+                            if (n >= 0) compact_epilogue(Jb.a, i, n, vrow);
+                        } else {
+                            row_epilogue(Jb.a, n < 0 ? Jb.a.n_out : n, vrow);
+                        }
                     } else {
                         row_epilogue(Jb.a, I.tl * 128 + row, vrow);
                         if (Jb.a.row_part)

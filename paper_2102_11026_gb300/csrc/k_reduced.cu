@@ -67,251 +67,356 @@ void launch_row_reduce(cudaStream_t s, const RowArgs& a, int n_blocks) {
 }
 
 // ------------------------------------------------------------- cubature --
-// One warp per cubature tet e (Sec. 5), displacement gradient G = dU Dm^{-1}
-// (F = I + G, formed from differences so small strains keep their accuracy):
+// Cubature forces and stiffness (Sec. 5) over the sampled tets e in C, with the
+// displacement gradient G = dU Dm^{-1} of each tet (F = I + G, formed from nodal
+// displacement differences so that small strains keep their accuracy):
 //   StVK: E = (G + G^T + G^T G)/2, S = 2 mu E + lam tr(E) I, P = F S,
 //         Psi = mu tr(E^2) + lam/2 tr(E)^2
 //   NH:   P = mu (F - F^{-T}) + lam ln(J) F^{-T},
 //         Psi = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2
 //   f_e = V_e P Dm^{-T} (nodes 1..3; node 0 = minus their sum)
-// Lane j < r takes the displacement direction of J's column j on the tet's 12
-// DOFs, dG_j, and its stress differential dP_j = dP[dG_j]; then
+// and, for every column j of J on the tet's 12 DOFs, the displacement direction dG_j
+// and stress differential dP_j = dP[dG_j]:
 //   g_j  = V_e P : dG_j            (= (J_e^T f_e)_j)
 //   K_ij = V_e dG_i : dP_j         (= (J_e^T K_e J_e)_ij)
-// Partial per slot: [w g (r) | w K upper (r(r+1)/2)], energy w V Psi (FP64).
-__device__ __forceinline__ void mat3_mul(const double* A, const double* B, double* C) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            C[i * 3 + j] = A[i * 3 + 0] * B[0 * 3 + j] + A[i * 3 + 1] * B[1 * 3 + j] +
-                           A[i * 3 + 2] * B[2 * 3 + j];
+// Work split (the per-tet algebra on every lane, the warp on the r columns):
+//   phase A   one tet per lane (up to 32 tets per warp at a time), FP32 in forms free of
+//             cancellation (below): F, P, the material terms dP needs, f_e (written out
+//             for W_L^T a), the energy (summed in FP64)
+//   phase B   per tet, lane j forms dG_j, dP_j and g_j; then the warp adds
+//             w_e V_e dG^T dP to a 32 x 32 register-blocked tile (lane: 4 rows x 8
+//             columns, the rows and columns broadcast from shared memory as float4)
+// Each block sums its warps' tiles and writes one partial row [g (r) | K upper
+// (r(r+1)/2, row-major i <= j)] and one FP64 energy: the column sums then add
+// n_parts rows instead of one per tet.  Fixed tet-to-warp assignment and summation
+// order: bitwise reproducible.
+// Cancellation-free forms (all terms at the scale of the result):
+//   NH   J - 1 = x = tr G + m2(G) + det G (m2: sum of the principal 2x2 minors),
+//        ln J = log1p(x), F - F^{-T} = G + F^{-T} G^T,
+//        Psi = mu [(x - log1p x) + 1/2 sum_{i<j} (G_ij + G_ji)^2 + sum_i G_ii^2
+//                  - 1/2 (tr G)^2 - det G] + lam/2 (log1p x)^2
+//        (the first-order parts of 1/2 (tr F^T F - 3) = tr G + |G|^2/2 and ln J cancel
+//        exactly and are left out)
+// J columns come from the compact cubature rows when the output stage wrote them
+// (Jc: [1 + rq][ldc], row 12 slot + 3 a + d = vertex a, axis d of the slot's tet,
+// column 0 = u), else from J ([r][N]) and u ([N]) at the DOFs.
+constexpr int kCubWarps = 4;   // warps per block
+
+// x - log1p(x) without cancellation: its Taylor series x^2/2 - x^3/3 + ... for
+// |x| < 1/4 (terms to x^14: truncation below 1e-9 of the result), the direct form
+// beyond (relative error ~ 2 eps / |x| <= 8 eps there).
+__device__ __forceinline__ float xm_log1p(float x) {
+    if (fabsf(x) < 0.25f) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 14; k >= 2; --k) s = fmaf(s, x, ((k & 1) ? -1.f : 1.f) / (float)k);
+        return s * x * x;
+    }
+    return x - log1pf(x);
 }
 
-constexpr int kCubWarps = 4;   // tets per block (one warp each): more SMs, one warp per scheduler
+struct CubTet {          // per-tet data phase A leaves for phase B (shared memory)
+    float F[9], P[9], M[9];   // M: S (StVK) or F^{-T} (NH)
+    float Bm[9];
+    float c1;                 // NH: mu - lam ln J
+    float wV;                 // w_e V_e
+    int v[4];
+    int slot;                 // cubature slot; -1: skipped (inverted or invalid)
+};
 
 __device__ __forceinline__ void cubature_impl(const CubArgs& A) {
     if (A.ns && A.ns->done) return;
-    __shared__ float sdG[kCubWarps][kMaxR][9];
-    __shared__ float sdP[kCubWarps][kMaxR][9];
+    const int b = blockIdx.x;
+    if (b >= A.n_parts) return;
+    // the tet records of phase A and, once every warp is done, the warps' tiles
+    union Shared { CubTet T[kCubWarps][32]; float K[kCubWarps][32][33]; };
+    __shared__ Shared sh;
+    auto& sT = sh.T;
+    auto& sK = sh.K;
+    __shared__ __align__(16) float sdG[kCubWarps][9][32];   // [k][i]: dG_i[k]
+    __shared__ __align__(16) float sdP[kCubWarps][9][32];   // [k][j]: w V dP_j[k]
+    __shared__ float sg[kCubWarps][32];
+    __shared__ double sE[kCubWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * kCubWarps + warp;
-    if (slot >= A.n_cub) return;
-    const int r = A.r;
+    const int r = A.r, np = A.np;
     const int nsym = r * (r + 1) / 2;
-    float* part = A.part + (size_t)slot * A.stride;
-    const int tet = A.cub_tets[slot];
-    const float wgt = A.cub_w[(A.ns ? (size_t)A.ns->frame * A.w_stride : 0) + slot];
-    if (tet < 0 || tet >= A.n_tet) {   // index checked here too: device arrays skip the host check
-        if (lane == 0) {
-            if (A.eval_flag) atomicExch(A.eval_flag, 2);
-            A.energy[slot] = 0.0;
+    const float mu = A.mu, lam = A.lam;
+    const float* __restrict__ wts = A.cub_w + (A.ns ? (size_t)A.ns->frame * A.w_stride : 0);
+    // this block's slots [s0, s1); warp w takes s0 + w, s0 + w + kCubWarps, ...
+    const int s0 = (int)((long long)A.n_cub * b / A.n_parts);
+    const int s1 = (int)((long long)A.n_cub * (b + 1) / A.n_parts);
+    const int mine = s1 - s0 > warp ? (s1 - s0 - warp + kCubWarps - 1) / kCubWarps : 0;
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
+    float g_acc = 0.f;
+    double e_acc = 0.0;
+    const int ib = lane >> 2, jb = lane & 3;   // tile block: rows 4 ib.., columns 8 jb..
+    for (int t0 = 0; t0 < mine; t0 += 32) {
+        const int nb = min(32, mine - t0);
+        // ---------------- phase A: one tet per lane
+        if (lane < nb) {
+            const int slot = s0 + warp + (t0 + lane) * kCubWarps;
+            CubTet& T = sT[warp][lane];
+            const int tet = A.cub_tets[slot];
+            T.slot = slot;
+            bool skip = false;
+            if (tet < 0 || tet >= A.n_tet) {   // device arrays skip the host's index check
+                if (A.eval_flag) atomicExch(A.eval_flag, 2);
+                skip = true;
+            } else {
+                int v[4];
+                for (int a = 0; a < 4; ++a) v[a] = A.tets[4 * tet + a];
+                float Bm[9];
+                for (int i = 0; i < 9; ++i) Bm[i] = A.Bm[9 * (size_t)tet + i];
+                const float V = A.vol[tet];
+                const float wgt = wts[slot];
+                float ue[12];
+                if (A.Jc) {
+                    const float4* uc = reinterpret_cast<const float4*>(A.Jc + 12 * (size_t)slot);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const float4 x = uc[q];
+                        ue[4 * q] = x.x; ue[4 * q + 1] = x.y; ue[4 * q + 2] = x.z; ue[4 * q + 3] = x.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) ue[k] = A.u[3 * v[k / 3] + k % 3];
+                }
+                if (np > 0) {   // linear subspace: + (U p) at the tet's DOFs
+                    for (int k = 0; k < 12; ++k) {
+                        const int dof = 3 * v[k / 3] + k % 3;
+                        float s = 0.f;
+                        for (int a = 0; a < np; ++a) s = fmaf(A.J[(size_t)a * A.N + dof], A.pv[a], s);
+                        ue[k] += s;
+                    }
+                }
+                // G = dU Bm, dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
+                float G[9];
+                for (int d = 0; d < 3; ++d)
+                    for (int j = 0; j < 3; ++j) {
+                        float s = 0.f;
+                        for (int c = 0; c < 3; ++c) s = fmaf(ue[3 * (c + 1) + d] - ue[d], Bm[c * 3 + j], s);
+                        G[d * 3 + j] = s;
+                    }
+                float F[9], P[9], M[9], c1 = 0.f, psi = 0.f;
+                for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.f : 0.f);
+                if (A.material == DAE_STVK) {
+                    float E[9];
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float gg = 0.f;
+                            for (int k = 0; k < 3; ++k) gg = fmaf(G[k * 3 + i], G[k * 3 + j], gg);
+                            E[i * 3 + j] = 0.5f * (G[i * 3 + j] + G[j * 3 + i] + gg);
+                        }
+                    const float trE = E[0] + E[4] + E[8];
+                    float trE2 = 0.f;
+                    for (int i = 0; i < 9; ++i) trE2 = fmaf(E[i], E[i], trE2);
+                    for (int i = 0; i < 9; ++i) M[i] = 2.f * mu * E[i] + ((i % 4) == 0 ? lam * trE : 0.f);
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float s = 0.f;
+                            for (int k = 0; k < 3; ++k) s = fmaf(F[i * 3 + k], M[k * 3 + j], s);
+                            P[i * 3 + j] = s;
+                        }
+                    psi = mu * trE2 + 0.5f * lam * trE * trE;
+                } else {
+                    const float trG = G[0] + G[4] + G[8];
+                    const float m2 = (G[0] * G[4] - G[1] * G[3]) + (G[0] * G[8] - G[2] * G[6]) +
+                                     (G[4] * G[8] - G[5] * G[7]);
+                    const float d3 = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                                     G[2] * (G[3] * G[7] - G[4] * G[6]);
+                    const float x = trG + m2 + d3;   // J - 1
+                    if (!(x > -1.f)) {
+                        if (A.eval_flag) atomicExch(A.eval_flag, 1);
+                        skip = true;
+                    } else {
+                        const float Jd = 1.f + x, lnJ = log1pf(x), iJ = 1.f / Jd;
+                        // F^{-T} = cof(F) / J
+                        M[0] = (F[4] * F[8] - F[5] * F[7]) * iJ;
+                        M[1] = (F[5] * F[6] - F[3] * F[8]) * iJ;
+                        M[2] = (F[3] * F[7] - F[4] * F[6]) * iJ;
+                        M[3] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+                        M[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+                        M[5] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+                        M[6] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+                        M[7] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+                        M[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+                        // P = mu (G + F^{-T} G^T) + lam ln J F^{-T}
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j) {
+                                float s = 0.f;
+                                for (int k = 0; k < 3; ++k) s = fmaf(M[i * 3 + k], G[j * 3 + k], s);
+                                P[i * 3 + j] = mu * (G[i * 3 + j] + s) + lam * lnJ * M[i * 3 + j];
+                            }
+                        c1 = mu - lam * lnJ;
+                        float sym = 0.f;
+                        sym += (G[1] + G[3]) * (G[1] + G[3]);
+                        sym += (G[2] + G[6]) * (G[2] + G[6]);
+                        sym += (G[5] + G[7]) * (G[5] + G[7]);
+                        const float dia = G[0] * G[0] + G[4] * G[4] + G[8] * G[8];
+                        psi = mu * (xm_log1p(x) + 0.5f * sym + dia - 0.5f * trG * trG - d3) +
+                              0.5f * lam * lnJ * lnJ;
+                    }
+                }
+                if (!skip) {
+                    // nodal forces: H = V P Bm^T, f(node c+1, d) = H[d][c], f(node 0) = -sum
+                    float fe[12];
+                    for (int d = 0; d < 3; ++d) {
+                        float f0 = 0.f;
+                        for (int c = 0; c < 3; ++c) {
+                            float h = 0.f;
+                            for (int k = 0; k < 3; ++k) h = fmaf(P[d * 3 + k], Bm[c * 3 + k], h);
+                            h *= V;
+                            fe[3 * (c + 1) + d] = wgt * h;
+                            f0 -= h;
+                        }
+                        fe[d] = wgt * f0;
+                    }
+                    float4* fw = reinterpret_cast<float4*>(A.fe_w + 12 * (size_t)slot);
+                    int4* fd = reinterpret_cast<int4*>(A.fe_dof + 12 * (size_t)slot);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        fw[q] = make_float4(fe[4 * q], fe[4 * q + 1], fe[4 * q + 2], fe[4 * q + 3]);
+                        int dd[4];
+                        for (int u = 0; u < 4; ++u) { const int k = 4 * q + u; dd[u] = 3 * v[k / 3] + k % 3; }
+                        fd[q] = make_int4(dd[0], dd[1], dd[2], dd[3]);
+                    }
+                    e_acc += (double)wgt * (double)V * (double)psi;
+                    for (int i = 0; i < 9; ++i) { T.F[i] = F[i]; T.P[i] = P[i]; T.M[i] = M[i]; T.Bm[i] = Bm[i]; }
+                    for (int a = 0; a < 4; ++a) T.v[a] = v[a];
+                    T.c1 = c1;
+                    T.wV = wgt * V;
+                }
+            }
+            if (skip) {
+                T.slot = -1;
+                float4* fw = reinterpret_cast<float4*>(A.fe_w + 12 * (size_t)slot);
+                int4* fd = reinterpret_cast<int4*>(A.fe_dof + 12 * (size_t)slot);
+                for (int q = 0; q < 3; ++q) { fw[q] = make_float4(0.f, 0.f, 0.f, 0.f); fd[q] = make_int4(0, 0, 0, 0); }
+            }
         }
-        for (int e = lane; e < r + nsym; e += 32) part[e] = 0.f;
-        if (lane < 12) { A.fe_w[slot * 12 + lane] = 0.f; A.fe_dof[slot * 12 + lane] = 0; }
-        return;
-    }
-    int v[4];
-    for (int a = 0; a < 4; ++a) v[a] = A.tets[4 * tet + a];
-    const float* Bmf = A.Bm + 9 * (size_t)tet;
-    const float Vf = A.vol[tet];
-    // per-tet FP64 part (F, P, Psi) once per warp: FP64 throughput is a small fraction
-    // of FP32 on this part, so the 31 other lanes wait and then read the results
-    __shared__ float sF[kCubWarps][9], sS[kCubWarps][9], sFiT[kCubWarps][9], sP[kCubWarps][9],
-        sLnJ[kCubWarps];
-    __shared__ int sBad[kCubWarps];
-    // lane j < r gathers column j of J on the tet's 12 DOFs now, so the loads are in
-    // flight while lane 0 forms the per-tet FP64 quantities
-    float Jg[12];
-    if (lane < r) {
-        const float* Jc = A.J + (size_t)lane * A.N;
+        __syncwarp();
+        // ---------------- phase B: the warp on the tet's r columns
+        for (int e = 0; e < nb; ++e) {
+            const CubTet& T = sT[warp][e];
+            if (T.slot < 0) continue;   // uniform over the warp
+            float dG[9], dP[9];
+            if (lane < r) {
+                float Jg[12];
+                if (A.Jc && lane >= np) {
+                    const float4* jc = reinterpret_cast<const float4*>(
+                        A.Jc + (size_t)(1 + lane - np) * A.ldc + 12 * (size_t)T.slot);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+                    for (int q = 0; q < 3; ++q) {
+                        const float4 x = jc[q];
+                        Jg[4 * q] = x.x; Jg[4 * q + 1] = x.y; Jg[4 * q + 2] = x.z; Jg[4 * q + 3] = x.w;
+                    }
+                } else {
+                    const float* Jcol = A.J + (size_t)lane * A.N;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) Jg[3 * a + d] = Jc[3 * v[a] + d];
-    }
-    // linear subspace: (U p) on the tet's 12 DOFs (U = the first np rows of J)
-    __shared__ float sUp[kCubWarps][12];
-    if (A.np > 0) {
-        if (lane < 12) {
-            const int dof = 3 * v[lane / 3] + lane % 3;
-            float acc = 0.f;
-            for (int a = 0; a < A.np; ++a) acc = fmaf(A.J[(size_t)a * A.N + dof], A.pv[a], acc);
-            sUp[warp][lane] = acc;
+                    for (int k = 0; k < 12; ++k) Jg[k] = Jcol[3 * T.v[k / 3] + k % 3];
+                }
+                for (int d = 0; d < 3; ++d)
+                    for (int j = 0; j < 3; ++j) {
+                        float s = 0.f;
+                        for (int c = 0; c < 3; ++c) s = fmaf(Jg[3 * (c + 1) + d] - Jg[d], T.Bm[c * 3 + j], s);
+                        dG[d * 3 + j] = s;
+                    }
+                if (A.material == DAE_STVK) {
+                    // dE = (dG^T F + F^T dG)/2, dS = 2 mu dE + lam tr(dE) I, dP = dG S + F dS
+                    float dE[9];
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float s = 0.f;
+                            for (int k = 0; k < 3; ++k)
+                                s = fmaf(dG[k * 3 + i], T.F[k * 3 + j], fmaf(T.F[k * 3 + i], dG[k * 3 + j], s));
+                            dE[i * 3 + j] = 0.5f * s;
+                        }
+                    const float trdE = dE[0] + dE[4] + dE[8];
+                    float dS[9];
+                    for (int i = 0; i < 9; ++i) dS[i] = 2.f * mu * dE[i] + ((i % 4) == 0 ? lam * trdE : 0.f);
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float s = 0.f;
+                            for (int k = 0; k < 3; ++k)
+                                s = fmaf(dG[i * 3 + k], T.M[k * 3 + j], fmaf(T.F[i * 3 + k], dS[k * 3 + j], s));
+                            dP[i * 3 + j] = s;
+                        }
+                } else {
+                    // dP = mu dG + (mu - lam lnJ) F^{-T} dG^T F^{-T} + lam (F^{-T}:dG) F^{-T}
+                    float tr = 0.f;
+                    for (int i = 0; i < 9; ++i) tr = fmaf(T.M[i], dG[i], tr);
+                    float M1[9];   // F^{-T} dG^T
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float s = 0.f;
+                            for (int k = 0; k < 3; ++k) s = fmaf(T.M[i * 3 + k], dG[j * 3 + k], s);
+                            M1[i * 3 + j] = s;
+                        }
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float s = 0.f;
+                            for (int k = 0; k < 3; ++k) s = fmaf(M1[i * 3 + k], T.M[k * 3 + j], s);
+                            dP[i * 3 + j] = mu * dG[i * 3 + j] + T.c1 * s + lam * tr * T.M[i * 3 + j];
+                        }
+                }
+                float gs = 0.f;
+                for (int i = 0; i < 9; ++i) gs = fmaf(T.P[i], dG[i], gs);
+                g_acc = fmaf(T.wV, gs, g_acc);
+            } else {
+                for (int i = 0; i < 9; ++i) { dG[i] = 0.f; dP[i] = 0.f; }
+            }
+            for (int k = 0; k < 9; ++k) {
+                sdG[warp][k][lane] = dG[k];
+                sdP[warp][k][lane] = T.wV * dP[k];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float4 gi = *reinterpret_cast<const float4*>(&sdG[warp][k][4 * ib]);
+                const float4 p0 = *reinterpret_cast<const float4*>(&sdP[warp][k][8 * jb]);
+                const float4 p1 = *reinterpret_cast<const float4*>(&sdP[warp][k][8 * jb + 4]);
+                const float gv[4] = {gi.x, gi.y, gi.z, gi.w};
+                const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(gv[a], pv[c], acc[a][c]);
+            }
+            __syncwarp();
         }
         __syncwarp();
     }
-    if (lane == 0) {
-        double Bm[9];
-        for (int i = 0; i < 9; ++i) Bm[i] = Bmf[i];
-        const double V = Vf;
-        // dU[d][c] = u(v_{c+1}, d) - u(v_0, d)
-        double dU[9];
-        for (int c = 0; c < 3; ++c)
-            for (int d = 0; d < 3; ++d) {
-                double u1 = (double)A.u[3 * v[c + 1] + d], u0 = (double)A.u[3 * v[0] + d];
-                if (A.np > 0) { u1 += (double)sUp[warp][3 * (c + 1) + d]; u0 += (double)sUp[warp][d]; }
-                dU[d * 3 + c] = u1 - u0;
-            }
-        double G[9], F[9], P[9], psi = 0.0, Finv_T[9], lnJ = 0.0, Sst[9];
-        mat3_mul(dU, Bm, G);
-        for (int i = 0; i < 9; ++i) F[i] = G[i] + ((i % 4) == 0 ? 1.0 : 0.0);
-        const double mu = A.mu, lam = A.lam;
-        int bad = 0;
-        for (int i = 0; i < 9; ++i) { Finv_T[i] = 0.0; Sst[i] = 0.0; }
-        if (A.material == DAE_STVK) {
-            double E[9];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    double gg = 0.0;
-                    for (int kk = 0; kk < 3; ++kk) gg += G[kk * 3 + i] * G[kk * 3 + j];
-                    E[i * 3 + j] = 0.5 * (G[i * 3 + j] + G[j * 3 + i] + gg);
-                }
-            const double trE = E[0] + E[4] + E[8];
-            double trE2 = 0.0;
-            for (int i = 0; i < 9; ++i) trE2 += E[i] * E[i];
-            for (int i = 0; i < 9; ++i) Sst[i] = 2.0 * mu * E[i] + ((i % 4) == 0 ? lam * trE : 0.0);
-            mat3_mul(F, Sst, P);
-            psi = mu * trE2 + 0.5 * lam * trE * trE;
-        } else {
-            // J - 1 = tr G + (principal 2x2 minors of G) + det G
-            const double trG = G[0] + G[4] + G[8];
-            const double m2 = G[0] * G[4] - G[1] * G[3] + G[0] * G[8] - G[2] * G[6] + G[4] * G[8] - G[5] * G[7];
-            const double detG = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
-                                G[2] * (G[3] * G[7] - G[4] * G[6]);
-            const double Jm1 = trG + m2 + detG;
-            const double Jd = 1.0 + Jm1;
-            if (!(Jd > 0.0)) {
-                bad = 1;
-                for (int i = 0; i < 9; ++i) P[i] = 0.0;
-            } else {
-                lnJ = log1p(Jm1);
-                // F^{-T} = cof(F) / J
-                double cof[9];
-                cof[0] = F[4] * F[8] - F[5] * F[7];
-                cof[1] = F[5] * F[6] - F[3] * F[8];
-                cof[2] = F[3] * F[7] - F[4] * F[6];
-                cof[3] = F[2] * F[7] - F[1] * F[8];
-                cof[4] = F[0] * F[8] - F[2] * F[6];
-                cof[5] = F[1] * F[6] - F[0] * F[7];
-                cof[6] = F[1] * F[5] - F[2] * F[4];
-                cof[7] = F[2] * F[3] - F[0] * F[5];
-                cof[8] = F[0] * F[4] - F[1] * F[3];
-                for (int i = 0; i < 9; ++i) Finv_T[i] = cof[i] / Jd;
-                for (int i = 0; i < 9; ++i) P[i] = mu * (F[i] - Finv_T[i]) + lam * lnJ * Finv_T[i];
-                double gg = 0.0;
-                for (int i = 0; i < 9; ++i) gg += G[i] * G[i];
-                // tr F^T F - 3 = 2 tr G + |G|^2
-                psi = 0.5 * mu * (2.0 * trG + gg) - mu * lnJ + 0.5 * lam * lnJ * lnJ;
-            }
-        }
-        for (int i = 0; i < 9; ++i) {
-            sF[warp][i] = (float)F[i]; sS[warp][i] = (float)Sst[i];
-            sFiT[warp][i] = (float)Finv_T[i]; sP[warp][i] = (float)P[i];
-        }
-        sLnJ[warp] = (float)lnJ;
-        sBad[warp] = bad;
-        A.energy[slot] = bad ? 0.0 : (double)wgt * V * psi;
-    }
-    __syncwarp();
-    const bool bad = sBad[warp] != 0;
-    float F[9], Sst[9], Finv_T[9], P[9], Bm[9];
-    for (int i = 0; i < 9; ++i) {
-        F[i] = sF[warp][i]; Sst[i] = sS[warp][i]; Finv_T[i] = sFiT[warp][i]; P[i] = sP[warp][i];
-        Bm[i] = Bmf[i];
-    }
-    const float lnJ = sLnJ[warp];
-    const float V = Vf;
-    const float mu = A.mu, lam = A.lam;
-    if (bad) {
-        if (lane == 0 && A.eval_flag) atomicExch(A.eval_flag, 1);
-        for (int e = lane; e < r + nsym; e += 32) part[e] = 0.f;
-        if (lane < 12) { A.fe_w[slot * 12 + lane] = 0.f; A.fe_dof[slot * 12 + lane] = 0; }
-        return;
-    }
-    // nodal forces: H = V P Bm^T, f(node c+1, d) = H[d][c], f(node 0) = -sum
-    if (lane < 12) {
-        int node = lane / 3, d = lane % 3;
-        float f = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            float Hdc = 0.f;
-            for (int kk = 0; kk < 3; ++kk) Hdc += P[d * 3 + kk] * Bm[c * 3 + kk];
-            Hdc *= V;
-            if (node == 0) f -= Hdc;
-            else if (c == node - 1) f = Hdc;
-        }
-        A.fe_w[slot * 12 + lane] = wgt * f;
-        A.fe_dof[slot * 12 + lane] = 3 * v[node] + d;
-    }
-    // directional quantities per column j
-    float g_j = 0.f;
-    if (lane < r) {
-        float dUj[9], dGj[9], dPj[9];
-        for (int c = 0; c < 3; ++c)
-            for (int d = 0; d < 3; ++d)
-                dUj[d * 3 + c] = Jg[3 * (c + 1) + d] - Jg[d];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                dGj[i * 3 + j] = dUj[i * 3 + 0] * (float)Bm[0 * 3 + j] +
-                                 dUj[i * 3 + 1] * (float)Bm[1 * 3 + j] +
-                                 dUj[i * 3 + 2] * (float)Bm[2 * 3 + j];
-        if (A.material == DAE_STVK) {
-            // dE = (dG^T F + F^T dG)/2, dS = 2 mu dE + lam tr(dE) I, dP = dG S + F dS
-            float dE[9];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    float s = 0.f;
-                    for (int k = 0; k < 3; ++k)
-                        s += dGj[k * 3 + i] * (float)F[k * 3 + j] + (float)F[k * 3 + i] * dGj[k * 3 + j];
-                    dE[i * 3 + j] = 0.5f * s;
-                }
-            float trdE = dE[0] + dE[4] + dE[8];
-            float dS[9];
-            for (int i = 0; i < 9; ++i) dS[i] = 2.f * (float)mu * dE[i] + ((i % 4) == 0 ? (float)lam * trdE : 0.f);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    float s = 0.f;
-                    for (int k = 0; k < 3; ++k)
-                        s += dGj[i * 3 + k] * (float)Sst[k * 3 + j] + (float)F[i * 3 + k] * dS[k * 3 + j];
-                    dPj[i * 3 + j] = s;
-                }
-        } else {
-            // dP = mu dG + (mu - lam lnJ) F^{-T} dG^T F^{-T} + lam (F^{-T}:dG) F^{-T}
-            float FiT[9];
-            for (int i = 0; i < 9; ++i) FiT[i] = (float)Finv_T[i];
-            float tr = 0.f;
-            for (int i = 0; i < 9; ++i) tr += FiT[i] * dGj[i];
-            float M1[9];   // F^{-T} dG^T
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    float s = 0.f;
-                    for (int k = 0; k < 3; ++k) s += FiT[i * 3 + k] * dGj[j * 3 + k];
-                    M1[i * 3 + j] = s;
-                }
-            const float c1 = (float)(mu - lam * lnJ);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    float s = 0.f;
-                    for (int k = 0; k < 3; ++k) s += M1[i * 3 + k] * FiT[k * 3 + j];
-                    dPj[i * 3 + j] = (float)mu * dGj[i * 3 + j] + c1 * s + (float)lam * tr * FiT[i * 3 + j];
-                }
-        }
-        float gs = 0.f;
-        for (int i = 0; i < 9; ++i) gs += (float)P[i] * dGj[i];
-        g_j = (float)(V * gs);
-        for (int i = 0; i < 9; ++i) { sdG[warp][lane][i] = dGj[i]; sdP[warp][lane][i] = dPj[i]; }
-    }
-    __syncwarp();
-    if (lane < r) part[lane] = wgt * g_j;
-    const float wV = (float)(wgt * V);
-    // (i, j) of upper-triangle entry e (row-major, i <= j), advanced 32 entries a step
-    int ui = 0, up = lane;
-    while (ui < r && up >= r - ui) { up -= r - ui; ++ui; }
-    for (int e = lane; e < nsym; e += 32) {
-        const int i = ui, j = ui + up;
-        up += 32;
-        while (ui < r && up >= r - ui) { up -= r - ui; ++ui; }
+    // ---------------- block sums: one partial row and one energy per block
+    __syncthreads();   // every warp is past phase B: the tet records may be overwritten
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sK[warp][4 * ib + a][8 * jb + c] = acc[a][c];
+    sg[warp][lane] = g_acc;
+    for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+    if (lane == 0) sE[warp] = e_acc;
+    __syncthreads();
+    float* part = A.part + (size_t)b * A.stride;
+    for (int e = threadIdx.x; e < r + nsym; e += blockDim.x) {
         float s = 0.f;
-        for (int k = 0; k < 9; ++k) s = fmaf(sdG[warp][i][k], sdP[warp][j][k], s);
-        part[r + e] = wV * s;
+        if (e < r) {
+            for (int w = 0; w < kCubWarps; ++w) s += sg[w][e];
+        } else {
+            int p = e - r, i = 0;
+            while (p >= r - i) { p -= r - i; ++i; }
+            const int j = i + p;
+            for (int w = 0; w < kCubWarps; ++w) s += sK[w][i][j];
+        }
+        part[e] = s;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kCubWarps; ++w) s += sE[w];
+        A.energy[b] = s;
     }
 }
 
@@ -322,14 +427,20 @@ __global__ void __launch_bounds__(32 * kCubWarps) k_cubature_b(const CubArgs* __
     cubature_impl(args[blockIdx.z]);
 }
 
-void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_cub) {
-    if (n_sys <= 0 || max_cub <= 0) return;
-    k_cubature_b<<<dim3((max_cub + kCubWarps - 1) / kCubWarps, 1, n_sys), 32 * kCubWarps, 0, s>>>(d_args);
+// Partial rows of a cubature set: one block per kCubWarps tets up to 4 blocks per SM.
+int cubature_parts(int n_cub, int sm_count) {
+    if (n_cub <= 0) return 0;
+    return std::max(1, std::min((n_cub + kCubWarps - 1) / kCubWarps, 4 * sm_count));
+}
+
+void launch_cubature_batched(cudaStream_t s, const CubArgs* d_args, int n_sys, int max_parts) {
+    if (n_sys <= 0 || max_parts <= 0) return;
+    k_cubature_b<<<dim3(max_parts, 1, n_sys), 32 * kCubWarps, 0, s>>>(d_args);
 }
 
 void launch_cubature(cudaStream_t s, const CubArgs& a) {
-    if (a.n_cub <= 0) return;
-    k_cubature<<<(a.n_cub + kCubWarps - 1) / kCubWarps, 32 * kCubWarps, 0, s>>>(a);
+    if (a.n_cub <= 0 || a.n_parts <= 0) return;
+    k_cubature<<<a.n_parts, 32 * kCubWarps, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------- W_L^T a GEMV --
@@ -345,7 +456,7 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& w, float a) {
 }
 
 __device__ __forceinline__ void wta_impl(const WtaArgs& A) {
-    if (A.ns && A.ns->done) return;
+    if (skip_reverse(A.ns)) return;
     if (A.run_flag && *A.run_flag == 0) return;
     const int k4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (k4 >= A.K) return;
@@ -438,7 +549,7 @@ void launch_wta(cudaStream_t s, const WtaArgs& a) {
 // activations (stacked columns, see dae_internal.h), so that J z + H[D,D] = W_L x_y.
 __device__ __forceinline__ void xy_impl(const float* X, int ld, int K, int r, const float* zvec,
                                         double h, float* xy, const NewtonState* ns) {
-    if (ns && ns->done) return;
+    if (skip_reverse(ns)) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const float ih = (float)(1.0 / h), ih2 = (float)(1.0 / (h * h));
@@ -527,7 +638,7 @@ constexpr int BW_THREADS = 128, BW_CHUNK = 32;
 // g[c][k] for k < n_o from the incoming partials (fixed summation order); one
 // thread per k forms the real part once and every i1 column from it.
 __global__ void k_bwd_prep(BwdArgs A) {
-    if (A.ns && A.ns->done) return;
+    if (skip_reverse(A.ns)) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= A.n_o) return;
     const int r = A.r;
@@ -549,7 +660,7 @@ __global__ void k_bwd_prep(BwdArgs A) {
 // and read as float4 over c.
 template <int NCOL>
 __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
-    if (A.ns && A.ns->done) return;
+    if (skip_reverse(A.ns)) return;
     __shared__ __align__(16) float gs[BW_CHUNK][NCOL];
     const int m = (blockIdx.x * BW_THREADS + threadIdx.x) * 2;
     const int ncol = 1 + A.r;
@@ -605,7 +716,7 @@ __global__ void __launch_bounds__(BW_THREADS) k_bwd(BwdArgs A) {
 __device__ __forceinline__ void bwd_prep_tc_impl(const BwdArgs& A, int Cb, int ld, float* g32,
                                                  __nv_bfloat16* gh, __nv_bfloat16* gl,
                                                  int out_f32, int out_bf16) {
-    if (A.ns && A.ns->done) return;
+    if (skip_reverse(A.ns)) return;
     if ((int)blockIdx.x * 32 >= ld) return;
     __shared__ float part[8][kMaxR + 1][33];
     __shared__ float sre[32];

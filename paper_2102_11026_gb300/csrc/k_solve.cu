@@ -196,49 +196,50 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
     return 0;
 }
 
-// Combine the reductions into phi, A, energy and the separate terms, then (if
-// control) take one step of the Newton / Armijo control.
-//   rowsum  [phi_dense (r) | Mr upper | B (i*r+j)]
+// The FP64 end of one evaluation, in two kernels around the reverse pass.
+//   rowsum  [phi_dense (rq) | Mr upper | B (i*rq+j)]
 //   cubsum  [g_int (r) | K_r upper]
-//   bwdsum  [(1+r) x r]: column 0 = J^T a, column 1+j = h (a^T H)[:, j]
+//   bwd     [(1+rq) x rq] per split: column 0 = J^T a, column 1+j = h (a^T H)[:, j]
 //   red     [phi (r) | A (r*r col-major) | energy | aH | Mr | B | Kr | g_int]
+// k_decide forms phi (Eqs. 7-8 times dt^2, Eq. 10 with a linear subspace) and the
+// energy, and under Newton control takes the line-search decision on the iterate just
+// evaluated (Armijo on |phi|^2, reading R6): accept it (a new Newton step follows,
+// unless it converged), or reject it and halve the step.  Only an accepted,
+// unconverged iterate needs the Newton matrix, so every other evaluation sets
+// ns->skip_rev and its reverse pass, W_L^T a and the solve are skipped: those are
+// phi-only evaluations.  k_control then forms A (Eq. 11) and solves A delta = -phi.
 
+// Linear subspace (np > 0): unknowns [p; q], decoder partials over rq = r - np.
+struct LinView {
+    const CtlArgs& C;
+    int rq, nc;
+    double inv_h, inv_h3;
+    __device__ double umj(int a, int j) const { return C.linsum[a * nc + 1 + j] * inv_h; }          // U^T M J
+    __device__ double umdj(int a, int j) const { return C.linsum[a * nc + 1 + rq + j] * inv_h3; }   // U^T M dJ
+};
 
-__device__ __forceinline__ void control_impl(const CtlArgs& C) {
-    if (C.ns && C.ns->done) {
-        // a finished frame never re-enters the evaluation loop
-        if (C.use_cond && threadIdx.x == 0) cudaGraphSetConditional(C.hcond, 0u);
-        return;
-    }
-    __shared__ double rhs[kMaxR];
-    __shared__ double x[kMaxR];
+__device__ __forceinline__ void decide_impl(const CtlArgs& C) {
+    if (C.ns && C.ns->done) return;
     __shared__ double sphi[kMaxR];
+    __shared__ double szp[kMaxR], szq[kMaxR];
     __shared__ int nonfinite;
-    __shared__ int decision;   // 0 reject, 1 accept-and-continue, 2 accept-and-stop, 3 stop
+    __shared__ double s_merit;
     __shared__ __align__(8) NewtonState S;
     const int r = C.r, t = threadIdx.x;
     const double dt2 = C.dt * C.dt;
     const double inv_h = 1.0 / C.h;   // one divide (exact for power-of-two steps)
     double* phi = C.red;
-    double* A = C.red + r;
     double* energy = C.red + r + r * r;
-    double* aH = energy + 1;
-    double* Mr = aH + r * r;
-    double* Bm = Mr + r * r;
-    double* Kr = Bm + r * r;
-    double* gint = Kr + r * r;
+    double* gint = energy + 1 + 4 * r * r;
     if (t == 0) nonfinite = 0;
     if (C.control) {
-        // stage the Newton state in shared memory (coalesced copy)
         const int nw = sizeof(NewtonState) / sizeof(int);
         for (int i = t; i < nw; i += blockDim.x)
             reinterpret_cast<int*>(&S)[i] = reinterpret_cast<const int*>(C.ns)[i];
     }
     __syncthreads();
-    // linear subspace (np > 0): unknowns [p; q], decoder partials over rq = r - np
-    const int np = C.np, rq = np > 0 ? C.rq : r, nsq = rq * (rq + 1) / 2, nc = 1 + 2 * rq;
-    const double inv_h3 = inv_h * inv_h * inv_h;
-    __shared__ double szp[kMaxR], szq[kMaxR];
+    const int np = C.np, rq = np > 0 ? C.rq : r;
+    const LinView lv{C, rq, 1 + 2 * rq, inv_h, inv_h * inv_h * inv_h};
     if (np > 0) {
         const double* qe = C.control ? S.q_trial : C.q_in;
         for (int i = t; i < r; i += blockDim.x) {
@@ -246,30 +247,6 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
             if (i < np) szp[i] = z; else szq[i - np] = z;
         }
         __syncthreads();
-    }
-    auto umj = [&](int a, int j) { return C.linsum[a * nc + 1 + j] * inv_h; };          // U^T M J
-    auto umdj = [&](int a, int j) { return C.linsum[a * nc + 1 + rq + j] * inv_h3; };   // U^T M dJ
-    for (int e = t; e < r * r; e += blockDim.x) {
-        const int i = e % r, j = e / r;   // column-major (i, j)
-        double ah = 0.0, mr, b = 0.0;
-        if (i >= np && j >= np) {
-            const int qi = i - np, qj = j - np;
-            ah = 0.5 * inv_h * (C.bwdsum[(1 + qj) * rq + qi] + C.bwdsum[(1 + qi) * rq + qj]);
-            mr = C.rowsum[rq + upper_idx(qi, qj, rq)];
-            b = C.rowsum[rq + nsq + qi * rq + qj];
-        } else if (i < np && j < np) {
-            mr = (double)C.UMU[i * np + j];              // U^T M U
-        } else if (i < np) {
-            mr = umj(i, j - np);                         // U^T M [J + dJ]
-            b = umdj(i, j - np);
-        } else {
-            mr = umj(j, i - np);                         // J^T M U
-        }
-        const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
-        const double a = ah + mr + b + dt2 * kr;
-        aH[e] = ah; Mr[e] = mr; Bm[e] = b; Kr[e] = kr;
-        A[e] = a;
-        if (!isfinite(a)) nonfinite = 1;
     }
     for (int i = t; i < r; i += blockDim.x) {
         const double g = C.have_cub ? C.cubsum[i] : 0.0;
@@ -279,12 +256,12 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
             // J^T (M y_q - dt^2 f_ext) + J^T M U z_p + dt^2 J^T f_C
             const int qi = i - np;
             p = C.rowsum[qi] + dt2 * g;
-            for (int a = 0; a < np; ++a) p += umj(a, qi) * szp[a];
+            for (int a = 0; a < np; ++a) p += lv.umj(a, qi) * szp[a];
         } else {
             // U^T M U z_p + U^T M (H[D,D] + J z_q) + dt^2 U^T (f_C - f_ext)
-            p = C.linsum[i * nc] * inv_h * inv_h + dt2 * (g - (C.Uf ? (double)C.Uf[i] : 0.0));
+            p = C.linsum[i * lv.nc] * inv_h * inv_h + dt2 * (g - (C.Uf ? (double)C.Uf[i] : 0.0));
             for (int b = 0; b < np; ++b) p += (double)C.UMU[i * np + b] * szp[b];
-            for (int j = 0; j < rq; ++j) p += umj(i, j) * szq[j];
+            for (int j = 0; j < rq; ++j) p += lv.umj(i, j) * szq[j];
         }
         phi[i] = p;
         sphi[i] = p;
@@ -293,19 +270,8 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     const double en = C.have_cub ? *C.esum : 0.0;
     if (t == 0) *energy = en;
     __syncthreads();
-    const int flag = C.eval_flag ? *C.eval_flag : 0;   // 1 inverted tet, 2 bad cubature index
-    const int inverted = flag != 0;
-    if (!C.control) {
-        if (t == 0) {
-            if (flag == 2) set_status(C.status, DAE_ERR_INVALID_ARG);
-            else if (inverted) set_status(C.status, DAE_ERR_INVERTED);
-            else if (nonfinite) set_status(C.status, DAE_ERR_NONFINITE);
-            if (C.eval_flag) *C.eval_flag = 0;
-        }
-        return;
-    }
+    if (!C.control) return;   // statuses of an assemble-only call: k_control
     // |phi|^2 by a warp reduction (serial FP64 chains are slow on this part)
-    __shared__ double s_merit;
     if (t < 32) {
         double m2 = t < r ? sphi[t] * sphi[t] : 0.0;
         for (int o = 16; o > 0; o >>= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
@@ -313,10 +279,12 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     }
     __syncthreads();
     if (t == 0) {
+        const int flag = C.eval_flag ? *C.eval_flag : 0;   // 1 inverted tet, 2 bad cubature index
+        const bool inverted = flag != 0;
         S.evals += 1;
         const double merit = s_merit;
         const bool bad = inverted || nonfinite || !isfinite(merit);
-        int dec;
+        int dec;   // 0 reject, 1 accept-and-continue, 2 accept-and-stop, 3 stop
         if (S.evals == 1) {
             if (bad) {
                 S.status = flag == 2 ? DAE_ERR_INVALID_ARG
@@ -341,70 +309,149 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
         } else if (dec == 0) {
             if (S.halvings >= C.max_halvings) dec = 3;
         }
-        if (dec != 3 && dec != 2 && S.evals >= C.max_evals) dec = 3;
-        decision = dec;
-    }
-    __syncthreads();
-    const int dec = decision;
-    if (dec == 1) {
-        for (int i = t; i < r; i += blockDim.x) rhs[i] = -sphi[i];
-        __syncthreads();
-        __shared__ double s_xn, s_qn;
-        __shared__ int lu_st;
-        if (t < 128) {
-            const int st0 = mixed_solve(A, rhs, x, r);
-            if (t == 0) lu_st = st0;
-        }
-        __syncthreads();
-        const int st = lu_st;
-        if (t < 32) {
-            double xn = t < r ? fabs(x[t]) : 0.0, qn = t < r ? fabs(S.q_acc[t]) : 0.0;
-            for (int o = 16; o > 0; o >>= 1) {
-                xn = fmax(xn, __shfl_xor_sync(0xffffffffu, xn, o));
-                qn = fmax(qn, __shfl_xor_sync(0xffffffffu, qn, o));
-            }
-            if (t == 0) { s_xn = xn; s_qn = qn; }
-        }
-        __syncthreads();
-        if (t == 0) {
-            if (st) {
-                S.status = st;
-                S.done = 1;
-            } else {
-                const double xn = s_xn, qn = s_qn;
-                if (C.xtol > 0.0 && xn <= C.xtol * fmax(1.0, qn)) {
-                    // the remaining correction is negligible: q_acc is the solution
-                    S.converged = 1;
-                    S.done = 1;
-                } else {
-                    // the first trial step is capped at max_step in the max-norm
-                    S.alpha = (C.max_step > 0.0 && xn > C.max_step) ? C.max_step / xn : 1.0;
-                    S.halvings = 0;
-                }
-            }
-        }
-        __syncthreads();
-        if (!st && !S.done)
-            for (int i = t; i < r; i += blockDim.x) {
-                S.delta[i] = x[i];
-                S.q_trial[i] = S.q_acc[i] + S.alpha * x[i];
-            }
-    } else if (dec == 0) {
-        if (t == 0) {
+        if ((dec == 0 || dec == 1) && S.evals >= C.max_evals) dec = 3;
+        if (dec == 1) {
+            S.skip_rev = 0;
+            S.nfull += 1;
+        } else if (dec == 0) {
+            S.skip_rev = 1;
             S.alpha *= 0.5;
             S.halvings += 1;
+            for (int i = 0; i < r; ++i) S.q_trial[i] = S.q_acc[i] + S.alpha * S.delta[i];
+        } else {
+            S.skip_rev = 1;
+            S.done = 1;
         }
+        if (C.eval_flag) *C.eval_flag = 0;
+        if (C.kcount) atomicAdd(C.kcount, (unsigned long long)C.kpe);
+    }
+    __syncthreads();
+    const int nw = sizeof(NewtonState) / sizeof(int);
+    for (int i = t; i < nw; i += blockDim.x)
+        reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
+}
+
+__global__ void k_decide(CtlArgs C) { decide_impl(C); }
+
+__device__ __forceinline__ void control_impl(const CtlArgs& C) {
+    const int t = threadIdx.x;
+    if (C.ns && (C.ns->done || C.ns->skip_rev)) {
+        // no Newton step from this evaluation: the loop ends once the frame is done
+        if (C.use_cond && t == 0) cudaGraphSetConditional(C.hcond, C.ns->done ? 0u : 1u);
+        return;
+    }
+    __shared__ double rhs[kMaxR];
+    __shared__ double x[kMaxR];
+    __shared__ int nonfinite;
+    __shared__ double sbwd[(kMaxR + 1) * kMaxR];
+    __shared__ __align__(8) NewtonState S;
+    const int r = C.r;
+    const double dt2 = C.dt * C.dt;
+    const double inv_h = 1.0 / C.h;
+    double* phi = C.red;
+    double* A = C.red + r;
+    double* energy = C.red + r + r * r;
+    double* aH = energy + 1;
+    double* Mr = aH + r * r;
+    double* Bm = Mr + r * r;
+    double* Kr = Bm + r * r;
+    if (t == 0) nonfinite = 0;
+    if (C.control) {
+        const int nw = sizeof(NewtonState) / sizeof(int);
+        for (int i = t; i < nw; i += blockDim.x)
+            reinterpret_cast<int*>(&S)[i] = reinterpret_cast<const int*>(C.ns)[i];
+    }
+    const int np = C.np, rq = np > 0 ? C.rq : r, nsq = rq * (rq + 1) / 2;
+    const LinView lv{C, rq, 1 + 2 * rq, inv_h, inv_h * inv_h * inv_h};
+    // column sums of the reverse pass's partials (one per split), in FP64
+    const int nb = (1 + rq) * rq;
+    for (int e = t; e < nb; e += blockDim.x) {
+        double acc = 0.0;
+        for (int p = 0; p < C.bwd_split; ++p) acc += (double)C.bwd_part[(size_t)p * nb + e];
+        sbwd[e] = acc;
+    }
+    __syncthreads();
+    for (int e = t; e < r * r; e += blockDim.x) {
+        const int i = e % r, j = e / r;   // column-major (i, j)
+        double ah = 0.0, mr, b = 0.0;
+        if (i >= np && j >= np) {
+            const int qi = i - np, qj = j - np;
+            ah = 0.5 * inv_h * (sbwd[(1 + qj) * rq + qi] + sbwd[(1 + qi) * rq + qj]);
+            mr = C.rowsum[rq + upper_idx(qi, qj, rq)];
+            b = C.rowsum[rq + nsq + qi * rq + qj];
+        } else if (i < np && j < np) {
+            mr = (double)C.UMU[i * np + j];              // U^T M U
+        } else if (i < np) {
+            mr = lv.umj(i, j - np);                      // U^T M [J + dJ]
+            b = lv.umdj(i, j - np);
+        } else {
+            mr = lv.umj(j, i - np);                      // J^T M U
+        }
+        const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
+        const double a = ah + mr + b + dt2 * kr;
+        aH[e] = ah; Mr[e] = mr; Bm[e] = b; Kr[e] = kr;
+        A[e] = a;
+        if (!isfinite(a)) nonfinite = 1;
+    }
+    if (!C.control) {
+        for (int i = t; i < r; i += blockDim.x)
+            if (!isfinite(phi[i])) nonfinite = 1;
         __syncthreads();
-        for (int i = t; i < r; i += blockDim.x) S.q_trial[i] = S.q_acc[i] + S.alpha * S.delta[i];
-    } else if (t == 0) {
-        S.done = 1;
+        if (t == 0) {
+            const int flag = C.eval_flag ? *C.eval_flag : 0;
+            if (flag == 2) set_status(C.status, DAE_ERR_INVALID_ARG);
+            else if (flag) set_status(C.status, DAE_ERR_INVERTED);
+            else if (nonfinite) set_status(C.status, DAE_ERR_NONFINITE);
+            if (C.eval_flag) *C.eval_flag = 0;
+        }
+        return;
+    }
+    for (int i = t; i < r; i += blockDim.x) rhs[i] = -S.phi[i];
+    __syncthreads();
+    __shared__ double s_xn, s_qn;
+    __shared__ int lu_st;
+    if (nonfinite) {
+        if (t == 0) lu_st = DAE_ERR_NONFINITE;
+    } else if (t < 128) {
+        const int st0 = mixed_solve(A, rhs, x, r);
+        if (t == 0) lu_st = st0;
+    }
+    __syncthreads();
+    const int st = lu_st;
+    if (t < 32) {
+        double xn = (t < r && !st) ? fabs(x[t]) : 0.0, qn = t < r ? fabs(S.q_acc[t]) : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            xn = fmax(xn, __shfl_xor_sync(0xffffffffu, xn, o));
+            qn = fmax(qn, __shfl_xor_sync(0xffffffffu, qn, o));
+        }
+        if (t == 0) { s_xn = xn; s_qn = qn; }
     }
     __syncthreads();
     if (t == 0) {
-        if (C.eval_flag) *C.eval_flag = 0;
-        if (C.kcount) atomicAdd(C.kcount, (unsigned long long)C.kpe);
-        if (C.use_cond) cudaGraphSetConditional(C.hcond, S.done ? 0u : 1u);
+        if (st) {
+            S.status = st;
+            S.done = 1;
+        } else {
+            const double xn = s_xn, qn = s_qn;
+            if (C.xtol > 0.0 && xn <= C.xtol * fmax(1.0, qn)) {
+                // the remaining correction is negligible: q_acc is the solution
+                S.converged = 1;
+                S.done = 1;
+            } else {
+                // the first trial step is capped at max_step in the max-norm
+                S.alpha = (C.max_step > 0.0 && xn > C.max_step) ? C.max_step / xn : 1.0;
+                S.halvings = 0;
+            }
+        }
     }
+    __syncthreads();
+    if (!st && !S.done)
+        for (int i = t; i < r; i += blockDim.x) {
+            S.delta[i] = x[i];
+            S.q_trial[i] = S.q_acc[i] + S.alpha * x[i];
+        }
+    __syncthreads();
+    if (t == 0 && C.use_cond) cudaGraphSetConditional(C.hcond, S.done ? 0u : 1u);
     const int nw = sizeof(NewtonState) / sizeof(int);
     for (int i = t; i < nw; i += blockDim.x)
         reinterpret_cast<int*>(C.ns)[i] = reinterpret_cast<const int*>(&S)[i];
@@ -424,14 +471,16 @@ void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c
     double* esum = bwdsum + (1 + r) * r;
     double* linsum = esum + 1;
     cs[0] = ColsumArgs{a.row_part, a.n_row_blocks, a.row_stride, rq + nsq + rq * rq, rowsum, a.ns};
-    cs[1] = ColsumArgs{a.cub_part, a.n_cub, a.cub_stride, a.n_cub > 0 ? r + nsym : 0, cubsum, a.ns};
-    cs[2] = ColsumArgs{a.bwd_part, a.bwd_split, (1 + rq) * rq, (1 + rq) * rq, bwdsum, a.ns};
+    cs[1] = ColsumArgs{a.cub_part, a.cub_parts, a.cub_stride, a.n_cub > 0 ? r + nsym : 0, cubsum, a.ns};
+    // the reverse pass's partials are summed by k_control (the reverse pass may be skipped)
+    cs[2] = ColsumArgs{nullptr, 0, 0, 0, bwdsum, a.ns};
     cs[3] = ColsumArgs{a.lin_part, a.lin_blocks, np * (1 + 2 * rq), np > 0 ? np * (1 + 2 * rq) : 0,
                        linsum, a.ns};
-    ds = DsumArgs{a.cub_energy, a.n_cub, esum, a.ns};
+    ds = DsumArgs{a.cub_energy, a.n_cub > 0 ? a.cub_parts : 0, esum, a.ns};
     memset(&c, 0, sizeof c);
     c.r = r; c.dt = a.dt; c.h = a.h;
-    c.rowsum = rowsum; c.cubsum = cubsum; c.bwdsum = bwdsum; c.esum = esum;
+    c.rowsum = rowsum; c.cubsum = cubsum; c.esum = esum;
+    c.bwd_part = a.bwd_part; c.bwd_split = a.bwd_split;
     c.have_cub = a.n_cub > 0;
     c.red = a.red; c.ns = a.ns; c.control = a.control;
     c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_step = a.max_step; c.xtol = a.xtol; c.max_iter = a.max_iter;
@@ -467,7 +516,7 @@ __global__ void __launch_bounds__(512) k_colsum4(const ColsumPack P) {
     colsum_impl(a.part, a.n_parts, a.stride, a.n_ent, a.out, a.ns);
 }
 
-void launch_assemble(cudaStream_t s, const AsmArgs& a) {
+void launch_decide(cudaStream_t s, const AsmArgs& a) {
     ColsumPack P;
     CtlArgs c;
     assemble_parts(a, P.cs, P.ds, c);
@@ -475,11 +524,19 @@ void launch_assemble(cudaStream_t s, const AsmArgs& a) {
     int max_ent = 1;
     for (int i = 0; i < 4; ++i) max_ent = P.cs[i].n_ent > max_ent ? P.cs[i].n_ent : max_ent;
     k_colsum4<<<dim3((max_ent + 31) / 32, 5), 512, 0, s>>>(P);
+    k_decide<<<1, 64, 0, s>>>(c);
+}
+
+void launch_control(cudaStream_t s, const AsmArgs& a) {
+    ColsumArgs cs[4];
+    DsumArgs ds;
+    CtlArgs c;
+    assemble_parts(a, cs, ds, c);
     k_control<<<1, 256, 0, s>>>(c);
 }
 
-// Grouped form: z = system; the four column sums in y (an empty sum skips), then the
-// energy sum and the control step, one block per system.
+// Grouped form: z = system; the column sums in y (an empty sum skips), then the energy
+// sum and the decision, one block per system; the control step after the reverse pass.
 __global__ void __launch_bounds__(512) k_colsum_b(const ColsumArgs* __restrict__ cs) {
     const ColsumArgs& a = cs[blockIdx.z * 4 + blockIdx.y];
     if ((int)blockIdx.x * 32 >= a.n_ent) return;
@@ -490,13 +547,19 @@ __global__ void k_dsum_b(const DsumArgs* __restrict__ ds) {
     if (a.n <= 0) return;
     dsum_impl(a.x, a.n, a.out, a.ns);
 }
+__global__ void k_decide_b(const CtlArgs* __restrict__ c) { decide_impl(c[blockIdx.x]); }
 __global__ void k_control_b(const CtlArgs* __restrict__ c) { control_impl(c[blockIdx.x]); }
 
-void launch_assemble_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
-                             const CtlArgs* c, int n_sys, int max_ent) {
+void launch_decide_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs* ds,
+                           const CtlArgs* c, int n_sys, int max_ent) {
     if (n_sys <= 0) return;
     k_colsum_b<<<dim3((max_ent + 31) / 32, 4, n_sys), 512, 0, s>>>(cs);
     k_dsum_b<<<n_sys, 256, 0, s>>>(ds);
+    k_decide_b<<<n_sys, 64, 0, s>>>(c);
+}
+
+void launch_control_batched(cudaStream_t s, const CtlArgs* c, int n_sys) {
+    if (n_sys <= 0) return;
     k_control_b<<<n_sys, 256, 0, s>>>(c);
 }
 
@@ -538,6 +601,7 @@ __global__ void k_frame_start(RollCtl* rc, NewtonState* ns, const double* qbar,
     if (i == 0) {
         ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
         ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
+        ns->skip_rev = 0; ns->nfull = 0;
         ns->status = 0; ns->frame = rc->frame;
         if (kcount) atomicAdd(kcount, 1ull);
         if (use) cudaGraphSetConditional(h, 1u);
@@ -607,6 +671,7 @@ __global__ void k_frame_begin_b(const FrameArgs* __restrict__ f, cudaGraphCondit
     if (i == 0) {
         ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
         ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
+        ns->skip_rev = 0; ns->nfull = 0;
         ns->status = 0; ns->frame = 0;
         if (use && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
     }

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t TMEM_COLS = (CP <= 32) ? 32 : (CP <= 64 ? 64 : 128);
     constexpr uint32_t ID = idesc(PREC == DAE_TF32 ? 2u : 1u, 128, CP);
 
-    if (A.ns && A.ns->done) return;
+    // the reverse-pass modes (2, 3) also stop when the evaluation needs no Newton matrix
+    if (A.ns && (A.ns->done || (A.mode >= 2 && A.ns->skip_rev))) return;
 
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull;

@@ -181,6 +181,17 @@ struct ActOut {
     }
 };
 
+// Output row n (a cubature DOF) of stacked row i in the compact form the cubature reads:
+// Jc[0][i] = u_n, Jc[1 + j][i] = J_nj (consecutive rows i of a warp: coalesced stores).
+static __device__ __noinline__ void compact_epilogue(const FwdArgs& A, int i, int n,
+                                                     const float* __restrict__ v) {
+    const size_t ld = A.ldc;
+    float* __restrict__ Jc = A.Jc;
+    const float fh = (float)A.inv_h;   // exact for the power-of-two steps the library uses
+    Jc[i] = v[0] + A.bias[n];
+    for (int j = 0; j < A.r; ++j) Jc[(size_t)(1 + j) * ld + i] = v[kShared + 3 * j] * fh;
+}
+
 static __device__ __noinline__ void row_epilogue(const FwdArgs& A, int n, const float* __restrict__ v) {
     const int mode = A.mode, r = A.r, CP = A.Cp, C = n_cols(r);
     const int n_out = A.n_out;

@@ -41,7 +41,7 @@ class dae_newton_report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("converged", ctypes.c_int),
                 ("status", ctypes.c_int), ("phi_norm0", ctypes.c_double),
                 ("phi_norm", ctypes.c_double), ("energy", ctypes.c_double),
-                ("alpha", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("full_evals", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -18,6 +18,21 @@ def relerr(x, ref):
     return np.linalg.norm(x - ref) / (den if den > 0 else 1.0)
 
 
+def colerr(x, ref):
+    """Largest per-column element error relative to that column's scale:
+    max_j max_i |x[i, j] - ref[i, j]| / max_i |ref[i, j]| (a vector is one column).
+    Unlike ``relerr`` it cannot dilute one wrong tile, row block or column of J in
+    the rest of the output; columns of exact zeros must come out exactly zero."""
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if ref.ndim == 1:
+        x, ref = x[:, None], ref[:, None]
+    err = np.abs(x - ref).max(axis=0)
+    scale = np.abs(ref).max(axis=0)
+    out = np.where(scale > 0, err / np.where(scale > 0, scale, 1.0), np.where(err > 0, np.inf, 0.0))
+    return float(out.max())
+
+
 class Gpu:
     def __init__(self, wl, prec="fp32", ctx=None):
         self.wl = wl
