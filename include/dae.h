@@ -150,6 +150,30 @@ dae_status dae_free_decoder(dae_decoder* dec);
 /* Change the GEMM arithmetic of a loaded decoder (builds splits if needed; synchronizes). */
 dae_status dae_decoder_set_precision(dae_decoder* dec, dae_prec prec);
 
+/* Work decomposition of the persistent layer chains (tensor-core precisions): the
+ * hidden layers of the stacked forward pass (dir 0) and of the complex-step reverse pass
+ * (dir 1) each run in one persistent launch, a layer cut into 128-row tiles with P CTAs
+ * per tile (P = 1, 2, 4 or 8; tiles x P at most the SM count), either as a split of the
+ * layer's K loop over the P CTAs (split = P, rep = 1; at least two 64-element k-blocks
+ * per CTA) or as P replicated K loops (split = 1, rep = P); each CTA finishes 128/P
+ * rows.  A plan is per precision: a precision change returns to the built-in plan.
+ * These are scheduling choices only; the paper has no counterpart (its passes are
+ * cuBLAS GEMMs, Sec. 6). */
+
+/* The current plan of direction dir: split[l], rep[l] for hidden layers l = 0..n_layers-2
+ * (network order in both directions).  Errors: INVALID_ARG, UNSUPPORTED (FP32). */
+dae_status dae_decoder_get_chain_plan(const dae_decoder* dec, int dir, int* split, int* rep);
+/* Set the plan of direction dir (NULL arrays: the built-in plan).  Every (split, rep)
+ * must be one of the candidates above for its layer, else INVALID_ARG.  Synchronizes. */
+dae_status dae_decoder_set_chain_plan(dae_decoder* dec, int dir, const int* split, const int* rep);
+/* Tile autotuner: for each direction, starting from the current plan, one pass over the
+ * layers tries every candidate of a layer and keeps it when the chain's launch time
+ * (CUDA events, mean of reps launches) drops by more than 1 %; the final plan is timed
+ * against the starting one, interleaved, and kept only if not slower.  ms (optional,
+ * 4 doubles): forward chain ms before / after, reverse chain ms before / after.
+ * Synchronizes; call it outside stream capture, once per decoder and precision. */
+dae_status dae_decoder_autotune(dae_decoder* dec, int reps, double* ms);
+
 /* ------------------------------------------------------------------- mesh -- */
 
 /*

@@ -598,6 +598,75 @@ dae_status build_chains(dae_decoder* d) {
     return DAE_OK;
 }
 
+// ------------------------------------------------------------ autotuner --
+// Candidate plans of one chain layer: P = 1, 2, 4 or 8 CTAs per 128-row tile (tiles x P
+// within the grid), each as replicated K loops or (P >= 2) as a K split with at least
+// two k-blocks per chunk.
+std::vector<std::pair<int, int>> plan_candidates(const ChainJob& j, int grid) {
+    std::vector<std::pair<int, int>> c;   // (split, rep)
+    for (int P = 1; P <= 8; P *= 2) {
+        if (j.tiles * P > grid) break;
+        c.push_back({1, P});
+        if (P >= 2 && j.nk >= 2 * P) c.push_back({P, 1});
+    }
+    return c;
+}
+
+// Mean device time (ms) of one launch of a direction's chain with the given job list,
+// over `reps` back-to-back launches after two warm-up launches (CUDA events on the
+// context's stream).  The buffers hold whatever the last evaluation left: the time of a
+// chain does not depend on the values.
+dae_status time_chain(dae_decoder* d, int dir, const std::vector<ChainJob>& jobs, int reps,
+                      double* ms) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    const int L = d->L;
+    ChainJob* dst = dir == 0 ? w.fwd_jobs : w.rev_jobs;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    CU(ctx, cudaMemcpy(dst, jobs.data(), sizeof(ChainJob) * (L - 1), cudaMemcpyHostToDevice));
+    ChainLaunch cl = {};
+    cl.jobs = dst; cl.n_jobs = L - 1; cl.Cp = dir == 0 ? w.Cp : w.Cb; cl.grid = ctx->sm_count;
+    cl.gb = w.gbar; cl.ns = nullptr; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+    cl.split_cnt = w.chain_cnt;
+    cudaEvent_t e0, e1;
+    CU(ctx, cudaEventCreate(&e0));
+    CU(ctx, cudaEventCreate(&e1));
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i) ok = launch_chain(ctx->stream, cl, d->prec);
+    cudaEventRecord(e0, ctx->stream);
+    for (int i = 0; i < reps && ok; ++i) ok = launch_chain(ctx->stream, cl, d->prec);
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->launches += 2 + reps;
+    if (!ok) return fail(ctx, DAE_ERR_CUDA, "chain launch failed while tuning");
+    if (e != cudaSuccess) return fail(ctx, DAE_ERR_CUDA, "chain timing: %s", cudaGetErrorString(e));
+    TRY(check_device_status(ctx));
+    *ms = t / reps;
+    return DAE_OK;
+}
+
+// Validated plan of one direction (sizes L - 1): every layer's (split, rep) must be a
+// candidate of plan_candidates.
+dae_status check_plan(dae_decoder* d, int dir, const int* split, const int* rep) {
+    std::vector<ChainJob> fj, rj;
+    size_t part, cf, cr;
+    chain_jobs(d, fj, rj, part, cf, cr);
+    const std::vector<ChainJob>& jobs = dir == 0 ? fj : rj;
+    for (int l = 0; l < d->L - 1; ++l) {
+        const ChainJob& j = jobs[dir == 0 ? l : d->L - 2 - l];
+        bool found = false;
+        for (auto c : plan_candidates(j, d->ctx->sm_count)) found |= (c.first == split[l] && c.second == rep[l]);
+        if (!found)
+            return fail(d->ctx, DAE_ERR_INVALID_ARG, "layer %d: (split %d, rep %d) is not a valid plan", l,
+                        split[l], rep[l]);
+    }
+    return DAE_OK;
+}
+
 dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* q_override,
                            double dt, double h, int mode, const Outs& o, int off = 0) {
     dae_ctx* ctx = d->ctx;
@@ -1867,6 +1936,10 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     // buffers, which build_chains below frees and reallocates: never replay it again
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     drop_graph(d->ws);
+    // a chain plan belongs to the precision it was set or tuned for
+    d->plan_prec = -1;
+    d->plan_split[0].clear(); d->plan_split[1].clear();
+    d->plan_rep[0].clear(); d->plan_rep[1].clear();
     if (prec == DAE_BF16 || prec == DAE_BF16X3) {
         for (auto& ly : d->layers) {
             size_t n = (size_t)ly.m_pad * ly.ld;
@@ -1946,6 +2019,143 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     d->ws.chain_ok = false;
     if (prec != DAE_FP32) TRY(build_chains(d));
     d->prec = prec;
+    return DAE_OK;
+}
+
+dae_status dae_decoder_get_chain_plan(const dae_decoder* d, int dir, int* split, int* rep) {
+    if (!d || (dir != 0 && dir != 1) || !split || !rep) return DAE_ERR_INVALID_ARG;
+    if (d->prec == DAE_FP32 || !d->ws.chain_ok)
+        return fail(d->ctx, DAE_ERR_UNSUPPORTED, "the layer chains run in the tensor-core precisions only");
+    std::vector<ChainJob> fj, rj;
+    size_t part, cf, cr;
+    chain_jobs(d, fj, rj, part, cf, cr);
+    for (int l = 0; l < d->L - 1; ++l) {
+        const ChainJob& j = dir == 0 ? fj[l] : rj[d->L - 2 - l];
+        split[l] = j.split;
+        rep[l] = j.rep;
+    }
+    return DAE_OK;
+}
+
+dae_status dae_decoder_set_chain_plan(dae_decoder* d, int dir, const int* split, const int* rep) {
+    if (!d || (dir != 0 && dir != 1)) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = d->ctx;
+    if (d->prec == DAE_FP32 || !d->ws.chain_ok)
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the layer chains run in the tensor-core precisions only");
+    CU(ctx, cudaSetDevice(ctx->device));
+    const int n = d->L - 1;
+    std::vector<int> sp(n), rp(n);
+    if (split && rep) {
+        TRY(check_plan(d, dir, split, rep));
+        sp.assign(split, split + n);
+        rp.assign(rep, rep + n);
+    } else {
+        // NULL arrays: back to the fixed heuristic for this direction
+        std::vector<ChainJob> fj, rj;
+        size_t part, cf, cr;
+        const int saved = d->plan_prec;
+        d->plan_prec = -1;
+        chain_jobs(d, fj, rj, part, cf, cr);
+        d->plan_prec = saved;
+        for (int l = 0; l < n; ++l) {
+            const ChainJob& j = dir == 0 ? fj[l] : rj[n - 1 - l];
+            sp[l] = j.split;
+            rp[l] = j.rep;
+        }
+    }
+    if (d->plan_prec != (int)d->prec || (int)d->plan_split[1 - dir].size() != n) {
+        // the other direction keeps its current plan
+        std::vector<int> os(n), orp(n);
+        TRY(dae_decoder_get_chain_plan(d, 1 - dir, os.data(), orp.data()));
+        d->plan_split[1 - dir] = os;
+        d->plan_rep[1 - dir] = orp;
+    }
+    d->plan_split[dir] = sp;
+    d->plan_rep[dir] = rp;
+    d->plan_prec = (int)d->prec;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_graph(d->ws);
+    d->id = g_dec_ids++;   // cached grouped plans bake the job lists
+    return build_chains(d);
+}
+
+dae_status dae_decoder_autotune(dae_decoder* d, int reps, double* ms) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = d->ctx;
+    if (d->prec == DAE_FP32 || !d->ws.chain_ok)
+        return fail(ctx, DAE_ERR_UNSUPPORTED, "the layer chains run in the tensor-core precisions only");
+    if (reps < 1) reps = 20;
+    CU(ctx, cudaSetDevice(ctx->device));
+    Workspace& w = d->ws;
+    const int L = d->L, n = L - 1, G = ctx->sm_count;
+    // room for the largest split any candidate may take
+    {
+        std::vector<ChainJob> fj, rj;
+        size_t part, cf, cr;
+        chain_jobs(d, fj, rj, part, cf, cr);
+        size_t need = 1;
+        for (const auto& j : fj) need = std::max(need, (size_t)j.tiles * 8 * (w.Cp + 1) * 128);
+        for (const auto& j : rj) need = std::max(need, (size_t)j.tiles * 8 * (w.Cb + 1) * 128);
+        need = std::max(need, (size_t)G * 2 * (w.Cp + 1) * 128);
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(w.chain_part);
+        TRY(dmalloc(ctx, &w.chain_part, need));
+    }
+    double out[4] = {0, 0, 0, 0};
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<ChainJob> fj, rj;
+        size_t part, cf, cr;
+        chain_jobs(d, fj, rj, part, cf, cr);
+        std::vector<ChainJob> jobs = dir == 0 ? fj : rj;   // launch order
+        const std::vector<ChainJob> start = jobs;
+        double best;
+        TRY(time_chain(d, dir, jobs, reps, &best));
+        // coordinate descent over the layers, one pass: a candidate replaces the current
+        // plan of its layer when it is faster by more than 1 % (timing noise)
+        for (int i = 0; i < n; ++i) {
+            for (auto c : plan_candidates(jobs[i], G)) {
+                if (c.first == jobs[i].split && c.second == jobs[i].rep) continue;
+                std::vector<ChainJob> trial = jobs;
+                trial[i].split = c.first;
+                trial[i].rep = c.second;
+                double t;
+                TRY(time_chain(d, dir, trial, reps, &t));
+                if (t < 0.99 * best) { best = t; jobs = trial; }
+            }
+        }
+        // the start and the result timed again, interleaved
+        double t0 = 0, t1 = 0;
+        for (int k = 0; k < 3; ++k) {
+            double a, b;
+            TRY(time_chain(d, dir, start, reps, &a));
+            TRY(time_chain(d, dir, jobs, reps, &b));
+            t0 += a / 3;
+            t1 += b / 3;
+        }
+        if (t1 > t0) { jobs = start; t1 = t0; }   // never keep a slower plan
+        out[2 * dir] = t0;
+        out[2 * dir + 1] = t1;
+        std::vector<int> sp(n), rp(n);
+        for (int i = 0; i < n; ++i) {
+            const int l = dir == 0 ? i : n - 1 - i;   // layer order
+            sp[l] = jobs[i].split;
+            rp[l] = jobs[i].rep;
+        }
+        if (d->plan_prec != (int)d->prec || (int)d->plan_split[1 - dir].size() != n) {
+            std::vector<int> os(n), orp(n);
+            TRY(dae_decoder_get_chain_plan(d, 1 - dir, os.data(), orp.data()));
+            d->plan_split[1 - dir] = os;
+            d->plan_rep[1 - dir] = orp;
+        }
+        d->plan_split[dir] = sp;
+        d->plan_rep[dir] = rp;
+        d->plan_prec = (int)d->prec;
+    }
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_graph(w);
+    d->id = g_dec_ids++;
+    TRY(build_chains(d));
+    if (ms) memcpy(ms, out, sizeof out);
     return DAE_OK;
 }
 

@@ -69,6 +69,9 @@ SIGNATURES = {
     "dae_load_decoder": ([_vp, _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp)], _i),
     "dae_free_decoder": ([_vp], _i),
     "dae_decoder_set_precision": ([_vp, _i], _i),
+    "dae_decoder_get_chain_plan": ([_vp, _i, _vp, _vp], _i),
+    "dae_decoder_set_chain_plan": ([_vp, _i, _vp, _vp], _i),
+    "dae_decoder_autotune": ([_vp, _i, _vp], _i),
     "dae_load_mesh": ([_vp, _i, _vp, _i, _vp, _vp, _i, _d, _d, ctypes.POINTER(_vp)], _i),
     "dae_free_mesh": ([_vp], _i),
     "dae_eval_derivs": ([_vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
@@ -204,6 +207,33 @@ def dae_free_decoder(dec):
 
 def dae_decoder_set_precision(ctx, dec, prec):
     _check(ctx, lib().dae_decoder_set_precision(dec, PREC[prec]))
+
+
+def dae_decoder_get_chain_plan(ctx, dec, n_hidden, direction):
+    """(split, rep) int arrays of the hidden layers for direction 0 (forward) or 1 (reverse)."""
+    split = np.zeros(n_hidden, np.int32)
+    rep = np.zeros(n_hidden, np.int32)
+    _check(ctx, lib().dae_decoder_get_chain_plan(dec, int(direction), split.ctypes.data,
+                                                 rep.ctypes.data))
+    return split, rep
+
+
+def dae_decoder_set_chain_plan(ctx, dec, direction, split=None, rep=None):
+    """Set a direction's plan (None: the built-in plan)."""
+    if split is None or rep is None:
+        _check(ctx, lib().dae_decoder_set_chain_plan(dec, int(direction), None, None))
+        return
+    split = np.ascontiguousarray(split, np.int32)
+    rep = np.ascontiguousarray(rep, np.int32)
+    _check(ctx, lib().dae_decoder_set_chain_plan(dec, int(direction), split.ctypes.data,
+                                                 rep.ctypes.data))
+
+
+def dae_decoder_autotune(ctx, dec, reps=20):
+    """Tune both chains' plans; returns (fwd ms before, after, rev ms before, after)."""
+    ms = np.zeros(4)
+    _check(ctx, lib().dae_decoder_autotune(dec, int(reps), ms.ctypes.data))
+    return tuple(float(x) for x in ms)
 
 
 def dae_load_mesh(ctx, X, tets, vmass, material="stvk", E=1e5, nu=0.4):

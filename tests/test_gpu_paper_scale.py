@@ -102,3 +102,54 @@ def test_paper_scale_rollout_frames(paper, prec, ratio):
     finally:
         g.close()
         dae.dae_destroy(ctx)
+
+
+def test_paper_scale_autotuned_plan(paper):
+    """The tile autotuner on the paper-scale decoder (BF16x3): the tuned plan keeps the
+    reduced system within the oracle tolerances and runs the Newton frames no slower than
+    the built-in plan (frames timed with CUDA events, the two plans interleaved)."""
+    import torch
+    import bench
+    from paper_2102_11026_gb300 import dae
+    wl, q0, ref = paper
+    d = wl.dec
+    n = wl.cub_tets.size
+    stream = torch.cuda.Stream()
+    ctx = dae.dae_create(0, stream.cuda_stream)
+    g = Gpu(wl, "bf16x3", ctx=ctx)
+    try:
+        nh = len(d.W) - 1
+        plans = {"built-in": [dae.dae_decoder_get_chain_plan(ctx, g.dec, nh, k) for k in (0, 1)]}
+        ms = dae.dae_decoder_autotune(ctx, g.dec, reps=10)
+        assert ms[1] <= ms[0] and ms[3] <= ms[2]
+        plans["tuned"] = [dae.dae_decoder_get_chain_plan(ctx, g.dec, nh, k) for k in (0, 1)]
+        rs = g.reduced(q0)
+        assert relerr(rs["phi"], ref["phi"]) <= 1e-3 and relerr(rs["A"], ref["A"]) <= 1e-3
+        dev = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+        cw = dev(bench.frame_weights(wl, 12, 2), torch.float32)
+        cub_t = dev(wl.cub_tets, torch.int32)
+        f_ext = dev(wl.f_ext, torch.float32)
+        opts = dae.dae_default_newton_opts()
+        times = {"built-in": [], "tuned": []}
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                for name, pl in plans.items():
+                    for k in (0, 1):
+                        dae.dae_decoder_set_chain_plan(ctx, g.dec, k, pl[k][0], pl[k][1])
+                    q = dev(wl.state.qbar, torch.float64)
+                    qd = dev(wl.state.qbar_dot, torch.float64)
+                    dae.dae_rollout(ctx, g.dec, g.mesh, cub_t, cw[:2 * n], 2, q, qd, wl.state.dt,
+                                    f_ext, opts)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    dae.dae_rollout(ctx, g.dec, g.mesh, cub_t, cw[2 * n:], 10, q, qd, wl.state.dt,
+                                    f_ext, opts, want_reports=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times[name].append(e0.elapsed_time(e1))
+        t_b, t_t = np.median(times["built-in"]), np.median(times["tuned"])
+        assert t_t <= 1.03 * t_b, (t_b, t_t, ms)
+    finally:
+        g.close()
+        dae.dae_destroy(ctx)
