@@ -348,6 +348,34 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
                                    double dt, const dae_newton_opts* opts,
                                    dae_newton_report* reports);
 
+/*
+ * One implicit-Euler Newton step of domains coupled at interfaces (deformation
+ * substructuring, Sec. 6, Fig. 1: the paper's cactus and puffer ball; the paper defers
+ * the coupling to Barbic & Zhao 2011).  The ties are read as penalty springs of
+ * stiffness k_c:
+ *   E_c = k_c/2 (sum_pairs |u_d[i] - u_e[j]|^2 + sum_anchors |u_d[i]|^2)
+ * where pair (d, i, e, j) says vertex i of domain d and vertex j of domain e coincide at
+ * rest, and anchor (d, i) holds vertex i of domain d at its rest position.  The unknown
+ * is all domains' latents; domain d's rows are its own Eq. 10 residual with the tie
+ * force -dE_c/du_d among its forces (so a^T H carries it), and the Newton matrix adds
+ * the tie Hessian: dt^2 k_c J_d[i]^T J_d[i] on the diagonal blocks and
+ * -dt^2 k_c J_d[i]^T J_e[j] off them.  One Newton control (tol, Armijo line search on the
+ * global |phi|^2, max_step, xtol from opts) for all domains; the step solves the block
+ * system over the forest of domains (pairs must join the domains into a forest: every
+ * connected component a tree) by block elimination from the leaves, in FP64.
+ *   systems   as in dae_newton_step_batched (tensor-core precision, one precision, each
+ *             decoder in one system, no linear subspace); q in/out per system
+ *   pairs     n_pairs x 4 ints (d, i, e, j), host array;  anchors  n_anchors x 2 ints (d, i)
+ *   rep       one report for the whole step (may be NULL); synchronizes
+ * u and J at the tie vertices come from the output layer's FP32 weights and input
+ * activations.  Errors: INVALID_ARG (indices, pairs within one domain), UNSUPPORTED (a
+ * cycle among the domains, FP32, a linear subspace), SINGULAR, INVERTED, NONFINITE, CUDA.
+ */
+dae_status dae_newton_step_coupled(dae_ctx* ctx, int n_sys, const dae_system* systems,
+                                   int n_pairs, const int* pairs, int n_anchors, const int* anchors,
+                                   double k_c, double dt, const dae_newton_opts* opts,
+                                   dae_newton_report* rep);
+
 /* ------------------------------------------------------- decoder training -- */
 
 /*

@@ -8,6 +8,10 @@
 #include <vector>
 
 #include <atomic>
+#include <functional>
+#include <map>
+#include <memory>
+#include <set>
 #include <cublas_v2.h>
 
 #include "dae_internal.h"
@@ -1367,6 +1371,140 @@ struct BatchKey {
     int n_cub, has_fext;
 };
 
+// Ties between the domains of one grouped step (dae_newton_step_coupled): the topology
+// on the host and its device arrays.
+struct Coupling {
+    int n_dom = 0, n_tv = 0, n_tot = 0, n_comp = 0;
+    std::vector<int> pairs, anchors;   // as given (cache key)
+    double kc = 0;
+    std::vector<int> off, ntv_dom, tv_dom, tv_vert, tv_slot, nb_off, nb, n_anch, dtv_off, dtv,
+        unk_dom, comp_off, order, parent, cp_off, cp;
+    char* dev = nullptr;               // one allocation: arguments and arrays
+    CoupledArgs* args = nullptr;       // device
+    CoupledState* cs = nullptr;        // device
+    ~Coupling() { if (dev) cudaFree(dev); }
+};
+
+// Tie vertices, neighbour lists, the domain forest (a pair joins a child domain to its
+// parent; the lowest domain of each connected component is its root) and its post-order.
+dae_status build_topology(dae_ctx* ctx, Coupling& c, const std::vector<int>& r,
+                          const std::vector<int>& n_vert, int n_pairs, const int* pairs,
+                          int n_anch, const int* anch) {
+    const int D = (int)r.size();
+    c.n_dom = D;
+    c.pairs.assign(pairs, pairs + 4 * (size_t)n_pairs);
+    c.anchors.assign(anch, anch + 2 * (size_t)n_anch);
+    c.off.assign(D + 1, 0);
+    for (int d = 0; d < D; ++d) c.off[d + 1] = c.off[d] + r[d];
+    c.n_tot = c.off[D];
+    c.unk_dom.resize(c.n_tot);
+    for (int d = 0; d < D; ++d)
+        for (int i = c.off[d]; i < c.off[d + 1]; ++i) c.unk_dom[i] = d;
+    std::map<std::pair<int, int>, int> tv;
+    auto tie = [&](int d, int v) -> int {
+        auto it = tv.find({d, v});
+        if (it != tv.end()) return it->second;
+        const int t = (int)c.tv_dom.size();
+        tv[{d, v}] = t;
+        c.tv_dom.push_back(d);
+        c.tv_vert.push_back(v);
+        return t;
+    };
+    auto bad_vertex = [&](int d, int v) { return d < 0 || d >= D || v < 0 || v >= n_vert[d]; };
+    std::vector<std::vector<int>> nbl;
+    std::vector<std::pair<int, int>> ptv(n_pairs);
+    for (int p = 0; p < n_pairs; ++p) {
+        const int d = pairs[4 * p], i = pairs[4 * p + 1], e = pairs[4 * p + 2], j = pairs[4 * p + 3];
+        if (bad_vertex(d, i) || bad_vertex(e, j))
+            return fail(ctx, DAE_ERR_INVALID_ARG, "tie pair %d: domain or vertex out of range", p);
+        if (d == e) return fail(ctx, DAE_ERR_INVALID_ARG, "tie pair %d joins a domain to itself", p);
+        ptv[p] = {tie(d, i), tie(e, j)};
+    }
+    std::vector<int> at(n_anch);
+    for (int a = 0; a < n_anch; ++a) {
+        if (bad_vertex(anch[2 * a], anch[2 * a + 1]))
+            return fail(ctx, DAE_ERR_INVALID_ARG, "anchor %d: domain or vertex out of range", a);
+        at[a] = tie(anch[2 * a], anch[2 * a + 1]);
+    }
+    c.n_tv = (int)c.tv_dom.size();
+    nbl.assign(c.n_tv, {});
+    for (auto& p : ptv) { nbl[p.first].push_back(p.second); nbl[p.second].push_back(p.first); }
+    c.n_anch.assign(c.n_tv, 0);
+    for (int t : at) c.n_anch[t] += 1;
+    c.nb_off.assign(c.n_tv + 1, 0);
+    c.nb.clear();
+    for (int t = 0; t < c.n_tv; ++t) {
+        c.nb.insert(c.nb.end(), nbl[t].begin(), nbl[t].end());
+        c.nb_off[t + 1] = (int)c.nb.size();
+    }
+    // each domain's tie vertices (slot = position in its list)
+    c.ntv_dom.assign(D, 0);
+    c.tv_slot.assign(c.n_tv, 0);
+    c.dtv_off.assign(D + 1, 0);
+    std::vector<std::vector<int>> dl(D);
+    for (int t = 0; t < c.n_tv; ++t) { c.tv_slot[t] = (int)dl[c.tv_dom[t]].size(); dl[c.tv_dom[t]].push_back(t); }
+    c.dtv.clear();
+    for (int d = 0; d < D; ++d) {
+        c.ntv_dom[d] = (int)dl[d].size();
+        c.dtv.insert(c.dtv.end(), dl[d].begin(), dl[d].end());
+        c.dtv_off[d + 1] = (int)c.dtv.size();
+    }
+    // the domain graph must be a forest
+    std::vector<int> uf(D);
+    for (int d = 0; d < D; ++d) uf[d] = d;
+    std::function<int(int)> find = [&](int x) { return uf[x] == x ? x : (uf[x] = find(uf[x])); };
+    std::set<std::pair<int, int>> edges;
+    for (auto& p : ptv) {
+        const int a = c.tv_dom[p.first], b = c.tv_dom[p.second];
+        edges.insert({std::min(a, b), std::max(a, b)});
+    }
+    std::vector<std::vector<int>> adj(D);
+    for (auto& e : edges) {
+        const int a = find(e.first), b = find(e.second);
+        if (a == b) return fail(ctx, DAE_ERR_UNSUPPORTED, "the ties' domain graph has a cycle (a forest is required)");
+        uf[a] = b;
+        adj[e.first].push_back(e.second);
+        adj[e.second].push_back(e.first);
+    }
+    // components: root = lowest domain; iterative DFS for parents and post-order
+    c.parent.assign(D, -2);
+    c.comp_off.assign(1, 0);
+    c.order.clear();
+    for (int root = 0; root < D; ++root) {
+        if (c.parent[root] != -2) continue;
+        c.parent[root] = -1;
+        std::vector<std::pair<int, size_t>> st{{root, 0}};
+        while (!st.empty()) {
+            auto& top = st.back();
+            const int d = top.first;
+            if (top.second < adj[d].size()) {
+                const int e = adj[d][top.second++];
+                if (c.parent[e] == -2) { c.parent[e] = d; st.push_back({e, 0}); }
+            } else {
+                c.order.push_back(d);
+                st.pop_back();
+            }
+        }
+        c.comp_off.push_back((int)c.order.size());
+    }
+    c.n_comp = (int)c.comp_off.size() - 1;
+    // the pairs of each child with its parent: (tie vertex in the child, in the parent)
+    std::vector<std::vector<int>> cpl(D);
+    for (auto& p : ptv) {
+        int a = p.first, b = p.second;
+        if (c.parent[c.tv_dom[a]] != c.tv_dom[b]) std::swap(a, b);
+        cpl[c.tv_dom[a]].push_back(a);
+        cpl[c.tv_dom[a]].push_back(b);
+    }
+    c.cp_off.assign(D + 1, 0);
+    c.cp.clear();
+    for (int d = 0; d < D; ++d) {
+        c.cp.insert(c.cp.end(), cpl[d].begin(), cpl[d].end());
+        c.cp_off[d + 1] = (int)(c.cp.size() / 2);
+    }
+    return DAE_OK;
+}
+
 struct BatchPlan {
     std::vector<BatchKey> key;
     double dt = 0;
@@ -1392,16 +1530,81 @@ struct BatchPlan {
     int max_elems = 0, max_cub = 0, max_K = 0, max_splits = 1, max_ld = 0, max_ent = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t staged = nullptr;   // host staging buffer free again
+    Coupling* cpl = nullptr;        // ties between the systems (dae_newton_step_coupled)
 };
 
 void free_batch(dae_ctx* ctx) {
-    BatchPlan* b = (BatchPlan*)ctx->batch;
-    if (!b) return;
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->dev) cudaFree(b->dev);
-    if (b->staged) cudaEventDestroy(b->staged);
-    delete b;
-    ctx->batch = nullptr;
+    for (void** slot : {&ctx->batch, &ctx->batch_coupled}) {
+        BatchPlan* b = (BatchPlan*)*slot;
+        if (!b) continue;
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->dev) cudaFree(b->dev);
+        if (b->staged) cudaEventDestroy(b->staged);
+        delete b->cpl;
+        delete b;
+        *slot = nullptr;
+    }
+}
+
+// Device copy of a coupling's topology and state, with the domains' records.
+dae_status upload_coupling(dae_ctx* ctx, Coupling& c, const std::vector<TieDom>& dom, double dt,
+                           double h, const dae_newton_opts& o) {
+    if (c.dev) cudaFree(c.dev);
+    c.dev = nullptr;
+    const int D = c.n_dom;
+    size_t off = 0;
+    auto place = [&](size_t bytes) { const size_t q = off; off += round_up(std::max(bytes, (size_t)16), 256); return q; };
+    auto ints = [&](const std::vector<int>& v) { return place(v.size() * sizeof(int)); };
+    const size_t o_args = place(sizeof(CoupledArgs)), o_cs = place(sizeof(CoupledState));
+    const size_t o_dom = place(D * sizeof(TieDom));
+    const size_t o_unk = ints(c.unk_dom), o_dtvo = ints(c.dtv_off), o_dtv = ints(c.dtv);
+    const size_t o_tvd = ints(c.tv_dom), o_tvv = ints(c.tv_vert), o_tvs = ints(c.tv_slot);
+    const size_t o_nbo = ints(c.nb_off), o_nb = ints(c.nb), o_na = ints(c.n_anch);
+    const size_t o_co = ints(c.comp_off), o_ord = ints(c.order), o_par = ints(c.parent);
+    const size_t o_cpo = ints(c.cp_off), o_cp = ints(c.cp);
+    const size_t o_uj = place((size_t)c.n_tv * 3 * (1 + kMaxR) * sizeof(float));
+    const size_t o_g = place((size_t)c.n_tv * 3 * sizeof(double));
+    const size_t o_q = place((size_t)4 * c.n_tot * sizeof(double));
+    const size_t o_S = place((size_t)D * kMaxR * kMaxR * sizeof(double));
+    const size_t o_X = place((size_t)D * kMaxR * kMaxR * sizeof(double));
+    const size_t o_y = place((size_t)D * kMaxR * sizeof(double));
+    CU(ctx, cudaMalloc(&c.dev, off));
+    CU(ctx, cudaMemset(c.dev, 0, off));
+    char* B = c.dev;
+    auto put = [&](size_t o_, const std::vector<int>& v) {
+        return v.empty() ? cudaSuccess : cudaMemcpy(B + o_, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+    };
+    CoupledArgs a;
+    memset(&a, 0, sizeof a);
+    a.n_dom = D; a.n_tv = c.n_tv; a.n_tot = c.n_tot;
+    a.dom = (const TieDom*)(B + o_dom);
+    a.unk_dom = (const int*)(B + o_unk); a.dtv_off = (const int*)(B + o_dtvo); a.dtv = (const int*)(B + o_dtv);
+    a.tv_dom = (const int*)(B + o_tvd); a.tv_vert = (const int*)(B + o_tvv); a.tv_slot = (const int*)(B + o_tvs);
+    a.nb_off = (const int*)(B + o_nbo); a.nb = (const int*)(B + o_nb); a.n_anch = (const int*)(B + o_na);
+    a.uJ = (float*)(B + o_uj); a.g = (double*)(B + o_g);
+    a.kc = c.kc; a.dt = dt; a.h = h;
+    a.cs = (CoupledState*)(B + o_cs);
+    double* q = (double*)(B + o_q);
+    a.q_acc = q; a.q_trial = q + c.n_tot; a.delta = q + 2 * c.n_tot; a.phi = q + 3 * c.n_tot;
+    a.tol = o.tol; a.c_armijo = o.c_armijo; a.max_step = o.max_step; a.xtol = o.xtol;
+    a.max_iter = o.max_iter; a.max_halvings = o.max_halvings; a.max_evals = o.max_evals;
+    a.n_comp = c.n_comp; a.comp_off = (const int*)(B + o_co); a.order = (const int*)(B + o_ord);
+    a.parent = (const int*)(B + o_par); a.cp_off = (const int*)(B + o_cpo); a.cp = (const int*)(B + o_cp);
+    a.S = (double*)(B + o_S); a.X = (double*)(B + o_X); a.y = (double*)(B + o_y);
+    cudaError_t e = cudaMemcpy(B + o_args, &a, sizeof a, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B + o_dom, dom.data(), D * sizeof(TieDom), cudaMemcpyHostToDevice);
+    for (auto pr : {std::make_pair(o_unk, &c.unk_dom), std::make_pair(o_dtvo, &c.dtv_off),
+                    std::make_pair(o_dtv, &c.dtv), std::make_pair(o_tvd, &c.tv_dom),
+                    std::make_pair(o_tvv, &c.tv_vert), std::make_pair(o_tvs, &c.tv_slot),
+                    std::make_pair(o_nbo, &c.nb_off), std::make_pair(o_nb, &c.nb),
+                    std::make_pair(o_na, &c.n_anch), std::make_pair(o_co, &c.comp_off),
+                    std::make_pair(o_ord, &c.order), std::make_pair(o_par, &c.parent),
+                    std::make_pair(o_cpo, &c.cp_off), std::make_pair(o_cp, &c.cp)})
+        if (e == cudaSuccess) e = put(pr.first, *pr.second);
+    if (e != cudaSuccess) return fail(ctx, DAE_ERR_CUDA, "coupling upload: %s", cudaGetErrorString(e));
+    c.args = (CoupledArgs*)(B + o_args);
+    c.cs = a.cs;
+    return DAE_OK;
 }
 
 dae_status ensure_pinned(dae_ctx* ctx, size_t bytes) {
@@ -1518,11 +1721,17 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         Phase p(ctx, DAE_PHASE_CUBATURE, 1);
         launch_cubature_batched(s, b->cub, n, b->max_cub);
     }
+    if (b->cpl) {
+        // u and J at the tie vertices (from the output layer's input activations)
+        Phase p(ctx, DAE_PHASE_CUBATURE, 1);
+        launch_tie_uj(s, b->cpl->args, b->cpl->n_tv);
+    }
     {
         // phi and the decisions: systems whose iterate starts no new Newton step skip the
-        // reverse pass below
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, 3);
+        // reverse pass below (coupled: every domain's phi, then one global decision)
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, b->cpl ? 4 : 3);
         launch_decide_batched(s, b->cs, b->ds, b->ctl, n, b->max_ent);
+        if (b->cpl) launch_coupled_decide(s, b->cpl->args);
     }
     {
         Phase p(ctx, DAE_PHASE_WTA, 2);
@@ -1542,8 +1751,13 @@ dae_status enqueue_batch_eval(dae_ctx* ctx, const BatchPlan* b, dae_prec prec,
         if (!launch_chain(s, cl, prec)) return fail(ctx, DAE_ERR_CUDA, "grouped chain launch failed");
     }
     {
-        Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
+        Phase p(ctx, DAE_PHASE_ASSEMBLE, b->cpl ? 4 : 2);
         launch_control_batched(s, b->ctl, n);
+        if (b->cpl) {
+            // the global Newton step over the domain forest, then the next trial
+            launch_coupled_solve(s, b->cpl->args, b->cpl->n_comp);
+            launch_coupled_update(s, b->cpl->args);
+        }
         launch_batch_cond(s, b->frame, n, hc, flag);
     }
     CU(ctx, cudaGetLastError());
@@ -1557,6 +1771,8 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
                        const std::vector<int>& hasf, const std::vector<int>& pred, double dt,
                        const dae_newton_opts& opts) {
     const int n = (int)ds.size();
+    Coupling* cpl = b->cpl;
+    std::vector<TieDom> tdom(cpl ? n : 0);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     if (b->dev) cudaFree(b->dev);
@@ -1627,7 +1843,9 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         const bool gram = w.G && w.G_mesh == m->id;
         WtaArgs& wa = wta[i];
         memset(&wa, 0, sizeof wa);
-        wa.fe_w = w.fe_w; wa.fe_dof = w.fe_dof; wa.n_pairs = 12 * ncub[i]; wa.dt2 = dt * dt;
+        wa.fe_w = w.fe_w; wa.fe_dof = w.fe_dof; wa.dt2 = dt * dt;
+        // coupled: the tie forces of the domain's tie vertices follow the cubature pairs
+        wa.n_pairs = 12 * ncub[i] + (cpl ? 3 * cpl->ntv_dom[i] : 0);
         wa.Wp = top.W; wa.ldp = top.ld; wa.K = K;
         memset(&xy[i], 0, sizeof xy[i]);
         if (gout) {
@@ -1678,11 +1896,19 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = ncub[i];
         aa.cub_stride = w.cub_stride; aa.cub_parts = ca.n_parts;
         aa.bwd_part = w.bwd_part[1]; aa.bwd_split = 1;
-        aa.red = w.red; aa.ns = w.ns; aa.control = 1;
+        aa.red = w.red; aa.ns = w.ns; aa.control = cpl ? 0 : 1;
         aa.tol = opts.tol; aa.c_armijo = opts.c_armijo; aa.max_iter = opts.max_iter;
         aa.max_step = opts.max_step; aa.xtol = opts.xtol;
         aa.max_halvings = opts.max_halvings; aa.max_evals = opts.max_evals;
         aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+        if (cpl) {
+            // coupled: each domain's phi and A only; the global decision reads the flags
+            aa.eval_flag = nullptr;
+            aa.status = nullptr;
+            const Layer& tl = d->layers[L - 1];
+            tdom[i] = TieDom{w.X[(L - 1) & 1], tl.ld, tl.W, tl.ld, tl.b, tl.n_in, r, cpl->off[i], w.ns,
+                             w.red, w.fe_w, w.fe_dof, 12 * ncub[i], w.eval_flag};
+        }
         assemble_parts(aa, &cs[4 * i], dsum[i], ctl[i]);
         for (int k = 0; k < 4; ++k) b->max_ent = std::max(b->max_ent, cs[4 * i + k].n_ent);
     }
@@ -1739,6 +1965,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
     CU(ctx, up(b->gather, gather.data(), n * sizeof(GatherArgs)));
     CU(ctx, up(b->wnet, wnet.data(), n * sizeof(WnetArgs)));
     CU(ctx, up(b->jobs, jobs.data(), jobs.size() * sizeof(ChainJob)));
+    if (cpl) TRY(upload_coupling(ctx, *cpl, tdom, dt, h, opts));
     CU(ctx, up(b->stage_off, stage_off.data(), stage_off.size() * sizeof(int)));
     CU(ctx, cudaMemset(b->gb, 0, sizeof(GridBar)));
     b->epoch = ctx->timeout_epoch;
@@ -1761,6 +1988,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         if (cudaGraphConditionalHandleCreate(&hc, g, 0, 0) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
         if (cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
         launch_frame_begin_batched(s, b->frame, n, hc, 1);
+        if (cpl) launch_coupled_begin(s, cpl->args);
         if (cudaStreamEndCapture(s, &g) != cudaSuccess) { st = DAE_ERR_CUDA; break; }
         cudaGraphNode_t a, loop;
         cudaGraph_t body;
@@ -2567,8 +2795,16 @@ dae_status dae_newton_step(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mes
     return DAE_OK;
 }
 
-dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sys, double dt,
-                                   const dae_newton_opts* opts_in, dae_newton_report* reps) {
+// Ties of a coupled step as given through the C ABI.
+struct TieSpec {
+    int n_pairs; const int* pairs; int n_anch; const int* anch; double kc;
+};
+
+// The grouped Newton step of n_sys systems: independent (spec == nullptr, per-system
+// reports in reps) or coupled by ties (one global report in grep).
+static dae_status grouped_step(dae_ctx* ctx, int n_sys, const dae_system* sys, double dt,
+                               const dae_newton_opts* opts_in, dae_newton_report* reps,
+                               const TieSpec* spec, dae_newton_report* grep) {
     if (!ctx) return DAE_ERR_INVALID_ARG;
     if (n_sys < 0 || (n_sys > 0 && !sys)) return fail(ctx, DAE_ERR_INVALID_ARG, "bad system list");
     if (n_sys == 0) return DAE_OK;
@@ -2604,9 +2840,22 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
     std::sort(seen.begin(), seen.end());
     if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
         return fail(ctx, DAE_ERR_INVALID_ARG, "a decoder appears in two systems (its workspace is per decoder)");
+    std::unique_ptr<Coupling> topo;
+    if (spec) {
+        std::vector<int> rr(n_sys), nv(n_sys);
+        for (int i = 0; i < n_sys; ++i) {
+            if (ds[i]->np > 0) return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: a linear subspace in a coupled step", i);
+            rr[i] = ds[i]->r;
+            nv[i] = ms[i]->n_vert;
+        }
+        topo.reset(new Coupling());
+        TRY(build_topology(ctx, *topo, rr, nv, spec->n_pairs, spec->pairs, spec->n_anch, spec->anch));
+        topo->kc = spec->kc;
+    }
     // per-system set-up that is cached across calls
     for (int i = 0; i < n_sys; ++i) {
-        TRY(ensure_cubature(ds[i], ncub[i], ncub[i]));
+        // (coupled: room for the tie forces after the cubature pairs of W_L^T a)
+        TRY(ensure_cubature(ds[i], ncub[i] + (topo ? topo->ntv_dom[i] : 0), ncub[i]));
         Workspace& wi = ds[i]->ws;
         if (pred[i] && wi.wn_cap < ncub[i]) {
             dfree(wi.wn_w);
@@ -2620,10 +2869,11 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
         if (ds[i]->np > 0 && !gram_out(ds[i], ms[i]))
             return fail(ctx, DAE_ERR_UNSUPPORTED, "system %d: the linear subspace needs the Gram form", i);
     }
-    BatchPlan* b = (BatchPlan*)ctx->batch;
+    void*& slot = spec ? ctx->batch_coupled : ctx->batch;
+    BatchPlan* b = (BatchPlan*)slot;
     if (!b) {
         b = new BatchPlan();
-        ctx->batch = b;
+        slot = b;
         CU(ctx, cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
     }
     for (int i = 0; i < n_sys; ++i)
@@ -2635,10 +2885,17 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
                           gram_out(ds[i], ms[i]) ? (w.Gs32 ? (const void*)w.Gs32 : (const void*)w.Gsh) : nullptr,
                           pred[i] ? (const void*)w.wn_w : nullptr, ncub[i], hasf[i]};
     }
-    const bool same = b->gexec && b->n == n_sys && b->dt == dt && b->prec == (int)ds[0]->prec &&
-                      memcmp(&b->opts, &opts, sizeof opts) == 0 &&
-                      memcmp(b->key.data(), key.data(), n_sys * sizeof(BatchKey)) == 0;
+    bool same = b->gexec && b->n == n_sys && b->dt == dt && b->prec == (int)ds[0]->prec &&
+                memcmp(&b->opts, &opts, sizeof opts) == 0 &&
+                memcmp(b->key.data(), key.data(), n_sys * sizeof(BatchKey)) == 0;
+    if (spec)
+        same = same && b->cpl && b->cpl->kc == topo->kc && b->cpl->pairs == topo->pairs &&
+               b->cpl->anchors == topo->anchors;
     if (!same) {
+        if (spec) {
+            delete b->cpl;
+            b->cpl = topo.release();
+        }
         TRY(build_batch(ctx, b, ds, ms, ncub, hasf, pred, dt, opts));
         b->key = key;
         b->n = n_sys;
@@ -2717,8 +2974,9 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
     if (ctx->prof_on) {
         // explicit launches (timed phases): the host reads the any-running flag after
         // every evaluation
-        ctx->launches += 2;
+        ctx->launches += b->cpl ? 3 : 2;
         launch_frame_begin_batched(ctx->stream, b->frame, n_sys, 0, 0);
+        if (b->cpl) launch_coupled_begin(ctx->stream, b->cpl->args);
         for (int e = 0; e < opts.max_evals; ++e) {
             TRY(enqueue_batch_eval(ctx, b, ds[0]->prec, 0, b->flag));
             int run = 0;
@@ -2759,7 +3017,43 @@ dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sy
             return fail(ctx, (dae_status)hs[worst].status, "system %d failed: %s", worst,
                         dae_status_string((dae_status)hs[worst].status));
     }
+    if (grep) {
+        CoupledState cs;
+        CU(ctx, cudaMemcpyAsync(&cs, b->cpl->cs, sizeof cs, cudaMemcpyDeviceToHost, ctx->stream));
+        TRY(check_device_status(ctx));
+        grep->iters = cs.iters;
+        grep->evals = cs.evals;
+        grep->converged = cs.converged;
+        grep->status = cs.status;
+        grep->phi_norm0 = cs.phi_norm0;
+        grep->phi_norm = std::sqrt(cs.merit_acc);
+        grep->energy = cs.energy;
+        grep->alpha = cs.alpha;
+        grep->full_evals = cs.nfull;
+        if (cs.status) return fail(ctx, (dae_status)cs.status, "coupled step failed: %s",
+                                   dae_status_string((dae_status)cs.status));
+    }
     return DAE_OK;
+}
+
+dae_status dae_newton_step_batched(dae_ctx* ctx, int n_sys, const dae_system* sys, double dt,
+                                   const dae_newton_opts* opts, dae_newton_report* reps) {
+    return grouped_step(ctx, n_sys, sys, dt, opts, reps, nullptr, nullptr);
+}
+
+dae_status dae_newton_step_coupled(dae_ctx* ctx, int n_sys, const dae_system* sys, int n_pairs,
+                                   const int* pairs, int n_anchors, const int* anchors, double k_c,
+                                   double dt, const dae_newton_opts* opts, dae_newton_report* rep) {
+    if (!ctx) return DAE_ERR_INVALID_ARG;
+    if (n_pairs < 0 || n_anchors < 0 || (n_pairs > 0 && !pairs) || (n_anchors > 0 && !anchors))
+        return fail(ctx, DAE_ERR_INVALID_ARG, "tie pairs / anchors missing");
+    if ((n_pairs > 0 && on_device(pairs)) || (n_anchors > 0 && on_device(anchors)))
+        return fail(ctx, DAE_ERR_INVALID_ARG, "tie pairs and anchors must be host arrays");
+    if (!(k_c >= 0)) return fail(ctx, DAE_ERR_INVALID_ARG, "k_c must be >= 0");
+    if (n_sys < 1) return fail(ctx, DAE_ERR_INVALID_ARG, "no systems");
+    const TieSpec spec{n_pairs, pairs, n_anchors, anchors, k_c};
+    dae_newton_report tmp;
+    return grouped_step(ctx, n_sys, sys, dt, opts, nullptr, &spec, rep ? rep : &tmp);
 }
 
 dae_status dae_last_report(dae_ctx* ctx, dae_newton_report* rep) {

@@ -245,6 +245,7 @@ struct dae_ctx {
     struct Rec { int phase; cudaEvent_t a, b; };
     std::vector<Rec> recs;
     void* batch = nullptr;               // cached plan of dae_newton_step_batched
+    void* batch_coupled = nullptr;       // cached plan of dae_newton_step_coupled
 };
 
 struct dae_decoder {
@@ -547,6 +548,52 @@ struct LinArgs {
 void launch_linear(cudaStream_t s, const LinArgs& a, int n_blocks);
 // grouped form (z = system; systems without a linear subspace have np = 0)
 void launch_linear_batched(cudaStream_t s, const LinArgs* d_args, int n_sys, int max_blocks);
+// ------------------------------------------------------ coupled domains --
+// Domains of a substructured body tied at interface vertices (penalty springs of
+// stiffness k_c between vertices that coincide at rest, and anchors holding a vertex at
+// rest; deformation substructuring, Sec. 6), stepped as one Newton system over all
+// domains' latents.  A tie vertex t is one (domain, vertex) that takes part in a tie.
+struct TieDom {
+    const float* X; int ldx;        // FP32 input activations of the output layer [Cp][ldx]
+    const float* W; int ld;         // output layer FP32 weights [m_pad][ld]
+    const float* b;                 // output layer bias
+    int K, r, off;                  // hidden width, latent size, first global unknown
+    NewtonState* ns;                // the domain's Newton state (q slices, flags)
+    const double* red;              // the domain's phi | A | energy buffer
+    float* fe_w; int* fe_dof;       // reverse-pass seed pairs; the tie forces go to [pair0, ...)
+    int pair0;                      // 12 n_cub
+    int* eval_flag;                 // cubature flag of the domain's evaluation
+};
+struct CoupledState {
+    double merit_acc, phi_norm0, alpha, energy, coupling_energy;
+    int halvings, iters, evals, done, converged, status, nfull, skip;
+};
+struct CoupledArgs {
+    int n_dom, n_tv, n_tot;
+    const TieDom* dom;
+    const int* unk_dom;                    // domain of global unknown k
+    const int* dtv_off; const int* dtv;    // CSR: tie vertices of domain d
+    const int* tv_dom; const int* tv_vert; const int* tv_slot;   // per tie vertex
+    const int* nb_off; const int* nb;      // CSR: tie vertices paired with tie vertex t
+    const int* n_anch;                     // anchors at tie vertex t
+    float* uJ;                             // [n_tv][3][1 + kMaxR]: u and J at the 3 DOFs
+    double* g;                             // [n_tv][3] tie force dE_c/du
+    double kc, dt, h;
+    CoupledState* cs;
+    double* q_acc; double* q_trial; double* delta; double* phi;   // [n_tot]
+    double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
+    // block solve over the domain forest: components, domains in post-order (children
+    // before parents), parents (-1: a component's root), the pairs of a child with its
+    // parent (tie vertex of the child, of the parent)
+    int n_comp; const int* comp_off; const int* order; const int* parent;
+    const int* cp_off; const int* cp;      // CSR over child domains: 2 ints per pair
+    double* S; double* X; double* y; int* piv;   // per domain [32 * 32], [32 * 32], [32], [32]
+};
+void launch_tie_uj(cudaStream_t s, const CoupledArgs* d_args, int n_tv);
+void launch_coupled_decide(cudaStream_t s, const CoupledArgs* d_args);
+void launch_coupled_solve(cudaStream_t s, const CoupledArgs* d_args, int n_comp);
+void launch_coupled_update(cudaStream_t s, const CoupledArgs* d_args);
+void launch_coupled_begin(cudaStream_t s, const CoupledArgs* d_args);
 // copy[i]: n bytes from src to dst (device memory), one block per copy
 struct CopyDesc { const void* src; void* dst; unsigned long long n; };
 void launch_copy_batch(cudaStream_t s, const CopyDesc* d, int n);

@@ -85,6 +85,8 @@ SIGNATURES = {
     "dae_predict_weights": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
     "dae_newton_step_batched": ([_vp, _i, ctypes.POINTER(dae_system), _d,
                                  ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
+    "dae_newton_step_coupled": ([_vp, _i, ctypes.POINTER(dae_system), _i, _vp, _i, _vp, _d, _d,
+                                 ctypes.POINTER(dae_newton_opts), ctypes.POINTER(dae_newton_report)], _i),
     "dae_reduce_rows_noalloc": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp], _i),
     "dae_profile_enable": ([_vp, ctypes.c_uint], _i),
     "dae_profile_read": ([_vp, _vp, _vp], _i),
@@ -300,6 +302,34 @@ def dae_newton_step_batched(ctx, systems, dt, opts=None, want_reports=True):
         ctx, n, arr, float(dt), ctypes.byref(opts) if opts is not None else None,
         ctypes.cast(reps, ctypes.POINTER(dae_newton_report)) if reps is not None else None))
     return list(reps)[:n] if reps is not None else None
+
+
+def _system_array(systems):
+    n = len(systems)
+    arr = (dae_system * max(n, 1))()
+    for i, y in enumerate(systems):
+        ct = y.get("cub_tets")
+        nc = int(ct.shape[0]) if ct is not None else 0
+        arr[i] = dae_system(y["dec"], y["mesh"], nc, _ptr(ct, np.int32),
+                            _ptr(y.get("cub_w"), np.float32, nc), _ptr(y["q"], np.float64),
+                            _ptr(y["qbar"], np.float64), _ptr(y["qbar_dot"], np.float64),
+                            _ptr(y.get("f_ext"), np.float32))
+    return arr
+
+
+def dae_newton_step_coupled(ctx, systems, pairs, anchors, k_c, dt, opts=None):
+    """Coupled step of the systems (dicts as for dae_newton_step_batched) tied by pairs
+    ((P, 4) ints d, i, e, j) and anchors ((Q, 2) ints d, i) of stiffness k_c; q is updated
+    in place; returns the step's report."""
+    arr = _system_array(systems)
+    pr = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 4))
+    an = np.ascontiguousarray(np.asarray(anchors, np.int32).reshape(-1, 2))
+    rep = dae_newton_report()
+    _check(ctx, lib().dae_newton_step_coupled(
+        ctx, len(systems), arr, int(pr.shape[0]), pr.ctypes.data if pr.size else None,
+        int(an.shape[0]), an.ctypes.data if an.size else None, float(k_c), float(dt),
+        ctypes.byref(opts) if opts is not None else None, ctypes.byref(rep)))
+    return rep
 
 
 def dae_decoder_attach_linear(ctx, dec, U):
