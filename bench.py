@@ -635,6 +635,9 @@ def run_train(args):
     poses = torch.as_tensor(np.concatenate(poses), device="cuda")
     Bt = 256
     tr = dae.dae_trainer_create(ctx, d.widths, d.act, max_batch=Bt)
+    # the training GEMMs in split BF16x3 (tensor cores) or FP32 (CUDA cores)
+    tprec = "fp32" if args.prec == "fp32" else "bf16x3"
+    dae.dae_trainer_set_precision(tr, tprec)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     teacher = []
     for w, x in zip(d.W, d.b):
@@ -689,6 +692,18 @@ def run_train(args):
     flops = train_flops(d.widths, Bt)
     peaks, src = load_peaks()
     tf = flops / (ms / 1e3) / 1e12
+    if tprec == "fp32":
+        # FP32 FFMA on the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flops x the SM clock
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": alu, "unit": "TFLOP/s", "frac": tf / alu,
+                "traffic": None,
+                "note": "peak derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x %.0f MHz" % sm_mhz}
+    else:
+        roof = {"bound": "tensor", "achieved": tf * 3, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": tf * 3 / peaks["bf16_tflops"], "traffic": None,
+                "note": "achieved counts the three BF16 MMAs of each split-BF16x3 product; "
+                        "peak: %s bf16 burst" % src}
     dae.dae_trainer_free(tr)
     dae.dae_destroy(ctx)
     if rank != 0:
@@ -696,16 +711,14 @@ def run_train(args):
     print(json.dumps({
         "metric": "decoder backward-pass TFLOP/s", "value": tf, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if tprec == "fp32" else "bf16x3",
         "data": "synthetic",
         "config": {"workload": "small decoder 5-64-256-1024-3000 tanh: backward of u and J w.r.t. "
                                "latents, weights and biases, batch 256 (1536 columns)",
                    "poses": "4096 from 64 rollouts x 64 frames of the small workload",
                    "gflop_per_backward": flops / 1e9},
-        "roofline": {"bound": "tensor", "achieved": tf * 3, "peak": peaks["bf16_tflops"],
-                     "unit": "TFLOP/s", "frac": tf * 3 / peaks["bf16_tflops"], "traffic": None,
-                     "note": "achieved counts the three BF16 MMAs of each split-BF16x3 product; "
-                             "peak: %s bf16 burst" % src},
+        "roofline": roof,
         "fit": {"steps": n_steps, "batch": Bt, "loss_first": losses[0], "loss_last": losses[-1],
                 "ms_per_adam_step": fit_ms / n_steps},
         "gpu_launches": int(launches),

@@ -403,6 +403,11 @@ typedef struct dae_trainer dae_trainer;
 dae_status dae_trainer_create(dae_ctx* ctx, int n_layers, const int* widths, dae_act act,
                               int max_batch, dae_trainer** out);
 dae_status dae_trainer_free(dae_trainer* t);
+/* GEMM arithmetic of the training pass: DAE_BF16X3 (default; tcgen05 tensor cores,
+ * three BF16 products per split operand pair, FP32 accumulation) or DAE_FP32 (FFMA on
+ * the CUDA cores from FP32 operands, FP32 accumulation).  Synchronizes; errors:
+ * UNSUPPORTED (another precision), OOM. */
+dae_status dae_trainer_set_precision(dae_trainer* t, dae_prec prec);
 dae_status dae_train_forward(dae_trainer* t, const float* const* W, const float* const* b, int B,
                              const double* q, float* uJ);
 dae_status dae_train_backward(dae_trainer* t, const float* const* W, const float* const* b, int B,

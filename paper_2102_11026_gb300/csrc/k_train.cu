@@ -168,6 +168,14 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfl
     lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// One element of an operand: FP32 (FP32 form) or split BF16 hi / lo.
+__device__ __forceinline__ void op_store_c(const Operand& P, size_t i, float v) {
+    if (P.cf) P.cf[i] = v; else split_store(v, P.ch, P.cl, i);
+}
+__device__ __forceinline__ void op_store_n(const Operand& P, size_t i, float v) {
+    if (P.nf) P.nf[i] = v; else split_store(v, P.nh, P.nl, i);
+}
+
 // Writes a 32 (k) x 32 (s) tile of comp's columns in both layouts: planes [c][k]
 // (ldc) and rows [k][c] (ldn), through a shared transpose so both stores coalesce.
 // v[ty][tx] holds neuron k0 + tx, sample s0 + ty.
@@ -176,11 +184,11 @@ __device__ __forceinline__ void store_both(const float (*v)[33], int k0, int s0,
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
     for (int yy = ty; yy < 32; yy += 8) {
         const int s = s0 + yy, k = k0 + tx;
-        if (s < nb && k < n) split_store(v[yy][tx], P.ch, P.cl, (size_t)(comp * B + s) * P.ldc + k);
+        if (s < nb && k < n) op_store_c(P, (size_t)(comp * B + s) * P.ldc + k, v[yy][tx]);
     }
     for (int yy = ty; yy < 32; yy += 8) {
         const int k = k0 + yy, s = s0 + tx;
-        if (s < nb && k < n) split_store(v[tx][yy], P.nh, P.nl, (size_t)k * P.ldn + comp * B + s);
+        if (s < nb && k < n) op_store_n(P, (size_t)k * P.ldn + comp * B + s, v[tx][yy]);
     }
 }
 
@@ -193,8 +201,8 @@ __global__ void k_train_seed(const double* q, int B, int r, Operand X) {
     if (k >= r || c >= B * (1 + r)) return;
     const int comp = c / B, s = c % B;
     const float v = comp == 0 ? (float)q[(size_t)s * r + k] : (comp - 1 == k ? 1.f : 0.f);
-    split_store(v, X.ch, X.cl, (size_t)c * X.ldc + k);
-    split_store(v, X.nh, X.nl, (size_t)k * X.ldn + c);
+    op_store_c(X, (size_t)c * X.ldc + k, v);
+    op_store_n(X, (size_t)k * X.ldn + c, v);
 }
 
 // ------------------------------------------------------------ activation --
@@ -325,6 +333,90 @@ __global__ void k_train_weights(const float* W, int n_out, int n_in, __nv_bfloat
         const int k = k0 + yy, i = i0 + tx;
         if (i < n_out && k < n_in) split_store(t[tx][yy], th, tl, (size_t)k * ldT + i);
     }
+}
+
+// ------------------------------------------------------------ FP32 form --
+// D[M][N] = A[M][K] B[N][K]^T in FP32 on the CUDA cores: a 64 x 64 output tile per CTA,
+// 256 threads with 4 x 4 outputs each, K in blocks of 32 staged through shared memory
+// as [k][row] (row stride 65: the stores of a warp hit distinct banks).  Rows up to the
+// tile edge and K up to nk x 64 lie inside the padded operands (zero padding).
+__global__ void __launch_bounds__(256) k_gemm_f32(const GemmArgs G) {
+    __shared__ float As[32][65], Bs[32][65];
+    const int t = threadIdx.x;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int tm = t >> 4, tn = t & 15;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int K = G.nk * 64;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int e = t; e < 64 * 32; e += 256) {
+            const int row = e >> 5, kk = e & 31;
+            As[kk][row] = G.a32[(size_t)(m0 + row) * G.lda + k0 + kk];
+            Bs[kk][row] = G.b32[(size_t)(n0 + row) * G.ldb + k0 + kk];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = As[kk][tm + 16 * i]; b[i] = Bs[kk][tn + 16 * i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float* __restrict__ out = G.out;
+    const size_t ldo = G.ldo;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tm + 16 * i;
+        if (m >= G.M) continue;
+        const float bv = (G.bias && G.out_mode == 1) ? G.bias[m] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tn + 16 * j;
+            if (n >= G.N) continue;
+            if (G.out_mode == 1) out[(size_t)n * ldo + m] = acc[i][j] + (n < G.bias_cols ? bv : 0.f);
+            else out[(size_t)m * ldo + n] = acc[i][j];
+        }
+    }
+}
+
+// Padded FP32 copies of W ([m_pad][ld]) and of W^T ([n_pad][ldT]); the padding stays
+// zero from the allocation.
+__global__ void k_train_weights_f32(const float* W, int n_out, int n_in, float* w, int ld, float* wt,
+                                    int ldT) {
+    __shared__ float tt[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int i = i0 + yy, k = k0 + tx;
+        const float v = (i < n_out && k < n_in) ? W[(size_t)i * n_in + k] : 0.f;
+        tt[yy][tx] = v;
+        if (i < n_out && k < n_in) w[(size_t)i * ld + k] = v;
+    }
+    if (wt == nullptr) return;   // uniform
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int k = k0 + yy, i = i0 + tx;
+        if (i < n_out && k < n_in) wt[(size_t)k * ldT + i] = tt[tx][yy];
+    }
+}
+
+bool launch_gemm_f32(cudaStream_t s, const GemmArgs& g) {
+    k_gemm_f32<<<dim3((g.M + 63) / 64, (g.N + 63) / 64), 256, 0, s>>>(g);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+void launch_train_weights_f32(cudaStream_t s, const float* W, int n_out, int n_in, float* w, int ld,
+                              float* wt, int ldT) {
+    k_train_weights_f32<<<dim3((n_in + 31) / 32, (n_out + 31) / 32), 256, 0, s>>>(W, n_out, n_in, w, ld,
+                                                                                  wt, ldT);
 }
 
 // ----------------------------------------------------------------- launches --

@@ -16,8 +16,11 @@ struct dae_trainer {
     struct TL {
         int n_in, n_out, ld, m_pad, ldT, mT_pad;
         __nv_bfloat16 *wh = nullptr, *wl = nullptr, *wth = nullptr, *wtl = nullptr;
+        float *wf = nullptr, *wtf = nullptr;       // FP32 form: padded W and W^T
         CUtensorMap tmW[2], tmWT[2];
     };
+    dae_prec prec = DAE_BF16X3;   // GEMM arithmetic: split BF16x3 (tensor cores) or FP32
+    float* opf[3][2] = {};        // FP32 operand arrays (planes, rows) of X[0], X[1], Zb
     std::vector<TL> layers;
     Operand X[2] = {};            // activations of a layer boundary (ping-pong)
     Operand Zb = {};              // cotangent of a layer's pre-activation
@@ -86,21 +89,25 @@ void free_operand(Operand& P) {
     P = Operand{};
 }
 
-GemmArgs gemm(const CUtensorMap* a, const CUtensorMap* b, float* out, int ldo, int mode, int M, int N,
-              int nk, const float* bias, int bias_cols, int* status) {
+// D = A B^T with A, B given as tensor maps (split BF16x3) and as FP32 arrays (FP32 form).
+GemmArgs gemm(const CUtensorMap* a, const float* a32, int lda, const CUtensorMap* b, const float* b32,
+              int ldb, float* out, int ldo, int mode, int M, int N, int nk, const float* bias,
+              int bias_cols, int* status) {
     GemmArgs g;
     memset(&g, 0, sizeof g);
     g.tm[0] = a[0]; g.tm[1] = a[1]; g.tm[2] = b[0]; g.tm[3] = b[1];
     g.out = out; g.ldo = ldo; g.out_mode = mode; g.M = M; g.N = N; g.nk = nk;
     g.bias = bias; g.bias_cols = bias_cols; g.status = status;
+    g.a32 = a32; g.lda = lda; g.b32 = b32; g.ldb = ldb;
     return g;
 }
 
 dae_status run_gemm(dae_trainer* t, const GemmArgs& g) {
     dae_ctx* ctx = t->ctx;
     ctx->launches += 1;
-    if (!launch_gemm_x3(ctx->stream, g, (g.M + 127) / 128, (g.N + 127) / 128))
-        return tfail(ctx, DAE_ERR_CUDA, "training GEMM launch failed");
+    const bool ok = t->prec == DAE_FP32 ? launch_gemm_f32(ctx->stream, g)
+                                        : launch_gemm_x3(ctx->stream, g, (g.M + 127) / 128, (g.N + 127) / 128);
+    if (!ok) return tfail(ctx, DAE_ERR_CUDA, "training GEMM launch failed");
     return DAE_OK;
 }
 
@@ -122,8 +129,12 @@ void stage_weights(dae_trainer* t, const float* const* W, bool transposed) {
     for (int l = 0; l < t->L; ++l) {
         auto& y = t->layers[l];
         t->ctx->launches += 1;
-        launch_train_weights(t->ctx->stream, W[l], y.n_out, y.n_in, y.wh, y.wl,  y.ld,
-                             transposed ? y.wth : nullptr, transposed ? y.wtl : nullptr, y.ldT);
+        if (t->prec == DAE_FP32)
+            launch_train_weights_f32(t->ctx->stream, W[l], y.n_out, y.n_in, y.wf, y.ld,
+                                     transposed ? y.wtf : nullptr, y.ldT);
+        else
+            launch_train_weights(t->ctx->stream, W[l], y.n_out, y.n_in, y.wh, y.wl,  y.ld,
+                                 transposed ? y.wth : nullptr, transposed ? y.wtl : nullptr, y.ldT);
     }
 }
 
@@ -136,6 +147,7 @@ dae_status set_batch(dae_trainer* t, int B) {
         const size_t n = (size_t)P->ldn * (P == &t->Zb ? t->nz_pad : t->nx_pad);
         TCU(ctx, cudaMemsetAsync(P->nh, 0, n * sizeof(__nv_bfloat16), ctx->stream));
         TCU(ctx, cudaMemsetAsync(P->nl, 0, n * sizeof(__nv_bfloat16), ctx->stream));
+        if (P->nf) TCU(ctx, cudaMemsetAsync(P->nf, 0, n * sizeof(float), ctx->stream));
     }
     t->last_B = B;
     return DAE_OK;
@@ -146,8 +158,8 @@ dae_status forward_layer(dae_trainer* t, int l, const float* bias, int B, float*
     auto& y = t->layers[l - 1];
     const int C = B * (1 + t->r);
     const int xb = (l - 1) & 1;
-    return run_gemm(t, gemm(y.tmW, t->tmXc[xb], out, ldo, 1, y.n_out, C, y.ld / 64, bias, B,
-                            t->ctx->d_status));
+    return run_gemm(t, gemm(y.tmW, y.wf, y.ld, t->tmXc[xb], t->X[xb].cf, t->X[xb].ldc, out, ldo, 1,
+                            y.n_out, C, y.ld / 64, bias, B, t->ctx->d_status));
 }
 
 }  // namespace
@@ -231,13 +243,46 @@ dae_status dae_trainer_free(dae_trainer* t) {
     if (!t) return DAE_ERR_INVALID_ARG;
     cudaSetDevice(t->ctx->device);
     cudaStreamSynchronize(t->ctx->stream);
-    for (auto& y : t->layers) { cudaFree(y.wh); cudaFree(y.wl); cudaFree(y.wth); cudaFree(y.wtl); }
+    for (auto& y : t->layers) {
+        cudaFree(y.wh); cudaFree(y.wl); cudaFree(y.wth); cudaFree(y.wtl); cudaFree(y.wf); cudaFree(y.wtf);
+    }
+    for (auto& pr : t->opf) { cudaFree(pr[0]); cudaFree(pr[1]); }
     free_operand(t->X[0]);
     free_operand(t->X[1]);
     free_operand(t->Zb);
     for (auto p : t->Zck) cudaFree(p);
     cudaFree(t->Ztmp); cudaFree(t->Xbar); cudaFree(t->zval);
     delete t;
+    return DAE_OK;
+}
+
+dae_status dae_trainer_set_precision(dae_trainer* t, dae_prec prec) {
+    if (!t) return DAE_ERR_INVALID_ARG;
+    dae_ctx* ctx = t->ctx;
+    if (prec != DAE_FP32 && prec != DAE_BF16X3)
+        return tfail(ctx, DAE_ERR_UNSUPPORTED, "trainer: FP32 or BF16X3 only");
+    TCU(ctx, cudaSetDevice(ctx->device));
+    TCU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (prec == DAE_FP32 && !t->opf[0][0]) {
+        // FP32 operands in both layouts and padded FP32 weights (zeroed once: padding)
+        Operand* ops[3] = {&t->X[0], &t->X[1], &t->Zb};
+        const int nrows[3] = {t->nx_pad, t->nx_pad, t->nz_pad};
+        for (int i = 0; i < 3; ++i) {
+            TTRY(talloc(ctx, &t->opf[i][0], (size_t)t->Cpad * ops[i]->ldc));
+            TTRY(talloc(ctx, &t->opf[i][1], (size_t)nrows[i] * t->Cpad));
+        }
+        for (auto& y : t->layers) {
+            TTRY(talloc(ctx, &y.wf, (size_t)y.m_pad * y.ld));
+            TTRY(talloc(ctx, &y.wtf, (size_t)y.mT_pad * y.ldT));
+        }
+    }
+    Operand* ops[3] = {&t->X[0], &t->X[1], &t->Zb};
+    for (int i = 0; i < 3; ++i) {
+        ops[i]->cf = prec == DAE_FP32 ? t->opf[i][0] : nullptr;
+        ops[i]->nf = prec == DAE_FP32 ? t->opf[i][1] : nullptr;
+    }
+    t->prec = prec;
+    t->last_B = -1;   // the row layouts' padding is zeroed again for the new form
     return DAE_OK;
 }
 
@@ -328,14 +373,15 @@ dae_status dae_train_backward(dae_trainer* t, const float* const* W, const float
             Zk = (k == 0) ? nullptr : ((k % 2 == 0) ? t->Zck[k] : t->Ztmp);
         }
         // W̄_l = Z̄_l X_k^T (contraction over the C batch columns), b̄_l = sum of Z̄_l values
-        TTRY(run_gemm(t, gemm(t->tmZn, t->tmXn[k & 1], g_W[l - 1], w[k], 0, w[l], w[k],
+        TTRY(run_gemm(t, gemm(t->tmZn, t->Zb.nf, t->Zb.ldn, t->tmXn[k & 1], t->X[k & 1].nf,
+                              t->X[k & 1].ldn, g_W[l - 1], w[k], 0, w[l], w[k],
                               (int)((C + 63) / 64), nullptr, 0, ctx->d_status)));
         ctx->launches += 1;
         launch_train_bias_grad(s, zv, zv_ld, w[l], B, g_b[l - 1]);
         if (l > 1) {
             // X̄_k = W_l^T Z̄_l, then Z̄_k through the activation of boundary k
-            TTRY(run_gemm(t, gemm(y.tmWT, t->tmZc, t->Xbar, t->ldz, 1, w[k], C, y.ldT / 64, nullptr, 0,
-                                  ctx->d_status)));
+            TTRY(run_gemm(t, gemm(y.tmWT, y.wtf, y.ldT, t->tmZc, t->Zb.cf, t->Zb.ldc, t->Xbar, t->ldz,
+                                  1, w[k], C, y.ldT / 64, nullptr, 0, ctx->d_status)));
             ctx->launches += 1;
             launch_train_act_bwd(s, t->Xbar, t->ldz, Zk, t->ldz, w[k], B, r, t->act, t->Zb, t->zval);
             zv = t->zval;

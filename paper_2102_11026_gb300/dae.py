@@ -94,6 +94,7 @@ SIGNATURES = {
     "dae_selftest_bounded_waits": ([_vp], _i),
     "dae_trainer_create": ([_vp, _i, _vp, _i, _i, ctypes.POINTER(_vp)], _i),
     "dae_trainer_free": ([_vp], _i),
+    "dae_trainer_set_precision": ([_vp, _i], _i),
     "dae_train_forward": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
     "dae_train_backward": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "dae_rollout": ([_vp, _vp, _vp, _i, _vp, _vp, _i, _vp, _vp, _d, _vp,
@@ -449,6 +450,11 @@ def dae_trainer_create(ctx, widths, act="tanh", max_batch=256):
 
 def dae_trainer_free(tr):
     lib().dae_trainer_free(tr.handle)
+
+
+def dae_trainer_set_precision(tr, prec):
+    """'bf16x3' (tensor cores, default) or 'fp32' (CUDA cores)."""
+    _check(tr.ctx, lib().dae_trainer_set_precision(tr.handle, PREC[prec]))
 
 
 def _tensor_ptr(t, dtype):
