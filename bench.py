@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--wnet", action="store_true",
                     help="predict the cubature weights with a weight network (N-64-64-64-n_tet)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the grouped-strings and training-pass records of the default line")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the per-precision-form rates and oracle errors")
     ap.add_argument("--form-frames", type=int, default=20,
@@ -482,6 +484,9 @@ def run_ours(args):
     dae.dae_destroy(ctx)
     if rank != 0:
         return
+    extra = None
+    if world == 1 and not args.no_extra and args.np == 0 and not args.wnet:
+        extra = measure_extra(args)
     line = {
         "metric": "reduced Newton iterations/s", "value": value, "unit": "iterations/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
@@ -500,8 +505,30 @@ def run_ours(args):
         "roofline": roof, "phase_share": phase_share, "phase_ms_per_evaluation": phase_ms_per_eval,
         "clocks": clocks,
         "gpu_launches": int(launches), "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
+        "other_workloads": extra,
     }
     print(json.dumps(line))
+
+
+def measure_extra(args):
+    """The grouped-strings step (320 independent depth-8 string decoders in one graph,
+    against per-string launches) and the training pass of the small decoder in both
+    forms, in the same run (short: 3 timed steps / 10 timed backward calls)."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.prec = 3, 2, "bf16x3"
+    st = run_strings(a, emit=False)
+    keep = ("metric", "value", "unit", "ms_per_step", "per_string_launches", "roofline", "clocks")
+    out["strings"] = {k: st[k] for k in keep if k in st}
+    out["strings"]["config"] = st["config"]["workload"]
+    for prec in ("bf16x3", "fp32"):
+        a = copy.copy(args)
+        a.steps, a.warmup, a.prec = 10, 3, prec
+        tr = run_train(a, emit=False)
+        out["train_" + prec] = {k: tr[k] for k in ("metric", "value", "unit", "ms_per_step",
+                                                   "roofline", "fit", "dtype") if k in tr}
+    return out
 
 
 def ctypes_report_bytes():
@@ -606,7 +633,7 @@ def train_flops(widths, B):
     return 2.0 * C * (sum(P) + sum(P[1:]) + sum(P[:-1]))
 
 
-def run_train(args):
+def run_train(args, emit=True):
     import torch
     from paper_2102_11026_gb300 import dae, synth
     from paper_2102_11026_gb300.autograd import decoder_uJ
@@ -708,7 +735,7 @@ def run_train(args):
     dae.dae_destroy(ctx)
     if rank != 0:
         return
-    print(json.dumps({
+    out = {
         "metric": "decoder backward-pass TFLOP/s", "value": tf, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -722,11 +749,14 @@ def run_train(args):
         "fit": {"steps": n_steps, "batch": Bt, "loss_first": losses[0], "loss_last": losses[-1],
                 "ms_per_adam_step": fit_ms / n_steps},
         "gpu_launches": int(launches),
-    }))
+    }
+    if not emit:
+        return out
+    print(json.dumps(out))
 
 
 # -------------------------------------------------------- grouped strings --
-def run_strings(args):
+def run_strings(args, emit=True):
     """One implicit-Euler Newton step of every string of the substructured model
     (320 independent strings, depth-8 decoders) per bench step: the grouped entry point
     (all strings in one graph) against per-string dae_newton_step calls.  Under torchrun
@@ -899,6 +929,8 @@ def run_strings(args):
         "phase_share": phase_share, "explicit_vs_graph_max_abs_diff": explicit_diff,
         "clocks": clocks, "gpu_launches": int(launches_step * K),
     }
+    if not emit:
+        return line
     print(json.dumps(line))
 
 
