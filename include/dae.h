@@ -94,7 +94,10 @@ typedef struct {
     double max_step;     /* first trial step of an update capped at |alpha delta|_inf <= max_step
                             (0.5, in latent units; 0 = no cap) */
     double xtol;         /* also stop when the next Newton step is negligible:
-                            |delta|_inf <= xtol * max(1, |q|_inf)  (1e-6; 0 = off) */
+                            |delta|_inf <= xtol * max(1, |q|_inf)  (1e-6; 0 = off), delta the
+                            Newton step at q or, when q was just accepted, its simplified-Newton
+                            estimate -A_prev^{-1} phi(q) from the factors of the previous
+                            iterate's Newton matrix (then A is not formed at q) */
 } dae_newton_opts;
 
 /* Per-frame outcome of dae_newton_step / dae_rollout. */

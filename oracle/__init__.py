@@ -498,7 +498,9 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
     max_step / |delta|_inf) (no cap when max_step is 0).  Stops when
     |phi| <= tol * max(1, |phi_0|), or when the next step is negligible,
     |delta|_inf <= xtol * max(1, |q|_inf) (q is then the solution; xtol = 0 turns
-    this test off).  Returns (q, report dict).  With a linear basis U (N x n_p) the
+    this test off), delta either the Newton step at q or, right after a step is
+    accepted, its simplified-Newton estimate -A_prev^{-1} phi(q) with the previous
+    iterate's Newton matrix.  Returns (q, report dict).  With a linear basis U (N x n_p) the
     unknown is r = [p; q] and the system is linear_subspace_system (qbar, qbar_dot and
     q0 are then (n_p + n_q)-vectors).
     """
@@ -558,11 +560,18 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
             alpha *= 0.5
         else:
             break
+        A_prev = rs["A"]
         q, rs = qt, rt
         it += 1
         alphas.append(alpha)
         hist.append(float(np.linalg.norm(rs["phi"])))
         converged = hist[-1] <= tol * max(1.0, phi0)
+        if not converged and it < max_iter and xtol > 0:
+            # simplified-Newton estimate of the next step with the previous Newton matrix:
+            # when it is negligible the iterate is the solution (no new A is needed)
+            est = np.linalg.solve(A_prev, -rs["phi"])
+            if float(np.max(np.abs(est))) <= xtol * max(1.0, float(np.max(np.abs(q)))):
+                converged = True
     return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs,
                    trials=trials, alphas=alphas, evals=evals)
 

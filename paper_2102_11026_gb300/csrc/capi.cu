@@ -253,6 +253,7 @@ dae_status alloc_workspace(dae_decoder* d) {
     }
     TRY(dmalloc(ctx, &w.red, red_size(r)));
     TRY(dmalloc(ctx, &w.ns, 1));
+    TRY(dmalloc(ctx, &w.lu, (size_t)(kMaxR * kMaxR + 3 * kMaxR)));
     TRY(dmalloc(ctx, &w.qbar, (size_t)r));
     TRY(dmalloc(ctx, &w.qbar_dot, (size_t)r));
     TRY(dmalloc(ctx, &w.q0, (size_t)r));
@@ -269,7 +270,7 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
     dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part); dfree(w.chain_cnt);
-    dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
+    dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.lu); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
     dfree(w.cub_part); dfree(w.cub_energy); dfree(w.cub_tets); dfree(w.cub_w); dfree(w.hist);
     if (w.gexec) cudaGraphExecDestroy(w.gexec);
@@ -537,9 +538,14 @@ dae_status prepare_gram_out(dae_decoder* d, const dae_mesh* m, int n_cub) {
 // else the fixed heuristic.
 void apply_plan(const dae_decoder* d, int dir, int l, ChainJob& j, int grid) {
     const auto& sp = d->plan_split[dir];
+    j.solo = 0;
     if (d->plan_prec == (int)d->prec && (int)sp.size() == d->L - 1) {
         j.split = sp[l];
         j.rep = d->plan_rep[dir][l];
+        if (j.rep == 0) {          // solo: the whole layer on CTA 0
+            j.rep = 1;
+            j.solo = 1;
+        }
     } else {
         chain_plan(j, grid);
     }
@@ -607,12 +613,14 @@ dae_status build_chains(dae_decoder* d) {
 // within the grid), each as replicated K loops or (P >= 2) as a K split with at least
 // two k-blocks per chunk.
 std::vector<std::pair<int, int>> plan_candidates(const ChainJob& j, int grid) {
-    std::vector<std::pair<int, int>> c;   // (split, rep)
+    std::vector<std::pair<int, int>> c;   // (split, rep); rep 0: solo
     for (int P = 1; P <= 8; P *= 2) {
         if (j.tiles * P > grid) break;
         c.push_back({1, P});
         if (P >= 2 && j.nk >= 2 * P) c.push_back({P, 1});
     }
+    // small layers on CTA 0 alone (no grid barrier between consecutive ones)
+    if (j.tiles <= 8 && j.tiles * j.nk <= 64) c.push_back({1, 0});
     return c;
 }
 
@@ -1010,6 +1018,7 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
         aa.max_halvings = P.opts->max_halvings; aa.max_evals = P.opts->max_evals;
     }
     aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+    aa.lu = P.control ? w.lu : nullptr;
     aa.hcond = P.hcond; aa.use_cond = P.use_cond; aa.kcount = P.kcount; aa.kpe = P.kpe;
     {
         Phase p(ctx, DAE_PHASE_ASSEMBLE, 2);
@@ -1901,6 +1910,7 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
         aa.max_step = opts.max_step; aa.xtol = opts.xtol;
         aa.max_halvings = opts.max_halvings; aa.max_evals = opts.max_evals;
         aa.eval_flag = w.eval_flag; aa.status = ctx->d_status;
+        aa.lu = cpl ? nullptr : w.lu;
         if (cpl) {
             // coupled: each domain's phi and A only; the global decision reads the flags
             aa.eval_flag = nullptr;
@@ -2260,7 +2270,7 @@ dae_status dae_decoder_get_chain_plan(const dae_decoder* d, int dir, int* split,
     for (int l = 0; l < d->L - 1; ++l) {
         const ChainJob& j = dir == 0 ? fj[l] : rj[d->L - 2 - l];
         split[l] = j.split;
-        rep[l] = j.rep;
+        rep[l] = j.solo ? 0 : j.rep;
     }
     return DAE_OK;
 }
@@ -2342,10 +2352,30 @@ dae_status dae_decoder_autotune(dae_decoder* d, int reps, double* ms) {
         // plan of its layer when it is faster by more than 1 % (timing noise)
         for (int i = 0; i < n; ++i) {
             for (auto c : plan_candidates(jobs[i], G)) {
-                if (c.first == jobs[i].split && c.second == jobs[i].rep) continue;
+                if (c.first == jobs[i].split && c.second == (jobs[i].solo ? 0 : jobs[i].rep)) continue;
                 std::vector<ChainJob> trial = jobs;
                 trial[i].split = c.first;
-                trial[i].rep = c.second;
+                trial[i].rep = c.second == 0 ? 1 : c.second;
+                trial[i].solo = c.second == 0 ? 1 : 0;
+                double t;
+                TRY(time_chain(d, dir, trial, reps, &t));
+                if (t < 0.99 * best) { best = t; jobs = trial; }
+            }
+        }
+        // runs of consecutive small layers on CTA 0 alone at either end of the chain (one
+        // solo layer still pays its grid barriers; a run skips those between its layers)
+        auto solo_ok = [&](const ChainJob& j) {
+            for (auto c : plan_candidates(j, G)) if (c.second == 0) return true;
+            return false;
+        };
+        for (int len = 2; len <= n; ++len) {
+            for (int end = 0; end < 2; ++end) {
+                const int a = end == 0 ? 0 : n - len;
+                bool ok = true;
+                for (int i = a; i < a + len; ++i) ok = ok && solo_ok(jobs[i]);
+                if (!ok) continue;
+                std::vector<ChainJob> trial = jobs;
+                for (int i = a; i < a + len; ++i) { trial[i].split = 1; trial[i].rep = 1; trial[i].solo = 1; }
                 double t;
                 TRY(time_chain(d, dir, trial, reps, &t));
                 if (t < 0.99 * best) { best = t; jobs = trial; }
@@ -2367,7 +2397,7 @@ dae_status dae_decoder_autotune(dae_decoder* d, int reps, double* ms) {
         for (int i = 0; i < n; ++i) {
             const int l = dir == 0 ? i : n - 1 - i;   // layer order
             sp[l] = jobs[i].split;
-            rp[l] = jobs[i].rep;
+            rp[l] = jobs[i].solo ? 0 : jobs[i].rep;
         }
         if (d->plan_prec != (int)d->prec || (int)d->plan_split[1 - dir].size() != n) {
             std::vector<int> os(n), orp(n);

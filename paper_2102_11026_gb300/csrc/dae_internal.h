@@ -78,6 +78,7 @@ struct NewtonState {
                              //    step (rejected, converged or stopped), so the reverse pass
                              //    and the Newton matrix are skipped (set by k_decide)
     int nfull;               // evaluations of the frame that formed the Newton matrix
+    int lu_ok;               // 1: the FP32 factors of the last Newton matrix are stored
 };
 
 struct ChainJob;
@@ -153,6 +154,7 @@ struct Workspace {
     // reduced system (FP64)
     double* red = nullptr;          // phi | A | energy | terms (see dae_assemble_reduced)
     NewtonState* ns = nullptr;
+    float* lu = nullptr;            // FP32 factors of the last Newton matrix (step estimate)
     double* qbar = nullptr;         // [r]
     double* qbar_dot = nullptr;     // [r]
     float* zvec = nullptr;          // [r] z = Delta - dt qbar_dot (FP32 copy)
@@ -347,7 +349,8 @@ struct ChainJob {
     int stream;                  // 1: equal k-block ranges per CTA (output layer, mode 1)
     int item_base;               // grouped stage: position of this job's first tile in the
                                  // stage's item list (jobs of one stage are consecutive)
-    int pad_;
+    int solo;                    // 1: every tile of the layer on CTA 0 (split = rep = 1); no
+                                 // grid barrier between consecutive solo layers
 };
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
@@ -442,6 +445,7 @@ struct AsmArgs {
     double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
     int* eval_flag;                          // per-evaluation flag of the cubature kernel
     int* status;                             // sticky device status (assemble-only mode)
+    float* lu;                               // stored FP32 Newton-matrix factors (control)
     cudaGraphConditionalHandle hcond; int use_cond;
     unsigned long long* kcount; int kpe;
     // linear subspace (np > 0): r above is the system size np + rq
@@ -481,6 +485,7 @@ struct CtlArgs {
     double tol, c_armijo, max_step, xtol; int max_iter, max_halvings, max_evals;
     int* eval_flag;     // set by the cubature kernel (inverted tet) for this evaluation
     int* status;
+    float* lu;          // FP32 factors of the last Newton matrix (null: no step estimate)
     int rq, np;                              // decoder latent size, linear basis size (r = np + rq)
     const double* linsum;                    // [np][1 + 2 rq] sums of V^T X
     const float* UMU; const float* Uf;

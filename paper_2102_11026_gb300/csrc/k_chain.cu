@@ -133,10 +133,11 @@ __device__ __forceinline__ Item item_of(int item, int P, int split, int nk) {
 // [c T / G, (c+1) T / G) of the job's T = tiles x nk k-blocks, so every CTA streams the
 // same number (at least one) of k-blocks.  The range is cut at tile edges into a head piece (end of a tile begun by
 // the previous CTA), a tail piece (start of a tile the next CTA ends) and whole
-// tiles, taken as head, one whole tile, tail, the other whole tiles: both pieces of a
-// cut tile are streamed early by their CTAs, so the CTA that finishes the tile does
-// so early, the pieces' epilogues overlap whole-tile MMAs, and every CTA ends on
-// whole tiles.
+// tiles, taken as tail, one whole tile, head, the other whole tiles: every CTA
+// publishes its tail piece first and finishes (last to arrive) the tile of its head
+// piece after one whole tile, so no CTA's finishing work delays a piece another CTA
+// waits for (a finishing epilogue, e.g. the Gram rows' reductions, takes several
+// microseconds), and every CTA ends on whole tiles.
 struct Walk {
     int P, split, nk, items, stream, G;
     long long T, g0, g1, hb, tb, cur;
@@ -150,6 +151,10 @@ struct Walk {
         G = G_;
         stage = 0;
         item = c;
+        if (J.solo) {            // a solo layer: every tile on CTA 0, in order
+            G = 1;
+            item = c == 0 ? 0 : items;
+        }
         T = g0 = g1 = hb = tb = cur = 0;
         if (stream) {                   // 64-bit divisions only where the ranges are used
             T = (long long)J.tiles * nk;
@@ -174,17 +179,17 @@ struct Walk {
                 seg(I, g0, g1);
                 return true;
             }
-            if (stage == 0) {                    // head piece
+            if (stage == 0) {                    // tail piece
                 stage = 1;
-                if (g0 < hb) { seg(I, g0, hb); return true; }
+                if (tb < g1 && tb >= hb) { seg(I, tb, g1); return true; }
             }
             if (stage == 1) {                    // first whole tile
                 stage = 2;
                 if (cur < tb) { seg(I, cur, cur + nk); cur += nk; return true; }
             }
-            if (stage == 2) {                    // tail piece
+            if (stage == 2) {                    // head piece
                 stage = 3;
-                if (tb < g1 && tb >= hb) { seg(I, tb, g1); return true; }
+                if (g0 < hb) { seg(I, g0, hb); return true; }
             }
             if (cur < tb) {                      // other whole tiles
                 seg(I, cur, cur + nk);
@@ -508,6 +513,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!wok) break;
                 if (Jb.a.mode == 1) {
                     // output layer (one row per thread, fused row reductions)
+                    if (I.tl < Jb.a.gram_tiles && et < 4 * Jb.a.r) {
+                        // the Gram rows' reductions read this tile's rows of the input
+                        // activations X (i1 columns): into L2 now, while the pieces settle
+                        // (the operand stream has evicted them)
+                        const int j = et >> 2, ln = et & 3;
+                        prefetch_line_l2(Jb.a.Xg + (size_t)(kShared + 3 * j) * Jb.a.ldxg +
+                                         (size_t)I.tl * 128 + 32 * ln);
+                    }
                     if (Jb.stream && (I.kb0 > 0 || I.kb1 < nk)) {
                         // a tile cut between CTAs: publish this piece; the last of the
                         // tile's CTAs sums the pieces in CTA order and finishes the tile
@@ -534,26 +547,46 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (!s_last) continue;
                         float4* own4 = reinterpret_cast<float4*>(tile);
                         constexpr int NE = (int)(TILE_BYTES / 16);
+                        // the partners' pieces into L2 first: every line's miss in flight at
+                        // once instead of eight loads per thread at a time
+                        for (int cc = cf; cc <= cl; ++cc) {
+                            if (cc == (int)blockIdx.x) continue;
+                            const char* src = reinterpret_cast<const char*>(
+                                split_part + ((size_t)cc * 2 + slot_of(cc)) * (TILE_BYTES / 4));
+                            for (uint32_t b = (uint32_t)et * 128u; b < TILE_BYTES; b += 128u * 128u)
+                                prefetch_line_l2(src + b);
+                        }
                         for (int e0 = et; e0 < NE; e0 += 128 * 8) {
-                            // eight float4 of every piece in flight at once
+                            // eight float4 of up to three pieces in flight at once (the
+                            // loads of the pieces do not wait for one another), summed in
+                            // CTA order
                             float4 acc[8];
-                            for (int cc = cf; cc <= cl; ++cc) {
-                                float4 v[8];
-                                const float4* src = reinterpret_cast<const float4*>(
-                                    split_part + ((size_t)cc * 2 + slot_of(cc)) * (TILE_BYTES / 4));
+                            for (int c0 = cf; c0 <= cl; c0 += 3) {
+                                float4 v[3][8];
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    const int e = e0 + u * 128;
-                                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                                    if (e < NE) v[u] = (cc == (int)blockIdx.x) ? own4[e] : __ldcg(src + e);
+                                for (int pc = 0; pc < 3; ++pc) {
+                                    const int cc = c0 + pc;
+                                    const float4* src = reinterpret_cast<const float4*>(
+                                        split_part + ((size_t)cc * 2 + slot_of(cc)) * (TILE_BYTES / 4));
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) {
+                                        const int e = e0 + u * 128;
+                                        v[pc][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                        if (cc <= cl && e < NE)
+                                            v[pc][u] = (cc == (int)blockIdx.x) ? own4[e] : __ldcg(src + e);
+                                    }
                                 }
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    if (cc == cf) {
-                                        acc[u] = v[u];
-                                    } else {
-                                        acc[u].x += v[u].x; acc[u].y += v[u].y;
-                                        acc[u].z += v[u].z; acc[u].w += v[u].w;
+                                for (int pc = 0; pc < 3; ++pc) {
+                                    if (c0 + pc > cl) break;
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) {
+                                        if (c0 + pc == cf) {
+                                            acc[u] = v[pc][u];
+                                        } else {
+                                            acc[u].x += v[pc][u].x; acc[u].y += v[pc][u].y;
+                                            acc[u].z += v[pc][u].z; acc[u].w += v[pc][u].w;
+                                        }
                                     }
                                 }
                             }
@@ -641,7 +674,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async_global();       // epilogue stores feed the next layer's TMA
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        // consecutive solo layers run on CTA 0 alone: its own CTA barrier orders them (the
+        // epilogue's stores were fenced for the next layer's TMA above)
+        const bool solo_next = !grouped && st + 1 < n_jobs && jobs[st].solo && jobs[st + 1].solo;
+        if (threadIdx.x == 0 && !solo_next) {
             if (!grid_barrier(gb, G, gen)) fail = 1;
         }
         __syncthreads();

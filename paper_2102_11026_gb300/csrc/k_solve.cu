@@ -87,7 +87,36 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
 // FP32 pivot is below 2^-20 max|A| (such A are beyond what the FP32 factors resolve).
 constexpr int kRefine = 3;
 
-__device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
+// One warp: d = U^{-1} L^{-1} P b in FP32 with the factors of mixed_solve (lane i holds
+// row i of the factors, the step ps at which it was the pivot, and b_i); returns d_i on
+// lane i.  Branch-free chains: steps past r are no-ops (perm 0, multiplier 0).
+__device__ __forceinline__ float lu_apply(const float* row, int ps, const int* pk, const float* rk,
+                                          float bv, int r) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < kMaxR; ++k) {
+        const float bp = __shfl_sync(full, bv, pk[k]);
+        const float m = (k < r && ps > k) ? row[k] : 0.f;
+        bv = fmaf(-m, bp, bv);
+    }
+    float d = 0.f;
+#pragma unroll
+    for (int k = kMaxR - 1; k >= 0; --k) {
+        const float xk = __shfl_sync(full, bv, pk[k]) * rk[k];
+        if (lane == k) d = xk;
+        const float m = (k < r && ps >= 0 && ps < k) ? row[k] : 0.f;
+        bv = fmaf(-m, xk, bv);
+    }
+    return d;
+}
+
+// Layout of the stored FP32 factors (lu_out of mixed_solve): [32][32] rows, then ps,
+// perm and 1/pivot per row (floats; perm and ps exact small integers).
+constexpr int kLuRows = 0, kLuPs = kMaxR * kMaxR, kLuPerm = kLuPs + kMaxR, kLuRinv = kLuPerm + kMaxR;
+constexpr int kLuFloats = kLuRinv + kMaxR;
+
+__device__ int mixed_solve(const double* A, const double* b, double* x, int r, float* lu_out) {
     __shared__ int perm[kMaxR];
     __shared__ float rinv[kMaxR], dsol[kMaxR];
     __shared__ double res[kMaxR], part[4][kMaxR];
@@ -149,11 +178,17 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
     }
     asm volatile("bar.sync 2, 128;" ::: "memory");
     if (s_sing) return DAE_ERR_SINGULAR;
+    if (lu_out && warp == 0) {
+        // the factors for the next iterate's simplified-Newton step estimate (k_decide)
+#pragma unroll
+        for (int j = 0; j < kMaxR; ++j) lu_out[kLuRows + lane * kMaxR + j] = row[j];
+        lu_out[kLuPs + lane] = (float)ps;
+        lu_out[kLuPerm + lane] = lane < r ? (float)perm[lane] : 0.f;
+        lu_out[kLuRinv + lane] = lane < r ? rinv[lane] : 0.f;
+    }
     for (int it = 0; it <= kRefine; ++it) {
         if (warp == 0) {
-            // d = U^{-1} L^{-1} P res in FP32; lane i holds the right-hand side of row i.
-            // Branch-free chains: steps past r are no-ops (perm 0, multiplier 0).
-            float bv = lane < r ? (float)res[lane] : 0.f;
+            // d = U^{-1} L^{-1} P res in FP32; lane i holds the right-hand side of row i
             int pk[kMaxR];
             float rk[kMaxR];
 #pragma unroll
@@ -161,20 +196,7 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r) {
                 pk[k] = k < r ? perm[k] : 0;
                 rk[k] = k < r ? rinv[k] : 0.f;
             }
-#pragma unroll
-            for (int k = 0; k < kMaxR; ++k) {
-                const float bp = __shfl_sync(full, bv, pk[k]);
-                const float m = (k < r && ps > k) ? row[k] : 0.f;
-                bv = fmaf(-m, bp, bv);
-            }
-            float d = 0.f;
-#pragma unroll
-            for (int k = kMaxR - 1; k >= 0; --k) {
-                const float xk = __shfl_sync(full, bv, pk[k]) * rk[k];
-                if (lane == k) d = xk;
-                const float m = (k < r && ps >= 0 && ps < k) ? row[k] : 0.f;
-                bv = fmaf(-m, xk, bv);
-            }
+            const float d = lu_apply(row, ps, pk, rk, lane < r ? (float)res[lane] : 0.f, r);
             if (lane < r) dsol[lane] = d;
         }
         asm volatile("bar.sync 2, 128;" ::: "memory");
@@ -271,11 +293,37 @@ __device__ __forceinline__ void decide_impl(const CtlArgs& C) {
     if (t == 0) *energy = en;
     __syncthreads();
     if (!C.control) return;   // statuses of an assemble-only call: k_control
-    // |phi|^2 by a warp reduction (serial FP64 chains are slow on this part)
+    // |phi|^2 by a warp reduction (serial FP64 chains are slow on this part), and the
+    // simplified-Newton estimate of the step from this iterate, -A_prev^{-1} phi, with the
+    // FP32 factors of the last Newton matrix (reading R6: a frame whose estimated next
+    // step is below xtol stops here, without forming A at this iterate)
+    __shared__ double s_est, s_qn;
+    __shared__ int s_est_ok;
     if (t < 32) {
         double m2 = t < r ? sphi[t] * sphi[t] : 0.0;
         for (int o = 16; o > 0; o >>= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
         if (t == 0) s_merit = m2;
+        const bool est = C.lu && S.lu_ok && C.xtol > 0.0;
+        if (est) {
+            float row[kMaxR], rk[kMaxR];
+            int pk[kMaxR];
+#pragma unroll
+            for (int j = 0; j < kMaxR; ++j) {
+                row[j] = C.lu[kLuRows + t * kMaxR + j];
+                pk[j] = (int)C.lu[kLuPerm + j];
+                rk[j] = C.lu[kLuRinv + j];
+            }
+            const int ps = (int)C.lu[kLuPs + t];
+            const float d = lu_apply(row, ps, pk, rk, t < r ? (float)(-sphi[t]) : 0.f, r);
+            double xn = (t < r && isfinite(d)) ? fabs((double)d) : (t < r ? INFINITY : 0.0);
+            double qn = t < r ? fabs(S.q_trial[t]) : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                xn = fmax(xn, __shfl_xor_sync(0xffffffffu, xn, o));
+                qn = fmax(qn, __shfl_xor_sync(0xffffffffu, qn, o));
+            }
+            if (t == 0) { s_est = xn; s_qn = qn; }
+        }
+        if (t == 0) s_est_ok = est ? 1 : 0;
     }
     __syncthreads();
     if (t == 0) {
@@ -306,6 +354,7 @@ __device__ __forceinline__ void decide_impl(const CtlArgs& C) {
             const double pn = sqrt(merit);
             if (pn <= C.tol * fmax(1.0, S.phi_norm0)) { S.converged = 1; dec = 2; }
             else if (S.iters >= C.max_iter) dec = 2;
+            else if (S.evals > 1 && s_est_ok && s_est <= C.xtol * fmax(1.0, s_qn)) { S.converged = 1; dec = 2; }
         } else if (dec == 0) {
             if (S.halvings >= C.max_halvings) dec = 3;
         }
@@ -413,7 +462,7 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     if (nonfinite) {
         if (t == 0) lu_st = DAE_ERR_NONFINITE;
     } else if (t < 128) {
-        const int st0 = mixed_solve(A, rhs, x, r);
+        const int st0 = mixed_solve(A, rhs, x, r, C.lu);
         if (t == 0) lu_st = st0;
     }
     __syncthreads();
@@ -441,6 +490,7 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
                 // the first trial step is capped at max_step in the max-norm
                 S.alpha = (C.max_step > 0.0 && xn > C.max_step) ? C.max_step / xn : 1.0;
                 S.halvings = 0;
+                S.lu_ok = C.lu ? 1 : 0;
             }
         }
     }
@@ -485,7 +535,7 @@ void assemble_parts(const AsmArgs& a, ColsumArgs cs[4], DsumArgs& ds, CtlArgs& c
     c.red = a.red; c.ns = a.ns; c.control = a.control;
     c.tol = a.tol; c.c_armijo = a.c_armijo; c.max_step = a.max_step; c.xtol = a.xtol; c.max_iter = a.max_iter;
     c.max_halvings = a.max_halvings; c.max_evals = a.max_evals;
-    c.eval_flag = a.eval_flag; c.status = a.status;
+    c.eval_flag = a.eval_flag; c.status = a.status; c.lu = a.lu;
     c.hcond = a.hcond; c.use_cond = a.use_cond; c.kcount = a.kcount; c.kpe = a.kpe;
     c.rq = rq; c.np = np; c.linsum = linsum; c.UMU = a.UMU; c.Uf = a.Uf;
     c.qbar = a.qbar; c.qbar_dot = a.qbar_dot; c.q_in = a.q_in;
@@ -601,7 +651,7 @@ __global__ void k_frame_start(RollCtl* rc, NewtonState* ns, const double* qbar,
     if (i == 0) {
         ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
         ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
-        ns->skip_rev = 0; ns->nfull = 0;
+        ns->skip_rev = 0; ns->nfull = 0; ns->lu_ok = 0;
         ns->status = 0; ns->frame = rc->frame;
         if (kcount) atomicAdd(kcount, 1ull);
         if (use) cudaGraphSetConditional(h, 1u);
@@ -671,7 +721,7 @@ __global__ void k_frame_begin_b(const FrameArgs* __restrict__ f, cudaGraphCondit
     if (i == 0) {
         ns->merit_acc = 0.0; ns->phi_norm0 = 0.0; ns->alpha = 1.0; ns->energy = 0.0;
         ns->halvings = 0; ns->iters = 0; ns->evals = 0; ns->done = 0; ns->converged = 0;
-        ns->skip_rev = 0; ns->nfull = 0;
+        ns->skip_rev = 0; ns->nfull = 0; ns->lu_ok = 0;
         ns->status = 0; ns->frame = 0;
         if (use && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
     }

@@ -407,7 +407,7 @@ static __device__ __forceinline__ void reduce_row_block(const FwdArgs& A, float*
         for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
     }
     const bool do_phi = (mat == 0 && bj == 0);
-#pragma unroll 4
+#pragma unroll 8
     for (int k = 0; k < 128; ++k) {
         const float* tk = tile + k * TS;
         const float mk = ms[k], ak = as[k];
@@ -519,26 +519,20 @@ static __device__ __forceinline__ void gram_row_reduce(const FwdArgs& A, float* 
         const float* __restrict__ X = A.Xg;
         const size_t ldx = A.ldxg;
         float py = vrow[3] * ih2;
-        for (int j0 = 0; j0 < r; j0 += 8) {
-            float pj[8], pd[8], xj[8], z[8];
+        // the row's input activations of every group first: all r global loads in flight
+        float xj[kMaxR];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = j0 + u < r ? j0 + u : r - 1;
+        for (int j = 0; j < kMaxR; ++j)
+            xj[j] = j < r ? X[(size_t)(kShared + 3 * j) * ldx + k] : 0.f;
+#pragma unroll
+        for (int j = 0; j < kMaxR; ++j) {
+            if (j < r) {
                 const int cb = kShared + 3 * j;
-                pj[u] = vrow[cb] * ih;
-                pd[u] = vrow[cb + 2] * ih3;
-                xj[u] = X[(size_t)cb * ldx + k] * ih;
-                z[u] = zs[j];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (j0 + u < r) {
-                    const int cb = kShared + 3 * (j0 + u);
-                    vrow[cb] = pj[u];
-                    vrow[cb + 1] = xj[u];
-                    vrow[cb + 2] = pd[u];
-                    py = fmaf(pj[u], z[u], py);
-                }
+                const float pj = vrow[cb] * ih;
+                vrow[cb] = pj;
+                vrow[cb + 1] = xj[j] * ih;
+                vrow[cb + 2] = vrow[cb + 2] * ih3;
+                py = fmaf(pj, zs[j], py);
             }
         }
         if (A.gy) A.gy[k] = py;
