@@ -521,10 +521,13 @@ def newton_solve(wl, q0=None, max_iter=None, tol=1e-8, c_armijo=1e-4, max_halvin
 
 
 def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
-                   max_step=0.5, xtol=1e-6):
+                   max_step=0.5, xtol=1e-6, estimate=True):
     """The Newton iteration of ``newton_solve`` on any system: ``system(x)`` returns a
     dict with ``phi`` and its Jacobian ``A`` at x, or raises ``Inverted`` (a trial
-    point the line search then halves away from).  Returns (q, report dict)."""
+    point the line search then halves away from).  ``estimate``: after an accepted
+    trial, stop when the simplified-Newton step with the previous Newton matrix is below
+    ``xtol`` (else only the full step at the new iterate is tested).  Returns
+    (q, report dict)."""
     q = np.asarray(q, np.float64).copy()
     rs = system(q)
     phi0 = np.linalg.norm(rs["phi"])
@@ -533,10 +536,12 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
     # (iteration, alpha, |phi(trial)|^2 / Armijo threshold, or None for an inverted
     # trial), the accepted step lengths, and the number of system evaluations
     trials, alphas, evals = [], [], 1
+    nfull = 0      # iterates whose Newton matrix was used (solved with)
     it = 0
     converged = phi0 <= tol * max(1.0, phi0)
     while not converged and it < max_iter:
         delta = np.linalg.solve(rs["A"], -rs["phi"])
+        nfull += 1
         m0 = float(rs["phi"] @ rs["phi"])
         dn = float(np.max(np.abs(delta)))
         if xtol > 0 and dn <= xtol * max(1.0, float(np.max(np.abs(q)))):
@@ -566,14 +571,14 @@ def newton_iterate(system, q, max_iter, tol=1e-8, c_armijo=1e-4, max_halvings=8,
         alphas.append(alpha)
         hist.append(float(np.linalg.norm(rs["phi"])))
         converged = hist[-1] <= tol * max(1.0, phi0)
-        if not converged and it < max_iter and xtol > 0:
+        if estimate and not converged and it < max_iter and xtol > 0:
             # simplified-Newton estimate of the next step with the previous Newton matrix:
             # when it is negligible the iterate is the solution (no new A is needed)
             est = np.linalg.solve(A_prev, -rs["phi"])
             if float(np.max(np.abs(est))) <= xtol * max(1.0, float(np.max(np.abs(q)))):
                 converged = True
     return q, dict(iters=it, converged=bool(converged), phi_hist=hist, final=rs,
-                   trials=trials, alphas=alphas, evals=evals)
+                   trials=trials, alphas=alphas, evals=evals, nfull=nfull)
 
 
 # --------------------------------------------------- coupled substructures --
@@ -651,13 +656,15 @@ def coupled_system(cm, Q, Qbar, Qdot, dt=None, cub_w=None):
 def coupled_newton_solve(cm, Q0=None, Qbar=None, Qdot=None, dt=None, max_iter=None,
                          cub_w=None, **kw):
     """The Newton iteration of ``newton_solve`` on the coupled system (one global LU
-    solve per iteration over all domains' latents).  Defaults: Qbar, Qdot stacked from
-    the domains' states, Q0 = Qbar + dt Qdot."""
+    solve per iteration over all domains' latents; every accepted unconverged iterate
+    forms the global Newton matrix, with no simplified-Newton stop).  Defaults: Qbar,
+    Qdot stacked from the domains' states, Q0 = Qbar + dt Qdot."""
     dt = cm.domains[0].state.dt if dt is None else dt
     Qbar = np.concatenate([wl.state.qbar for wl in cm.domains]) if Qbar is None else Qbar
     Qdot = np.concatenate([wl.state.qbar_dot for wl in cm.domains]) if Qdot is None else Qdot
     Q0 = Qbar + dt * Qdot if Q0 is None else Q0
     max_iter = cm.domains[0].max_iter if max_iter is None else max_iter
+    kw.setdefault("estimate", False)
     Q, rep = newton_iterate(lambda x: coupled_system(cm, x, Qbar, Qdot, dt, cub_w), Q0,
                             max_iter, **kw)
     rep["qdot"] = (Q - Qbar) / dt

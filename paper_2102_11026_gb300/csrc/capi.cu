@@ -214,6 +214,7 @@ dae_status alloc_workspace(dae_decoder* d) {
     w.n_row_blocks = (N + 127) / 128;
     w.row_stride = r + r * (r + 1) / 2 + r * r;
     TRY(dmalloc(ctx, &w.row_part, (size_t)w.n_row_blocks * w.row_stride));
+    w.row_part_cap = w.n_row_blocks;
     // reverse-pass partials: the largest of the W_L^T a splits and the hidden splits
     const int K = d->widths[L - 1];
     size_t need = (size_t)(128 + kMaxPairSplits + 1) * K;   // dense + pair + f_ext splits
@@ -268,7 +269,7 @@ void free_workspace(Workspace& w) {
     for (int i = 0; i < 2; ++i) { dfree(w.G32[i]); dfree(w.Gh[i]); dfree(w.Gl[i]); }
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
-    dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part);
+    dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part); dfree(w.out_part);
     dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part); dfree(w.chain_cnt);
     dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.lu); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
@@ -495,6 +496,36 @@ dae_status ensure_gs(dae_decoder* d, const dae_mesh* m, int n_cub) {
         w.Jc_cap = jc;
         w.graph_ok = false;
     }
+    // the stream-form output stage stores its items unfinished (k_out_finish sums and
+    // finishes them): raw_m slots per CTA, the most tiles one CTA's k-block range touches
+    {
+        const int G = ctx->sm_count;
+        const long long nk = w.ldGs / (f32 ? 32 : 64);
+        const long long T = (long long)(Gt + Rt) * nk;
+        int mx = 0;
+        if (T >= G)
+            for (int c = 0; c < G; ++c) {
+                const long long a = T * c / G, b = T * (c + 1) / G;
+                mx = std::max(mx, (int)((b - 1) / nk - a / nk + 1));
+            }
+        const size_t need = (size_t)G * mx * 128 * (w.Cp + 1);
+        if (need > w.out_part_cap) {
+            CU(ctx, cudaStreamSynchronize(ctx->stream));
+            dfree(w.out_part);
+            TRY(dmalloc(ctx, &w.out_part, need));
+            w.out_part_cap = need;
+            w.graph_ok = false;
+        }
+        w.raw_m = mx;
+        const int rows = kFinishBlocks * Gt;   // partial rows of the finish kernel
+        if (rows > w.row_part_cap) {
+            CU(ctx, cudaStreamSynchronize(ctx->stream));
+            dfree(w.row_part);
+            TRY(dmalloc(ctx, &w.row_part, (size_t)rows * w.row_stride));
+            w.row_part_cap = rows;
+            w.graph_ok = false;
+        }
+    }
     if (w.gs_G_mesh != m->id) {
         const size_t n = (size_t)K * w.ldGs;   // G is [K][ldG], ldG = ldGs
         if (f32) launch_round_tf32(ctx->stream, w.G, w.Gs32, n);
@@ -611,7 +642,7 @@ dae_status build_chains(dae_decoder* d) {
 // ------------------------------------------------------------ autotuner --
 // Candidate plans of one chain layer: P = 1, 2, 4 or 8 CTAs per 128-row tile (tiles x P
 // within the grid), each as replicated K loops or (P >= 2) as a K split with at least
-// two k-blocks per chunk.
+// two k-blocks per chunk; and, for a small layer, every tile on CTA 0 (rep 0: solo).
 std::vector<std::pair<int, int>> plan_candidates(const ChainJob& j, int grid) {
     std::vector<std::pair<int, int>> c;   // (split, rep); rep 0: solo
     for (int P = 1; P <= 8; P *= 2) {
@@ -715,15 +746,22 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
         const long long T = (long long)job.tiles * job.nk;
         job.stream = (T >= ctx->sm_count && (job.tiles > ctx->sm_count || o.gram)) ? 1 : 0;
         job.cnt_off = 0;
+        // the Gram form's items go out unfinished and a second kernel sums and finishes
+        // them with many CTAs: no CTA of the stream waits for another's pieces, and the
+        // rows' reductions run on all SMs instead of on one CTA per tile
+        job.raw = (o.gram && job.stream && w.raw_m > 0) ? 1 : 0;
+        job.raw_m = job.raw ? w.raw_m : 0;
         ctx->launches += 1;
         launch_store_job(s, w.out_job, job);
         ChainLaunch cl = {};
         cl.jobs = w.out_job; cl.n_jobs = 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
-        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status;
+        cl.split_part = job.raw ? w.out_part : w.chain_part;
         cl.split_cnt = w.chain_cnt;
-        Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
+        Phase p(ctx, DAE_PHASE_FWD_OUT, job.raw ? 2 : 1);
         if (!launch_chain(s, cl, d->prec))
             return fail(ctx, DAE_ERR_CUDA, "output-layer launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        if (job.raw) launch_out_finish(s, w.out_job, job.tiles, w.Cp, w.out_part, ctx->sm_count, ns);
     }
     for (int l = chain ? L : 0; l < L; ++l) {
         FwdArgs a;
@@ -1007,7 +1045,8 @@ dae_status enqueue_eval(dae_decoder* d, const dae_mesh* m, NewtonState* ns,
     aa.rq = r; aa.np = np; aa.lin_part = w.lin_part; aa.lin_blocks = w.lin_blocks;
     aa.UMU = w.UMU; aa.Uf = P.f_ext ? w.Uf : nullptr; aa.qbar = w.qbar; aa.qbar_dot = w.qbar_dot;
     aa.q_in = q_override;
-    aa.row_part = w.row_part; aa.n_row_blocks = gout ? w.Gt : w.n_row_blocks;
+    aa.row_part = w.row_part;
+    aa.n_row_blocks = gout ? (w.raw_m > 0 ? kFinishBlocks * w.Gt : w.Gt) : w.n_row_blocks;
     aa.row_stride = w.row_stride;
     aa.cub_part = w.cub_part; aa.cub_energy = w.cub_energy; aa.n_cub = P.n_cub;
     aa.cub_stride = w.cub_stride; aa.cub_parts = ca.n_parts;

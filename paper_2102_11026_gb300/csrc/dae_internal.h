@@ -202,6 +202,13 @@ struct Workspace {
     CUtensorMap tmGs[2];
     bool gs_ok = false;             // stacked operand ready (G part current)
     float* gy = nullptr;            // [K] G x_y, written by the G tiles' epilogue
+    // the output stage's unfinished items (single-system Newton path): CTA c's item over
+    // tile t in slot c * raw_m + (t - first tile of c), [128][Cp + 1] FP32 each; summed
+    // and finished by k_out_finish
+    float* out_part = nullptr;
+    size_t out_part_cap = 0;
+    int raw_m = 0;
+    int row_part_cap = 0;           // rows of row_part (the finish kernel writes 4 per G tile)
     // weight network (cubature weights predicted at run time), first layer composed with
     // the output layer: h1 = sin(B1 x + c1), x the output layer's input (real column)
     int wn_H1 = 0, wn_H2 = 0, wn_H3 = 0, wn_ntet = 0;
@@ -351,6 +358,8 @@ struct ChainJob {
                                  // stage's item list (jobs of one stage are consecutive)
     int solo;                    // 1: every tile of the layer on CTA 0 (split = rep = 1); no
                                  // grid barrier between consecutive solo layers
+    int raw;                     // stream job whose items are stored unfinished (raw_m slots
+    int raw_m;                   // per CTA in the launch's split_part) for k_out_finish
 };
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
@@ -365,6 +374,14 @@ struct ChainLaunch {
 };
 constexpr int kMaxGroupJobs = 512;   // jobs of one grouped stage
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec);
+// The output stage's raw items summed (in CTA order) and finished: G tiles' row
+// reductions (kFinishBlocks partial rows per tile into a.row_part, G x_y), the cubature
+// rows' u and J into a.Jc.  d_job: the stream job (device copy, `tiles` tiles, Cp
+// columns) whose launch over `grid` CTAs stored them in `part`.
+void launch_out_finish(cudaStream_t s, const ChainJob* d_job, int tiles, int Cp, const float* part,
+                       int grid, const NewtonState* ns);
+constexpr int kFinishRows = 32;                   // rows per block of k_out_finish
+constexpr int kFinishBlocks = 128 / kFinishRows;  // blocks (partial rows) per tile
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job);
 int run_wait_selftest(cudaStream_t s, GridBar* gb, int* out, int nblocks);
 // Work decomposition of one chain layer: sets job.split and job.rep.

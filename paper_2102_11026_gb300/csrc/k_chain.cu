@@ -511,6 +511,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 mbar_arrive(&tempty[ab]);      // this accumulator may be overwritten
                 if (!wok) break;
+                if (Jb.raw) {
+                    // store the item unfinished: k_out_finish sums each tile's items in
+                    // CTA order and finishes the tile (slot: this CTA's tiles in order)
+                    fence_proxy_async_smem();
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (et == 0) {
+                        const long long Tt = (long long)tiles * nk;
+                        const int ft = (int)((Tt * blockIdx.x / G) / nk);
+                        float* dst = split_part +
+                                     ((size_t)blockIdx.x * Jb.raw_m + (size_t)(I.tl - ft)) * (TILE_BYTES / 4);
+                        bulk_store_wait(dst, tile, TILE_BYTES);
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");   // the tile is reused next item
+                    continue;
+                }
                 if (Jb.a.mode == 1) {
                     // output layer (one row per thread, fused row reductions)
                     if (I.tl < Jb.a.gram_tiles && et < 4 * Jb.a.r) {
@@ -755,6 +770,71 @@ bool launch_chain_prec(cudaStream_t s, const ChainLaunch& c) {
 
 }  // namespace
 
+// The output stage's raw items finished.  Block (t, b) takes rows [32 b, 32 b + 32) of
+// tile t: it sums the items of the tile's CTAs cf..cl in CTA order (bitwise
+// reproducible), then a G tile's rows give the reductions over their 32 rows (one
+// partial row per block) and G x_y, a cubature tile's rows their u and J.
+__global__ void __launch_bounds__(128) k_out_finish(const ChainJob* __restrict__ pj,
+                                                    const float* __restrict__ part, int G,
+                                                    const NewtonState* ns) {
+    if (ns && ns->done) return;
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ float s_z[kMaxR];
+    const ChainJob& J = *pj;
+    const FwdArgs& A = J.a;
+    const int t = blockIdx.x, b = blockIdx.y, et = threadIdx.x;
+    const int TS = A.Cp + 1, nk = J.nk;
+    const long long T = (long long)J.tiles * nk;
+    const int cf = stream_cta((long long)t * nk, T, G);
+    const int cl = stream_cta((long long)(t + 1) * nk - 1, T, G);
+    const size_t tile_f = (size_t)128 * TS;
+    const int NE4 = kFinishRows * TS / 4;   // float4 of this block's rows (TS * 32 / 4)
+    float4* tile4 = reinterpret_cast<float4*>(fsm);
+    constexpr int EB = 8;                   // float4 loads in flight per thread and item
+    for (int e0 = et; e0 < NE4; e0 += 128 * EB) {
+        float4 acc[EB];
+        for (int c = cf; c <= cl; ++c) {
+            const int ft = (int)((T * c / G) / nk);
+            const float4* src = reinterpret_cast<const float4*>(
+                                    part + ((size_t)c * J.raw_m + (size_t)(t - ft)) * tile_f) +
+                                (size_t)b * NE4;
+            float4 v[EB];
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+                const int e = e0 + u * 128;
+                v[u] = e < NE4 ? __ldcg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+                if (c == cf) {
+                    acc[u] = v[u];
+                } else {
+                    acc[u].x += v[u].x; acc[u].y += v[u].y; acc[u].z += v[u].z; acc[u].w += v[u].w;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < EB; ++u)
+            if (e0 + u * 128 < NE4) tile4[e0 + u * 128] = acc[u];
+    }
+    if (t < A.gram_tiles && et < A.r) s_z[et] = A.zvec[et];
+    __syncthreads();
+    const int row = et;
+    if (t < A.gram_tiles) {
+        gram_row_reduce<kFinishRows>(A, fsm, TS, row, t * 128 + b * kFinishRows + row, true,
+                                     t * kFinishBlocks + b, s_z);
+    } else if (row < kFinishRows) {
+        const int i = (t - A.gram_tiles) * 128 + b * kFinishRows + row;
+        const int n = i < A.n_map ? A.row_map[i] : -1;
+        const float* vrow = fsm + (size_t)row * TS;
+        if (A.Jc) {
+            if (n >= 0) compact_epilogue(A, i, n, vrow);
+        } else {
+            row_epilogue(A, n < 0 ? A.n_out : n, vrow);
+        }
+    }
+}
+
 // Self-test of the bounded waits: an mbarrier that nothing arrives on and a grid
 // barrier that expects one CTA more than the grid has.  Both must give up within
 // their limit; out[b] = 1 when CTA b saw both time out.
@@ -788,6 +868,13 @@ __global__ void k_store_job(ChainJob* dst, ChainJob job) {
 
 void launch_store_job(cudaStream_t s, ChainJob* dst, const ChainJob& job) {
     k_store_job<<<1, 128, 0, s>>>(dst, job);
+}
+
+void launch_out_finish(cudaStream_t s, const ChainJob* d_job, int tiles, int Cp, const float* part,
+                       int grid, const NewtonState* ns) {
+    // the block's rows (Cp + 1 floats each) and their weights and scalars
+    const size_t smem = ((size_t)kFinishRows * (Cp + 1) + 2 * kFinishRows) * sizeof(float);
+    k_out_finish<<<dim3(tiles, kFinishBlocks), 128, smem, s>>>(d_job, part, grid, ns);
 }
 
 bool launch_chain(cudaStream_t s, const ChainLaunch& c, dae_prec prec) {

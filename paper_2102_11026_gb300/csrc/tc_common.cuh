@@ -372,18 +372,20 @@ static __device__ __noinline__ void slice_epilogue(const FwdArgs& A, const float
     for (int cc = n_cols(r) + sub; cc < CP; cc += tpr) o.put((size_t)cc * ldy + n, 0.f);
 }
 
-// Output-row reductions fused into the output layer's epilogue, over one tile's
-// Partials of one 128-row block held in shared memory (row stride TS): per row k a
+// Partials of one block of NR rows held in shared memory (row stride TS): per row k a
 // left factor L_k,i (column kShared + 3i + xoff), right factors R_k,j (column kShared +
-// 3j: J side; + 2: dJ side), a weight ms[k] and a scalar as[k];
+// 3j: J side; + 2: dJ side), a weight ms[k] and a scalar as[k] (ms, as after the NR
+// rows);
 //   out = [sum_k L_k,i as_k | sum_k ms_k L_k,i R_k,j (upper) | sum_k ms_k L_k,i R'_k,j]
-// in the layout of k_row_reduce, by the 128 epilogue threads (named barrier 1).
+// in the layout of k_row_reduce (partial row tl), by 128 threads (named barrier 1;
+// thread `row` owns a 4 x 4 block of one of the two r x r sums).
+template <int NR = 128>
 static __device__ __forceinline__ void reduce_row_block(const FwdArgs& A, float* tile, int TS,
                                                      int row, int tl, int xoff) {
     const int r = A.r;
     float* __restrict__ out = A.row_part + (size_t)tl * A.row_stride;
-    float* ms = tile + (size_t)128 * TS;
-    float* as = ms + 128;
+    float* ms = tile + (size_t)NR * TS;
+    float* as = ms + NR;
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const int nsym = r * (r + 1) / 2;
     // 4x4 register blocks: threads 0-63 own blocks of J^T M J, 64-127 of J^T M dJ;
@@ -408,7 +410,7 @@ static __device__ __forceinline__ void reduce_row_block(const FwdArgs& A, float*
     }
     const bool do_phi = (mat == 0 && bj == 0);
 #pragma unroll 8
-    for (int k = 0; k < 128; ++k) {
+    for (int k = 0; k < NR; ++k) {
         const float* tk = tile + k * TS;
         const float mk = ms[k], ak = as[k];
         float Ji[4], Xj[4];
@@ -505,6 +507,8 @@ static __device__ __forceinline__ void fused_row_reduce(const FwdArgs& A, float*
 //   J^T (M y - dt^2 f_ext) = sum_k xJ_k (py_k - dt^2 (W_L^T f_ext)_k),
 // the same partials as fused_row_reduce over the N output rows.  py = (G x_y)_k goes to
 // A.gy (the reverse pass's seed W_L^T M y).
+// NR rows per block: threads row < NR form their row's terms, all 128 the sums.
+template <int NR = 128>
 static __device__ __forceinline__ void gram_row_reduce(const FwdArgs& A, float* tile, int TS,
                                                     int row, int k, bool wok, int tl,
                                                     const float* zs) {
@@ -512,10 +516,12 @@ static __device__ __forceinline__ void gram_row_reduce(const FwdArgs& A, float* 
     const float ih = (float)A.inv_h, ih2 = (float)A.inv_h2, ih3 = (float)A.inv_h3;
     const double dt2 = A.dt * A.dt;
     float* vrow = tile + (size_t)row * TS;
-    float* ms = tile + (size_t)128 * TS;
-    float* as = ms + 128;
+    float* ms = tile + (size_t)NR * TS;
+    float* as = ms + NR;
     float av = 0.f;
-    if (wok && k < K) {
+    if (row >= NR) {
+        // no row of this block
+    } else if (wok && k < K) {
         const float* __restrict__ X = A.Xg;
         const size_t ldx = A.ldxg;
         float py = vrow[3] * ih2;
@@ -540,9 +546,11 @@ static __device__ __forceinline__ void gram_row_reduce(const FwdArgs& A, float* 
     } else {
         for (int c = 0; c < CP; ++c) vrow[c] = 0.f;
     }
-    ms[row] = 1.f;
-    as[row] = av;
-    reduce_row_block(A, tile, TS, row, tl, 1);
+    if (row < NR) {
+        ms[row] = 1.f;
+        as[row] = av;
+    }
+    reduce_row_block<NR>(A, tile, TS, row, tl, 1);
 }
 
 }  // namespace tc

@@ -67,10 +67,10 @@ def test_line_search_halves_and_rejects_inverted_trial(prec):
         g.close()
     assert rep.status == 0
     assert rep.iters == ro["iters"] and rep.evals == ro["evals"]
-    # only iterates that start a new Newton step form A (one per solve: the first iterate
-    # and the accepted trials before the last); rejected trials and the final accepted
+    # only iterates whose Newton matrix is solved with form A (the first iterate and the
+    # accepted trials that do not end the frame); rejected trials and the final accepted
     # one are phi-only evaluations
-    assert rep.full_evals == ro["iters"] and rep.full_evals < rep.evals
+    assert rep.full_evals == ro["nfull"] and rep.full_evals < rep.evals
     assert rep.alpha == ro["alphas"][-1]                 # powers of two: exact
     assert bool(rep.converged) == ro["converged"]
     tol = 1e-4 if prec == "fp32" else 1e-3

@@ -371,6 +371,27 @@ def test_newton_step_cap_and_step_tolerance():
     assert rx["iters"] <= rt["iters"]
 
 
+def test_simplified_newton_stop_agrees_with_the_full_step():
+    """After an accepted trial, the stop on the simplified-Newton estimate -A_prev^{-1}
+    phi(q) takes the same decision as the full step -A(q)^{-1} phi(q) on a
+    quadratically converging frame: the same iterate and count of iterations, one Newton
+    matrix fewer, and the true remaining step at the end is below xtol.  (An estimate
+    formed with the previous residual, or with the sign of a step already taken, would
+    not stop, and the count of matrices would not drop.)"""
+    wl = synth.custom([3, 8, 8, 3 * 27], (3, 3, 3), 12, 3, "tanh", "stvk", 1e3, 0.3, True)
+    q0 = synth.newton_start(wl.state)
+    xtol = 1e-6
+    qe, re = oracle.newton_solve(wl, q0=q0, max_iter=20, tol=0.0, xtol=xtol)
+    system = lambda x: oracle.reduced_system(wl, x)
+    qn, rn = oracle.newton_iterate(system, q0, 20, tol=0.0, xtol=xtol, estimate=False)
+    assert re["converged"] and rn["converged"]
+    assert re["iters"] == rn["iters"] >= 2 and np.array_equal(qe, qn)
+    assert re["nfull"] == re["iters"] and rn["nfull"] == rn["iters"] + 1
+    rs = oracle.reduced_system(wl, qe)
+    step = np.linalg.solve(rs["A"], -rs["phi"])
+    assert np.abs(step).max() <= xtol * max(1.0, np.abs(qe).max())
+
+
 # --------------------------------------------- decoder backward (u, J) ---
 
 def _uJ_loss(dec, Q, gu, gJ):
