@@ -14,10 +14,9 @@
 // rows into the spare rows of the staging tile before summing.  Either way each of
 // the P CTAs of a tile finishes 128/P rows, so the activation epilogue of a layer is
 // spread over tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue
-// runs, the producer prefetches the next layer's weight tiles into L2 and issues the
-// weight half of the next layer's first k-blocks into the free ring slots (weights
-// do not depend on the layer in flight); after the grid barrier it adds only the
-// activation half of those slots.
+// runs, the producer issues the weight half of the next layer's first k-blocks into the
+// free ring slots (weights do not depend on the layer in flight); after the grid
+// barrier it adds only the activation half of those slots.
 //
 // Roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5 epilogue.
 // The accumulator is staged through a shared-memory tile so the MMA of the next
@@ -101,14 +100,6 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 __device__ __forceinline__ void prefetch_line_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
-
-__device__ __forceinline__ void prefetch_l2_2d(const CUtensorMap* map, int c0, int c1) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1)
-                 : "memory");
-}
-
 
 struct Item {
     int tl, ks, kb0, kb1;
@@ -386,9 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 pre_n = 0;
-                // the next layer's weight tiles of this CTA's items into L2 (they do not
-                // depend on this layer's output), and its job header into L1 (every
-                // role reads it right after the grid barrier)
+                // the next layer's job header into L1 (every role reads it right after the
+                // grid barrier) and its first weight tiles into the ring
                 if (!grouped && st + 1 < n_jobs && !fail) {
                     const ChainJob& Nb = jobs[st + 1];
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(&Nb.tiles));
@@ -412,13 +402,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
-                    Walk Wn(Nb, blockIdx.x, G);
-                    while (Wn.next(I)) {
-                        for (int kb = I.kb0; kb < I.kb1; ++kb) {
-                            prefetch_l2_2d(&Nb.tm[0], kb * KB, I.tl * 128);
-                            if constexpr (X3) prefetch_l2_2d(&Nb.tm[1], kb * KB, I.tl * 128);
-                        }
-                    }
+                    // (the rest of the next layer's weights is not prefetched into L2: that
+                    // stream competed with this layer's split-K exchange through L2, and the
+                    // large layers stream at the rate of their CTAs' pipelines either way)
                 }
             }
         } else if (warp == 1) {
