@@ -609,6 +609,11 @@ void chain_jobs(const dae_decoder* d, std::vector<ChainJob>& fj, std::vector<Cha
         cnt_r += j.tiles;
         part = std::max(part, (size_t)j.tiles * j.split * (w.Cb + 1) * 128);
     }
+    // the per-tile ready counters follow the split counters in the same array
+    cnt_f = (cnt_f + kRdyStride - 1) / kRdyStride * kRdyStride;
+    cnt_r = (cnt_r + kRdyStride - 1) / kRdyStride * kRdyStride;
+    for (auto& j : fj) { j.rdy_off = (int)cnt_f; cnt_f += (size_t)j.tiles * kRdyStride; }
+    for (auto& j : rj) { j.rdy_off = (int)cnt_r; cnt_r += (size_t)j.tiles * kRdyStride; }
 }
 
 // Job lists of the persistent layer-chain kernel (both directions).

@@ -360,7 +360,11 @@ struct ChainJob {
                                  // grid barrier between consecutive solo layers
     int raw;                     // stream job whose items are stored unfinished (raw_m slots
     int raw_m;                   // per CTA in the launch's split_part) for k_out_finish
+    int rdy_off;                 // first per-tile ready counter of this layer (chains of one
+                                 // decoder): arrivals of the CTAs finishing the tile's rows,
+                                 // one counter per kRdyStride words (its own 128-byte line)
 };
+constexpr int kRdyStride = 32;
 struct GridBar { unsigned count; unsigned gen; };
 struct ChainLaunch {
     const ChainJob* jobs; int n_jobs; int Cp; int grid;

@@ -65,6 +65,20 @@ __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& gen) {
     return true;
 }
 
+// Bounded wait (one thread) until a producer tile's ready counter reaches `target`
+// arrivals; then the async proxy (the TMA loads that follow) may read what they wrote.
+__device__ bool wait_ready(const unsigned* cnt, unsigned target) {
+    if (ld_acquire(cnt) < target) {
+        const uint64_t t0 = globaltimer();
+        while (ld_acquire(cnt) < target) {
+            if (globaltimer() - t0 > kWaitNs) return false;
+            __nanosleep(32);   // fewer polls of a line the finishers update
+        }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -306,6 +320,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t nred = 0; // split reductions of this CTA (rbar phases)
     const bool grouped = stage_off != nullptr;
     const int n_st = grouped ? n_stages : n_jobs;
+    // a single decoder's chain runs without grid barriers between its layers: each CTA
+    // finishing rows of a tile counts itself on the tile's ready counter, and a k-block's
+    // activations are loaded once the tile that wrote them is complete (one grid barrier
+    // at the end, after which the counters are zeroed for the next launch).  Two
+    // activation buffers suffice: a layer's rows are written only after its CTAs (or their
+    // split partners) consumed every tile of the layer before, hence after every read of
+    // the buffer they overwrite.
+    const bool flow = !grouped && n_jobs > 1;
     for (int st = 0; st < n_st; ++st) {
         const int j0 = grouped ? stage_off[st] : st;
         const int nj = grouped ? stage_off[st + 1] - j0 : 1;
@@ -320,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (threadIdx.x == 0) s_base[nj] = jobs[j0 + nj - 1].item_base + jobs[j0 + nj - 1].tiles;
             __syncthreads();
-        } else if (st > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        } else if (!flow && st > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
             // the previous layer's split counters are no longer read: zero them for the
             // next launch (counters of one launch are disjoint per layer)
             const ChainJob& Pb = jobs[st - 1];
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
         }
         if (warp == 0) {
-            if (lane == 0 && !fail) {
+            if (lane == 0 && !*(volatile int*)&fail) {
                 StageWalk W(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
                 const ChainJob* Jp;
                 const ChainJob* Jlast = nullptr;
@@ -344,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 int kc = 0;   // k-blocks of this stage so far
+                int rdy_tile = -1;   // previous layer's tile known complete (flow)
                 while (!fail && W.next(Jp, I)) {
                     const CUtensorMap* tmA = &Jp->tm[0];
                     const CUtensorMap* tmAlo = &Jp->tm[1];
@@ -369,17 +392,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mbar_expect_tx(&full[s], STAGE);
                         uint8_t* base = smem + (size_t)s * STAGE;
                         tma_load_2d(base, tmA, &full[s], kb * KB, I.tl * 128);
-                        tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
-                        if constexpr (X3) {
-                            tma_load_2d(base + A_BYTES + B_BYTES, tmAlo, &full[s], kb * KB, I.tl * 128);
-                            tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
+                        if constexpr (X3) tma_load_2d(base + A_BYTES + B_BYTES, tmAlo, &full[s], kb * KB, I.tl * 128);
+                        if (flow && st > 0) {
+                            // the previous layer's tile holding this k-block's rows
+                            const int pt = kb * KB / 128;
+                            if (pt != rdy_tile) {
+                                const ChainJob& Pb = jobs[st - 1];
+                                const unsigned P = (unsigned)(Pb.split > Pb.rep ? Pb.split : Pb.rep);
+                                if (!wait_ready(split_cnt + Pb.rdy_off + pt * kRdyStride, P)) {
+                                    // settle the slot so that the MMA warp is not left waiting
+                                    mbar_complete_tx(&full[s], B_BYTES * (X3 ? 2u : 1u));
+                                    fail = 1;
+                                    break;
+                                }
+                                rdy_tile = pt;
+                            }
                         }
+                        tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
+                        if constexpr (X3) tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
                     }
                 }
                 pre_n = 0;
                 // the next layer's job header into L1 (every role reads it right after the
                 // grid barrier) and its first weight tiles into the ring
-                if (!grouped && st + 1 < n_jobs && !fail) {
+                if (!flow && !grouped && st + 1 < n_jobs && !fail) {
                     const ChainJob& Nb = jobs[st + 1];
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(&Nb.tiles));
                     // the first k-blocks of the next layer's weights straight into the free
@@ -408,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         } else if (warp == 1) {
-            if (lane == 0 && !fail) {
+            if (lane == 0 && !*(volatile int*)&fail) {
                 StageWalk W(jobs, j0, nj, grouped, s_base, s_skip, blockIdx.x, G);
                 const ChainJob* Jp;
                 Item I;
@@ -449,7 +485,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const ChainJob* Jp;
             const ChainJob* Jlast = nullptr;
             Item I;
-            for (; W.next(Jp, I); ++it) {
+            // without barriers between layers, a failure elsewhere in the CTA ends the
+            // epilogue's layers too (decided by all its threads together)
+            const bool go = !flow || epi_all(!*(volatile int*)&fail);
+            for (; go && W.next(Jp, I); ++it) {
                 const ChainJob& Jb = *Jp;
                 const int tiles = Jb.tiles, split = Jb.split, nk = Jb.nk;
                 const int P = split > Jb.rep ? split : Jb.rep;
@@ -464,17 +503,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     Jlast = Jp;
                 }
-                if (et == 0 && Jb.a.mode != 1) {
-                    // this slice's epilogue inputs into L2 while the MMAs run
+                if (Jb.a.mode != 1) {
+                    // this slice's epilogue inputs into L2 while the MMAs run (one row of T
+                    // per thread: a single thread issuing them all held the whole epilogue
+                    // back when the MMAs were already done)
                     const int n0 = I.tl * 128 + I.ks * R;
                     const int n1 = min(n0 + R, Jb.a.n_out);
                     const int n_out = Jb.a.n_out;
                     if (Jb.a.mode == 2 && n0 < n1) {
-                        prefetch_line_l2(Jb.a.S1 + n0);
-                        for (int c = 0; c < Jb.a.r; ++c)
+                        if (et < Jb.a.r)
                             for (int nn = n0; nn < n1; nn += 32)
-                                prefetch_line_l2(Jb.a.T + (size_t)c * n_out + nn);
-                    } else if (Jb.a.mode == 0 && n0 < n1) {
+                                prefetch_line_l2(Jb.a.T + (size_t)et * n_out + nn);
+                        else if (et == Jb.a.r)
+                            prefetch_line_l2(Jb.a.S1 + n0);
+                    } else if (Jb.a.mode == 0 && n0 < n1 && et == 0) {
                         prefetch_line_l2(Jb.a.bias + n0);
                     }
                 }
@@ -670,10 +712,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 slice_epilogue<PREC>(Jb.a, tile, TS, I.tl, I.ks * R, R, et);
+                if (flow) {
+                    // this CTA's rows of the tile are written: count it on the tile's ready
+                    // counter (the stores fenced for the consumers' TMA, then a release)
+                    fence_proxy_async_global();
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (et == 0)
+                        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(split_cnt + Jb.rdy_off + I.tl * kRdyStride)
+                                     : "memory");
+                }
                 asm volatile("bar.sync 1, 128;" ::: "memory");   // the tile is reused next item
             }
             fence_proxy_async_global();       // epilogue stores feed the next layer's TMA
         }
+        if (flow && st + 1 < n_st) continue;   // each role goes on with the next layer
         __syncthreads();
         // consecutive solo layers run on CTA 0 alone: its own CTA barrier orders them (the
         // epilogue's stores were fenced for the next layer's TMA above)
@@ -684,7 +736,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         if (fail) break;
     }
-    if (!fail && n_jobs > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (flow) {
+        // every CTA is past every wait (the grid barrier after the last layer): zero the
+        // split and ready counters of all layers for the next launch
+        __syncthreads();
+        if (!fail && blockIdx.x == 0)
+            for (int j = 0; j < n_jobs; ++j) {
+                const ChainJob& Pb = jobs[j];
+                for (int t = threadIdx.x; t < Pb.tiles; t += blockDim.x) {
+                    if (Pb.split > 1) split_cnt[Pb.cnt_off + t] = 0u;
+                    split_cnt[Pb.rdy_off + t * kRdyStride] = 0u;
+                }
+            }
+    } else if (!fail && n_jobs > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
         const ChainJob& Pb = jobs[n_jobs - 1];
         if (Pb.split > 1)
             for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
