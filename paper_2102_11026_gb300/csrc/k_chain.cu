@@ -4,14 +4,15 @@
 //
 // One CTA per SM for the whole chain (cooperative launch): barriers, TMEM and the
 // instruction stream are set up once instead of once per layer.  Each layer
-// ("job") is cut into items (128-row tile x K range) dealt round-robin to the CTAs;
-// a grid-wide barrier separates the layers (the next layer's TMA reads the
-// activations the previous layer's epilogue wrote).
+// ("job") is cut into items (128-row tile x K range) dealt round-robin to the CTAs.
+// In a single decoder's chain a layer's k-block is loaded once the tile of the layer
+// before that wrote its rows is complete (per-tile ready counters, no barrier between
+// layers); grouped launches put a grid-wide barrier between their stages.
 //
 // Short-K layers replicate the whole K loop on `rep` CTAs per tile; long-K layers
-// split K over `split` CTAs per tile, which publish their partial tiles (one bulk
-// copy each), wait for one another and bulk-load the partners' slices of their own
-// rows into the spare rows of the staging tile before summing.  Either way each of
+// split K over `split` CTAs per tile, which publish the partners' slices of their
+// partial tiles (bulk copies), wait for one another and bulk-load the partners' slices
+// of their own rows into the spare rows of the staging tile before summing.  Either way each of
 // the P CTAs of a tile finishes 128/P rows, so the activation epilogue of a layer is
 // spread over tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue
 // runs, the producer issues the weight half of the next layer's first k-blocks into the
@@ -525,13 +526,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 bool wok = epi_all(ok);
                 if (wok) {
+                    // up to three 16-column loads in flight before each wait
+                    constexpr int LB = NC < 3 ? NC : 3;
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        float v[16];
-                        tmem_ld16(tmem + ab * ACC_COLS + ((uint32_t)lane_base << 16) + 16 * c, v);
+                    for (int c0 = 0; c0 < NC; c0 += LB) {
+                        float v[LB][16];
+#pragma unroll
+                        for (int u = 0; u < LB; ++u)
+                            if (c0 + u < NC)
+                                tmem_ld16(tmem + ab * ACC_COLS + ((uint32_t)lane_base << 16) + 16 * (c0 + u), v[u]);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) vrow[16 * c + i] = v[i];
+                        for (int u = 0; u < LB; ++u)
+                            if (c0 + u < NC)
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) vrow[16 * (c0 + u) + i] = v[u][i];
                     }
                 } else {
                     fail = 1;
@@ -666,16 +675,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                     unsigned* cnt = split_cnt + Jb.cnt_off + I.tl;
                     bool got = true;
                     if (et == 0) {
+                        // the partners' slices of this chunk's partial tile (this chunk's own
+                        // slice stays here), then a release on the tile's counter
                         float* dst = split_part + ((size_t)I.tl * split + I.ks) * (TILE_BYTES / 4);
-                        bulk_store_wait(dst, tile, TILE_BYTES);
+                        const uint32_t sf = (uint32_t)R * TS;
+                        for (int c = 0; c < split; ++c)
+                            if (c != I.ks)
+                                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                                                 dst + (size_t)c * sf),
+                                             "r"(smem_u32(tile + (size_t)c * sf)), "r"(sf * 4u)
+                                             : "memory");
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
                         fence_proxy_async_global();
-                        __threadfence();
-                        atomicAdd(cnt, 1u);
+                        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
                         const uint64_t t0 = globaltimer();
                         while (ld_acquire(cnt) != (unsigned)split) {
                             if (globaltimer() - t0 > kWaitNs) { got = false; break; }
                         }
-                        __threadfence();
+                        // the partners' slices are read by the bulk loads below (async proxy)
+                        fence_proxy_async_global();
                     }
                     // chunk s's rows [r0, r0 + R) into this tile's rows [s R, s R + R): the
                     // tile is published, its own rows stay in place, and the split * R = 128
@@ -696,18 +715,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     wok = epi_all(mbar_wait(&rbar, nred & 1));
                     ++nred;
                     if (!wok) { fail = 1; break; }
-                    // sum in chunk order (bitwise reproducible); split <= 8, the eight
-                    // loads of an element issue together
-                    float* own = tile + (size_t)r0 * TS;
-#pragma unroll 2
-                    for (int e = et; e < (int)slice_f; e += 128) {
-                        float v[8];
+                    // sum in chunk order (bitwise reproducible), four floats at a time (a
+                    // slice is R x TS floats, R a multiple of 4: 16-byte aligned)
+                    float4* own4 = reinterpret_cast<float4*>(tile + (size_t)r0 * TS);
+                    const float4* t4 = reinterpret_cast<const float4*>(tile);
+                    const int n4 = (int)slice_f / 4;
+                    for (int e = et; e < n4; e += 128) {
+                        float4 v[8];
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) v[s] = (s >= split) ? 0.f : tile[(size_t)s * slice_f + e];
-                        float acc = v[0];
+                        for (int c = 0; c < 8; ++c)
+                            if (c < split) v[c] = t4[(size_t)c * n4 + e];
+                        float4 a = v[0];
 #pragma unroll
-                        for (int s = 1; s < 8; ++s) acc += v[s];
-                        own[e] = acc;
+                        for (int c = 1; c < 8; ++c)
+                            if (c < split) { a.x += v[c].x; a.y += v[c].y; a.z += v[c].z; a.w += v[c].w; }
+                        own4[e] = a;
                     }
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
