@@ -171,6 +171,19 @@ def hidden_chain_bytes(wl, prec):
     return tot
 
 
+def output_stage_bytes(wl, prec):
+    """Algorithmic DRAM bytes of the Newton path's output stage (Gram form), which runs as
+    the last job of the forward chain's launch: the stacked operand [G ; W_L rows at the
+    12|C| cubature DOFs] once (K + 12|C| rows of K, operand form), its input columns once,
+    and u and J at the cubature DOFs written."""
+    d = wl.dec
+    r, K = d.r, d.widths[-2]
+    C = 4 + 3 * r
+    wbytes = {"fp32": 4, "tf32": 4, "bf16": 2, "bf16x3": 4}[prec]
+    rows = K + 12 * wl.cub_tets.size
+    return rows * K * wbytes + C * K * wbytes + 12 * wl.cub_tets.size * (1 + r) * 4
+
+
 def algorithmic_flops(wl, gram=True):
     """2 [sum_hidden P_l C_f + P_out C_f + sum_hidden P_l (1 + r) + K]: the stacked forward
     over all C_f = 3r + 4 columns (the output stage in Gram form: K x K of G plus the 12|C|
@@ -391,17 +404,21 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     t_hid, c_hid = prof["fwd_hidden"]
     avg_ms = t_hid / max(c_hid, 1)
-    bytes_hid = hidden_chain_bytes(wl, args.prec)
+    # the tensor-core forms run the Gram-form output stage as the chain launch's last job
+    fused = args.prec != "fp32"
+    bytes_hid = hidden_chain_bytes(wl, args.prec) + (output_stage_bytes(wl, args.prec) if fused else 0)
     achieved = bytes_hid / (avg_ms / 1e3) / 1e9
     hbm = peaks["hbm_gbs"]
-    traffic = load_traffic(args.workload, args.prec)
+    traffic = load_traffic(args.workload, args.prec + ("/fused" if fused else ""))
     tc = args.prec != "fp32"
-    flops_hid = hidden_chain_flops(wl)
+    flops_hid = hidden_chain_flops(wl) + (output_stage_flops(wl) if fused else 0.0)
     tf_hid = flops_hid / (avg_ms / 1e3) / 1e12
     tpeak = tensor_peak(peaks, args.prec)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
-            "kernel": "hidden forward chain (k_chain, %d layers, %s)" % (len(d.W) - 1, args.prec),
+            "kernel": ("forward chain: %d hidden layers + Gram-form output stage (k_chain, one "
+                       "launch, %s)" % (len(d.W) - 1, args.prec)) if fused else
+                      "hidden forward chain (k_chain, %d layers, %s)" % (len(d.W) - 1, args.prec),
             "peak_source": "%s hbm_gbs" % peak_src,
             "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_hid}
     tot_ph = sum(v[0] for v in prof_all.values())
@@ -558,6 +575,13 @@ def hidden_chain_flops(wl):
     return 2.0 * sum(w.size for w in d.W[:-1]) * (3 * d.r + 4)
 
 
+def output_stage_flops(wl):
+    """2 (K^2 + 12|C| K)(3r + 4): the Gram-form output stage over the stacked columns."""
+    d = wl.dec
+    K = d.widths[-2]
+    return 2.0 * (K * K + 12 * wl.cub_tets.size * K) * (3 * d.r + 4)
+
+
 def measure_forms(ctx, stream, wl, dec, mesh, ref, args, n_frames):
     """Every precision form of the decoder GEMMs on one workload: Newton iterations/s
     over ``n_frames`` frames (device buffers, CUDA events on the context's stream, after
@@ -614,7 +638,9 @@ def measure_forms(ctx, stream, wl, dec, mesh, ref, args, n_frames):
 
 
 def load_traffic(workload, prec):
-    """DRAM bytes per hidden forward chain launch from the committed ncu summary, if any."""
+    """DRAM bytes per launch of the timed forward kernel from the committed ncu summary, if
+    any ("<workload>/<precision>[/fused]": the fused key for the chain launch that also
+    runs the output stage)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(p):
         with open(p) as f:

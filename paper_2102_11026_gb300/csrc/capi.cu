@@ -625,7 +625,8 @@ dae_status build_chains(dae_decoder* d) {
     size_t part, cnt_f, cnt_r;
     chain_jobs(d, fj, rj, part, cnt_f, cnt_r);
     if (!w.fwd_jobs) {
-        CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * (L - 1)));
+        // the hidden layers, and a slot for the output stage run as the chain's last job
+        CU(ctx, cudaMalloc(&w.fwd_jobs, sizeof(ChainJob) * L));
         CU(ctx, cudaMalloc(&w.rev_jobs, sizeof(ChainJob) * (L - 1)));
         CU(ctx, cudaMalloc(&w.out_job, sizeof(ChainJob)));
         TRY(dmalloc(ctx, &w.gbar, 1));
@@ -730,43 +731,51 @@ dae_status enqueue_forward(dae_decoder* d, const NewtonState* ns, const double* 
     }
     const bool chain = d->ws.chain_ok;
     if (chain) {
-        // hidden layers: one persistent cooperative launch for the whole chain
-        ChainLaunch cl = {};
-        cl.jobs = w.fwd_jobs; cl.n_jobs = L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
-        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
-        cl.split_cnt = w.chain_cnt;
-        Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
-        if (!launch_chain(s, cl, d->prec))
-            return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    }
-    if (chain) {
-        // output layer: a one-job persistent launch, its epilogue (outputs and the fused
-        // row reductions) overlapping the next tile's loads and MMAs
+        // the output layer's job: a stream of k-block ranges per CTA when the tiles do not
+        // divide evenly over the grid (and the Gram form's few long tiles), provided every
+        // CTA gets at least one k-block (a tile's finisher counts one piece from each CTA
+        // its k-blocks span)
         ChainJob job;
         make_out_job(d, o, dt, h, job);
-        // stream the output layer's tiles x nk k-blocks in equal ranges per CTA when the
-        // tiles do not divide evenly over the grid (and the Gram form's few long tiles),
-        // provided every CTA gets at least one k-block: a tile's finisher counts one piece
-        // from each CTA its k-blocks span
         const long long T = (long long)job.tiles * job.nk;
         job.stream = (T >= ctx->sm_count && (job.tiles > ctx->sm_count || o.gram)) ? 1 : 0;
         job.cnt_off = 0;
         // the Gram form's items go out unfinished and a second kernel sums and finishes
         // them with many CTAs: no CTA of the stream waits for another's pieces, and the
-        // rows' reductions run on all SMs instead of on one CTA per tile
+        // rows' reductions run on all SMs instead of on one CTA per tile.  That output
+        // stage then runs as the last job of the hidden chain's launch: its k-blocks start
+        // as soon as the last hidden layer's tiles holding their rows are written
         job.raw = (o.gram && job.stream && w.raw_m > 0) ? 1 : 0;
         job.raw_m = job.raw ? w.raw_m : 0;
-        ctx->launches += 1;
-        launch_store_job(s, w.out_job, job);
-        ChainLaunch cl = {};
-        cl.jobs = w.out_job; cl.n_jobs = 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
-        cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status;
-        cl.split_part = job.raw ? w.out_part : w.chain_part;
-        cl.split_cnt = w.chain_cnt;
-        Phase p(ctx, DAE_PHASE_FWD_OUT, job.raw ? 2 : 1);
-        if (!launch_chain(s, cl, d->prec))
-            return fail(ctx, DAE_ERR_CUDA, "output-layer launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-        if (job.raw) launch_out_finish(s, w.out_job, job.tiles, w.Cp, w.out_part, ctx->sm_count, ns);
+        job.raw_part = job.raw ? w.out_part : nullptr;
+        const bool fuse = job.raw != 0;
+        if (fuse) {
+            ctx->launches += 1;
+            launch_store_job(s, w.fwd_jobs + (L - 1), job);
+        }
+        {
+            ChainLaunch cl = {};
+            cl.jobs = w.fwd_jobs; cl.n_jobs = fuse ? L : L - 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
+            cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+            cl.split_cnt = w.chain_cnt;
+            Phase p(ctx, DAE_PHASE_FWD_HIDDEN, 1);
+            if (!launch_chain(s, cl, d->prec))
+                return fail(ctx, DAE_ERR_CUDA, "layer-chain launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (fuse) {
+            Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
+            launch_out_finish(s, w.fwd_jobs + (L - 1), job.tiles, w.Cp, w.out_part, ctx->sm_count, ns);
+        } else {
+            ctx->launches += 1;
+            launch_store_job(s, w.out_job, job);
+            ChainLaunch cl = {};
+            cl.jobs = w.out_job; cl.n_jobs = 1; cl.Cp = w.Cp; cl.grid = ctx->sm_count;
+            cl.gb = w.gbar; cl.ns = ns; cl.status = ctx->d_status; cl.split_part = w.chain_part;
+            cl.split_cnt = w.chain_cnt;
+            Phase p(ctx, DAE_PHASE_FWD_OUT, 1);
+            if (!launch_chain(s, cl, d->prec))
+                return fail(ctx, DAE_ERR_CUDA, "output-layer launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
     }
     for (int l = chain ? L : 0; l < L; ++l) {
         FwdArgs a;

@@ -360,6 +360,7 @@ struct ChainJob {
                                  // grid barrier between consecutive solo layers
     int raw;                     // stream job whose items are stored unfinished (raw_m slots
     int raw_m;                   // per CTA in the launch's split_part) for k_out_finish
+    float* raw_part;             // raw job: the items' slots
     int rdy_off;                 // first per-tile ready counter of this layer (chains of one
                                  // decoder): arrivals of the CTAs finishing the tile's rows,
                                  // one counter per kRdyStride words (its own 128-byte line)

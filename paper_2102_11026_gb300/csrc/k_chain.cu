@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (et == 0) {
                         const long long Tt = (long long)tiles * nk;
                         const int ft = (int)((Tt * blockIdx.x / G) / nk);
-                        float* dst = split_part +
+                        float* dst = Jb.raw_part +
                                      ((size_t)blockIdx.x * Jb.raw_m + (size_t)(I.tl - ft)) * (TILE_BYTES / 4);
                         bulk_store_wait(dst, tile, TILE_BYTES);
                     }
@@ -765,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!fail && blockIdx.x == 0)
             for (int j = 0; j < n_jobs; ++j) {
                 const ChainJob& Pb = jobs[j];
+                if (Pb.stream) continue;   // the output stage: no split or ready counters
                 for (int t = threadIdx.x; t < Pb.tiles; t += blockDim.x) {
                     if (Pb.split > 1) split_cnt[Pb.cnt_off + t] = 0u;
                     split_cnt[Pb.rdy_off + t * kRdyStride] = 0u;
