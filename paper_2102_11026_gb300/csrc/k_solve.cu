@@ -120,64 +120,76 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r, f
     __shared__ int perm[kMaxR];
     __shared__ float rinv[kMaxR], dsol[kMaxR];
     __shared__ double res[kMaxR], part[4][kMaxR];
-    __shared__ int s_sing;
+    __shared__ int s_sing, s_p;
+    __shared__ unsigned s_used;
+    __shared__ int s_ps[kMaxR];
+    __shared__ float F[kMaxR][kMaxR + 1];   // the FP32 factors in place, row i = row i of A
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const unsigned full = 0xffffffffu;
-    float row[kMaxR];   // warp 0: row `lane` of the FP32 factors (L left of its pivot step, U from it)
+    float row[kMaxR];   // warp 0: row `lane` of the factors (L left of its pivot step, U from it)
     int ps = -1;        // warp 0: the elimination step at which row `lane` was the pivot
     if (t < r) { x[t] = 0.0; res[t] = b[t]; }
+    for (int e = t; e < kMaxR * kMaxR; e += 128) {
+        const int i = e & (kMaxR - 1), j = e / kMaxR;
+        F[i][j] = (i < r && j < r) ? (float)A[(size_t)j * r + i] : 0.f;
+    }
+    if (t < kMaxR) s_ps[t] = -1;
+    if (t == 0) { s_used = 0u; s_sing = 0; }
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    float am = 0.f;
     if (warp == 0) {
-        float am = 0.f;
 #pragma unroll
-        for (int j = 0; j < kMaxR; ++j) {
-            row[j] = (lane < r && j < r) ? (float)A[(size_t)j * r + lane] : 0.f;
-            am = fmaxf(am, fabsf(row[j]));
-        }
+        for (int j = 0; j < kMaxR; ++j) am = fmaxf(am, fabsf(F[lane][j]));
         for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(full, am, o));
-        unsigned used = 0u;
-        int sing = 0;
-        // k runs in a rolled loop: row[k] is read and written through unrolled selects,
-        // so the row stays in registers
-        for (int k = 0; k < r && !sing; ++k) {
-            float rk = 0.f;
-#pragma unroll
-            for (int j = 0; j < kMaxR; ++j)
-                if (j == k) rk = row[j];
-            // pivot: the largest |row[k]| among the unused rows in one warp reduction.  Key:
-            // the bits of |v| (non-negative floats order like unsigned integers) with the
-            // low 5 mantissa bits replaced by 31 - lane, so among values equal to 2^-18
-            // relative the lowest row wins (any of them is a sound partial pivot; the FP64
+    }
+    // LU with partial pivoting, no row swaps: per column k warp 0 picks the pivot row among
+    // the rows not yet used, then the 128 threads update the other unused rows (thread
+    // (lane, warp) takes row lane, columns k+1+warp, k+5+warp, ...), then the multipliers
+    // replace column k.  Column k+1 is updated by warp 0, which searches it next.
+    for (int k = 0; k < r; ++k) {
+        if (warp == 0) {
+            const unsigned used = s_used;
+            const float v = F[lane][k];
+            // the largest |v| among the unused rows in one warp reduction.  Key: the bits
+            // of |v| (non-negative floats order like unsigned integers) with the low 5
+            // mantissa bits replaced by 31 - lane, so among values equal to 2^-18 relative
+            // the lowest row wins (any of them is a sound partial pivot; the FP64
             // refinement below fixes the solution's accuracy)
             const unsigned key = (lane < r && !((used >> lane) & 1u))
-                                     ? ((__float_as_uint(fabsf(rk)) & ~31u) | (31u - (unsigned)lane))
+                                     ? ((__float_as_uint(fabsf(v)) & ~31u) | (31u - (unsigned)lane))
                                      : 0u;
             const unsigned best = __reduce_max_sync(full, key);
             const int p = 31 - (int)(best & 31u);
-            const float v = __uint_as_float(best & ~31u);
-            if (!(v > 0x1p-20f * am) || !isfinite(v)) {
-                sing = 1;
-                break;
-            }
-            const float inv = __frcp_rn(__shfl_sync(full, rk, p));
-            used |= 1u << p;
-            if (lane == p) ps = k;
-            if (lane == 0) { perm[k] = p; rinv[k] = inv; }
-            const bool act = lane < r && !((used >> lane) & 1u);
-            const float l = rk * inv;
-            // branch-free: all 32 broadcasts issue back to back, updates are selects
-            float pr[kMaxR];
-#pragma unroll
-            for (int j = 0; j < kMaxR; ++j) pr[j] = __shfl_sync(full, row[j], p);
-#pragma unroll
-            for (int j = 0; j < kMaxR; ++j) {
-                const float upd = fmaf(-l, pr[j], row[j]);
-                row[j] = (act && j > k) ? upd : ((act && j == k) ? l : row[j]);
+            const float pv = __uint_as_float(best & ~31u);
+            if (lane == 0) {
+                if (!(pv > 0x1p-20f * am) || !isfinite(pv)) {
+                    s_sing = 1;
+                } else {
+                    perm[k] = p;
+                    rinv[k] = __frcp_rn(F[p][k]);
+                    s_ps[p] = k;
+                    s_used = used | (1u << p);
+                    s_p = p;
+                }
             }
         }
-        if (lane == 0) s_sing = sing;
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (s_sing) break;
+        const int p = s_p;
+        const bool act = lane < r && !((s_used >> lane) & 1u);
+        const float l = act ? F[lane][k] * rinv[k] : 0.f;
+        if (act)
+            for (int j = k + 1 + warp; j < r; j += 4) F[lane][j] = fmaf(-l, F[p][j], F[lane][j]);
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (warp == 0 && act) F[lane][k] = l;
+        __syncwarp();
     }
-    asm volatile("bar.sync 2, 128;" ::: "memory");
     if (s_sing) return DAE_ERR_SINGULAR;
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < kMaxR; ++j) row[j] = F[lane][j];
+        ps = s_ps[lane];
+    }
     if (lu_out && warp == 0) {
         // the factors for the next iterate's simplified-Newton step estimate (k_decide)
 #pragma unroll
