@@ -216,6 +216,21 @@ dae_status dae_eval_derivs(dae_ctx* ctx, const dae_decoder* dec, const double* q
                            float* u, float* J, float* Hqq, float* dJ, float* Hw, float* Sdd);
 
 /*
+ * Multicomplex activation of dae_eval_derivs (an ablation of the truncated form).
+ * exact = 0 (default): the activation of every stacked number is its multicomplex Taylor
+ * expansion with the terms of relative order h_cs^2 dropped (Sec. 4.4, Fig. 5), which
+ * lets all perturbations share the real, i2 and i2i3 columns (3r + 4 columns).
+ * exact = 1: every perturbation e_j is its own tricomplex number
+ * q + h e_j i1 + h Delta (i2 + i3) + h^2 w i2i3 with its own real part (6r + 4 columns),
+ * and the activation is evaluated in exact multicomplex arithmetic (Sec. 4.1, Eq. 16;
+ * App. A: recursive addition theorems, tanh(X + iY) = (sinh 2X + i sin 2Y)/(cosh 2X +
+ * cos 2Y)), in FP32 on the CUDA cores.  The two agree to O(h_cs^2) ~ 1e-12 relative,
+ * far below FP32 rounding.  Only the FP32 form, r <= 17 and no linear basis; a
+ * precision change sets it back to 0.  Errors: INVALID_ARG, UNSUPPORTED.
+ */
+dae_status dae_decoder_set_cs_mode(dae_decoder* dec, int exact);
+
+/*
  * Reduced system at q: phi (Eqs. 7-8 times dt^2), A (Eq. 11 with n_p = 0) and
  * the cubature elastic energy sum_e w_e V_e Psi_e(F_e).
  *   cub_tets  n_cub tet indices (distinct), cub_w n_cub non-negative weights (Sec. 5)

@@ -270,6 +270,7 @@ void free_workspace(Workspace& w) {
     for (auto& p : w.S1) dfree(p);
     for (auto& p : w.T) dfree(p);
     dfree(w.u); dfree(w.HDD); dfree(w.a); dfree(w.J); dfree(w.dJ); dfree(w.row_part); dfree(w.out_part);
+    dfree(w.Xe[0]); dfree(w.Xe[1]);
     dfree(w.fwd_jobs); dfree(w.rev_jobs); dfree(w.out_job); dfree(w.gbar); dfree(w.chain_part); dfree(w.chain_cnt);
     dfree(w.gbuf); dfree(w.split_part); dfree(w.split_cnt); dfree(w.red); dfree(w.ns); dfree(w.lu); dfree(w.qbar); dfree(w.qbar_dot); dfree(w.q0);
     dfree(w.zvec); dfree(w.eval_flag); dfree(w.f_ext); dfree(w.fe_w); dfree(w.fe_dof);
@@ -2086,6 +2087,46 @@ dae_status build_batch(dae_ctx* ctx, BatchPlan* b, const std::vector<dae_decoder
 }  // namespace
 
 // =============================================================== C ABI ====
+// The forward pass in exact multicomplex columns (CUDA-core FP32 kernels): the seed
+// and every layer with the exact epilogue, into the outputs of o (u, J, Hqq, dJ).
+dae_status enqueue_forward_exact(dae_decoder* d, const double* dq, double dt, double h, int mode,
+                                 const Outs& o) {
+    dae_ctx* ctx = d->ctx;
+    Workspace& w = d->ws;
+    cudaStream_t s = ctx->stream;
+    const int r = d->r, L = d->L;
+    const int Cpx = pad_cols_exact(r);
+    if (!w.Xe[0] || w.Cpx != Cpx) {
+        CU(ctx, cudaStreamSynchronize(s));
+        dfree(w.Xe[0]); dfree(w.Xe[1]);
+        TRY(dmalloc(ctx, &w.Xe[0], (size_t)Cpx * w.ldx_max));
+        TRY(dmalloc(ctx, &w.Xe[1], (size_t)Cpx * w.ldx_max));
+        w.Cpx = Cpx;
+    }
+    const int ld0 = (int)round_up(r, kKPad);
+    {
+        Phase p(ctx, DAE_PHASE_SEED, 1);
+        launch_seed_exact(s, dq, w.qbar, w.qbar_dot, dt, h, mode, r, Cpx, ld0, w.Xe[0]);
+    }
+    for (int l = 0; l < L; ++l) {
+        FwdArgs a;
+        fill_fwd_args(d, l, a);
+        a.Cp = Cpx;
+        a.exact = 1;
+        a.X = w.Xe[l & 1]; a.Xh = a.Xl = nullptr;
+        a.Y = a.last ? nullptr : w.Xe[(l + 1) & 1];
+        a.Yh = a.Yl = nullptr; a.out_bf16 = 0; a.out_f32 = 1;
+        a.S1 = nullptr; a.T = nullptr;
+        a.inv_h = 1.0 / h; a.inv_h2 = 1.0 / (h * h); a.inv_h3 = 1.0 / (h * h * h);
+        a.inv_dt2 = 1.0 / (dt * dt);
+        if (a.last) { a.u = o.u; a.J = o.J; a.dJ = o.dJ; a.HDD = o.HDD; a.Hqq = o.Hqq; }
+        Phase p(ctx, a.last ? DAE_PHASE_FWD_OUT : DAE_PHASE_FWD_HIDDEN, 1);
+        launch_fwd_simt(s, a);
+    }
+    CU(ctx, cudaGetLastError());
+    return DAE_OK;
+}
+
 extern "C" {
 
 int dae_version(void) { return DAE_VERSION; }
@@ -2227,8 +2268,10 @@ dae_status dae_decoder_set_precision(dae_decoder* d, dae_prec prec) {
     // buffers, which build_chains below frees and reallocates: never replay it again
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     drop_graph(d->ws);
-    // a chain plan belongs to the precision it was set or tuned for
+    // a chain plan belongs to the precision it was set or tuned for; the exact
+    // multicomplex activation to the FP32 form
     d->plan_prec = -1;
+    if (prec != DAE_FP32) d->cs_exact = 0;
     d->plan_split[0].clear(); d->plan_split[1].clear();
     d->plan_rep[0].clear(); d->plan_rep[1].clear();
     if (prec == DAE_BF16 || prec == DAE_BF16X3) {
@@ -2740,6 +2783,16 @@ dae_status dae_free_mesh(dae_mesh* m) {
     return DAE_OK;
 }
 
+dae_status dae_decoder_set_cs_mode(dae_decoder* d, int exact) {
+    if (!d) return DAE_ERR_INVALID_ARG;
+    if (exact && (d->prec != DAE_FP32 || d->r > kMaxRExact || d->np > 0))
+        return fail(d->ctx, DAE_ERR_UNSUPPORTED,
+                    "the exact multicomplex activation runs in the FP32 form, r <= %d, no linear basis",
+                    kMaxRExact);
+    d->cs_exact = exact ? 1 : 0;
+    return DAE_OK;
+}
+
 dae_status dae_eval_derivs(dae_ctx* ctx, const dae_decoder* dec_c, const double* q,
                            const double* qbar, const double* qbar_dot, double dt, float* u,
                            float* J, float* Hqq, float* dJ, float* Hw, float* Sdd) {
@@ -2767,16 +2820,21 @@ dae_status dae_eval_derivs(dae_ctx* ctx, const dae_decoder* dec_c, const double*
     const double h = std::ldexp(1.0, -20);
     Outs o;
     o.u = du; o.J = dJo; o.Hqq = dHqq; o.dJ = ddJ;
-    if (du || dJo || dHqq || ddJ) TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_FULL, o));
+    const bool exact = d->cs_exact && d->prec == DAE_FP32;
+    auto fwd = [&](int mode, const Outs& oo) {
+        return exact ? enqueue_forward_exact(d, dq, dt, h, mode, oo)
+                     : enqueue_forward(d, nullptr, dq, dt, h, mode, oo);
+    };
+    if (du || dJo || dHqq || ddJ) TRY(fwd(SEED_FULL, o));
     if (dHw) {
         Outs o2;
         o2.dJ = dHw;
-        TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_HW, o2));
+        TRY(fwd(SEED_HW, o2));
     }
     if (dSdd) {
         Outs o3;
         o3.dJ = dSdd;
-        TRY(enqueue_forward(d, nullptr, dq, dt, h, SEED_SDD, o3));
+        TRY(fwd(SEED_SDD, o3));
     }
     TRY(st.finish());
     if (st.any_host) return check_device_status(ctx);

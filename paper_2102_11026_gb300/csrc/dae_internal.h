@@ -27,6 +27,16 @@ namespace dae {
 constexpr int kShared = 4;
 __host__ __device__ inline int n_cols(int r) { return kShared + 3 * r; }
 __host__ __device__ inline int pad_cols(int r) { return (n_cols(r) + 15) / 16 * 16; }
+// Exact (untruncated) multicomplex columns, an ablation of the shared-column form: column
+// 0 the unperturbed input (u = D(q)), columns 1-3 the number q + h Delta (i2 + i3) as
+// [real, i2 (= i3), i2i3] (H[D,D]), then per latent direction j six columns at
+// kSharedX + 6j: the tricomplex number q + h e_j i1 + h Delta (i2 + i3) + h^2 w i2i3 as
+// [real, i1, i2 (= i3), i1i2 (= i1i3), i2i3, i1i2i3]; every group carries its own real
+// part (which differs from D(q) by O(h^2)).
+constexpr int kSharedX = 4;
+__host__ __device__ inline int n_cols_exact(int r) { return kSharedX + 6 * r; }
+__host__ __device__ inline int pad_cols_exact(int r) { return (n_cols_exact(r) + 15) / 16 * 16; }
+constexpr int kMaxRExact = 17;   // 6r + 4 columns within the FP32 kernel's 112
 constexpr int kMaxR = 32;
 constexpr int kRowTile = 128;     // output rows per tile (tcgen05 M, SIMT uses 64)
 constexpr int kKPad = 64;         // K padding (128 bytes of BF16)
@@ -108,6 +118,8 @@ struct Workspace {
     int Cp = 0, C = 0;
     size_t ldx_max = 0;            // max padded width over all layer inputs/outputs
     float* X[2] = {nullptr, nullptr};             // FP32 activations [Cp][ld]
+    float* Xe[2] = {nullptr, nullptr};            // exact multicomplex columns [Cpx][ld] (on demand)
+    int Cpx = 0;
     __nv_bfloat16* Xh[2] = {nullptr, nullptr};    // BF16 hi [Cp][ld]
     __nv_bfloat16* Xl[2] = {nullptr, nullptr};    // BF16 lo [Cp][ld]
     std::vector<float*> S1;        // per hidden layer: act'(z) [n]
@@ -273,6 +285,7 @@ struct dae_decoder {
     // dae_decoder_autotune / dae_decoder_set_chain_plan for the precision in plan_prec.
     std::vector<int> plan_split[2], plan_rep[2];
     int plan_prec = -1;
+    int cs_exact = 0;               // dae_eval_derivs with the exact multicomplex activation
 };
 
 struct dae_mesh {
@@ -331,6 +344,7 @@ struct FwdArgs {
     // the cubature rows' u and J in compact form instead of at their DOFs (null: at the
     // DOFs): Jc[0][i] = u, Jc[1 + j][i] = J e_j for stacked row i < n_map, stride ldc
     float* Jc; int ldc;
+    int exact;                               // 1: exact multicomplex columns (n_cols_exact)
 };
 
 // off: the decoder's coordinates start at entry off of the state (the linear subspace's
@@ -340,6 +354,10 @@ void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override
                  int r, int Cp, int ld0, float* X, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
                  int out_bf16, float* zvec, int off = 0);
 void launch_fwd_simt(cudaStream_t s, const FwdArgs& a);
+// Input columns of the exact multicomplex batch (layout at n_cols_exact; modes as
+// launch_seed).
+void launch_seed_exact(cudaStream_t s, const double* q, const double* qbar, const double* qbar_dot,
+                       double dt, double h, int mode, int r, int Cp, int ld0, float* X);
 bool launch_fwd_tc(cudaStream_t s, const FwdArgs& a, dae_prec prec, int sm_count);
 
 // Persistent layer-chain kernel (k_chain.cu): one job per GEMM layer.

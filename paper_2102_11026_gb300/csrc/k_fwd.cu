@@ -2,6 +2,7 @@
 // layer GEMM with the fused multicomplex activation / output epilogue.
 #include "dae_internal.h"
 #include "epilogue.cuh"
+#include "multicomplex.cuh"
 
 namespace dae {
 
@@ -65,6 +66,95 @@ void launch_seed(cudaStream_t s, const NewtonState* ns, const double* q_override
                                           ld0, X, Xh, Xl, out_bf16, zvec, off);
 }
 
+// Exact multicomplex columns (layout at n_cols_exact): column 0 = q; the number
+// q + h c (i2 + i3) in columns 1-3; per direction j the number
+// q + h e_j i1 + h c (i2 + i3) + h^2 g i2i3, c = Delta (0 in SEED_HW), g = w (0 in SEED_SDD).
+__global__ void k_seed_exact(const double* q, const double* qbar, const double* qbar_dot, double dt,
+                             double h, int mode, int r, int Cp, int ld0, float* X) {
+    const int C = n_cols_exact(r);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Cp * ld0; idx += gridDim.x * blockDim.x) {
+        const int c = idx / ld0, k = idx % ld0;
+        double v = 0.0;
+        if (k < r && c < C) {
+            const double D = q[k] - qbar[k];
+            const double w = 3.0 * D - dt * qbar_dot[k];
+            const double hc = (mode == SEED_HW) ? 0.0 : h * D;
+            const double hg = (mode == SEED_SDD) ? 0.0 : h * h * w;
+            if (c == 0 || c == 1) {
+                v = q[k];
+            } else if (c == 2) {
+                v = hc;
+            } else if (c >= kSharedX) {
+                const int j = (c - kSharedX) / 6, comp = (c - kSharedX) % 6;
+                if (comp == 0) v = q[k];
+                else if (comp == 1) v = (j == k) ? h : 0.0;
+                else if (comp == 2) v = hc;
+                else if (comp == 4) v = hg;
+            }
+        }
+        X[(size_t)c * ld0 + k] = (float)v;
+    }
+}
+
+void launch_seed_exact(cudaStream_t s, const double* q, const double* qbar, const double* qbar_dot,
+                       double dt, double h, int mode, int r, int Cp, int ld0, float* X) {
+    const int n = Cp * ld0;
+    k_seed_exact<<<(n + 255) / 256, 256, 0, s>>>(q, qbar, qbar_dot, dt, h, mode, r, Cp, ld0, X);
+}
+
+// Exact multicomplex epilogue of one row (hidden layer: the activation of every number
+// in the row, outputs in the same layout; output layer: u, J, H[D,D] and dJ from the
+// linear layer's components).
+__device__ void exact_row(const FwdArgs& A, const float* v, int n, int grp) {
+    using namespace mc;
+    const int r = A.r;
+    if (!A.last) {
+        const size_t ldy = A.ldy;
+        float* Y = A.Y;
+        if (n >= A.n_out) {
+            for (int c = grp; c < A.Cp; c += 4) Y[(size_t)c * ldy + n] = 0.f;
+            return;
+        }
+        const float b = A.bias[n];
+        if (grp == 0) {
+            Y[n] = act(A.act, v[0] + b);
+            // q + h c (i2 + i3): (re + i2 c) + i3 (c + i2 g)
+            const C2 z{C1{v[1] + b, v[2]}, C1{v[2], v[3]}};
+            const C2 o = act(A.act, z);
+            Y[ldy + n] = o.x.x;
+            Y[2 * ldy + n] = o.x.y;
+            Y[3 * ldy + n] = o.y.y;
+            for (int cc = n_cols_exact(r); cc < A.Cp; ++cc) Y[(size_t)cc * ldy + n] = 0.f;
+        }
+        for (int j = grp; j < r; j += 4) {
+            const int cb = kSharedX + 6 * j;
+            // [real, i1, i2, i1i2, i2i3, i1i2i3] with i3 = i2 and i1i3 = i1i2
+            const C3 z{C2{C1{v[cb] + b, v[cb + 2]}, C1{v[cb + 2], v[cb + 4]}},
+                       C2{C1{v[cb + 1], v[cb + 3]}, C1{v[cb + 3], v[cb + 5]}}};
+            const C3 o = act(A.act, z);
+            Y[(size_t)cb * ldy + n] = o.x.x.x;
+            Y[(size_t)(cb + 1) * ldy + n] = o.y.x.x;
+            Y[(size_t)(cb + 2) * ldy + n] = o.x.x.y;
+            Y[(size_t)(cb + 3) * ldy + n] = o.y.x.y;
+            Y[(size_t)(cb + 4) * ldy + n] = o.x.y.y;
+            Y[(size_t)(cb + 5) * ldy + n] = o.y.y.y;
+        }
+    } else {
+        if (n >= A.n_out) return;
+        const size_t N = A.n_out;
+        if (grp == 0) {
+            if (A.u) A.u[n] = v[0] + A.bias[n];
+            if (A.HDD) A.HDD[n] = (float)(v[3] * A.inv_h2);
+            if (A.Hqq) A.Hqq[n] = (float)(v[3] * A.inv_h2 * A.inv_dt2);
+        }
+        for (int j = grp; j < r; j += 4) {
+            const int cb = kSharedX + 6 * j;
+            if (A.J) A.J[(size_t)j * N + n] = (float)(v[cb + 1] * A.inv_h);
+            if (A.dJ) A.dJ[(size_t)j * N + n] = (float)(v[cb + 5] * A.inv_h3);
+        }
+    }
+}
+
 // ------------------------------------------------------- CUDA-core GEMM --
 // Tile: 64 output rows x Cp component columns, K step 32, 256 threads; thread
 // (ty, tx) accumulates rows 4ty..4ty+3 and columns tx + 16 i.
@@ -91,6 +181,10 @@ __device__ void simt_epilogue(const FwdArgs& A, float (*tile)[16 * NC + 1], int 
     const int n = m0 + row;
     const int r = A.r, C = n_cols(r);
     const float* v = tile[row];
+    if (A.exact) {
+        exact_row(A, v, n, grp);
+        return;
+    }
     if (!A.last) {
         if (n >= A.ldy) return;
         const size_t ldy = A.ldy;

@@ -69,6 +69,7 @@ SIGNATURES = {
     "dae_load_decoder": ([_vp, _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp)], _i),
     "dae_free_decoder": ([_vp], _i),
     "dae_decoder_set_precision": ([_vp, _i], _i),
+    "dae_decoder_set_cs_mode": ([_vp, _i], _i),
     "dae_decoder_get_chain_plan": ([_vp, _i, _vp, _vp], _i),
     "dae_decoder_set_chain_plan": ([_vp, _i, _vp, _vp], _i),
     "dae_decoder_autotune": ([_vp, _i, _vp], _i),
@@ -210,6 +211,12 @@ def dae_free_decoder(dec):
 
 def dae_decoder_set_precision(ctx, dec, prec):
     _check(ctx, lib().dae_decoder_set_precision(dec, PREC[prec]))
+
+
+def dae_decoder_set_cs_mode(ctx, dec, exact):
+    """True: dae_eval_derivs evaluates the activation in exact multicomplex arithmetic
+    (FP32 form only); False: the truncated shared-column form."""
+    _check(ctx, lib().dae_decoder_set_cs_mode(dec, 1 if exact else 0))
 
 
 def dae_decoder_get_chain_plan(ctx, dec, n_hidden, direction):
