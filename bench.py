@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--wnet", action="store_true",
                     help="predict the cubature weights with a weight network (N-64-64-64-n_tet)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the tile autotuner on the decoder before timing (set-up, untimed)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the grouped-strings and training-pass records of the default line")
     ap.add_argument("--no-forms", action="store_true",
@@ -314,6 +316,9 @@ def run_ours(args):
     dec = dae.dae_load_decoder(ctx, d.widths, d.W, d.b, d.act, args.prec)
     mesh = dae.dae_load_mesh(ctx, m.X.reshape(-1), m.tets.reshape(-1), m.vmass, m.material,
                              m.E, m.nu)
+    tuned = None
+    if getattr(args, "autotune", False) and args.prec != "fp32":
+        tuned = [round(x, 4) for x in dae.dae_decoder_autotune(ctx, dec, reps=20)]
     if args.wnet:
         from paper_2102_11026_gb300 import synth
         net = synth.make_wnet(d.n_out, m.n_tet, 7)
@@ -510,7 +515,9 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic",
-        "config": workload_config(args, wl, K, full_all, flops, ms, world),
+        "config": dict(workload_config(args, wl, K, full_all, flops, ms, world),
+                       tile_plan="autotuned (forward ms before/after, reverse before/after: %s)" % tuned
+                       if tuned else "built-in"),
         "rates": {"newton_iterations_per_s": value, "evaluations_per_s": evals_all / (ms / 1e3),
                   "full_evaluations_per_s": full_all / (ms / 1e3),
                   "frames_per_s": K * world / (ms / 1e3)},
