@@ -316,7 +316,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) gen = *(volatile unsigned*)&gb->gen;
 
     uint32_t pk = 0;   // stage-ring position (producer and MMA walk it identically)
-    int pre_n = 0;     // producer: k-blocks of the next stage whose weights are already issued
     uint32_t it = 0;   // items taken by this CTA: accumulator it & 1, its use it >> 1
     uint32_t nred = 0; // split reductions of this CTA (rbar phases)
     const bool grouped = stage_off != nullptr;
@@ -343,12 +342,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (threadIdx.x == 0) s_base[nj] = jobs[j0 + nj - 1].item_base + jobs[j0 + nj - 1].tiles;
             __syncthreads();
-        } else if (!flow && st > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-            // the previous layer's split counters are no longer read: zero them for the
-            // next launch (counters of one launch are disjoint per layer)
-            const ChainJob& Pb = jobs[st - 1];
-            if (Pb.split > 1)
-                for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
         }
         if (warp == 0) {
             if (lane == 0 && !*(volatile int*)&fail) {
@@ -366,7 +359,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (X3) { prefetch_tmap(&Jp->tm[1]); prefetch_tmap(&Jp->tm[3]); }
                     }
                 }
-                int kc = 0;   // k-blocks of this stage so far
                 int rdy_tile = -1;   // previous layer's tile known complete (flow)
                 while (!fail && W.next(Jp, I)) {
                     const CUtensorMap* tmA = &Jp->tm[0];
@@ -379,16 +371,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (X3) { prefetch_tmap(tmAlo); prefetch_tmap(tmBlo); }
                         Jlast = Jp;
                     }
-                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk, ++kc) {
+                    for (int kb = I.kb0; kb < I.kb1; ++kb, ++pk) {
                         const int s = pk % stages;
                         const uint32_t ph = (pk / stages) & 1;
-                        if (kc < pre_n) {
-                            // weights issued ahead, before the grid barrier: the activations only
-                            uint8_t* base = smem + (size_t)s * STAGE;
-                            tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
-                            if constexpr (X3) tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
-                            continue;
-                        }
                         if (!mbar_wait(&empty[s], ph ^ 1)) { fail = 1; break; }
                         mbar_expect_tx(&full[s], STAGE);
                         uint8_t* base = smem + (size_t)s * STAGE;
@@ -412,36 +397,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tma_load_2d(base + A_BYTES, tmB, &full[s], kb * KB, 0);
                         if constexpr (X3) tma_load_2d(base + 2 * A_BYTES + B_BYTES, tmBlo, &full[s], kb * KB, 0);
                     }
-                }
-                pre_n = 0;
-                // the next layer's job header into L1 (every role reads it right after the
-                // grid barrier) and its first weight tiles into the ring
-                if (!flow && !grouped && st + 1 < n_jobs && !fail) {
-                    const ChainJob& Nb = jobs[st + 1];
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(&Nb.tiles));
-                    // the first k-blocks of the next layer's weights straight into the free
-                    // ring slots (the epilogue uses no ring slot); their activations follow
-                    // after the grid barrier
-                    {
-                        Walk Wa(Nb, blockIdx.x, G);
-                        Item Ia;
-                        if (Wa.next(Ia)) {
-                            for (int kb = Ia.kb0; kb < Ia.kb1 && pre_n < stages; ++kb) {
-                                const uint32_t kk = pk + (uint32_t)pre_n;
-                                const int s = kk % stages;
-                                if (!mbar_wait(&empty[s], ((kk / stages) & 1) ^ 1)) { fail = 1; break; }
-                                mbar_expect_tx(&full[s], STAGE);
-                                uint8_t* base = smem + (size_t)s * STAGE;
-                                tma_load_2d(base, &Nb.tm[0], &full[s], kb * KB, Ia.tl * 128);
-                                if constexpr (X3)
-                                    tma_load_2d(base + A_BYTES + B_BYTES, &Nb.tm[1], &full[s], kb * KB, Ia.tl * 128);
-                                ++pre_n;
-                            }
-                        }
-                    }
-                    // (the rest of the next layer's weights is not prefetched into L2: that
-                    // stream competed with this layer's split-K exchange through L2, and the
-                    // large layers stream at the rate of their CTAs' pipelines either way)
                 }
             }
         } else if (warp == 1) {
@@ -749,12 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (flow && st + 1 < n_st) continue;   // each role goes on with the next layer
         __syncthreads();
-        // consecutive solo layers run on CTA 0 alone: its own CTA barrier orders them (the
-        // epilogue's stores were fenced for the next layer's TMA above)
-        const bool solo_next = !grouped && st + 1 < n_jobs && jobs[st].solo && jobs[st + 1].solo;
-        if (threadIdx.x == 0 && !solo_next) {
-            if (!grid_barrier(gb, G, gen)) fail = 1;
-        }
+        if (threadIdx.x == 0 && !grid_barrier(gb, G, gen)) fail = 1;
         __syncthreads();
         if (fail) break;
     }
@@ -776,12 +726,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (Pb.split > 1)
             for (int t = 0; t < Pb.tiles; ++t) split_cnt[Pb.cnt_off + t] = 0u;
     }
-    // drain: nothing in flight may outlive the CTA (weights issued ahead for a stage that
-    // did not run have no activation loads: their bytes are counted as done)
+    // drain: nothing in flight may outlive the CTA
     if (warp == 0 && lane == 0) {
-        for (int i = 0; i < pre_n; ++i)
-            mbar_complete_tx(&full[(pk + (uint32_t)i) % stages], B_BYTES * (X3 ? 2u : 1u));
-        const uint32_t end = pk + (uint32_t)pre_n;
+        const uint32_t end = pk;
         for (uint32_t k = (end > (uint32_t)stages ? end - stages : 0); k < end; ++k)
             if (!mbar_wait(&full[k % stages], (k / stages) & 1)) fail = 1;
     }
