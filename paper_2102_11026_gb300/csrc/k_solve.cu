@@ -71,7 +71,7 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
     return i * r - i * (i - 1) / 2 + (j - i);
 }
 
-// Solve A x = b in FP64 accuracy (r <= 32, A column-major FP64 in global memory) by
+// Solve A x = b in FP64 accuracy (r <= 32, A column-major FP64, in shared memory) by
 // mixed-precision iterative refinement (Wilkinson; Moler 1967): LU with partial
 // pivoting of the FP32-rounded A, then x <- x + U^{-1} L^{-1} P (b - A x) with the
 // residual formed in FP64.  Each correction shrinks the error by about
@@ -86,6 +86,7 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
 // Called by the 128 threads of warps 0-3.  Returns 0, or DAE_ERR_SINGULAR when an
 // FP32 pivot is below 2^-20 max|A| (such A are beyond what the FP32 factors resolve).
 constexpr int kRefine = 3;
+constexpr int kCtlThreads = 256;   // threads of k_control (its assembly assumes this count)
 
 // One warp: d = U^{-1} L^{-1} P b in FP32 with the factors of mixed_solve (lane i holds
 // row i of the factors, the step ps at which it was the pivot, and b_i); returns d_i on
@@ -178,8 +179,21 @@ __device__ int mixed_solve(const double* A, const double* b, double* x, int r, f
         const int p = s_p;
         const bool act = lane < r && !((s_used >> lane) & 1u);
         const float l = act ? F[lane][k] * rinv[k] : 0.f;
-        if (act)
-            for (int j = k + 1 + warp; j < r; j += 4) F[lane][j] = fmaf(-l, F[p][j], F[lane][j]);
+        if (act) {
+            // this thread's (<= 8) columns: every operand load in flight before the stores
+            // (row p is not written at step k, row `lane` only by its own threads)
+            float fp[kMaxR / 4], fl[kMaxR / 4];
+#pragma unroll
+            for (int u = 0; u < kMaxR / 4; ++u) {
+                const int j = k + 1 + warp + 4 * u;
+                if (j < r) { fp[u] = F[p][j]; fl[u] = F[lane][j]; }
+            }
+#pragma unroll
+            for (int u = 0; u < kMaxR / 4; ++u) {
+                const int j = k + 1 + warp + 4 * u;
+                if (j < r) F[lane][j] = fmaf(-l, fp[u], fl[u]);
+            }
+        }
         asm volatile("bar.sync 2, 128;" ::: "memory");
         if (warp == 0 && act) F[lane][k] = l;
         __syncwarp();
@@ -405,6 +419,7 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     __shared__ double x[kMaxR];
     __shared__ int nonfinite;
     __shared__ double sbwd[(kMaxR + 1) * kMaxR];
+    __shared__ double sA[kMaxR * kMaxR];   // A for the solve's residuals
     __shared__ __align__(8) NewtonState S;
     const int r = C.r;
     const double dt2 = C.dt * C.dt;
@@ -432,27 +447,44 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
         sbwd[e] = acc;
     }
     __syncthreads();
-    for (int e = t; e < r * r; e += blockDim.x) {
-        const int i = e % r, j = e / r;   // column-major (i, j)
-        double ah = 0.0, mr, b = 0.0;
-        if (i >= np && j >= np) {
-            const int qi = i - np, qj = j - np;
-            ah = 0.5 * inv_h * (sbwd[(1 + qj) * rq + qi] + sbwd[(1 + qi) * rq + qj]);
-            mr = C.rowsum[rq + upper_idx(qi, qj, rq)];
-            b = C.rowsum[rq + nsq + qi * rq + qj];
-        } else if (i < np && j < np) {
-            mr = (double)C.UMU[i * np + j];              // U^T M U
-        } else if (i < np) {
-            mr = lv.umj(i, j - np);                      // U^T M [J + dJ]
-            b = lv.umdj(i, j - np);
-        } else {
-            mr = lv.umj(j, i - np);                      // J^T M U
+    // thread t assembles the elements e = t + kCtlThreads u: every term of its elements
+    // is loaded before the first store (the column sums and the terms are disjoint
+    // regions of one buffer, which the compiler cannot tell)
+    constexpr int kAsmIt = (kMaxR * kMaxR + kCtlThreads - 1) / kCtlThreads;
+    double v_ah[kAsmIt], v_mr[kAsmIt], v_b[kAsmIt], v_kr[kAsmIt];
+#pragma unroll
+    for (int u = 0; u < kAsmIt; ++u) {
+        const int e = t + kCtlThreads * u;
+        double ah = 0.0, mr = 0.0, b = 0.0, kr = 0.0;
+        if (e < r * r) {
+            const int i = e % r, j = e / r;   // column-major (i, j)
+            if (i >= np && j >= np) {
+                const int qi = i - np, qj = j - np;
+                ah = 0.5 * inv_h * (sbwd[(1 + qj) * rq + qi] + sbwd[(1 + qi) * rq + qj]);
+                mr = C.rowsum[rq + upper_idx(qi, qj, rq)];
+                b = C.rowsum[rq + nsq + qi * rq + qj];
+            } else if (i < np && j < np) {
+                mr = (double)C.UMU[i * np + j];              // U^T M U
+            } else if (i < np) {
+                mr = lv.umj(i, j - np);                      // U^T M [J + dJ]
+                b = lv.umdj(i, j - np);
+            } else {
+                mr = lv.umj(j, i - np);                      // J^T M U
+            }
+            if (C.have_cub) kr = C.cubsum[r + upper_idx(i, j, r)];
         }
-        const double kr = C.have_cub ? C.cubsum[r + upper_idx(i, j, r)] : 0.0;
-        const double a = ah + mr + b + dt2 * kr;
-        aH[e] = ah; Mr[e] = mr; Bm[e] = b; Kr[e] = kr;
-        A[e] = a;
-        if (!isfinite(a)) nonfinite = 1;
+        v_ah[u] = ah; v_mr[u] = mr; v_b[u] = b; v_kr[u] = kr;
+    }
+#pragma unroll
+    for (int u = 0; u < kAsmIt; ++u) {
+        const int e = t + kCtlThreads * u;
+        if (e < r * r) {
+            const double a = v_ah[u] + v_mr[u] + v_b[u] + dt2 * v_kr[u];
+            aH[e] = v_ah[u]; Mr[e] = v_mr[u]; Bm[e] = v_b[u]; Kr[e] = v_kr[u];
+            A[e] = a;
+            sA[e] = a;
+            if (!isfinite(a)) nonfinite = 1;
+        }
     }
     if (!C.control) {
         for (int i = t; i < r; i += blockDim.x)
@@ -474,7 +506,7 @@ __device__ __forceinline__ void control_impl(const CtlArgs& C) {
     if (nonfinite) {
         if (t == 0) lu_st = DAE_ERR_NONFINITE;
     } else if (t < 128) {
-        const int st0 = mixed_solve(A, rhs, x, r, C.lu);
+        const int st0 = mixed_solve(sA, rhs, x, r, C.lu);
         if (t == 0) lu_st = st0;
     }
     __syncthreads();
@@ -594,7 +626,7 @@ void launch_control(cudaStream_t s, const AsmArgs& a) {
     DsumArgs ds;
     CtlArgs c;
     assemble_parts(a, cs, ds, c);
-    k_control<<<1, 256, 0, s>>>(c);
+    k_control<<<1, kCtlThreads, 0, s>>>(c);
 }
 
 // Grouped form: z = system; the column sums in y (an empty sum skips), then the energy
@@ -622,7 +654,7 @@ void launch_decide_batched(cudaStream_t s, const ColsumArgs* cs, const DsumArgs*
 
 void launch_control_batched(cudaStream_t s, const CtlArgs* c, int n_sys) {
     if (n_sys <= 0) return;
-    k_control_b<<<n_sys, 256, 0, s>>>(c);
+    k_control_b<<<n_sys, kCtlThreads, 0, s>>>(c);
 }
 
 // --------------------------------------------------------- frame control --
