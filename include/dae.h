@@ -160,8 +160,9 @@ dae_status dae_decoder_set_precision(dae_decoder* dec, dae_prec prec);
  * layer's K loop over the P CTAs (split = P, rep = 1; at least two 64-element k-blocks
  * per CTA) or as P replicated K loops (split = 1, rep = P); each CTA finishes 128/P
  * rows.  A small layer (at most 8 tiles and 64 tile k-blocks) may also run solo
- * (split = 1, rep = 0): all its tiles on CTA 0 while the other CTAs skip it; no grid
- * barrier separates consecutive solo layers.  A plan is per precision: a precision
+ * (split = 1, rep = 0): all its tiles on CTA 0 while the other CTAs skip it; a run of
+ * consecutive solo layers hands its activations from layer to layer inside CTA 0.  A
+ * plan is per precision: a precision
  * change returns to the built-in plan.
  * These are scheduling choices only; the paper has no counterpart (its passes are
  * cuBLAS GEMMs, Sec. 6). */

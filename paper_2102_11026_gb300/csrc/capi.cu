@@ -2458,8 +2458,9 @@ dae_status dae_decoder_autotune(dae_decoder* d, int reps, double* ms) {
                 if (t < 0.99 * best) { best = t; jobs = trial; }
             }
         }
-        // runs of consecutive small layers on CTA 0 alone at either end of the chain (one
-        // solo layer still pays its grid barriers; a run skips those between its layers)
+        // runs of consecutive small layers on CTA 0 alone at either end of the chain (a run
+        // hands its activations from layer to layer inside CTA 0, with no wait on other
+        // CTAs' ready counters between its layers)
         auto solo_ok = [&](const ChainJob& j) {
             for (auto c : plan_candidates(j, G)) if (c.second == 0) return true;
             return false;
