@@ -78,11 +78,12 @@ __device__ __forceinline__ int upper_idx(int i, int j, int r) {
 // kappa(A) r eps_32, so kRefine corrections reach FP64 rounding for the reduced
 // Newton matrices (kappa ~ 1e1 - 1e3).  FP64 issue is scarce on this part (each
 // dependent FP64 operation costs ~100 cycles; an FP64 LU took ~60 us of latency),
-// while the FP32 factorisation is one warp with no barriers.
-//   LU: lane i of warp 0 holds row i in registers; per column k the warp picks the
-//   pivot row among the rows not yet used (largest |.|, lowest index on ties)
-//   without swapping rows, broadcasts it lane to lane, stores the multipliers in
-//   place and updates its row (fully unrolled over the <= 32 columns).
+// so the factorisation runs in FP32.
+//   LU: the FP32-rounded A in shared memory, row i in row i; per column k warp 0 picks
+//   the pivot row among the rows not yet used (largest |.|, lowest index on ties)
+//   without swapping rows, the 128 threads update the other unused rows' columns
+//   right of k, and the multipliers replace column k.  Warp 0 then holds row i of the
+//   factors in lane i's registers for the triangular solves.
 // Called by the 128 threads of warps 0-3.  Returns 0, or DAE_ERR_SINGULAR when an
 // FP32 pivot is below 2^-20 max|A| (such A are beyond what the FP32 factors resolve).
 constexpr int kRefine = 3;
