@@ -14,10 +14,10 @@
 // partial tiles (bulk copies), wait for one another and bulk-load the partners' slices
 // of their own rows into the spare rows of the staging tile before summing.  Either way each of
 // the P CTAs of a tile finishes 128/P rows, so the activation epilogue of a layer is
-// spread over tiles x P CTAs instead of one CTA per tile.  While a layer's epilogue
-// runs, the producer issues the weight half of the next layer's first k-blocks into the
-// free ring slots (weights do not depend on the layer in flight); after the grid
-// barrier it adds only the activation half of those slots.
+// spread over tiles x P CTAs instead of one CTA per tile.  The producer issues each
+// k-block's weight half at once (weights do not depend on the layer in flight) and its
+// activation half once the tile that wrote those rows is complete, so a CTA's next
+// layer streams while its own epilogue of the layer before still runs.
 //
 // Roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5 epilogue.
 // The accumulator is staged through a shared-memory tile so the MMA of the next
