@@ -657,7 +657,7 @@ std::vector<std::pair<int, int>> plan_candidates(const ChainJob& j, int grid) {
         c.push_back({1, P});
         if (P >= 2 && j.nk >= 2 * P) c.push_back({P, 1});
     }
-    // small layers on CTA 0 alone (no grid barrier between consecutive ones)
+    // small layers on CTA 0 alone (the other CTAs skip them)
     if (j.tiles <= 8 && j.tiles * j.nk <= 64) c.push_back({1, 0});
     return c;
 }

@@ -374,8 +374,8 @@ struct ChainJob {
     int stream;                  // 1: equal k-block ranges per CTA (output layer, mode 1)
     int item_base;               // grouped stage: position of this job's first tile in the
                                  // stage's item list (jobs of one stage are consecutive)
-    int solo;                    // 1: every tile of the layer on CTA 0 (split = rep = 1); no
-                                 // grid barrier between consecutive solo layers
+    int solo;                    // 1: every tile of the layer on CTA 0 (split = rep = 1); the
+                                 // other CTAs skip the layer
     int raw;                     // stream job whose items are stored unfinished (raw_m slots
     int raw_m;                   // per CTA in the launch's split_part) for k_out_finish
     float* raw_part;             // raw job: the items' slots
