@@ -3223,17 +3223,11 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     fill_opts(opts_in, &opts);
     const int r = d->np + d->r;   // system size
     Stage st(ctx);
-    st.need(q, r * 8); st.need(qdot, r * 8);
-    st.need(q_traj, (size_t)n_frames * r * 8);
-    TRY(st.reserve(st.plan));
-    double *dq, *dqd, *dtraj;
-    TRY(st.inout(q, r, &dq, true));
-    TRY(st.inout(qdot, r, &dqd, true));
-    TRY(st.inout(q_traj, (size_t)n_frames * r, &dtraj, false));
     Workspace& w = d->ws;
     TRY(ensure_frames(d, n_frames));
-    CU(ctx, cudaMemcpyAsync(w.qbar, dq, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    CU(ctx, cudaMemcpyAsync(w.qbar_dot, dqd, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    // the state straight into the frame state and back (host or device memory alike)
+    CU(ctx, cudaMemcpyAsync(w.qbar, q, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(w.qbar_dot, qdot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
     const int* dct = nullptr;
     const float* dcw = nullptr;
     TRY(stage_cubature(d, st, n_cub, cub_tets, cub_w, n_cub * n_frames, &dct, &dcw));
@@ -3252,18 +3246,22 @@ dae_status dae_rollout(dae_ctx* ctx, const dae_decoder* dec_c, const dae_mesh* m
     P.wnet = cub_w ? 0 : 1;
     if (n_frames > 0) TRY(run_frames(d, m, P, n_frames, 0, 1, nullptr));
     CU(ctx, cudaGetLastError());
-    CU(ctx, cudaMemcpyAsync(dq, w.qbar, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    CU(ctx, cudaMemcpyAsync(dqd, w.qbar_dot, r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    if (dtraj && n_frames > 0)
-        CU(ctx, cudaMemcpyAsync(dtraj, w.traj, (size_t)n_frames * r * sizeof(double),
-                                cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(q, w.qbar, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(qdot, w.qbar_dot, r * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    if (q_traj && n_frames > 0)
+        CU(ctx, cudaMemcpyAsync(q_traj, w.traj, (size_t)n_frames * r * sizeof(double),
+                                cudaMemcpyDefault, ctx->stream));
     ctx->last_ns = n_frames > 0 ? w.hist + (n_frames - 1) : nullptr;
-    TRY(st.finish());
+    if (!(reports && n_frames > 0)) {
+        // host outputs are complete when the call returns (device ones stay asynchronous)
+        if (!on_device(q) || !on_device(qdot) || (q_traj && !on_device(q_traj)))
+            CU(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     if (reports && n_frames > 0) {
         std::vector<NewtonState> hs(n_frames);
         CU(ctx, cudaMemcpyAsync(hs.data(), w.hist, n_frames * sizeof(NewtonState),
                                 cudaMemcpyDeviceToHost, ctx->stream));
-        TRY(check_device_status(ctx));
+        TRY(check_device_status(ctx));   // one wait for every copy above
         int worst = 0;
         for (int f = 0; f < n_frames; ++f) {
             to_report(hs[f], &reports[f]);
