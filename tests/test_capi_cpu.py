@@ -77,3 +77,101 @@ def test_every_entry_point_rejects_null_handles():
         checked += 1
     assert checked >= 25
     assert L.dae_last_error(None) == b"null context"
+
+
+# ----------------------------------------------------------------------------
+# The binding's ctypes signatures and structures against the header's prototypes:
+# a parameter count, an operand kind or a field out of step would pass arguments or
+# read reports wrongly without any error, so both are read from include/dae.h.
+
+def _header_source():
+    src = open(os.path.join(ROOT, "include", "dae.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return re.sub(r"//[^\n]*", "", src)
+
+
+_SCALARS = {"int": ctypes.c_int, "dae_status": ctypes.c_int, "dae_prec": ctypes.c_int,
+            "dae_act": ctypes.c_int, "dae_material": ctypes.c_int, "unsigned": ctypes.c_uint,
+            "double": ctypes.c_double, "float": ctypes.c_float, "long long": ctypes.c_longlong,
+            "size_t": ctypes.c_size_t}
+
+
+def _c_type(decl):
+    """Type part of a parameter declaration 'const float* const* W' -> 'const float* const*'."""
+    decl = " ".join(decl.split())
+    m = re.match(r"^(.*?)\s*\b([A-Za-z_]\w*)$", decl)
+    t = m.group(1) if m and m.group(1) else decl
+    return t
+
+
+def _is_pointer_ctype(t):
+    return (t in (ctypes.c_void_p, ctypes.c_char_p) or
+            (isinstance(t, type) and issubclass(t, ctypes._Pointer)))
+
+
+def _same_scalar(t, expected):
+    floats = (ctypes.c_float, ctypes.c_double)
+    return (ctypes.sizeof(t) == ctypes.sizeof(expected) and
+            (t in floats) == (expected in floats))
+
+
+def header_prototypes():
+    out = {}
+    for ret, name, params in re.findall(
+            r"([A-Za-z_][\w \*]*?)\b(dae_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", _header_source(), flags=re.S):
+        p = params.strip()
+        out[name] = (" ".join(ret.split()), [] if p in ("", "void") else
+                     [_c_type(x) for x in p.split(",")])
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    protos = header_prototypes()
+    assert len(protos) >= 30
+    assert set(protos) == set(dae.SIGNATURES), set(protos) ^ set(dae.SIGNATURES)
+    for name, (ret, params) in protos.items():
+        args, res = dae.SIGNATURES[name]
+        assert len(args) == len(params), (name, params, args)
+        for i, (ct, a) in enumerate(zip(params, args)):
+            if "*" in ct:
+                assert _is_pointer_ctype(a), (name, i, ct, a)
+            else:
+                base = " ".join(w for w in ct.split() if w != "const")
+                assert base in _SCALARS, (name, i, ct)
+                assert not _is_pointer_ctype(a) and _same_scalar(a, _SCALARS[base]), (name, i, ct, a)
+        if ret == "void":
+            assert res is None, name
+        elif "*" in ret:
+            assert res is ctypes.c_char_p, (name, ret, res)
+        else:
+            assert res is not None and _same_scalar(res, _SCALARS[ret]), (name, ret, res)
+
+
+def header_structs():
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\w*\s*\{(.*?)\}\s*(\w+)\s*;", _header_source(),
+                                 flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if decl:
+                t = _c_type(decl)
+                fields.append((decl[len(t):].strip(), t))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_the_header():
+    structs = header_structs()
+    mirrors = {"dae_newton_opts": dae.dae_newton_opts, "dae_newton_report": dae.dae_newton_report,
+               "dae_system": dae.dae_system}
+    assert set(mirrors) <= set(structs), set(structs)
+    for name, cls in mirrors.items():
+        fields = structs[name]
+        assert [f for f, _ in fields] == [f for f, _ in cls._fields_], name
+        for (fname, ct), (_, t) in zip(fields, cls._fields_):
+            if "*" in ct:
+                assert _is_pointer_ctype(t), (name, fname, ct, t)
+            else:
+                base = " ".join(w for w in ct.split() if w != "const")
+                assert _same_scalar(t, _SCALARS[base]), (name, fname, ct, t)
